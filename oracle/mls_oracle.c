@@ -1,0 +1,317 @@
+/*
+ * FP64 CPU oracle for the moving-least-squares (MLS) field reconstruction.
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the slow, plain statement of what
+ * the CUDA path computes.  Only the tests, the smoke check and the CPU
+ * baseline leg of the benchmark load it; the library never does.  It shares
+ * no code, header, table or helper with the CUDA path.
+ *
+ * What it computes, per pixel centre p of a W x H grid over the view
+ * rectangle [x0,x1] x [y0,y1] (pixel (u,v) has centre
+ * (x0 + (u+1/2)(x1-x0)/W, y0 + (v+1/2)(y1-y0)/H), row-major, v = 0 at y0):
+ *
+ *   r_i^2 = |x_i - p|^2 over all n points x_i (Section 3.3: every pixel
+ *           depends on every data point, Section 4.5 O(whn))
+ *   w_i   = weight(r_i)          (Section 3.3, Eq. eq-weights gives the
+ *           inverse-distance form 1/r^(2 alpha); the Gaussian exp(-r^2/h^2)
+ *           and the Wendland C2 form (1-q)^4 (4q+1), q = r/rho < 1, are the
+ *           compact / smooth alternatives)
+ *   b(d)  = (1, d_x, d_y [, d_x^2, d_x d_y, d_y^2]),  d = (x_i - p)/s
+ *   M     = sum_i w_i b(d_i) b(d_i)^T,   R = sum_i w_i b(d_i) f_i^T
+ *   c     = M^{-1} R,   f(p) = b(0)^T c = row 0 of c
+ *
+ * This is the weighted least-squares polynomial fit evaluated at p; with the
+ * linear basis it is the paper's affine MLS (Section 3.3.2, Eq.
+ * eq-affinemls with the weighted centroids of Eqs. eq-pstar/eq-qstar), with
+ * the constant basis it is the weighted mean of Section 3.3.1 (Eq.
+ * eq-meanmls without the displacement term).  Each data dimension f_d is
+ * fitted with the same M (the values q_i of the paper are read as the
+ * point's data values).
+ *
+ * Readings where the paper is silent:
+ *  - stabilised weights: Gaussian w_i = exp(-(r_i^2 - m)/h^2) and
+ *    inverse-distance w_i = (m / r_i^2)^alpha with m = min_i r_i^2; a common
+ *    positive factor on every weight leaves c unchanged, so this is the same
+ *    fit without underflow;
+ *  - inverse distance with a point exactly at p: f(p) is the mean value of
+ *    the points at p (the limit of Section 3.3.1 / criterion 2 of Section 3.3);
+ *  - degenerate pixels: with k basis terms, if fewer than k points carry a
+ *    positive weight (Gaussian and inverse distance: all n points count;
+ *    Wendland: points with r < rho), or the Cholesky factorisation of the
+ *    diagonally equilibrated Me = S M S (S = diag(M_aa^{-1/2})) fails, or
+ *    rcond_1(Me) = 1/(|Me|_1 |Me^{-1}|_1) < rcond_min, the next lower degree
+ *    is tried (2 -> 1 -> 0); with no point in support the value is NaN;
+ *  - iso-bands (Section 3.4, discrete colours): band_d = #{j : t_dj <= f_d},
+ *    255 for NaN.
+ *
+ * Build: gcc -O2 -fopenmp -ffp-contract=off -shared -fPIC (contraction off so
+ * that the x86 and Arm builds round identically).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define OR_GAUSS 0
+#define OR_WENDLAND 1
+#define OR_INVDIST 2
+
+/* Basis term a of degree <= 2 evaluated at (dx, dy). */
+static double basis_term(int a, double dx, double dy) {
+    switch (a) {
+    case 0: return 1.0;
+    case 1: return dx;
+    case 2: return dy;
+    case 3: return dx * dx;
+    case 4: return dx * dy;
+    default: return dy * dy;
+    }
+}
+
+static int n_terms(int degree) { return (degree + 1) * (degree + 2) / 2; }
+
+/* Cholesky of a k x k symmetric matrix A (row-major) into lower L.
+ * Returns 0 on success, -1 if a pivot is not positive. */
+static int cholesky(int k, const double *A, double *L) {
+    memset(L, 0, sizeof(double) * k * k);
+    for (int j = 0; j < k; ++j) {
+        double s = A[j * k + j];
+        for (int t = 0; t < j; ++t) s -= L[j * k + t] * L[j * k + t];
+        if (!(s > 0.0)) return -1;
+        double ljj = sqrt(s);
+        L[j * k + j] = ljj;
+        for (int i = j + 1; i < k; ++i) {
+            double v = A[i * k + j];
+            for (int t = 0; t < j; ++t) v -= L[i * k + t] * L[j * k + t];
+            L[i * k + j] = v / ljj;
+        }
+    }
+    return 0;
+}
+
+/* Solve L L^T x = b in place. */
+static void chol_solve(int k, const double *L, double *x) {
+    for (int i = 0; i < k; ++i) {
+        double v = x[i];
+        for (int t = 0; t < i; ++t) v -= L[i * k + t] * x[t];
+        x[i] = v / L[i * k + i];
+    }
+    for (int i = k - 1; i >= 0; --i) {
+        double v = x[i];
+        for (int t = i + 1; t < k; ++t) v -= L[t * k + i] * x[t];
+        x[i] = v / L[i * k + i];
+    }
+}
+
+static double norm1(int k, const double *A) {
+    double best = 0.0;
+    for (int j = 0; j < k; ++j) {
+        double s = 0.0;
+        for (int i = 0; i < k; ++i) s += fabs(A[i * k + j]);
+        if (s > best) best = s;
+    }
+    return best;
+}
+
+/*
+ * Evaluate the MLS fit for a list of pixels.
+ *
+ *   xy       n x 2 positions (row-major), F n x D values (row-major)
+ *   degree   0, 1 or 2; weight OR_*; h = Gaussian h / Wendland radius /
+ *            inverse-distance basis scale; alpha = inverse-distance exponent
+ *   pix      npix pixel indices v*W+u (NULL: all W*H pixels in order)
+ *   field    out, npix x D
+ *   deg_used out, npix (-1: no point in support, value NaN)
+ *   rcond    out, npix: rcond_1(Me) at the degree used (1 for degree 0,
+ *            0 when no degree was usable)
+ *   count    out, npix: points with positive weight under the rule above
+ *   mstab    out, npix: m = min_i r_i^2 (0 for Wendland)
+ *   amb      out, npix: bit 0 set when an rcond tested lay within a factor
+ *            amb_factor of rcond_min; bit 1 set when a Wendland point lay
+ *            within a relative amb_boundary of the support radius and could
+ *            move the count across a k threshold.  Optional (NULL).
+ * Returns 0, or -1 on bad arguments.
+ */
+int oracle_mls(int64_t n, int32_t D, const double *xy, const double *F,
+               int32_t degree, int32_t weight, double h, double alpha,
+               int32_t W, int32_t H, double x0, double y0, double x1, double y1,
+               int64_t npix, const int64_t *pix, double rcond_min,
+               double amb_factor, double amb_boundary,
+               double *field, int8_t *deg_used, double *rcond_out,
+               int64_t *count_out, double *mstab_out, uint8_t *amb,
+               int32_t nthreads) {
+    if (n < 1 || D < 1 || degree < 0 || degree > 2 || !(h > 0.0) || W < 1 || H < 1)
+        return -1;
+    if (weight != OR_GAUSS && weight != OR_WENDLAND && weight != OR_INVDIST) return -1;
+    if (pix == NULL) npix = (int64_t)W * H;
+    const double sx = (x1 - x0) / (double)W;
+    const double sy = (y1 - y0) / (double)H;
+    const double inv_s = 1.0 / h;
+    const double h2 = h * h;
+    const double rho2 = h * h;
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel
+#endif
+    {
+        double *wt = (double *)malloc(sizeof(double) * (size_t)n);
+        double *r2 = (double *)malloc(sizeof(double) * (size_t)n);
+        double M[36], R6[6 * 256], Me[36], L[36], Minv[36], col[6];
+        double *Rbuf = (D <= 256) ? R6 : (double *)malloc(sizeof(double) * 6 * (size_t)D);
+#ifdef _OPENMP
+#pragma omp for schedule(dynamic, 16)
+#endif
+        for (int64_t q = 0; q < npix; ++q) {
+            const int64_t id = pix ? pix[q] : q;
+            const int64_t u = id % W, v = id / W;
+            const double px = x0 + ((double)u + 0.5) * sx;
+            const double py = y0 + ((double)v + 0.5) * sy;
+            double *out = field + q * D;
+
+            /* squared distances and the stabiliser m = min r^2 */
+            double m = INFINITY;
+            for (int64_t i = 0; i < n; ++i) {
+                const double dx = xy[2 * i] - px, dy = xy[2 * i + 1] - py;
+                r2[i] = dx * dx + dy * dy;
+                if (r2[i] < m) m = r2[i];
+            }
+            int64_t count = 0, nboundary = 0;
+            int coincident = 0;
+            for (int64_t i = 0; i < n; ++i) {
+                double w;
+                if (weight == OR_GAUSS) {
+                    w = exp(-(r2[i] - m) / h2);
+                    count++;
+                } else if (weight == OR_WENDLAND) {
+                    const double qd = sqrt(r2[i]) / h;
+                    if (r2[i] < rho2) {
+                        const double t = 1.0 - qd;
+                        w = t * t * t * t * (4.0 * qd + 1.0);
+                        count++;
+                    } else {
+                        w = 0.0;
+                    }
+                    if (fabs(r2[i] / rho2 - 1.0) < amb_boundary) nboundary++;
+                } else {
+                    if (m == 0.0) {
+                        w = (r2[i] == 0.0) ? 1.0 : 0.0;
+                        coincident = 1;
+                    } else {
+                        w = pow(m / r2[i], alpha);
+                    }
+                    count++;
+                }
+                wt[i] = w;
+            }
+            if (mstab_out) mstab_out[q] = (weight == OR_WENDLAND) ? 0.0 : m;
+            if (count_out) count_out[q] = count;
+            uint8_t ambq = 0;
+
+            int used = -1;
+            double rc_used = 0.0;
+            if (coincident) {
+                /* inverse distance, pixel centre on a data point: mean value */
+                double sw = 0.0;
+                for (int d = 0; d < D; ++d) out[d] = 0.0;
+                for (int64_t i = 0; i < n; ++i) {
+                    if (wt[i] == 0.0) continue;
+                    sw += 1.0;
+                    for (int d = 0; d < D; ++d) out[d] += F[i * D + d];
+                }
+                for (int d = 0; d < D; ++d) out[d] /= sw;
+                used = 0;
+                rc_used = 1.0;
+            } else {
+                for (int deg = degree; deg >= 0 && used < 0; --deg) {
+                    const int k = n_terms(deg);
+                    if (weight == OR_WENDLAND && nboundary > 0 &&
+                        count - nboundary < k && k <= count + nboundary)
+                        ambq |= 2;
+                    if (count < k) continue;
+                    memset(M, 0, sizeof(M));
+                    memset(Rbuf, 0, sizeof(double) * (size_t)k * D);
+                    for (int64_t i = 0; i < n; ++i) {
+                        const double w = wt[i];
+                        if (w == 0.0) continue;
+                        const double dx = (xy[2 * i] - px) * inv_s;
+                        const double dy = (xy[2 * i + 1] - py) * inv_s;
+                        double b[6];
+                        for (int a = 0; a < k; ++a) b[a] = basis_term(a, dx, dy);
+                        for (int a = 0; a < k; ++a) {
+                            for (int c = 0; c < k; ++c) M[a * k + c] += w * b[a] * b[c];
+                            for (int d = 0; d < D; ++d) Rbuf[a * D + d] += w * b[a] * F[i * D + d];
+                        }
+                    }
+                    /* equilibrate, factor, condition */
+                    int ok = 1;
+                    double sdiag[6];
+                    for (int a = 0; a < k; ++a) {
+                        if (!(M[a * k + a] > 0.0)) { ok = 0; break; }
+                        sdiag[a] = 1.0 / sqrt(M[a * k + a]);
+                    }
+                    double rc = 0.0;
+                    if (ok) {
+                        for (int a = 0; a < k; ++a)
+                            for (int c = 0; c < k; ++c) Me[a * k + c] = M[a * k + c] * sdiag[a] * sdiag[c];
+                        if (cholesky(k, Me, L) != 0) ok = 0;
+                    }
+                    if (ok) {
+                        for (int c = 0; c < k; ++c) {
+                            for (int a = 0; a < k; ++a) col[a] = (a == c) ? 1.0 : 0.0;
+                            chol_solve(k, L, col);
+                            for (int a = 0; a < k; ++a) Minv[a * k + c] = col[a];
+                        }
+                        rc = 1.0 / (norm1(k, Me) * norm1(k, Minv));
+                        if (rc >= rcond_min / amb_factor && rc <= rcond_min * amb_factor) ambq |= 1;
+                        if (!(rc >= rcond_min)) ok = 0;
+                    } else if (deg > 0) {
+                        /* a failed factorisation is the singular end of the scale */
+                        rc = 0.0;
+                    }
+                    if (!ok) continue;
+                    /* f_d = row 0 of M^{-1} R, M^{-1} = S Me^{-1} S */
+                    for (int d = 0; d < D; ++d) {
+                        double acc = 0.0;
+                        for (int c = 0; c < k; ++c)
+                            acc += sdiag[0] * Minv[0 * k + c] * sdiag[c] * Rbuf[c * D + d];
+                        out[d] = acc;
+                    }
+                    used = deg;
+                    rc_used = rc;
+                }
+                if (used < 0)
+                    for (int d = 0; d < D; ++d) out[d] = NAN;
+            }
+            if (deg_used) deg_used[q] = (int8_t)used;
+            if (rcond_out) rcond_out[q] = rc_used;
+            if (amb) amb[q] = ambq;
+        }
+        if (Rbuf != R6) free(Rbuf);
+        free(wt);
+        free(r2);
+    }
+    return 0;
+}
+
+/*
+ * Iso-band labels (Section 3.4, discrete colours): for each pixel and
+ * dimension, the number of levels t_dj (ascending, D x L) with t_dj <= f_d;
+ * 255 when f_d is NaN.  field and bands are npix x D.
+ */
+int oracle_bands(int64_t npix, int32_t D, const double *field, const double *levels,
+                 int32_t L, uint8_t *bands) {
+    if (npix < 0 || D < 1 || L < 0 || L > 254) return -1;
+    for (int64_t q = 0; q < npix; ++q)
+        for (int d = 0; d < D; ++d) {
+            const double f = field[q * D + d];
+            if (isnan(f)) { bands[q * D + d] = 255; continue; }
+            int c = 0;
+            for (int j = 0; j < L; ++j)
+                if (levels[d * L + j] <= f) c++;
+            bands[q * D + d] = (uint8_t)c;
+        }
+    return 0;
+}
