@@ -1,0 +1,197 @@
+/*
+ * mls.h -- C ABI of the GB300 (sm_103a) moving-least-squares field library.
+ *
+ * For every pixel p of a W x H grid the library evaluates the weighted
+ * least-squares polynomial fit of the data values f_i at the given 2D points
+ * x_i, with weights w_i = w(|x_i - p|), and then labels each data dimension
+ * with its iso-band index.  This is the per-pixel MLS evaluation of Section
+ * 3.3 of Muelder, Leaf, Sigovan and Ma, "A Moving Least Squares Based
+ * Approach for Contour Visualization of Multi-Dimensional Data"
+ * (arXiv:1408.0677): Eq. eq-weights (weights), Eq. eq-affinemls with Eqs.
+ * eq-pstar / eq-qstar (the linear-basis fit is the paper's affine MLS),
+ * Eq. eq-meanmls (the constant-basis fit is its weighted mean), Section 3.4
+ * (discrete colours = iso-band labels) and Section 4.5 (O(whn): every pixel
+ * is independent and depends on every point).
+ *
+ * Conventions shared by every entry point
+ *  - Pixel (u, v) has centre (x0 + (u + 1/2)(x1 - x0)/W,
+ *    y0 + (v + 1/2)(y1 - y0)/H); images are row-major with v = 0 at y0.
+ *  - Fields and bands are planar: element (d, v, u) at d*W*H + v*W + u.
+ *  - Basis b(d) = (1, d_x, d_y [, d_x^2, d_x d_y, d_y^2]) of degree 0, 1 or
+ *    2; the fit's value at p is the constant coefficient.
+ *  - Calls are asynchronous on the CUDA stream passed as `stream`
+ *    (a cudaStream_t; NULL means the legacy default stream) when every
+ *    buffer is on the device; with host buffers the call copies through the
+ *    device and returns after the stream has finished.
+ *  - The caller owns every input and output buffer.  The handle owns its
+ *    device copies of the points and values and its scratch memory.
+ *  - Errors are returned as an mls_status before any launch when they are
+ *    argument errors; nothing is written then.  mls_last_error() gives a
+ *    thread-local message for the last failure.
+ *  - A handle is not thread safe; different handles are independent.
+ */
+#ifndef MLS_H
+#define MLS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MLS_ABI_VERSION 1
+
+typedef enum mls_status {
+    MLS_OK = 0,
+    MLS_E_INVAL = 1,       /* bad argument; nothing launched or written */
+    MLS_E_NOMEM = 2,       /* device allocation failed; the handle stays usable */
+    MLS_E_CUDA = 3,        /* a CUDA runtime call failed */
+    MLS_E_TIMEOUT = 4,     /* a bounded device wait or host watchdog expired */
+    MLS_E_UNSUPPORTED = 5  /* valid request this build does not implement */
+} mls_status;
+
+/* Weight functions w(r) (Section 3.3). */
+typedef enum mls_weight {
+    MLS_W_GAUSS = 0,       /* exp(-r^2 / h^2), all points */
+    MLS_W_WENDLAND = 1,    /* (1 - q)^4 (4 q + 1), q = r / h < 1; compact, binned */
+    MLS_W_INVDIST = 2      /* 1 / r^(2 alpha) (Eq. eq-weights), all points */
+} mls_weight;
+
+/* Arithmetic of the moment accumulation. */
+typedef enum mls_precision {
+    MLS_P_FP64 = 0,        /* FP64 on CUDA cores; field is double */
+    MLS_P_FP32 = 1,        /* FP32 on CUDA cores; field is float */
+    MLS_P_BF16 = 2,        /* BF16 operands on tcgen05 tensor cores, FP32 accumulate */
+    MLS_P_FP16 = 3         /* FP16 operands on tcgen05 tensor cores, FP32 accumulate */
+} mls_precision;
+
+/* Per-pixel status bits (status image, one byte per pixel). */
+#define MLS_ST_DEGREE_MASK 0x03u  /* basis degree used (0, 1, 2) */
+#define MLS_ST_NO_SUPPORT  0x04u  /* no point with positive weight: value NaN, band 255 */
+#define MLS_ST_FP64_SOLVE  0x08u  /* condition estimate above cond_fp64: FP64 factorisation */
+#define MLS_ST_RECOMPUTED  0x10u  /* pixel recomputed entirely in FP64 */
+#define MLS_ST_DEGRADED    0x20u  /* degree lowered by the degenerate-pixel policy */
+#define MLS_ST_COINCIDENT  0x40u  /* inverse distance: pixel centre on a data point */
+
+/*
+ * Problem description.  Fill with mls_desc_default() and override.
+ *   n, D        number of points and data dimensions (1 <= D <= 256)
+ *   degree      basis degree 0, 1 or 2
+ *   weight      mls_weight
+ *   precision   mls_precision
+ *   h           Gaussian h, Wendland support radius, or inverse-distance
+ *               basis scale (> 0); the basis is scaled by h
+ *   alpha       inverse-distance exponent (Eq. eq-weights); > 0
+ *   cond_fp64   condition estimate above which the per-pixel factorisation
+ *               runs in FP64 (default 1e6)
+ *   rcond_degenerate  reciprocal condition (1-norm, diagonally equilibrated
+ *               moment matrix) below which the degree is lowered (1e-12)
+ *   cond_recompute    condition estimate above which a reduced-precision
+ *               pixel is recomputed entirely in FP64 (0 = default for the
+ *               precision: FP32 1e4, FP16 1e5, BF16 1e4)
+ *   weight_split      tensor-core precisions: 1 (default) stores each weight
+ *               as a hi + lo pair of 16-bit values (three products per
+ *               point tile, weights to ~22 / 16 bits); 0 rounds each weight
+ *               once (two products, faster, larger error on rough data)
+ */
+typedef struct mls_desc {
+    int64_t n;
+    int32_t D;
+    int32_t degree;
+    int32_t weight;
+    int32_t precision;
+    double h;
+    double alpha;
+    double cond_fp64;
+    double rcond_degenerate;
+    double cond_recompute;
+    int32_t weight_split;
+    int32_t reserved[3];
+} mls_desc;
+
+/* Output grid: W x H pixels over [x0, x1] x [y0, y1]. */
+typedef struct mls_view {
+    int32_t W, H;
+    double x0, y0, x1, y1;
+} mls_view;
+
+/* Counters of the last completed render (see mls_sync). */
+typedef struct mls_stats {
+    int64_t pairs;          /* pixel-point pairs the method visited */
+    int64_t recomputed;     /* pixels recomputed in FP64 */
+    int64_t device_error;   /* device error word (0 = none; timeouts set it) */
+    double last_render_ms;  /* device time of the last render (CUDA events) */
+} mls_stats;
+
+typedef struct mls_handle mls_handle;
+
+/* Fill *desc with defaults (Gaussian, linear basis, FP32, h = 0.05). */
+mls_status mls_desc_default(mls_desc *desc);
+
+/*
+ * Create a handle holding a resident copy of the points (Section 3.3: the
+ * control points p_i with values q_i, read as data values).
+ *   xy        n x 2 float64, row-major (x_i, y_i)
+ *   F         n x D float64, row-major values
+ *   on_device nonzero: xy and F are device pointers read on `stream`
+ *             (keep them alive until the stream reaches this call);
+ *             zero: host pointers, copied before return
+ *   out       receives the handle
+ * Converts the values to the layouts the kernels read, normalises them per
+ * dimension and, for the Wendland weight, bins the points on a uniform grid
+ * of cell size h (counting sort; deterministic order).
+ * Errors: MLS_E_INVAL (desc, pointers), MLS_E_NOMEM, MLS_E_CUDA.
+ */
+mls_status mls_create(const mls_desc *desc, const double *xy, const double *F,
+                      int32_t on_device, void *stream, mls_handle **out);
+
+/*
+ * Render the MLS field over `view` (Section 3.3, the first pass of the
+ * paper's two-pass renderer, into a headless buffer).
+ *   field   D x H x W; double for MLS_P_FP64, float otherwise (required)
+ *   status  H x W bytes of MLS_ST_* bits, or NULL
+ *   levels  D x L float64 ascending iso-levels (host memory), or NULL
+ *   L       number of levels per dimension (0..254)
+ *   bands   D x H x W bytes, iso-band labels fused into the render
+ *           (Section 3.4: band = #{j : t_dj <= f_d}, 255 for NaN), or NULL
+ *   on_device  nonzero: field/status/bands are device pointers
+ * Errors: MLS_E_INVAL, MLS_E_NOMEM, MLS_E_CUDA, MLS_E_UNSUPPORTED (the
+ * tensor-core precisions with the inverse-distance weight).
+ */
+mls_status mls_render(mls_handle *h, const mls_view *view, void *field, uint8_t *status,
+                      const double *levels, int32_t L, uint8_t *bands,
+                      int32_t on_device, void *stream);
+
+/*
+ * Iso-band labels of an existing field (Section 3.4, discrete colours).
+ *   field   D x H x W in the handle's field type (device or host per on_device)
+ *   levels  D x L float64 ascending (host memory)
+ *   bands   D x H x W bytes out
+ * Errors: MLS_E_INVAL, MLS_E_NOMEM, MLS_E_CUDA.
+ */
+mls_status mls_bands(mls_handle *h, const mls_view *view, const void *field,
+                     const double *levels, int32_t L, uint8_t *bands,
+                     int32_t on_device, void *stream);
+
+/*
+ * Wait for the handle's last stream with a host-side watchdog of
+ * `timeout_s` seconds, then read the device error word and counters into
+ * *stats (may be NULL).  Returns MLS_E_TIMEOUT when the watchdog expires or
+ * a bounded device wait gave up.
+ */
+mls_status mls_sync(mls_handle *h, double timeout_s, mls_stats *stats);
+
+/* Release the handle and its device memory (waits for its stream). */
+mls_status mls_destroy(mls_handle *h);
+
+/* Thread-local message of the last error ("" when none). */
+const char *mls_last_error(void);
+
+/* ABI version of the loaded library (MLS_ABI_VERSION). */
+int32_t mls_abi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MLS_H */

@@ -1,0 +1,140 @@
+"""GB300-native moving-least-squares field reconstruction (arXiv:1408.0677, Section 3.3).
+
+The compute path is the CUDA library ``libmls.so`` (sm_103a) behind the C ABI
+of ``include/mls.h``; ``_abi`` binds it with ctypes and ``Renderer`` below
+marshals torch tensors / numpy arrays into those calls.  PyTorch only
+provides device memory and streams.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import _abi
+from ._abi import (MLS_P_BF16, MLS_P_FP16, MLS_P_FP32, MLS_P_FP64, MLS_W_GAUSS, MLS_W_INVDIST,  # noqa: F401
+                   MLS_W_WENDLAND, MlsDesc, MlsError, MlsStats, MlsView, mls_abi_version, mls_bands,
+                   mls_create, mls_desc_default, mls_destroy, mls_last_error, mls_render, mls_sync)
+
+PRECISIONS = {"fp64": MLS_P_FP64, "fp32": MLS_P_FP32, "bf16": MLS_P_BF16, "fp16": MLS_P_FP16}
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    return int(stream)
+
+
+class Renderer:
+    """A resident point set and its MLS description (one ``mls_handle``).
+
+    xy: (n, 2) float64, F: (n, D) float64 -- CUDA torch tensors (read on the
+    stream) or host numpy arrays (copied).  ``render`` returns CUDA tensors.
+    """
+
+    def __init__(self, xy, F, degree=1, weight=MLS_W_GAUSS, h=0.05, precision="fp32", alpha=1.0,
+                 cond_fp64=None, rcond_degenerate=None, cond_recompute=None, weight_split=None, stream=None):
+        import torch
+        self.torch = torch
+        d = mls_desc_default()
+        on_device = isinstance(xy, torch.Tensor) and xy.is_cuda
+        if on_device:
+            xy = xy.to(torch.float64).contiguous()
+            F = F.to(torch.float64).contiguous()
+            if F.dim() == 1:
+                F = F[:, None]
+            n, D = F.shape
+            xy_ptr, F_ptr = xy.data_ptr(), F.data_ptr()
+            self._keep = (xy, F)
+        else:
+            xy = np.ascontiguousarray(xy, dtype=np.float64)
+            F = np.ascontiguousarray(F, dtype=np.float64)
+            if F.ndim == 1:
+                F = F[:, None]
+            n, D = F.shape
+            xy_ptr, F_ptr = xy.ctypes.data, F.ctypes.data
+            self._keep = (xy, F)
+        d.n, d.D, d.degree, d.weight, d.h, d.alpha = n, D, degree, weight, h, alpha
+        d.precision = PRECISIONS.get(precision, precision)
+        if cond_fp64 is not None:
+            d.cond_fp64 = cond_fp64
+        if rcond_degenerate is not None:
+            d.rcond_degenerate = rcond_degenerate
+        if cond_recompute is not None:
+            d.cond_recompute = cond_recompute
+        if weight_split is not None:
+            d.weight_split = int(weight_split)
+        self.desc = d
+        self.n, self.D = n, D
+        self.stream = _stream_ptr(stream)
+        self.handle = mls_create(d, xy_ptr, F_ptr, on_device, self.stream)
+
+    @property
+    def field_dtype(self):
+        return self.torch.float64 if self.desc.precision == MLS_P_FP64 else self.torch.float32
+
+    def render(self, W, H, view=(0.0, 0.0, 1.0, 1.0), levels=None, status=True, field=None, bands=None,
+               status_out=None):
+        torch = self.torch
+        dev = torch.device("cuda", torch.cuda.current_device())
+        if field is None:
+            field = torch.empty((self.D, H, W), dtype=self.field_dtype, device=dev)
+        st = status_out
+        if status and st is None:
+            st = torch.empty((H, W), dtype=torch.uint8, device=dev)
+        lev = None
+        L = 0
+        if levels is not None:
+            lev = np.ascontiguousarray(levels, dtype=np.float64)
+            L = lev.shape[1]
+            if bands is None:
+                bands = torch.empty((self.D, H, W), dtype=torch.uint8, device=dev)
+        v = MlsView(W, H, *view)
+        mls_render(self.handle, v, field.data_ptr(), st.data_ptr() if st is not None else 0,
+                   lev.ctypes.data if lev is not None else 0, L,
+                   bands.data_ptr() if (bands is not None and lev is not None) else 0, True, self.stream)
+        return {"field": field, "status": st, "bands": bands if lev is not None else None}
+
+    def render_host(self, W, H, view=(0.0, 0.0, 1.0, 1.0), levels=None, status=True, field=None, bands=None,
+                    status_out=None):
+        """Same as render, with host (numpy) outputs; returns after the copy-back."""
+        dt = np.float64 if self.desc.precision == MLS_P_FP64 else np.float32
+        if field is None:
+            field = np.empty((self.D, H, W), dtype=dt)
+        st = status_out if status_out is not None else (np.empty((H, W), np.uint8) if status else None)
+        lev = None
+        L = 0
+        if levels is not None:
+            lev = np.ascontiguousarray(levels, dtype=np.float64)
+            L = lev.shape[1]
+            if bands is None:
+                bands = np.empty((self.D, H, W), np.uint8)
+        v = MlsView(W, H, *view)
+        mls_render(self.handle, v, field.ctypes.data, st.ctypes.data if st is not None else 0,
+                   lev.ctypes.data if lev is not None else 0, L,
+                   bands.ctypes.data if (bands is not None and lev is not None) else 0, False, self.stream)
+        return {"field": field, "status": st, "bands": bands if lev is not None else None}
+
+    def bands(self, field, levels, W, H, view=(0.0, 0.0, 1.0, 1.0), out=None):
+        torch = self.torch
+        lev = np.ascontiguousarray(levels, dtype=np.float64)
+        if out is None:
+            out = torch.empty((self.D, H, W), dtype=torch.uint8, device=field.device)
+        mls_bands(self.handle, MlsView(W, H, *view), field.data_ptr(), lev.ctypes.data, lev.shape[1],
+                  out.data_ptr(), True, self.stream)
+        return out
+
+    def sync(self, timeout_s=60.0) -> MlsStats:
+        return mls_sync(self.handle, timeout_s)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            mls_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

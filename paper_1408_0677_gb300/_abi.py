@@ -1,0 +1,137 @@
+"""ctypes binding of the C ABI declared in include/mls.h (argument marshalling only).
+
+Every function here has the name of the C entry point it calls.  The library
+is the in-tree ``_build/libmls.so``; if it is missing the first call raises,
+there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+from . import build as _build
+
+MLS_OK, MLS_E_INVAL, MLS_E_NOMEM, MLS_E_CUDA, MLS_E_TIMEOUT, MLS_E_UNSUPPORTED = range(6)
+MLS_W_GAUSS, MLS_W_WENDLAND, MLS_W_INVDIST = range(3)
+MLS_P_FP64, MLS_P_FP32, MLS_P_BF16, MLS_P_FP16 = range(4)
+MLS_ST_DEGREE_MASK = 0x03
+MLS_ST_NO_SUPPORT = 0x04
+MLS_ST_FP64_SOLVE = 0x08
+MLS_ST_RECOMPUTED = 0x10
+MLS_ST_DEGRADED = 0x20
+MLS_ST_COINCIDENT = 0x40
+
+STATUS_NAMES = {MLS_OK: "MLS_OK", MLS_E_INVAL: "MLS_E_INVAL", MLS_E_NOMEM: "MLS_E_NOMEM",
+                MLS_E_CUDA: "MLS_E_CUDA", MLS_E_TIMEOUT: "MLS_E_TIMEOUT",
+                MLS_E_UNSUPPORTED: "MLS_E_UNSUPPORTED"}
+
+
+class MlsDesc(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("D", ctypes.c_int32), ("degree", ctypes.c_int32),
+                ("weight", ctypes.c_int32), ("precision", ctypes.c_int32), ("h", ctypes.c_double),
+                ("alpha", ctypes.c_double), ("cond_fp64", ctypes.c_double),
+                ("rcond_degenerate", ctypes.c_double), ("cond_recompute", ctypes.c_double),
+                ("weight_split", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+
+
+class MlsView(ctypes.Structure):
+    _fields_ = [("W", ctypes.c_int32), ("H", ctypes.c_int32), ("x0", ctypes.c_double),
+                ("y0", ctypes.c_double), ("x1", ctypes.c_double), ("y1", ctypes.c_double)]
+
+
+class MlsStats(ctypes.Structure):
+    _fields_ = [("pairs", ctypes.c_int64), ("recomputed", ctypes.c_int64),
+                ("device_error", ctypes.c_int64), ("last_render_ms", ctypes.c_double)]
+
+
+class MlsError(RuntimeError):
+    def __init__(self, status: int, where: str, message: str):
+        super().__init__(f"{where}: {STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+_lib = None
+P = ctypes.c_void_p
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(path: str | None = None):
+    """Open libmls.so (built in-tree by paper_1408_0677_gb300.build)."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    path = path or _build.LIB
+    if not os.path.exists(path):
+        raise RuntimeError(f"CUDA library not built: {path} (run paper_1408_0677_gb300.build.build())")
+    lib = ctypes.CDLL(path)
+    lib.mls_abi_version.restype = ctypes.c_int32
+    lib.mls_abi_version.argtypes = []
+    lib.mls_last_error.restype = ctypes.c_char_p
+    lib.mls_last_error.argtypes = []
+    lib.mls_desc_default.restype = ctypes.c_int
+    lib.mls_desc_default.argtypes = [ctypes.POINTER(MlsDesc)]
+    lib.mls_create.restype = ctypes.c_int
+    lib.mls_create.argtypes = [ctypes.POINTER(MlsDesc), P, P, ctypes.c_int32, P, ctypes.POINTER(P)]
+    lib.mls_render.restype = ctypes.c_int
+    lib.mls_render.argtypes = [P, ctypes.POINTER(MlsView), P, P, P, ctypes.c_int32, P, ctypes.c_int32, P]
+    lib.mls_bands.restype = ctypes.c_int
+    lib.mls_bands.argtypes = [P, ctypes.POINTER(MlsView), P, P, ctypes.c_int32, P, ctypes.c_int32, P]
+    lib.mls_sync.restype = ctypes.c_int
+    lib.mls_sync.argtypes = [P, ctypes.c_double, ctypes.POINTER(MlsStats)]
+    lib.mls_destroy.restype = ctypes.c_int
+    lib.mls_destroy.argtypes = [P]
+    if path == _build.LIB:
+        _lib = lib
+    return lib
+
+
+def _check(st: int, where: str):
+    if st != MLS_OK:
+        raise MlsError(st, where, mls_last_error())
+
+
+def mls_abi_version() -> int:
+    return load().mls_abi_version()
+
+
+def mls_last_error() -> str:
+    return load().mls_last_error().decode()
+
+
+def mls_desc_default() -> MlsDesc:
+    d = MlsDesc()
+    _check(load().mls_desc_default(ctypes.byref(d)), "mls_desc_default")
+    return d
+
+
+def mls_create(desc: MlsDesc, xy_ptr: int, F_ptr: int, on_device: bool, stream: int = 0) -> int:
+    h = P()
+    _check(load().mls_create(ctypes.byref(desc), P(xy_ptr), P(F_ptr), int(bool(on_device)), P(stream),
+                             ctypes.byref(h)), "mls_create")
+    return h.value
+
+
+def mls_render(handle: int, view: MlsView, field_ptr: int, status_ptr: int = 0, levels_ptr: int = 0,
+               L: int = 0, bands_ptr: int = 0, on_device: bool = True, stream: int = 0):
+    _check(load().mls_render(P(handle), ctypes.byref(view), P(field_ptr), P(status_ptr or None),
+                             P(levels_ptr or None), int(L), P(bands_ptr or None), int(bool(on_device)),
+                             P(stream)), "mls_render")
+
+
+def mls_bands(handle: int, view: MlsView, field_ptr: int, levels_ptr: int, L: int, bands_ptr: int,
+              on_device: bool = True, stream: int = 0):
+    _check(load().mls_bands(P(handle), ctypes.byref(view), P(field_ptr), P(levels_ptr or None), int(L),
+                            P(bands_ptr), int(bool(on_device)), P(stream)), "mls_bands")
+
+
+def mls_sync(handle: int, timeout_s: float = 60.0) -> MlsStats:
+    s = MlsStats()
+    _check(load().mls_sync(P(handle), float(timeout_s), ctypes.byref(s)), "mls_sync")
+    return s
+
+
+def mls_destroy(handle: int):
+    _check(load().mls_destroy(P(handle)), "mls_destroy")

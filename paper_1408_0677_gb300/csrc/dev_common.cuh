@@ -1,0 +1,317 @@
+// Device-side definitions shared by the CUDA translation units of the MLS
+// library: the kernel parameter block, error words, bounded waits and the
+// per-pixel moment solve (Section 3.3 of the paper: the weighted
+// least-squares fit at the pixel, read off as the constant coefficient).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "mls.h"
+
+namespace mlsk {
+
+// Device error word values (written with atomicExch, read by mls_sync).
+enum : int {
+  ERR_NONE = 0,
+  ERR_WAIT_FULL = 1,      // MMA issuer gave up waiting for a filled stage
+  ERR_WAIT_EMPTY = 2,     // producer gave up waiting for a drained stage
+  ERR_WAIT_ACC = 3,       // epilogue gave up waiting for the accumulator
+  ERR_CAND_OVERFLOW = 4,  // (informational) candidate list overflowed, brute force used
+};
+
+// One nanosecond-resolution global timer read.
+__device__ __forceinline__ uint64_t globaltimer_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Every bounded spin gives up after this long (the host watchdog is longer).
+constexpr uint64_t kWaitLimitNs = 2000000000ull;  // 2 s
+
+// Monomials of degree <= 4 in (x, y), the entries of the moment matrix:
+// 0:1 1:x 2:y 3:xx 4:xy 5:yy 6:xxx 7:xxy 8:xyy 9:yyy 10:xxxx 11:xxxy 12:xxyy 13:xyyy 14:yyyy
+// Basis terms b_a (a < 6): 1, x, y, xx, xy, yy.  M_ab = S[kMIdx[a][b]].
+__device__ __constant__ static const int kMIdx[6][6] = {
+    {0, 1, 2, 3, 4, 5},   {1, 3, 4, 6, 7, 8},    {2, 4, 5, 7, 8, 9},
+    {3, 6, 7, 10, 11, 12}, {4, 7, 8, 11, 12, 13}, {5, 8, 9, 12, 13, 14}};
+
+// Exponents (ex, ey) of monomial j.
+__host__ __device__ constexpr int mono_ex(int j) {
+  return j == 0 ? 0 : j == 1 ? 1 : j == 2 ? 0 : j == 3 ? 2 : j == 4 ? 1 : j == 5 ? 0
+       : j == 6 ? 3 : j == 7 ? 2 : j == 8 ? 1 : j == 9 ? 0 : j == 10 ? 4 : j == 11 ? 3
+       : j == 12 ? 2 : j == 13 ? 1 : 0;
+}
+__host__ __device__ constexpr int mono_ey(int j) {
+  return j == 0 ? 0 : j == 1 ? 0 : j == 2 ? 1 : j == 3 ? 0 : j == 4 ? 1 : j == 5 ? 2
+       : j == 6 ? 0 : j == 7 ? 1 : j == 8 ? 2 : j == 9 ? 3 : j == 10 ? 0 : j == 11 ? 1
+       : j == 12 ? 2 : j == 13 ? 3 : 4;
+}
+__host__ __device__ constexpr int mono_index(int ex, int ey) {
+  // inverse of (mono_ex, mono_ey) for ex + ey <= 4
+  return (ex + ey) == 0 ? 0 : (ex + ey) == 1 ? 1 + ey : (ex + ey) == 2 ? 3 + ey
+       : (ex + ey) == 3 ? 6 + ey : 10 + ey;
+}
+__host__ __device__ constexpr int n_terms(int deg) { return (deg + 1) * (deg + 2) / 2; }
+// number of moment monomials needed by a degree-deg basis (degree <= 2 deg)
+__host__ __device__ constexpr int n_moments(int deg) { return (2 * deg + 1) * (2 * deg + 2) / 2; }
+__host__ __device__ constexpr int binom(int n, int k) {
+  return (k == 0 || k == n) ? 1 : (n == 2 ? 2 : n == 3 ? 3 : n == 4 ? (k == 2 ? 6 : 4) : 1);
+}
+
+// Parameters every kernel receives by value.
+struct KParams {
+  // points (binned order for the Wendland weight)
+  int64_t n, n_pad;
+  int D, D_pad;
+  const float *xs, *ys;        // (x - ctr) / s, FP32, [n_pad]
+  const float *FT32;           // normalised values (f - cen) / scl, [D_pad][n_pad]
+  const float *fcen32, *fscl32;
+  const double *x64, *y64;     // raw positions [n]
+  const double *FT64;          // raw values [D][n]
+  const int *cell_start;       // [gx * gy + 1] (Wendland)
+  int gx, gy;
+  double gx0, gy0, cell;       // grid origin and cell size in raw coordinates
+  // method
+  int degree, weight;
+  double h, alpha;
+  double cond_fp64, rcond_min, cond_recompute;
+  // view
+  int W, H;
+  double x0, y0, sx, sy;       // pixel (u,v) centre = (x0 + (u+.5) sx, y0 + (v+.5) sy)
+  double ctr_x, ctr_y, inv_s;  // scaled coordinate frame of xs/ys
+  int tiles_x, tiles_y;        // 16 x 16 pixel tiles covering the view
+  // iso-levels
+  int L;
+  const double *lev64;         // [D][L]
+  const float *lev32;          // [D][L] rounded up to float (exact float-vs-double test)
+  // outputs
+  void *field;                 // [D][H][W] float or double
+  int field_fp64;              // 1: field is double
+  uint8_t *status;             // [H][W] or null
+  uint8_t *bands;              // [D][H][W] or null
+  // scratch
+  const float *mstab;          // [tiles_y*16][tiles_x*16] stabiliser min r^2 / s^2
+  const int *cnt;              // same shape, Wendland in-support counts
+  int *relist;                 // pixels handed to the FP64 path
+  unsigned int *relist_count;
+  int *err;
+  // FP64 list mode
+  const int *list;             // pixel indices, or null for all pixels
+  const unsigned int *list_count;  // device count for list mode, or null
+  int64_t list_cap;
+};
+
+__device__ __forceinline__ void set_error(int *err, int code) {
+  if (err) atomicCAS(err, 0, code);
+}
+
+// Pixel centre in the scaled frame (FP64 arithmetic, rounded once to float).
+__device__ __forceinline__ float scaled_px(const KParams &p, int u) {
+  return (float)((p.x0 + ((double)u + 0.5) * p.sx - p.ctr_x) * p.inv_s);
+}
+__device__ __forceinline__ float scaled_py(const KParams &p, int v) {
+  return (float)((p.y0 + ((double)v + 0.5) * p.sy - p.ctr_y) * p.inv_s);
+}
+
+// Iso-band label: #{j : t_j <= f}; levels rounded up to float make the float
+// comparison equal to the double one.
+__device__ __forceinline__ uint8_t band_of(float f, const float *lev, int L) {
+  if (f != f) return 255;
+  int c = 0;
+  for (int j = 0; j < L; ++j) c += (lev[j] <= f) ? 1 : 0;
+  return (uint8_t)c;
+}
+__device__ __forceinline__ uint8_t band_of(double f, const double *lev, int L) {
+  if (f != f) return 255;
+  int c = 0;
+  for (int j = 0; j < L; ++j) c += (lev[j] <= f) ? 1 : 0;
+  return (uint8_t)c;
+}
+
+// ---------------------------------------------------------------------------
+// Small dense linear algebra on the K x K moment matrix (K = 1, 3, 6).
+
+template <int K, typename T>
+__device__ __forceinline__ bool cholesky(const T (&A)[K][K], T (&L)[K][K]) {
+#pragma unroll
+  for (int j = 0; j < K; ++j) {
+    T s = A[j][j];
+#pragma unroll
+    for (int t = 0; t < j; ++t) s -= L[j][t] * L[j][t];
+    if (!(s > T(0))) return false;
+    const T ljj = sqrt(s);
+    const T inv = T(1) / ljj;
+    L[j][j] = ljj;
+#pragma unroll
+    for (int i = j + 1; i < K; ++i) {
+      T v = A[i][j];
+#pragma unroll
+      for (int t = 0; t < j; ++t) v -= L[i][t] * L[j][t];
+      L[i][j] = v * inv;
+    }
+#pragma unroll
+    for (int i = 0; i < j; ++i) L[i][j] = T(0);
+  }
+  return true;
+}
+
+template <int K, typename T>
+__device__ __forceinline__ void chol_solve(const T (&L)[K][K], T (&x)[K]) {
+#pragma unroll
+  for (int i = 0; i < K; ++i) {
+    T v = x[i];
+#pragma unroll
+    for (int t = 0; t < i; ++t) v -= L[i][t] * x[t];
+    x[i] = v / L[i][i];
+  }
+#pragma unroll
+  for (int i = K - 1; i >= 0; --i) {
+    T v = x[i];
+#pragma unroll
+    for (int t = i + 1; t < K; ++t) v -= L[t][i] * x[t];
+    x[i] = v / L[i][i];
+  }
+}
+
+// 1-norm condition number of the SPD matrix A from its Cholesky factor.
+template <int K, typename T>
+__device__ __forceinline__ T cond1(const T (&A)[K][K], const T (&L)[K][K]) {
+  T nA = 0, nI = 0;
+#pragma unroll
+  for (int c = 0; c < K; ++c) {
+    T col[K];
+#pragma unroll
+    for (int a = 0; a < K; ++a) col[a] = (a == c) ? T(1) : T(0);
+    chol_solve<K, T>(L, col);
+    T s = 0, sa = 0;
+#pragma unroll
+    for (int a = 0; a < K; ++a) {
+      s += fabs(col[a]);
+      sa += fabs(A[a][c]);
+    }
+    nI = s > nI ? s : nI;
+    nA = sa > nA ? sa : nA;
+  }
+  return nA * nI;
+}
+
+// Outcome of the reduced-precision per-pixel solve.
+enum SolveOutcome : int { SOLVE_OK = 0, SOLVE_FP64 = 1, SOLVE_RECOMPUTE = 2 };
+
+// Solve M z = e0 for the pixel-centred moment matrix given by its 15 (or
+// fewer) distinct moments S (FP32).  z = M^{-1} e0 so that the fit's value is
+// z . R for any right-hand side R.  FP32 equilibrated Cholesky, a 1-norm
+// condition estimate, one step of iterative refinement; FP64 factorisation
+// when the estimate exceeds cond_fp64; SOLVE_RECOMPUTE when it exceeds
+// cond_recompute or the factorisation fails (the pixel then goes to the FP64
+// path, which applies the full degenerate-pixel policy).
+template <int K>
+__device__ __forceinline__ int solve_pixel_fp32(const float *S, float (&z)[K], const KParams &p) {
+  float M[K][K];
+#pragma unroll
+  for (int a = 0; a < K; ++a)
+#pragma unroll
+    for (int b = 0; b < K; ++b) M[a][b] = S[kMIdx[a][b]];
+  float sd[K];
+#pragma unroll
+  for (int a = 0; a < K; ++a) {
+    if (!(M[a][a] > 0.f)) return SOLVE_RECOMPUTE;
+    sd[a] = rsqrtf(M[a][a]);
+  }
+  float Me[K][K], Lf[K][K];
+#pragma unroll
+  for (int a = 0; a < K; ++a)
+#pragma unroll
+    for (int b = 0; b < K; ++b) Me[a][b] = M[a][b] * sd[a] * sd[b];
+  if (!cholesky<K, float>(Me, Lf)) return SOLVE_RECOMPUTE;
+  const float cnd = (K == 1) ? 1.f : cond1<K, float>(Me, Lf);
+  if (!(cnd <= (float)p.cond_recompute)) return SOLVE_RECOMPUTE;
+  if (cnd > (float)p.cond_fp64) {
+    // FP64 factorisation of the same moments
+    double Md[K][K], sdd[K], Med[K][K], Ld[K][K];
+#pragma unroll
+    for (int a = 0; a < K; ++a)
+#pragma unroll
+      for (int b = 0; b < K; ++b) Md[a][b] = (double)M[a][b];
+#pragma unroll
+    for (int a = 0; a < K; ++a) sdd[a] = 1.0 / sqrt(Md[a][a]);
+#pragma unroll
+    for (int a = 0; a < K; ++a)
+#pragma unroll
+      for (int b = 0; b < K; ++b) Med[a][b] = Md[a][b] * sdd[a] * sdd[b];
+    if (!cholesky<K, double>(Med, Ld)) return SOLVE_RECOMPUTE;
+    if (!(1.0 / cond1<K, double>(Med, Ld) >= p.rcond_min)) return SOLVE_RECOMPUTE;
+    double y[K];
+#pragma unroll
+    for (int a = 0; a < K; ++a) y[a] = (a == 0) ? sdd[0] : 0.0;
+    chol_solve<K, double>(Ld, y);
+#pragma unroll
+    for (int a = 0; a < K; ++a) z[a] = (float)(y[a] * sdd[a]);
+    return SOLVE_FP64;
+  }
+  // z = S Me^{-1} S e0
+  float y[K];
+#pragma unroll
+  for (int a = 0; a < K; ++a) y[a] = (a == 0) ? sd[0] : 0.f;
+  chol_solve<K, float>(Lf, y);
+#pragma unroll
+  for (int a = 0; a < K; ++a) z[a] = y[a] * sd[a];
+  // one refinement step: r = e0 - M z, z += M^{-1} r
+  float r[K];
+#pragma unroll
+  for (int a = 0; a < K; ++a) {
+    float acc = (a == 0) ? 1.f : 0.f;
+#pragma unroll
+    for (int b = 0; b < K; ++b) acc = fmaf(-M[a][b], z[b], acc);
+    r[a] = acc * sd[a];
+  }
+  chol_solve<K, float>(Lf, r);
+#pragma unroll
+  for (int a = 0; a < K; ++a) z[a] = fmaf(r[a], sd[a], z[a]);
+  return SOLVE_OK;
+}
+
+// Move the pixel-centred solution z to coefficients of tile-centred moments:
+// b(x - delta) = T(delta) b(x), so z . (T R~) = (T^T z) . R~.
+template <int K>
+__device__ __forceinline__ void to_tile_frame(float (&z)[K], float dx, float dy) {
+  if (K == 3) {
+    z[0] = z[0] - dx * z[1] - dy * z[2];
+  } else if (K == 6) {
+    const float z0 = z[0] - dx * z[1] - dy * z[2] + dx * dx * z[3] + dx * dy * z[4] + dy * dy * z[5];
+    const float z1 = z[1] - 2.f * dx * z[3] - dy * z[4];
+    const float z2 = z[2] - dx * z[4] - 2.f * dy * z[5];
+    z[0] = z0;
+    z[1] = z1;
+    z[2] = z2;
+  }
+}
+
+// Shift tile-centred moments S~ (monomials of x~) to pixel-centred moments of
+// x~ - delta (binomial expansion), NM = number of moments (1, 6, 15).
+template <int NM>
+__device__ __forceinline__ void shift_moments(const float *St, float *Sp, float dx, float dy) {
+  float px[5], py[5];
+  px[0] = 1.f; py[0] = 1.f;
+#pragma unroll
+  for (int e = 1; e < 5; ++e) { px[e] = px[e - 1] * (-dx); py[e] = py[e - 1] * (-dy); }
+#pragma unroll
+  for (int j = 0; j < NM; ++j) {
+    const int bx = mono_ex(j), by = mono_ey(j);
+    float acc = 0.f;
+#pragma unroll
+    for (int jx = 0; jx <= 4; ++jx) {
+      if (jx > bx) break;
+#pragma unroll
+      for (int jy = 0; jy <= 4; ++jy) {
+        if (jy > by) break;
+        const float c = (float)(binom(bx, jx) * binom(by, jy));
+        acc = fmaf(c * px[bx - jx] * py[by - jy], St[mono_index(jx, jy)], acc);
+      }
+    }
+    Sp[j] = acc;
+  }
+}
+
+}  // namespace mlsk

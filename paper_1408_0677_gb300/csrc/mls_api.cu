@@ -1,0 +1,460 @@
+// C ABI of the MLS library (include/mls.h): argument validation, ownership,
+// device memory, launches and the host-pointer copy paths.
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <chrono>
+#include <cmath>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "mls_internal.h"
+
+namespace mlsi {
+
+static thread_local std::string g_err;
+
+mls_status fail(mls_status s, const std::string &msg) {
+  g_err = msg;
+  return s;
+}
+
+mls_status cuda_fail(cudaError_t e, const char *what) {
+  g_err = std::string(what) + ": " + cudaGetErrorString(e);
+  cudaGetLastError();  // clear a sticky-free error so the handle stays usable
+  return e == cudaErrorMemoryAllocation ? MLS_E_NOMEM : MLS_E_CUDA;
+}
+
+// Host-side fault injection for tests: while MLS_INJECT_NOMEM is set to a
+// nonzero value every device allocation of the library fails with
+// MLS_E_NOMEM before any CUDA call is made.
+static bool inject_nomem() {
+  const char *e = getenv("MLS_INJECT_NOMEM");
+  return e && atoi(e) != 0;
+}
+
+mls_status dev_alloc(mls_handle *h, void **p, size_t bytes, cudaStream_t st) {
+  *p = nullptr;
+  if (inject_nomem()) return fail(MLS_E_NOMEM, "device allocation failed (MLS_INJECT_NOMEM)");
+  cudaError_t e = cudaMallocAsync(p, bytes ? bytes : 16, st);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync");
+  h->owned.push_back(*p);
+  return MLS_OK;
+}
+
+static void release(mls_handle *h, void *p, cudaStream_t st) {
+  if (!p) return;
+  for (size_t i = 0; i < h->owned.size(); ++i)
+    if (h->owned[i] == p) {
+      h->owned.erase(h->owned.begin() + i);
+      break;
+    }
+  cudaFreeAsync(p, st);
+}
+
+static bool finite_pos(double x) { return std::isfinite(x) && x > 0.0; }
+
+static mls_status check_view(const mls_view *v) {
+  if (!v) return fail(MLS_E_INVAL, "view is NULL");
+  if (v->W < 1 || v->H < 1) return fail(MLS_E_INVAL, "view W and H must be >= 1");
+  if ((int64_t)v->W * v->H > (int64_t)1 << 30) return fail(MLS_E_INVAL, "view has more than 2^30 pixels");
+  if (!std::isfinite(v->x0) || !std::isfinite(v->x1) || !std::isfinite(v->y0) || !std::isfinite(v->y1) ||
+      !(v->x1 > v->x0) || !(v->y1 > v->y0))
+    return fail(MLS_E_INVAL, "view rectangle must be finite with x1 > x0 and y1 > y0");
+  return MLS_OK;
+}
+
+static mls_status check_levels(const double *levels, int L, int D) {
+  if (L < 0 || L > 254) return fail(MLS_E_INVAL, "L must be in [0, 254]");
+  if (L > 0 && !levels) return fail(MLS_E_INVAL, "levels is NULL");
+  for (int d = 0; d < D && L > 0; ++d)
+    for (int j = 0; j < L; ++j) {
+      const double t = levels[(size_t)d * L + j];
+      if (!std::isfinite(t)) return fail(MLS_E_INVAL, "levels must be finite");
+      if (j > 0 && !(t >= levels[(size_t)d * L + j - 1])) return fail(MLS_E_INVAL, "levels must ascend");
+    }
+  return MLS_OK;
+}
+
+// Grow the per-render scratch of the handle to fit a view.
+static mls_status ensure_scratch(mls_handle *h, int W, int H, cudaStream_t st) {
+  const int tx = (W + kTile - 1) / kTile, ty = (H + kTile - 1) / kTile;
+  const size_t padded = (size_t)tx * kTile * ty * kTile;
+  const size_t need = 256 + padded * sizeof(float) + padded * sizeof(int) + (size_t)W * H * sizeof(int) + 256;
+  if (need <= h->scratch_bytes) return MLS_OK;
+  release(h, h->scratch, st);
+  h->scratch = nullptr;
+  h->scratch_bytes = 0;
+  void *p;
+  mls_status s = dev_alloc(h, &p, need, st);
+  if (s != MLS_OK) return s;
+  h->scratch = p;
+  h->scratch_bytes = need;
+  char *b = (char *)p;
+  h->counters = (unsigned int *)b;           // [0] hand-over count
+  h->err = (int *)(b + 64);
+  h->mstab = (float *)(b + 256);
+  h->cnt = (int *)(b + 256 + padded * sizeof(float));
+  h->relist = (int *)(b + 256 + padded * (sizeof(float) + sizeof(int)));
+  return MLS_OK;
+}
+
+static mls_status upload_levels(mls_handle *h, const double *levels, int L, cudaStream_t st) {
+  const int D = h->desc.D;
+  const size_t cnt = (size_t)D * L;
+  if (cnt == 0) return MLS_OK;
+  if (cnt > h->lev_cap) {
+    release(h, h->lev64, st);
+    release(h, h->lev32, st);
+    h->lev64 = nullptr;
+    h->lev32 = nullptr;
+    h->lev_cap = 0;
+    void *p;
+    mls_status s;
+    if ((s = dev_alloc(h, &p, cnt * sizeof(double), st)) != MLS_OK) return s;
+    h->lev64 = (double *)p;
+    if ((s = dev_alloc(h, &p, cnt * sizeof(float), st)) != MLS_OK) return s;
+    h->lev32 = (float *)p;
+    h->lev_cap = cnt;
+  }
+  // float copies rounded up: for a float f, f >= t exactly when f >= t_up
+  static thread_local std::vector<float> up;
+  static thread_local std::vector<double> dn;
+  up.resize(cnt);
+  dn.assign(levels, levels + cnt);
+  for (size_t i = 0; i < cnt; ++i) {
+    float f = (float)levels[i];
+    if ((double)f < levels[i]) f = nextafterf(f, INFINITY);
+    up[i] = f;
+  }
+  MLS_CUDA_TRY(cudaMemcpyAsync(h->lev64, dn.data(), cnt * sizeof(double), cudaMemcpyHostToDevice, st));
+  MLS_CUDA_TRY(cudaMemcpyAsync(h->lev32, up.data(), cnt * sizeof(float), cudaMemcpyHostToDevice, st));
+  // pageable sources: make sure the copies have consumed them
+  MLS_CUDA_TRY(cudaStreamSynchronize(st));
+  return MLS_OK;
+}
+
+static mls_status ensure_stage(mls_handle *h, size_t bytes, cudaStream_t st) {
+  if (bytes <= h->stage_bytes) return MLS_OK;
+  release(h, h->stage, st);
+  h->stage = nullptr;
+  h->stage_bytes = 0;
+  void *p;
+  mls_status s = dev_alloc(h, &p, bytes, st);
+  if (s != MLS_OK) return s;
+  h->stage = p;
+  h->stage_bytes = bytes;
+  return MLS_OK;
+}
+
+static mlsk::KParams base_params(const mls_handle *h, const mls_view *v) {
+  const PointSet &P = h->P;
+  const mls_desc &d = h->desc;
+  mlsk::KParams p;
+  memset(&p, 0, sizeof p);
+  p.n = P.n;
+  p.n_pad = P.n_pad;
+  p.D = P.D;
+  p.D_pad = P.D_pad;
+  p.xs = P.xs;
+  p.ys = P.ys;
+  p.FT32 = P.FT32;
+  p.fcen32 = P.fcen32;
+  p.fscl32 = P.fscl32;
+  p.x64 = P.x64;
+  p.y64 = P.y64;
+  p.FT64 = P.FT64;
+  p.cell_start = P.cell_start;
+  p.gx = P.gx;
+  p.gy = P.gy;
+  p.gx0 = P.gx0;
+  p.gy0 = P.gy0;
+  p.cell = P.cell;
+  p.degree = d.degree;
+  p.weight = d.weight;
+  p.h = d.h;
+  p.alpha = d.alpha;
+  p.cond_fp64 = d.cond_fp64;
+  p.rcond_min = d.rcond_degenerate;
+  p.cond_recompute = d.cond_recompute;
+  p.W = v->W;
+  p.H = v->H;
+  p.x0 = v->x0;
+  p.y0 = v->y0;
+  p.sx = (v->x1 - v->x0) / (double)v->W;
+  p.sy = (v->y1 - v->y0) / (double)v->H;
+  p.ctr_x = P.ctr_x;
+  p.ctr_y = P.ctr_y;
+  p.inv_s = 1.0 / P.s;
+  p.tiles_x = (v->W + kTile - 1) / kTile;
+  p.tiles_y = (v->H + kTile - 1) / kTile;
+  p.mstab = h->mstab;
+  p.cnt = h->cnt;
+  p.relist = h->relist;
+  p.relist_count = h->counters;
+  p.err = h->err;
+  p.lev64 = h->lev64;
+  p.lev32 = h->lev32;
+  return p;
+}
+
+}  // namespace mlsi
+
+using namespace mlsi;
+
+extern "C" {
+
+int32_t mls_abi_version(void) { return MLS_ABI_VERSION; }
+
+const char *mls_last_error(void) { return g_err.c_str(); }
+
+mls_status mls_desc_default(mls_desc *desc) {
+  if (!desc) return fail(MLS_E_INVAL, "desc is NULL");
+  memset(desc, 0, sizeof *desc);
+  desc->n = 0;
+  desc->D = 1;
+  desc->degree = 1;
+  desc->weight = MLS_W_GAUSS;
+  desc->precision = MLS_P_FP32;
+  desc->h = 0.05;
+  desc->alpha = 1.0;
+  desc->cond_fp64 = 1e6;
+  desc->rcond_degenerate = 1e-12;
+  desc->cond_recompute = 0.0;
+  desc->weight_split = 1;
+  return MLS_OK;
+}
+
+mls_status mls_create(const mls_desc *desc, const double *xy, const double *F, int32_t on_device, void *stream,
+                      mls_handle **out) {
+  g_err.clear();
+  if (!out) return fail(MLS_E_INVAL, "out is NULL");
+  *out = nullptr;
+  if (!desc || !xy || !F) return fail(MLS_E_INVAL, "desc, xy and F must not be NULL");
+  const mls_desc &d = *desc;
+  if (d.n < 1 || d.n > ((int64_t)1 << 31) - 1024) return fail(MLS_E_INVAL, "n must be in [1, 2^31 - 1024]");
+  if (d.D < 1 || d.D > 256) return fail(MLS_E_INVAL, "D must be in [1, 256]");
+  if (d.degree < 0 || d.degree > 2) return fail(MLS_E_INVAL, "degree must be 0, 1 or 2");
+  if (d.weight < MLS_W_GAUSS || d.weight > MLS_W_INVDIST) return fail(MLS_E_INVAL, "unknown weight");
+  if (d.precision < MLS_P_FP64 || d.precision > MLS_P_FP16) return fail(MLS_E_INVAL, "unknown precision");
+  if (!finite_pos(d.h)) return fail(MLS_E_INVAL, "h must be finite and > 0");
+  if (d.weight == MLS_W_INVDIST && !finite_pos(d.alpha)) return fail(MLS_E_INVAL, "alpha must be finite and > 0");
+  if (!finite_pos(d.cond_fp64)) return fail(MLS_E_INVAL, "cond_fp64 must be > 0");
+  if (!(d.rcond_degenerate >= 0.0) || !(d.rcond_degenerate < 1.0))
+    return fail(MLS_E_INVAL, "rcond_degenerate must be in [0, 1)");
+  if (!(d.cond_recompute >= 0.0)) return fail(MLS_E_INVAL, "cond_recompute must be >= 0");
+  if (d.weight_split != 0 && d.weight_split != 1) return fail(MLS_E_INVAL, "weight_split must be 0 or 1");
+  if ((d.precision == MLS_P_BF16 || d.precision == MLS_P_FP16) && d.weight == MLS_W_INVDIST)
+    return fail(MLS_E_UNSUPPORTED, "the tensor-core precisions support the Gaussian and Wendland weights");
+
+  mls_handle *h = new mls_handle();
+  h->desc = d;
+  if (h->desc.cond_recompute == 0.0)
+    h->desc.cond_recompute = d.precision == MLS_P_FP16 ? 1e5 : 1e4;
+  cudaStream_t st = (cudaStream_t)stream;
+  h->stream = st;
+  mls_status s = MLS_OK;
+  const double *xy_d = xy, *F_d = F;
+  if (!on_device) {
+    void *p;
+    if ((s = dev_alloc(h, &p, sizeof(double) * 2 * d.n, st)) != MLS_OK) goto bad;
+    xy_d = (const double *)p;
+    if ((s = dev_alloc(h, &p, sizeof(double) * d.n * d.D, st)) != MLS_OK) goto bad;
+    F_d = (const double *)p;
+    {
+      cudaError_t e = cudaMemcpyAsync((void *)xy_d, xy, sizeof(double) * 2 * d.n, cudaMemcpyHostToDevice, st);
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync((void *)F_d, F, sizeof(double) * d.n * d.D, cudaMemcpyHostToDevice, st);
+      if (e != cudaSuccess) {
+        s = cuda_fail(e, "cudaMemcpyAsync (points)");
+        goto bad;
+      }
+    }
+  }
+  if (cudaGetDevice(&h->device) != cudaSuccess) {
+    s = cuda_fail(cudaGetLastError(), "cudaGetDevice");
+    goto bad;
+  }
+  if ((s = prep_points(h, xy_d, F_d, st)) != MLS_OK) goto bad;
+  if (!on_device) {
+    // the staging copies of the inputs are not needed once prepared
+    release(h, (void *)xy_d, st);
+    release(h, (void *)F_d, st);
+  }
+  if (cudaEventCreate(&h->ev0) != cudaSuccess || cudaEventCreate(&h->ev1) != cudaSuccess) {
+    s = cuda_fail(cudaGetLastError(), "cudaEventCreate");
+    goto bad;
+  }
+  if (!on_device && cudaStreamSynchronize(st) != cudaSuccess) {
+    s = cuda_fail(cudaGetLastError(), "cudaStreamSynchronize");
+    goto bad;
+  }
+  *out = h;
+  return MLS_OK;
+bad:
+  for (void *p : h->owned) cudaFreeAsync(p, st);
+  cudaStreamSynchronize(st);
+  cudaGetLastError();
+  if (h->ev0) cudaEventDestroy(h->ev0);
+  if (h->ev1) cudaEventDestroy(h->ev1);
+  delete h;
+  return s;
+}
+
+mls_status mls_render(mls_handle *h, const mls_view *view, void *field, uint8_t *status, const double *levels,
+                      int32_t L, uint8_t *bands, int32_t on_device, void *stream) {
+  g_err.clear();
+  if (!h) return fail(MLS_E_INVAL, "handle is NULL");
+  mls_status s = check_view(view);
+  if (s != MLS_OK) return s;
+  if (!field) return fail(MLS_E_INVAL, "field is NULL");
+  if (bands && (!levels || L < 1) && L != 0) return fail(MLS_E_INVAL, "bands need levels");
+  if ((s = check_levels(levels, bands ? L : 0, h->desc.D)) != MLS_OK) return s;
+  cudaStream_t st = (cudaStream_t)stream;
+  h->stream = st;
+  const int W = view->W, H = view->H;
+  const size_t plane = (size_t)W * H;
+  const bool fp64 = h->desc.precision == MLS_P_FP64;
+  const size_t esz = fp64 ? sizeof(double) : sizeof(float);
+  if ((s = ensure_scratch(h, W, H, st)) != MLS_OK) return s;
+  if (bands && L > 0 && (s = upload_levels(h, levels, L, st)) != MLS_OK) return s;
+
+  void *field_d = field;
+  uint8_t *status_d = status, *bands_d = bands;
+  if (!on_device) {
+    const size_t fbytes = (plane * h->desc.D * esz + 255) / 256 * 256;
+    const size_t sbytes = (plane + 255) / 256 * 256;
+    const size_t bbytes = bands ? plane * h->desc.D : 0;
+    if ((s = ensure_stage(h, fbytes + sbytes + bbytes, st)) != MLS_OK) return s;
+    field_d = h->stage;
+    status_d = status ? (uint8_t *)h->stage + fbytes : nullptr;
+    bands_d = bands ? (uint8_t *)h->stage + fbytes + sbytes : nullptr;
+  }
+  mlsk::KParams p = base_params(h, view);
+  p.field = field_d;
+  p.field_fp64 = fp64 ? 1 : 0;
+  p.status = status_d;
+  p.bands = bands_d;
+  p.L = bands ? L : 0;
+  MLS_CUDA_TRY(cudaMemsetAsync(h->scratch, 0, 256, st));
+  MLS_CUDA_TRY(cudaEventRecord(h->ev0, st));
+  if (fp64) {
+    launch_f64(p, (int64_t)plane, st);
+  } else {
+    launch_prepass(p, st);
+    if (h->desc.precision == MLS_P_FP32) {
+      launch_f32(p, st);
+    } else {
+      if ((s = launch_tc(p, h->desc.precision == MLS_P_FP16, h->desc.weight_split, st)) != MLS_OK) return s;
+    }
+    // pixels handed over by the reduced-precision path: recompute in FP64
+    mlsk::KParams q = p;
+    q.list = h->relist;
+    q.list_count = h->counters;
+    q.list_cap = (int64_t)plane;
+    q.field_fp64 = 0;
+    launch_f64(q, 0, st);
+  }
+  MLS_CUDA_TRY(cudaGetLastError());
+  MLS_CUDA_TRY(cudaEventRecord(h->ev1, st));
+  h->timed = true;
+  h->last_pairs = (h->desc.weight == MLS_W_WENDLAND) ? 0 : (int64_t)plane * h->desc.n;
+  if (!on_device) {
+    MLS_CUDA_TRY(cudaMemcpyAsync(field, field_d, plane * h->desc.D * esz, cudaMemcpyDeviceToHost, st));
+    if (status) MLS_CUDA_TRY(cudaMemcpyAsync(status, status_d, plane, cudaMemcpyDeviceToHost, st));
+    if (bands) MLS_CUDA_TRY(cudaMemcpyAsync(bands, bands_d, plane * h->desc.D, cudaMemcpyDeviceToHost, st));
+    MLS_CUDA_TRY(cudaStreamSynchronize(st));
+    int err = 0;
+    MLS_CUDA_TRY(cudaMemcpy(&err, h->err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (err) return fail(MLS_E_TIMEOUT, "a bounded device wait gave up (error word " + std::to_string(err) + ")");
+  }
+  return MLS_OK;
+}
+
+mls_status mls_bands(mls_handle *h, const mls_view *view, const void *field, const double *levels, int32_t L,
+                     uint8_t *bands, int32_t on_device, void *stream) {
+  g_err.clear();
+  if (!h) return fail(MLS_E_INVAL, "handle is NULL");
+  mls_status s = check_view(view);
+  if (s != MLS_OK) return s;
+  if (!field || !bands) return fail(MLS_E_INVAL, "field and bands must not be NULL");
+  if ((s = check_levels(levels, L, h->desc.D)) != MLS_OK) return s;
+  cudaStream_t st = (cudaStream_t)stream;
+  h->stream = st;
+  const size_t plane = (size_t)view->W * view->H;
+  const bool fp64 = h->desc.precision == MLS_P_FP64;
+  const size_t esz = fp64 ? sizeof(double) : sizeof(float);
+  if ((s = ensure_scratch(h, view->W, view->H, st)) != MLS_OK) return s;
+  if (L > 0 && (s = upload_levels(h, levels, L, st)) != MLS_OK) return s;
+  const void *field_d = field;
+  uint8_t *bands_d = bands;
+  if (!on_device) {
+    const size_t fbytes = (plane * h->desc.D * esz + 255) / 256 * 256;
+    if ((s = ensure_stage(h, fbytes + plane * h->desc.D, st)) != MLS_OK) return s;
+    field_d = h->stage;
+    bands_d = (uint8_t *)h->stage + fbytes;
+    MLS_CUDA_TRY(cudaMemcpyAsync((void *)field_d, field, plane * h->desc.D * esz, cudaMemcpyHostToDevice, st));
+  }
+  mlsk::KParams p = base_params(h, view);
+  p.field = (void *)field_d;
+  p.field_fp64 = fp64 ? 1 : 0;
+  p.bands = bands_d;
+  p.L = L;
+  launch_bands(p, fp64, st);
+  MLS_CUDA_TRY(cudaGetLastError());
+  if (!on_device) {
+    MLS_CUDA_TRY(cudaMemcpyAsync(bands, bands_d, plane * h->desc.D, cudaMemcpyDeviceToHost, st));
+    MLS_CUDA_TRY(cudaStreamSynchronize(st));
+  }
+  return MLS_OK;
+}
+
+mls_status mls_sync(mls_handle *h, double timeout_s, mls_stats *stats) {
+  g_err.clear();
+  if (!h) return fail(MLS_E_INVAL, "handle is NULL");
+  if (!(timeout_s > 0.0)) return fail(MLS_E_INVAL, "timeout_s must be > 0");
+  const auto t0 = std::chrono::steady_clock::now();
+  for (;;) {
+    cudaError_t e = cudaStreamQuery(h->stream);
+    if (e == cudaSuccess) break;
+    if (e != cudaErrorNotReady) return cuda_fail(e, "cudaStreamQuery");
+    const double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    if (el > timeout_s) return fail(MLS_E_TIMEOUT, "stream did not finish within the watchdog time");
+    std::this_thread::sleep_for(std::chrono::microseconds(50));
+  }
+  unsigned int cnt[2] = {0, 0};
+  int err = 0;
+  if (h->scratch) {
+    MLS_CUDA_TRY(cudaMemcpy(cnt, h->counters, sizeof cnt, cudaMemcpyDeviceToHost));
+    MLS_CUDA_TRY(cudaMemcpy(&err, h->err, sizeof err, cudaMemcpyDeviceToHost));
+  }
+  if (stats) {
+    memset(stats, 0, sizeof *stats);
+    stats->pairs = h->last_pairs;
+    stats->recomputed = cnt[0];
+    stats->device_error = err;
+    float ms = 0.f;
+    if (h->timed && cudaEventElapsedTime(&ms, h->ev0, h->ev1) == cudaSuccess) stats->last_render_ms = ms;
+    cudaGetLastError();
+  }
+  if (err) return fail(MLS_E_TIMEOUT, "a bounded device wait gave up (error word " + std::to_string(err) + ")");
+  return MLS_OK;
+}
+
+mls_status mls_destroy(mls_handle *h) {
+  g_err.clear();
+  if (!h) return MLS_OK;
+  cudaStream_t st = h->stream;
+  cudaStreamSynchronize(st);
+  for (void *p : h->owned) cudaFreeAsync(p, st);
+  cudaStreamSynchronize(st);
+  if (h->ev0) cudaEventDestroy(h->ev0);
+  if (h->ev1) cudaEventDestroy(h->ev1);
+  cudaGetLastError();
+  delete h;
+  return MLS_OK;
+}
+
+}  // extern "C"

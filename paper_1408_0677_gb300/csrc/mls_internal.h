@@ -1,0 +1,84 @@
+// Host-side internals of the MLS library: the handle and the launchers that
+// each CUDA translation unit exports to the C ABI layer.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "dev_common.cuh"
+#include "mls.h"
+
+namespace mlsi {
+
+constexpr int kTile = 16;            // tensor / prepass tile side (pixels)
+constexpr int kPointPad = 64;        // points are padded to a multiple of this
+
+struct PointSet {
+  int64_t n = 0, n_pad = 0;
+  int D = 0, D_pad = 0;
+  double s = 1.0, ctr_x = 0.0, ctr_y = 0.0;
+  double bbox[4] = {0, 0, 0, 0};     // xmin, ymin, xmax, ymax
+  double *x64 = nullptr, *y64 = nullptr, *FT64 = nullptr;
+  float *xs = nullptr, *ys = nullptr, *FT32 = nullptr;
+  double *fcen = nullptr, *fscl = nullptr;
+  float *fcen32 = nullptr, *fscl32 = nullptr;
+  int *cell_start = nullptr;
+  int gx = 0, gy = 0;
+  double gx0 = 0, gy0 = 0, cell = 0;
+};
+
+}  // namespace mlsi
+
+struct mls_handle {
+  mls_desc desc;
+  int device = 0;
+  cudaStream_t stream = nullptr;     // stream of the last call
+  mlsi::PointSet P;
+  std::vector<void *> owned;         // handle-lifetime device allocations
+  // per-render scratch, grown on demand
+  void *scratch = nullptr;
+  size_t scratch_bytes = 0;
+  float *mstab = nullptr;
+  int *cnt = nullptr;
+  int *relist = nullptr;
+  unsigned int *counters = nullptr;  // [0] recompute count
+  int *err = nullptr;
+  double *lev64 = nullptr;
+  float *lev32 = nullptr;
+  size_t lev_cap = 0;
+  // staging for host-pointer calls
+  void *stage = nullptr;
+  size_t stage_bytes = 0;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  int64_t last_pairs = 0;
+  bool timed = false;
+};
+
+namespace mlsi {
+
+// prep.cu
+mls_status prep_points(mls_handle *h, const double *xy_dev, const double *F_dev, cudaStream_t st);
+// prepass.cu: stabiliser m = min r^2 (Gaussian, inverse distance) or support
+// counts (Wendland) over the padded tile grid
+void launch_prepass(const mlsk::KParams &p, cudaStream_t st);
+// plain.cu
+void launch_f32(const mlsk::KParams &p, cudaStream_t st);
+void launch_f64(const mlsk::KParams &p, int64_t npix, cudaStream_t st);
+void launch_bands(const mlsk::KParams &p, bool fp64, cudaStream_t st);
+// tc.cu
+mls_status launch_tc(const mlsk::KParams &p, int fp16, int wsplit, cudaStream_t st);
+
+// errors (mls_api.cu)
+mls_status fail(mls_status s, const std::string &msg);
+mls_status cuda_fail(cudaError_t e, const char *what);
+mls_status dev_alloc(mls_handle *h, void **p, size_t bytes, cudaStream_t st);
+
+}  // namespace mlsi
+
+#define MLS_CUDA_TRY(expr)                                        \
+  do {                                                            \
+    cudaError_t e__ = (expr);                                     \
+    if (e__ != cudaSuccess) return mlsi::cuda_fail(e__, #expr);   \
+  } while (0)

@@ -1,0 +1,547 @@
+// CUDA-core MLS kernels: the plain FP32 form (one thread per pixel, points
+// staged through shared memory), the FP64 form (one warp per pixel, used for
+// FP64 renders and for the pixels the reduced-precision paths hand over),
+// and the standalone iso-band labelling.
+//
+// Per pixel p and point x_i (Section 3.3 of the paper, generalised to D data
+// dimensions): w_i = w(|x_i - p|); with d_i = (x_i - p)/h and basis
+// b = (1, d_x, d_y, d_x^2, d_x d_y, d_y^2) truncated to the degree,
+// M = sum w b b^T is held as its distinct moments sum w d^a (|a| <= 2 deg)
+// and R = sum w b f^T; the fit's value is e0 . M^{-1} R.
+#include <float.h>
+#include <string.h>
+
+#include <algorithm>
+
+#include "mls_internal.h"
+
+namespace mlsi {
+namespace {
+
+using namespace mlsk;
+
+constexpr float kLog2e = 1.4426950408889634f;
+
+// Monomials of degree <= 4 of (dx, dy) (index order of kMIdx).
+template <int NM>
+__device__ __forceinline__ void monomials(float dx, float dy, float (&m)[15]) {
+  m[0] = 1.f;
+  if (NM > 1) {
+    m[1] = dx; m[2] = dy;
+    m[3] = dx * dx; m[4] = dx * dy; m[5] = dy * dy;
+  }
+  if (NM > 6) {
+    m[6] = m[3] * dx; m[7] = m[3] * dy; m[8] = m[5] * dx; m[9] = m[5] * dy;
+    m[10] = m[3] * m[3]; m[11] = m[3] * m[4]; m[12] = m[3] * m[5]; m[13] = m[4] * m[5]; m[14] = m[5] * m[5];
+  }
+}
+
+__device__ __forceinline__ void cell_range_d(double lo, double hi, double r, double g0, double inv_cell, int g,
+                                             int &c0, int &c1) {
+  c0 = (int)floor((lo - r - g0) * inv_cell);
+  c1 = (int)floor((hi + r - g0) * inv_cell);
+  c0 = max(c0, 0);
+  c1 = min(c1, g - 1);
+}
+
+// ---------------------------------------------------------------------------
+// Plain FP32: one thread per pixel, 16 x 8 pixels per block.
+constexpr int kF32Chunk = 128;
+constexpr int kF32DC = 16;
+
+template <int DEG, int WK>
+__global__ __launch_bounds__(128) void k_mls_f32(KParams p) {
+  constexpr int K = n_terms(DEG), NM = n_moments(DEG), DC = kF32DC;
+  __shared__ float sx[kF32Chunk], sy[kF32Chunk];
+  __shared__ float sf[DC][kF32Chunk];
+  const int t = threadIdx.x;
+  const int u = blockIdx.x * 16 + (t & 15), v = blockIdx.y * 8 + (t >> 4);
+  const bool inside = (u < p.W) && (v < p.H);
+  const float px = scaled_px(p, u), py = scaled_py(p, v);
+  const size_t pstride = (size_t)p.tiles_x * 16;
+  const float m = (WK == MLS_W_WENDLAND) ? 0.f : p.mstab[(size_t)v * pstride + u];
+  const int count = (WK == MLS_W_WENDLAND) ? p.cnt[(size_t)v * pstride + u] : (int)(p.n < (1 << 30) ? p.n : (1 << 30));
+  const float alpha = (float)p.alpha;
+  // point ranges: all points, or the cell rows overlapping the block's pixels +- h
+  int nr = 1, cx0 = 0, cx1 = 0, cy0 = 0;
+  if (WK == MLS_W_WENDLAND) {
+    const int bu0 = blockIdx.x * 16, bv0 = blockIdx.y * 8;
+    const double xa = p.x0 + (bu0 + 0.5) * p.sx, xb = p.x0 + (bu0 + 15.5) * p.sx;
+    const double ya = p.y0 + (bv0 + 0.5) * p.sy, yb = p.y0 + (bv0 + 7.5) * p.sy;
+    const double inv_cell = 1.0 / p.cell;
+    int cy1;
+    cell_range_d(fmin(xa, xb), fmax(xa, xb), p.h, p.gx0, inv_cell, p.gx, cx0, cx1);
+    cell_range_d(fmin(ya, yb), fmax(ya, yb), p.h, p.gy0, inv_cell, p.gy, cy0, cy1);
+    nr = (cx0 <= cx1) ? max(cy1 - cy0 + 1, 0) : 0;
+  }
+  const size_t plane = (size_t)p.W * p.H;
+  const size_t pix = (size_t)v * p.W + u;
+  float *field = (float *)p.field;
+  bool handed_over = false;
+  uint8_t st = 0;
+
+  for (int d0 = 0; d0 < p.D; d0 += DC) {
+    float S[15], R[K][DC];
+#pragma unroll
+    for (int j = 0; j < 15; ++j) S[j] = 0.f;
+#pragma unroll
+    for (int a = 0; a < K; ++a)
+#pragma unroll
+      for (int dd = 0; dd < DC; ++dd) R[a][dd] = 0.f;
+    float csum[DC];
+    int ccnt = 0;
+#pragma unroll
+    for (int dd = 0; dd < DC; ++dd) csum[dd] = 0.f;
+    for (int r = 0; r < nr; ++r) {
+      int a0, a1;
+      if (WK == MLS_W_WENDLAND) {
+        a0 = p.cell_start[(cy0 + r) * p.gx + cx0];
+        a1 = p.cell_start[(cy0 + r) * p.gx + cx1 + 1];
+      } else {
+        a0 = 0;
+        a1 = (int)p.n;
+      }
+      for (int base = a0; base < a1; base += kF32Chunk) {
+        __syncthreads();
+        const int cnt = min(kF32Chunk, a1 - base);
+        if (t < cnt) {
+          sx[t] = p.xs[base + t];
+          sy[t] = p.ys[base + t];
+        }
+        for (int e = t; e < DC * kF32Chunk; e += 128) {
+          const int dd = e / kF32Chunk, j = e % kF32Chunk;
+          sf[dd][j] = (j < cnt) ? p.FT32[(size_t)(d0 + dd) * p.n_pad + base + j] : 0.f;
+        }
+        __syncthreads();
+        for (int j = 0; j < cnt; ++j) {
+          const float dx = sx[j] - px, dy = sy[j] - py;
+          const float r2 = fmaf(dx, dx, dy * dy);
+          float w;
+          if (WK == MLS_W_GAUSS) {
+            w = exp2f((m - r2) * kLog2e);
+          } else if (WK == MLS_W_WENDLAND) {
+            const float q = sqrtf(r2);
+            const float o = 1.f - q;
+            const float o2 = o * o;
+            w = (q < 1.f) ? o2 * o2 * fmaf(4.f, q, 1.f) : 0.f;
+          } else {
+            if (r2 == 0.f) {
+              ++ccnt;
+#pragma unroll
+              for (int dd = 0; dd < DC; ++dd) csum[dd] += sf[dd][j];
+              w = 0.f;
+            } else {
+              w = exp2f(alpha * __log2f(m / r2));
+            }
+          }
+          float mo[15];
+          monomials<NM>(dx, dy, mo);
+#pragma unroll
+          for (int q = 0; q < NM; ++q) S[q] = fmaf(w, mo[q], S[q]);
+#pragma unroll
+          for (int a = 0; a < K; ++a) {
+            const float wb = w * mo[a];
+#pragma unroll
+            for (int dd = 0; dd < DC; ++dd) R[a][dd] = fmaf(wb, sf[dd][j], R[a][dd]);
+          }
+        }
+      }
+    }
+    // --- per-pixel solve
+    if (!inside) continue;
+    float z[K];
+    bool write = true;
+    if (WK == MLS_W_INVDIST && ccnt > 0) {
+      st = MLS_ST_COINCIDENT;
+#pragma unroll
+      for (int dd = 0; dd < DC; ++dd) {
+        const int d = d0 + dd;
+        if (d < p.D) {
+          const float f = fmaf(csum[dd] / (float)ccnt, p.fscl32[d], p.fcen32[d]);
+          field[(size_t)d * plane + pix] = f;
+          if (p.bands) p.bands[(size_t)d * plane + pix] = band_of(f, p.lev32 + (size_t)d * p.L, p.L);
+        }
+      }
+      continue;
+    }
+    if (count == 0) {
+      st = MLS_ST_NO_SUPPORT;
+#pragma unroll
+      for (int dd = 0; dd < DC; ++dd) {
+        const int d = d0 + dd;
+        if (d < p.D) {
+          field[(size_t)d * plane + pix] = __int_as_float(0x7fc00000);
+          if (p.bands) p.bands[(size_t)d * plane + pix] = 255;
+        }
+      }
+      continue;
+    }
+    int outcome = SOLVE_RECOMPUTE;
+    // pixels whose support count is near a degree threshold go to FP64,
+    // which applies the count rule in the same precision as the definition
+    if (!(WK == MLS_W_WENDLAND && count <= K + 2)) outcome = solve_pixel_fp32<K>(S, z, p);
+    if (outcome == SOLVE_RECOMPUTE) {
+      write = false;
+      if (d0 == 0) {
+        const unsigned int k = atomicAdd(p.relist_count, 1u);
+        p.relist[k] = (int)pix;
+      }
+      handed_over = true;
+    } else {
+      st = (uint8_t)(DEG | (outcome == SOLVE_FP64 ? MLS_ST_FP64_SOLVE : 0));
+    }
+    if (write) {
+#pragma unroll
+      for (int dd = 0; dd < DC; ++dd) {
+        const int d = d0 + dd;
+        if (d < p.D) {
+          float acc = 0.f;
+#pragma unroll
+          for (int a = 0; a < K; ++a) acc = fmaf(z[a], R[a][dd], acc);
+          const float f = fmaf(acc, p.fscl32[d], p.fcen32[d]);
+          field[(size_t)d * plane + pix] = f;
+          if (p.bands) p.bands[(size_t)d * plane + pix] = band_of(f, p.lev32 + (size_t)d * p.L, p.L);
+        }
+      }
+    }
+  }
+  if (inside && !handed_over && p.status) p.status[pix] = st;
+}
+
+// ---------------------------------------------------------------------------
+// FP64: one warp per pixel; lanes split the points, moments are summed by a
+// butterfly reduction, every lane applies the full degree policy.
+constexpr int kF64DC = 8;
+// On the hand-over path (pixels recomputed for a reduced-precision render)
+// Gaussian pairs with (r^2 - m)/h^2 above this are not accumulated: their
+// weight is below e^-60 of the largest, which leaves every moment unchanged
+// at FP64 rounding unless the significant points alone are degenerate for
+// the basis.  FP64 renders sum every pair.
+constexpr double kGaussCut = 60.0;
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+template <int DEG, int WK, typename OutT>
+__global__ __launch_bounds__(256) void k_mls_f64(KParams p, int64_t npix_all) {
+  constexpr int NM = n_moments(DEG), DC = kF64DC;
+  const int lane = threadIdx.x & 31;
+  const int64_t warp0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int64_t npix = p.list ? (int64_t)((int64_t)*p.list_count < p.list_cap ? (int64_t)*p.list_count : p.list_cap)
+                              : npix_all;
+  const size_t plane = (size_t)p.W * p.H;
+  const double inv_s = 1.0 / p.h;
+  const double h2 = p.h * p.h;
+  const int64_t n = p.n;
+  OutT *field = (OutT *)p.field;
+
+  for (int64_t q = warp0; q < npix; q += nwarps) {
+    const int64_t id = p.list ? p.list[q] : q;
+    const int u = (int)(id % p.W), v = (int)(id / p.W);
+    // the same expression order as the FP64 definition, without contraction
+    const double px = __dadd_rn(p.x0, __dmul_rn(__dadd_rn((double)u, 0.5), p.sx));
+    const double py = __dadd_rn(p.y0, __dmul_rn(__dadd_rn((double)v, 0.5), p.sy));
+    // candidate ranges
+    int a0s[3] = {0, 0, 0}, a1s[3] = {0, 0, 0};
+    int nr = 1;
+    if (WK == MLS_W_WENDLAND) {
+      const double inv_cell = 1.0 / p.cell;
+      int cx0, cx1, cy0, cy1;
+      cell_range_d(px, px, p.h, p.gx0, inv_cell, p.gx, cx0, cx1);
+      cell_range_d(py, py, p.h, p.gy0, inv_cell, p.gy, cy0, cy1);
+      nr = 0;
+      for (int cy = cy0; cy <= cy1 && cx0 <= cx1 && nr < 3; ++cy) {
+        a0s[nr] = p.cell_start[cy * p.gx + cx0];
+        a1s[nr] = p.cell_start[cy * p.gx + cx1 + 1];
+        ++nr;
+      }
+    } else {
+      a1s[0] = (int)n;
+    }
+    // stabiliser m = min r^2 (Gaussian, inverse distance)
+    double m = 0.0;
+    if (WK != MLS_W_WENDLAND) {
+      double mm = DBL_MAX;
+      for (int64_t i = lane; i < n; i += 32) {
+        const double dx = __dadd_rn(p.x64[i], -px), dy = __dadd_rn(p.y64[i], -py);
+        mm = fmin(mm, __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)));
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) mm = fmin(mm, __shfl_xor_sync(0xffffffffu, mm, o));
+      m = mm;
+    }
+    const bool coincident = (WK == MLS_W_INVDIST) && (m == 0.0);
+    uint8_t st = MLS_ST_RECOMPUTED;
+    for (int d0 = 0; d0 < p.D; d0 += DC) {
+      double S[15], R[6][DC], csum[DC];
+      int64_t count = 0, ccnt = 0;
+#pragma unroll
+      for (int j = 0; j < 15; ++j) S[j] = 0.0;
+#pragma unroll
+      for (int a = 0; a < 6; ++a)
+#pragma unroll
+        for (int dd = 0; dd < DC; ++dd) R[a][dd] = 0.0;
+#pragma unroll
+      for (int dd = 0; dd < DC; ++dd) csum[dd] = 0.0;
+      for (int r = 0; r < nr; ++r) {
+        for (int64_t i = a0s[r] + lane; i < a1s[r]; i += 32) {
+          const double dx = __dadd_rn(p.x64[i], -px), dy = __dadd_rn(p.y64[i], -py);
+          const double r2 = __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy));
+          double w;
+          if (WK == MLS_W_GAUSS) {
+            ++count;
+            if (p.list && r2 - m > kGaussCut * h2) continue;
+            w = exp(-(r2 - m) / h2);
+          } else if (WK == MLS_W_WENDLAND) {
+            if (r2 < h2) {
+              const double qd = sqrt(r2) / p.h;
+              const double o = 1.0 - qd;
+              w = o * o * o * o * (4.0 * qd + 1.0);
+              ++count;
+            } else {
+              w = 0.0;
+            }
+          } else {
+            ++count;
+            if (coincident) {
+              w = 0.0;
+              if (r2 == 0.0) {
+                ++ccnt;
+#pragma unroll
+                for (int dd = 0; dd < DC; ++dd)
+                  if (d0 + dd < p.D) csum[dd] += p.FT64[(size_t)(d0 + dd) * n + i];
+              }
+            } else {
+              w = pow(m / r2, p.alpha);
+            }
+          }
+          if (w == 0.0) continue;
+          const double ddx = dx * inv_s, ddy = dy * inv_s;
+          double mo[15];
+          mo[0] = 1.0;
+          if (NM > 1) {
+            mo[1] = ddx; mo[2] = ddy; mo[3] = ddx * ddx; mo[4] = ddx * ddy; mo[5] = ddy * ddy;
+          }
+          if (NM > 6) {
+            mo[6] = mo[3] * ddx; mo[7] = mo[3] * ddy; mo[8] = mo[5] * ddx; mo[9] = mo[5] * ddy;
+            mo[10] = mo[3] * mo[3]; mo[11] = mo[3] * mo[4]; mo[12] = mo[3] * mo[5];
+            mo[13] = mo[4] * mo[5]; mo[14] = mo[5] * mo[5];
+          }
+#pragma unroll
+          for (int j = 0; j < NM; ++j) S[j] += w * mo[j];
+          double fv[DC];
+#pragma unroll
+          for (int dd = 0; dd < DC; ++dd) fv[dd] = (d0 + dd < p.D) ? p.FT64[(size_t)(d0 + dd) * n + i] : 0.0;
+#pragma unroll
+          for (int a = 0; a < n_terms(DEG); ++a) {
+            const double wb = w * mo[a];
+#pragma unroll
+            for (int dd = 0; dd < DC; ++dd) R[a][dd] += wb * fv[dd];
+          }
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < NM; ++j) S[j] = warp_sum(S[j]);
+#pragma unroll
+      for (int a = 0; a < n_terms(DEG); ++a)
+#pragma unroll
+        for (int dd = 0; dd < DC; ++dd) R[a][dd] = warp_sum(R[a][dd]);
+      count = warp_sum(count);
+      if (WK == MLS_W_INVDIST) {
+        ccnt = warp_sum(ccnt);
+#pragma unroll
+        for (int dd = 0; dd < DC; ++dd) csum[dd] = warp_sum(csum[dd]);
+      }
+      // degree policy (every lane, identical arithmetic)
+      double out[DC];
+      int used = -1;
+      if (coincident) {
+#pragma unroll
+        for (int dd = 0; dd < DC; ++dd) out[dd] = csum[dd] / (double)ccnt;
+        used = 0;
+        st |= MLS_ST_COINCIDENT;
+      } else {
+        for (int deg = DEG; deg >= 0 && used < 0; --deg) {
+          const int k = n_terms(deg);
+          if (count < k) continue;
+          double Mm[6][6], sdg[6], Me[6][6], Lm[6][6];
+          bool ok = true;
+          for (int a = 0; a < k; ++a)
+            for (int b = 0; b < k; ++b) Mm[a][b] = S[kMIdx[a][b]];
+          for (int a = 0; a < k && ok; ++a) {
+            if (!(Mm[a][a] > 0.0)) ok = false;
+            else sdg[a] = 1.0 / sqrt(Mm[a][a]);
+          }
+          if (!ok) continue;
+          for (int a = 0; a < k; ++a)
+            for (int b = 0; b < k; ++b) Me[a][b] = Mm[a][b] * sdg[a] * sdg[b];
+          // Cholesky
+          for (int j = 0; j < k && ok; ++j) {
+            double s = Me[j][j];
+            for (int tt = 0; tt < j; ++tt) s -= Lm[j][tt] * Lm[j][tt];
+            if (!(s > 0.0)) { ok = false; break; }
+            const double ljj = sqrt(s);
+            Lm[j][j] = ljj;
+            for (int i2 = j + 1; i2 < k; ++i2) {
+              double vv = Me[i2][j];
+              for (int tt = 0; tt < j; ++tt) vv -= Lm[i2][tt] * Lm[j][tt];
+              Lm[i2][j] = vv / ljj;
+            }
+          }
+          if (!ok) continue;
+          // inverse, rcond_1
+          double Inv[6][6];
+          for (int c = 0; c < k; ++c) {
+            double col[6];
+            for (int a = 0; a < k; ++a) col[a] = (a == c) ? 1.0 : 0.0;
+            for (int i2 = 0; i2 < k; ++i2) {
+              double vv = col[i2];
+              for (int tt = 0; tt < i2; ++tt) vv -= Lm[i2][tt] * col[tt];
+              col[i2] = vv / Lm[i2][i2];
+            }
+            for (int i2 = k - 1; i2 >= 0; --i2) {
+              double vv = col[i2];
+              for (int tt = i2 + 1; tt < k; ++tt) vv -= Lm[tt][i2] * col[tt];
+              col[i2] = vv / Lm[i2][i2];
+            }
+            for (int a = 0; a < k; ++a) Inv[a][c] = col[a];
+          }
+          double nA = 0.0, nI = 0.0;
+          for (int c = 0; c < k; ++c) {
+            double sa = 0.0, si = 0.0;
+            for (int a = 0; a < k; ++a) { sa += fabs(Me[a][c]); si += fabs(Inv[a][c]); }
+            nA = fmax(nA, sa);
+            nI = fmax(nI, si);
+          }
+          const double rc = 1.0 / (nA * nI);
+          if (!(rc >= p.rcond_min)) continue;
+#pragma unroll
+          for (int dd = 0; dd < DC; ++dd) {
+            double acc = 0.0;
+            for (int c = 0; c < k; ++c) acc += sdg[0] * Inv[0][c] * sdg[c] * R[c][dd];
+            out[dd] = acc;
+          }
+          used = deg;
+        }
+      }
+      if (used < 0) {
+        st |= MLS_ST_NO_SUPPORT;
+#pragma unroll
+        for (int dd = 0; dd < DC; ++dd) out[dd] = __longlong_as_double(0x7ff8000000000000ll);
+      } else {
+        st = (uint8_t)((st & ~MLS_ST_DEGREE_MASK) | used | (used < DEG ? MLS_ST_DEGRADED : 0));
+      }
+      // lane dd writes dimension d0 + dd
+#pragma unroll
+      for (int dd = 0; dd < DC; ++dd) {
+        const int d = d0 + dd;
+        if (lane == dd && d < p.D) {
+          const OutT f = (OutT)out[dd];
+          field[(size_t)d * plane + id] = f;
+          if (p.bands) {
+            if (sizeof(OutT) == 8)
+              p.bands[(size_t)d * plane + id] = band_of((double)f, p.lev64 + (size_t)d * p.L, p.L);
+            else
+              p.bands[(size_t)d * plane + id] = band_of((float)f, p.lev32 + (size_t)d * p.L, p.L);
+          }
+        }
+      }
+    }
+    if (lane == 0 && p.status) {
+      if (!p.list) st &= ~MLS_ST_RECOMPUTED;
+      p.status[id] = st;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Standalone labels: 16 consecutive pixels of one dimension per thread.
+template <typename T>
+__global__ void k_bands(const T *field, const double *lev64, const float *lev32, int L, int64_t plane, int D,
+                        uint8_t *bands) {
+  extern __shared__ unsigned char smem_raw[];
+  const int d = blockIdx.y;
+  if (sizeof(T) == 8) {
+    double *lv = (double *)smem_raw;
+    for (int j = threadIdx.x; j < L; j += blockDim.x) lv[j] = lev64[(size_t)d * L + j];
+  } else {
+    float *lv = (float *)smem_raw;
+    for (int j = threadIdx.x; j < L; j += blockDim.x) lv[j] = lev32[(size_t)d * L + j];
+  }
+  __syncthreads();
+  const int64_t i0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) * 16;
+  if (i0 >= plane) return;
+  const T *f = field + (size_t)d * plane;
+  uint8_t *b = bands + (size_t)d * plane;
+  uint8_t out[16];
+#pragma unroll
+  for (int k = 0; k < 16; ++k) {
+    if (i0 + k < plane) {
+      const T x = f[i0 + k];
+      out[k] = (sizeof(T) == 8) ? band_of((double)x, (const double *)smem_raw, L)
+                                : band_of((float)x, (const float *)smem_raw, L);
+    }
+  }
+  if (i0 + 16 <= plane && (((uintptr_t)(b + i0)) & 15) == 0) {
+    uint4 pk;
+    memcpy(&pk, out, 16);
+    *(uint4 *)(b + i0) = pk;
+  } else {
+    for (int k = 0; k < 16 && i0 + k < plane; ++k) b[i0 + k] = out[k];
+  }
+}
+
+template <int DEG>
+void f32_dispatch_w(const KParams &p, cudaStream_t st) {
+  dim3 grid(p.tiles_x, p.tiles_y * 2);
+  if (p.weight == MLS_W_GAUSS) k_mls_f32<DEG, MLS_W_GAUSS><<<grid, 128, 0, st>>>(p);
+  else if (p.weight == MLS_W_WENDLAND) k_mls_f32<DEG, MLS_W_WENDLAND><<<grid, 128, 0, st>>>(p);
+  else k_mls_f32<DEG, MLS_W_INVDIST><<<grid, 128, 0, st>>>(p);
+}
+
+template <int DEG, typename OutT>
+void f64_dispatch_w(const KParams &p, int64_t npix, cudaStream_t st) {
+  int grid;
+  if (p.list) grid = 152 * 8;
+  else grid = (int)std::min<int64_t>((npix + 7) / 8, 152 * 64);
+  if (grid < 1) grid = 1;
+  if (p.weight == MLS_W_GAUSS) k_mls_f64<DEG, MLS_W_GAUSS, OutT><<<grid, 256, 0, st>>>(p, npix);
+  else if (p.weight == MLS_W_WENDLAND) k_mls_f64<DEG, MLS_W_WENDLAND, OutT><<<grid, 256, 0, st>>>(p, npix);
+  else k_mls_f64<DEG, MLS_W_INVDIST, OutT><<<grid, 256, 0, st>>>(p, npix);
+}
+
+}  // namespace
+
+void launch_f32(const KParams &p, cudaStream_t st) {
+  if (p.degree == 0) f32_dispatch_w<0>(p, st);
+  else if (p.degree == 1) f32_dispatch_w<1>(p, st);
+  else f32_dispatch_w<2>(p, st);
+}
+
+void launch_f64(const KParams &p, int64_t npix, cudaStream_t st) {
+  // FP64 renders write double; hand-over lists from the reduced paths write float
+  if (p.field_fp64) {
+    if (p.degree == 0) f64_dispatch_w<0, double>(p, npix, st);
+    else if (p.degree == 1) f64_dispatch_w<1, double>(p, npix, st);
+    else f64_dispatch_w<2, double>(p, npix, st);
+  } else {
+    if (p.degree == 0) f64_dispatch_w<0, float>(p, npix, st);
+    else if (p.degree == 1) f64_dispatch_w<1, float>(p, npix, st);
+    else f64_dispatch_w<2, float>(p, npix, st);
+  }
+}
+
+void launch_bands(const KParams &p, bool fp64, cudaStream_t st) {
+  const int64_t plane = (int64_t)p.W * p.H;
+  dim3 grid((unsigned)((plane + 16 * 256 - 1) / (16 * 256)), (unsigned)p.D);
+  const size_t sm = (size_t)p.L * (fp64 ? 8 : 4) + 16;
+  if (fp64) k_bands<double><<<grid, 256, sm, st>>>((const double *)p.field, p.lev64, p.lev32, p.L, plane, p.D, p.bands);
+  else k_bands<float><<<grid, 256, sm, st>>>((const float *)p.field, p.lev64, p.lev32, p.L, plane, p.D, p.bands);
+}
+
+}  // namespace mlsi

@@ -1,0 +1,137 @@
+// Per-pixel prepass over the padded 16 x 16 tile grid.
+//
+// Gaussian and inverse-distance weights: the stabiliser m(p) = min_i
+// |x_i - p|^2 (in units of h^2).  Multiplying every weight of a pixel by the
+// same positive factor leaves the fit unchanged, so the kernels use
+// exp(-(r^2 - m)/h^2) and (m / r^2)^alpha, whose largest value is 1: no
+// underflow of the reduced-precision weights.  The search is culled per tile:
+// a bound B = min_i (largest squared distance from x_i to the tile's pixel
+// centres) is found first; only points whose smallest squared distance to
+// the tile is <= B can be nearest to one of its pixels.
+//
+// Wendland weight: the number of points within the support radius of each
+// pixel, from the cells of the uniform grid that overlap the tile.
+#include <float.h>
+
+#include "mls_internal.h"
+
+namespace mlsi {
+namespace {
+
+using mlsk::KParams;
+
+__device__ __forceinline__ float block_min(float v, float *red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fminf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) red[w] = v;
+  __syncthreads();
+  float r = red[0];
+  for (int i = 1; i < (int)(blockDim.x >> 5); ++i) r = fminf(r, red[i]);
+  return r;
+}
+
+__global__ __launch_bounds__(256) void k_prepass_min(KParams p) {
+  __shared__ float red[8];
+  __shared__ float cx[256], cy[256];
+  __shared__ int ccount;
+  const int t = threadIdx.x;
+  const int u0 = blockIdx.x * 16, v0 = blockIdx.y * 16;
+  const int u = u0 + (t & 15), v = v0 + (t >> 4);
+  const float px = mlsk::scaled_px(p, u), py = mlsk::scaled_py(p, v);
+  const float X0 = mlsk::scaled_px(p, u0), X1 = mlsk::scaled_px(p, u0 + 15);
+  const float Y0 = mlsk::scaled_py(p, v0), Y1 = mlsk::scaled_py(p, v0 + 15);
+  const int n = (int)p.n;
+  // bound on every tile pixel's nearest squared distance
+  float b = FLT_MAX;
+  for (int i = t; i < n; i += 256) {
+    const float x = p.xs[i], y = p.ys[i];
+    const float fx = fmaxf(fabsf(x - X0), fabsf(x - X1));
+    const float fy = fmaxf(fabsf(y - Y0), fabsf(y - Y1));
+    b = fminf(b, fx * fx + fy * fy);
+  }
+  const float bound = block_min(b, red) * 1.0001f + 1e-30f;
+  // stream the points in chunks, keep those that may be nearest
+  float m = FLT_MAX;
+  for (int base = 0; base < n; base += 256) {
+    if (t == 0) ccount = 0;
+    __syncthreads();
+    const int i = base + t;
+    if (i < n) {
+      const float x = p.xs[i], y = p.ys[i];
+      const float ox = fmaxf(fmaxf(X0 - x, x - X1), 0.f);
+      const float oy = fmaxf(fmaxf(Y0 - y, y - Y1), 0.f);
+      if (ox * ox + oy * oy <= bound) {
+        const int k = atomicAdd(&ccount, 1);
+        cx[k] = x;
+        cy[k] = y;
+      }
+    }
+    __syncthreads();
+    const int c = ccount;
+    for (int k = 0; k < c; ++k) {
+      const float dx = cx[k] - px, dy = cy[k] - py;
+      m = fminf(m, dx * dx + dy * dy);
+    }
+    __syncthreads();
+  }
+  const int stride = p.tiles_x * 16;
+  const_cast<float *>(p.mstab)[(size_t)v * stride + u] = m;
+}
+
+// Inclusive cell range [c0, c1] covering [lo - r, hi + r] along one axis.
+__device__ __forceinline__ void cell_range(double lo, double hi, double r, double g0, double inv_cell, int g,
+                                           int &c0, int &c1) {
+  c0 = (int)floor((lo - r - g0) * inv_cell);
+  c1 = (int)floor((hi + r - g0) * inv_cell);
+  c0 = max(c0, 0);
+  c1 = min(c1, g - 1);
+}
+
+__global__ __launch_bounds__(256) void k_prepass_count(KParams p) {
+  __shared__ float cx[256], cy[256];
+  const int t = threadIdx.x;
+  const int u0 = blockIdx.x * 16, v0 = blockIdx.y * 16;
+  const int u = u0 + (t & 15), v = v0 + (t >> 4);
+  const float px = mlsk::scaled_px(p, u), py = mlsk::scaled_py(p, v);
+  // tile rectangle of pixel centres in raw coordinates
+  const double xlo = p.x0 + (u0 + 0.5) * p.sx, xhi = p.x0 + (u0 + 15.5) * p.sx;
+  const double ylo = p.y0 + (v0 + 0.5) * p.sy, yhi = p.y0 + (v0 + 15.5) * p.sy;
+  const double inv_cell = 1.0 / p.cell;
+  int cx0, cx1, cy0, cy1;
+  cell_range(fmin(xlo, xhi), fmax(xlo, xhi), p.h, p.gx0, inv_cell, p.gx, cx0, cx1);
+  cell_range(fmin(ylo, yhi), fmax(ylo, yhi), p.h, p.gy0, inv_cell, p.gy, cy0, cy1);
+  int count = 0;
+  for (int cyy = cy0; cyy <= cy1 && cx0 <= cx1; ++cyy) {
+    const int a = p.cell_start[cyy * p.gx + cx0];
+    const int e = p.cell_start[cyy * p.gx + cx1 + 1];
+    for (int base = a; base < e; base += 256) {
+      __syncthreads();
+      if (base + t < e) {
+        cx[t] = p.xs[base + t];
+        cy[t] = p.ys[base + t];
+      }
+      __syncthreads();
+      const int c = min(256, e - base);
+      for (int k = 0; k < c; ++k) {
+        const float dx = cx[k] - px, dy = cy[k] - py;
+        count += (dx * dx + dy * dy < 1.f) ? 1 : 0;
+      }
+    }
+  }
+  const int stride = p.tiles_x * 16;
+  const_cast<int *>(p.cnt)[(size_t)v * stride + u] = count;
+}
+
+}  // namespace
+
+void launch_prepass(const KParams &p, cudaStream_t st) {
+  dim3 grid(p.tiles_x, p.tiles_y);
+  if (p.weight == MLS_W_WENDLAND)
+    k_prepass_count<<<grid, 256, 0, st>>>(p);
+  else
+    k_prepass_min<<<grid, 256, 0, st>>>(p);
+}
+
+}  // namespace mlsi

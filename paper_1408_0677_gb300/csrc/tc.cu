@@ -1,0 +1,694 @@
+// Tensor-core MLS (tcgen05 + TMEM, sm_103a).
+//
+// For a 16 x 16 pixel tile with centre c and points x_i, write x~_i =
+// (x_i - c)/h and delta_p = (p - c)/h.  The weighted least-squares fit at p
+// (Section 3.3 of the paper) does not depend on where the polynomial basis
+// is centred, so the moments can be taken in the tile frame:
+//   S~_a(p) = sum_i w_pi x~_i^a           (|a| <= 2 deg: the matrix M)
+//   R~_ad(p) = sum_i w_pi b_a(x~_i) f_id  (the right-hand sides)
+// Both are one product  W[pixels x points] . G[points x (16 + K D)]  whose
+// operand G depends only on the tile and the points; only w is generated per
+// (pixel, point) pair.  This is the P.V product of attention with
+// P = exp(...):
+//   - warps 0-3 generate the weights in registers (one exp2 per pair, FP32)
+//     and store them as FP16/BF16 into a 128B-swizzled K-major A tile;
+//   - warps 4-7 build G for the point tile as a hi + lo pair of FP16/BF16
+//     operands (G = G_hi + G_lo to ~22 / 16 bits: the moment matrix needs more
+//     than one 16-bit rounding, the weights do not);
+//   - one thread of warp 8 issues tcgen05.mma (kind::f16, FP32 accumulate in
+//     TMEM) for two 128-pixel accumulators, D += A.G_hi + A.G_lo;
+//   - the epilogue reads the moments back with tcgen05.ld, shifts M to the
+//     pixel frame, solves (FP32 Cholesky + refinement, FP64 above cond_fp64),
+//     evaluates the fit, labels the iso-bands and stores.
+// Pixels whose condition estimate exceeds cond_recompute, whose support count
+// sits near a degree threshold, or whose nearest point is so far that range
+// clipping of G could matter, are handed to the FP64 path.
+//
+// Every mbarrier wait is bounded (globaltimer); on expiry the kernel records
+// an error word, skips the remaining work, frees its TMEM and returns.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include "mls_internal.h"
+
+namespace mlsi {
+namespace {
+
+using namespace mlsk;
+
+constexpr int kM = 128;           // pixels per accumulator (TMEM lanes)
+constexpr int kKT = 64;           // points per stage = one 128-byte row of 16-bit values
+constexpr int kStages = 2;
+constexpr int kNMax = 256;        // operand columns per accumulator (TMEM budget 2 x 256)
+constexpr int kThreads = 288;     // 9 warps
+constexpr float kRMax = 15.f;     // |x~|_inf clip of the operand (FP16 range of x~^4)
+constexpr float kLog2e = 1.4426950408889634f;
+
+constexpr int kABytes = kM * 128;                  // 16 KB per A tile
+constexpr int kBBytes = kNMax * 128;               // 32 KB per B tile
+// Two kernel shapes share one layout: two 128-pixel accumulators with single
+// 16-bit weights, or one accumulator with weights split hi + lo; either way
+// a stage holds two A tiles.
+constexpr int kOffA = 0;                           // A[stage][acc or part]
+constexpr int kOffB = kOffA + kStages * 2 * kABytes;      // 64 KB: B[stage][part]
+constexpr int kOffPrm = kOffB + kStages * 2 * kBBytes;    // 192 KB: per-warp point params
+constexpr int kOffBar = kOffPrm + 4 * kKT * 16;           // 196 KB
+constexpr int kSmemBytes = kOffBar + 128 + 1024;          // + alignment slack
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ bool mbar_test(uint32_t bar, uint32_t parity) {
+  uint32_t done;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.b32 %0, 1, 0, p;\n\t}"
+      : "=r"(done)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+// Wait for the phase of the given parity to complete, at most kWaitLimitNs.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int *err, int code, uint64_t limit) {
+  if (mbar_test(bar, parity)) return true;
+  const uint64_t t0 = globaltimer_ns();
+  while (!mbar_test(bar, parity)) {
+    if (globaltimer_ns() - t0 > limit) {
+      set_error(err, code);
+      return false;
+    }
+  }
+  return true;
+}
+
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_alloc(uint32_t slot, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(slot), "r"(ncols)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups
+// 1024 bytes apart (the layout of rows of 64 16-bit values written with the
+// XOR swizzle below).
+__device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr) {
+  return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
+         ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+
+__device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                        uint32_t accum) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum)
+      : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+               : "memory");
+}
+
+// 32 lanes x 16 columns of 32-bit from TMEM, waited in the same statement.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n\t"
+      "tcgen05.wait::ld.sync.aligned;"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr)
+      : "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Byte offset of the 16-byte chunk c of row m in a 128B-swizzled K-major tile.
+__device__ __forceinline__ uint32_t sw128_off(int m, int c) {
+  return (uint32_t)((m >> 3) * 1024 + (m & 7) * 128 + ((c ^ (m & 7)) << 4));
+}
+
+template <bool FP16>
+__device__ __forceinline__ uint32_t pack2(float lo, float hi) {
+  if (FP16) {
+    __half2 h = __floats2half2_rn(lo, hi);
+    return *reinterpret_cast<uint32_t *>(&h);
+  } else {
+    __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<uint32_t *>(&h);
+  }
+}
+template <bool FP16>
+__device__ __forceinline__ float2 unpack2(uint32_t u) {
+  if (FP16) {
+    __half2 h = *reinterpret_cast<__half2 *>(&u);
+    return __half22float2(h);
+  } else {
+    __nv_bfloat162 h = *reinterpret_cast<__nv_bfloat162 *>(&u);
+    return __bfloat1622float2(h);
+  }
+}
+
+// Eight operand values -> hi and lo 16-byte chunks (G = hi + lo).
+template <bool FP16>
+__device__ __forceinline__ void split8(const float (&x)[8], uint4 &hi, uint4 &lo) {
+  uint32_t h[4], l[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    h[q] = pack2<FP16>(x[2 * q], x[2 * q + 1]);
+    const float2 b = unpack2<FP16>(h[q]);
+    l[q] = pack2<FP16>(x[2 * q] - b.x, x[2 * q + 1] - b.y);
+  }
+  hi = make_uint4(h[0], h[1], h[2], h[3]);
+  lo = make_uint4(l[0], l[1], l[2], l[3]);
+}
+
+__device__ __forceinline__ float ex2_approx(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+// Weight of one (pixel, point) pair from the tile-frame point parameters
+// prm = (a, b, c): Gaussian log2 weight a + b dx + c dy + E, or Wendland q^2.
+template <int WK>
+__device__ __forceinline__ float pair_weight(float4 prm, float E, float dx, float dy) {
+  const float t = fmaf(prm.y, dx, fmaf(prm.z, dy, prm.x + E));
+  if (WK == MLS_W_GAUSS) {
+    return ex2_approx(t);
+  } else {
+    const float q = sqrtf(fmaxf(t, 0.f));
+    const float o = 1.f - q;
+    const float o2 = o * o;
+    return (q < 1.f) ? o2 * o2 * fmaf(4.f, q, 1.f) : 0.f;
+  }
+}
+
+// The sequence of point tiles a CTA visits: all points, or for the Wendland
+// weight the cell rows of the uniform grid overlapping the tile +- h.  Tile
+// starts are rounded down to 8 points; indices outside [lo, hi) are masked.
+struct RangeIter {
+  int cx0, cx1, cy0, cy1, cy;
+  int lo, hi, base;
+  bool all;
+  int n;
+};
+
+__device__ __forceinline__ void ranges_init(const KParams &p, int u0, int v0, int hgt, RangeIter &it) {
+  it.n = (int)p.n;
+  if (p.weight != MLS_W_WENDLAND) {
+    it.all = true;
+    it.lo = 0;
+    it.hi = it.n;
+    it.base = 0;
+    it.cy = it.cy1 = 0;
+    return;
+  }
+  it.all = false;
+  const double xlo = p.x0 + (u0 + 0.5) * p.sx, xhi = p.x0 + (u0 + 15.5) * p.sx;
+  const double ylo = p.y0 + (v0 + 0.5) * p.sy, yhi = p.y0 + (v0 + hgt - 0.5) * p.sy;
+  const double inv_cell = 1.0 / p.cell;
+  it.cx0 = max((int)floor((fmin(xlo, xhi) - p.h - p.gx0) * inv_cell), 0);
+  it.cx1 = min((int)floor((fmax(xlo, xhi) + p.h - p.gx0) * inv_cell), p.gx - 1);
+  it.cy0 = max((int)floor((fmin(ylo, yhi) - p.h - p.gy0) * inv_cell), 0);
+  it.cy1 = min((int)floor((fmax(ylo, yhi) + p.h - p.gy0) * inv_cell), p.gy - 1);
+  it.cy = it.cy0;
+  it.lo = it.hi = it.base = 0;
+  if (it.cx0 > it.cx1) it.cy = it.cy1 + 1;
+  // position on the first non-empty row
+  while (it.cy <= it.cy1) {
+    it.lo = p.cell_start[it.cy * p.gx + it.cx0];
+    it.hi = p.cell_start[it.cy * p.gx + it.cx1 + 1];
+    if (it.hi > it.lo) break;
+    ++it.cy;
+  }
+  it.base = it.lo & ~7;
+}
+
+__device__ __forceinline__ bool ranges_valid(const RangeIter &it) {
+  return it.all ? (it.base < it.hi) : (it.cy <= it.cy1);
+}
+
+__device__ __forceinline__ void ranges_next(const KParams &p, RangeIter &it) {
+  it.base += kKT;
+  if (it.base < it.hi) return;
+  if (it.all) return;
+  ++it.cy;
+  while (it.cy <= it.cy1) {
+    it.lo = p.cell_start[it.cy * p.gx + it.cx0];
+    it.hi = p.cell_start[it.cy * p.gx + it.cx1 + 1];
+    if (it.hi > it.lo) break;
+    ++it.cy;
+  }
+  it.base = it.lo & ~7;
+}
+
+template <int DEG, int WK, bool FP16, int NACC, bool WSPLIT>
+__global__ void __launch_bounds__(kThreads, 1) k_mls_tc(KParams p, int d0, int Dc, int N, uint32_t idesc) {
+  static_assert(NACC * (WSPLIT ? 2 : 1) == 2, "a stage holds two A tiles");
+  constexpr int K = n_terms(DEG), NM = n_moments(DEG);
+  constexpr int TH = 8 * NACC;          // tile height in pixels (width 16)
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char *smem = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  const uint32_t sbase = smem_u32(smem);
+  uint64_t *bars = (uint64_t *)(smem + kOffBar);
+  const uint32_t bar_full0 = smem_u32(&bars[0]);    // full[s] at +8 s
+  const uint32_t bar_empty0 = smem_u32(&bars[2]);   // empty[s]
+  const uint32_t bar_acc = smem_u32(&bars[4]);
+  uint32_t *tmem_slot = (uint32_t *)(smem + kOffBar + 64);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int u0 = blockIdx.x * 16, v0 = blockIdx.y * TH;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kStages; ++s) {
+      mbar_init(bar_full0 + 8 * s, 8);
+      mbar_init(bar_empty0 + 8 * s, 1);
+    }
+    mbar_init(bar_acc, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 8) tmem_alloc(smem_u32(tmem_slot), 512);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  // tile frame: centre at the pixel corner (u0 + 8, v0 + TH/2)
+  const float cxs = (float)((p.x0 + (u0 + 8) * p.sx - p.ctr_x) * p.inv_s);
+  const float cys = (float)((p.y0 + (v0 + TH / 2) * p.sy - p.ctr_y) * p.inv_s);
+  const uint64_t limit = kWaitLimitNs;
+  bool alive = true;
+
+  RangeIter it;
+  ranges_init(p, u0, v0, TH, it);
+
+  if (warp < 4) {
+    // ------------------------------------------------ weight producers
+    const int t = threadIdx.x;                 // row t of every accumulator
+    float dx[NACC], dy[NACC], E[NACC];
+#pragma unroll
+    for (int a = 0; a < NACC; ++a) {
+      const int q = a * 128 + t;
+      const int u = u0 + (q & 15), v = v0 + (q >> 4);
+      dx[a] = (float)(((q & 15) + 0.5 - 8.0) * p.sx * p.inv_s);
+      dy[a] = (float)(((q >> 4) + 0.5 - 0.5 * TH) * p.sy * p.inv_s);
+      const size_t pi = (size_t)v * (p.tiles_x * 16) + u;
+      if (WK == MLS_W_GAUSS)
+        E[a] = kLog2e * (p.mstab[pi] - (dx[a] * dx[a] + dy[a] * dy[a]));
+      else
+        E[a] = dx[a] * dx[a] + dy[a] * dy[a];
+    }
+    float4 *prm = (float4 *)(smem + kOffPrm) + warp * kKT;
+    int kt = 0;
+    for (; ranges_valid(it) && alive; ranges_next(p, it), ++kt) {
+      const int s = kt & 1;
+      __syncwarp();
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int j = lane + 32 * h;
+        const int i = it.base + j;
+        float x = 0.f, y = 0.f;
+        bool ok = (i >= it.lo) && (i < it.hi);
+        if (ok) {
+          x = p.xs[i] - cxs;
+          y = p.ys[i] - cys;
+          ok = fmaxf(fabsf(x), fabsf(y)) <= kRMax;
+        }
+        float4 v;
+        if (WK == MLS_W_GAUSS)
+          v = ok ? make_float4(-kLog2e * (x * x + y * y), 2.f * kLog2e * x, 2.f * kLog2e * y, 0.f)
+                 : make_float4(-INFINITY, 0.f, 0.f, 0.f);
+        else
+          v = ok ? make_float4(x * x + y * y, -2.f * x, -2.f * y, 0.f) : make_float4(INFINITY, 0.f, 0.f, 0.f);
+        prm[j] = v;
+      }
+      __syncwarp();
+      if (!mbar_wait(bar_empty0 + 8 * s, ((kt >> 1) & 1) ^ 1, p.err, ERR_WAIT_EMPTY, limit)) {
+        alive = false;
+        break;
+      }
+      unsigned char *A0 = smem + kOffA + (s * 2 + 0) * kABytes;
+      unsigned char *A1 = smem + kOffA + (s * 2 + 1) * kABytes;
+#pragma unroll 1
+      for (int c = 0; c < 8; ++c) {
+        float w0[8], w1[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          const float4 pr = prm[8 * c + j];
+          w0[j] = pair_weight<WK>(pr, E[0], dx[0], dy[0]);
+          if (NACC == 2) w1[j] = pair_weight<WK>(pr, E[NACC - 1], dx[NACC - 1], dy[NACC - 1]);
+        }
+        uint4 q0, q1;
+        if (WSPLIT) {
+          split8<FP16>(w0, q0, q1);          // A0 = hi, A1 = lo of accumulator 0
+        } else {
+          q0.x = pack2<FP16>(w0[0], w0[1]); q0.y = pack2<FP16>(w0[2], w0[3]);
+          q0.z = pack2<FP16>(w0[4], w0[5]); q0.w = pack2<FP16>(w0[6], w0[7]);
+          q1.x = pack2<FP16>(w1[0], w1[1]); q1.y = pack2<FP16>(w1[2], w1[3]);
+          q1.z = pack2<FP16>(w1[4], w1[5]); q1.w = pack2<FP16>(w1[6], w1[7]);
+        }
+        *(uint4 *)(A0 + sw128_off(t, c)) = q0;
+        *(uint4 *)(A1 + sw128_off(t, c)) = q1;
+      }
+      fence_proxy_async();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(bar_full0 + 8 * s);
+    }
+  } else if (warp < 8) {
+    // ------------------------------------------------ operand builders
+    const int tt = threadIdx.x - 128;
+    const int g = tt & 7;          // 8-point group of the tile
+    const int rr = tt >> 3;        // row class 0..15
+    int kt = 0;
+    for (; ranges_valid(it) && alive; ranges_next(p, it), ++kt) {
+      const int s = kt & 1;
+      const int i0 = it.base + 8 * g;
+      float xv[8], yv[8], msk[8];
+      if (i0 < p.n_pad) {
+        const float4 xa = *(const float4 *)(p.xs + i0), xb = *(const float4 *)(p.xs + i0 + 4);
+        const float4 ya = *(const float4 *)(p.ys + i0), yb = *(const float4 *)(p.ys + i0 + 4);
+        xv[0] = xa.x; xv[1] = xa.y; xv[2] = xa.z; xv[3] = xa.w; xv[4] = xb.x; xv[5] = xb.y; xv[6] = xb.z; xv[7] = xb.w;
+        yv[0] = ya.x; yv[1] = ya.y; yv[2] = ya.z; yv[3] = ya.w; yv[4] = yb.x; yv[5] = yb.y; yv[6] = yb.z; yv[7] = yb.w;
+      } else {
+#pragma unroll
+        for (int j = 0; j < 8; ++j) xv[j] = yv[j] = 0.f;
+      }
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const int i = i0 + j;
+        xv[j] -= cxs;
+        yv[j] -= cys;
+        const bool ok = (i >= it.lo) && (i < it.hi) && fmaxf(fabsf(xv[j]), fabsf(yv[j])) <= kRMax;
+        msk[j] = ok ? 1.f : 0.f;
+        if (!ok) { xv[j] = 0.f; yv[j] = 0.f; }
+      }
+      if (!mbar_wait(bar_empty0 + 8 * s, ((kt >> 1) & 1) ^ 1, p.err, ERR_WAIT_EMPTY, limit)) {
+        alive = false;
+        break;
+      }
+      unsigned char *Bh = smem + kOffB + (s * 2 + 0) * kBBytes;
+      unsigned char *Bl = smem + kOffB + (s * 2 + 1) * kBBytes;
+      // monomial row rr of the moment part (rows 0..15; rows >= NM are zero)
+      {
+        float val[8];
+        const int ex = mono_ex(rr < 15 ? rr : 0), ey = mono_ey(rr < 15 ? rr : 0);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          float m = msk[j];
+          for (int e = 0; e < ex; ++e) m *= xv[j];
+          for (int e = 0; e < ey; ++e) m *= yv[j];
+          val[j] = (rr < NM) ? m : 0.f;
+        }
+        uint4 hi, lo;
+        split8<FP16>(val, hi, lo);
+        *(uint4 *)(Bh + sw128_off(rr, g)) = hi;
+        *(uint4 *)(Bl + sw128_off(rr, g)) = lo;
+      }
+      // value rows 16 + d K + a, dimensions d = rr, rr + 16, ...
+      float bas[K][8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        bas[0][j] = msk[j];
+        if (K > 1) { bas[1][j] = msk[j] * xv[j]; bas[2][j] = msk[j] * yv[j]; }
+        if (K > 3) {
+          bas[3][j] = msk[j] * xv[j] * xv[j];
+          bas[4][j] = msk[j] * xv[j] * yv[j];
+          bas[5][j] = msk[j] * yv[j] * yv[j];
+        }
+      }
+      for (int d = rr; d < Dc; d += 16) {
+        float fv[8];
+        if (i0 < p.n_pad) {
+          const float *fr = p.FT32 + (size_t)(d0 + d) * p.n_pad + i0;
+          const float4 fa = *(const float4 *)fr, fb = *(const float4 *)(fr + 4);
+          fv[0] = fa.x; fv[1] = fa.y; fv[2] = fa.z; fv[3] = fa.w; fv[4] = fb.x; fv[5] = fb.y; fv[6] = fb.z; fv[7] = fb.w;
+        } else {
+#pragma unroll
+          for (int j = 0; j < 8; ++j) fv[j] = 0.f;
+        }
+#pragma unroll
+        for (int a = 0; a < K; ++a) {
+          float val[8];
+#pragma unroll
+          for (int j = 0; j < 8; ++j) val[j] = bas[a][j] * fv[j];
+          uint4 hi, lo;
+          split8<FP16>(val, hi, lo);
+          const int row = 16 + d * K + a;
+          *(uint4 *)(Bh + sw128_off(row, g)) = hi;
+          *(uint4 *)(Bl + sw128_off(row, g)) = lo;
+        }
+      }
+      // zero rows that pad N to a multiple of 16
+      for (int row = 16 + Dc * K + rr; row < N; row += 16) {
+        if (row >= 16 + Dc * K) {
+          const uint4 z = make_uint4(0, 0, 0, 0);
+          *(uint4 *)(Bh + sw128_off(row, g)) = z;
+          *(uint4 *)(Bl + sw128_off(row, g)) = z;
+        }
+      }
+      fence_proxy_async();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(bar_full0 + 8 * s);
+    }
+  } else {
+    // ------------------------------------------------ MMA issuer
+    if (lane == 0) {
+      int kt = 0;
+      for (; ranges_valid(it) && alive; ranges_next(p, it), ++kt) {
+        const int s = kt & 1;
+        if (!mbar_wait(bar_full0 + 8 * s, (kt >> 1) & 1, p.err, ERR_WAIT_FULL, limit)) {
+          alive = false;
+          break;
+        }
+        tc_fence_after();
+        // products per accumulator: A.G_hi + A.G_lo, or with split weights
+        // A_hi.G_hi + A_hi.G_lo + A_lo.G_hi (A_lo.G_lo is below FP32 rounding)
+        constexpr int NT = WSPLIT ? 3 : 2;
+#pragma unroll
+        for (int a = 0; a < NACC; ++a) {
+#pragma unroll
+          for (int k = 0; k < kKT / 16; ++k) {
+#pragma unroll
+            for (int term = 0; term < NT; ++term) {
+              const int ap = WSPLIT ? (term == 2 ? 1 : 0) : a;
+              const int bp = (term == 1) ? 1 : 0;
+              const uint32_t abase = sbase + kOffA + (s * 2 + ap) * kABytes;
+              const uint32_t bbase = sbase + kOffB + (s * 2 + bp) * kBBytes;
+              mma_f16(tmem + a * 256, desc_sw128(abase + 32 * k), desc_sw128(bbase + 32 * k), idesc,
+                      (kt | k | term) != 0 ? 1u : 0u);
+            }
+          }
+        }
+        mma_commit(bar_empty0 + 8 * s);
+      }
+      mma_commit(bar_acc);
+    }
+    __syncwarp();
+  }
+
+  // ------------------------------------------------ epilogue (warps 0-7)
+  // Has any point tile been visited?  (Recompute from the iterator start.)
+  RangeIter it2;
+  ranges_init(p, u0, v0, TH, it2);
+  const bool any_tile = ranges_valid(it2);
+  if (warp < 8) {
+    const bool acc_ok = __all_sync(0xffffffffu, mbar_wait(bar_acc, 0, p.err, ERR_WAIT_ACC, limit));
+    tc_fence_after();
+    const int wg = warp >> 2;
+    // two accumulators: one warpgroup each; one accumulator: the warpgroups
+    // share it and take alternate groups of value columns
+    const int a = (NACC == 2) ? wg : 0;
+    const bool primary = (NACC == 2) || wg == 0;
+    const int gfirst = (NACC == 2) ? 0 : wg, gstep = (NACC == 2) ? 1 : 2;
+    const int m = 32 * (warp & 3) + lane;
+    const int q = a * 128 + m;
+    const int u = u0 + (q & 15), v = v0 + (q >> 4);
+    const bool inside = (u < p.W) && (v < p.H);
+    const size_t pi = (size_t)v * (p.tiles_x * 16) + u;
+    const float dxp = (float)(((q & 15) + 0.5 - 8.0) * p.sx * p.inv_s);
+    const float dyp = (float)(((q >> 4) + 0.5 - 0.5 * TH) * p.sy * p.inv_s);
+    const uint32_t tbase = tmem + a * 256 + ((uint32_t)(32 * (warp & 3)) << 16);
+    const bool read = acc_ok && any_tile;   // warp-uniform
+    float St[16];
+    if (read) tmem_ld16(tbase, St);
+    else
+#pragma unroll
+      for (int j = 0; j < 16; ++j) St[j] = 0.f;
+    int count;
+    bool handover = false;
+    if (WK == MLS_W_WENDLAND) {
+      count = p.cnt[pi];
+      handover = (count > 0) && (count <= K + 2);
+    } else {
+      count = (int)(p.n < (1 << 30) ? p.n : (1 << 30));
+      // clipping |x~|_inf <= kRMax is exact in 16-bit arithmetic only when the
+      // pixel has a point within (kRMax - |delta|_inf - 4.2) h
+      const float reach = kRMax - fmaxf(fabsf(dxp), fabsf(dyp));
+      handover = !(p.mstab[pi] <= reach * reach - 18.f) || !read;
+    }
+    float z[K];
+    int outcome = SOLVE_RECOMPUTE;
+    const bool nosup = (count == 0);
+    if (!nosup && !handover) {
+      float Sp[15];
+      shift_moments<NM>(St, Sp, dxp, dyp);
+      outcome = solve_pixel_fp32<K>(Sp, z, p);
+      if (outcome != SOLVE_RECOMPUTE) to_tile_frame<K>(z, dxp, dyp);
+    }
+    const bool done = !nosup && outcome != SOLVE_RECOMPUTE;
+    const bool give = !nosup && outcome == SOLVE_RECOMPUTE;
+    const size_t plane = (size_t)p.W * p.H;
+    const size_t pix = (size_t)v * p.W + u;
+    float *field = (float *)p.field;
+    if (primary && inside && give && d0 == 0) {
+      const unsigned int k = atomicAdd(p.relist_count, 1u);
+      p.relist[k] = (int)pix;
+    }
+    if (primary && inside && nosup) {
+      for (int d = d0; d < d0 + Dc; ++d) {
+        field[(size_t)d * plane + pix] = __int_as_float(0x7fc00000);
+        if (p.bands) p.bands[(size_t)d * plane + pix] = 255;
+      }
+    }
+    // value columns in groups of 48 (K = 3, 6) or 16 (K = 1)
+    constexpr int GC = (K == 1) ? 16 : 48;
+    constexpr int GD = GC / K;
+    for (int gbase = gfirst * GD; gbase < Dc; gbase += gstep * GD) {
+      float rv[GC];
+      if (read) {
+#pragma unroll
+        for (int c = 0; c < GC / 16; ++c) {
+          float tmp[16];
+          tmem_ld16(tbase + 16 + gbase * K + 16 * c, tmp);
+#pragma unroll
+          for (int j = 0; j < 16; ++j) rv[16 * c + j] = tmp[j];
+        }
+      }
+      if (done && inside && read) {
+#pragma unroll
+        for (int dd = 0; dd < GD; ++dd) {
+          const int d = gbase + dd;
+          if (d < Dc) {
+            float acc = 0.f;
+#pragma unroll
+            for (int b = 0; b < K; ++b) acc = fmaf(z[b], rv[dd * K + b], acc);
+            const int dg = d0 + d;
+            const float f = fmaf(acc, p.fscl32[dg], p.fcen32[dg]);
+            field[(size_t)dg * plane + pix] = f;
+            if (p.bands) p.bands[(size_t)dg * plane + pix] = band_of(f, p.lev32 + (size_t)dg * p.L, p.L);
+          }
+        }
+      }
+    }
+    if (primary && inside && p.status && d0 == 0 && !give)
+      p.status[pix] = nosup ? (uint8_t)MLS_ST_NO_SUPPORT
+                            : (uint8_t)(DEG | (outcome == SOLVE_FP64 ? MLS_ST_FP64_SOLVE : 0));
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 8) {
+    tc_fence_after();
+    tmem_dealloc(tmem, 512);
+  }
+}
+
+// Bounded-wait self test: waits on an mbarrier phase that nothing completes
+// and reports the error code the kernel leaves behind.
+__global__ void k_wait_selftest(int *err, uint64_t limit_ns) {
+  __shared__ uint64_t bar;
+  const uint32_t b = smem_u32(&bar);
+  if (threadIdx.x == 0) {
+    mbar_init(b, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) mbar_wait(b, 0, err, ERR_WAIT_FULL, limit_ns);
+}
+
+template <int DEG, int WK, bool FP16, int NACC, bool WSPLIT>
+void launch_one(const KParams &p, int d0, int Dc, int N, uint32_t idesc, cudaStream_t st) {
+  dim3 grid(p.tiles_x, p.tiles_y * (2 / NACC));
+  auto k = k_mls_tc<DEG, WK, FP16, NACC, WSPLIT>;
+  cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+  k<<<grid, kThreads, kSmemBytes, st>>>(p, d0, Dc, N, idesc);
+}
+
+template <int DEG, int WK>
+void launch_deg_w(const KParams &p, int fp16, int wsplit, int d0, int Dc, int N, uint32_t idesc,
+                  cudaStream_t st) {
+  if (fp16) {
+    if (wsplit) launch_one<DEG, WK, true, 1, true>(p, d0, Dc, N, idesc, st);
+    else launch_one<DEG, WK, true, 2, false>(p, d0, Dc, N, idesc, st);
+  } else {
+    if (wsplit) launch_one<DEG, WK, false, 1, true>(p, d0, Dc, N, idesc, st);
+    else launch_one<DEG, WK, false, 2, false>(p, d0, Dc, N, idesc, st);
+  }
+}
+
+}  // namespace
+
+// Dimensions per pass so that 16 + K Dc columns fit one 256-column accumulator.
+static int dims_per_pass(int degree) {
+  const int K = mlsk::n_terms(degree);
+  const int group = (K == 1) ? 16 : 48 / K;   // the epilogue reads whole groups
+  int dc = (kNMax - 16) / K;
+  dc -= dc % group;
+  return dc;
+}
+
+mls_status launch_tc(const KParams &p, int fp16, int wsplit, cudaStream_t st) {
+  const int K = mlsk::n_terms(p.degree);
+  const int dmax = dims_per_pass(p.degree);
+  const int passes = (p.D + dmax - 1) / dmax;
+  const int per = (p.D + passes - 1) / passes;   // balanced passes
+  for (int d0 = 0; d0 < p.D; d0 += per) {
+    const int Dc = (p.D - d0 < per) ? p.D - d0 : per;
+    const int group = (K == 1) ? 16 : 48 / K;
+    const int Dg = (Dc + group - 1) / group * group;    // columns the epilogue reads
+    int N = 16 + Dg * K;
+    N = (N + 15) / 16 * 16;
+    if (N > kNMax) return fail(MLS_E_UNSUPPORTED, "operand wider than one accumulator");
+    const uint32_t fmt = fp16 ? 0u : 1u;
+    const uint32_t idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(N >> 3) << 17) |
+                           ((uint32_t)(kM >> 4) << 24);
+    if (p.weight == MLS_W_GAUSS) {
+      if (p.degree == 0) launch_deg_w<0, MLS_W_GAUSS>(p, fp16, wsplit, d0, Dc, N, idesc, st);
+      else if (p.degree == 1) launch_deg_w<1, MLS_W_GAUSS>(p, fp16, wsplit, d0, Dc, N, idesc, st);
+      else launch_deg_w<2, MLS_W_GAUSS>(p, fp16, wsplit, d0, Dc, N, idesc, st);
+    } else if (p.weight == MLS_W_WENDLAND) {
+      if (p.degree == 0) launch_deg_w<0, MLS_W_WENDLAND>(p, fp16, wsplit, d0, Dc, N, idesc, st);
+      else if (p.degree == 1) launch_deg_w<1, MLS_W_WENDLAND>(p, fp16, wsplit, d0, Dc, N, idesc, st);
+      else launch_deg_w<2, MLS_W_WENDLAND>(p, fp16, wsplit, d0, Dc, N, idesc, st);
+    } else {
+      return fail(MLS_E_UNSUPPORTED, "tensor-core path takes the Gaussian and Wendland weights");
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "k_mls_tc launch");
+  }
+  return MLS_OK;
+}
+
+}  // namespace mlsi
+
+extern "C" int mls_debug_wait_selftest(int64_t limit_ns, int *code_out) {
+  int *d = nullptr;
+  if (cudaMalloc(&d, sizeof(int)) != cudaSuccess) return MLS_E_CUDA;
+  cudaMemset(d, 0, sizeof(int));
+  mlsi::k_wait_selftest<<<1, 32>>>(d, (uint64_t)limit_ns);
+  cudaError_t e = cudaDeviceSynchronize();
+  int code = 0;
+  cudaMemcpy(&code, d, sizeof(int), cudaMemcpyDeviceToHost);
+  cudaFree(d);
+  if (code_out) *code_out = code;
+  return e == cudaSuccess ? MLS_OK : MLS_E_CUDA;
+}

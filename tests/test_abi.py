@@ -1,0 +1,114 @@
+"""The C ABI without a GPU: the library loads, exports every declared symbol,
+its structs match the header, and argument errors return before any launch."""
+import ctypes
+import os
+import re
+import subprocess
+import tempfile
+
+import pytest
+
+from paper_1408_0677_gb300 import _abi, build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "mls.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return _abi.load()
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(mls_[a-z_]+)\s*\(", text)))
+
+
+def test_library_exports_every_declared_symbol(lib):
+    names = declared_functions()
+    assert "mls_create" in names and "mls_render" in names and "mls_bands" in names and "mls_destroy" in names
+    out = subprocess.run(["nm", "-D", "--defined-only", _abi.library_path()], capture_output=True, text=True).stdout
+    exported = set(re.findall(r"\bT (mls_\w+)", out))
+    missing = [n for n in names if n not in exported]
+    assert not missing, f"declared but not exported: {missing}"
+    for n in names:
+        assert hasattr(lib, n)
+
+
+def test_struct_layout_matches_header():
+    src = r'''
+#include <stdio.h>
+#include <stddef.h>
+#include "mls.h"
+int main(void) {
+  printf("%zu %zu %zu %zu %zu\n", sizeof(mls_desc), offsetof(mls_desc, h), offsetof(mls_desc, cond_recompute),
+         sizeof(mls_view), sizeof(mls_stats));
+  return 0;
+}
+'''
+    with tempfile.TemporaryDirectory() as d:
+        c = os.path.join(d, "t.c")
+        exe = os.path.join(d, "t")
+        open(c, "w").write(src)
+        subprocess.check_call(["gcc", "-I" + os.path.join(ROOT, "include"), c, "-o", exe])
+        vals = [int(x) for x in subprocess.check_output([exe]).split()]
+    assert vals == [ctypes.sizeof(_abi.MlsDesc), _abi.MlsDesc.h.offset, _abi.MlsDesc.cond_recompute.offset,
+                    ctypes.sizeof(_abi.MlsView), ctypes.sizeof(_abi.MlsStats)]
+
+
+def test_abi_version_and_defaults(lib):
+    assert _abi.mls_abi_version() == 1
+    d = _abi.mls_desc_default()
+    assert d.cond_fp64 == 1e6 and d.rcond_degenerate == 1e-12 and d.precision == _abi.MLS_P_FP32
+
+
+def _desc(**kw):
+    d = _abi.mls_desc_default()
+    d.n, d.D, d.degree, d.h = 10, 2, 1, 0.1
+    for k, v in kw.items():
+        setattr(d, k, v)
+    return d
+
+
+@pytest.mark.parametrize("kw,code", [
+    (dict(n=0), _abi.MLS_E_INVAL),
+    (dict(D=0), _abi.MLS_E_INVAL),
+    (dict(D=257), _abi.MLS_E_INVAL),
+    (dict(degree=3), _abi.MLS_E_INVAL),
+    (dict(h=0.0), _abi.MLS_E_INVAL),
+    (dict(h=float("nan")), _abi.MLS_E_INVAL),
+    (dict(weight=7), _abi.MLS_E_INVAL),
+    (dict(precision=9), _abi.MLS_E_INVAL),
+    (dict(weight=_abi.MLS_W_INVDIST, alpha=-1.0), _abi.MLS_E_INVAL),
+    (dict(rcond_degenerate=2.0), _abi.MLS_E_INVAL),
+    (dict(weight=_abi.MLS_W_INVDIST, precision=_abi.MLS_P_FP16), _abi.MLS_E_UNSUPPORTED),
+])
+def test_create_rejects_bad_descriptors_before_any_launch(lib, kw, code):
+    buf = (ctypes.c_double * 64)()
+    with pytest.raises(_abi.MlsError) as e:
+        _abi.mls_create(_desc(**kw), ctypes.addressof(buf), ctypes.addressof(buf), False)
+    assert e.value.status == code
+    assert _abi.mls_last_error() != ""
+
+
+def test_null_arguments(lib):
+    assert lib.mls_create(None, None, None, 0, None, None) == _abi.MLS_E_INVAL
+    h = ctypes.c_void_p()
+    d = _desc()
+    assert lib.mls_create(ctypes.byref(d), None, None, 0, None, ctypes.byref(h)) == _abi.MLS_E_INVAL
+    v = _abi.MlsView(4, 4, 0, 0, 1, 1)
+    assert lib.mls_render(None, ctypes.byref(v), None, None, None, 0, None, 1, None) == _abi.MLS_E_INVAL
+    assert lib.mls_bands(None, ctypes.byref(v), None, None, 0, None, 1, None) == _abi.MLS_E_INVAL
+    assert lib.mls_sync(None, 1.0, None) == _abi.MLS_E_INVAL
+    assert lib.mls_destroy(None) == _abi.MLS_OK
+
+
+def test_injected_allocation_failure_returns_nomem(lib, monkeypatch):
+    """Host-side fault injection: the allocation fails before any CUDA call."""
+    monkeypatch.setenv("MLS_INJECT_NOMEM", "1")
+    buf = (ctypes.c_double * 64)()
+    with pytest.raises(_abi.MlsError) as e:
+        _abi.mls_create(_desc(), ctypes.addressof(buf), ctypes.addressof(buf), False)
+    assert e.value.status == _abi.MLS_E_NOMEM

@@ -1,0 +1,148 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1408_0677_gb300 import inputs
+from tests.gpu_util import compare, gpu_render
+
+pytestmark = pytest.mark.gpu
+
+G, WD, ID = inputs.WEIGHT_GAUSS, inputs.WEIGHT_WENDLAND, inputs.WEIGHT_INVDIST
+ALL_PREC = ["fp64", "fp32", "fp16", "bf16"]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+def _ref(wl, pixels=None):
+    return oracle.mls(wl.xy, wl.F, wl.degree, wl.weight, wl.h, wl.W, wl.H, view=wl.view, pixels=pixels,
+                      alpha=wl.alpha)
+
+
+@pytest.mark.parametrize("precision", ALL_PREC)
+def test_wine_shaped_full_grid(precision):
+    """n=178, D=13, 256x256, linear basis, Gaussian h=0.05: every pixel."""
+    wl = inputs.wine_shaped()
+    res = gpu_render(wl, precision)
+    err, npx = compare(wl, res, _ref(wl), precision)
+    assert npx > 0.99 * wl.W * wl.H
+    print(f"wine-shaped {precision}: max err {err:.3g} of range over {npx} pixels")
+
+
+SMALL = [
+    # seed, n, D, W, H, degree, weight, h
+    (1, 60, 3, 37, 23, 2, G, 0.12),
+    (2, 60, 5, 50, 17, 1, G, 0.08),
+    (3, 40, 2, 33, 33, 0, G, 0.1),
+    (4, 400, 4, 45, 38, 2, WD, 0.15),
+    (5, 300, 3, 31, 29, 1, WD, 0.1),
+    (6, 80, 2, 26, 19, 0, WD, 0.08),
+    (7, 50, 3, 29, 21, 1, ID, 0.2),
+    (8, 50, 2, 17, 35, 2, ID, 0.2),
+    (9, 200, 17, 40, 40, 2, G, 0.1),
+]
+
+
+@pytest.mark.parametrize("case", SMALL, ids=[f"s{c[0]}" for c in SMALL])
+@pytest.mark.parametrize("precision", ALL_PREC)
+def test_small_ragged_cases(case, precision):
+    seed, n, D, W, H, degree, weight, h = case
+    if weight == ID and precision in ("fp16", "bf16"):
+        pytest.skip("tensor-core precisions take the Gaussian and Wendland weights")
+    wl = inputs.small_random(seed, n, D, W, H, degree, weight, h)
+    res = gpu_render(wl, precision)
+    compare(wl, res, _ref(wl), precision)
+
+
+@pytest.mark.parametrize("precision", ALL_PREC)
+def test_fourier_10k_sampled(precision):
+    """n=10,000, D=32, 1024x1024, quadratic, Gaussian h=0.02: full render, 2048 sampled pixels."""
+    wl = inputs.fourier_10k()
+    pix = inputs.sample_pixels(11, wl.W, wl.H, 2048 if precision != "fp64" else 512)
+    res = gpu_render(wl, precision)
+    err, npx = compare(wl, res, _ref(wl, pix), precision, pixels=pix)
+    print(f"fourier-10k {precision}: max err {err:.3g} of range, recomputed {res['stats'].recomputed}")
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp16", "bf16"])
+def test_clusters_200k_sampled(precision):
+    """n=200,000, D=64, 2048x2048, quadratic, Wendland radius 0.015 with binning."""
+    wl = inputs.clusters_200k()
+    rng = np.random.default_rng(12)
+    pix = inputs.sample_pixels(12, wl.W, wl.H, 1024)
+    # plus a dense 32x32 window in a cluster core and a sparse one
+    c = (wl.xy[0] * wl.W).astype(int)
+    win = [(min(max(c[1] - 16, 0), wl.H - 32) + dv) * wl.W + min(max(c[0] - 16, 0), wl.W - 32) + du
+           for dv in range(32) for du in range(32)]
+    pix = np.unique(np.concatenate([pix, np.array(win, np.int64), rng.integers(0, 64, 256)]))
+    res = gpu_render(wl, precision)
+    err, npx = compare(wl, res, _ref(wl, pix), precision, pixels=pix)
+    print(f"clusters-200k {precision}: max err {err:.3g} of range, recomputed {res['stats'].recomputed}")
+
+
+@pytest.mark.parametrize("precision", ALL_PREC)
+def test_single_point_and_tiny_grid(precision):
+    wl = inputs.small_random(21, 1, 2, 1, 1, 2, G, 0.1)
+    res = gpu_render(wl, precision)
+    compare(wl, res, _ref(wl), precision)
+    np.testing.assert_allclose(res["field"].reshape(-1), wl.F[0], rtol=1e-6)
+    assert (res["status"][0, 0] & 0x03) == 0
+
+
+@pytest.mark.parametrize("precision", ALL_PREC)
+def test_empty_support_is_nan_and_band_255(precision):
+    wl = inputs.small_random(22, 30, 2, 48, 48, 2, WD, 0.05)
+    wl.xy = 0.2 + 0.1 * wl.xy      # points only in a corner
+    res = gpu_render(wl, precision)
+    compare(wl, res, _ref(wl), precision)
+    far = res["status"][-1, -1]
+    assert far & 0x04 and np.isnan(res["field"][:, -1, -1]).all() and (res["bands"][:, -1, -1] == 255).all()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "fp16"])
+def test_standalone_bands_equal_fused(precision):
+    import torch
+
+    from paper_1408_0677_gb300 import Renderer
+    wl = inputs.small_random(23, 100, 4, 70, 45, 2, G, 0.1)
+    r = Renderer(torch.from_numpy(wl.xy).cuda(), torch.from_numpy(wl.F).cuda(), degree=2, weight=G, h=0.1,
+                 precision=precision)
+    out = r.render(wl.W, wl.H, levels=wl.levels)
+    b2 = r.bands(out["field"], wl.levels, wl.W, wl.H)
+    r.sync()
+    assert torch.equal(out["bands"], b2)
+    r.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "fp16"])
+def test_host_pointer_path_matches_device_path(precision):
+    from paper_1408_0677_gb300 import Renderer
+    wl = inputs.small_random(24, 120, 3, 33, 27, 1, G, 0.1)
+    dev = gpu_render(wl, precision)
+    r = Renderer(wl.xy, wl.F, degree=1, weight=G, h=0.1, precision=precision)
+    host = r.render_host(wl.W, wl.H, levels=wl.levels)
+    r.close()
+    assert np.array_equal(host["field"], dev["field"], equal_nan=True)
+    assert np.array_equal(host["bands"], dev["bands"])
+    assert np.array_equal(host["status"], dev["status"])
+
+
+def test_injected_nomem_leaves_handle_usable(monkeypatch):
+    import torch
+
+    from paper_1408_0677_gb300 import MlsError, Renderer
+    wl = inputs.small_random(25, 50, 2, 20, 20, 1, G, 0.1)
+    r = Renderer(torch.from_numpy(wl.xy).cuda(), torch.from_numpy(wl.F).cuda(), degree=1, weight=G, h=0.1)
+    monkeypatch.setenv("MLS_INJECT_NOMEM", "1")
+    with pytest.raises(MlsError) as e:
+        r.render(wl.W, wl.H)
+    assert e.value.status == 2
+    monkeypatch.delenv("MLS_INJECT_NOMEM")
+    out = r.render(wl.W, wl.H)
+    r.sync()
+    assert torch.isfinite(out["field"]).all()
+    r.close()
