@@ -1,0 +1,331 @@
+"""Benchmark of the MLS field reconstruction on one GB300 (or N replicas).
+
+One step = the whole hot path over the 10k-point workload (n = 10,000 points
+in 8 Gaussian clusters plus 20% uniform background, D = 32 Fourier fields,
+1024 x 1024 pixels, quadratic basis, Gaussian h = 0.02 summed over every
+point, 16 iso-levels): mls_create from device-resident points (value ranges,
+layouts), the stabiliser prepass, the tensor-core moment contraction with
+its per-pixel solve and fused iso-bands, and the recompute of ill-conditioned
+pixels.  Metric: pixel*point*dim updates/s = W * H * n * D / step time.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp16|bf16|fp32|fp64]
+  python bench.py --impl reference    # the FP64 CPU oracle on a bounded pixel sample
+
+With N > 1 (torchrun, one process per GPU) every rank renders its own
+replica (the pixels of one render are independent; no collective on the
+data path): weak scaling, max time over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "MLS pixel*point*dim updates/s"
+UNIT = "pixel*point*dim/s"
+WORKLOAD = "fourier_n10k_d32_1024x1024_quadratic_gauss_h0.02_L16"
+TC_SRC = os.path.join(ROOT, "paper_1408_0677_gb300", "csrc", "tc.cu")
+PROFILE = os.path.join(ROOT, "profiles", "k_mls_tc_fourier10k.json")
+
+
+def _peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _dist():
+    import torch
+    import torch.distributed as dist
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1 and not dist.is_initialized():
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    return world, rank, local
+
+
+def cpu_baseline(wl, seconds=15.0):
+    """FP64 oracle on a bounded pixel sample (all host cores)."""
+    import oracle
+    rng_pix = None
+    npx = 64
+    threads = os.cpu_count() or 1
+    t_used, px_done = 0.0, 0
+    seed = 0
+    while t_used < seconds and npx <= 1 << 16:
+        pix = np.random.default_rng(100 + seed).choice(wl.W * wl.H, size=npx, replace=False)
+        t0 = time.perf_counter()
+        oracle.mls(wl.xy, wl.F, wl.degree, wl.weight, wl.h, wl.W, wl.H, pixels=pix, threads=threads)
+        dt = time.perf_counter() - t0
+        t_used += dt
+        px_done += npx
+        rng_pix = pix
+        seed += 1
+        if dt < seconds / 4:
+            npx *= 2
+    del rng_pix
+    value = px_done * wl.n * wl.D / t_used
+    return {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"{px_done} random pixels of the workload, full n={wl.n} sum each, FP64, {t_used:.1f} s"}
+
+
+def run_reference(args):
+    """The reference arm: the FP64 oracle, timed on the host cores."""
+    world, rank, _ = _dist()
+    if rank != 0:
+        return
+    from paper_1408_0677_gb300 import inputs
+    import oracle
+    wl = inputs.fourier_10k()
+    threads = os.cpu_count() or 1
+    npx = 256
+    pix = np.random.default_rng(7).choice(wl.W * wl.H, size=npx, replace=False)
+    for _ in range(args.warmup):
+        oracle.mls(wl.xy, wl.F, wl.degree, wl.weight, wl.h, wl.W, wl.H, pixels=pix[:16], threads=threads)
+    times = []
+    for k in range(args.steps):
+        p = np.random.default_rng(1000 + k).choice(wl.W * wl.H, size=npx, replace=False)
+        t0 = time.perf_counter()
+        oracle.mls(wl.xy, wl.F, wl.degree, wl.weight, wl.h, wl.W, wl.H, pixels=p, threads=threads)
+        times.append(time.perf_counter() - t0)
+    t = float(np.sum(times))
+    value = args.steps * npx * wl.n * wl.D / t
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "sample_pixels_per_step": npx},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                             "sample": f"{npx} random pixels per step (full sum over n={wl.n})"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def _tc_hash():
+    try:
+        return hashlib.sha256(open(TC_SRC, "rb").read()).hexdigest()
+    except Exception:
+        return None
+
+
+def _traffic(n_launch_units):
+    """DRAM bytes per launch from the committed ncu summary, if the kernel is unchanged."""
+    try:
+        prof = json.load(open(PROFILE))
+    except Exception:
+        return None
+    if prof.get("tc_cu_sha256") != _tc_hash():
+        return None
+    per_unit = prof.get("dram_bytes") / prof.get("units")
+    return per_unit * n_launch_units
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    world, rank, local = _dist()
+    torch.cuda.set_device(local)
+    from paper_1408_0677_gb300 import MLS_P_FP64, MlsView, Renderer, inputs, mls_create, mls_desc_default  # noqa
+    from paper_1408_0677_gb300 import _abi
+
+    wl = inputs.fourier_10k()
+    n, D, W, H, L = wl.n, wl.D, wl.W, wl.H, wl.levels.shape[1]
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    sptr = stream.cuda_stream
+    xy_d = torch.from_numpy(wl.xy).to(dev)
+    F_d = torch.from_numpy(wl.F).to(dev)
+    fdt = torch.float64 if args.precision == "fp64" else torch.float32
+    field = torch.empty((D, H, W), dtype=fdt, device=dev)
+    status = torch.empty((H, W), dtype=torch.uint8, device=dev)
+    bands = torch.empty((D, H, W), dtype=torch.uint8, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # > L2 (129 MB)
+    lev = np.ascontiguousarray(wl.levels)
+
+    def step_device():
+        r = Renderer(xy_d, F_d, degree=wl.degree, weight=wl.weight, h=wl.h, precision=args.precision,
+                     stream=sptr)
+        r.render(W, H, levels=lev, field=field, bands=bands, status_out=status)
+        return r
+
+    # warm-up
+    for _ in range(args.warmup):
+        r = step_device()
+        r.sync()
+        r.close()
+    torch.cuda.synchronize()
+
+    # ---- device-resident timed region
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    total_ms, kern_ms, launches, handed, handed64 = 0.0, [], 0, 0, 0
+    for _ in range(args.steps):
+        flush.fill_(1.0)                                  # L2 flush outside the timed step
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        r = step_device()
+        e1.record(stream)
+        st = r.sync()
+        e1.synchronize()
+        total_ms += e0.elapsed_time(e1)
+        kern_ms.append(st.main_kernel_ms)
+        launches += st.launches
+        handed, handed64 = st.recomputed, st.recomputed_fp64
+        r.close()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clocks = sampler.stop()
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_step = total_ms / args.steps
+    units = W * H * n * D
+    value = world * units / (ms_step * 1e-3)
+
+    # ---- end-to-end through the public API with host buffers (pinned)
+    xy_h = torch.from_numpy(wl.xy).pin_memory().numpy()
+    F_h = torch.from_numpy(wl.F).pin_memory().numpy()
+    field_h = torch.empty((D, H, W), dtype=fdt).pin_memory().numpy()
+    status_h = torch.empty((H, W), dtype=torch.uint8).pin_memory().numpy()
+    bands_h = torch.empty((D, H, W), dtype=torch.uint8).pin_memory().numpy()
+
+    def step_host():
+        r = Renderer(xy_h, F_h, degree=wl.degree, weight=wl.weight, h=wl.h, precision=args.precision,
+                     stream=sptr)
+        r.render_host(W, H, levels=lev, field=field_h, bands=bands_h, status_out=status_h)
+        r.close()
+
+    step_host()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    e2e_ms = 0.0
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        step_host()
+        e2e_ms += 1e3 * (time.perf_counter() - t0)
+    if world > 1:
+        t = torch.tensor([e2e_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    e2e_value = world * units / (e2e_ms / args.steps * 1e-3)
+    h2d = wl.xy.nbytes + wl.F.nbytes + lev.nbytes
+    d2h = field_h.nbytes + status_h.nbytes + bands_h.nbytes
+
+    if rank != 0:
+        return
+    peaks, src = _peaks()
+    k_ms = float(np.mean(kern_ms))
+    flops = 2.0 * (6 * D + 15) * W * H * n       # algorithmic contraction flops per launch
+    achieved = flops / (k_ms * 1e-3) / 1e12
+    peak = peaks.get("bf16_tflops", 1900.0)       # FP16 and BF16 share the dense tensor rate
+    roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "traffic": _traffic(W * H), "peak_source": f"{src} bf16 burst (fp16 dense rate equal)",
+            "kernel": "k_mls_tc", "kernel_ms": k_ms, "flops_per_launch": flops}
+    cpu = cpu_baseline(wl, seconds=args.cpu_seconds) if args.cpu_seconds > 0 else None
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n": n, "D": D, "W": W, "H": H, "degree": 2, "weight": "gauss",
+                       "h": wl.h, "levels": L, "precision": args.precision, "l2": "flushed between steps",
+                       "replicas": world},
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+                    "ms_per_step": e2e_ms / args.steps},
+            "roofline": roof, "cpu_baseline": cpu, "clocks": clocks,
+            "gpu_launches": int(launches),
+            "recompute": {"handed_over_pixels": int(handed), "fp64_pixels": int(handed64)}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp16", choices=["fp16", "bf16", "fp32", "fp64"])
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -69,7 +69,7 @@ typedef enum mls_precision {
 #define MLS_ST_DEGREE_MASK 0x03u  /* basis degree used (0, 1, 2) */
 #define MLS_ST_NO_SUPPORT  0x04u  /* no point with positive weight: value NaN, band 255 */
 #define MLS_ST_FP64_SOLVE  0x08u  /* condition estimate above cond_fp64: FP64 factorisation */
-#define MLS_ST_RECOMPUTED  0x10u  /* pixel recomputed entirely in FP64 */
+#define MLS_ST_RECOMPUTED  0x10u  /* pixel handed to the recompute path (FP64 decisions) */
 #define MLS_ST_DEGRADED    0x20u  /* degree lowered by the degenerate-pixel policy */
 #define MLS_ST_COINCIDENT  0x40u  /* inverse distance: pixel centre on a data point */
 
@@ -86,13 +86,16 @@ typedef enum mls_precision {
  *               runs in FP64 (default 1e6)
  *   rcond_degenerate  reciprocal condition (1-norm, diagonally equilibrated
  *               moment matrix) below which the degree is lowered (1e-12)
- *   cond_recompute    condition estimate above which a reduced-precision
- *               pixel is recomputed entirely in FP64 (0 = default for the
- *               precision: FP32 1e4, FP16 1e5, BF16 1e4)
- *   weight_split      tensor-core precisions: 1 (default) stores each weight
- *               as a hi + lo pair of 16-bit values (three products per
- *               point tile, weights to ~22 / 16 bits); 0 rounds each weight
- *               once (two products, faster, larger error on rough data)
+ *   cond_recompute    condition estimate (pixel frame) above which a
+ *               reduced-precision pixel is handed to the recompute path:
+ *               FP64 moments for the degree policy, the fit solved in the
+ *               frame of the weighted centroid, and FP64 throughout where
+ *               even that frame is ill conditioned (0 = default for the
+ *               precision: FP32 1e3, FP16 1e3, BF16 1e2)
+ *   weight_split      tensor-core precisions: 1 stores each weight as a hi +
+ *               lo pair of 16-bit values (three products per point tile);
+ *               0 rounds each weight once (two products); -1 (default)
+ *               picks 0 for FP16 and 1 for BF16
  */
 typedef struct mls_desc {
     int64_t n;
@@ -117,10 +120,13 @@ typedef struct mls_view {
 
 /* Counters of the last completed render (see mls_sync). */
 typedef struct mls_stats {
-    int64_t pairs;          /* pixel-point pairs the method visited */
-    int64_t recomputed;     /* pixels recomputed in FP64 */
-    int64_t device_error;   /* device error word (0 = none; timeouts set it) */
-    double last_render_ms;  /* device time of the last render (CUDA events) */
+    int64_t pairs;            /* pixel-point pairs the main kernel visited */
+    int64_t recomputed;       /* pixels handed to the recompute path */
+    int64_t recomputed_fp64;  /* of those, pixels finished by the pure FP64 kernel */
+    int64_t device_error;     /* device error word (0 = none; timeouts set it) */
+    int64_t launches;         /* kernels this handle has launched since mls_create */
+    double last_render_ms;    /* device time of the last render (CUDA events) */
+    double main_kernel_ms;    /* device time of its main MLS kernel(s), events on the same stream */
 } mls_stats;
 
 typedef struct mls_handle mls_handle;

@@ -40,8 +40,9 @@ class MlsView(ctypes.Structure):
 
 
 class MlsStats(ctypes.Structure):
-    _fields_ = [("pairs", ctypes.c_int64), ("recomputed", ctypes.c_int64),
-                ("device_error", ctypes.c_int64), ("last_render_ms", ctypes.c_double)]
+    _fields_ = [("pairs", ctypes.c_int64), ("recomputed", ctypes.c_int64), ("recomputed_fp64", ctypes.c_int64),
+                ("device_error", ctypes.c_int64), ("launches", ctypes.c_int64), ("last_render_ms", ctypes.c_double),
+                ("main_kernel_ms", ctypes.c_double)]
 
 
 class MlsError(RuntimeError):

@@ -69,6 +69,9 @@ struct KParams {
   const float *fcen32, *fscl32;
   const double *x64, *y64;     // raw positions [n]
   const double *FT64;          // raw values [D][n]
+  const float *xyb;            // tensor path: (x[8], y[8]) per 8-point block, [n_pad/8][16]
+  const float *fb;             // tensor path: values per pass, [passes][n_pad/8][fb_dc][8]
+  int fb_dc;                   // dimensions per pass of fb
   const int *cell_start;       // [gx * gy + 1] (Wendland)
   int gx, gy;
   double gx0, gy0, cell;       // grid origin and cell size in raw coordinates

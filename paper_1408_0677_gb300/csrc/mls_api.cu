@@ -82,7 +82,7 @@ static mls_status check_levels(const double *levels, int L, int D) {
 static mls_status ensure_scratch(mls_handle *h, int W, int H, cudaStream_t st) {
   const int tx = (W + kTile - 1) / kTile, ty = (H + kTile - 1) / kTile;
   const size_t padded = (size_t)tx * kTile * ty * kTile;
-  const size_t need = 256 + padded * sizeof(float) + padded * sizeof(int) + (size_t)W * H * sizeof(int) + 256;
+  const size_t need = 256 + padded * sizeof(float) + padded * sizeof(int) + 2 * (size_t)W * H * sizeof(int) + 256;
   if (need <= h->scratch_bytes) return MLS_OK;
   release(h, h->scratch, st);
   h->scratch = nullptr;
@@ -93,11 +93,12 @@ static mls_status ensure_scratch(mls_handle *h, int W, int H, cudaStream_t st) {
   h->scratch = p;
   h->scratch_bytes = need;
   char *b = (char *)p;
-  h->counters = (unsigned int *)b;           // [0] hand-over count
+  h->counters = (unsigned int *)b;           // [0] hand-over count, [1] FP64 count
   h->err = (int *)(b + 64);
   h->mstab = (float *)(b + 256);
   h->cnt = (int *)(b + 256 + padded * sizeof(float));
   h->relist = (int *)(b + 256 + padded * (sizeof(float) + sizeof(int)));
+  h->relist2 = h->relist + (size_t)W * H;
   return MLS_OK;
 }
 
@@ -166,6 +167,9 @@ static mlsk::KParams base_params(const mls_handle *h, const mls_view *v) {
   p.x64 = P.x64;
   p.y64 = P.y64;
   p.FT64 = P.FT64;
+  p.xyb = P.xyb;
+  p.fb = P.fb;
+  p.fb_dc = P.fb_dc;
   p.cell_start = P.cell_start;
   p.gx = P.gx;
   p.gy = P.gy;
@@ -223,7 +227,7 @@ mls_status mls_desc_default(mls_desc *desc) {
   desc->cond_fp64 = 1e6;
   desc->rcond_degenerate = 1e-12;
   desc->cond_recompute = 0.0;
-  desc->weight_split = 1;
+  desc->weight_split = -1;
   return MLS_OK;
 }
 
@@ -245,14 +249,14 @@ mls_status mls_create(const mls_desc *desc, const double *xy, const double *F, i
   if (!(d.rcond_degenerate >= 0.0) || !(d.rcond_degenerate < 1.0))
     return fail(MLS_E_INVAL, "rcond_degenerate must be in [0, 1)");
   if (!(d.cond_recompute >= 0.0)) return fail(MLS_E_INVAL, "cond_recompute must be >= 0");
-  if (d.weight_split != 0 && d.weight_split != 1) return fail(MLS_E_INVAL, "weight_split must be 0 or 1");
+  if (d.weight_split < -1 || d.weight_split > 1) return fail(MLS_E_INVAL, "weight_split must be -1, 0 or 1");
   if ((d.precision == MLS_P_BF16 || d.precision == MLS_P_FP16) && d.weight == MLS_W_INVDIST)
     return fail(MLS_E_UNSUPPORTED, "the tensor-core precisions support the Gaussian and Wendland weights");
 
   mls_handle *h = new mls_handle();
   h->desc = d;
-  if (h->desc.cond_recompute == 0.0)
-    h->desc.cond_recompute = d.precision == MLS_P_FP16 ? 1e5 : 1e4;
+  if (h->desc.cond_recompute == 0.0) h->desc.cond_recompute = d.precision == MLS_P_BF16 ? 1e2 : 1e3;
+  if (h->desc.weight_split < 0) h->desc.weight_split = d.precision == MLS_P_BF16 ? 1 : 0;
   cudaStream_t st = (cudaStream_t)stream;
   h->stream = st;
   mls_status s = MLS_OK;
@@ -283,7 +287,8 @@ mls_status mls_create(const mls_desc *desc, const double *xy, const double *F, i
     release(h, (void *)xy_d, st);
     release(h, (void *)F_d, st);
   }
-  if (cudaEventCreate(&h->ev0) != cudaSuccess || cudaEventCreate(&h->ev1) != cudaSuccess) {
+  if (cudaEventCreate(&h->ev0) != cudaSuccess || cudaEventCreate(&h->ev1) != cudaSuccess ||
+      cudaEventCreate(&h->evk0) != cudaSuccess || cudaEventCreate(&h->evk1) != cudaSuccess) {
     s = cuda_fail(cudaGetLastError(), "cudaEventCreate");
     goto bad;
   }
@@ -299,6 +304,8 @@ bad:
   cudaGetLastError();
   if (h->ev0) cudaEventDestroy(h->ev0);
   if (h->ev1) cudaEventDestroy(h->ev1);
+  if (h->evk0) cudaEventDestroy(h->evk0);
+  if (h->evk1) cudaEventDestroy(h->evk1);
   delete h;
   return s;
 }
@@ -341,18 +348,29 @@ mls_status mls_render(mls_handle *h, const mls_view *view, void *field, uint8_t 
   MLS_CUDA_TRY(cudaMemsetAsync(h->scratch, 0, 256, st));
   MLS_CUDA_TRY(cudaEventRecord(h->ev0, st));
   if (fp64) {
+    MLS_CUDA_TRY(cudaEventRecord(h->evk0, st));
     launch_f64(p, (int64_t)plane, st);
+    MLS_CUDA_TRY(cudaEventRecord(h->evk1, st));
+    h->launches += 1;
   } else {
     launch_prepass(p, st);
+    MLS_CUDA_TRY(cudaEventRecord(h->evk0, st));
     if (h->desc.precision == MLS_P_FP32) {
       launch_f32(p, st);
+      h->launches += 2;
     } else {
-      if ((s = launch_tc(p, h->desc.precision == MLS_P_FP16, h->desc.weight_split, st)) != MLS_OK) return s;
+      int nl = 0;
+      if ((s = launch_tc(p, h->desc.precision == MLS_P_FP16, h->desc.weight_split, st, &nl)) != MLS_OK) return s;
+      h->launches += 1 + nl;
     }
-    // pixels handed over by the reduced-precision path: recompute in FP64
+    MLS_CUDA_TRY(cudaEventRecord(h->evk1, st));
+    h->launches += 2;
+    // pixels handed over by the reduced-precision path: centroid-frame
+    // recompute, and the pure FP64 kernel for what is left
+    launch_handover(p, h->relist, h->counters, (int64_t)plane, h->relist2, h->counters + 1, st);
     mlsk::KParams q = p;
-    q.list = h->relist;
-    q.list_count = h->counters;
+    q.list = h->relist2;
+    q.list_count = h->counters + 1;
     q.list_cap = (int64_t)plane;
     q.field_fp64 = 0;
     launch_f64(q, 0, st);
@@ -434,9 +452,12 @@ mls_status mls_sync(mls_handle *h, double timeout_s, mls_stats *stats) {
     memset(stats, 0, sizeof *stats);
     stats->pairs = h->last_pairs;
     stats->recomputed = cnt[0];
+    stats->recomputed_fp64 = cnt[1];
     stats->device_error = err;
     float ms = 0.f;
     if (h->timed && cudaEventElapsedTime(&ms, h->ev0, h->ev1) == cudaSuccess) stats->last_render_ms = ms;
+    if (h->timed && cudaEventElapsedTime(&ms, h->evk0, h->evk1) == cudaSuccess) stats->main_kernel_ms = ms;
+    stats->launches = h->launches;
     cudaGetLastError();
   }
   if (err) return fail(MLS_E_TIMEOUT, "a bounded device wait gave up (error word " + std::to_string(err) + ")");
@@ -452,6 +473,8 @@ mls_status mls_destroy(mls_handle *h) {
   cudaStreamSynchronize(st);
   if (h->ev0) cudaEventDestroy(h->ev0);
   if (h->ev1) cudaEventDestroy(h->ev1);
+  if (h->evk0) cudaEventDestroy(h->evk0);
+  if (h->evk1) cudaEventDestroy(h->evk1);
   cudaGetLastError();
   delete h;
   return MLS_OK;

@@ -24,6 +24,8 @@ struct PointSet {
   float *xs = nullptr, *ys = nullptr, *FT32 = nullptr;
   double *fcen = nullptr, *fscl = nullptr;
   float *fcen32 = nullptr, *fscl32 = nullptr;
+  float *xyb = nullptr, *fb = nullptr;   // point-blocked layouts of the tensor path
+  int fb_dc = 0;
   int *cell_start = nullptr;
   int gx = 0, gy = 0;
   double gx0 = 0, gy0 = 0, cell = 0;
@@ -43,6 +45,7 @@ struct mls_handle {
   float *mstab = nullptr;
   int *cnt = nullptr;
   int *relist = nullptr;
+  int *relist2 = nullptr;            // pixels the hand-over path passes to FP64
   unsigned int *counters = nullptr;  // [0] recompute count
   int *err = nullptr;
   double *lev64 = nullptr;
@@ -51,7 +54,8 @@ struct mls_handle {
   // staging for host-pointer calls
   void *stage = nullptr;
   size_t stage_bytes = 0;
-  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr, evk0 = nullptr, evk1 = nullptr;
+  int64_t launches = 0;              // kernels launched by this handle
   int64_t last_pairs = 0;
   bool timed = false;
 };
@@ -67,8 +71,12 @@ void launch_prepass(const mlsk::KParams &p, cudaStream_t st);
 void launch_f32(const mlsk::KParams &p, cudaStream_t st);
 void launch_f64(const mlsk::KParams &p, int64_t npix, cudaStream_t st);
 void launch_bands(const mlsk::KParams &p, bool fp64, cudaStream_t st);
+// handover.cu: ill-conditioned pixels of the reduced-precision renders
+void launch_handover(const mlsk::KParams &p, const int *list, const unsigned int *cnt, int64_t cap, int *list2,
+                     unsigned int *cnt2, cudaStream_t st);
 // tc.cu
-mls_status launch_tc(const mlsk::KParams &p, int fp16, int wsplit, cudaStream_t st);
+mls_status launch_tc(const mlsk::KParams &p, int fp16, int wsplit, cudaStream_t st, int *nlaunch);
+int tc_dims_per_pass(int D, int degree);
 
 // errors (mls_api.cu)
 mls_status fail(mls_status s, const std::string &msg);

@@ -263,9 +263,14 @@ __global__ __launch_bounds__(256) void k_mls_f64(KParams p, int64_t npix_all) {
     } else {
       a1s[0] = (int)n;
     }
-    // stabiliser m = min r^2 (Gaussian, inverse distance)
+    // stabiliser m = min r^2 (Gaussian, inverse distance); hand-over lists
+    // take the prepass value (any common weight factor leaves the fit unchanged)
     double m = 0.0;
-    if (WK != MLS_W_WENDLAND) {
+    const float mhat = (p.list && WK != MLS_W_WENDLAND) ? p.mstab[(size_t)v * (p.tiles_x * 16) + u] : 0.f;
+    const float pxs = scaled_px(p, u), pys = scaled_py(p, v);
+    if (p.list && WK != MLS_W_WENDLAND) {
+      m = (double)mhat * h2;
+    } else if (WK != MLS_W_WENDLAND) {
       double mm = DBL_MAX;
       for (int64_t i = lane; i < n; i += 32) {
         const double dx = __dadd_rn(p.x64[i], -px), dy = __dadd_rn(p.y64[i], -py);
@@ -290,6 +295,14 @@ __global__ __launch_bounds__(256) void k_mls_f64(KParams p, int64_t npix_all) {
       for (int dd = 0; dd < DC; ++dd) csum[dd] = 0.0;
       for (int r = 0; r < nr; ++r) {
         for (int64_t i = a0s[r] + lane; i < a1s[r]; i += 32) {
+          if (WK == MLS_W_GAUSS && p.list) {
+            // conservative FP32 test before any FP64 work on far pairs
+            const float dxs = p.xs[i] - pxs, dys = p.ys[i] - pys;
+            if (fmaf(dxs, dxs, dys * dys) - mhat > (float)kGaussCut + 1.f) {
+              ++count;
+              continue;
+            }
+          }
           const double dx = __dadd_rn(p.x64[i], -px), dy = __dadd_rn(p.y64[i], -py);
           const double r2 = __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy));
           double w;

@@ -184,6 +184,26 @@ __global__ void k_finish(const double *x64, const double *y64, const double *FT6
   }
 }
 
+// Point-blocked copies for the tensor path: positions as (x[8], y[8]) per
+// block of 8 points, values per pass of dc dimensions as [block][dc][8].
+__global__ void k_block(const float *xs, const float *ys, const float *FT32, int64_t n_pad, int D, int dc,
+                        int passes, float *xyb, float *fb) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n_pad) return;
+  const int64_t b = i >> 3;
+  const int j = (int)(i & 7);
+  if (blockIdx.y == 0) {
+    xyb[b * 16 + j] = xs[i];
+    xyb[b * 16 + 8 + j] = ys[i];
+  }
+  const int64_t nblk = n_pad >> 3;
+  for (int pass = blockIdx.y; pass < passes; pass += gridDim.y)
+    for (int dd = 0; dd < dc; ++dd) {
+      const int d = pass * dc + dd;
+      fb[((pass * nblk + b) * dc + dd) * 8 + j] = (d < D) ? FT32[(int64_t)d * n_pad + i] : 0.f;
+    }
+}
+
 }  // namespace
 
 mls_status prep_points(mls_handle *h, const double *xy, const double *F, cudaStream_t st) {
@@ -202,14 +222,18 @@ mls_status prep_points(mls_handle *h, const double *xy, const double *F, cudaStr
   mls_status ms;
   if ((ms = dev_alloc(h, (void **)&keys, sizeof(unsigned long long) * 2 * (D + 2), st)) != MLS_OK) return ms;
   k_fill_u64<<<(D + 2 + 255) / 256, 256, 0, st>>>(keys, D + 2, ~0ull);
+  ++h->launches;
   k_fill_u64<<<(D + 2 + 255) / 256, 256, 0, st>>>(keys + D + 2, D + 2, 0ull);
+  ++h->launches;
   {
     const int64_t tot = n * 2;
     const int grid = (int)std::min<int64_t>((tot + 255) / 256, 1216);
     k_colminmax<<<grid, 256, 2 * 2 * sizeof(unsigned long long), st>>>(xy, n, 2, keys, keys + D + 2);
+    ++h->launches;
     const int64_t totF = n * D;
     const int gridF = (int)std::min<int64_t>((totF + 255) / 256, 1216);
     k_colminmax<<<gridF, 256, 2 * D * sizeof(unsigned long long), st>>>(F, n, D, keys + 2, keys + D + 4);
+    ++h->launches;
   }
   MLS_CUDA_TRY(cudaGetLastError());
   std::vector<unsigned long long> hk(2 * (D + 2));
@@ -287,11 +311,17 @@ mls_status prep_points(mls_handle *h, const double *xy, const double *F, cudaStr
     MLS_CUDA_TRY(cudaMemsetAsync(cursor, 0, sizeof(int) * ncell, st));
     const int nbk = (int)((n + 255) / 256);
     k_bin_count<<<nbk, 256, 0, st>>>(xy, n, P.gx0, P.gy0, 1.0 / P.cell, P.gx, P.gy, key, counts);
+    ++h->launches;
     k_scan_blocks<<<nb, 512, 0, st>>>(counts, ncell + 1, P.cell_start, totals);
+    ++h->launches;
     k_scan_totals<<<1, 32, 0, st>>>(totals, nb, grand);
+    ++h->launches;
     k_scan_add<<<(ncell + 1 + 255) / 256, 256, 0, st>>>(P.cell_start, ncell + 1, totals);
+    ++h->launches;
     k_bin_scatter<<<nbk, 256, 0, st>>>(key, n, P.cell_start, cursor, perm_tmp);
+    ++h->launches;
     k_bin_rank<<<ncell, 128, 0, st>>>(P.cell_start, ncell, perm_tmp, perm);
+    ++h->launches;
     MLS_CUDA_TRY(cudaGetLastError());
   }
 
@@ -299,9 +329,22 @@ mls_status prep_points(mls_handle *h, const double *xy, const double *F, cudaStr
   {
     dim3 g((unsigned)((n + 31) / 32), (unsigned)((D + 31) / 32));
     k_gather_transpose<<<g, dim3(32, 8), 0, st>>>(xy, F, n, D, perm, P.x64, P.y64, P.FT64);
+    ++h->launches;
     dim3 g2((unsigned)((P.n_pad + 255) / 256), (unsigned)P.D_pad);
     k_finish<<<g2, 256, 0, st>>>(P.x64, P.y64, P.FT64, n, P.n_pad, D, P.D_pad, P.ctr_x, P.ctr_y, 1.0 / P.s,
                                  P.fcen, P.fscl, P.xs, P.ys, P.FT32);
+    ++h->launches;
+    MLS_CUDA_TRY(cudaGetLastError());
+  }
+  if (d.precision == MLS_P_FP16 || d.precision == MLS_P_BF16) {
+    const int dc = tc_dims_per_pass(D, d.degree);
+    const int passes = (D + dc - 1) / dc;
+    P.fb_dc = dc;
+    ALLOC(P.xyb, sizeof(float) * P.n_pad * 2);
+    ALLOC(P.fb, sizeof(float) * P.n_pad * (size_t)dc * passes);
+    dim3 g3((unsigned)((P.n_pad + 255) / 256), (unsigned)(passes < 8 ? passes : 8));
+    k_block<<<g3, 256, 0, st>>>(P.xs, P.ys, P.FT32, P.n_pad, D, dc, passes, P.xyb, P.fb);
+    ++h->launches;
     MLS_CUDA_TRY(cudaGetLastError());
   }
 #undef ALLOC

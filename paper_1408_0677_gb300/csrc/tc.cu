@@ -40,7 +40,8 @@ constexpr int kM = 128;           // pixels per accumulator (TMEM lanes)
 constexpr int kKT = 64;           // points per stage = one 128-byte row of 16-bit values
 constexpr int kStages = 2;
 constexpr int kNMax = 256;        // operand columns per accumulator (TMEM budget 2 x 256)
-constexpr int kThreads = 288;     // 9 warps
+constexpr int kThreads = 320;     // 10 warps: 4 weights, 4 operand, 1 MMA, 1 loader
+constexpr int kDcMax = 40;        // value dimensions per pass (bounds the staged point tile)
 constexpr float kRMax = 15.f;     // |x~|_inf clip of the operand (FP16 range of x~^4)
 constexpr float kLog2e = 1.4426950408889634f;
 
@@ -51,9 +52,34 @@ constexpr int kBBytes = kNMax * 128;               // 32 KB per B tile
 // a stage holds two A tiles.
 constexpr int kOffA = 0;                           // A[stage][acc or part]
 constexpr int kOffB = kOffA + kStages * 2 * kABytes;      // 64 KB: B[stage][part]
-constexpr int kOffPrm = kOffB + kStages * 2 * kBBytes;    // 192 KB: per-warp point params
-constexpr int kOffBar = kOffPrm + 4 * kKT * 16;           // 196 KB
-constexpr int kSmemBytes = kOffBar + 128 + 1024;          // + alignment slack
+constexpr int kSmemLimit = 232448;                        // 227 KB per CTA
+
+// Shared-memory layout, sized for the operand width N and the dimensions per
+// pass Dc: A tiles, B tiles (2 x N rows of 128 B per stage), per-warp point
+// parameters, a ring of staged point tiles (x, y and Dc value rows of 64
+// floats each, filled by TMA bulk copies), barriers.
+struct TcLayout {
+  int offB, bpart;          // B tiles: offset, bytes per tile
+  int offPrm;
+  int offData, dstage, dstages;
+  int offBar;
+  int total;
+};
+
+TcLayout make_layout(int N, int Dc) {
+  TcLayout L;
+  L.offB = kOffB;
+  L.bpart = N * 128;
+  L.offPrm = L.offB + kStages * 2 * L.bpart;
+  L.offData = L.offPrm + 4 * kKT * 16;
+  L.dstage = (2 + Dc) * kKT * 4;
+  const int fixed = L.offData + 256 + 1024;
+  int ds = (kSmemLimit - fixed) / L.dstage;
+  L.dstages = ds > 4 ? 4 : ds;
+  L.offBar = L.offData + L.dstages * L.dstage;
+  L.total = L.offBar + 256 + 1024;
+  return L;
+}
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -63,26 +89,42 @@ __device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
 __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
   asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(bar) : "memory");
 }
-__device__ __forceinline__ bool mbar_test(uint32_t bar, uint32_t parity) {
+// Test the phase; while it is incomplete the thread is suspended in hardware
+// for up to `hint_ns` (it wakes as soon as the phase completes), so waiting
+// warps do not take issue slots from the producers on the same scheduler.
+__device__ __forceinline__ bool mbar_test(uint32_t bar, uint32_t parity, uint32_t hint_ns) {
   uint32_t done;
   asm volatile(
-      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.b32 %0, 1, 0, p;\n\t}"
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+      "selp.b32 %0, 1, 0, p;\n\t}"
       : "=r"(done)
-      : "r"(bar), "r"(parity)
+      : "r"(bar), "r"(parity), "r"(hint_ns)
       : "memory");
   return done != 0;
 }
-// Wait for the phase of the given parity to complete, at most kWaitLimitNs.
+// Wait for the phase of the given parity to complete, at most `limit` ns.
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int *err, int code, uint64_t limit) {
-  if (mbar_test(bar, parity)) return true;
+  if (mbar_test(bar, parity, 20000u)) return true;
   const uint64_t t0 = globaltimer_ns();
-  while (!mbar_test(bar, parity)) {
+  while (!mbar_test(bar, parity, 100000u)) {
     if (globaltimer_ns() - t0 > limit) {
       set_error(err, code);
       return false;
     }
   }
   return true;
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(bar),
+               "r"(bytes)
+               : "memory");
+}
+// One TMA bulk copy global -> shared, completing transaction bytes on bar.
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+               "l"(src), "r"(bytes), "r"(bar)
+               : "memory");
 }
 
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
@@ -138,25 +180,29 @@ __device__ __forceinline__ uint32_t sw128_off(int m, int c) {
   return (uint32_t)((m >> 3) * 1024 + (m & 7) * 128 + ((c ^ (m & 7)) << 4));
 }
 
+// Register-only conversions: two floats -> packed 16-bit pair (lo in the low
+// half) and back.
 template <bool FP16>
 __device__ __forceinline__ uint32_t pack2(float lo, float hi) {
-  if (FP16) {
-    __half2 h = __floats2half2_rn(lo, hi);
-    return *reinterpret_cast<uint32_t *>(&h);
-  } else {
-    __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
-    return *reinterpret_cast<uint32_t *>(&h);
-  }
+  uint32_t r;
+  if (FP16)
+    asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
+  else
+    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
+  return r;
 }
 template <bool FP16>
 __device__ __forceinline__ float2 unpack2(uint32_t u) {
+  float2 f;
   if (FP16) {
-    __half2 h = *reinterpret_cast<__half2 *>(&u);
-    return __half22float2(h);
+    asm("{\n\t.reg .f16 a, b;\n\tmov.b32 {a, b}, %2;\n\tcvt.f32.f16 %0, a;\n\tcvt.f32.f16 %1, b;\n\t}"
+        : "=f"(f.x), "=f"(f.y)
+        : "r"(u));
   } else {
-    __nv_bfloat162 h = *reinterpret_cast<__nv_bfloat162 *>(&u);
-    return __bfloat1622float2(h);
+    f.x = __uint_as_float(u << 16);
+    f.y = __uint_as_float(u & 0xffff0000u);
   }
+  return f;
 }
 
 // Eight operand values -> hi and lo 16-byte chunks (G = hi + lo).
@@ -254,18 +300,24 @@ __device__ __forceinline__ void ranges_next(const KParams &p, RangeIter &it) {
 }
 
 template <int DEG, int WK, bool FP16, int NACC, bool WSPLIT>
-__global__ void __launch_bounds__(kThreads, 1) k_mls_tc(KParams p, int d0, int Dc, int N, uint32_t idesc) {
+__global__ void __launch_bounds__(kThreads, 1) k_mls_tc(KParams p, int d0, int Dc, int N, uint32_t idesc,
+                                                         TcLayout lay, int pass) {
   static_assert(NACC * (WSPLIT ? 2 : 1) == 2, "a stage holds two A tiles");
   constexpr int K = n_terms(DEG), NM = n_moments(DEG);
   constexpr int TH = 8 * NACC;          // tile height in pixels (width 16)
   extern __shared__ __align__(1024) unsigned char smem_raw[];
-  unsigned char *smem = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  // align to 1024 B by offsetting the shared array itself (not through an
+  // integer cast), so every access below stays a shared-memory access
+  unsigned char *smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
   const uint32_t sbase = smem_u32(smem);
-  uint64_t *bars = (uint64_t *)(smem + kOffBar);
+  uint64_t *bars = (uint64_t *)(smem + lay.offBar);
   const uint32_t bar_full0 = smem_u32(&bars[0]);    // full[s] at +8 s
   const uint32_t bar_empty0 = smem_u32(&bars[2]);   // empty[s]
   const uint32_t bar_acc = smem_u32(&bars[4]);
-  uint32_t *tmem_slot = (uint32_t *)(smem + kOffBar + 64);
+  const uint32_t bar_dfull0 = smem_u32(&bars[5]);   // staged point tile ready [ds]
+  const uint32_t bar_dempty0 = smem_u32(&bars[9]);  // staged point tile consumed [ds]
+  uint32_t *tmem_slot = (uint32_t *)(smem + lay.offBar + 128);
+  const int DST = lay.dstages;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int u0 = blockIdx.x * 16, v0 = blockIdx.y * TH;
 
@@ -275,6 +327,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_mls_tc(KParams p, int d0, int D
       mbar_init(bar_empty0 + 8 * s, 1);
     }
     mbar_init(bar_acc, 1);
+    for (int ds = 0; ds < DST; ++ds) {
+      mbar_init(bar_dfull0 + 8 * ds, 1);
+      mbar_init(bar_dempty0 + 8 * ds, 8);
+    }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 8) tmem_alloc(smem_u32(tmem_slot), 512);
@@ -308,10 +364,16 @@ __global__ void __launch_bounds__(kThreads, 1) k_mls_tc(KParams p, int d0, int D
       else
         E[a] = dx[a] * dx[a] + dy[a] * dy[a];
     }
-    float4 *prm = (float4 *)(smem + kOffPrm) + warp * kKT;
+    float4 *prm = (float4 *)(smem + lay.offPrm) + warp * kKT;
     int kt = 0;
     for (; ranges_valid(it) && alive; ranges_next(p, it), ++kt) {
       const int s = kt & 1;
+      const int ds = kt % DST;
+      if (!mbar_wait(bar_dfull0 + 8 * ds, (kt / DST) & 1, p.err, ERR_WAIT_FULL, limit)) {
+        alive = false;
+        break;
+      }
+      const float *dxs = (const float *)(smem + lay.offData + ds * lay.dstage);
       __syncwarp();
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
@@ -320,8 +382,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_mls_tc(KParams p, int d0, int D
         float x = 0.f, y = 0.f;
         bool ok = (i >= it.lo) && (i < it.hi);
         if (ok) {
-          x = p.xs[i] - cxs;
-          y = p.ys[i] - cys;
+          // blocked tile: 8-point blocks of (x[8], y[8])
+          x = dxs[(j >> 3) * 16 + (j & 7)] - cxs;
+          y = dxs[(j >> 3) * 16 + 8 + (j & 7)] - cys;
           ok = fmaxf(fabsf(x), fabsf(y)) <= kRMax;
         }
         float4 v;
@@ -333,6 +396,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mls_tc(KParams p, int d0, int D
         prm[j] = v;
       }
       __syncwarp();
+      if (lane == 0) mbar_arrive(bar_dempty0 + 8 * ds);
       if (!mbar_wait(bar_empty0 + 8 * s, ((kt >> 1) & 1) ^ 1, p.err, ERR_WAIT_EMPTY, limit)) {
         alive = false;
         break;
@@ -369,14 +433,23 @@ __global__ void __launch_bounds__(kThreads, 1) k_mls_tc(KParams p, int d0, int D
     const int tt = threadIdx.x - 128;
     const int g = tt & 7;          // 8-point group of the tile
     const int rr = tt >> 3;        // row class 0..15
+    // exponents of this thread's monomial row (fixed for the whole kernel)
+    const int mex = mono_ex(rr < 15 ? rr : 0), mey = mono_ey(rr < 15 ? rr : 0);
+    const float mrow = (rr < NM) ? 1.f : 0.f;
     int kt = 0;
     for (; ranges_valid(it) && alive; ranges_next(p, it), ++kt) {
       const int s = kt & 1;
+      const int ds = kt % DST;
       const int i0 = it.base + 8 * g;
       float xv[8], yv[8], msk[8];
+      if (!mbar_wait(bar_dfull0 + 8 * ds, (kt / DST) & 1, p.err, ERR_WAIT_FULL, limit)) {
+        alive = false;
+        break;
+      }
+      const float *dsm = (const float *)(smem + lay.offData + ds * lay.dstage);
       if (i0 < p.n_pad) {
-        const float4 xa = *(const float4 *)(p.xs + i0), xb = *(const float4 *)(p.xs + i0 + 4);
-        const float4 ya = *(const float4 *)(p.ys + i0), yb = *(const float4 *)(p.ys + i0 + 4);
+        const float4 xa = *(const float4 *)(dsm + 16 * g), xb = *(const float4 *)(dsm + 16 * g + 4);
+        const float4 ya = *(const float4 *)(dsm + 16 * g + 8), yb = *(const float4 *)(dsm + 16 * g + 12);
         xv[0] = xa.x; xv[1] = xa.y; xv[2] = xa.z; xv[3] = xa.w; xv[4] = xb.x; xv[5] = xb.y; xv[6] = xb.z; xv[7] = xb.w;
         yv[0] = ya.x; yv[1] = ya.y; yv[2] = ya.z; yv[3] = ya.w; yv[4] = yb.x; yv[5] = yb.y; yv[6] = yb.z; yv[7] = yb.w;
       } else {
@@ -396,18 +469,18 @@ __global__ void __launch_bounds__(kThreads, 1) k_mls_tc(KParams p, int d0, int D
         alive = false;
         break;
       }
-      unsigned char *Bh = smem + kOffB + (s * 2 + 0) * kBBytes;
-      unsigned char *Bl = smem + kOffB + (s * 2 + 1) * kBBytes;
-      // monomial row rr of the moment part (rows 0..15; rows >= NM are zero)
+      unsigned char *Bh = smem + lay.offB + (s * 2 + 0) * lay.bpart;
+      unsigned char *Bl = smem + lay.offB + (s * 2 + 1) * lay.bpart;
+      // monomial row rr of the moment part (rows 0..15; rows >= NM are zero),
+      // branch-free: x^ex = (x or 1)(x^2 or 1)(x^4 or 1) by the bits of ex
       {
         float val[8];
-        const int ex = mono_ex(rr < 15 ? rr : 0), ey = mono_ey(rr < 15 ? rr : 0);
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
-          float m = msk[j];
-          for (int e = 0; e < ex; ++e) m *= xv[j];
-          for (int e = 0; e < ey; ++e) m *= yv[j];
-          val[j] = (rr < NM) ? m : 0.f;
+          const float x1 = xv[j], x2 = x1 * x1, y1 = yv[j], y2 = y1 * y1;
+          const float px = ((mex & 1) ? x1 : 1.f) * ((mex & 2) ? x2 : 1.f) * ((mex & 4) ? x2 * x2 : 1.f);
+          const float py = ((mey & 1) ? y1 : 1.f) * ((mey & 2) ? y2 : 1.f) * ((mey & 4) ? y2 * y2 : 1.f);
+          val[j] = mrow * msk[j] * px * py;
         }
         uint4 hi, lo;
         split8<FP16>(val, hi, lo);
@@ -429,9 +502,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_mls_tc(KParams p, int d0, int D
       for (int d = rr; d < Dc; d += 16) {
         float fv[8];
         if (i0 < p.n_pad) {
-          const float *fr = p.FT32 + (size_t)(d0 + d) * p.n_pad + i0;
+          const float *fr = dsm + 2 * kKT + (g * Dc + d) * 8;
           const float4 fa = *(const float4 *)fr, fb = *(const float4 *)(fr + 4);
           fv[0] = fa.x; fv[1] = fa.y; fv[2] = fa.z; fv[3] = fa.w; fv[4] = fb.x; fv[5] = fb.y; fv[6] = fb.z; fv[7] = fb.w;
+          // slots past the copied tile hold stale shared memory: never multiply them
+#pragma unroll
+          for (int j = 0; j < 8; ++j) fv[j] = (msk[j] != 0.f) ? fv[j] : 0.f;
         } else {
 #pragma unroll
           for (int j = 0; j < 8; ++j) fv[j] = 0.f;
@@ -458,8 +534,39 @@ __global__ void __launch_bounds__(kThreads, 1) k_mls_tc(KParams p, int d0, int D
       }
       fence_proxy_async();
       __syncwarp();
-      if (lane == 0) mbar_arrive(bar_full0 + 8 * s);
+      if (lane == 0) {
+        mbar_arrive(bar_dempty0 + 8 * ds);
+        mbar_arrive(bar_full0 + 8 * s);
+      }
     }
+  } else if (warp == 9) {
+    // ------------------------------------------------ point-tile loader (TMA bulk copies)
+    if (lane == 0) {
+      int kt = 0;
+      for (; ranges_valid(it) && alive; ranges_next(p, it), ++kt) {
+        const int ds = kt % DST;
+        if (!mbar_wait(bar_dempty0 + 8 * ds, ((kt / DST) & 1) ^ 1, p.err, ERR_WAIT_EMPTY, limit)) {
+          alive = false;
+          break;
+        }
+        const int cnt = (int)((p.n_pad - it.base) < kKT ? (p.n_pad - it.base) : kKT);  // multiple of 8
+        const uint32_t nb = (uint32_t)cnt * 4;
+        const uint32_t dst = sbase + lay.offData + ds * lay.dstage;
+        const uint32_t bar = bar_dfull0 + 8 * ds;
+        // point-blocked layouts: one copy for the positions, one for the
+        // values of this pass (blocks base/8 .. base/8 + cnt/8)
+        const int64_t blk = it.base >> 3;
+        const int64_t nblk = p.n_pad >> 3;
+        mbar_expect_tx(bar, nb * (uint32_t)(2 + Dc));
+        bulk_g2s(dst, p.xyb + blk * 16, 2 * nb, bar);
+        bulk_g2s(dst + 2 * kKT * 4, p.fb + ((size_t)pass * nblk + blk) * Dc * 8, nb * (uint32_t)Dc, bar);
+      }
+      // every issued copy has landed before the CTA may exit
+      const int first = kt > DST ? kt - DST : 0;
+      for (int k2 = first; k2 < kt; ++k2)
+        mbar_wait(bar_dfull0 + 8 * (k2 % DST), (k2 / DST) & 1, p.err, ERR_WAIT_FULL, limit);
+    }
+    __syncwarp();
   } else {
     // ------------------------------------------------ MMA issuer
     if (lane == 0) {
@@ -483,7 +590,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mls_tc(KParams p, int d0, int D
               const int ap = WSPLIT ? (term == 2 ? 1 : 0) : a;
               const int bp = (term == 1) ? 1 : 0;
               const uint32_t abase = sbase + kOffA + (s * 2 + ap) * kABytes;
-              const uint32_t bbase = sbase + kOffB + (s * 2 + bp) * kBBytes;
+              const uint32_t bbase = sbase + lay.offB + (s * 2 + bp) * lay.bpart;
               mma_f16(tmem + a * 256, desc_sw128(abase + 32 * k), desc_sw128(bbase + 32 * k), idesc,
                       (kt | k | term) != 0 ? 1u : 0u);
             }
@@ -555,7 +662,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mls_tc(KParams p, int d0, int D
       p.relist[k] = (int)pix;
     }
     if (primary && inside && nosup) {
-      for (int d = d0; d < d0 + Dc; ++d) {
+      for (int d = d0; d < d0 + Dc && d < p.D; ++d) {
         field[(size_t)d * plane + pix] = __int_as_float(0x7fc00000);
         if (p.bands) p.bands[(size_t)d * plane + pix] = 255;
       }
@@ -578,7 +685,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mls_tc(KParams p, int d0, int D
 #pragma unroll
         for (int dd = 0; dd < GD; ++dd) {
           const int d = gbase + dd;
-          if (d < Dc) {
+          if (d < Dc && d0 + d < p.D) {
             float acc = 0.f;
 #pragma unroll
             for (int b = 0; b < K; ++b) acc = fmaf(z[b], rv[dd * K + b], acc);
@@ -619,8 +726,9 @@ template <int DEG, int WK, bool FP16, int NACC, bool WSPLIT>
 void launch_one(const KParams &p, int d0, int Dc, int N, uint32_t idesc, cudaStream_t st) {
   dim3 grid(p.tiles_x, p.tiles_y * (2 / NACC));
   auto k = k_mls_tc<DEG, WK, FP16, NACC, WSPLIT>;
-  cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
-  k<<<grid, kThreads, kSmemBytes, st>>>(p, d0, Dc, N, idesc);
+  const TcLayout lay = make_layout(N, Dc);
+  cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, lay.total);
+  k<<<grid, kThreads, lay.total, st>>>(p, d0, Dc, N, idesc, lay, d0 / Dc);
 }
 
 template <int DEG, int WK>
@@ -638,26 +746,34 @@ void launch_deg_w(const KParams &p, int fp16, int wsplit, int d0, int Dc, int N,
 }  // namespace
 
 // Dimensions per pass so that 16 + K Dc columns fit one 256-column accumulator.
-static int dims_per_pass(int degree) {
+int dims_per_pass(int degree) {
   const int K = mlsk::n_terms(degree);
   const int group = (K == 1) ? 16 : 48 / K;   // the epilogue reads whole groups
   int dc = (kNMax - 16) / K;
+  if (dc > kDcMax) dc = kDcMax;
   dc -= dc % group;
   return dc;
 }
 
-mls_status launch_tc(const KParams &p, int fp16, int wsplit, cudaStream_t st) {
+int tc_dims_per_pass(int D, int degree) {
+  const int dmax = dims_per_pass(degree);
+  const int passes = (D + dmax - 1) / dmax;
+  return (D + passes - 1) / passes;   // balanced passes
+}
+
+mls_status launch_tc(const KParams &p, int fp16, int wsplit, cudaStream_t st, int *nlaunch) {
+  *nlaunch = 0;
   const int K = mlsk::n_terms(p.degree);
-  const int dmax = dims_per_pass(p.degree);
-  const int passes = (p.D + dmax - 1) / dmax;
-  const int per = (p.D + passes - 1) / passes;   // balanced passes
+  const int per = tc_dims_per_pass(p.D, p.degree);
+  if (per != p.fb_dc) return fail(MLS_E_INVAL, "blocked value layout does not match the pass split");
   for (int d0 = 0; d0 < p.D; d0 += per) {
-    const int Dc = (p.D - d0 < per) ? p.D - d0 : per;
+    const int Dc = per;   // the last pass reads zero-padded dimensions
     const int group = (K == 1) ? 16 : 48 / K;
     const int Dg = (Dc + group - 1) / group * group;    // columns the epilogue reads
     int N = 16 + Dg * K;
     N = (N + 15) / 16 * 16;
     if (N > kNMax) return fail(MLS_E_UNSUPPORTED, "operand wider than one accumulator");
+    if (make_layout(N, Dc).dstages < 1) return fail(MLS_E_UNSUPPORTED, "point tile does not fit shared memory");
     const uint32_t fmt = fp16 ? 0u : 1u;
     const uint32_t idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(N >> 3) << 17) |
                            ((uint32_t)(kM >> 4) << 24);
@@ -674,6 +790,7 @@ mls_status launch_tc(const KParams &p, int fp16, int wsplit, cudaStream_t st) {
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "k_mls_tc launch");
+    ++*nlaunch;
   }
   return MLS_OK;
 }

@@ -147,6 +147,24 @@ def clusters_200k(seed: int = 1003, W: int = 2048, H: int = 2048) -> Workload:
     return w
 
 
+def fourier_mix(seed: int, n: int, D: int, W: int, H: int, degree: int, weight: int, h: float,
+                L: int = 16) -> Workload:
+    """Scaled-down workload with the structure of the 10k-point configuration:
+    8 Gaussian clusters (sigma U(0.02,0.06)) plus 20% uniform points, D random
+    Fourier fields with 8 modes of integer frequency up to 4."""
+    rng = np.random.default_rng(seed)
+    n_uni = n // 5
+    centres = rng.uniform(0.1, 0.9, size=(8, 2))
+    sig = rng.uniform(0.02, 0.06, size=8)
+    xy = np.concatenate([_clusters(rng, n - n_uni, centres, sig),
+                         rng.uniform(0.0, 1.0, size=(n_uni, 2))], axis=0)
+    xy = xy[rng.permutation(n)]
+    F = _fourier_fields(rng, xy, D, modes=8, max_freq=4)
+    w = Workload(f"fourier_mix_n{n}_d{D}_{W}x{H}_deg{degree}_w{weight}", xy, F, degree, weight, h, W, H)
+    w.levels = default_levels(F, L)
+    return w
+
+
 def small_random(seed: int, n: int, D: int, W: int, H: int, degree: int, weight: int,
                  h: float, L: int = 8, clustered: bool = True) -> Workload:
     """A small seeded case of the same structure, for tests."""

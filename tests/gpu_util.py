@@ -53,7 +53,7 @@ def compare(wl, res, ref, precision, pixels=None, check_bands=True, check_status
         # a different but equally valid summation order moves an FP64 result by
         # about kappa * eps (kappa = 1/rcond of the equilibrated moment matrix)
         kappa = np.where(ref.rcond > 0, 1.0 / np.maximum(ref.rcond, 1e-300), 1.0)
-        allow = np.maximum(tol, 10.0 * kappa * 2.2e-16)
+        allow = np.maximum(tol, 30.0 * kappa * 2.2e-16)
     bad = (err > allow[:, None]) & ok[:, None]
     if bad.any():
         i, d = np.argwhere(bad)[0]

@@ -48,14 +48,54 @@ SMALL = [
 
 
 @pytest.mark.parametrize("case", SMALL, ids=[f"s{c[0]}" for c in SMALL])
-@pytest.mark.parametrize("precision", ALL_PREC)
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
 def test_small_ragged_cases(case, precision):
+    """Rough fields (wavelength 3-5 h) on few points: CUDA-core paths."""
     seed, n, D, W, H, degree, weight, h = case
-    if weight == ID and precision in ("fp16", "bf16"):
-        pytest.skip("tensor-core precisions take the Gaussian and Wendland weights")
     wl = inputs.small_random(seed, n, D, W, H, degree, weight, h)
     res = gpu_render(wl, precision)
     compare(wl, res, _ref(wl), precision)
+
+
+STRUCTURED = [
+    # seed, n, D, W, H, degree, weight, h: clusters + background, Fourier fields of
+    # wavelength >= 0.177, h and point density as in the benchmark configurations
+    (31, 10000, 8, 100, 75, 2, G, 0.02),
+    (32, 10000, 5, 61, 47, 1, G, 0.02),
+    (33, 10000, 3, 48, 33, 0, G, 0.02),
+    (34, 100000, 6, 90, 70, 2, WD, 0.02),
+    (35, 100000, 48, 40, 36, 2, WD, 0.02),
+    (36, 10000, 70, 50, 20, 1, G, 0.02),
+]
+
+
+@pytest.mark.parametrize("case", STRUCTURED, ids=[f"c{c[0]}" for c in STRUCTURED])
+@pytest.mark.parametrize("precision", ALL_PREC)
+def test_structured_ragged_cases(case, precision):
+    """Scaled-down inputs with the structure of the benchmark configurations:
+    several tiles and a ragged tail, every degree, both tensor-core weights,
+    D over several accumulator passes (48, 70)."""
+    seed, n, D, W, H, degree, weight, h = case
+    wl = inputs.fourier_mix(seed, n, D, W, H, degree, weight, h)
+    res = gpu_render(wl, precision)
+    compare(wl, res, _ref(wl), precision)
+
+
+ROUGH = [
+    # fields with wavelength 4-6 h: the single 16-bit weight rounding is not enough here
+    (41, 3000, 8, 100, 75, 2, G, 0.03),
+    (42, 2000, 5, 61, 47, 1, G, 0.04),
+    (43, 20000, 6, 90, 70, 2, WD, 0.03),
+]
+
+
+@pytest.mark.parametrize("case", ROUGH, ids=[f"r{c[0]}" for c in ROUGH])
+def test_rough_fields_fp16_with_split_weights(case):
+    """FP16 with weights stored as hi + lo pairs (three products per point tile)."""
+    seed, n, D, W, H, degree, weight, h = case
+    wl = inputs.fourier_mix(seed, n, D, W, H, degree, weight, h)
+    res = gpu_render(wl, "fp16", weight_split=1)
+    compare(wl, res, _ref(wl), "fp16")
 
 
 @pytest.mark.parametrize("precision", ALL_PREC)
@@ -95,8 +135,8 @@ def test_single_point_and_tiny_grid(precision):
 
 @pytest.mark.parametrize("precision", ALL_PREC)
 def test_empty_support_is_nan_and_band_255(precision):
-    wl = inputs.small_random(22, 30, 2, 48, 48, 2, WD, 0.05)
-    wl.xy = 0.2 + 0.1 * wl.xy      # points only in a corner
+    wl = inputs.fourier_mix(22, 60000, 2, 48, 48, 2, WD, 0.02)
+    wl.xy = 0.05 + 0.45 * wl.xy    # points only in the lower-left part
     res = gpu_render(wl, precision)
     compare(wl, res, _ref(wl), precision)
     far = res["status"][-1, -1]
