@@ -208,7 +208,7 @@ def run_ours(args):
 
     def step_device():
         r = Renderer(xy_d, F_d, degree=wl.degree, weight=wl.weight, h=wl.h, precision=args.precision,
-                     stream=sptr)
+                     weight_split=args.weight_split, stream=sptr)
         r.render(W, H, levels=lev, field=field, bands=bands, status_out=status)
         return r
 
@@ -262,7 +262,7 @@ def run_ours(args):
 
     def step_host():
         r = Renderer(xy_h, F_h, degree=wl.degree, weight=wl.weight, h=wl.h, precision=args.precision,
-                     stream=sptr)
+                     weight_split=args.weight_split, stream=sptr)
         r.render_host(W, H, levels=lev, field=field_h, bands=bands_h, status_out=status_h)
         r.close()
 
@@ -318,6 +318,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="fp16", choices=["fp16", "bf16", "fp32", "fp64"])
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--weight-split", type=int, default=None, choices=[0, 1])
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

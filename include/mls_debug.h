@@ -1,0 +1,38 @@
+/* Test hooks of libmls: device self-checks that the test suite calls
+ * through the same C ABI as the renderer.  None of them is needed to
+ * render; each allocates its own device memory, runs on the current device
+ * and synchronises before it returns. */
+#ifndef MLS_DEBUG_H
+#define MLS_DEBUG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Bounded waits (the failure detection of the tensor-core kernel).  Launches
+ * one warp that waits on an mbarrier phase nothing completes; the wait gives
+ * up after limit_ns nanoseconds of the device clock, records its error code
+ * (1 = a wait for a filled operand stage gave up) and the kernel returns.
+ * *code_out receives that code (0 = no wait gave up).  Returns MLS_OK when
+ * the kernel ran and the context is still usable, MLS_E_CUDA otherwise. */
+int mls_debug_wait_selftest(int64_t limit_ns, int *code_out);
+
+/* The double-float weight functions of the hand-over path, evaluated on n
+ * arguments a = arg_hi[i] + arg_lo[i] (host arrays of float; out a host
+ * array of n doubles receiving hi + lo of the result):
+ *   kind 0: exp(a), for -70 <= a <= 1 (the Gaussian weight of Section 3.3,
+ *           Eq. eq-weights, relative to the stabiliser: exp(-(r^2 - m)/h^2));
+ *   kind 1: the Wendland C2 weight (1 - q)^4 (4 q + 1), q = sqrt(a), 0 <= a < 1
+ *           (the compactly supported weight of the Section 3.3 weight family);
+ *   kind 2: sqrt(a), a >= 0.
+ * Returns MLS_E_INVAL for a bad kind, n < 0 or a null array with n > 0,
+ * MLS_E_NOMEM / MLS_E_CUDA on device failures, MLS_OK otherwise. */
+int mls_debug_df_weight(int kind, const float *arg_hi, const float *arg_lo, int64_t n, double *out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MLS_DEBUG_H */

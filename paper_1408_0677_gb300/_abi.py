@@ -84,6 +84,11 @@ def load(path: str | None = None):
     lib.mls_sync.argtypes = [P, ctypes.c_double, ctypes.POINTER(MlsStats)]
     lib.mls_destroy.restype = ctypes.c_int
     lib.mls_destroy.argtypes = [P]
+    # test hooks (include/mls_debug.h)
+    lib.mls_debug_wait_selftest.restype = ctypes.c_int
+    lib.mls_debug_wait_selftest.argtypes = [ctypes.c_int64, ctypes.POINTER(ctypes.c_int)]
+    lib.mls_debug_df_weight.restype = ctypes.c_int
+    lib.mls_debug_df_weight.argtypes = [ctypes.c_int, P, P, ctypes.c_int64, P]
     if path == _build.LIB:
         _lib = lib
     return lib

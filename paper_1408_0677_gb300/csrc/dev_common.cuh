@@ -65,7 +65,9 @@ struct KParams {
   int64_t n, n_pad;
   int D, D_pad;
   const float *xs, *ys;        // (x - ctr) / s, FP32, [n_pad]
+  const float *xs_lo, *ys_lo;  // low parts: xs + xs_lo = (x - ctr) / s to ~48 bits
   const float *FT32;           // normalised values (f - cen) / scl, [D_pad][n_pad]
+  const float *FR32;           // the same values point-major, [n_pad][D] (hand-over path)
   const float *fcen32, *fscl32;
   const double *x64, *y64;     // raw positions [n]
   const double *FT64;          // raw values [D][n]
@@ -79,6 +81,7 @@ struct KParams {
   int degree, weight;
   double h, alpha;
   double cond_fp64, rcond_min, cond_recompute;
+  float lambda_max;            // bound on sum_a |z_a| sqrt(M_00 M_aa) kept on the fast path
   // view
   int W, H;
   double x0, y0, sx, sy;       // pixel (u,v) centre = (x0 + (u+.5) sx, y0 + (v+.5) sy)
@@ -96,6 +99,7 @@ struct KParams {
   // scratch
   const float *mstab;          // [tiles_y*16][tiles_x*16] stabiliser min r^2 / s^2
   const int *cnt;              // same shape, Wendland in-support counts
+  const float *tcen;           // [tiles_y][tiles_x][2] moment frame centre of each tile (scaled)
   int *relist;                 // pixels handed to the FP64 path
   unsigned int *relist_count;
   int *err;
@@ -130,6 +134,103 @@ __device__ __forceinline__ uint8_t band_of(double f, const double *lev, int L) {
   int c = 0;
   for (int j = 0; j < L; ++j) c += (lev[j] <= f) ? 1 : 0;
   return (uint8_t)c;
+}
+
+// ---------------------------------------------------------------------------
+// Double-float arithmetic: a value held as an unevaluated sum hi + lo of two
+// FP32 numbers (about 48 significant bits).  Error-free transformations
+// (Knuth's two-sum; the FMA two-product), so no step relies on FP64 units.
+struct df32 {
+  float hi, lo;
+};
+__device__ __forceinline__ df32 df_two_sum(float a, float b) {
+  const float s = a + b;
+  const float bb = s - a;
+  return {s, (a - (s - bb)) + (b - bb)};
+}
+__device__ __forceinline__ df32 df_quick(float a, float b) {   // |a| >= |b|
+  const float s = a + b;
+  return {s, b - (s - a)};
+}
+__device__ __forceinline__ df32 df_add(df32 a, df32 b) {
+  df32 s = df_two_sum(a.hi, b.hi);
+  s.lo += a.lo + b.lo;
+  return df_quick(s.hi, s.lo);
+}
+__device__ __forceinline__ df32 df_mul(df32 a, df32 b) {
+  const float p = a.hi * b.hi;
+  const float e = fmaf(a.hi, b.hi, -p);
+  return df_quick(p, fmaf(a.hi, b.lo, fmaf(a.lo, b.hi, e)));
+}
+__device__ __forceinline__ df32 df_mul_f(df32 a, float b) {
+  const float p = a.hi * b;
+  const float e = fmaf(a.hi, b, -p);
+  return df_quick(p, fmaf(a.lo, b, e));
+}
+// (ahi + alo) - (bhi + blo)
+__device__ __forceinline__ df32 df_diff(float ahi, float alo, float bhi, float blo) {
+  df32 s = df_two_sum(ahi, -bhi);
+  s.lo += alo - blo;
+  return df_quick(s.hi, s.lo);
+}
+
+// Table of 2^(j/64), j = 0..63, as double-float pairs, for df_exp.  Filled
+// once per block (FP64 exp2 of 64 arguments) by df_exp_table_init.
+__device__ __forceinline__ void df_exp_table_init(float2 *tab) {
+  for (int j = threadIdx.x; j < 64; j += blockDim.x) {
+    const double v = exp2((double)j / 64.0);
+    tab[j] = make_float2((float)v, (float)(v - (double)(float)v));
+  }
+}
+
+// exp(a) of a double-float argument, -70 <= a <= 1, in FP32 arithmetic, to
+// about 1e-14 relative (below -70 the low part of the result is subnormal).  Table-driven method of P. T. P. Tang (ACM TOMS
+// 15(2), 1989): a = (64 k + j) ln2/64 + r with |r| <= ln2/128, so that
+// exp(a) = 2^k 2^(j/64) exp(r); exp(r) - 1 from its Taylor series, the
+// first two terms in double-float and the rest (below 3e-8) in FP32.
+// ln2/64 = C1 + C2 + C3 with C1 of 10 significant bits, so that N C1 is
+// exact for |N| < 2^14 and a - N C1 is exact.
+__device__ __forceinline__ df32 df_exp(df32 a, const float2 *tab) {
+  constexpr float kInvC = 92.332481384277344f;        // 64 / ln 2 (rounded)
+  constexpr float C1 = 0.010833740234375f;           // 710 / 2^16
+  constexpr float C2 = -3.3155381515825866e-06f;
+  constexpr float C3 = 2.5727683872212026e-14f;
+  const float N = rintf(a.hi * kInvC);
+  const float t = fmaf(-N, C1, a.hi);                // exact
+  df32 r = df_two_sum(t, a.lo);
+  const float p2 = N * C2, e2 = fmaf(N, C2, -p2);    // N C2 exactly
+  r = df_add(r, {-p2, -e2});
+  r = df_add(r, {-N * C3, 0.f});
+  const df32 r2 = df_mul(r, r);
+  const float q = r.hi;
+  const float tail = q * q * q * fmaf(q, fmaf(q, 1.f / 120.f, 1.f / 24.f), 1.f / 6.f);
+  df32 e = df_add(r, {0.5f * r2.hi, 0.5f * r2.lo});
+  e = df_add(e, {tail, 0.f});
+  const df32 one_e = df_add({1.f, 0.f}, e);
+  const int Ni = (int)N;
+  const int j = Ni & 63, k = Ni >> 6;                // N = 64 k + j, 0 <= j < 64
+  const float2 T = tab[j];
+  const df32 w = df_mul({T.x, T.y}, one_e);
+  const float scale = __int_as_float((k + 127) << 23);   // 2^k, normal for k >= -126
+  return {w.hi * scale, w.lo * scale};
+}
+
+// sqrt of a double-float r >= 0: the FP32 root corrected by one Newton step
+// on the residual (Karp and Markstein, ACM TOMS 23(4), 1997).
+__device__ __forceinline__ df32 df_sqrt(df32 r) {
+  if (!(r.hi > 0.f)) return {0.f, 0.f};
+  const float s = sqrtf(r.hi);
+  const float res = fmaf(-s, s, r.hi) + r.lo;        // r - s^2
+  return df_quick(s, res / (2.f * s));
+}
+
+// Wendland C2 weight (1 - q)^4 (4 q + 1) at q = sqrt(r2) < 1, double-float.
+__device__ __forceinline__ df32 df_wendland(df32 r2) {
+  const df32 q = df_sqrt(r2);
+  const df32 o = df_add({1.f, 0.f}, {-q.hi, -q.lo});
+  const df32 o2 = df_mul(o, o);
+  const df32 q4 = df_add({1.f, 0.f}, {4.f * q.hi, 4.f * q.lo});
+  return df_mul(df_mul(o2, o2), q4);
 }
 
 // ---------------------------------------------------------------------------
@@ -202,20 +303,25 @@ __device__ __forceinline__ T cond1(const T (&A)[K][K], const T (&L)[K][K]) {
 // Outcome of the reduced-precision per-pixel solve.
 enum SolveOutcome : int { SOLVE_OK = 0, SOLVE_FP64 = 1, SOLVE_RECOMPUTE = 2 };
 
-// Solve M z = e0 for the pixel-centred moment matrix given by its 15 (or
-// fewer) distinct moments S (FP32).  z = M^{-1} e0 so that the fit's value is
-// z . R for any right-hand side R.  FP32 equilibrated Cholesky, a 1-norm
-// condition estimate, one step of iterative refinement; FP64 factorisation
-// when the estimate exceeds cond_fp64; SOLVE_RECOMPUTE when it exceeds
-// cond_recompute or the factorisation fails (the pixel then goes to the FP64
-// path, which applies the full degenerate-pixel policy).
+// Solve M z = b for the moment matrix given by its distinct moments S in a
+// frame whose origin is offset from the pixel by -delta, with b = b(delta) the
+// basis at the pixel: the fit's value is then z . R for the right-hand sides
+// R taken in the same frame.  FP32 equilibrated Cholesky, a 1-norm condition
+// estimate, one step of iterative refinement; FP64 factorisation when the
+// estimate exceeds cond_fp64; SOLVE_RECOMPUTE when it exceeds cond_recompute,
+// when the factorisation fails, or when the pixel-frame condition (bounded by
+// the frame condition times the growth of the basis under the shift) could
+// come near the degeneracy threshold.  Recomputed pixels go to the hand-over
+// path, which applies the full degree policy.
 template <int K>
-__device__ __forceinline__ int solve_pixel_fp32(const float *S, float (&z)[K], const KParams &p) {
+__device__ __forceinline__ int solve_pixel_fp32(const float *S, float dx, float dy, float (&z)[K],
+                                                const KParams &p) {
   float M[K][K];
 #pragma unroll
   for (int a = 0; a < K; ++a)
 #pragma unroll
     for (int b = 0; b < K; ++b) M[a][b] = S[kMIdx[a][b]];
+  float bv[6] = {1.f, dx, dy, dx * dx, dx * dy, dy * dy};
   float sd[K];
 #pragma unroll
   for (int a = 0; a < K; ++a) {
@@ -228,8 +334,18 @@ __device__ __forceinline__ int solve_pixel_fp32(const float *S, float (&z)[K], c
 #pragma unroll
     for (int b = 0; b < K; ++b) Me[a][b] = M[a][b] * sd[a] * sd[b];
   if (!cholesky<K, float>(Me, Lf)) return SOLVE_RECOMPUTE;
+  // a pivot this small means a condition beyond what FP32 can estimate
+#pragma unroll
+  for (int a = 0; a < K; ++a)
+    if (!(Lf[a][a] * Lf[a][a] > 1e-6f)) return SOLVE_RECOMPUTE;
   const float cnd = (K == 1) ? 1.f : cond1<K, float>(Me, Lf);
   if (!(cnd <= (float)p.cond_recompute)) return SOLVE_RECOMPUTE;
+  if (K > 1) {
+    const float gr = 1.f + fmaxf(fabsf(dx), fabsf(dy));
+    const float g2 = gr * gr;
+    const float growth = (K == 3) ? g2 : g2 * g2;
+    if (!(cnd * growth * 100.f < (float)(1.0 / p.rcond_min))) return SOLVE_RECOMPUTE;
+  }
   if (cnd > (float)p.cond_fp64) {
     // FP64 factorisation of the same moments
     double Md[K][K], sdd[K], Med[K][K], Ld[K][K];
@@ -244,27 +360,26 @@ __device__ __forceinline__ int solve_pixel_fp32(const float *S, float (&z)[K], c
 #pragma unroll
       for (int b = 0; b < K; ++b) Med[a][b] = Md[a][b] * sdd[a] * sdd[b];
     if (!cholesky<K, double>(Med, Ld)) return SOLVE_RECOMPUTE;
-    if (!(1.0 / cond1<K, double>(Med, Ld) >= p.rcond_min)) return SOLVE_RECOMPUTE;
     double y[K];
 #pragma unroll
-    for (int a = 0; a < K; ++a) y[a] = (a == 0) ? sdd[0] : 0.0;
+    for (int a = 0; a < K; ++a) y[a] = (double)bv[a] * sdd[a];
     chol_solve<K, double>(Ld, y);
 #pragma unroll
     for (int a = 0; a < K; ++a) z[a] = (float)(y[a] * sdd[a]);
     return SOLVE_FP64;
   }
-  // z = S Me^{-1} S e0
+  // z = S Me^{-1} S b
   float y[K];
 #pragma unroll
-  for (int a = 0; a < K; ++a) y[a] = (a == 0) ? sd[0] : 0.f;
+  for (int a = 0; a < K; ++a) y[a] = bv[a] * sd[a];
   chol_solve<K, float>(Lf, y);
 #pragma unroll
   for (int a = 0; a < K; ++a) z[a] = y[a] * sd[a];
-  // one refinement step: r = e0 - M z, z += M^{-1} r
+  // one refinement step: r = b - M z, z += M^{-1} r
   float r[K];
 #pragma unroll
   for (int a = 0; a < K; ++a) {
-    float acc = (a == 0) ? 1.f : 0.f;
+    float acc = bv[a];
 #pragma unroll
     for (int b = 0; b < K; ++b) acc = fmaf(-M[a][b], z[b], acc);
     r[a] = acc * sd[a];
@@ -272,49 +387,14 @@ __device__ __forceinline__ int solve_pixel_fp32(const float *S, float (&z)[K], c
   chol_solve<K, float>(Lf, r);
 #pragma unroll
   for (int a = 0; a < K; ++a) z[a] = fmaf(r[a], sd[a], z[a]);
+  // rounding of each right-hand side R_a moves the value by at most about
+  // eps * sqrt(M_00 M_aa) |z_a| (Cauchy-Schwarz): keep the pixel only when
+  // that amplification is small
+  float lambda = 0.f;
+#pragma unroll
+  for (int a = 0; a < K; ++a) lambda = fmaf(fabsf(z[a]), sqrtf(M[0][0] * M[a][a]), lambda);
+  if (!(lambda <= p.lambda_max)) return SOLVE_RECOMPUTE;
   return SOLVE_OK;
-}
-
-// Move the pixel-centred solution z to coefficients of tile-centred moments:
-// b(x - delta) = T(delta) b(x), so z . (T R~) = (T^T z) . R~.
-template <int K>
-__device__ __forceinline__ void to_tile_frame(float (&z)[K], float dx, float dy) {
-  if (K == 3) {
-    z[0] = z[0] - dx * z[1] - dy * z[2];
-  } else if (K == 6) {
-    const float z0 = z[0] - dx * z[1] - dy * z[2] + dx * dx * z[3] + dx * dy * z[4] + dy * dy * z[5];
-    const float z1 = z[1] - 2.f * dx * z[3] - dy * z[4];
-    const float z2 = z[2] - dx * z[4] - 2.f * dy * z[5];
-    z[0] = z0;
-    z[1] = z1;
-    z[2] = z2;
-  }
-}
-
-// Shift tile-centred moments S~ (monomials of x~) to pixel-centred moments of
-// x~ - delta (binomial expansion), NM = number of moments (1, 6, 15).
-template <int NM>
-__device__ __forceinline__ void shift_moments(const float *St, float *Sp, float dx, float dy) {
-  float px[5], py[5];
-  px[0] = 1.f; py[0] = 1.f;
-#pragma unroll
-  for (int e = 1; e < 5; ++e) { px[e] = px[e - 1] * (-dx); py[e] = py[e - 1] * (-dy); }
-#pragma unroll
-  for (int j = 0; j < NM; ++j) {
-    const int bx = mono_ex(j), by = mono_ey(j);
-    float acc = 0.f;
-#pragma unroll
-    for (int jx = 0; jx <= 4; ++jx) {
-      if (jx > bx) break;
-#pragma unroll
-      for (int jy = 0; jy <= 4; ++jy) {
-        if (jy > by) break;
-        const float c = (float)(binom(bx, jx) * binom(by, jy));
-        acc = fmaf(c * px[bx - jx] * py[by - jy], St[mono_index(jx, jy)], acc);
-      }
-    }
-    Sp[j] = acc;
-  }
 }
 
 }  // namespace mlsk

@@ -1,22 +1,30 @@
 // Hand-over path of the reduced-precision renders: pixels whose moment
-// matrix is ill conditioned in the pixel frame (one warp per pixel).
+// matrix is ill conditioned in the frame the fast kernels use (one warp per
+// pixel).
 //
-// The value of the weighted least-squares fit does not depend on the frame
-// of the polynomial basis, but the rounding error of moments accumulated in
-// FP32 / tensor-core arithmetic grows with the condition number of the frame
-// they are accumulated in.  For a pixel whose weighted points lie to one
-// side (the usual cause), the pixel frame is badly conditioned while a frame
-// centred on the weighted centroid of the points and scaled by their spread
-// is not.  So, per listed pixel:
-//   pass 1 (FP64): the distinct moments of the pixel-centred, h-scaled basis
-//          and the support count -- the degree policy is decided on these
-//          exactly as the FP64 definition does (equilibrated Cholesky,
-//          rcond_1 threshold, support count);
-//   solve  (FP64): the moments are moved to the centroid frame, where the
-//          normal matrix is factorised and z = M_c^{-1} b(p) is formed;
-//   pass 2 (FP32): the right-hand sides R_c = sum w b_c(x) f are accumulated
-//          in the centroid frame, lane-parallel with a tree reduction, and
-//          the value is z . R_c.
+// The value of the weighted least-squares fit (Section 3.3) does not depend
+// on the frame of the polynomial basis, but the rounding error of moments
+// accumulated in FP32 / tensor-core arithmetic grows with the condition
+// number of the frame they are accumulated in.  For a pixel whose weighted
+// points lie to one side (the usual cause), the pixel frame is badly
+// conditioned while a frame centred on the weighted centroid of the points
+// and scaled by their spread is not.  So, per listed pixel:
+//   pass 1 (double-float, ~48 bits, on the FP32 units): the distinct moments
+//          of the pixel-centred, h-scaled basis and the support count; the
+//          degree policy is decided on these as the FP64 definition does
+//          (equilibrated factorisation, rcond_1 threshold, support count);
+//   solve  (FP64, the warp's lanes sharing the work): the moments are moved
+//          to the centroid frame, where the normal matrix is factorised and
+//          z = M_c^{-1} b_c(p) is formed;
+//   pass 2 (double-float): the value is sum_i phi_i f_i with the MLS shape
+//          functions phi_i = w_i z . b_c(x_i) -- equal to z . R_c -- so each
+//          (point, dimension) pair costs one multiply-add; the lanes hold one
+//          dimension each and read the values point-major.
+// Both passes walk the candidate points 32 at a time, compact the near ones
+// (Gaussian weight above e^-40 of the largest, inside the Wendland support)
+// into a per-warp ring in shared memory, and process them in dense batches of
+// 32 so that no lane idles on a far point.  Weights are double-float too
+// (exp and sqrt in FP32 arithmetic: FP64 throughput is low on this part).
 // Pixels still ill conditioned in the centroid frame, and inverse-distance
 // pixels whose centre lies on a data point, go on to the pure FP64 kernel.
 #include <float.h>
@@ -28,103 +36,351 @@ namespace {
 
 using namespace mlsk;
 
-constexpr int kDC = 16;                 // value dimensions per pass 2 sweep
-constexpr double kCut = 60.0;           // Gaussian pairs with (r^2 - m)/h^2 above: weight < e^-60
-constexpr double kKappaCentroid = 3e3;  // above: the pixel goes to the FP64 kernel
-// FP32 rounding of the right-hand sides moves the value by at most about
-// eps32 * lambda * (summation growth) of the normalised data range, with
-// lambda = sum_a |z_a| sqrt(M_00 M_aa) (Cauchy-Schwarz on each R_a); above
-// this bound the pixel goes to the FP64 kernel.
-constexpr double kLambdaMax = 2e3;
-constexpr double kLog2e = 1.4426950408889634;
+constexpr int kWarps = 8;               // warps per block, one pixel each
+constexpr int kRing = 64;               // ring of compacted near points per warp
+constexpr int kDL = 2;                  // value dimensions per lane per sweep
+constexpr float kCut = 40.f;            // Gaussian pairs with (r^2 - m)/h^2 above: weight < e^-40
+// centroid-frame condition above which the pixel goes to the FP64 kernel
+// (moments and right-hand sides are double-float accurate, ~1e-14)
+constexpr double kKappaCentroid = 1e8;
 
-template <typename T>
-__device__ __forceinline__ T wsum(T v) {
+// moment index of the product of basis terms a and b
+__host__ __device__ constexpr int midx(int a, int b) {
+  return mono_index(mono_ex(a) + mono_ex(b), mono_ey(a) + mono_ey(b));
+}
+
+// ---------------------------------------------------------------------------
+// Double-float helpers without renormalisation, for long accumulations.
+
+// a * b as an unevaluated pair (p, e)
+__device__ __forceinline__ df32 df_prod(df32 a, df32 b) {
+  const float p = a.hi * b.hi;
+  float e = fmaf(a.hi, b.hi, -p);
+  e = fmaf(a.hi, b.lo, e);
+  e = fmaf(a.lo, b.hi, e);
+  return {p, e};
+}
+__device__ __forceinline__ df32 df_prod_f(df32 a, float b) {
+  const float p = a.hi * b;
+  const float e = fmaf(a.lo, b, fmaf(a.hi, b, -p));
+  return {p, e};
+}
+// s += x (two-sum on the high parts, low parts summed)
+__device__ __forceinline__ void df_acc(df32 &s, df32 x) {
+  const float t = s.hi + x.hi;
+  const float bb = t - s.hi;
+  const float err = (s.hi - (t - bb)) + (x.hi - bb);
+  s.lo += err + x.lo;
+  s.hi = t;
+}
+// normalised warp-wide sum
+__device__ __forceinline__ df32 df_warp_sum(df32 v) {
+  v = df_two_sum(v.hi, v.lo);
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  for (int o = 16; o > 0; o >>= 1) {
+    const df32 t = {__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o)};
+    v = df_add(v, t);
+  }
   return v;
 }
 
-// Equilibrated Cholesky of the k x k matrix from distinct moments (runtime k);
-// returns rcond_1 (0 on failure).  Lm receives the factor of the equilibrated
-// matrix, sd the equilibration.
-__device__ double factor_moments(const double *S, int k, double (&Lm)[6][6], double (&sd)[6]) {
-  double Me[6][6];
-  for (int a = 0; a < k; ++a) {
-    const double d = S[kMIdx[a][a]];
-    if (!(d > 0.0)) return 0.0;
-    sd[a] = 1.0 / sqrt(d);
+// ---------------------------------------------------------------------------
+// Near points and their weights.
+
+// Whether a point enters the sums: Gaussian weight above e^-kCut of the
+// largest, inside the Wendland support (double-float distance), any point
+// but a coincident one for inverse distance.
+template <int WK>
+__device__ __forceinline__ bool near_test(df32 ex, df32 ey, float mhat) {
+  if (WK == MLS_W_GAUSS) return fmaf(ex.hi, ex.hi, ey.hi * ey.hi) - mhat <= kCut;
+  if (WK == MLS_W_WENDLAND) {
+    const df32 r2d = df_add(df_mul(ex, ex), df_mul(ey, ey));
+    return (r2d.hi < 1.f) || (r2d.hi == 1.f && r2d.lo < 0.f);
   }
-  for (int a = 0; a < k; ++a)
-    for (int b = 0; b < k; ++b) Me[a][b] = S[kMIdx[a][b]] * sd[a] * sd[b];
-  for (int j = 0; j < k; ++j) {
-    double s = Me[j][j];
-    for (int t = 0; t < j; ++t) s -= Lm[j][t] * Lm[j][t];
-    if (!(s > 0.0)) return 0.0;
-    const double ljj = sqrt(s);
-    Lm[j][j] = ljj;
-    for (int i = j + 1; i < k; ++i) {
+  return !(ex.hi == 0.f && ex.lo == 0.f && ey.hi == 0.f && ey.lo == 0.f);
+}
+
+// Weight of one pair, double-float, from the double-float offset (units of
+// h): Gaussian relative to the stabiliser (exp(m - r^2)), Wendland in units
+// of the radius, inverse distance (m / r^2)^alpha (FP64 pow).
+template <int WK>
+__device__ __forceinline__ df32 pair_wdf(df32 ex, df32 ey, float mhat, double alpha, const float2 *tab) {
+  const df32 r2 = df_add(df_mul(ex, ex), df_mul(ey, ey));
+  if (WK == MLS_W_GAUSS) return df_exp(df_add({mhat, 0.f}, {-r2.hi, -r2.lo}), tab);
+  if (WK == MLS_W_WENDLAND) return df_wendland(r2);
+  const double w = pow((double)mhat / ((double)r2.hi + (double)r2.lo), alpha);
+  return {(float)w, (float)(w - (double)(float)w)};
+}
+
+// Candidate index ranges of one pixel: all points, or the rows of grid cells
+// that overlap the Wendland support (cells are at least h wide: <= 3 rows).
+struct Ranges {
+  int a0[3], a1[3], nr;
+};
+
+// Walk the candidates 32 at a time, compact the near ones into the warp's
+// ring and call body(valid, i, ex, ey) on dense batches, one point per lane
+// (only the last batch has lanes with valid == false).  The whole warp calls
+// body.  Returns the number of near points; *coincident is set when a
+// candidate lies exactly on the pixel centre (inverse distance).
+template <int WK, typename Body>
+__device__ __forceinline__ int for_near(const KParams &p, const Ranges &R, float pxh, float pxl, float pyh,
+                                        float pyl, float mhat, int lane, int *ri, float4 *rx, int *coincident,
+                                        Body body) {
+  const unsigned int lt = (1u << lane) - 1u;
+  int head = 0, total = 0, coin = 0;
+  for (int r = 0; r < R.nr; ++r) {
+    for (int base = R.a0[r]; base < R.a1[r]; base += 32) {
+      const int i = base + lane;
+      bool nr = false;
+      df32 ex = {0.f, 0.f}, ey = {0.f, 0.f};
+      if (i < R.a1[r]) {
+        ex = df_diff(p.xs[i], p.xs_lo[i], pxh, pxl);
+        ey = df_diff(p.ys[i], p.ys_lo[i], pyh, pyl);
+        nr = near_test<WK>(ex, ey, mhat);
+        if (WK == MLS_W_INVDIST && !nr) coin = 1;
+      }
+      const unsigned int bal = __ballot_sync(0xffffffffu, nr);
+      if (nr) {
+        const int s = head + __popc(bal & lt);   // < 64: head < 32 here
+        ri[s] = i;
+        rx[s] = make_float4(ex.hi, ex.lo, ey.hi, ey.lo);
+      }
+      head += __popc(bal);
+      total += __popc(bal);
+      __syncwarp();
+      if (head >= 32) {
+        const float4 e = rx[lane];
+        const int ii = ri[lane];
+        __syncwarp();
+        if (lane < head - 32) {
+          ri[lane] = ri[lane + 32];
+          rx[lane] = rx[lane + 32];
+        }
+        __syncwarp();
+        head -= 32;
+        body(true, ii, df32{e.x, e.y}, df32{e.z, e.w});
+      }
+    }
+  }
+  if (head > 0) {
+    const bool v = lane < head;
+    const float4 e = v ? rx[lane] : make_float4(0.f, 0.f, 0.f, 0.f);
+    const int ii = v ? ri[lane] : 0;
+    body(v, ii, df32{e.x, e.y}, df32{e.z, e.w});
+  }
+  __syncwarp();
+  *coincident = __any_sync(0xffffffffu, coin);
+  return total;
+}
+
+// ---------------------------------------------------------------------------
+// FP64 factorisation shared by the warp.
+
+// 1/d for a positive normal d: FP32 seed and two Newton steps (each doubles
+// the number of correct bits: 2^-23 -> 2^-46 -> FP64 rounding).
+__device__ __forceinline__ double rcp64(double d) {
+  double r = (double)__frcp_rn((float)d);
+  r = r * fma(-d, r, 2.0);
+  r = r * fma(-d, r, 2.0);
+  return r;
+}
+
+// Equilibrated LDL^T factorisation of the K x K moment matrix S[midx(a, b)]
+// and rcond_1 = 1 / (|Me|_1 |Me^-1|_1) of the equilibrated matrix Me
+// (columns of the inverse: lane c < K forms column c).  Returns 0 when a
+// diagonal entry or a pivot is not positive.  L (unit lower), dinv (inverse
+// pivots) and sd (equilibration 1/sqrt(M_aa)) receive the factorisation.
+template <int K>
+__device__ double ldl_rcond(const double (&S)[15], int lane, double (&L)[6][6], double (&dinv)[6],
+                            double (&sd)[6]) {
+  double Me[K][K];
+  bool ok = true;
+#pragma unroll
+  for (int a = 0; a < K; ++a) {
+    const double d = S[midx(a, a)];
+    ok = ok && (d > 0.0);
+    sd[a] = ok ? rsqrt(d) : 0.0;
+  }
+  if (!ok) return 0.0;
+#pragma unroll
+  for (int a = 0; a < K; ++a)
+#pragma unroll
+    for (int b = 0; b <= a; ++b) Me[a][b] = Me[b][a] = S[midx(a, b)] * sd[a] * sd[b];
+  // LDL^T (no square roots): D_j = Me_jj - sum_t L_jt^2 D_t,
+  // L_ij = (Me_ij - sum_t L_it L_jt D_t) / D_j
+  double Dg[K];
+#pragma unroll
+  for (int j = 0; j < K; ++j) {
+    double dj = Me[j][j];
+#pragma unroll
+    for (int t = 0; t < j; ++t) dj -= L[j][t] * L[j][t] * Dg[t];
+    if (!(dj > 0.0)) return 0.0;
+    Dg[j] = dj;
+    dinv[j] = rcp64(dj);
+#pragma unroll
+    for (int i = j + 1; i < K; ++i) {
       double v = Me[i][j];
-      for (int t = 0; t < j; ++t) v -= Lm[i][t] * Lm[j][t];
-      Lm[i][j] = v / ljj;
+#pragma unroll
+      for (int t = 0; t < j; ++t) v -= L[i][t] * L[j][t] * Dg[t];
+      L[i][j] = v * dinv[j];
     }
   }
-  double nA = 0.0, nI = 0.0;
-  for (int c = 0; c < k; ++c) {
-    double col[6];
-    for (int a = 0; a < k; ++a) col[a] = (a == c) ? 1.0 : 0.0;
-    for (int i = 0; i < k; ++i) {
-      double v = col[i];
-      for (int t = 0; t < i; ++t) v -= Lm[i][t] * col[t];
-      col[i] = v / Lm[i][i];
+  // column `lane` of Me^-1 and of Me
+  double nI = 0.0, nA = 0.0;
+  if (lane < K) {
+    double col[K];
+#pragma unroll
+    for (int a = 0; a < K; ++a) col[a] = (a == lane) ? 1.0 : 0.0;
+#pragma unroll
+    for (int i = 0; i < K; ++i)
+#pragma unroll
+      for (int t = 0; t < i; ++t) col[i] -= L[i][t] * col[t];
+#pragma unroll
+    for (int i = 0; i < K; ++i) col[i] *= dinv[i];
+#pragma unroll
+    for (int i = K - 1; i >= 0; --i)
+#pragma unroll
+      for (int t = i + 1; t < K; ++t) col[i] -= L[t][i] * col[t];
+#pragma unroll
+    for (int a = 0; a < K; ++a) {
+      nI += fabs(col[a]);
+      double me = 0.0;
+#pragma unroll
+      for (int c = 0; c < K; ++c) me = (c == lane) ? Me[a][c] : me;
+      nA += fabs(me);
     }
-    for (int i = k - 1; i >= 0; --i) {
-      double v = col[i];
-      for (int t = i + 1; t < k; ++t) v -= Lm[t][i] * col[t];
-      col[i] = v / Lm[i][i];
-    }
-    double sa = 0.0, si = 0.0;
-    for (int a = 0; a < k; ++a) {
-      sa += fabs(Me[a][c]);
-      si += fabs(col[a]);
-    }
-    nA = fmax(nA, sa);
-    nI = fmax(nI, si);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    nI = fmax(nI, __shfl_xor_sync(0xffffffffu, nI, o));
+    nA = fmax(nA, __shfl_xor_sync(0xffffffffu, nA, o));
   }
   return 1.0 / (nA * nI);
 }
 
-// The weight of one pair as used by both passes: FP64 distance, FP32 rounding
-// of the weight (its relative error ~1e-7 acts as a common perturbation of
-// the least-squares weights, far below the tolerance of these paths).
-template <int WK>
-__device__ __forceinline__ float pair_w(double r2, double m, double h, double h2, float alpha) {
-  if (WK == MLS_W_GAUSS) {
-    return exp2f((float)(-(r2 - m) / h2 * kLog2e));
-  } else if (WK == MLS_W_WENDLAND) {
-    const float q = (float)(sqrt(r2) / h), o = 1.f - q, o2 = o * o;
-    return o2 * o2 * fmaf(4.f, q, 1.f);
-  } else {
-    return exp2f(alpha * log2f((float)(m / r2)));
-  }
+// b <- M^-1 b with M = S^-1 Me S^-1 factorised as above: S Me^-1 S b.
+template <int K>
+__device__ __forceinline__ void ldl_solve(const double (&L)[6][6], const double (&dinv)[6], const double (&sd)[6],
+                                          double (&b)[6]) {
+#pragma unroll
+  for (int a = 0; a < K; ++a) b[a] *= sd[a];
+#pragma unroll
+  for (int i = 0; i < K; ++i)
+#pragma unroll
+    for (int t = 0; t < i; ++t) b[i] -= L[i][t] * b[t];
+#pragma unroll
+  for (int i = 0; i < K; ++i) b[i] *= dinv[i];
+#pragma unroll
+  for (int i = K - 1; i >= 0; --i)
+#pragma unroll
+    for (int t = i + 1; t < K; ++t) b[i] -= L[t][i] * b[t];
+#pragma unroll
+  for (int a = 0; a < K; ++a) b[a] *= sd[a];
 }
 
-__device__ __forceinline__ double ipow(double x, int e) {
-  double r = 1.0;
-  for (int i = 0; i < e; ++i) r *= x;
-  return r;
+// Moments of the frame centred on (cx, cy) and scaled by isg, from the
+// pixel-frame moments (binomial expansion of (x - cx)^bx (y - cy)^by): lane
+// j < NM forms moment j from the warp's copy of the pixel-frame moments in
+// shared memory, then every lane gathers them.
+template <int NM>
+__device__ __forceinline__ void centroid_moments(const double *sS, double cx, double cy, double isg, int lane,
+                                                 double (&Sc)[15]) {
+  double mine = 0.0;
+  if (lane < NM) {
+    const int bx = mono_ex(lane), by = mono_ey(lane);
+    double pcx[5], pcy[5];
+    pcx[0] = pcy[0] = 1.0;
+#pragma unroll
+    for (int e = 1; e < 5; ++e) {
+      pcx[e] = pcx[e - 1] * -cx;
+      pcy[e] = pcy[e - 1] * -cy;
+    }
+    for (int jx = 0; jx <= bx; ++jx)
+      for (int jy = 0; jy <= by; ++jy)
+        mine += (double)(binom(bx, jx) * binom(by, jy)) * pcx[bx - jx] * pcy[by - jy] * sS[mono_index(jx, jy)];
+    double sc = 1.0;
+    for (int e = 0; e < bx + by; ++e) sc *= isg;
+    mine *= sc;
+  }
+#pragma unroll
+  for (int j = 0; j < 15; ++j) Sc[j] = (j < NM) ? __shfl_sync(0xffffffffu, mine, j) : 0.0;
 }
+
+// z = M_c^-1 b_c(pixel) in the frame of the weighted centroid (degree of K
+// terms); fr receives that frame as pass 2 applies it (centre hi, lo in x
+// and y; 1/sigma).  Returns false when the centroid frame is degenerate or
+// still ill conditioned.
+template <int K>
+__device__ bool centroid_solve(const double (&Sd)[15], const double *sS, int lane, double (&z)[6],
+                               float (&fr)[5]) {
+  constexpr int DEGK = K == 6 ? 2 : 1;
+  const double cx0 = Sd[1] / Sd[0], cy0 = Sd[2] / Sd[0];
+  const double var = (Sd[3] + Sd[5]) / Sd[0] - cx0 * cx0 - cy0 * cy0;
+  if (!(var > 0.0)) return false;
+  fr[0] = (float)cx0;
+  fr[1] = (float)(cx0 - (double)fr[0]);
+  fr[2] = (float)cy0;
+  fr[3] = (float)(cy0 - (double)fr[2]);
+  fr[4] = (float)rsqrt(var);
+  const double cx = (double)fr[0] + (double)fr[1], cy = (double)fr[2] + (double)fr[3];
+  const double isg = (double)fr[4];
+  double Sc[15];
+  centroid_moments<n_moments(DEGK)>(sS, cx, cy, isg, lane, Sc);
+  double L[6][6], dinv[6], sd[6];
+  const double rcc = ldl_rcond<K>(Sc, lane, L, dinv, sd);
+  if (!(rcc > 1.0 / kKappaCentroid)) return false;
+  const double ex = -cx * isg, ey = -cy * isg;
+  double b[6] = {1.0, ex, ey, ex * ex, ex * ey, ey * ey};
+  ldl_solve<K>(L, dinv, sd, b);
+#pragma unroll
+  for (int a = 0; a < 6; ++a) z[a] = (a < K) ? b[a] : 0.0;
+  return true;
+}
+
+// Degree policy on the pixel-frame moments (support count, then rcond_1 of
+// the equilibrated matrix against rcond_min, highest degree first), then z.
+// Returns the degree used (-1: no degree qualifies); *bad is set when the
+// pixel needs the FP64 kernel.
+template <int DEG>
+__device__ int pixel_policy(const double (&Sd)[15], const double *sS, long long count, double rcond_min, int lane,
+                            double (&z)[6], float (&fr)[5], bool *bad) {
+  double L[6][6], dinv[6], sd[6];
+  int used = -1;
+  if (DEG >= 2 && count >= 6 && ldl_rcond<6>(Sd, lane, L, dinv, sd) >= rcond_min) used = 2;
+  else if (DEG >= 1 && count >= 3 && ldl_rcond<3>(Sd, lane, L, dinv, sd) >= rcond_min) used = 1;
+  else if (count >= 1 && Sd[0] > 0.0) used = 0;
+  for (int a = 0; a < 6; ++a) z[a] = 0.0;
+  fr[0] = fr[1] = fr[2] = fr[3] = 0.f;
+  fr[4] = 1.f;
+  *bad = false;
+  if (used == 0) z[0] = 1.0 / Sd[0];
+  else if (used == 1) *bad = !centroid_solve<3>(Sd, sS, lane, z, fr);
+  else if (used == 2) *bad = !centroid_solve<6>(Sd, sS, lane, z, fr);
+  return used;
+}
+
+// ---------------------------------------------------------------------------
 
 template <int DEG, int WK>
-__global__ __launch_bounds__(256) void k_handover(KParams p, const int *list, const unsigned int *list_count,
-                                                  int64_t cap, int *list2, unsigned int *list2_count) {
-  constexpr int K = n_terms(DEG), NM = n_moments(DEG);
-  const int lane = threadIdx.x & 31;
+__global__ __launch_bounds__(kWarps * 32, 2) void k_handover(KParams p, const int *list,
+                                                          const unsigned int *list_count, int64_t cap, int *list2,
+                                                          unsigned int *list2_count) {
+  constexpr int NM = n_moments(DEG);
+  __shared__ int s_ri[kWarps][kRing];
+  __shared__ float4 s_rx[kWarps][kRing];
+  __shared__ double s_S[kWarps][16];
+  __shared__ float2 s_tab[64];
+  if (WK == MLS_W_GAUSS) df_exp_table_init(s_tab);
+  __syncthreads();
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  int *ri = s_ri[wib];
+  float4 *rx = s_rx[wib];
   const int64_t warp0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   const int64_t npix = (int64_t)*list_count < cap ? (int64_t)*list_count : cap;
   const size_t plane = (size_t)p.W * p.H;
-  const double h = p.h, h2 = h * h, inv_s = 1.0 / h;
+  const double inv_s = 1.0 / p.h;
   float *field = (float *)p.field;
 
   for (int64_t qi = warp0; qi < npix; qi += nwarps) {
@@ -132,144 +388,92 @@ __global__ __launch_bounds__(256) void k_handover(KParams p, const int *list, co
     const int u = id % p.W, v = id / p.W;
     const double px = __dadd_rn(p.x0, __dmul_rn(__dadd_rn((double)u, 0.5), p.sx));
     const double py = __dadd_rn(p.y0, __dmul_rn(__dadd_rn((double)v, 0.5), p.sy));
-    const float pxs = scaled_px(p, u), pys = scaled_py(p, v);
-    const size_t pi = (size_t)v * (p.tiles_x * 16) + u;
-    const float mhat = (WK == MLS_W_WENDLAND) ? 0.f : p.mstab[pi];
-    const double m = (double)mhat * h2;
-    int a0s[3] = {0, 0, 0}, a1s[3] = {0, 0, 0}, nr = 1;
+    const float mhat = (WK == MLS_W_WENDLAND) ? 0.f : p.mstab[(size_t)v * (p.tiles_x * 16) + u];
+    Ranges R;
     if (WK == MLS_W_WENDLAND) {
       const double inv_cell = 1.0 / p.cell;
-      const int cx0 = max((int)floor((px - h - p.gx0) * inv_cell), 0);
-      const int cx1 = min((int)floor((px + h - p.gx0) * inv_cell), p.gx - 1);
-      const int cy0 = max((int)floor((py - h - p.gy0) * inv_cell), 0);
-      const int cy1 = min((int)floor((py + h - p.gy0) * inv_cell), p.gy - 1);
-      nr = 0;
-      for (int cy = cy0; cy <= cy1 && cx0 <= cx1 && nr < 3; ++cy, ++nr) {
-        a0s[nr] = p.cell_start[cy * p.gx + cx0];
-        a1s[nr] = p.cell_start[cy * p.gx + cx1 + 1];
+      const int cx0 = max((int)floor((px - p.h - p.gx0) * inv_cell), 0);
+      const int cx1 = min((int)floor((px + p.h - p.gx0) * inv_cell), p.gx - 1);
+      const int cy0 = max((int)floor((py - p.h - p.gy0) * inv_cell), 0);
+      const int cy1 = min((int)floor((py + p.h - p.gy0) * inv_cell), p.gy - 1);
+      R.nr = 0;
+      for (int cy = cy0; cy <= cy1 && cx0 <= cx1 && R.nr < 3; ++cy, ++R.nr) {
+        R.a0[R.nr] = p.cell_start[cy * p.gx + cx0];
+        R.a1[R.nr] = p.cell_start[cy * p.gx + cx1 + 1];
       }
     } else {
-      a1s[0] = (int)p.n;
+      R.nr = 1;
+      R.a0[0] = 0;
+      R.a1[0] = (int)p.n;
     }
+    // pixel position in the scaled frame as hi + lo
+    const double pxs64 = (px - p.ctr_x) * inv_s, pys64 = (py - p.ctr_y) * inv_s;
+    const float pxh = (float)pxs64, pxl = (float)(pxs64 - (double)pxh);
+    const float pyh = (float)pys64, pyl = (float)(pys64 - (double)pyh);
 
-    // ---- pass 1: FP64 pixel-frame moments and support count
-    double S[15];
+    // ---- pass 1: double-float pixel-frame moments of the near points
+    df32 S[NM];
 #pragma unroll
-    for (int j = 0; j < 15; ++j) S[j] = 0.0;
-    long long count = 0;
+    for (int j = 0; j < NM; ++j) S[j] = {0.f, 0.f};
     int coincident = 0;
-    for (int r = 0; r < nr; ++r) {
-      for (int i = a0s[r] + lane; i < a1s[r]; i += 32) {
-        if (WK == MLS_W_GAUSS) {
-          ++count;
-          const float dxs = p.xs[i] - pxs, dys = p.ys[i] - pys;
-          if (fmaf(dxs, dxs, dys * dys) - mhat > (float)kCut + 1.f) continue;
-        }
-        const double dx = __dadd_rn(p.x64[i], -px), dy = __dadd_rn(p.y64[i], -py);
-        const double r2 = __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy));
-        if (WK == MLS_W_GAUSS) {
-          if (r2 - m > kCut * h2) continue;
-        } else if (WK == MLS_W_WENDLAND) {
-          if (!(r2 < h2)) continue;
-          ++count;
-        } else {
-          ++count;
-          if (r2 == 0.0) {
-            coincident = 1;
-            continue;
-          }
-        }
-        const double w = (double)pair_w<WK>(r2, m, h, h2, (float)p.alpha);
-        const double ex = dx * inv_s, ey = dy * inv_s;
-        double mo[15];
-        mo[0] = 1.0;
-        if (NM > 1) { mo[1] = ex; mo[2] = ey; mo[3] = ex * ex; mo[4] = ex * ey; mo[5] = ey * ey; }
+    const int nnear = for_near<WK>(p, R, pxh, pxl, pyh, pyl, mhat, lane, ri, rx, &coincident,
+                                   [&](bool valid, int, df32 ex, df32 ey) {
+      if (!valid) return;
+      const df32 w = pair_wdf<WK>(ex, ey, mhat, p.alpha, s_tab);
+      df_acc(S[0], w);
+      if (NM > 1) {
+        const df32 wx = df_prod(w, ex), wy = df_prod(w, ey);
+        const df32 wxx = df_prod(wx, ex), wxy = df_prod(wx, ey), wyy = df_prod(wy, ey);
+        df_acc(S[1], wx);
+        df_acc(S[2], wy);
+        df_acc(S[3], wxx);
+        df_acc(S[4], wxy);
+        df_acc(S[5], wyy);
         if (NM > 6) {
-          mo[6] = mo[3] * ex; mo[7] = mo[3] * ey; mo[8] = mo[5] * ex; mo[9] = mo[5] * ey;
-          mo[10] = mo[3] * mo[3]; mo[11] = mo[3] * mo[4]; mo[12] = mo[3] * mo[5]; mo[13] = mo[4] * mo[5];
-          mo[14] = mo[5] * mo[5];
+          const df32 wxxx = df_prod(wxx, ex), wxxy = df_prod(wxx, ey);
+          const df32 wxyy = df_prod(wyy, ex), wyyy = df_prod(wyy, ey);
+          df_acc(S[6], wxxx);
+          df_acc(S[7], wxxy);
+          df_acc(S[8], wxyy);
+          df_acc(S[9], wyyy);
+          df_acc(S[10], df_prod(wxxx, ex));
+          df_acc(S[11], df_prod(wxxx, ey));
+          df_acc(S[12], df_prod(wxxy, ey));
+          df_acc(S[13], df_prod(wxyy, ey));
+          df_acc(S[14], df_prod(wyyy, ey));
         }
-#pragma unroll
-        for (int j = 0; j < NM; ++j) S[j] += w * mo[j];
       }
-    }
+    });
+    double Sd[15];
 #pragma unroll
-    for (int j = 0; j < NM; ++j) S[j] = wsum(S[j]);
-    count = wsum(count);
-    const bool to_fp64 = (WK == MLS_W_INVDIST) && __any_sync(0xffffffffu, coincident);
-
-    // ---- degree policy on the pixel-frame moments (FP64)
-    int used = -1;
-    double Lm[6][6], sd[6];
-    if (!to_fp64) {
-      for (int deg = DEG; deg >= 0 && used < 0; --deg) {
-        const int k = n_terms(deg);
-        if (count < k) continue;
-        const double rc = factor_moments(S, k, Lm, sd);
-        if (rc >= p.rcond_min) used = deg;
-      }
-    }
-    // ---- centroid frame and the solve for z
-    double z[6] = {0, 0, 0, 0, 0, 0};
-    double cxh = 0.0, cyh = 0.0, isg = 1.0;    // centroid offset (raw units) and 1/(h sigma)
-    bool bad = to_fp64;
-    if (!bad && used == 0) {
-      z[0] = 1.0 / S[0];
-    } else if (!bad && used > 0) {
-      const int k = n_terms(used);
-      const double cx = S[1] / S[0], cy = S[2] / S[0];
-      const double var = (S[3] + S[5]) / S[0] - cx * cx - cy * cy;
-      if (!(var > 0.0)) {
-        bad = true;
+    for (int j = 0; j < 15; ++j) {
+      if (j < NM) {
+        const df32 t = df_warp_sum(S[j]);
+        Sd[j] = (double)t.hi + (double)t.lo;
       } else {
-        const double sg = sqrt(var);
-        double Sc[15];
-        const int nm = n_moments(used);
-        for (int j = 0; j < nm; ++j) {
-          const int bx = mono_ex(j), by = mono_ey(j);
-          double acc = 0.0;
-          for (int jx = 0; jx <= bx; ++jx)
-            for (int jy = 0; jy <= by; ++jy)
-              acc += binom(bx, jx) * binom(by, jy) * ipow(-cx, bx - jx) * ipow(-cy, by - jy) *
-                     S[mono_index(jx, jy)];
-          Sc[j] = acc / ipow(sg, bx + by);
-        }
-        double Lc[6][6], sdc[6];
-        const double rcc = factor_moments(Sc, k, Lc, sdc);
-        if (!(rcc > 1.0 / kKappaCentroid)) {
-          bad = true;
-        } else {
-          // z = M_c^{-1} b_c(pixel), b_c(pixel) at (-cx, -cy)/sg
-          const double ex = -cx / sg, ey = -cy / sg;
-          double b[6] = {1.0, ex, ey, ex * ex, ex * ey, ey * ey};
-          for (int a = 0; a < k; ++a) b[a] *= sdc[a];
-          for (int i = 0; i < k; ++i) {
-            double vv = b[i];
-            for (int t = 0; t < i; ++t) vv -= Lc[i][t] * b[t];
-            b[i] = vv / Lc[i][i];
-          }
-          for (int i = k - 1; i >= 0; --i) {
-            double vv = b[i];
-            for (int t = i + 1; t < k; ++t) vv -= Lc[t][i] * b[t];
-            b[i] = vv / Lc[i][i];
-          }
-          double lambda = 0.0;
-          for (int a = 0; a < k; ++a) {
-            z[a] = b[a] * sdc[a];
-            lambda += fabs(z[a]) * sqrt(Sc[0] * Sc[kMIdx[a][a]]);
-          }
-          if (!(lambda <= kLambdaMax)) bad = true;
-          cxh = cx * h;
-          cyh = cy * h;
-          isg = inv_s / sg;
-        }
+        Sd[j] = 0.0;
       }
     }
+#pragma unroll
+    for (int j = 0; j < 15; ++j)
+      if (lane == j) s_S[wib][j] = Sd[j];
+    __syncwarp();
+    const long long count = (WK == MLS_W_WENDLAND) ? nnear : p.n;
+    // inverse distance: a coincident point (or a zero stabiliser) goes to the
+    // FP64 kernel, which gives the pixel that point's value
+    bool bad = WK == MLS_W_INVDIST && (coincident || !(mhat > 0.f));
+
+    // ---- degree policy (pixel frame) and the solve in the centroid frame (FP64)
+    double z[6];
+    float fr[5];
+    int used = -1;
+    if (!bad) used = pixel_policy<DEG>(Sd, s_S[wib], count, p.rcond_min, lane, z, fr, &bad);
     if (bad) {
       if (lane == 0) {
         const unsigned int k2 = atomicAdd(list2_count, 1u);
         list2[k2] = id;
       }
+      __syncwarp();
       continue;
     }
     if (used < 0) {
@@ -278,56 +482,55 @@ __global__ __launch_bounds__(256) void k_handover(KParams p, const int *list, co
         if (p.bands) p.bands[(size_t)d * plane + id] = 255;
       }
       if (lane == 0 && p.status) p.status[id] = MLS_ST_NO_SUPPORT | MLS_ST_RECOMPUTED;
+      __syncwarp();
       continue;
     }
     const int ku = n_terms(used);
+    df32 zd[6];
+#pragma unroll
+    for (int a = 0; a < 6; ++a) zd[a] = {(float)z[a], (float)(z[a] - (double)(float)z[a])};
+    const float cxh = fr[0], cxl = fr[1], cyh = fr[2], cyl = fr[3], isg = fr[4];
 
-    // ---- pass 2: FP32 right-hand sides in the centroid frame
-    for (int d0 = 0; d0 < p.D; d0 += kDC) {
-      float R[K][kDC];
+    // ---- pass 2: value = sum_i phi_i f_i, phi_i = w_i z . b_c(x_i); lanes over dimensions
+    for (int d0 = 0; d0 < p.D; d0 += 32 * kDL) {
+      df32 acc[kDL];
 #pragma unroll
-      for (int a = 0; a < K; ++a)
-#pragma unroll
-        for (int dd = 0; dd < kDC; ++dd) R[a][dd] = 0.f;
-      for (int r = 0; r < nr; ++r) {
-        for (int i = a0s[r] + lane; i < a1s[r]; i += 32) {
-          if (WK == MLS_W_GAUSS) {
-            const float dxs = p.xs[i] - pxs, dys = p.ys[i] - pys;
-            if (fmaf(dxs, dxs, dys * dys) - mhat > (float)kCut + 1.f) continue;
+      for (int t = 0; t < kDL; ++t) acc[t] = {0.f, 0.f};
+      int unused;
+      for_near<WK>(p, R, pxh, pxl, pyh, pyl, mhat, lane, ri, rx, &unused,
+                   [&](bool valid, int i, df32 ex, df32 ey) {
+        df32 phi = {0.f, 0.f};
+        if (valid) {
+          const df32 w = pair_wdf<WK>(ex, ey, mhat, p.alpha, s_tab);
+          df32 zb = zd[0];
+          if (ku > 1) {
+            const df32 cxe = df_mul_f(df_diff(ex.hi, ex.lo, cxh, cxl), isg);
+            const df32 cye = df_mul_f(df_diff(ey.hi, ey.lo, cyh, cyl), isg);
+            zb = df_add(zb, df_add(df_mul(zd[1], cxe), df_mul(zd[2], cye)));
+            if (ku > 3) {
+              const df32 t = df_add(df_mul(zd[3], cxe), df_mul(zd[4], cye));
+              zb = df_add(zb, df_add(df_mul(t, cxe), df_mul(df_mul(zd[5], cye), cye)));
+            }
           }
-          const double dx = __dadd_rn(p.x64[i], -px), dy = __dadd_rn(p.y64[i], -py);
-          const double r2 = __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy));
-          if (WK == MLS_W_GAUSS) {
-            if (r2 - m > kCut * h2) continue;
-          } else if (WK == MLS_W_WENDLAND) {
-            if (!(r2 < h2)) continue;
-          }
-          const float w = pair_w<WK>(r2, m, h, h2, (float)p.alpha);
-          // centroid-frame coordinates formed in FP64 (no cancellation in FP32)
-          const float ex = (float)((dx - cxh) * isg), ey = (float)((dy - cyh) * isg);
-          float b[6];
-          b[0] = w;
-          if (K > 1) { b[1] = w * ex; b[2] = w * ey; }
-          if (K > 3) { b[3] = w * ex * ex; b[4] = w * ex * ey; b[5] = w * ey * ey; }
-#pragma unroll
-          for (int dd = 0; dd < kDC; ++dd) {
-            const float f = (d0 + dd < p.D) ? p.FT32[(size_t)(d0 + dd) * p.n_pad + i] : 0.f;
-#pragma unroll
-            for (int a = 0; a < K; ++a) R[a][dd] = fmaf(b[a], f, R[a][dd]);
-          }
+          phi = df_mul(w, zb);
         }
-      }
+        const int nb = __popc(__ballot_sync(0xffffffffu, valid));
+#pragma unroll 4
+        for (int j = 0; j < nb; ++j) {
+          const df32 ph = {__shfl_sync(0xffffffffu, phi.hi, j), __shfl_sync(0xffffffffu, phi.lo, j)};
+          const int ij = __shfl_sync(0xffffffffu, i, j);
+          const float *fp = p.FR32 + (size_t)ij * p.D + d0 + lane;
 #pragma unroll
-      for (int a = 0; a < K; ++a)
+          for (int t = 0; t < kDL; ++t)
+            if (d0 + lane + 32 * t < p.D) df_acc(acc[t], df_prod_f(ph, fp[32 * t]));
+        }
+      });
 #pragma unroll
-        for (int dd = 0; dd < kDC; ++dd) R[a][dd] = wsum(R[a][dd]);
-#pragma unroll
-      for (int dd = 0; dd < kDC; ++dd) {
-        const int d = d0 + dd;
-        if (lane == dd && d < p.D) {
-          double acc = 0.0;
-          for (int a = 0; a < ku; ++a) acc += z[a] * (double)R[a][dd];
-          const float f = (float)((double)p.fcen32[d] + (double)p.fscl32[d] * acc);
+      for (int t = 0; t < kDL; ++t) {
+        const int d = d0 + lane + 32 * t;
+        if (d < p.D) {
+          const double fv = (double)acc[t].hi + (double)acc[t].lo;
+          const float f = (float)((double)p.fcen32[d] + (double)p.fscl32[d] * fv);
           field[(size_t)d * plane + id] = f;
           if (p.bands) p.bands[(size_t)d * plane + id] = band_of(f, p.lev32 + (size_t)d * p.L, p.L);
         }
@@ -335,16 +538,17 @@ __global__ __launch_bounds__(256) void k_handover(KParams p, const int *list, co
     }
     if (lane == 0 && p.status)
       p.status[id] = (uint8_t)(used | MLS_ST_RECOMPUTED | (used < DEG ? MLS_ST_DEGRADED : 0));
+    __syncwarp();
   }
 }
 
 template <int WK>
 void launch_w(const KParams &p, const int *list, const unsigned int *cnt, int64_t cap, int *list2,
               unsigned int *cnt2, cudaStream_t st) {
-  const int grid = 152 * 8;
-  if (p.degree == 0) k_handover<0, WK><<<grid, 256, 0, st>>>(p, list, cnt, cap, list2, cnt2);
-  else if (p.degree == 1) k_handover<1, WK><<<grid, 256, 0, st>>>(p, list, cnt, cap, list2, cnt2);
-  else k_handover<2, WK><<<grid, 256, 0, st>>>(p, list, cnt, cap, list2, cnt2);
+  const int grid = 152 * 2;   // one resident wave (2 blocks of 8 warps per SM)
+  if (p.degree == 0) k_handover<0, WK><<<grid, kWarps * 32, 0, st>>>(p, list, cnt, cap, list2, cnt2);
+  else if (p.degree == 1) k_handover<1, WK><<<grid, kWarps * 32, 0, st>>>(p, list, cnt, cap, list2, cnt2);
+  else k_handover<2, WK><<<grid, kWarps * 32, 0, st>>>(p, list, cnt, cap, list2, cnt2);
 }
 
 }  // namespace
@@ -356,4 +560,38 @@ void launch_handover(const KParams &p, const int *list, const unsigned int *cnt,
   else launch_w<MLS_W_INVDIST>(p, list, cnt, cap, list2, cnt2, st);
 }
 
+// Test hook: the double-float weight functions on given arguments.
+__global__ void k_debug_df_weight(int kind, const float *ahi, const float *alo, int64_t n, double *out) {
+  __shared__ float2 tab[64];
+  mlsk::df_exp_table_init(tab);
+  __syncthreads();
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const mlsk::df32 a = {ahi[i], alo[i]};
+    const mlsk::df32 w = kind == 0 ? mlsk::df_exp(a, tab) : kind == 1 ? mlsk::df_wendland(a) : mlsk::df_sqrt(a);
+    out[i] = (double)w.hi + (double)w.lo;
+  }
+}
+
 }  // namespace mlsi
+
+extern "C" int mls_debug_df_weight(int kind, const float *arg_hi, const float *arg_lo, int64_t n, double *out) {
+  if (kind < 0 || kind > 2 || n < 0 || (n > 0 && (!arg_hi || !arg_lo || !out))) return MLS_E_INVAL;
+  if (n == 0) return MLS_OK;
+  float *d = nullptr;
+  double *o = nullptr;
+  if (cudaMalloc(&d, sizeof(float) * 2 * n) != cudaSuccess) return MLS_E_NOMEM;
+  if (cudaMalloc(&o, sizeof(double) * n) != cudaSuccess) {
+    cudaFree(d);
+    return MLS_E_NOMEM;
+  }
+  cudaError_t e = cudaMemcpy(d, arg_hi, sizeof(float) * n, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(d + n, arg_lo, sizeof(float) * n, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) {
+    mlsi::k_debug_df_weight<<<152, 256>>>(kind, d, d + n, n, o);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpy(out, o, sizeof(double) * n, cudaMemcpyDeviceToHost);
+  cudaFree(d);
+  cudaFree(o);
+  return e == cudaSuccess ? MLS_OK : MLS_E_CUDA;
+}

@@ -82,7 +82,9 @@ static mls_status check_levels(const double *levels, int L, int D) {
 static mls_status ensure_scratch(mls_handle *h, int W, int H, cudaStream_t st) {
   const int tx = (W + kTile - 1) / kTile, ty = (H + kTile - 1) / kTile;
   const size_t padded = (size_t)tx * kTile * ty * kTile;
-  const size_t need = 256 + padded * sizeof(float) + padded * sizeof(int) + 2 * (size_t)W * H * sizeof(int) + 256;
+  const size_t ntile = (size_t)tx * ty;
+  const size_t need = 256 + padded * sizeof(float) + padded * sizeof(int) + 2 * (size_t)W * H * sizeof(int) +
+                      2 * ntile * sizeof(float) + 256;
   if (need <= h->scratch_bytes) return MLS_OK;
   release(h, h->scratch, st);
   h->scratch = nullptr;
@@ -99,6 +101,7 @@ static mls_status ensure_scratch(mls_handle *h, int W, int H, cudaStream_t st) {
   h->cnt = (int *)(b + 256 + padded * sizeof(float));
   h->relist = (int *)(b + 256 + padded * (sizeof(float) + sizeof(int)));
   h->relist2 = h->relist + (size_t)W * H;
+  h->tcen = (float *)(h->relist2 + (size_t)W * H);
   return MLS_OK;
 }
 
@@ -161,7 +164,10 @@ static mlsk::KParams base_params(const mls_handle *h, const mls_view *v) {
   p.D_pad = P.D_pad;
   p.xs = P.xs;
   p.ys = P.ys;
+  p.xs_lo = P.xs_lo;
+  p.ys_lo = P.ys_lo;
   p.FT32 = P.FT32;
+  p.FR32 = P.FR32;
   p.fcen32 = P.fcen32;
   p.fscl32 = P.fscl32;
   p.x64 = P.x64;
@@ -183,6 +189,11 @@ static mlsk::KParams base_params(const mls_handle *h, const mls_view *v) {
   p.cond_fp64 = d.cond_fp64;
   p.rcond_min = d.rcond_degenerate;
   p.cond_recompute = d.cond_recompute;
+  // amplification of right-hand-side rounding the fast path accepts, from the
+  // precision of its weights and operands (calibrated against the FP64 oracle)
+  p.lambda_max = d.precision == MLS_P_FP32 ? 1000.f
+               : d.precision == MLS_P_FP16 ? (d.weight_split ? 1000.f : 30.f)
+               : (d.weight_split ? 50.f : 10.f);
   p.W = v->W;
   p.H = v->H;
   p.x0 = v->x0;
@@ -196,6 +207,7 @@ static mlsk::KParams base_params(const mls_handle *h, const mls_view *v) {
   p.tiles_y = (v->H + kTile - 1) / kTile;
   p.mstab = h->mstab;
   p.cnt = h->cnt;
+  p.tcen = h->tcen;
   p.relist = h->relist;
   p.relist_count = h->counters;
   p.err = h->err;

@@ -22,6 +22,8 @@ struct PointSet {
   double bbox[4] = {0, 0, 0, 0};     // xmin, ymin, xmax, ymax
   double *x64 = nullptr, *y64 = nullptr, *FT64 = nullptr;
   float *xs = nullptr, *ys = nullptr, *FT32 = nullptr;
+  float *FR32 = nullptr;             // point-major normalised values (reduced-precision renders)
+  float *xs_lo = nullptr, *ys_lo = nullptr;
   double *fcen = nullptr, *fscl = nullptr;
   float *fcen32 = nullptr, *fscl32 = nullptr;
   float *xyb = nullptr, *fb = nullptr;   // point-blocked layouts of the tensor path
@@ -46,6 +48,7 @@ struct mls_handle {
   int *cnt = nullptr;
   int *relist = nullptr;
   int *relist2 = nullptr;            // pixels the hand-over path passes to FP64
+  float *tcen = nullptr;             // per-tile moment frame centres
   unsigned int *counters = nullptr;  // [0] recompute count
   int *err = nullptr;
   double *lev64 = nullptr;

@@ -57,7 +57,12 @@ __global__ __launch_bounds__(128) void k_mls_f32(KParams p) {
   const int t = threadIdx.x;
   const int u = blockIdx.x * 16 + (t & 15), v = blockIdx.y * 8 + (t >> 4);
   const bool inside = (u < p.W) && (v < p.H);
-  const float px = scaled_px(p, u), py = scaled_py(p, v);
+  // moments in the frame of the tile's weighted centroid (see the prepass);
+  // (dpx, dpy) = pixel minus frame origin
+  const int tile = (int)(blockIdx.y >> 1) * p.tiles_x + (int)blockIdx.x;
+  const float cxs = p.tcen[2 * tile], cys = p.tcen[2 * tile + 1];
+  const float dpx = (float)((p.x0 + (u + 0.5) * p.sx - p.ctr_x) * p.inv_s - (double)cxs);
+  const float dpy = (float)((p.y0 + (v + 0.5) * p.sy - p.ctr_y) * p.inv_s - (double)cys);
   const size_t pstride = (size_t)p.tiles_x * 16;
   const float m = (WK == MLS_W_WENDLAND) ? 0.f : p.mstab[(size_t)v * pstride + u];
   const int count = (WK == MLS_W_WENDLAND) ? p.cnt[(size_t)v * pstride + u] : (int)(p.n < (1 << 30) ? p.n : (1 << 30));
@@ -105,8 +110,8 @@ __global__ __launch_bounds__(128) void k_mls_f32(KParams p) {
         __syncthreads();
         const int cnt = min(kF32Chunk, a1 - base);
         if (t < cnt) {
-          sx[t] = p.xs[base + t];
-          sy[t] = p.ys[base + t];
+          sx[t] = p.xs[base + t] - cxs;
+          sy[t] = p.ys[base + t] - cys;
         }
         for (int e = t; e < DC * kF32Chunk; e += 128) {
           const int dd = e / kF32Chunk, j = e % kF32Chunk;
@@ -114,8 +119,9 @@ __global__ __launch_bounds__(128) void k_mls_f32(KParams p) {
         }
         __syncthreads();
         for (int j = 0; j < cnt; ++j) {
-          const float dx = sx[j] - px, dy = sy[j] - py;
-          const float r2 = fmaf(dx, dx, dy * dy);
+          const float dx = sx[j], dy = sy[j];               // frame coordinates
+          const float qx = dx - dpx, qy = dy - dpy;         // from the pixel
+          const float r2 = fmaf(qx, qx, qy * qy);
           float w;
           if (WK == MLS_W_GAUSS) {
             w = exp2f((m - r2) * kLog2e);
@@ -179,7 +185,7 @@ __global__ __launch_bounds__(128) void k_mls_f32(KParams p) {
     int outcome = SOLVE_RECOMPUTE;
     // pixels whose support count is near a degree threshold go to FP64,
     // which applies the count rule in the same precision as the definition
-    if (!(WK == MLS_W_WENDLAND && count <= K + 2)) outcome = solve_pixel_fp32<K>(S, z, p);
+    if (!(WK == MLS_W_WENDLAND && count <= K + 2)) outcome = solve_pixel_fp32<K>(S, dpx, dpy, z, p);
     if (outcome == SOLVE_RECOMPUTE) {
       write = false;
       if (d0 == 0) {

@@ -168,19 +168,26 @@ __global__ void k_gather_transpose(const double *xy, const double *F, int64_t n,
   }
 }
 
-// FP32 layouts: scaled positions and normalised values, zero padded.
+// FP32 layouts: scaled positions and normalised values, zero padded;
+// optionally the values point-major as well.
 __global__ void k_finish(const double *x64, const double *y64, const double *FT64, int64_t n, int64_t n_pad,
                          int D, int D_pad, double ctr_x, double ctr_y, double inv_s, const double *cen,
-                         const double *scl, float *xs, float *ys, float *FT32) {
+                         const double *scl, float *xs, float *ys, float *FT32, float *xs_lo, float *ys_lo,
+                         float *FR32) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int d = blockIdx.y;
   if (i >= n_pad) return;
   float v = 0.f;
   if (d < D && i < n) v = (float)((FT64[(int64_t)d * n + i] - cen[d]) / scl[d]);
   FT32[(int64_t)d * n_pad + i] = v;
+  if (FR32 && d < D) FR32[i * D + d] = v;
   if (d == 0) {
-    xs[i] = (i < n) ? (float)((x64[i] - ctr_x) * inv_s) : 0.f;
-    ys[i] = (i < n) ? (float)((y64[i] - ctr_y) * inv_s) : 0.f;
+    const double X = (i < n) ? (x64[i] - ctr_x) * inv_s : 0.0;
+    const double Y = (i < n) ? (y64[i] - ctr_y) * inv_s : 0.0;
+    xs[i] = (float)X;
+    ys[i] = (float)Y;
+    xs_lo[i] = (float)(X - (double)(float)X);
+    ys_lo[i] = (float)(Y - (double)(float)Y);
   }
 }
 
@@ -274,7 +281,10 @@ mls_status prep_points(mls_handle *h, const double *xy, const double *F, cudaStr
   ALLOC(P.FT64, sizeof(double) * n * D);
   ALLOC(P.xs, sizeof(float) * P.n_pad);
   ALLOC(P.ys, sizeof(float) * P.n_pad);
+  ALLOC(P.xs_lo, sizeof(float) * P.n_pad);
+  ALLOC(P.ys_lo, sizeof(float) * P.n_pad);
   ALLOC(P.FT32, sizeof(float) * P.n_pad * P.D_pad);
+  if (d.precision != MLS_P_FP64) ALLOC(P.FR32, sizeof(float) * P.n_pad * D);
   ALLOC(P.fcen, sizeof(double) * D);
   ALLOC(P.fscl, sizeof(double) * D);
   ALLOC(P.fcen32, sizeof(float) * D);
@@ -332,7 +342,7 @@ mls_status prep_points(mls_handle *h, const double *xy, const double *F, cudaStr
     ++h->launches;
     dim3 g2((unsigned)((P.n_pad + 255) / 256), (unsigned)P.D_pad);
     k_finish<<<g2, 256, 0, st>>>(P.x64, P.y64, P.FT64, n, P.n_pad, D, P.D_pad, P.ctr_x, P.ctr_y, 1.0 / P.s,
-                                 P.fcen, P.fscl, P.xs, P.ys, P.FT32);
+                                 P.fcen, P.fscl, P.xs, P.ys, P.FT32, P.xs_lo, P.ys_lo, P.FR32);
     ++h->launches;
     MLS_CUDA_TRY(cudaGetLastError());
   }

@@ -11,6 +11,12 @@
 //
 // Wendland weight: the number of points within the support radius of each
 // pixel, from the cells of the uniform grid that overlap the tile.
+//
+// Both also give each tile the frame its moments are accumulated in: the
+// weighted centroid of the points around the tile centre (Gaussian weights of
+// scale h, or the Wendland weights).  A pixel whose points lie to one side is
+// badly conditioned in its own frame but not in this one, so far fewer pixels
+// need the hand-over path; the fit itself does not depend on the frame.
 #include <float.h>
 
 #include "mls_internal.h"
@@ -19,6 +25,18 @@ namespace mlsi {
 namespace {
 
 using mlsk::KParams;
+
+__device__ __forceinline__ float block_sum(float v, float *red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) red[w] = v;
+  __syncthreads();
+  float r = 0.f;
+  for (int i = 0; i < (int)(blockDim.x >> 5); ++i) r += red[i];
+  return r;
+}
 
 __device__ __forceinline__ float block_min(float v, float *red) {
 #pragma unroll
@@ -78,6 +96,32 @@ __global__ __launch_bounds__(256) void k_prepass_min(KParams p) {
   }
   const int stride = p.tiles_x * 16;
   const_cast<float *>(p.mstab)[(size_t)v * stride + u] = m;
+
+  // frame of the tile: Gaussian-weighted centroid of the points around its centre
+  const float Cx = mlsk::scaled_px(p, u0 + 8) - 0.5f * (mlsk::scaled_px(p, u0 + 8) - mlsk::scaled_px(p, u0 + 7));
+  const float Cy = mlsk::scaled_py(p, v0 + 8) - 0.5f * (mlsk::scaled_py(p, v0 + 8) - mlsk::scaled_py(p, v0 + 7));
+  float mc = FLT_MAX;
+  for (int i = t; i < n; i += 256) {
+    const float dx = p.xs[i] - Cx, dy = p.ys[i] - Cy;
+    mc = fminf(mc, dx * dx + dy * dy);
+  }
+  mc = block_min(mc, red);
+  float sw = 0.f, swx = 0.f, swy = 0.f;
+  for (int i = t; i < n; i += 256) {
+    const float dx = p.xs[i] - Cx, dy = p.ys[i] - Cy;
+    const float w = exp2f((mc - (dx * dx + dy * dy)) * 1.4426950408889634f);
+    sw += w;
+    swx = fmaf(w, dx, swx);
+    swy = fmaf(w, dy, swy);
+  }
+  sw = block_sum(sw, red);
+  swx = block_sum(swx, red);
+  swy = block_sum(swy, red);
+  if (t == 0) {
+    float *tc = const_cast<float *>(p.tcen) + 2 * (blockIdx.y * p.tiles_x + blockIdx.x);
+    tc[0] = (sw > 0.f) ? Cx + swx / sw : Cx;
+    tc[1] = (sw > 0.f) ? Cy + swy / sw : Cy;
+  }
 }
 
 // Inclusive cell range [c0, c1] covering [lo - r, hi + r] along one axis.
@@ -122,6 +166,33 @@ __global__ __launch_bounds__(256) void k_prepass_count(KParams p) {
   }
   const int stride = p.tiles_x * 16;
   const_cast<int *>(p.cnt)[(size_t)v * stride + u] = count;
+
+  // frame of the tile: Wendland-weighted centroid around its centre
+  __shared__ float red[8];
+  const float Cx = 0.5f * (mlsk::scaled_px(p, u0 + 7) + mlsk::scaled_px(p, u0 + 8));
+  const float Cy = 0.5f * (mlsk::scaled_py(p, v0 + 7) + mlsk::scaled_py(p, v0 + 8));
+  float sw = 0.f, swx = 0.f, swy = 0.f;
+  for (int cyy = cy0; cyy <= cy1 && cx0 <= cx1; ++cyy) {
+    const int a = p.cell_start[cyy * p.gx + cx0];
+    const int e = p.cell_start[cyy * p.gx + cx1 + 1];
+    for (int i = a + t; i < e; i += 256) {
+      const float dx = p.xs[i] - Cx, dy = p.ys[i] - Cy;
+      const float q = sqrtf(dx * dx + dy * dy);
+      const float o = 1.f - q, o2 = o * o;
+      const float w = (q < 1.f) ? o2 * o2 * fmaf(4.f, q, 1.f) : 0.f;
+      sw += w;
+      swx = fmaf(w, dx, swx);
+      swy = fmaf(w, dy, swy);
+    }
+  }
+  sw = block_sum(sw, red);
+  swx = block_sum(swx, red);
+  swy = block_sum(swy, red);
+  if (t == 0) {
+    float *tc = const_cast<float *>(p.tcen) + 2 * (blockIdx.y * p.tiles_x + blockIdx.x);
+    tc[0] = (sw > 0.f) ? Cx + swx / sw : Cx;
+    tc[1] = (sw > 0.f) ? Cy + swy / sw : Cy;
+  }
 }
 
 }  // namespace

@@ -339,9 +339,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_mls_tc(KParams p, int d0, int D
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
 
-  // tile frame: centre at the pixel corner (u0 + 8, v0 + TH/2)
-  const float cxs = (float)((p.x0 + (u0 + 8) * p.sx - p.ctr_x) * p.inv_s);
-  const float cys = (float)((p.y0 + (v0 + TH / 2) * p.sy - p.ctr_y) * p.inv_s);
+  // moment frame of the tile: the weighted centroid of the points near its
+  // centre (from the prepass); the fit is solved in this frame
+  const int tile = (v0 >> 4) * p.tiles_x + (u0 >> 4);
+  const float cxs = p.tcen[2 * tile], cys = p.tcen[2 * tile + 1];
   const uint64_t limit = kWaitLimitNs;
   bool alive = true;
 
@@ -356,8 +357,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_mls_tc(KParams p, int d0, int D
     for (int a = 0; a < NACC; ++a) {
       const int q = a * 128 + t;
       const int u = u0 + (q & 15), v = v0 + (q >> 4);
-      dx[a] = (float)(((q & 15) + 0.5 - 8.0) * p.sx * p.inv_s);
-      dy[a] = (float)(((q >> 4) + 0.5 - 0.5 * TH) * p.sy * p.inv_s);
+      dx[a] = (float)((p.x0 + (u + 0.5) * p.sx - p.ctr_x) * p.inv_s - (double)cxs);
+      dy[a] = (float)((p.y0 + (v + 0.5) * p.sy - p.ctr_y) * p.inv_s - (double)cys);
       const size_t pi = (size_t)v * (p.tiles_x * 16) + u;
       if (WK == MLS_W_GAUSS)
         E[a] = kLog2e * (p.mstab[pi] - (dx[a] * dx[a] + dy[a] * dy[a]));
@@ -622,8 +623,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_mls_tc(KParams p, int d0, int D
     const int u = u0 + (q & 15), v = v0 + (q >> 4);
     const bool inside = (u < p.W) && (v < p.H);
     const size_t pi = (size_t)v * (p.tiles_x * 16) + u;
-    const float dxp = (float)(((q & 15) + 0.5 - 8.0) * p.sx * p.inv_s);
-    const float dyp = (float)(((q >> 4) + 0.5 - 0.5 * TH) * p.sy * p.inv_s);
+    const float dxp = (float)((p.x0 + (u + 0.5) * p.sx - p.ctr_x) * p.inv_s - (double)cxs);
+    const float dyp = (float)((p.y0 + (v + 0.5) * p.sy - p.ctr_y) * p.inv_s - (double)cys);
     const uint32_t tbase = tmem + a * 256 + ((uint32_t)(32 * (warp & 3)) << 16);
     const bool read = acc_ok && any_tile;   // warp-uniform
     float St[16];
@@ -646,12 +647,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mls_tc(KParams p, int d0, int D
     float z[K];
     int outcome = SOLVE_RECOMPUTE;
     const bool nosup = (count == 0);
-    if (!nosup && !handover) {
-      float Sp[15];
-      shift_moments<NM>(St, Sp, dxp, dyp);
-      outcome = solve_pixel_fp32<K>(Sp, z, p);
-      if (outcome != SOLVE_RECOMPUTE) to_tile_frame<K>(z, dxp, dyp);
-    }
+    if (!nosup && !handover) outcome = solve_pixel_fp32<K>(St, dxp, dyp, z, p);
     const bool done = !nosup && outcome != SOLVE_RECOMPUTE;
     const bool give = !nosup && outcome == SOLVE_RECOMPUTE;
     const size_t plane = (size_t)p.W * p.H;

@@ -12,6 +12,8 @@ from paper_1408_0677_gb300 import _abi, build
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 HEADER = os.path.join(ROOT, "include", "mls.h")
+HEADERS = sorted(os.path.join(ROOT, "include", f) for f in os.listdir(os.path.join(ROOT, "include"))
+                 if f.endswith(".h"))
 
 
 @pytest.fixture(scope="module")
@@ -21,14 +23,17 @@ def lib():
 
 
 def declared_functions():
-    text = open(HEADER).read()
-    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    return sorted(set(re.findall(r"\b(mls_[a-z_]+)\s*\(", text)))
+    names = set()
+    for hdr in HEADERS:
+        text = re.sub(r"/\*.*?\*/", "", open(hdr).read(), flags=re.S)
+        names |= set(re.findall(r"\b(mls_[a-z0-9_]+)\s*\(", text))
+    return sorted(names)
 
 
 def test_library_exports_every_declared_symbol(lib):
     names = declared_functions()
     assert "mls_create" in names and "mls_render" in names and "mls_bands" in names and "mls_destroy" in names
+    assert "mls_debug_wait_selftest" in names and "mls_debug_df_weight" in names
     out = subprocess.run(["nm", "-D", "--defined-only", _abi.library_path()], capture_output=True, text=True).stdout
     exported = set(re.findall(r"\bT (mls_\w+)", out))
     missing = [n for n in names if n not in exported]
@@ -103,6 +108,9 @@ def test_null_arguments(lib):
     assert lib.mls_bands(None, ctypes.byref(v), None, None, 0, None, 1, None) == _abi.MLS_E_INVAL
     assert lib.mls_sync(None, 1.0, None) == _abi.MLS_E_INVAL
     assert lib.mls_destroy(None) == _abi.MLS_OK
+    assert lib.mls_debug_df_weight(3, None, None, 1, None) == _abi.MLS_E_INVAL
+    assert lib.mls_debug_df_weight(0, None, None, 4, None) == _abi.MLS_E_INVAL
+    assert lib.mls_debug_df_weight(0, None, None, 0, None) == _abi.MLS_OK
 
 
 def test_injected_allocation_failure_returns_nomem(lib, monkeypatch):
