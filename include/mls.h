@@ -179,6 +179,42 @@ mls_status mls_bands(mls_handle *h, const mls_view *view, const void *field,
                      const double *levels, int32_t L, uint8_t *bands,
                      int32_t on_device, void *stream);
 
+/* Most levels (D * L) that mls_bands_noalloc accepts. */
+#define MLS_NOALLOC_MAX_LEVELS 4096
+
+/*
+ * Iso-band labels without any device allocation.  The paper has no
+ * counterpart: this serves callers that cannot allocate device memory, such
+ * as an application whose device memory belongs to its own pool allocator
+ * (a cudaMalloc here could fail or fragment that pool) or a frame loop that
+ * must not stall in cudaMalloc / cudaFree (both may synchronise the device).
+ * The labels are those of mls_bands: band = #{j : t_dj <= f_d}, 255 for NaN.
+ *
+ *   D, W, H     dimensions and raster size; D * L <= MLS_NOALLOC_MAX_LEVELS
+ *   field       device, D x H x W, float (field_fp64 = 0) or double (1)
+ *   levels      host, D x L doubles, ascending per dimension, finite
+ *   L           1 .. 254
+ *   bands       device, D x H x W bytes out
+ *   stream      CUDA stream of the work (NULL: the legacy default stream)
+ *
+ * The levels are kept in a fixed array of the library's device data
+ * (MLS_NOALLOC_MAX_LEVELS x 12 bytes = 48 KiB), which every device that
+ * loads the library holds until the process exits.  The first call on a
+ * device looks up that array's device address (loading the library's module
+ * on the device), so make the first call before any stream capture.  Every
+ * call on a device shares the array and leaves its levels there; calls whose
+ * work overlaps on the GPU race on it, so order them on one stream.  Nothing
+ * in the array needs to start at zero.  The host levels may be reused when
+ * the call returns; the labels are ready when the stream reaches them.
+ * Nothing is allocated: no cudaMalloc, cudaFree or allocating library call.
+ * Errors: MLS_E_INVAL (bad sizes, D * L above the maximum, NULL pointers,
+ * levels not ascending or not finite), MLS_E_UNSUPPORTED (device ordinal
+ * above 63), MLS_E_CUDA.
+ */
+mls_status mls_bands_noalloc(int32_t D, int32_t W, int32_t H, const void *field,
+                             int32_t field_fp64, const double *levels, int32_t L,
+                             uint8_t *bands, void *stream);
+
 /*
  * Wait for the handle's last stream with a host-side watchdog of
  * `timeout_s` seconds, then read the device error word and counters into

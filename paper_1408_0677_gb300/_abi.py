@@ -84,6 +84,9 @@ def load(path: str | None = None):
     lib.mls_sync.argtypes = [P, ctypes.c_double, ctypes.POINTER(MlsStats)]
     lib.mls_destroy.restype = ctypes.c_int
     lib.mls_destroy.argtypes = [P]
+    lib.mls_bands_noalloc.restype = ctypes.c_int
+    lib.mls_bands_noalloc.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, P, ctypes.c_int32, P,
+                                      ctypes.c_int32, P, P]
     # test hooks (include/mls_debug.h)
     lib.mls_debug_wait_selftest.restype = ctypes.c_int
     lib.mls_debug_wait_selftest.argtypes = [ctypes.c_int64, ctypes.POINTER(ctypes.c_int)]
@@ -131,6 +134,13 @@ def mls_bands(handle: int, view: MlsView, field_ptr: int, levels_ptr: int, L: in
               on_device: bool = True, stream: int = 0):
     _check(load().mls_bands(P(handle), ctypes.byref(view), P(field_ptr), P(levels_ptr or None), int(L),
                             P(bands_ptr), int(bool(on_device)), P(stream)), "mls_bands")
+
+
+def mls_bands_noalloc(D: int, W: int, H: int, field_ptr: int, field_fp64: bool, levels_ptr: int, L: int,
+                      bands_ptr: int, stream: int = 0):
+    """Iso-band labels into caller buffers, without any device allocation."""
+    _check(load().mls_bands_noalloc(int(D), int(W), int(H), P(field_ptr), int(bool(field_fp64)), P(levels_ptr),
+                                    int(L), P(bands_ptr), P(stream)), "mls_bands_noalloc")
 
 
 def mls_sync(handle: int, timeout_s: float = 60.0) -> MlsStats:
