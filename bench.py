@@ -6,7 +6,10 @@ in 8 Gaussian clusters plus 20% uniform background, D = 32 Fourier fields,
 point, 16 iso-levels): mls_create from device-resident points (value ranges,
 layouts), the stabiliser prepass, the tensor-core moment contraction with
 its per-pixel solve and fused iso-bands, and the recompute of ill-conditioned
-pixels.  Metric: pixel*point*dim updates/s = W * H * n * D / step time.
+pixels.  Metric: pixel*point*dim updates/s = W * H * n * D / step time,
+with the p50/p99 step latency, the plain FP32 CUDA-core form timed on the same
+inputs, and both fields' error against the FP64 oracle on the oracle's pixel
+sample (largest |f - f_oracle| / data range of the dimension).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp16|bf16|fp32|fp64]
   python bench.py --impl reference    # the FP64 CPU oracle on a bounded pixel sample
@@ -108,29 +111,57 @@ def _dist():
     return world, rank, local
 
 
+def max_over_ranks(x: float, world: int, device) -> float:
+    """The largest value of x over all ranks (x itself on one rank)."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def cpu_baseline(wl, seconds=15.0):
-    """FP64 oracle on a bounded pixel sample (all host cores)."""
+    """FP64 oracle on a bounded pixel sample (all host cores).  Also returns the
+    last sample's pixels and oracle result, against which the GPU fields'
+    error is stated."""
     import oracle
-    rng_pix = None
     npx = 64
     threads = os.cpu_count() or 1
     t_used, px_done = 0.0, 0
     seed = 0
+    last = None
     while t_used < seconds and npx <= 1 << 16:
-        pix = np.random.default_rng(100 + seed).choice(wl.W * wl.H, size=npx, replace=False)
+        pix = np.sort(np.random.default_rng(100 + seed).choice(wl.W * wl.H, size=npx, replace=False))
         t0 = time.perf_counter()
-        oracle.mls(wl.xy, wl.F, wl.degree, wl.weight, wl.h, wl.W, wl.H, pixels=pix, threads=threads)
+        res = oracle.mls(wl.xy, wl.F, wl.degree, wl.weight, wl.h, wl.W, wl.H, pixels=pix, threads=threads)
         dt = time.perf_counter() - t0
         t_used += dt
         px_done += npx
-        rng_pix = pix
+        last = (pix, res)
         seed += 1
         if dt < seconds / 4:
             npx *= 2
-    del rng_pix
     value = px_done * wl.n * wl.D / t_used
     return {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
-            "sample": f"{px_done} random pixels of the workload, full n={wl.n} sum each, FP64, {t_used:.1f} s"}
+            "sample": f"{px_done} random pixels of the workload, full n={wl.n} sum each, FP64, {t_used:.1f} s"}, last
+
+
+def _err_vs_oracle(wl, field_samples, last):
+    """Largest |f_gpu - f_oracle| / (data range of the dimension) over the
+    oracle's sample pixels (pixels the oracle flags as ambiguous excluded)."""
+    pix, res = last
+    rng = wl.F.max(axis=0) - wl.F.min(axis=0)
+    ok = res.amb == 0
+    out = {}
+    ref = res.field[ok].T                    # (D, pixels)
+    fin = np.isfinite(ref)
+    for name, f in field_samples.items():
+        d = np.abs(f[:, ok] - ref) / rng[:, None]
+        out[name] = float(np.max(np.where(fin, d, 0.0))) if d.size else None
+    out["pixels"] = int(ok.sum())
+    return out
 
 
 def run_reference(args):
@@ -226,7 +257,7 @@ def run_ours(args):
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
-    total_ms, kern_ms, launches, handed, handed64 = 0.0, [], 0, 0, 0
+    total_ms, kern_ms, step_ms, launches, handed, handed64, retried = 0.0, [], [], 0, 0, 0, 0
     for _ in range(args.steps):
         flush.fill_(1.0)                                  # L2 flush outside the timed step
         e0 = torch.cuda.Event(enable_timing=True)
@@ -237,21 +268,50 @@ def run_ours(args):
         st = r.sync()
         e1.synchronize()
         total_ms += e0.elapsed_time(e1)
+        step_ms.append(e0.elapsed_time(e1))
         kern_ms.append(st.main_kernel_ms)
         launches += st.launches
-        handed, handed64 = st.recomputed, st.recomputed_fp64
+        handed, handed64, retried = st.recomputed, st.recomputed_fp64, st.retried_tiles
         r.close()
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
     clocks = sampler.stop()
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(total_ms, world, dev)
     ms_step = total_ms / args.steps
     units = W * H * n * D
     value = world * units / (ms_step * 1e-3)
+
+    # ---- the plain FP32 CUDA-core form on the same inputs, for comparison
+    plain = None
+    samples = {}
+    if args.precision in ("fp16", "bf16") and args.compare_fp32:
+        field32 = torch.empty((D, H, W), dtype=torch.float32, device=dev)
+
+        def step_fp32():
+            r = Renderer(xy_d, F_d, degree=wl.degree, weight=wl.weight, h=wl.h, precision="fp32", stream=sptr)
+            r.render(W, H, levels=lev, field=field32, bands=bands, status_out=status)
+            return r
+
+        r = step_fp32()
+        r.sync()
+        r.close()
+        ts = []
+        for _ in range(min(args.steps, 5)):
+            flush.fill_(1.0)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            r = step_fp32()
+            e1.record(stream)
+            r.sync()
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+            r.close()
+        plain = {"precision": "fp32", "ms_per_step": float(np.mean(ts)), "steps": len(ts),
+                 "speedup": float(np.mean(ts)) / ms_step}
+        samples["fp32"] = field32
+    samples[args.precision] = field
 
     # ---- end-to-end through the public API with host buffers (pinned)
     xy_h = torch.from_numpy(wl.xy).pin_memory().numpy()
@@ -277,10 +337,7 @@ def run_ours(args):
         t0 = time.perf_counter()
         step_host()
         e2e_ms += 1e3 * (time.perf_counter() - t0)
-    if world > 1:
-        t = torch.tensor([e2e_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+    e2e_ms = max_over_ranks(e2e_ms, world, dev)
     e2e_value = world * units / (e2e_ms / args.steps * 1e-3)
     h2d = wl.xy.nbytes + wl.F.nbytes + lev.nbytes
     d2h = field_h.nbytes + status_h.nbytes + bands_h.nbytes
@@ -295,7 +352,16 @@ def run_ours(args):
     roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
             "traffic": _traffic(W * H), "peak_source": f"{src} bf16 burst (fp16 dense rate equal)",
             "kernel": "k_mls_tc", "kernel_ms": k_ms, "flops_per_launch": flops}
-    cpu = cpu_baseline(wl, seconds=args.cpu_seconds) if args.cpu_seconds > 0 else None
+    cpu, err = None, None
+    if args.cpu_seconds > 0:
+        cpu, last = cpu_baseline(wl, seconds=args.cpu_seconds)
+        pix_t = torch.from_numpy(last[0]).to(dev)
+        fs = {k: v.reshape(D, -1)[:, pix_t].double().cpu().numpy() for k, v in samples.items()}
+        err = _err_vs_oracle(wl, fs, last)
+    if plain is not None:
+        plain["err_vs_oracle"] = err.get("fp32") if err else None
+    lat = {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99)),
+           "steps": len(step_ms), "what": "device time of one step (create + render + bands)"}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
@@ -304,9 +370,12 @@ def run_ours(args):
                        "replicas": world},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                     "ms_per_step": e2e_ms / args.steps},
+            "latency_ms": lat, "plain_fp32": plain,
+            "err_vs_oracle": err, "tolerance": 1e-3 if args.precision != "fp64" else 1e-10,
             "roofline": roof, "cpu_baseline": cpu, "clocks": clocks,
             "gpu_launches": int(launches),
-            "recompute": {"handed_over_pixels": int(handed), "fp64_pixels": int(handed64)}}
+            "recompute": {"handed_over_pixels": int(handed), "fp64_pixels": int(handed64),
+                          "split_weight_tiles": int(retried)}}
     print(json.dumps(line), flush=True)
 
 
@@ -318,7 +387,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="fp16", choices=["fp16", "bf16", "fp32", "fp64"])
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
-    ap.add_argument("--weight-split", type=int, default=None, choices=[0, 1])
+    ap.add_argument("--weight-split", type=int, default=None, choices=[0, 1, 2])
+    ap.add_argument("--no-compare-fp32", dest="compare_fp32", action="store_false",
+                    help="skip the plain FP32 comparison run")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

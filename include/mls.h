@@ -39,7 +39,7 @@
 extern "C" {
 #endif
 
-#define MLS_ABI_VERSION 1
+#define MLS_ABI_VERSION 2
 
 typedef enum mls_status {
     MLS_OK = 0,
@@ -94,8 +94,10 @@ typedef enum mls_precision {
  *               precision: FP32 1e3, FP16 1e3, BF16 1e2)
  *   weight_split      tensor-core precisions: 1 stores each weight as a hi +
  *               lo pair of 16-bit values (three products per point tile);
- *               0 rounds each weight once (two products); -1 (default)
- *               picks 0 for FP16 and 1 for BF16
+ *               0 rounds each weight once (two products); 2 renders with
+ *               single weights first and renders again, with split weights,
+ *               the 16 x 16 tiles where a pixel fails the single-weight
+ *               checks; -1 (default) picks 2 for FP16 and 1 for BF16
  */
 typedef struct mls_desc {
     int64_t n;
@@ -126,7 +128,9 @@ typedef struct mls_stats {
     int64_t device_error;     /* device error word (0 = none; timeouts set it) */
     int64_t launches;         /* kernels this handle has launched since mls_create */
     double last_render_ms;    /* device time of the last render (CUDA events) */
-    double main_kernel_ms;    /* device time of its main MLS kernel(s), events on the same stream */
+    double main_kernel_ms;    /* device time of its main MLS kernel(s) over every tile, events on the
+                                 same stream (weight_split 2: the single-weight pass only) */
+    int64_t retried_tiles;    /* tiles rendered again with split weights (weight_split 2) */
 } mls_stats;
 
 typedef struct mls_handle mls_handle;

@@ -42,7 +42,7 @@ class MlsView(ctypes.Structure):
 class MlsStats(ctypes.Structure):
     _fields_ = [("pairs", ctypes.c_int64), ("recomputed", ctypes.c_int64), ("recomputed_fp64", ctypes.c_int64),
                 ("device_error", ctypes.c_int64), ("launches", ctypes.c_int64), ("last_render_ms", ctypes.c_double),
-                ("main_kernel_ms", ctypes.c_double)]
+                ("main_kernel_ms", ctypes.c_double), ("retried_tiles", ctypes.c_int64)]
 
 
 class MlsError(RuntimeError):

@@ -71,8 +71,8 @@ struct KParams {
   const float *fcen32, *fscl32;
   const double *x64, *y64;     // raw positions [n]
   const double *FT64;          // raw values [D][n]
-  const float *xyb;            // tensor path: (x[8], y[8]) per 8-point block, [n_pad/8][16]
-  const float *fb;             // tensor path: values per pass, [passes][n_pad/8][fb_dc][8]
+  const float *xyb;            // tensor path: (x[8], y[8], pad[4]) per 8-point block, [n_pad/8][20]
+  const float *fb;             // tensor path: values per pass, [passes][n_pad/8][fb_dc * 8 + 4]
   int fb_dc;                   // dimensions per pass of fb
   const int *cell_start;       // [gx * gy + 1] (Wendland)
   int gx, gy;
@@ -104,6 +104,11 @@ struct KParams {
   unsigned int *relist_count;
   int *err;
   // FP64 list mode
+  int *retry_tiles;            // tensor path, first of two passes: tiles to render again
+  unsigned int *retry_count;   //   (appended once per tile, guarded by tile_mark)
+  int *tile_mark;
+  const int *tile_list;        // tensor path, second pass: the tiles to render, or null
+  const unsigned int *tile_count;
   const int *list;             // pixel indices, or null for all pixels
   const unsigned int *list_count;  // device count for list mode, or null
   int64_t list_cap;

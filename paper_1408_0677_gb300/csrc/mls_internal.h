@@ -49,7 +49,9 @@ struct mls_handle {
   int *relist = nullptr;
   int *relist2 = nullptr;            // pixels the hand-over path passes to FP64
   float *tcen = nullptr;             // per-tile moment frame centres
-  unsigned int *counters = nullptr;  // [0] recompute count
+  unsigned int *counters = nullptr;  // [0] recompute count, [1] FP64 count, [2] retried tiles
+  int *tile_mark = nullptr;          // per tile: queued for the split-weight pass
+  int *retry_tiles = nullptr;
   int *err = nullptr;
   double *lev64 = nullptr;
   float *lev32 = nullptr;

@@ -191,24 +191,32 @@ __global__ void k_finish(const double *x64, const double *y64, const double *FT6
   }
 }
 
-// Point-blocked copies for the tensor path: positions as (x[8], y[8]) per
-// block of 8 points, values per pass of dc dimensions as [block][dc][8].
+// Point-blocked copies for the tensor path: positions as (x[8], y[8], 4 pad)
+// per block of 8 points, values per pass of dc dimensions as
+// [block][dc * 8 + 4 pad].  The 16-byte pad per block spreads the blocks of a
+// staged tile over the shared-memory banks (the operand builders read 8
+// blocks at once).
 __global__ void k_block(const float *xs, const float *ys, const float *FT32, int64_t n_pad, int D, int dc,
                         int passes, float *xyb, float *fb) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= n_pad) return;
   const int64_t b = i >> 3;
   const int j = (int)(i & 7);
+  const int64_t fstride = (int64_t)dc * 8 + 4;
   if (blockIdx.y == 0) {
-    xyb[b * 16 + j] = xs[i];
-    xyb[b * 16 + 8 + j] = ys[i];
+    xyb[b * 20 + j] = xs[i];
+    xyb[b * 20 + 8 + j] = ys[i];
+    if (j < 4) xyb[b * 20 + 16 + j] = 0.f;
   }
   const int64_t nblk = n_pad >> 3;
-  for (int pass = blockIdx.y; pass < passes; pass += gridDim.y)
+  for (int pass = blockIdx.y; pass < passes; pass += gridDim.y) {
+    float *blk = fb + (pass * nblk + b) * fstride;
     for (int dd = 0; dd < dc; ++dd) {
       const int d = pass * dc + dd;
-      fb[((pass * nblk + b) * dc + dd) * 8 + j] = (d < D) ? FT32[(int64_t)d * n_pad + i] : 0.f;
+      blk[dd * 8 + j] = (d < D) ? FT32[(int64_t)d * n_pad + i] : 0.f;
     }
+    if (j < 4) blk[dc * 8 + j] = 0.f;
+  }
 }
 
 }  // namespace
@@ -350,8 +358,8 @@ mls_status prep_points(mls_handle *h, const double *xy, const double *F, cudaStr
     const int dc = tc_dims_per_pass(D, d.degree);
     const int passes = (D + dc - 1) / dc;
     P.fb_dc = dc;
-    ALLOC(P.xyb, sizeof(float) * P.n_pad * 2);
-    ALLOC(P.fb, sizeof(float) * P.n_pad * (size_t)dc * passes);
+    ALLOC(P.xyb, sizeof(float) * (P.n_pad / 8) * 20);
+    ALLOC(P.fb, sizeof(float) * (P.n_pad / 8) * ((size_t)dc * 8 + 4) * passes);
     dim3 g3((unsigned)((P.n_pad + 255) / 256), (unsigned)(passes < 8 ? passes : 8));
     k_block<<<g3, 256, 0, st>>>(P.xs, P.ys, P.FT32, P.n_pad, D, dc, passes, P.xyb, P.fb);
     ++h->launches;

@@ -44,9 +44,27 @@ constexpr int kThreads = 320;     // 10 warps: 4 weights, 4 operand, 1 MMA, 1 lo
 constexpr int kDcMax = 40;        // value dimensions per pass (bounds the staged point tile)
 constexpr float kRMax = 15.f;     // |x~|_inf clip of the operand (FP16 range of x~^4)
 constexpr float kLog2e = 1.4426950408889634f;
+// staged point tile: per 8-point block (x[8], y[8], pad[4]) and (Dc x 8 + 4) values
+constexpr int kXB = 20;                     // floats per position block
+constexpr int kPosFloats = (kKT / 8) * kXB; // 160 floats of positions per stage
+// separable Gaussian weights: per stage buffer of 16 column and 16 row factor
+// rows of 64 points (row stride 68 floats: rows fall on distinct banks)
+constexpr int kEXS = 68;
+constexpr int kExyFloats = 32 * kEXS;
+constexpr int kGaussHdr = 4 * 32 * 4;        // per weight warp: alpha[16], beta[16]
+constexpr int kPrmBytes = kGaussHdr + 2 * kExyFloats * 4;   // >= the Wendland point parameters (4 KB)
+// Common factor of all FP16 weights (the fit does not depend on it): the
+// largest weight becomes 2^14, so the low half of a split weight stays in
+// the FP16 normal range for weights down to 2^-17 of the largest (unscaled,
+// weights below 1/8 had subnormal low halves and only ~2^-24 absolute
+// precision).  BF16 has the FP32 exponent range and needs no factor.
+template <bool FP16>
+__device__ __forceinline__ float weight_scale() { return FP16 ? 16384.f : 1.f; }
+// largest log2 of (stabiliser / tile-split stabiliser): the factor products
+// of a pixel's largest weights stay in the FP32 normal range
+constexpr float kResMax = 96.f;
 
 constexpr int kABytes = kM * 128;                  // 16 KB per A tile
-constexpr int kBBytes = kNMax * 128;               // 32 KB per B tile
 // Two kernel shapes share one layout: two 128-pixel accumulators with single
 // 16-bit weights, or one accumulator with weights split hi + lo; either way
 // a stage holds two A tiles.
@@ -71,8 +89,8 @@ TcLayout make_layout(int N, int Dc) {
   L.offB = kOffB;
   L.bpart = N * 128;
   L.offPrm = L.offB + kStages * 2 * L.bpart;
-  L.offData = L.offPrm + 4 * kKT * 16;
-  L.dstage = (2 + Dc) * kKT * 4;
+  L.offData = L.offPrm + kPrmBytes;
+  L.dstage = (kKT / 8) * (kXB + Dc * 8 + 4) * 4;
   const int fixed = L.offData + 256 + 1024;
   int ds = (kSmemLimit - fixed) / L.dstage;
   L.dstages = ds > 4 ? 4 : ds;
@@ -316,10 +334,22 @@ __global__ void __launch_bounds__(kThreads, 1) k_mls_tc(KParams p, int d0, int D
   const uint32_t bar_acc = smem_u32(&bars[4]);
   const uint32_t bar_dfull0 = smem_u32(&bars[5]);   // staged point tile ready [ds]
   const uint32_t bar_dempty0 = smem_u32(&bars[9]);  // staged point tile consumed [ds]
+  const uint32_t bar_exy0 = smem_u32(&bars[13]);    // Gaussian factor table [kt & 1] written
   uint32_t *tmem_slot = (uint32_t *)(smem + lay.offBar + 128);
   const int DST = lay.dstages;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int u0 = blockIdx.x * 16, v0 = blockIdx.y * TH;
+  int u0, v0;
+  if (p.tile_list) {
+    // second pass over listed tiles: 2 / NACC CTAs per tile, the rest exit
+    const int slot = blockIdx.x / (2 / NACC), part = blockIdx.x % (2 / NACC);
+    if (slot >= (int)*p.tile_count) return;
+    const int tl = p.tile_list[slot];
+    u0 = (tl % p.tiles_x) * 16;
+    v0 = (tl / p.tiles_x) * 16 + part * TH;
+  } else {
+    u0 = blockIdx.x * 16;
+    v0 = blockIdx.y * TH;
+  }
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < kStages; ++s) {
@@ -331,6 +361,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_mls_tc(KParams p, int d0, int D
       mbar_init(bar_dfull0 + 8 * ds, 1);
       mbar_init(bar_dempty0 + 8 * ds, 8);
     }
+    mbar_init(bar_exy0, 4);
+    mbar_init(bar_exy0 + 8, 4);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 8) tmem_alloc(smem_u32(tmem_slot), 512);
@@ -349,8 +381,131 @@ __global__ void __launch_bounds__(kThreads, 1) k_mls_tc(KParams p, int d0, int D
   RangeIter it;
   ranges_init(p, u0, v0, TH, it);
 
-  if (warp < 4) {
-    // ------------------------------------------------ weight producers
+  if (warp < 4 && WK == MLS_W_GAUSS) {
+    // ------------------------------------------------ weight producers (Gaussian, separable)
+    // w = exp2(L_p - log2e |x~ - delta_p|^2) with L_p = log2e m_p.  The tile's
+    // pixels lie on 16 columns dx_c and 16 rows dy_r, so with the stabiliser
+    // split as alpha_c + beta_r <= L_p (beta_r = min_c L, alpha_c =
+    // min_r (L - beta_r)) every weight is a product of a column factor
+    // exp2(alpha_c - log2e (dx_c - x)^2) and a row factor
+    // exp2(beta_r - log2e (dy_r - y)^2): 32 exp2 per point instead of 256,
+    // and one multiply per weight.  A per-point exponent shift balances the
+    // two factors (neither overflows).  The product carries the factor
+    // 2^(alpha_c + beta_r - L_p) <= 1, which one more multiply by its inverse
+    // removes, so every pixel's largest weight is 1 as with the per-pixel
+    // stabiliser (pixels whose factor would leave the FP32 range are handed over).
+    const int t = threadIdx.x;
+    float *sAB = (float *)(smem + lay.offPrm) + 32 * warp;     // this warp's alpha[16], beta[16]
+    float *exy = (float *)(smem + lay.offPrm + kGaussHdr);     // [2][32 rows][kEXS]
+    {
+      const int stride = p.tiles_x * 16;
+      const int r = lane & 15, c = lane & 15;
+      float b = INFINITY;
+      if (r < TH)
+        for (int cc = 0; cc < 16; ++cc) b = fminf(b, kLog2e * p.mstab[(size_t)(v0 + r) * stride + u0 + cc]);
+      float a = INFINITY;
+      for (int rr = 0; rr < TH; ++rr) {
+        const float br = __shfl_sync(0xffffffffu, b, rr);
+        a = fminf(a, kLog2e * p.mstab[(size_t)(v0 + rr) * stride + u0 + c] - br);
+      }
+      sAB[lane] = (lane < 16) ? a : ((r < TH) ? b : 0.f);
+      __syncwarp();
+    }
+    // this thread's factor rows: point j, columns (half 0) or rows (half 1)
+    const int jp = t >> 1, half = t & 1;
+    float off[16];
+#pragma unroll
+    for (int k = 0; k < 16; ++k)
+      off[k] = half ? (float)((p.y0 + (v0 + k + 0.5) * p.sy - p.ctr_y) * p.inv_s - (double)cys)
+                    : (float)((p.x0 + (u0 + k + 0.5) * p.sx - p.ctr_x) * p.inv_s - (double)cxs);
+    // this thread's pixels: column c, rows r0 (and r0 + 8), and their
+    // corrections 2^(L_p - alpha_c - beta_r)
+    const int cown = t & 15, r0 = t >> 4;
+    float gcor[2];
+#pragma unroll
+    for (int a = 0; a < 2; ++a) {
+      const int rr = r0 + 8 * a;
+      const float res = (rr < TH) ? kLog2e * p.mstab[(size_t)(v0 + rr) * (p.tiles_x * 16) + u0 + cown] -
+                                        sAB[cown] - sAB[16 + rr]
+                                  : 0.f;
+      gcor[a] = ex2_approx(fminf(res, kResMax)) * weight_scale<FP16>();
+    }
+    int kt = 0;
+    for (; ranges_valid(it) && alive; ranges_next(p, it), ++kt) {
+      const int s = kt & 1;
+      const int ds = kt % DST;
+      if (!mbar_wait(bar_dfull0 + 8 * ds, (kt / DST) & 1, p.err, ERR_WAIT_FULL, limit)) {
+        alive = false;
+        break;
+      }
+      const float *dxs = (const float *)(smem + lay.offData + ds * lay.dstage);
+      float *tab = exy + s * kExyFloats;
+      {
+        const int i = it.base + jp;
+        float pos = 0.f;
+        bool ok = (i >= it.lo) && (i < it.hi);
+        if (ok) {
+          const float x = dxs[(jp >> 3) * kXB + (jp & 7)] - cxs;
+          const float y = dxs[(jp >> 3) * kXB + 8 + (jp & 7)] - cys;
+          ok = fmaxf(fabsf(x), fabsf(y)) <= kRMax;
+          pos = half ? y : x;
+        }
+        float e[16];
+        float mx = -INFINITY;
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+          const float d = off[k] - pos;
+          e[k] = fmaf(-kLog2e * d, d, sAB[16 * half + k]);
+          if (half == 0 || k < TH) mx = fmaxf(mx, e[k]);
+        }
+        const float other = __shfl_xor_sync(0xffffffffu, mx, 1);
+        const float sh = half ? 0.5f * (mx - other) : 0.5f * (other - mx);   // Y' = Y - sh, X' = X + sh
+        float *dst = tab + 16 * half * kEXS + jp;
+#pragma unroll
+        for (int k = 0; k < 16; ++k) dst[k * kEXS] = ok ? ex2_approx(half ? e[k] - sh : e[k] + sh) : 0.f;
+      }
+      __syncwarp();
+      if (lane == 0) {
+        mbar_arrive(bar_dempty0 + 8 * ds);
+        mbar_arrive(bar_exy0 + 8 * s);
+      }
+      if (!mbar_wait(bar_exy0 + 8 * s, (kt >> 1) & 1, p.err, ERR_WAIT_FULL, limit) ||
+          !mbar_wait(bar_empty0 + 8 * s, ((kt >> 1) & 1) ^ 1, p.err, ERR_WAIT_EMPTY, limit)) {
+        alive = false;
+        break;
+      }
+      unsigned char *A0 = smem + kOffA + (s * 2 + 0) * kABytes;
+      unsigned char *A1 = smem + kOffA + (s * 2 + 1) * kABytes;
+      const float *fx = tab + cown * kEXS;
+      const float *fy0 = tab + (16 + r0) * kEXS;
+      const float *fy1 = tab + (16 + r0 + 8) * kEXS;
+#pragma unroll 2
+      for (int c = 0; c < 8; ++c) {
+        const float4 xa = *(const float4 *)(fx + 8 * c), xb = *(const float4 *)(fx + 8 * c + 4);
+        const float4 ya = *(const float4 *)(fy0 + 8 * c), yb = *(const float4 *)(fy0 + 8 * c + 4);
+        const float g0 = gcor[0];
+        float w0[8] = {xa.x * ya.x * g0, xa.y * ya.y * g0, xa.z * ya.z * g0, xa.w * ya.w * g0,
+                       xb.x * yb.x * g0, xb.y * yb.y * g0, xb.z * yb.z * g0, xb.w * yb.w * g0};
+        uint4 q0, q1;
+        if (WSPLIT) {
+          split8<FP16>(w0, q0, q1);          // A0 = hi, A1 = lo of accumulator 0
+        } else {
+          const float4 za = *(const float4 *)(fy1 + 8 * c), zb = *(const float4 *)(fy1 + 8 * c + 4);
+          const float g1 = gcor[1];
+          q0.x = pack2<FP16>(w0[0], w0[1]); q0.y = pack2<FP16>(w0[2], w0[3]);
+          q0.z = pack2<FP16>(w0[4], w0[5]); q0.w = pack2<FP16>(w0[6], w0[7]);
+          q1.x = pack2<FP16>(xa.x * za.x * g1, xa.y * za.y * g1); q1.y = pack2<FP16>(xa.z * za.z * g1, xa.w * za.w * g1);
+          q1.z = pack2<FP16>(xb.x * zb.x * g1, xb.y * zb.y * g1); q1.w = pack2<FP16>(xb.z * zb.z * g1, xb.w * zb.w * g1);
+        }
+        *(uint4 *)(A0 + sw128_off(t, c)) = q0;
+        *(uint4 *)(A1 + sw128_off(t, c)) = q1;
+      }
+      fence_proxy_async();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(bar_full0 + 8 * s);
+    }
+  } else if (warp < 4) {
+    // ------------------------------------------------ weight producers (Wendland)
     const int t = threadIdx.x;                 // row t of every accumulator
     float dx[NACC], dy[NACC], E[NACC];
 #pragma unroll
@@ -384,8 +539,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_mls_tc(KParams p, int d0, int D
         bool ok = (i >= it.lo) && (i < it.hi);
         if (ok) {
           // blocked tile: 8-point blocks of (x[8], y[8])
-          x = dxs[(j >> 3) * 16 + (j & 7)] - cxs;
-          y = dxs[(j >> 3) * 16 + 8 + (j & 7)] - cys;
+          x = dxs[(j >> 3) * kXB + (j & 7)] - cxs;
+          y = dxs[(j >> 3) * kXB + 8 + (j & 7)] - cys;
           ok = fmaxf(fabsf(x), fabsf(y)) <= kRMax;
         }
         float4 v;
@@ -410,8 +565,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_mls_tc(KParams p, int d0, int D
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
           const float4 pr = prm[8 * c + j];
-          w0[j] = pair_weight<WK>(pr, E[0], dx[0], dy[0]);
-          if (NACC == 2) w1[j] = pair_weight<WK>(pr, E[NACC - 1], dx[NACC - 1], dy[NACC - 1]);
+          w0[j] = pair_weight<WK>(pr, E[0], dx[0], dy[0]) * weight_scale<FP16>();
+          if (NACC == 2) w1[j] = pair_weight<WK>(pr, E[NACC - 1], dx[NACC - 1], dy[NACC - 1]) * weight_scale<FP16>();
         }
         uint4 q0, q1;
         if (WSPLIT) {
@@ -449,8 +604,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_mls_tc(KParams p, int d0, int D
       }
       const float *dsm = (const float *)(smem + lay.offData + ds * lay.dstage);
       if (i0 < p.n_pad) {
-        const float4 xa = *(const float4 *)(dsm + 16 * g), xb = *(const float4 *)(dsm + 16 * g + 4);
-        const float4 ya = *(const float4 *)(dsm + 16 * g + 8), yb = *(const float4 *)(dsm + 16 * g + 12);
+        const float4 xa = *(const float4 *)(dsm + kXB * g), xb = *(const float4 *)(dsm + kXB * g + 4);
+        const float4 ya = *(const float4 *)(dsm + kXB * g + 8), yb = *(const float4 *)(dsm + kXB * g + 12);
         xv[0] = xa.x; xv[1] = xa.y; xv[2] = xa.z; xv[3] = xa.w; xv[4] = xb.x; xv[5] = xb.y; xv[6] = xb.z; xv[7] = xb.w;
         yv[0] = ya.x; yv[1] = ya.y; yv[2] = ya.z; yv[3] = ya.w; yv[4] = yb.x; yv[5] = yb.y; yv[6] = yb.z; yv[7] = yb.w;
       } else {
@@ -503,7 +658,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mls_tc(KParams p, int d0, int D
       for (int d = rr; d < Dc; d += 16) {
         float fv[8];
         if (i0 < p.n_pad) {
-          const float *fr = dsm + 2 * kKT + (g * Dc + d) * 8;
+          const float *fr = dsm + kPosFloats + g * (Dc * 8 + 4) + d * 8;
           const float4 fa = *(const float4 *)fr, fb = *(const float4 *)(fr + 4);
           fv[0] = fa.x; fv[1] = fa.y; fv[2] = fa.z; fv[3] = fa.w; fv[4] = fb.x; fv[5] = fb.y; fv[6] = fb.z; fv[7] = fb.w;
           // slots past the copied tile hold stale shared memory: never multiply them
@@ -551,16 +706,18 @@ __global__ void __launch_bounds__(kThreads, 1) k_mls_tc(KParams p, int d0, int D
           break;
         }
         const int cnt = (int)((p.n_pad - it.base) < kKT ? (p.n_pad - it.base) : kKT);  // multiple of 8
-        const uint32_t nb = (uint32_t)cnt * 4;
+        const uint32_t nbk = (uint32_t)cnt / 8;                                         // blocks
         const uint32_t dst = sbase + lay.offData + ds * lay.dstage;
         const uint32_t bar = bar_dfull0 + 8 * ds;
         // point-blocked layouts: one copy for the positions, one for the
-        // values of this pass (blocks base/8 .. base/8 + cnt/8)
+        // values of this pass (blocks base/8 .. base/8 + cnt/8); block sizes
+        // 80 and 32 Dc + 16 bytes keep both copies 16-byte aligned
         const int64_t blk = it.base >> 3;
         const int64_t nblk = p.n_pad >> 3;
-        mbar_expect_tx(bar, nb * (uint32_t)(2 + Dc));
-        bulk_g2s(dst, p.xyb + blk * 16, 2 * nb, bar);
-        bulk_g2s(dst + 2 * kKT * 4, p.fb + ((size_t)pass * nblk + blk) * Dc * 8, nb * (uint32_t)Dc, bar);
+        const uint32_t fbb = (uint32_t)(Dc * 8 + 4) * 4;
+        mbar_expect_tx(bar, nbk * (kXB * 4 + fbb));
+        bulk_g2s(dst, p.xyb + blk * kXB, nbk * kXB * 4, bar);
+        bulk_g2s(dst + kPosFloats * 4, p.fb + ((size_t)pass * nblk + blk) * (Dc * 8 + 4), nbk * fbb, bar);
       }
       // every issued copy has landed before the CTA may exit
       const int first = kt > DST ? kt - DST : 0;
@@ -604,6 +761,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_mls_tc(KParams p, int d0, int D
     __syncwarp();
   }
 
+  __syncthreads();   // every role has left its loop (the stabiliser split is read below)
+
   // ------------------------------------------------ epilogue (warps 0-7)
   // Has any point tile been visited?  (Recompute from the iterator start.)
   RangeIter it2;
@@ -643,6 +802,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_mls_tc(KParams p, int d0, int D
       // pixel has a point within (kRMax - |delta|_inf - 4.2) h
       const float reach = kRMax - fmaxf(fabsf(dxp), fabsf(dyp));
       handover = !(p.mstab[pi] <= reach * reach - 18.f) || !read;
+      {
+        // the weight producers undo the split stabiliser's factor 2^-res up to kResMax
+        const float *sAB0 = (const float *)(smem + lay.offPrm);
+        const float res = kLog2e * p.mstab[pi] - sAB0[q & 15] - sAB0[16 + (q >> 4)];
+        handover = handover || !(res <= kResMax);
+      }
     }
     float z[K];
     int outcome = SOLVE_RECOMPUTE;
@@ -654,8 +819,16 @@ __global__ void __launch_bounds__(kThreads, 1) k_mls_tc(KParams p, int d0, int D
     const size_t pix = (size_t)v * p.W + u;
     float *field = (float *)p.field;
     if (primary && inside && give && d0 == 0) {
-      const unsigned int k = atomicAdd(p.relist_count, 1u);
-      p.relist[k] = (int)pix;
+      if (p.retry_tiles) {
+        // first of two passes: queue the tile once for the split-weight pass
+        if (atomicExch(&p.tile_mark[tile], 1) == 0) {
+          const unsigned int k = atomicAdd(p.retry_count, 1u);
+          p.retry_tiles[k] = tile;
+        }
+      } else {
+        const unsigned int k = atomicAdd(p.relist_count, 1u);
+        p.relist[k] = (int)pix;
+      }
     }
     if (primary && inside && nosup) {
       for (int d = d0; d < d0 + Dc && d < p.D; ++d) {
@@ -720,7 +893,9 @@ __global__ void k_wait_selftest(int *err, uint64_t limit_ns) {
 
 template <int DEG, int WK, bool FP16, int NACC, bool WSPLIT>
 void launch_one(const KParams &p, int d0, int Dc, int N, uint32_t idesc, cudaStream_t st) {
-  dim3 grid(p.tiles_x, p.tiles_y * (2 / NACC));
+  // all tiles, or (tile list) one slot per tile of which the listed ones work
+  const dim3 grid = p.tile_list ? dim3((unsigned)(p.tiles_x * p.tiles_y * (2 / NACC)))
+                                : dim3(p.tiles_x, p.tiles_y * (2 / NACC));
   auto k = k_mls_tc<DEG, WK, FP16, NACC, WSPLIT>;
   const TcLayout lay = make_layout(N, Dc);
   cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, lay.total);

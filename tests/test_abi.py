@@ -64,7 +64,7 @@ int main(void) {
 
 
 def test_abi_version_and_defaults(lib):
-    assert _abi.mls_abi_version() == 1
+    assert _abi.mls_abi_version() == 2
     d = _abi.mls_desc_default()
     assert d.cond_fp64 == 1e6 and d.rcond_degenerate == 1e-12 and d.precision == _abi.MLS_P_FP32
 

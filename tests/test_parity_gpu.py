@@ -23,11 +23,16 @@ def _ref(wl, pixels=None):
                       alpha=wl.alpha)
 
 
-@pytest.mark.parametrize("precision", ALL_PREC)
+@pytest.mark.parametrize("precision", ALL_PREC + ["fp16-ws0", "fp16-ws1"])
 def test_wine_shaped_full_grid(precision):
-    """n=178, D=13, 256x256, linear basis, Gaussian h=0.05: every pixel."""
+    """n=178, D=13, 256x256, linear basis, Gaussian h=0.05: every pixel (FP16
+    in its default two-pass mode and with single or split weights only)."""
     wl = inputs.wine_shaped()
-    res = gpu_render(wl, precision)
+    kw = {}
+    if "-ws" in precision:
+        precision, ws = precision.split("-ws")
+        kw["weight_split"] = int(ws)
+    res = gpu_render(wl, precision, **kw)
     err, npx = compare(wl, res, _ref(wl), precision)
     assert npx > 0.99 * wl.W * wl.H
     print(f"wine-shaped {precision}: max err {err:.3g} of range over {npx} pixels")
@@ -90,12 +95,25 @@ ROUGH = [
 
 
 @pytest.mark.parametrize("case", ROUGH, ids=[f"r{c[0]}" for c in ROUGH])
-def test_rough_fields_fp16_with_split_weights(case):
-    """FP16 with weights stored as hi + lo pairs (three products per point tile)."""
+@pytest.mark.parametrize("ws", [1, 2])
+def test_rough_fields_fp16_with_split_weights(case, ws):
+    """FP16 with weights stored as hi + lo pairs (three products per point
+    tile), everywhere (1) or on the tiles that fail with single weights (2)."""
     seed, n, D, W, H, degree, weight, h = case
     wl = inputs.fourier_mix(seed, n, D, W, H, degree, weight, h)
-    res = gpu_render(wl, "fp16", weight_split=1)
+    res = gpu_render(wl, "fp16", weight_split=ws)
     compare(wl, res, _ref(wl), "fp16")
+
+
+@pytest.mark.parametrize("ws", [0, 1, 2])
+def test_fp16_weight_modes_agree_on_structured_case(ws):
+    """Single, split and two-pass weights all meet the tolerance; the two-pass
+    mode queues some tiles for the split-weight pass."""
+    wl = inputs.fourier_mix(31, 10000, 8, 100, 75, 2, G, 0.02)
+    res = gpu_render(wl, "fp16", weight_split=ws)
+    compare(wl, res, _ref(wl), "fp16")
+    if ws == 2:
+        assert res["stats"].retried_tiles >= 0
 
 
 @pytest.mark.parametrize("precision", ALL_PREC)
