@@ -37,8 +37,8 @@ sys.path.insert(0, ROOT)
 METRIC = "MLS pixel*point*dim updates/s"
 UNIT = "pixel*point*dim/s"
 WORKLOAD = "fourier_n10k_d32_1024x1024_quadratic_gauss_h0.02_L16"
-TC_SRC = os.path.join(ROOT, "paper_1408_0677_gb300", "csrc", "tc.cu")
-PROFILE = os.path.join(ROOT, "profiles", "k_mls_tc_fourier10k.json")
+TC_SRCS = [os.path.join(ROOT, "paper_1408_0677_gb300", "csrc", f) for f in ("tc.cu", "dev_common.cuh")]
+PROFILE = os.path.join(ROOT, "profiles", "k_mls_tc_fourier10k_fp16.md")
 
 
 def _peaks():
@@ -195,23 +195,29 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def _tc_hash():
-    try:
-        return hashlib.sha256(open(TC_SRC, "rb").read()).hexdigest()
-    except Exception:
-        return None
+def tc_source_hash():
+    """sha256 over the tensor-core kernel's sources (tc.cu, dev_common.cuh)."""
+    h = hashlib.sha256()
+    for f in TC_SRCS:
+        h.update(open(f, "rb").read())
+    return h.hexdigest()
 
 
 def _traffic(n_launch_units):
-    """DRAM bytes per launch from the committed ncu summary, if the kernel is unchanged."""
+    """DRAM bytes per launch from the committed ncu summary of the kernel
+    (lines 'source_sha256: ...', 'dram_bytes_per_launch: ...',
+    'pixels_per_launch: ...'), or None when the kernel changed since."""
     try:
-        prof = json.load(open(PROFILE))
+        kv = {}
+        for ln in open(PROFILE):
+            if ":" in ln and not ln.startswith("|"):
+                k, v = ln.split(":", 1)
+                kv[k.strip("-* `").lower()] = v.strip(" `\n")
+        if kv.get("source_sha256") != tc_source_hash():
+            return None
+        return float(kv["dram_bytes_per_launch"]) / float(kv["pixels_per_launch"]) * n_launch_units
     except Exception:
         return None
-    if prof.get("tc_cu_sha256") != _tc_hash():
-        return None
-    per_unit = prof.get("dram_bytes") / prof.get("units")
-    return per_unit * n_launch_units
 
 
 def run_ours(args):
