@@ -29,6 +29,13 @@ __device__ __forceinline__ uint64_t globaltimer_ns() {
 // Every bounded spin gives up after this long (the host watchdog is longer).
 constexpr uint64_t kWaitLimitNs = 2000000000ull;  // 2 s
 
+// Wendland support counts (prepass): bit kCntBoundary marks a pixel with a
+// point whose squared distance (units of the radius) lies within
+// kCntEdgeTol of 1, where FP32 and FP64 may count it differently.
+constexpr int kCntBoundary = 1 << 30;
+constexpr int kCntMask = kCntBoundary - 1;
+constexpr float kCntEdgeTol = 4e-6f;
+
 // Monomials of degree <= 4 in (x, y), the entries of the moment matrix:
 // 0:1 1:x 2:y 3:xx 4:xy 5:yy 6:xxx 7:xxy 8:xyy 9:yyy 10:xxxx 11:xxxy 12:xxyy 13:xyyy 14:yyyy
 // Basis terms b_a (a < 6): 1, x, y, xx, xy, yy.  M_ab = S[kMIdx[a][b]].
@@ -400,6 +407,44 @@ __device__ __forceinline__ int solve_pixel_fp32(const float *S, float dx, float 
   for (int a = 0; a < K; ++a) lambda = fmaf(fabsf(z[a]), sqrtf(M[0][0] * M[a][a]), lambda);
   if (!(lambda <= p.lambda_max)) return SOLVE_RECOMPUTE;
   return SOLVE_OK;
+}
+
+// Degree policy by support count (Wendland), then the FP32 solve: the highest
+// degree whose n_terms fits the count, using the leading block of the same
+// moments; z is zero past that degree's terms.  Returns the solve outcome and
+// the degree in *deg (the count is exact unless the boundary flag is set).
+template <int K>
+__device__ __forceinline__ int solve_by_count(int count, const float *S, float dx, float dy, float (&z)[K],
+                                              const KParams &p, int *deg) {
+#pragma unroll
+  for (int a = 0; a < K; ++a) z[a] = 0.f;
+  if (count >= K) {
+    *deg = (K == 6) ? 2 : (K == 3) ? 1 : 0;
+    return solve_pixel_fp32<K>(S, dx, dy, z, p);
+  }
+  if (K == 6 && count >= 3) {
+    float z3[3];
+    *deg = 1;
+    const int o = solve_pixel_fp32<3>(S, dx, dy, z3, p);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) z[a] = z3[a];
+    return o;
+  }
+  float z1[1];
+  *deg = 0;
+  const int o = solve_pixel_fp32<1>(S, dx, dy, z1, p);
+  z[0] = z1[0];
+  return o;
+}
+
+// Whether a boundary-flagged count could cross a degree threshold (count
+// within one of n_terms for some degree <= DEG): such pixels go to the FP64
+// definition.
+template <int K>
+__device__ __forceinline__ bool count_uncertain(int cflag) {
+  if (!(cflag & kCntBoundary)) return false;
+  const int c = cflag & kCntMask;
+  return (c >= 0 && c <= 2) || (K >= 3 && c >= 2 && c <= 4) || (K >= 6 && c >= 5 && c <= 7);
 }
 
 }  // namespace mlsk

@@ -65,7 +65,8 @@ __global__ __launch_bounds__(128) void k_mls_f32(KParams p) {
   const float dpy = (float)((p.y0 + (v + 0.5) * p.sy - p.ctr_y) * p.inv_s - (double)cys);
   const size_t pstride = (size_t)p.tiles_x * 16;
   const float m = (WK == MLS_W_WENDLAND) ? 0.f : p.mstab[(size_t)v * pstride + u];
-  const int count = (WK == MLS_W_WENDLAND) ? p.cnt[(size_t)v * pstride + u] : (int)(p.n < (1 << 30) ? p.n : (1 << 30));
+  const int cflag = (WK == MLS_W_WENDLAND) ? p.cnt[(size_t)v * pstride + u] : 0;
+  const int count = (WK == MLS_W_WENDLAND) ? (cflag & kCntMask) : (int)(p.n < (1 << 30) ? p.n : (1 << 30));
   const float alpha = (float)p.alpha;
   // point ranges: all points, or the cell rows overlapping the block's pixels +- h
   int nr = 1, cx0 = 0, cx1 = 0, cy0 = 0;
@@ -170,7 +171,8 @@ __global__ __launch_bounds__(128) void k_mls_f32(KParams p) {
       }
       continue;
     }
-    if (count == 0) {
+    const bool uncertain = (WK == MLS_W_WENDLAND) && count_uncertain<K>(cflag);
+    if (count == 0 && !uncertain) {
       st = MLS_ST_NO_SUPPORT;
 #pragma unroll
       for (int dd = 0; dd < DC; ++dd) {
@@ -183,9 +185,10 @@ __global__ __launch_bounds__(128) void k_mls_f32(KParams p) {
       continue;
     }
     int outcome = SOLVE_RECOMPUTE;
-    // pixels whose support count is near a degree threshold go to FP64,
-    // which applies the count rule in the same precision as the definition
-    if (!(WK == MLS_W_WENDLAND && count <= K + 2)) outcome = solve_pixel_fp32<K>(S, dpx, dpy, z, p);
+    int degu = DEG;
+    // the count rule of the degree policy; pixels whose count could differ
+    // from the FP64 count at a degree threshold go to the FP64 path
+    if (!uncertain) outcome = solve_by_count<K>(count, S, dpx, dpy, z, p, &degu);
     if (outcome == SOLVE_RECOMPUTE) {
       write = false;
       if (d0 == 0) {
@@ -194,7 +197,7 @@ __global__ __launch_bounds__(128) void k_mls_f32(KParams p) {
       }
       handed_over = true;
     } else {
-      st = (uint8_t)(DEG | (outcome == SOLVE_FP64 ? MLS_ST_FP64_SOLVE : 0));
+      st = (uint8_t)(degu | (outcome == SOLVE_FP64 ? MLS_ST_FP64_SOLVE : 0) | (degu < DEG ? MLS_ST_DEGRADED : 0));
     }
     if (write) {
 #pragma unroll

@@ -10,7 +10,9 @@
 // the tile is <= B can be nearest to one of its pixels.
 //
 // Wendland weight: the number of points within the support radius of each
-// pixel, from the cells of the uniform grid that overlap the tile.
+// pixel, from the cells of the uniform grid that overlap the tile, with a
+// flag (kCntBoundary) when a point lies so close to the support boundary that
+// FP32 and FP64 could count it differently.
 //
 // Both also give each tile the frame its moments are accumulated in: the
 // weighted centroid of the points around the tile centre (Gaussian weights of
@@ -147,6 +149,7 @@ __global__ __launch_bounds__(256) void k_prepass_count(KParams p) {
   cell_range(fmin(xlo, xhi), fmax(xlo, xhi), p.h, p.gx0, inv_cell, p.gx, cx0, cx1);
   cell_range(fmin(ylo, yhi), fmax(ylo, yhi), p.h, p.gy0, inv_cell, p.gy, cy0, cy1);
   int count = 0;
+  bool edge = false;
   for (int cyy = cy0; cyy <= cy1 && cx0 <= cx1; ++cyy) {
     const int a = p.cell_start[cyy * p.gx + cx0];
     const int e = p.cell_start[cyy * p.gx + cx1 + 1];
@@ -160,12 +163,14 @@ __global__ __launch_bounds__(256) void k_prepass_count(KParams p) {
       const int c = min(256, e - base);
       for (int k = 0; k < c; ++k) {
         const float dx = cx[k] - px, dy = cy[k] - py;
-        count += (dx * dx + dy * dy < 1.f) ? 1 : 0;
+        const float q2 = dx * dx + dy * dy;
+        count += (q2 < 1.f) ? 1 : 0;
+        edge = edge || fabsf(q2 - 1.f) < mlsk::kCntEdgeTol;
       }
     }
   }
   const int stride = p.tiles_x * 16;
-  const_cast<int *>(p.cnt)[(size_t)v * stride + u] = count;
+  const_cast<int *>(p.cnt)[(size_t)v * stride + u] = count | (edge ? mlsk::kCntBoundary : 0);
 
   // frame of the tile: Wendland-weighted centroid around its centre
   __shared__ float red[8];

@@ -794,8 +794,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_mls_tc(KParams p, int d0, int D
     int count;
     bool handover = false;
     if (WK == MLS_W_WENDLAND) {
-      count = p.cnt[pi];
-      handover = (count > 0) && (count <= K + 2);
+      const int cflag = p.cnt[pi];
+      count = cflag & kCntMask;
+      handover = count_uncertain<K>(cflag);
     } else {
       count = (int)(p.n < (1 << 30) ? p.n : (1 << 30));
       // clipping |x~|_inf <= kRMax is exact in 16-bit arithmetic only when the
@@ -811,8 +812,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_mls_tc(KParams p, int d0, int D
     }
     float z[K];
     int outcome = SOLVE_RECOMPUTE;
-    const bool nosup = (count == 0);
-    if (!nosup && !handover) outcome = solve_pixel_fp32<K>(St, dxp, dyp, z, p);
+    int degu = DEG;
+    const bool nosup = (count == 0) && !handover;
+    if (!nosup && !handover) outcome = solve_by_count<K>(count, St, dxp, dyp, z, p, &degu);
     const bool done = !nosup && outcome != SOLVE_RECOMPUTE;
     const bool give = !nosup && outcome == SOLVE_RECOMPUTE;
     const size_t plane = (size_t)p.W * p.H;
@@ -868,7 +870,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_mls_tc(KParams p, int d0, int D
     }
     if (primary && inside && p.status && d0 == 0 && !give)
       p.status[pix] = nosup ? (uint8_t)MLS_ST_NO_SUPPORT
-                            : (uint8_t)(DEG | (outcome == SOLVE_FP64 ? MLS_ST_FP64_SOLVE : 0));
+                            : (uint8_t)(degu | (outcome == SOLVE_FP64 ? MLS_ST_FP64_SOLVE : 0) |
+                                        (degu < DEG ? MLS_ST_DEGRADED : 0));
   }
   tc_fence_before();
   __syncthreads();
