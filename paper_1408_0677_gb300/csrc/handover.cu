@@ -13,9 +13,9 @@
 //          of the pixel-centred, h-scaled basis and the support count; the
 //          degree policy is decided on these as the FP64 definition does
 //          (equilibrated factorisation, rcond_1 threshold, support count);
-//   solve  (FP64, the warp's lanes sharing the work): the moments are moved
-//          to the centroid frame, where the normal matrix is factorised and
-//          z = M_c^{-1} b_c(p) is formed;
+//   solve  (FP64, one lane per pixel for a chunk of 32 pixels): the moments
+//          are moved to the centroid frame, where the normal matrix is
+//          factorised and z = M_c^{-1} b_c(p) is formed;
 //   pass 2 (double-float): the value is sum_i phi_i f_i with the MLS shape
 //          functions phi_i = w_i z . b_c(x_i) -- equal to z . R_c -- so each
 //          (point, dimension) pair costs one multiply-add; the lanes hold one
@@ -36,7 +36,7 @@ namespace {
 
 using namespace mlsk;
 
-constexpr int kWarps = 8;               // warps per block, one pixel each
+constexpr int kWarps = 4;               // warps per block (each owns chunks of 32 pixels)
 constexpr int kRing = 64;               // ring of compacted near points per warp
 constexpr int kDL = 2;                  // value dimensions per lane per sweep
 constexpr float kCut = 40.f;            // Gaussian pairs with (r^2 - m)/h^2 above: weight < e^-40
@@ -175,7 +175,9 @@ __device__ __forceinline__ int for_near(const KParams &p, const Ranges &R, float
 }
 
 // ---------------------------------------------------------------------------
-// FP64 factorisation shared by the warp.
+// FP64 degree policy and centroid-frame solve, one lane per pixel (GB300's
+// FP64 units are few: running the policy once per lane for 32 pixels instead
+// of redundantly on every lane of a warp cuts its FP64 instructions 32-fold).
 
 // 1/d for a positive normal d: FP32 seed and two Newton steps (each doubles
 // the number of correct bits: 2^-23 -> 2^-46 -> FP64 rounding).
@@ -187,22 +189,19 @@ __device__ __forceinline__ double rcp64(double d) {
 }
 
 // Equilibrated LDL^T factorisation of the K x K moment matrix S[midx(a, b)]
-// and rcond_1 = 1 / (|Me|_1 |Me^-1|_1) of the equilibrated matrix Me
-// (columns of the inverse: lane c < K forms column c).  Returns 0 when a
-// diagonal entry or a pivot is not positive.  L (unit lower), dinv (inverse
-// pivots) and sd (equilibration 1/sqrt(M_aa)) receive the factorisation.
+// and rcond_1 = 1 / (|Me|_1 |Me^-1|_1) of the equilibrated matrix Me.
+// Returns 0 when a diagonal entry or a pivot is not positive.  L (unit
+// lower), dinv (inverse pivots) and sd (equilibration 1/sqrt(M_aa)) receive
+// the factorisation.
 template <int K>
-__device__ double ldl_rcond(const double (&S)[15], int lane, double (&L)[6][6], double (&dinv)[6],
-                            double (&sd)[6]) {
+__device__ double ldl_rcond(const double (&S)[15], double (&L)[6][6], double (&dinv)[6], double (&sd)[6]) {
   double Me[K][K];
-  bool ok = true;
 #pragma unroll
   for (int a = 0; a < K; ++a) {
     const double d = S[midx(a, a)];
-    ok = ok && (d > 0.0);
-    sd[a] = ok ? rsqrt(d) : 0.0;
+    if (!(d > 0.0)) return 0.0;
+    sd[a] = rsqrt(d);
   }
-  if (!ok) return 0.0;
 #pragma unroll
   for (int a = 0; a < K; ++a)
 #pragma unroll
@@ -226,12 +225,13 @@ __device__ double ldl_rcond(const double (&S)[15], int lane, double (&L)[6][6], 
       L[i][j] = v * dinv[j];
     }
   }
-  // column `lane` of Me^-1 and of Me
+  // 1-norms of Me and of its inverse (columns by forward / back substitution)
   double nI = 0.0, nA = 0.0;
-  if (lane < K) {
+#pragma unroll
+  for (int c = 0; c < K; ++c) {
     double col[K];
 #pragma unroll
-    for (int a = 0; a < K; ++a) col[a] = (a == lane) ? 1.0 : 0.0;
+    for (int a = 0; a < K; ++a) col[a] = (a == c) ? 1.0 : 0.0;
 #pragma unroll
     for (int i = 0; i < K; ++i)
 #pragma unroll
@@ -242,19 +242,14 @@ __device__ double ldl_rcond(const double (&S)[15], int lane, double (&L)[6][6], 
     for (int i = K - 1; i >= 0; --i)
 #pragma unroll
       for (int t = i + 1; t < K; ++t) col[i] -= L[t][i] * col[t];
+    double si = 0.0, sa = 0.0;
 #pragma unroll
     for (int a = 0; a < K; ++a) {
-      nI += fabs(col[a]);
-      double me = 0.0;
-#pragma unroll
-      for (int c = 0; c < K; ++c) me = (c == lane) ? Me[a][c] : me;
-      nA += fabs(me);
+      si += fabs(col[a]);
+      sa += fabs(Me[a][c]);
     }
-  }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    nI = fmax(nI, __shfl_xor_sync(0xffffffffu, nI, o));
-    nA = fmax(nA, __shfl_xor_sync(0xffffffffu, nA, o));
+    nI = fmax(nI, si);
+    nA = fmax(nA, sa);
   }
   return 1.0 / (nA * nI);
 }
@@ -280,31 +275,33 @@ __device__ __forceinline__ void ldl_solve(const double (&L)[6][6], const double 
 }
 
 // Moments of the frame centred on (cx, cy) and scaled by isg, from the
-// pixel-frame moments (binomial expansion of (x - cx)^bx (y - cy)^by): lane
-// j < NM forms moment j from the warp's copy of the pixel-frame moments in
-// shared memory, then every lane gathers them.
+// pixel-frame moments: binomial expansion of (x - cx)^bx (y - cy)^by.
 template <int NM>
-__device__ __forceinline__ void centroid_moments(const double *sS, double cx, double cy, double isg, int lane,
+__device__ __forceinline__ void centroid_moments(const double (&S)[15], double cx, double cy, double isg,
                                                  double (&Sc)[15]) {
-  double mine = 0.0;
-  if (lane < NM) {
-    const int bx = mono_ex(lane), by = mono_ey(lane);
-    double pcx[5], pcy[5];
-    pcx[0] = pcy[0] = 1.0;
+  double pcx[5], pcy[5], ps[5];
+  pcx[0] = pcy[0] = ps[0] = 1.0;
 #pragma unroll
-    for (int e = 1; e < 5; ++e) {
-      pcx[e] = pcx[e - 1] * -cx;
-      pcy[e] = pcy[e - 1] * -cy;
-    }
-    for (int jx = 0; jx <= bx; ++jx)
-      for (int jy = 0; jy <= by; ++jy)
-        mine += (double)(binom(bx, jx) * binom(by, jy)) * pcx[bx - jx] * pcy[by - jy] * sS[mono_index(jx, jy)];
-    double sc = 1.0;
-    for (int e = 0; e < bx + by; ++e) sc *= isg;
-    mine *= sc;
+  for (int e = 1; e < 5; ++e) {
+    pcx[e] = pcx[e - 1] * -cx;
+    pcy[e] = pcy[e - 1] * -cy;
+    ps[e] = ps[e - 1] * isg;
   }
 #pragma unroll
-  for (int j = 0; j < 15; ++j) Sc[j] = (j < NM) ? __shfl_sync(0xffffffffu, mine, j) : 0.0;
+  for (int j = 0; j < 15; ++j) {
+    double acc = 0.0;
+    if (j < NM) {
+      const int bx = mono_ex(j), by = mono_ey(j);
+#pragma unroll
+      for (int jx = 0; jx <= 4; ++jx)
+#pragma unroll
+        for (int jy = 0; jy <= 4; ++jy)
+          if (jx <= bx && jy <= by)
+            acc += (double)(binom(bx, jx) * binom(by, jy)) * pcx[bx - jx] * pcy[by - jy] * S[mono_index(jx, jy)];
+      acc *= ps[bx + by];
+    }
+    Sc[j] = acc;
+  }
 }
 
 // z = M_c^-1 b_c(pixel) in the frame of the weighted centroid (degree of K
@@ -312,8 +309,7 @@ __device__ __forceinline__ void centroid_moments(const double *sS, double cx, do
 // and y; 1/sigma).  Returns false when the centroid frame is degenerate or
 // still ill conditioned.
 template <int K>
-__device__ bool centroid_solve(const double (&Sd)[15], const double *sS, int lane, double (&z)[6],
-                               float (&fr)[5]) {
+__device__ bool centroid_solve(const double (&Sd)[15], double (&z)[6], float (&fr)[5]) {
   constexpr int DEGK = K == 6 ? 2 : 1;
   const double cx0 = Sd[1] / Sd[0], cy0 = Sd[2] / Sd[0];
   const double var = (Sd[3] + Sd[5]) / Sd[0] - cx0 * cx0 - cy0 * cy0;
@@ -326,9 +322,9 @@ __device__ bool centroid_solve(const double (&Sd)[15], const double *sS, int lan
   const double cx = (double)fr[0] + (double)fr[1], cy = (double)fr[2] + (double)fr[3];
   const double isg = (double)fr[4];
   double Sc[15];
-  centroid_moments<n_moments(DEGK)>(sS, cx, cy, isg, lane, Sc);
+  centroid_moments<n_moments(DEGK)>(Sd, cx, cy, isg, Sc);
   double L[6][6], dinv[6], sd[6];
-  const double rcc = ldl_rcond<K>(Sc, lane, L, dinv, sd);
+  const double rcc = ldl_rcond<K>(Sc, L, dinv, sd);
   if (!(rcc > 1.0 / kKappaCentroid)) return false;
   const double ex = -cx * isg, ey = -cy * isg;
   double b[6] = {1.0, ex, ey, ex * ex, ex * ey, ey * ey};
@@ -343,53 +339,63 @@ __device__ bool centroid_solve(const double (&Sd)[15], const double *sS, int lan
 // Returns the degree used (-1: no degree qualifies); *bad is set when the
 // pixel needs the FP64 kernel.
 template <int DEG>
-__device__ int pixel_policy(const double (&Sd)[15], const double *sS, long long count, double rcond_min, int lane,
-                            double (&z)[6], float (&fr)[5], bool *bad) {
+__device__ int pixel_policy(const double (&Sd)[15], long long count, double rcond_min, double (&z)[6],
+                            float (&fr)[5], bool *bad) {
   double L[6][6], dinv[6], sd[6];
   int used = -1;
-  if (DEG >= 2 && count >= 6 && ldl_rcond<6>(Sd, lane, L, dinv, sd) >= rcond_min) used = 2;
-  else if (DEG >= 1 && count >= 3 && ldl_rcond<3>(Sd, lane, L, dinv, sd) >= rcond_min) used = 1;
+  if (DEG >= 2 && count >= 6 && ldl_rcond<6>(Sd, L, dinv, sd) >= rcond_min) used = 2;
+  else if (DEG >= 1 && count >= 3 && ldl_rcond<3>(Sd, L, dinv, sd) >= rcond_min) used = 1;
   else if (count >= 1 && Sd[0] > 0.0) used = 0;
   for (int a = 0; a < 6; ++a) z[a] = 0.0;
   fr[0] = fr[1] = fr[2] = fr[3] = 0.f;
   fr[4] = 1.f;
   *bad = false;
   if (used == 0) z[0] = 1.0 / Sd[0];
-  else if (used == 1) *bad = !centroid_solve<3>(Sd, sS, lane, z, fr);
-  else if (used == 2) *bad = !centroid_solve<6>(Sd, sS, lane, z, fr);
+  else if (used == 1) *bad = !centroid_solve<3>(Sd, z, fr);
+  else if (used == 2) *bad = !centroid_solve<6>(Sd, z, fr);
   return used;
 }
 
 // ---------------------------------------------------------------------------
 
+// Per-warp state of a chunk of up to 32 pixels between the three phases.
+struct ChunkSlot {
+  double S[15];    // pixel-frame moments
+  double z[6];     // solution in the centroid frame
+  float fr[5];     // centroid frame
+  long long count;
+  int flags;       // bit 0: needs the FP64 kernel; bits 8..: degree used + 1
+};
+
 template <int DEG, int WK>
-__global__ __launch_bounds__(kWarps * 32, 2) void k_handover(KParams p, const int *list,
+__global__ __launch_bounds__(kWarps * 32, 4) void k_handover(KParams p, const int *list,
                                                           const unsigned int *list_count, int64_t cap, int *list2,
                                                           unsigned int *list2_count) {
   constexpr int NM = n_moments(DEG);
   __shared__ int s_ri[kWarps][kRing];
   __shared__ float4 s_rx[kWarps][kRing];
-  __shared__ double s_S[kWarps][16];
+  __shared__ ChunkSlot s_chunk[kWarps][32];
   __shared__ float2 s_tab[64];
   if (WK == MLS_W_GAUSS) df_exp_table_init(s_tab);
   __syncthreads();
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   int *ri = s_ri[wib];
   float4 *rx = s_rx[wib];
+  ChunkSlot *slots = s_chunk[wib];
   const int64_t warp0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   const int64_t npix = (int64_t)*list_count < cap ? (int64_t)*list_count : cap;
+  const int64_t nchunks = (npix + 31) / 32;
   const size_t plane = (size_t)p.W * p.H;
   const double inv_s = 1.0 / p.h;
   float *field = (float *)p.field;
 
-  for (int64_t qi = warp0; qi < npix; qi += nwarps) {
-    const int id = list[qi];
+  // everything pass 1 and pass 2 need about pixel `id`
+  auto setup = [&](int id, Ranges &R, float &mhat, float &pxh, float &pxl, float &pyh, float &pyl) {
     const int u = id % p.W, v = id / p.W;
     const double px = __dadd_rn(p.x0, __dmul_rn(__dadd_rn((double)u, 0.5), p.sx));
     const double py = __dadd_rn(p.y0, __dmul_rn(__dadd_rn((double)v, 0.5), p.sy));
-    const float mhat = (WK == MLS_W_WENDLAND) ? 0.f : p.mstab[(size_t)v * (p.tiles_x * 16) + u];
-    Ranges R;
+    mhat = (WK == MLS_W_WENDLAND) ? 0.f : p.mstab[(size_t)v * (p.tiles_x * 16) + u];
     if (WK == MLS_W_WENDLAND) {
       const double inv_cell = 1.0 / p.cell;
       const int cx0 = max((int)floor((px - p.h - p.gx0) * inv_cell), 0);
@@ -408,136 +414,170 @@ __global__ __launch_bounds__(kWarps * 32, 2) void k_handover(KParams p, const in
     }
     // pixel position in the scaled frame as hi + lo
     const double pxs64 = (px - p.ctr_x) * inv_s, pys64 = (py - p.ctr_y) * inv_s;
-    const float pxh = (float)pxs64, pxl = (float)(pxs64 - (double)pxh);
-    const float pyh = (float)pys64, pyl = (float)(pys64 - (double)pyh);
+    pxh = (float)pxs64;
+    pxl = (float)(pxs64 - (double)pxh);
+    pyh = (float)pys64;
+    pyl = (float)(pys64 - (double)pyh);
+  };
 
-    // ---- pass 1: double-float pixel-frame moments of the near points
-    df32 S[NM];
-#pragma unroll
-    for (int j = 0; j < NM; ++j) S[j] = {0.f, 0.f};
-    int coincident = 0;
-    const int nnear = for_near<WK>(p, R, pxh, pxl, pyh, pyl, mhat, lane, ri, rx, &coincident,
-                                   [&](bool valid, int, df32 ex, df32 ey) {
-      if (!valid) return;
-      const df32 w = pair_wdf<WK>(ex, ey, mhat, p.alpha, s_tab);
-      df_acc(S[0], w);
-      if (NM > 1) {
-        const df32 wx = df_prod(w, ex), wy = df_prod(w, ey);
-        const df32 wxx = df_prod(wx, ex), wxy = df_prod(wx, ey), wyy = df_prod(wy, ey);
-        df_acc(S[1], wx);
-        df_acc(S[2], wy);
-        df_acc(S[3], wxx);
-        df_acc(S[4], wxy);
-        df_acc(S[5], wyy);
-        if (NM > 6) {
-          const df32 wxxx = df_prod(wxx, ex), wxxy = df_prod(wxx, ey);
-          const df32 wxyy = df_prod(wyy, ex), wyyy = df_prod(wyy, ey);
-          df_acc(S[6], wxxx);
-          df_acc(S[7], wxxy);
-          df_acc(S[8], wxyy);
-          df_acc(S[9], wyyy);
-          df_acc(S[10], df_prod(wxxx, ex));
-          df_acc(S[11], df_prod(wxxx, ey));
-          df_acc(S[12], df_prod(wxxy, ey));
-          df_acc(S[13], df_prod(wxyy, ey));
-          df_acc(S[14], df_prod(wyyy, ey));
-        }
-      }
-    });
-    double Sd[15];
-#pragma unroll
-    for (int j = 0; j < 15; ++j) {
-      if (j < NM) {
-        const df32 t = df_warp_sum(S[j]);
-        Sd[j] = (double)t.hi + (double)t.lo;
-      } else {
-        Sd[j] = 0.0;
-      }
-    }
-#pragma unroll
-    for (int j = 0; j < 15; ++j)
-      if (lane == j) s_S[wib][j] = Sd[j];
-    __syncwarp();
-    const long long count = (WK == MLS_W_WENDLAND) ? nnear : p.n;
-    // inverse distance: a coincident point (or a zero stabiliser) goes to the
-    // FP64 kernel, which gives the pixel that point's value
-    bool bad = WK == MLS_W_INVDIST && (coincident || !(mhat > 0.f));
+  for (int64_t ch = warp0; ch < nchunks; ch += nwarps) {
+    const int64_t q0 = ch * 32;
+    const int nq = (int)((npix - q0) < 32 ? (npix - q0) : 32);
 
-    // ---- degree policy (pixel frame) and the solve in the centroid frame (FP64)
-    double z[6];
-    float fr[5];
-    int used = -1;
-    if (!bad) used = pixel_policy<DEG>(Sd, s_S[wib], count, p.rcond_min, lane, z, fr, &bad);
-    if (bad) {
-      if (lane == 0) {
-        const unsigned int k2 = atomicAdd(list2_count, 1u);
-        list2[k2] = id;
-      }
-      __syncwarp();
-      continue;
-    }
-    if (used < 0) {
-      for (int d = lane; d < p.D; d += 32) {
-        field[(size_t)d * plane + id] = __int_as_float(0x7fc00000);
-        if (p.bands) p.bands[(size_t)d * plane + id] = 255;
-      }
-      if (lane == 0 && p.status) p.status[id] = MLS_ST_NO_SUPPORT | MLS_ST_RECOMPUTED;
-      __syncwarp();
-      continue;
-    }
-    const int ku = n_terms(used);
-    df32 zd[6];
+    // ---- phase 1 (warp per pixel): double-float pixel-frame moments
+    for (int j = 0; j < nq; ++j) {
+      const int id = list[q0 + j];
+      Ranges R;
+      float mhat, pxh, pxl, pyh, pyl;
+      setup(id, R, mhat, pxh, pxl, pyh, pyl);
+      df32 S[NM];
 #pragma unroll
-    for (int a = 0; a < 6; ++a) zd[a] = {(float)z[a], (float)(z[a] - (double)(float)z[a])};
-    const float cxh = fr[0], cxl = fr[1], cyh = fr[2], cyl = fr[3], isg = fr[4];
-
-    // ---- pass 2: value = sum_i phi_i f_i, phi_i = w_i z . b_c(x_i); lanes over dimensions
-    for (int d0 = 0; d0 < p.D; d0 += 32 * kDL) {
-      df32 acc[kDL];
-#pragma unroll
-      for (int t = 0; t < kDL; ++t) acc[t] = {0.f, 0.f};
-      int unused;
-      for_near<WK>(p, R, pxh, pxl, pyh, pyl, mhat, lane, ri, rx, &unused,
-                   [&](bool valid, int i, df32 ex, df32 ey) {
-        df32 phi = {0.f, 0.f};
-        if (valid) {
-          const df32 w = pair_wdf<WK>(ex, ey, mhat, p.alpha, s_tab);
-          df32 zb = zd[0];
-          if (ku > 1) {
-            const df32 cxe = df_mul_f(df_diff(ex.hi, ex.lo, cxh, cxl), isg);
-            const df32 cye = df_mul_f(df_diff(ey.hi, ey.lo, cyh, cyl), isg);
-            zb = df_add(zb, df_add(df_mul(zd[1], cxe), df_mul(zd[2], cye)));
-            if (ku > 3) {
-              const df32 t = df_add(df_mul(zd[3], cxe), df_mul(zd[4], cye));
-              zb = df_add(zb, df_add(df_mul(t, cxe), df_mul(df_mul(zd[5], cye), cye)));
-            }
+      for (int k = 0; k < NM; ++k) S[k] = {0.f, 0.f};
+      int coincident = 0;
+      const int nnear = for_near<WK>(p, R, pxh, pxl, pyh, pyl, mhat, lane, ri, rx, &coincident,
+                                     [&](bool valid, int, df32 ex, df32 ey) {
+        if (!valid) return;
+        const df32 w = pair_wdf<WK>(ex, ey, mhat, p.alpha, s_tab);
+        df_acc(S[0], w);
+        if (NM > 1) {
+          const df32 wx = df_prod(w, ex), wy = df_prod(w, ey);
+          const df32 wxx = df_prod(wx, ex), wxy = df_prod(wx, ey), wyy = df_prod(wy, ey);
+          df_acc(S[1], wx);
+          df_acc(S[2], wy);
+          df_acc(S[3], wxx);
+          df_acc(S[4], wxy);
+          df_acc(S[5], wyy);
+          if (NM > 6) {
+            const df32 wxxx = df_prod(wxx, ex), wxxy = df_prod(wxx, ey);
+            const df32 wxyy = df_prod(wyy, ex), wyyy = df_prod(wyy, ey);
+            df_acc(S[6], wxxx);
+            df_acc(S[7], wxxy);
+            df_acc(S[8], wxyy);
+            df_acc(S[9], wyyy);
+            df_acc(S[10], df_prod(wxxx, ex));
+            df_acc(S[11], df_prod(wxxx, ey));
+            df_acc(S[12], df_prod(wxxy, ey));
+            df_acc(S[13], df_prod(wxyy, ey));
+            df_acc(S[14], df_prod(wyyy, ey));
           }
-          phi = df_mul(w, zb);
-        }
-        const int nb = __popc(__ballot_sync(0xffffffffu, valid));
-#pragma unroll 4
-        for (int j = 0; j < nb; ++j) {
-          const df32 ph = {__shfl_sync(0xffffffffu, phi.hi, j), __shfl_sync(0xffffffffu, phi.lo, j)};
-          const int ij = __shfl_sync(0xffffffffu, i, j);
-          const float *fp = p.FR32 + (size_t)ij * p.D + d0 + lane;
-#pragma unroll
-          for (int t = 0; t < kDL; ++t)
-            if (d0 + lane + 32 * t < p.D) df_acc(acc[t], df_prod_f(ph, fp[32 * t]));
         }
       });
 #pragma unroll
-      for (int t = 0; t < kDL; ++t) {
-        const int d = d0 + lane + 32 * t;
-        if (d < p.D) {
-          const double fv = (double)acc[t].hi + (double)acc[t].lo;
-          const float f = (float)((double)p.fcen32[d] + (double)p.fscl32[d] * fv);
-          field[(size_t)d * plane + id] = f;
-          if (p.bands) p.bands[(size_t)d * plane + id] = band_of(f, p.lev32 + (size_t)d * p.L, p.L);
+      for (int k = 0; k < 15; ++k) {
+        double v = 0.0;
+        if (k < NM) {
+          const df32 t = df_warp_sum(S[k]);
+          v = (double)t.hi + (double)t.lo;
         }
+        if (lane == k) slots[j].S[k] = v;
+      }
+      if (lane == 0) {
+        slots[j].count = (WK == MLS_W_WENDLAND) ? nnear : p.n;
+        // inverse distance: a coincident point (or a zero stabiliser) goes to
+        // the FP64 kernel, which gives the pixel that point's value
+        slots[j].flags = (WK == MLS_W_INVDIST && (coincident || !(mhat > 0.f))) ? 1 : 0;
+      }
+      __syncwarp();
+    }
+
+    // ---- phase 2 (lane per pixel): degree policy and centroid-frame solve in FP64
+    if (lane < nq) {
+      ChunkSlot &sl = slots[lane];
+      if (!(sl.flags & 1)) {
+        double Sd[15], z[6];
+        float fr[5];
+#pragma unroll
+        for (int k = 0; k < 15; ++k) Sd[k] = sl.S[k];
+        bool bad = false;
+        const int used = pixel_policy<DEG>(Sd, sl.count, p.rcond_min, z, fr, &bad);
+#pragma unroll
+        for (int a = 0; a < 6; ++a) sl.z[a] = z[a];
+#pragma unroll
+        for (int a = 0; a < 5; ++a) sl.fr[a] = fr[a];
+        sl.flags = (bad ? 1 : 0) | ((used + 1) << 8);
       }
     }
-    if (lane == 0 && p.status)
-      p.status[id] = (uint8_t)(used | MLS_ST_RECOMPUTED | (used < DEG ? MLS_ST_DEGRADED : 0));
+    __syncwarp();
+
+    // ---- phase 3 (warp per pixel): value = sum_i phi_i f_i, phi_i = w_i z . b_c(x_i)
+    for (int j = 0; j < nq; ++j) {
+      const int id = list[q0 + j];
+      const int flags = slots[j].flags;
+      if (flags & 1) {
+        if (lane == 0) {
+          const unsigned int k2 = atomicAdd(list2_count, 1u);
+          list2[k2] = id;
+        }
+        continue;
+      }
+      const int used = (flags >> 8) - 1;
+      if (used < 0) {
+        for (int d = lane; d < p.D; d += 32) {
+          field[(size_t)d * plane + id] = __int_as_float(0x7fc00000);
+          if (p.bands) p.bands[(size_t)d * plane + id] = 255;
+        }
+        if (lane == 0 && p.status) p.status[id] = MLS_ST_NO_SUPPORT | MLS_ST_RECOMPUTED;
+        continue;
+      }
+      Ranges R;
+      float mhat, pxh, pxl, pyh, pyl;
+      setup(id, R, mhat, pxh, pxl, pyh, pyl);
+      const int ku = n_terms(used);
+      df32 zd[6];
+#pragma unroll
+      for (int a = 0; a < 6; ++a) {
+        const double za = slots[j].z[a];
+        zd[a] = {(float)za, (float)(za - (double)(float)za)};
+      }
+      const float cxh = slots[j].fr[0], cxl = slots[j].fr[1], cyh = slots[j].fr[2], cyl = slots[j].fr[3],
+                  isg = slots[j].fr[4];
+      for (int d0 = 0; d0 < p.D; d0 += 32 * kDL) {
+        df32 acc[kDL];
+#pragma unroll
+        for (int t = 0; t < kDL; ++t) acc[t] = {0.f, 0.f};
+        int unused;
+        for_near<WK>(p, R, pxh, pxl, pyh, pyl, mhat, lane, ri, rx, &unused,
+                     [&](bool valid, int i, df32 ex, df32 ey) {
+          df32 phi = {0.f, 0.f};
+          if (valid) {
+            const df32 w = pair_wdf<WK>(ex, ey, mhat, p.alpha, s_tab);
+            df32 zb = zd[0];
+            if (ku > 1) {
+              const df32 cxe = df_mul_f(df_diff(ex.hi, ex.lo, cxh, cxl), isg);
+              const df32 cye = df_mul_f(df_diff(ey.hi, ey.lo, cyh, cyl), isg);
+              zb = df_add(zb, df_add(df_mul(zd[1], cxe), df_mul(zd[2], cye)));
+              if (ku > 3) {
+                const df32 t = df_add(df_mul(zd[3], cxe), df_mul(zd[4], cye));
+                zb = df_add(zb, df_add(df_mul(t, cxe), df_mul(df_mul(zd[5], cye), cye)));
+              }
+            }
+            phi = df_mul(w, zb);
+          }
+          const int nb = __popc(__ballot_sync(0xffffffffu, valid));
+#pragma unroll 4
+          for (int jj = 0; jj < nb; ++jj) {
+            const df32 ph = {__shfl_sync(0xffffffffu, phi.hi, jj), __shfl_sync(0xffffffffu, phi.lo, jj)};
+            const int ij = __shfl_sync(0xffffffffu, i, jj);
+            const float *fp = p.FR32 + (size_t)ij * p.D + d0 + lane;
+#pragma unroll
+            for (int t = 0; t < kDL; ++t)
+              if (d0 + lane + 32 * t < p.D) df_acc(acc[t], df_prod_f(ph, fp[32 * t]));
+          }
+        });
+#pragma unroll
+        for (int t = 0; t < kDL; ++t) {
+          const int d = d0 + lane + 32 * t;
+          if (d < p.D) {
+            const double fv = (double)acc[t].hi + (double)acc[t].lo;
+            const float f = (float)((double)p.fcen32[d] + (double)p.fscl32[d] * fv);
+            field[(size_t)d * plane + id] = f;
+            if (p.bands) p.bands[(size_t)d * plane + id] = band_of(f, p.lev32 + (size_t)d * p.L, p.L);
+          }
+        }
+      }
+      if (lane == 0 && p.status)
+        p.status[id] = (uint8_t)(used | MLS_ST_RECOMPUTED | (used < DEG ? MLS_ST_DEGRADED : 0));
+    }
     __syncwarp();
   }
 }
@@ -545,7 +585,7 @@ __global__ __launch_bounds__(kWarps * 32, 2) void k_handover(KParams p, const in
 template <int WK>
 void launch_w(const KParams &p, const int *list, const unsigned int *cnt, int64_t cap, int *list2,
               unsigned int *cnt2, cudaStream_t st) {
-  const int grid = 152 * 2;   // one resident wave (2 blocks of 8 warps per SM)
+  const int grid = 152 * 4;   // one resident wave (4 blocks of 4 warps per SM)
   if (p.degree == 0) k_handover<0, WK><<<grid, kWarps * 32, 0, st>>>(p, list, cnt, cap, list2, cnt2);
   else if (p.degree == 1) k_handover<1, WK><<<grid, kWarps * 32, 0, st>>>(p, list, cnt, cap, list2, cnt2);
   else k_handover<2, WK><<<grid, kWarps * 32, 0, st>>>(p, list, cnt, cap, list2, cnt2);
