@@ -385,7 +385,11 @@ __global__ __launch_bounds__(kWarps * 32, 4) void k_handover(KParams p, const in
   const int64_t warp0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   const int64_t npix = (int64_t)*list_count < cap ? (int64_t)*list_count : cap;
-  const int64_t nchunks = (npix + 31) / 32;
+  // pixels per chunk: up to 32 (one per lane in the policy phase), fewer
+  // when there are too few pixels to give every warp a full chunk
+  const int64_t per = (npix + nwarps - 1) / nwarps;
+  const int csz = per >= 32 ? 32 : (per < 1 ? 1 : (int)per);
+  const int64_t nchunks = (npix + csz - 1) / csz;
   const size_t plane = (size_t)p.W * p.H;
   const double inv_s = 1.0 / p.h;
   float *field = (float *)p.field;
@@ -421,8 +425,8 @@ __global__ __launch_bounds__(kWarps * 32, 4) void k_handover(KParams p, const in
   };
 
   for (int64_t ch = warp0; ch < nchunks; ch += nwarps) {
-    const int64_t q0 = ch * 32;
-    const int nq = (int)((npix - q0) < 32 ? (npix - q0) : 32);
+    const int64_t q0 = ch * csz;
+    const int nq = (int)((npix - q0) < csz ? (npix - q0) : csz);
 
     // ---- phase 1 (warp per pixel): double-float pixel-frame moments
     for (int j = 0; j < nq; ++j) {
