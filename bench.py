@@ -385,6 +385,102 @@ def run_ours(args):
     print(json.dumps(line), flush=True)
 
 
+def run_batch(args):
+    """64 independent datasets (n log-uniform 200-50,000, D 4-64, 256^2-1024^2,
+    linear or quadratic, Gaussian h = 0.5/sqrt(n)) rendered by one CUDA graph
+    per step (mls_batch_render, autotuned weight mode)."""
+    import torch
+    import torch.distributed as dist
+    world, rank, local = _dist()
+    torch.cuda.set_device(local)
+    from paper_1408_0677_gb300 import Batch, Renderer, inputs
+    wls = inputs.batch_datasets(seed=1004, count=64)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    xy_d = [torch.from_numpy(w.xy).to(dev) for w in wls]
+    F_d = [torch.from_numpy(w.F).to(dev) for w in wls]
+    rs = [Renderer(x, f, degree=w.degree, weight=w.weight, h=w.h, precision=args.precision,
+                   weight_split=args.weight_split, stream=stream.cuda_stream) for w, x, f in zip(wls, xy_d, F_d)]
+    b = Batch(rs, autotune=args.weight_split is None, stream=stream.cuda_stream)
+    entries = [(w.W, w.H, (0.0, 0.0, 1.0, 1.0), w.levels) for w in wls]
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    for _ in range(args.warmup):
+        b.render(entries)
+        b.sync()
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    step_ms = []
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        b.render(entries)
+        e1.record(stream)
+        st = b.sync()
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clocks = sampler.stop()
+    ms_step = max_over_ranks(float(np.sum(step_ms)), world, dev) / args.steps
+    units = sum(w.W * w.H * w.n * w.D for w in wls)
+    value = world * units / (ms_step * 1e-3)
+    # end to end: points uploaded from pinned host memory, the batch render,
+    # every field read back
+    xy_h = [torch.from_numpy(w.xy).pin_memory() for w in wls]
+    F_h = [torch.from_numpy(w.F).pin_memory() for w in wls]
+    outs = b.render(entries)
+    b.sync()
+    host = [torch.empty(o["field"].shape, dtype=o["field"].dtype).pin_memory() for o in outs]
+    e2e = []
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for k in range(len(wls)):
+            xy_d[k].copy_(xy_h[k], non_blocking=True)
+            F_d[k].copy_(F_h[k], non_blocking=True)
+        outs = b.render(entries)
+        for o, hbuf in zip(outs, host):
+            hbuf.copy_(o["field"], non_blocking=True)
+        b.sync()
+        torch.cuda.synchronize()
+        e2e.append(1e3 * (time.perf_counter() - t0))
+    e2e_ms = max_over_ranks(float(np.mean(e2e)), world, dev)
+    if rank != 0:
+        return
+    peaks, src = _peaks()
+    flops = sum(2.0 * (w.D * (3 if w.degree == 1 else 6) + (6 if w.degree == 1 else 15)) * w.W * w.H * w.n
+                for w in wls)
+    achieved = flops / (ms_step * 1e-3) / 1e12
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
+            "config": {"workload": "batch64_n200-50k_d4-64_256-1024sq_gauss", "datasets": len(wls),
+                       "pairs_dims": units, "precision": args.precision, "l2": "flushed between steps",
+                       "replicas": world},
+            "e2e": {"value": world * units / (e2e_ms * 1e-3), "unit": UNIT,
+                    "h2d_bytes_per_step": int(sum(w.xy.nbytes + w.F.nbytes for w in wls)),
+                    "d2h_bytes_per_step": int(sum(h.numel() * h.element_size() for h in host)), "ms_per_step": e2e_ms},
+            "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99)),
+                           "steps": len(step_ms), "what": "device time of one batch render (one graph launch)"},
+            "roofline": {"bound": "tensor", "achieved": achieved, "peak": peaks.get("bf16_tflops", 1900.0),
+                         "unit": "TFLOP/s", "frac": achieved / peaks.get("bf16_tflops", 1900.0), "traffic": None,
+                         "peak_source": f"{src} bf16 burst", "kernel": "whole batch graph",
+                         "flops_per_step": flops},
+            "cpu_baseline": None, "clocks": clocks, "gpu_launches": int(st.launches) * args.steps,
+            "batch": {"captures": int(st.captures), "replays": int(st.replays),
+                      "handed_over_pixels": int(st.recomputed)}}
+    print(json.dumps(line), flush=True)
+    b.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -396,11 +492,15 @@ def main():
     ap.add_argument("--weight-split", type=int, default=None, choices=[0, 1, 2])
     ap.add_argument("--no-compare-fp32", dest="compare_fp32", action="store_false",
                     help="skip the plain FP32 comparison run")
+    ap.add_argument("--workload", default="fourier10k", choices=["fourier10k", "batch64"],
+                    help="the 10k-point render (default) or 64 datasets in one graph")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batch64":
+        run_batch(args)
     else:
         run_ours(args)
 

@@ -183,6 +183,60 @@ mls_status mls_bands(mls_handle *h, const mls_view *view, const void *field,
                      const double *levels, int32_t L, uint8_t *bands,
                      int32_t on_device, void *stream);
 
+/* ---------------------------------------------------------------------------
+ * Batches (no counterpart in the paper, which renders one dataset per frame,
+ * Section 4 Performance): many resident datasets rendered together.
+ * mls_batch_render prepares every dataset (scratch, level uploads: these
+ * may allocate and synchronise), then launches ONE CUDA graph in which each
+ * dataset's kernels run on their own branch, so small datasets fill the GPU
+ * together.  The graph is captured on the first call and replayed while the
+ * views, buffers and level counts stay the same (a change re-captures).
+ * With MLS_BATCH_AUTOTUNE the first call times, per FP16/BF16 dataset, split
+ * weights everywhere against the two-pass scheme (weight_split 1 and 2) on
+ * the actual view and keeps the faster; both meet the same error bound.
+ */
+typedef struct mls_batch mls_batch;
+
+#define MLS_BATCH_AUTOTUNE 1
+
+typedef struct mls_batch_stats {
+    int64_t datasets;
+    int64_t pairs;            /* pixel-point pairs of the last render (full-sum datasets) */
+    int64_t recomputed;       /* pixels handed to the recompute path, all datasets */
+    int64_t device_error;     /* first non-zero device error word (0 = none) */
+    int64_t launches;         /* kernels per batch render */
+    int64_t captures;         /* graph captures so far */
+    int64_t replays;          /* graph launches so far */
+    double last_render_ms;    /* device time of the last batch render (events around the graph) */
+} mls_batch_stats;
+
+/*
+ * Group `count` handles (distinct, same device; the caller keeps ownership
+ * and must not destroy them before the batch) into a batch.
+ * Errors: MLS_E_INVAL, MLS_E_CUDA.
+ */
+mls_status mls_batch_create(int32_t count, mls_handle *const *handles, int32_t flags,
+                            mls_batch **out);
+
+/*
+ * Render every dataset k of the batch over views[k] into device buffers
+ * fields[k] (D_k x H_k x W_k, float or double per its precision), status[k]
+ * and bands[k] (each array or entry may be NULL), with levels[k] (host, D_k x
+ * L[k] doubles; NULL / L[k] = 0 for no bands).  Asynchronous on `stream`;
+ * the buffers must stay valid until mls_batch_sync returns.  Render calls on
+ * one batch must not overlap (the datasets' scratch is reused).
+ * Errors: MLS_E_INVAL (naming the dataset), MLS_E_NOMEM, MLS_E_CUDA.
+ */
+mls_status mls_batch_render(mls_batch *b, const mls_view *views, void *const *fields,
+                            uint8_t *const *status, const double *const *levels,
+                            const int32_t *L, uint8_t *const *bands, void *stream);
+
+/* Wait for the last batch render (host watchdog of timeout_s) and fill *stats. */
+mls_status mls_batch_sync(mls_batch *b, double timeout_s, mls_batch_stats *stats);
+
+/* Release the batch (waits for its last render; the handles stay alive). */
+mls_status mls_batch_destroy(mls_batch *b);
+
 /* Most levels (D * L) that mls_bands_noalloc accepts. */
 #define MLS_NOALLOC_MAX_LEVELS 4096
 

@@ -13,8 +13,10 @@ import numpy as np
 
 from . import _abi
 from ._abi import (MLS_P_BF16, MLS_P_FP16, MLS_P_FP32, MLS_P_FP64, MLS_W_GAUSS, MLS_W_INVDIST,  # noqa: F401
-                   MLS_W_WENDLAND, MlsDesc, MlsError, MlsStats, MlsView, mls_abi_version, mls_bands,
-                   mls_create, mls_desc_default, mls_destroy, mls_last_error, mls_render, mls_sync)
+                   MLS_W_WENDLAND, MLS_BATCH_AUTOTUNE, MlsBatchStats, MlsDesc, MlsError, MlsStats, MlsView,
+                   mls_abi_version, mls_bands, mls_batch_create, mls_batch_destroy, mls_batch_render,
+                   mls_batch_sync, mls_create, mls_desc_default, mls_destroy, mls_last_error, mls_render,
+                   mls_sync)
 
 PRECISIONS = {"fp64": MLS_P_FP64, "fp32": MLS_P_FP32, "bf16": MLS_P_BF16, "fp16": MLS_P_FP16}
 
@@ -131,6 +133,66 @@ class Renderer:
     def close(self):
         if getattr(self, "handle", None):
             mls_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Many resident datasets (``Renderer`` objects) rendered by one CUDA graph
+    (``mls_batch_*``).  ``render`` takes one (W, H, view, levels) entry per
+    dataset and returns one output dict per dataset; the outputs are reused by
+    later calls with the same shapes, so the captured graph is replayed."""
+
+    def __init__(self, renderers, autotune=False, stream=None):
+        import torch
+        self.torch = torch
+        self.renderers = list(renderers)
+        self.stream = _stream_ptr(stream)
+        self.handle = mls_batch_create([r.handle for r in self.renderers],
+                                       MLS_BATCH_AUTOTUNE if autotune else 0)
+        self._out = None
+        self._key = None
+
+    def render(self, entries, status=True):
+        """entries: list of (W, H, view, levels or None)."""
+        torch = self.torch
+        n = len(self.renderers)
+        assert len(entries) == n
+        key = tuple((W, H, tuple(view), None if lev is None else np.asarray(lev).shape)
+                    for (W, H, view, lev) in entries)
+        dev = torch.device("cuda", torch.cuda.current_device())
+        if key != self._key:
+            outs = []
+            for r, (W, H, view, lev) in zip(self.renderers, entries):
+                o = {"field": torch.empty((r.D, H, W), dtype=r.field_dtype, device=dev),
+                     "status": torch.empty((H, W), dtype=torch.uint8, device=dev) if status else None,
+                     "bands": torch.empty((r.D, H, W), dtype=torch.uint8, device=dev) if lev is not None else None}
+                outs.append(o)
+            self._out, self._key = outs, key
+        outs = self._out
+        views = (MlsView * n)(*[MlsView(W, H, *view) for (W, H, view, _) in entries])
+        P = ctypes.c_void_p
+        fields = (P * n)(*[o["field"].data_ptr() for o in outs])
+        sts = (P * n)(*[o["status"].data_ptr() if o["status"] is not None else None for o in outs])
+        levs = [None if lev is None else np.ascontiguousarray(lev, dtype=np.float64) for (_, _, _, lev) in entries]
+        self._levs = levs
+        lev_p = (P * n)(*[lv.ctypes.data if lv is not None else None for lv in levs])
+        Ls = (ctypes.c_int32 * n)(*[lv.shape[1] if lv is not None else 0 for lv in levs])
+        bnd = (P * n)(*[o["bands"].data_ptr() if o["bands"] is not None else None for o in outs])
+        mls_batch_render(self.handle, views, fields, sts, lev_p, Ls, bnd, self.stream)
+        return outs
+
+    def sync(self, timeout_s=120.0) -> MlsBatchStats:
+        return mls_batch_sync(self.handle, timeout_s)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            mls_batch_destroy(self.handle)
             self.handle = None
 
     def __del__(self):

@@ -45,6 +45,15 @@ class MlsStats(ctypes.Structure):
                 ("main_kernel_ms", ctypes.c_double), ("retried_tiles", ctypes.c_int64)]
 
 
+class MlsBatchStats(ctypes.Structure):
+    _fields_ = [("datasets", ctypes.c_int64), ("pairs", ctypes.c_int64), ("recomputed", ctypes.c_int64),
+                ("device_error", ctypes.c_int64), ("launches", ctypes.c_int64), ("captures", ctypes.c_int64),
+                ("replays", ctypes.c_int64), ("last_render_ms", ctypes.c_double)]
+
+
+MLS_BATCH_AUTOTUNE = 1
+
+
 class MlsError(RuntimeError):
     def __init__(self, status: int, where: str, message: str):
         super().__init__(f"{where}: {STATUS_NAMES.get(status, status)}: {message}")
@@ -84,6 +93,14 @@ def load(path: str | None = None):
     lib.mls_sync.argtypes = [P, ctypes.c_double, ctypes.POINTER(MlsStats)]
     lib.mls_destroy.restype = ctypes.c_int
     lib.mls_destroy.argtypes = [P]
+    lib.mls_batch_create.restype = ctypes.c_int
+    lib.mls_batch_create.argtypes = [ctypes.c_int32, P, ctypes.c_int32, ctypes.POINTER(P)]
+    lib.mls_batch_render.restype = ctypes.c_int
+    lib.mls_batch_render.argtypes = [P, P, P, P, P, P, P, P]
+    lib.mls_batch_sync.restype = ctypes.c_int
+    lib.mls_batch_sync.argtypes = [P, ctypes.c_double, ctypes.POINTER(MlsBatchStats)]
+    lib.mls_batch_destroy.restype = ctypes.c_int
+    lib.mls_batch_destroy.argtypes = [P]
     lib.mls_bands_noalloc.restype = ctypes.c_int
     lib.mls_bands_noalloc.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, P, ctypes.c_int32, P,
                                       ctypes.c_int32, P, P]
@@ -141,6 +158,34 @@ def mls_bands_noalloc(D: int, W: int, H: int, field_ptr: int, field_fp64: bool, 
     """Iso-band labels into caller buffers, without any device allocation."""
     _check(load().mls_bands_noalloc(int(D), int(W), int(H), P(field_ptr), int(bool(field_fp64)), P(levels_ptr),
                                     int(L), P(bands_ptr), P(stream)), "mls_bands_noalloc")
+
+
+def mls_batch_create(handles, flags: int = 0) -> int:
+    arr = (P * len(handles))(*[P(h) for h in handles])
+    out = P()
+    _check(load().mls_batch_create(len(handles), ctypes.cast(arr, P), int(flags), ctypes.byref(out)),
+           "mls_batch_create")
+    return out.value
+
+
+def mls_batch_render(batch: int, views, fields, status, levels, L, bands, stream: int = 0):
+    """views: ctypes array of MlsView; the others ctypes pointer arrays (or None)."""
+    _check(load().mls_batch_render(P(batch), ctypes.cast(views, P), ctypes.cast(fields, P),
+                                   ctypes.cast(status, P) if status is not None else None,
+                                   ctypes.cast(levels, P) if levels is not None else None,
+                                   ctypes.cast(L, P) if L is not None else None,
+                                   ctypes.cast(bands, P) if bands is not None else None, P(stream)),
+           "mls_batch_render")
+
+
+def mls_batch_sync(batch: int, timeout_s: float = 60.0) -> MlsBatchStats:
+    st = MlsBatchStats()
+    _check(load().mls_batch_sync(P(batch), float(timeout_s), ctypes.byref(st)), "mls_batch_sync")
+    return st
+
+
+def mls_batch_destroy(batch: int):
+    _check(load().mls_batch_destroy(P(batch)), "mls_batch_destroy")
 
 
 def mls_sync(handle: int, timeout_s: float = 60.0) -> MlsStats:

@@ -116,6 +116,7 @@ struct KParams {
   int *tile_mark;
   const int *tile_list;        // tensor path, second pass: the tiles to render, or null
   const unsigned int *tile_count;
+  int pixel_frame;             // FP32 kernel: moments in each pixel's own frame (not the tile's)
   const int *list;             // pixel indices, or null for all pixels
   const unsigned int *list_count;  // device count for list mode, or null
   int64_t list_cap;

@@ -112,10 +112,10 @@ __device__ __forceinline__ df32 pair_wdf(df32 ex, df32 ey, float mhat, double al
   return {(float)w, (float)(w - (double)(float)w)};
 }
 
-// Candidate index ranges of one pixel: all points, or the rows of grid cells
-// that overlap the Wendland support (cells are at least h wide: <= 3 rows).
+// Candidate points of one pixel: all points (all_n > 0), or the cells
+// [cx0, cx1] x [cy0, cy1] of the uniform grid that cover its near radius.
 struct Ranges {
-  int a0[3], a1[3], nr;
+  int cx0, cx1, cy0, cy1, all_n;
 };
 
 // Walk the candidates 32 at a time, compact the near ones into the warp's
@@ -129,12 +129,27 @@ __device__ __forceinline__ int for_near(const KParams &p, const Ranges &R, float
                                         Body body) {
   const unsigned int lt = (1u << lane) - 1u;
   int head = 0, total = 0, coin = 0;
-  for (int r = 0; r < R.nr; ++r) {
-    for (int base = R.a0[r]; base < R.a1[r]; base += 32) {
+  const int nrow = R.all_n > 0 ? 1 : (R.cx0 <= R.cx1 ? R.cy1 - R.cy0 + 1 : 0);
+  // the lanes fetch the index ranges of up to 32 cell rows at once
+  int my0 = 0, my1 = 0;
+  for (int r = 0; r < nrow; ++r) {
+    if ((r & 31) == 0) {
+      const int rr = r + lane;
+      if (R.all_n > 0) {
+        my0 = 0;
+        my1 = R.all_n;
+      } else if (rr < nrow) {
+        my0 = p.cell_start[(R.cy0 + rr) * p.gx + R.cx0];
+        my1 = p.cell_start[(R.cy0 + rr) * p.gx + R.cx1 + 1];
+      }
+    }
+    const int a0 = __shfl_sync(0xffffffffu, my0, r & 31);
+    const int a1 = __shfl_sync(0xffffffffu, my1, r & 31);
+    for (int base = a0; base < a1; base += 32) {
       const int i = base + lane;
       bool nr = false;
       df32 ex = {0.f, 0.f}, ey = {0.f, 0.f};
-      if (i < R.a1[r]) {
+      if (i < a1) {
         ex = df_diff(p.xs[i], p.xs_lo[i], pxh, pxl);
         ey = df_diff(p.ys[i], p.ys_lo[i], pyh, pyl);
         nr = near_test<WK>(ex, ey, mhat);
@@ -400,21 +415,20 @@ __global__ __launch_bounds__(kWarps * 32, 4) void k_handover(KParams p, const in
     const double px = __dadd_rn(p.x0, __dmul_rn(__dadd_rn((double)u, 0.5), p.sx));
     const double py = __dadd_rn(p.y0, __dmul_rn(__dadd_rn((double)v, 0.5), p.sy));
     mhat = (WK == MLS_W_WENDLAND) ? 0.f : p.mstab[(size_t)v * (p.tiles_x * 16) + u];
-    if (WK == MLS_W_WENDLAND) {
-      const double inv_cell = 1.0 / p.cell;
-      const int cx0 = max((int)floor((px - p.h - p.gx0) * inv_cell), 0);
-      const int cx1 = min((int)floor((px + p.h - p.gx0) * inv_cell), p.gx - 1);
-      const int cy0 = max((int)floor((py - p.h - p.gy0) * inv_cell), 0);
-      const int cy1 = min((int)floor((py + p.h - p.gy0) * inv_cell), p.gy - 1);
-      R.nr = 0;
-      for (int cy = cy0; cy <= cy1 && cx0 <= cx1 && R.nr < 3; ++cy, ++R.nr) {
-        R.a0[R.nr] = p.cell_start[cy * p.gx + cx0];
-        R.a1[R.nr] = p.cell_start[cy * p.gx + cx1 + 1];
-      }
+    if (WK == MLS_W_INVDIST) {
+      R.all_n = (int)p.n;
+      R.cx0 = R.cx1 = R.cy0 = R.cy1 = 0;
     } else {
-      R.nr = 1;
-      R.a0[0] = 0;
-      R.a1[0] = (int)p.n;
+      // near radius: the support (Wendland), or r^2 <= m + kCut (Gaussian),
+      // widened by a relative 1e-5 against rounding
+      const double rad = (WK == MLS_W_WENDLAND ? 1.0 : sqrt(fmax((double)mhat, 0.0) + (double)kCut)) * p.h *
+                         (1.0 + 1e-5);
+      const double inv_cell = 1.0 / p.cell;
+      R.all_n = 0;
+      R.cx0 = max((int)floor((px - rad - p.gx0) * inv_cell), 0);
+      R.cx1 = min((int)floor((px + rad - p.gx0) * inv_cell), p.gx - 1);
+      R.cy0 = max((int)floor((py - rad - p.gy0) * inv_cell), 0);
+      R.cy1 = min((int)floor((py + rad - p.gy0) * inv_cell), p.gy - 1);
     }
     // pixel position in the scaled frame as hi + lo
     const double pxs64 = (px - p.ctr_x) * inv_s, pys64 = (py - p.ctr_y) * inv_s;

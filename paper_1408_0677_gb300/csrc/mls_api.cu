@@ -160,6 +160,8 @@ static mls_status ensure_stage(mls_handle *h, size_t bytes, cudaStream_t st) {
 // near lambda 1000, smooth and rough Fourier fields do not.  Single FP16
 // weights (scaled by 2^14 in the tensor kernel) are accepted up to 60.
 constexpr float kLambdaSplitFp16 = 200.f;
+// Tile width (16 pixels) in units of h above which the tile frame is not used.
+constexpr double kTileFrameMaxH = 4.0;
 
 static mlsk::KParams base_params(const mls_handle *h, const mls_view *v) {
   const PointSet &P = h->P;
@@ -330,24 +332,28 @@ bad:
   return s;
 }
 
-mls_status mls_render(mls_handle *h, const mls_view *view, void *field, uint8_t *status, const double *levels,
-                      int32_t L, uint8_t *bands, int32_t on_device, void *stream) {
-  g_err.clear();
+}  // extern "C"
+
+namespace mlsi {
+
+// Host-side part of a render: validation, scratch, level upload, staging;
+// fills the kernel parameters.  Everything here may allocate or synchronise,
+// so none of it runs inside a stream capture.
+static mls_status render_prepare(mls_handle *h, const mls_view *view, void *field, uint8_t *status,
+                                 const double *levels, int32_t L, uint8_t *bands, int32_t on_device,
+                                 cudaStream_t st, mlsk::KParams *out) {
   if (!h) return fail(MLS_E_INVAL, "handle is NULL");
   mls_status s = check_view(view);
   if (s != MLS_OK) return s;
   if (!field) return fail(MLS_E_INVAL, "field is NULL");
   if (bands && (!levels || L < 1) && L != 0) return fail(MLS_E_INVAL, "bands need levels");
   if ((s = check_levels(levels, bands ? L : 0, h->desc.D)) != MLS_OK) return s;
-  cudaStream_t st = (cudaStream_t)stream;
-  h->stream = st;
   const int W = view->W, H = view->H;
   const size_t plane = (size_t)W * H;
   const bool fp64 = h->desc.precision == MLS_P_FP64;
   const size_t esz = fp64 ? sizeof(double) : sizeof(float);
   if ((s = ensure_scratch(h, W, H, st)) != MLS_OK) return s;
   if (bands && L > 0 && (s = upload_levels(h, levels, L, st)) != MLS_OK) return s;
-
   void *field_d = field;
   uint8_t *status_d = status, *bands_d = bands;
   if (!on_device) {
@@ -365,19 +371,40 @@ mls_status mls_render(mls_handle *h, const mls_view *view, void *field, uint8_t 
   p.status = status_d;
   p.bands = bands_d;
   p.L = bands ? L : 0;
+  *out = p;
+  return MLS_OK;
+}
+
+// Device part of a render: memsets and kernel launches only (capturable in
+// a CUDA graph).  With `timing` the handle's events bracket the render and
+// its main kernel.  *nlaunch receives the kernels launched.
+static mls_status render_enqueue(mls_handle *h, const mlsk::KParams &p, cudaStream_t st, bool timing,
+                                 int64_t *nlaunch) {
+  mls_status s;
+  const size_t plane = (size_t)p.W * p.H;
+  const bool fp64 = h->desc.precision == MLS_P_FP64;
+  int64_t launches = 0;
   MLS_CUDA_TRY(cudaMemsetAsync(h->scratch, 0, 256, st));
-  MLS_CUDA_TRY(cudaEventRecord(h->ev0, st));
+  if (timing) MLS_CUDA_TRY(cudaEventRecord(h->ev0, st));
   if (fp64) {
-    MLS_CUDA_TRY(cudaEventRecord(h->evk0, st));
+    if (timing) MLS_CUDA_TRY(cudaEventRecord(h->evk0, st));
     launch_f64(p, (int64_t)plane, st);
-    MLS_CUDA_TRY(cudaEventRecord(h->evk1, st));
-    h->launches += 1;
+    if (timing) MLS_CUDA_TRY(cudaEventRecord(h->evk1, st));
+    launches += 1;
   } else {
     launch_prepass(p, st);
-    MLS_CUDA_TRY(cudaEventRecord(h->evk0, st));
-    if (h->desc.precision == MLS_P_FP32) {
-      launch_f32(p, st);
-      h->launches += 2;
+    if (timing) MLS_CUDA_TRY(cudaEventRecord(h->evk0, st));
+    // A 16 x 16 tile much wider than h has no moment frame that suits all
+    // its pixels (the tensor path shares one per tile): such renders use the
+    // CUDA-core kernel with each pixel in its own frame, at FP32 limits.
+    const double tile_h = kTile * fmax(fabs(p.sx), fabs(p.sy)) / h->desc.h;
+    if (tile_h > kTileFrameMaxH || h->desc.precision == MLS_P_FP32) {
+      mlsk::KParams pf = p;
+      pf.pixel_frame = tile_h > kTileFrameMaxH ? 1 : 0;
+      pf.lambda_max = 1000.f;
+      launch_f32(pf, st);
+      launches += 2;
+      if (timing) MLS_CUDA_TRY(cudaEventRecord(h->evk1, st));
     } else {
       const bool fp16 = h->desc.precision == MLS_P_FP16;
       int nl = 0;
@@ -391,22 +418,21 @@ mls_status mls_render(mls_handle *h, const mls_view *view, void *field, uint8_t 
         p1.retry_count = h->counters + 2;
         p1.tile_mark = h->tile_mark;
         if ((s = launch_tc(p1, fp16, 0, st, &nl)) != MLS_OK) return s;
-        h->launches += 1 + nl;
-        MLS_CUDA_TRY(cudaEventRecord(h->evk1, st));   // main kernel: the pass over every tile
+        launches += 1 + nl;
+        if (timing) MLS_CUDA_TRY(cudaEventRecord(h->evk1, st));   // main kernel: the pass over every tile
         mlsk::KParams p2 = p;
         p2.lambda_max = fp16 ? kLambdaSplitFp16 : 50.f;
         p2.tile_list = h->retry_tiles;
         p2.tile_count = h->counters + 2;
         if ((s = launch_tc(p2, fp16, 1, st, &nl)) != MLS_OK) return s;
-        h->launches += nl;
+        launches += nl;
       } else {
         if ((s = launch_tc(p, fp16, h->desc.weight_split, st, &nl)) != MLS_OK) return s;
-        h->launches += 1 + nl;
-        MLS_CUDA_TRY(cudaEventRecord(h->evk1, st));
+        launches += 1 + nl;
+        if (timing) MLS_CUDA_TRY(cudaEventRecord(h->evk1, st));
       }
     }
-    if (h->desc.precision == MLS_P_FP32) MLS_CUDA_TRY(cudaEventRecord(h->evk1, st));
-    h->launches += 2;
+    launches += 2;
     // pixels handed over by the reduced-precision path: centroid-frame
     // recompute, and the pure FP64 kernel for what is left
     launch_handover(p, h->relist, h->counters, (int64_t)plane, h->relist2, h->counters + 1, st);
@@ -418,13 +444,34 @@ mls_status mls_render(mls_handle *h, const mls_view *view, void *field, uint8_t 
     launch_f64(q, 0, st);
   }
   MLS_CUDA_TRY(cudaGetLastError());
-  MLS_CUDA_TRY(cudaEventRecord(h->ev1, st));
-  h->timed = true;
+  if (timing) MLS_CUDA_TRY(cudaEventRecord(h->ev1, st));
+  h->timed = timing;
   h->last_pairs = (h->desc.weight == MLS_W_WENDLAND) ? 0 : (int64_t)plane * h->desc.n;
+  *nlaunch = launches;
+  return MLS_OK;
+}
+
+}  // namespace mlsi
+
+extern "C" {
+
+mls_status mls_render(mls_handle *h, const mls_view *view, void *field, uint8_t *status, const double *levels,
+                      int32_t L, uint8_t *bands, int32_t on_device, void *stream) {
+  g_err.clear();
+  cudaStream_t st = (cudaStream_t)stream;
+  mlsk::KParams p;
+  mls_status s = render_prepare(h, view, field, status, levels, L, bands, on_device, st, &p);
+  if (s != MLS_OK) return s;
+  h->stream = st;
+  int64_t nl = 0;
+  if ((s = render_enqueue(h, p, st, true, &nl)) != MLS_OK) return s;
+  h->launches += nl;
   if (!on_device) {
-    MLS_CUDA_TRY(cudaMemcpyAsync(field, field_d, plane * h->desc.D * esz, cudaMemcpyDeviceToHost, st));
-    if (status) MLS_CUDA_TRY(cudaMemcpyAsync(status, status_d, plane, cudaMemcpyDeviceToHost, st));
-    if (bands) MLS_CUDA_TRY(cudaMemcpyAsync(bands, bands_d, plane * h->desc.D, cudaMemcpyDeviceToHost, st));
+    const size_t plane = (size_t)view->W * view->H;
+    const size_t esz = h->desc.precision == MLS_P_FP64 ? sizeof(double) : sizeof(float);
+    MLS_CUDA_TRY(cudaMemcpyAsync(field, p.field, plane * h->desc.D * esz, cudaMemcpyDeviceToHost, st));
+    if (status) MLS_CUDA_TRY(cudaMemcpyAsync(status, p.status, plane, cudaMemcpyDeviceToHost, st));
+    if (bands) MLS_CUDA_TRY(cudaMemcpyAsync(bands, p.bands, plane * h->desc.D, cudaMemcpyDeviceToHost, st));
     MLS_CUDA_TRY(cudaStreamSynchronize(st));
     int err = 0;
     MLS_CUDA_TRY(cudaMemcpy(&err, h->err, sizeof(int), cudaMemcpyDeviceToHost));
@@ -520,6 +567,267 @@ mls_status mls_destroy(mls_handle *h) {
   if (h->evk1) cudaEventDestroy(h->evk1);
   cudaGetLastError();
   delete h;
+  return MLS_OK;
+}
+
+
+// ---------------------------------------------------------------------------
+// Batches: many resident datasets rendered by one CUDA graph.
+
+}  // extern "C"
+
+struct mls_batch {
+  std::vector<mls_handle *> hs;
+  int flags = 0;
+  cudaStream_t origin = nullptr;          // capture origin, level uploads
+  std::vector<cudaStream_t> child;        // one branch per dataset
+  cudaEvent_t fork = nullptr;
+  std::vector<cudaEvent_t> join;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  std::vector<uint64_t> sig;              // what the captured graph was built for
+  std::vector<int64_t> nl;                // kernels per dataset per render
+  cudaStream_t last = nullptr;
+  bool timed = false, tuned = false;
+  int64_t captures = 0, replays = 0;
+};
+
+namespace mlsi {
+
+static void batch_free(mls_batch *b) {
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  for (cudaStream_t c : b->child)
+    if (c) cudaStreamDestroy(c);
+  for (cudaEvent_t e : b->join)
+    if (e) cudaEventDestroy(e);
+  if (b->fork) cudaEventDestroy(b->fork);
+  if (b->ev0) cudaEventDestroy(b->ev0);
+  if (b->ev1) cudaEventDestroy(b->ev1);
+  if (b->origin) cudaStreamDestroy(b->origin);
+  cudaGetLastError();
+  delete b;
+}
+
+static void sig_push(std::vector<uint64_t> &v, const void *p) { v.push_back((uint64_t)(uintptr_t)p); }
+static void sig_push(std::vector<uint64_t> &v, double d) {
+  uint64_t u;
+  memcpy(&u, &d, sizeof u);
+  v.push_back(u);
+}
+
+// Autotuner: for each tensor-precision dataset, time split weights everywhere
+// (1) against the two-pass scheme (2) on the actual view and keep the faster.
+// Both meet the same error bound; which is faster depends on how many tiles
+// the single-weight pass queues.
+static mls_status batch_tune(mls_batch *b, const mls_view *views, void *const *fields, uint8_t *const *status,
+                             const double *const *levels, const int32_t *L, uint8_t *const *bands) {
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+    return cuda_fail(cudaGetLastError(), "cudaEventCreate");
+  mls_status s = MLS_OK;
+  for (size_t k = 0; k < b->hs.size() && s == MLS_OK; ++k) {
+    mls_handle *h = b->hs[k];
+    if (h->desc.precision != MLS_P_FP16 && h->desc.precision != MLS_P_BF16) continue;
+    float best = 1e30f;
+    int best_ws = h->desc.weight_split;
+    for (int ws = 1; ws <= 2 && s == MLS_OK; ++ws) {
+      h->desc.weight_split = ws;
+      mlsk::KParams p;
+      s = render_prepare(h, &views[k], fields[k], status ? status[k] : nullptr, levels ? levels[k] : nullptr,
+                         L ? L[k] : 0, bands ? bands[k] : nullptr, 1, b->origin, &p);
+      float t = 0.f;
+      for (int rep = 0; rep < 2 && s == MLS_OK; ++rep) {   // the first run warms up
+        int64_t nl = 0;
+        if (cudaEventRecord(e0, b->origin) != cudaSuccess) s = cuda_fail(cudaGetLastError(), "cudaEventRecord");
+        if (s == MLS_OK) s = render_enqueue(h, p, b->origin, false, &nl);
+        if (s == MLS_OK && cudaEventRecord(e1, b->origin) != cudaSuccess)
+          s = cuda_fail(cudaGetLastError(), "cudaEventRecord");
+        if (s == MLS_OK && cudaEventSynchronize(e1) != cudaSuccess)
+          s = cuda_fail(cudaGetLastError(), "cudaEventSynchronize");
+        if (s == MLS_OK) cudaEventElapsedTime(&t, e0, e1);
+        h->launches += nl;
+      }
+      if (s == MLS_OK && t < best) {
+        best = t;
+        best_ws = ws;
+      }
+    }
+    h->desc.weight_split = best_ws;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return s;
+}
+
+}  // namespace mlsi
+
+extern "C" {
+
+mls_status mls_batch_create(int32_t count, mls_handle *const *handles, int32_t flags, mls_batch **out) {
+  g_err.clear();
+  if (!out) return fail(MLS_E_INVAL, "out is NULL");
+  *out = nullptr;
+  if (count < 1 || count > 4096 || !handles) return fail(MLS_E_INVAL, "count must be in [1, 4096] with handles");
+  if (flags & ~MLS_BATCH_AUTOTUNE) return fail(MLS_E_INVAL, "unknown batch flags");
+  int dev = -1;
+  for (int k = 0; k < count; ++k) {
+    if (!handles[k]) return fail(MLS_E_INVAL, "a handle is NULL");
+    for (int j = 0; j < k; ++j)
+      if (handles[j] == handles[k]) return fail(MLS_E_INVAL, "a handle appears twice in the batch");
+    if (dev >= 0 && handles[k]->device != dev) return fail(MLS_E_INVAL, "handles live on different devices");
+    dev = handles[k]->device;
+  }
+  mls_batch *b = new mls_batch;
+  b->hs.assign(handles, handles + count);
+  b->flags = flags;
+  bool ok = cudaStreamCreateWithFlags(&b->origin, cudaStreamNonBlocking) == cudaSuccess &&
+            cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) == cudaSuccess &&
+            cudaEventCreate(&b->ev0) == cudaSuccess && cudaEventCreate(&b->ev1) == cudaSuccess;
+  b->child.assign(count, nullptr);
+  b->join.assign(count, nullptr);
+  for (int k = 0; k < count && ok; ++k)
+    ok = cudaStreamCreateWithFlags(&b->child[k], cudaStreamNonBlocking) == cudaSuccess &&
+         cudaEventCreateWithFlags(&b->join[k], cudaEventDisableTiming) == cudaSuccess;
+  if (!ok) {
+    mls_status s = cuda_fail(cudaGetLastError(), "batch streams and events");
+    batch_free(b);
+    return s;
+  }
+  *out = b;
+  return MLS_OK;
+}
+
+mls_status mls_batch_render(mls_batch *b, const mls_view *views, void *const *fields, uint8_t *const *status,
+                            const double *const *levels, const int32_t *L, uint8_t *const *bands, void *stream) {
+  g_err.clear();
+  if (!b || !views || !fields) return fail(MLS_E_INVAL, "batch, views and fields must not be NULL");
+  const size_t n = b->hs.size();
+  cudaStream_t st = (cudaStream_t)stream;
+  // host preparation is ordered after the previous batch render
+  if (b->timed) MLS_CUDA_TRY(cudaStreamWaitEvent(b->origin, b->ev1, 0));
+  mls_status s;
+  if ((b->flags & MLS_BATCH_AUTOTUNE) && !b->tuned) {
+    if ((s = batch_tune(b, views, fields, status, levels, L, bands)) != MLS_OK) return s;
+    b->tuned = true;
+  }
+  std::vector<mlsk::KParams> ps(n);
+  std::vector<uint64_t> sig;
+  for (size_t k = 0; k < n; ++k) {
+    mls_handle *h = b->hs[k];
+    s = render_prepare(h, &views[k], fields[k], status ? status[k] : nullptr, levels ? levels[k] : nullptr,
+                       L ? L[k] : 0, bands ? bands[k] : nullptr, 1, b->origin, &ps[k]);
+    if (s != MLS_OK) return fail(s, "dataset " + std::to_string(k) + ": " + g_err);
+    const mls_view &v = views[k];
+    sig.push_back(((uint64_t)(uint32_t)v.W << 32) | (uint32_t)v.H);
+    sig_push(sig, v.x0);
+    sig_push(sig, v.y0);
+    sig_push(sig, v.x1);
+    sig_push(sig, v.y1);
+    sig_push(sig, ps[k].field);
+    sig_push(sig, (const void *)ps[k].status);
+    sig_push(sig, (const void *)ps[k].bands);
+    sig.push_back((uint64_t)ps[k].L);
+    sig_push(sig, h->scratch);
+    sig_push(sig, (const void *)h->lev64);
+    sig_push(sig, (const void *)h->lev32);
+    sig.push_back((uint64_t)h->desc.weight_split);
+  }
+  // every upload has landed before the graph reads it
+  MLS_CUDA_TRY(cudaStreamSynchronize(b->origin));
+  if (!b->exec || sig != b->sig) {
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    b->exec = nullptr;
+    b->graph = nullptr;
+    b->nl.assign(n, 0);
+    MLS_CUDA_TRY(cudaStreamBeginCapture(b->origin, cudaStreamCaptureModeRelaxed));
+    mls_status cs = MLS_OK;
+    if (cudaEventRecord(b->fork, b->origin) != cudaSuccess) cs = cuda_fail(cudaGetLastError(), "fork");
+    for (size_t k = 0; k < n && cs == MLS_OK; ++k) {
+      if (cudaStreamWaitEvent(b->child[k], b->fork, 0) != cudaSuccess) {
+        cs = cuda_fail(cudaGetLastError(), "branch");
+        break;
+      }
+      cs = render_enqueue(b->hs[k], ps[k], b->child[k], false, &b->nl[k]);
+      if (cs == MLS_OK && (cudaEventRecord(b->join[k], b->child[k]) != cudaSuccess ||
+                           cudaStreamWaitEvent(b->origin, b->join[k], 0) != cudaSuccess))
+        cs = cuda_fail(cudaGetLastError(), "join");
+    }
+    cudaGraph_t g = nullptr;
+    const cudaError_t ec = cudaStreamEndCapture(b->origin, &g);
+    if (cs != MLS_OK) {
+      if (g) cudaGraphDestroy(g);
+      return cs;
+    }
+    if (ec != cudaSuccess) return cuda_fail(ec, "cudaStreamEndCapture");
+    b->graph = g;
+    MLS_CUDA_TRY(cudaGraphInstantiate(&b->exec, b->graph, 0));
+    b->sig = sig;
+    ++b->captures;
+  }
+  MLS_CUDA_TRY(cudaEventRecord(b->ev0, st));
+  MLS_CUDA_TRY(cudaGraphLaunch(b->exec, st));
+  MLS_CUDA_TRY(cudaEventRecord(b->ev1, st));
+  ++b->replays;
+  b->last = st;
+  b->timed = true;
+  for (size_t k = 0; k < n; ++k) {
+    b->hs[k]->stream = st;
+    b->hs[k]->launches += b->nl[k];
+  }
+  return MLS_OK;
+}
+
+mls_status mls_batch_sync(mls_batch *b, double timeout_s, mls_batch_stats *stats) {
+  g_err.clear();
+  if (!b) return fail(MLS_E_INVAL, "batch is NULL");
+  const auto t0 = std::chrono::steady_clock::now();
+  if (b->timed) {
+    for (;;) {
+      const cudaError_t e = cudaEventQuery(b->ev1);
+      if (e == cudaSuccess) break;
+      if (e != cudaErrorNotReady) return cuda_fail(e, "cudaEventQuery");
+      const double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+      if (el > timeout_s) return fail(MLS_E_TIMEOUT, "batch did not finish within the watchdog time");
+      std::this_thread::sleep_for(std::chrono::microseconds(50));
+    }
+  }
+  mls_batch_stats bs;
+  memset(&bs, 0, sizeof bs);
+  bs.datasets = (int64_t)b->hs.size();
+  int first_err = 0;
+  for (size_t k = 0; k < b->hs.size(); ++k) {
+    mls_handle *h = b->hs[k];
+    unsigned int cnt[3] = {0, 0, 0};
+    int err = 0;
+    if (h->scratch) {
+      MLS_CUDA_TRY(cudaMemcpy(cnt, h->counters, sizeof cnt, cudaMemcpyDeviceToHost));
+      MLS_CUDA_TRY(cudaMemcpy(&err, h->err, sizeof err, cudaMemcpyDeviceToHost));
+    }
+    bs.pairs += h->last_pairs;
+    bs.recomputed += cnt[0];
+    if (err && !first_err) first_err = err;
+    if (k < b->nl.size()) bs.launches += b->nl[k];
+  }
+  bs.device_error = first_err;
+  bs.captures = b->captures;
+  bs.replays = b->replays;
+  float ms = 0.f;
+  if (b->timed && cudaEventElapsedTime(&ms, b->ev0, b->ev1) == cudaSuccess) bs.last_render_ms = ms;
+  cudaGetLastError();
+  if (stats) *stats = bs;
+  if (first_err) return fail(MLS_E_TIMEOUT, "a bounded device wait gave up in the batch");
+  return MLS_OK;
+}
+
+mls_status mls_batch_destroy(mls_batch *b) {
+  g_err.clear();
+  if (!b) return MLS_OK;
+  if (b->timed) cudaEventSynchronize(b->ev1);
+  cudaStreamSynchronize(b->origin);
+  batch_free(b);
   return MLS_OK;
 }
 

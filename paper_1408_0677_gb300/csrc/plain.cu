@@ -57,8 +57,9 @@ __global__ __launch_bounds__(128) void k_mls_f32(KParams p) {
   const int t = threadIdx.x;
   const int u = blockIdx.x * 16 + (t & 15), v = blockIdx.y * 8 + (t >> 4);
   const bool inside = (u < p.W) && (v < p.H);
-  // moments in the frame of the tile's weighted centroid (see the prepass);
-  // (dpx, dpy) = pixel minus frame origin
+  // moments in the frame of the tile's weighted centroid (see the prepass),
+  // (dpx, dpy) = pixel minus frame origin; or, when the tile is large
+  // compared with h (p.pixel_frame), in each pixel's own frame
   const int tile = (int)(blockIdx.y >> 1) * p.tiles_x + (int)blockIdx.x;
   const float cxs = p.tcen[2 * tile], cys = p.tcen[2 * tile + 1];
   const float dpx = (float)((p.x0 + (u + 0.5) * p.sx - p.ctr_x) * p.inv_s - (double)cxs);
@@ -142,7 +143,8 @@ __global__ __launch_bounds__(128) void k_mls_f32(KParams p) {
             }
           }
           float mo[15];
-          monomials<NM>(dx, dy, mo);
+          if (p.pixel_frame) monomials<NM>(qx, qy, mo);
+          else monomials<NM>(dx, dy, mo);
 #pragma unroll
           for (int q = 0; q < NM; ++q) S[q] = fmaf(w, mo[q], S[q]);
 #pragma unroll
@@ -188,7 +190,8 @@ __global__ __launch_bounds__(128) void k_mls_f32(KParams p) {
     int degu = DEG;
     // the count rule of the degree policy; pixels whose count could differ
     // from the FP64 count at a degree threshold go to the FP64 path
-    if (!uncertain) outcome = solve_by_count<K>(count, S, dpx, dpy, z, p, &degu);
+    if (!uncertain)
+      outcome = solve_by_count<K>(count, S, p.pixel_frame ? 0.f : dpx, p.pixel_frame ? 0.f : dpy, z, p, &degu);
     if (outcome == SOLVE_RECOMPUTE) {
       write = false;
       if (d0 == 0) {

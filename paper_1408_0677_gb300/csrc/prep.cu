@@ -304,7 +304,10 @@ mls_status prep_points(mls_handle *h, const double *xy, const double *F, cudaStr
 
   // --- binning for the compact-support weight
   int *perm = nullptr;
-  if (d.weight == MLS_W_WENDLAND) {
+  // binning for the compact-support weight, and for the Gaussian (the
+  // hand-over path visits only the cells within its cut radius; the full-sum
+  // kernels read every point and do not depend on the order)
+  if (d.weight != MLS_W_INVDIST) {
     double cell = d.h;
     const double ex = hi[0] - lo[0], ey = hi[1] - lo[1];
     // keep the grid below 16M cells

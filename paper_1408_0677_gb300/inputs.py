@@ -165,6 +165,25 @@ def fourier_mix(seed: int, n: int, D: int, W: int, H: int, degree: int, weight: 
     return w
 
 
+def batch_datasets(seed: int = 1004, count: int = 64, n_range=(200, 50_000), D_range=(4, 64),
+                   side_range=(256, 1024)) -> list:
+    """Independent datasets for batched rendering: n log-uniform in n_range,
+    D uniform in D_range, a square grid with side uniform in side_range,
+    linear or quadratic basis, Gaussian h = 0.5 / sqrt(n), each with the
+    cluster + background structure and Fourier fields of fourier_mix."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for k in range(count):
+        n = int(round(np.exp(rng.uniform(np.log(n_range[0]), np.log(n_range[1])))))
+        D = int(rng.integers(D_range[0], D_range[1] + 1))
+        side = int(rng.integers(side_range[0], side_range[1] + 1))
+        degree = int(rng.integers(1, 3))
+        wl = fourier_mix(int(rng.integers(1 << 30)), n, D, side, side, degree, WEIGHT_GAUSS, 0.5 / np.sqrt(n))
+        wl.name = f"batch{k}_n{n}_d{D}_{side}sq_deg{degree}"
+        out.append(wl)
+    return out
+
+
 def small_random(seed: int, n: int, D: int, W: int, H: int, degree: int, weight: int,
                  h: float, L: int = 8, clustered: bool = True) -> Workload:
     """A small seeded case of the same structure, for tests."""

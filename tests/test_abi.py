@@ -108,6 +108,11 @@ def test_null_arguments(lib):
     assert lib.mls_bands(None, ctypes.byref(v), None, None, 0, None, 1, None) == _abi.MLS_E_INVAL
     assert lib.mls_sync(None, 1.0, None) == _abi.MLS_E_INVAL
     assert lib.mls_destroy(None) == _abi.MLS_OK
+    assert lib.mls_batch_create(0, None, 0, ctypes.byref(h)) == _abi.MLS_E_INVAL
+    assert lib.mls_batch_create(1, None, 0, None) == _abi.MLS_E_INVAL
+    assert lib.mls_batch_render(None, None, None, None, None, None, None, None) == _abi.MLS_E_INVAL
+    assert lib.mls_batch_sync(None, 1.0, None) == _abi.MLS_E_INVAL
+    assert lib.mls_batch_destroy(None) == _abi.MLS_OK
     assert lib.mls_debug_df_weight(3, None, None, 1, None) == _abi.MLS_E_INVAL
     assert lib.mls_debug_df_weight(0, None, None, 4, None) == _abi.MLS_E_INVAL
     assert lib.mls_debug_df_weight(0, None, None, 0, None) == _abi.MLS_OK

@@ -204,3 +204,13 @@ def test_injected_nomem_leaves_handle_usable(monkeypatch):
     r.sync()
     assert torch.isfinite(out["field"]).all()
     r.close()
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp16", "bf16"])
+@pytest.mark.parametrize("degree", [1, 2])
+def test_tiles_much_wider_than_h_use_pixel_frames(precision, degree):
+    """h far below the tile width (16 pixels span ~31 h): every pixel is
+    solved in its own frame on the CUDA-core path."""
+    wl = inputs.fourier_mix(51 + degree, 3000, 4, 64, 48, degree, G, 0.008)
+    res = gpu_render(wl, precision)
+    compare(wl, res, _ref(wl), precision)
