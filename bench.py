@@ -481,6 +481,101 @@ def run_batch(args):
     b.close()
 
 
+def run_serve(args):
+    """Serving: Poisson arrivals (200 requests/s) of iso-band renders of four
+    resident datasets (1M points each, D = 16, 64 clusters, quadratic,
+    Wendland radius 0.006), viewports 512^2-2048^2 over zoom windows of side
+    log-uniform in [1/16, 1]; continuous batching in the library's server.
+    Latency counts from each request's arrival time."""
+    import ctypes
+
+    import torch
+    world, rank, local = _dist()
+    torch.cuda.set_device(local)
+    from paper_1408_0677_gb300 import MlsRequest, MlsView, Renderer, Server, inputs
+    from paper_1408_0677_gb300._abi import mls_server_poll, mls_server_submit
+    rng = np.random.default_rng(1005)
+    dsets = []
+    for k in range(4):
+        r0 = np.random.default_rng(2000 + k)
+        centres = r0.uniform(0.1, 0.9, size=(64, 2))
+        xy = inputs._clusters(r0, 1_000_000, centres, r0.uniform(0.01, 0.05, size=64))
+        F = inputs._fourier_fields(r0, xy, 16, modes=8, max_freq=4)
+        lev = inputs.default_levels(F, 16)
+        r = Renderer(torch.from_numpy(xy).cuda(), torch.from_numpy(F).cuda(), degree=2,
+                     weight=inputs.WEIGHT_WENDLAND, h=0.006, precision=args.precision)
+        dsets.append((r, np.ascontiguousarray(lev)))
+    nreq = args.requests
+    arrivals = np.cumsum(rng.exponential(1.0 / args.rate, size=nreq))
+    specs = []
+    for _ in range(nreq):
+        k = int(rng.integers(4))
+        side = int(round(np.exp(rng.uniform(np.log(512), np.log(2048)))))
+        win = float(np.exp(rng.uniform(np.log(1 / 16), 0.0)))
+        x0, y0 = rng.uniform(0.0, 1.0 - win, size=2)
+        specs.append((k, side, (x0, y0, x0 + win, y0 + win)))
+    pool = [torch.empty(16 * 2048 * 2048, dtype=torch.uint8).pin_memory() for _ in range(args.slots * 4)]
+    free = list(range(len(pool)))
+    srv = Server(slots=args.slots, mem_budget=args.mem_gb << 30)
+    # warm-up: one request per dataset
+    for r, lev in dsets:
+        srv.submit(r, 256, 256, levels=lev)
+    srv.drain()
+    srv.poll()
+    inflight = {}
+    lat, queued, dev_ms, px_dims = [], [], [], 0
+    t0 = time.perf_counter()
+
+    def collect():
+        nonlocal px_dims
+        for d in mls_server_poll(srv.handle):
+            k, side, t_arr, buf = inflight.pop(d.id)
+            free.append(buf)
+            t_done = time.perf_counter() - t0
+            lat.append(1e3 * (t_done - t_arr))
+            queued.append(d.queued_ms)
+            dev_ms.append(d.device_ms)
+            px_dims += side * side * 16
+
+    for i, (k, side, view) in enumerate(specs):
+        while time.perf_counter() - t0 < arrivals[i]:
+            collect()
+            time.sleep(0.0002)
+        while not free:
+            collect()
+            time.sleep(0.0002)
+        buf = free.pop()
+        r, lev = dsets[k]
+        req = MlsRequest(r.handle, MlsView(side, side, *view), lev.ctypes.data, lev.shape[1], 0,
+                         pool[buf].data_ptr(), None, None)
+        rid = mls_server_submit(srv.handle, req)
+        inflight[rid] = (k, side, arrivals[i], buf)
+    while inflight:
+        collect()
+        time.sleep(0.0005)
+    wall = time.perf_counter() - t0
+    st = srv.drain()
+    srv.close()
+    if rank != 0:
+        return
+    value = px_dims / wall
+    line = {"metric": "served pixel*dim/s (iso-band renders)", "value": value, "unit": "pixel*dim/s",
+            "n_gpus": 1, "steps": nreq, "warmup": len(dsets), "ms_per_step": 1e3 * wall / nreq,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": args.precision,
+            "data": "synthetic",
+            "config": {"workload": "serve_poisson200_4x1M_d16_wendland_512-2048sq_zoom", "rate_per_s": args.rate,
+                       "requests": nreq, "slots": args.slots, "mem_budget_gb": args.mem_gb},
+            "requests_per_s": nreq / wall,
+            "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                           "what": "arrival to completion (bands on the host)"},
+            "queued_ms": {"p50": float(np.percentile(queued, 50)), "p99": float(np.percentile(queued, 99))},
+            "device_ms": {"p50": float(np.percentile(dev_ms, 50)), "p99": float(np.percentile(dev_ms, 99))},
+            "server": {"peak_inflight": int(st.peak_inflight), "peak_bytes": int(st.peak_bytes),
+                       "failed": int(st.failed)},
+            "e2e": None, "roofline": None, "cpu_baseline": None}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -492,8 +587,12 @@ def main():
     ap.add_argument("--weight-split", type=int, default=None, choices=[0, 1, 2])
     ap.add_argument("--no-compare-fp32", dest="compare_fp32", action="store_false",
                     help="skip the plain FP32 comparison run")
-    ap.add_argument("--workload", default="fourier10k", choices=["fourier10k", "batch64"],
-                    help="the 10k-point render (default) or 64 datasets in one graph")
+    ap.add_argument("--workload", default="fourier10k", choices=["fourier10k", "batch64", "serve"],
+                    help="the 10k-point render (default), 64 datasets in one graph, or the serving mix")
+    ap.add_argument("--rate", type=float, default=200.0, help="serve: requests per second")
+    ap.add_argument("--requests", type=int, default=400, help="serve: number of requests")
+    ap.add_argument("--slots", type=int, default=8, help="serve: requests in flight at most")
+    ap.add_argument("--mem-gb", type=int, default=16, help="serve: device memory budget (GiB)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -501,6 +600,8 @@ def main():
         run_reference(args)
     elif args.workload == "batch64":
         run_batch(args)
+    elif args.workload == "serve":
+        run_serve(args)
     else:
         run_ours(args)
 

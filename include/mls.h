@@ -237,6 +237,69 @@ mls_status mls_batch_sync(mls_batch *b, double timeout_s, mls_batch_stats *stats
 /* Release the batch (waits for its last render; the handles stay alive). */
 mls_status mls_batch_destroy(mls_batch *b);
 
+/* ---------------------------------------------------------------------------
+ * Serving (no counterpart in the paper, whose renders follow user
+ * interaction one at a time, Section 3.5): a worker thread admits render
+ * requests on resident datasets into a pool of stream slots while the
+ * requests already admitted hold less device memory than a budget.  Each
+ * admitted request gets its own scratch and outputs (stream-ordered
+ * allocations, freed when it completes), so requests on the same dataset
+ * overlap on the device and a request that arrives while others run starts
+ * as soon as a slot and memory are free (continuous batching).
+ */
+typedef struct mls_server mls_server;
+
+typedef struct mls_server_config {
+    int32_t slots;          /* requests in flight at most, 1 .. 64 */
+    int32_t reserved;
+    int64_t mem_budget;     /* device bytes the requests in flight may hold */
+} mls_server_config;
+
+typedef struct mls_request {
+    mls_handle *dataset;    /* resident dataset (mls_create), alive until the request completes */
+    mls_view view;
+    const double *levels;   /* host D x L doubles, copied at submit; NULL when L = 0 */
+    int32_t L;              /* 0 .. 254 */
+    int32_t reserved;
+    uint8_t *bands;         /* host D x H x W out (page-locked for overlap), or NULL */
+    uint8_t *status;        /* host H x W out, or NULL */
+    void *field;            /* host D x H x W float (double for FP64 datasets), or NULL */
+} mls_request;
+
+typedef struct mls_request_done {
+    int64_t id;
+    int32_t status;         /* mls_status of the request */
+    int32_t reserved;
+    double latency_ms;      /* submit to completion seen by the worker (host clock) */
+    double queued_ms;       /* submit to admission */
+    double device_ms;       /* its kernels and copies (events on its slot stream) */
+    int64_t footprint;      /* device bytes it held */
+} mls_request_done;
+
+typedef struct mls_server_stats {
+    int64_t submitted, completed, failed;
+    int64_t peak_inflight;  /* most requests in flight at once */
+    int64_t peak_bytes;     /* most device bytes held by requests in flight */
+} mls_server_stats;
+
+/* Start a server (worker thread on the current device).  Errors: MLS_E_INVAL, MLS_E_CUDA. */
+mls_status mls_server_create(const mls_server_config *cfg, mls_server **out);
+
+/* Queue a request (thread-safe, returns at once) and give its id.  The host
+ * output buffers must stay valid until it completes.  Errors: MLS_E_INVAL
+ * (bad view, levels or buffers), MLS_E_NOMEM (its footprint exceeds the
+ * whole budget). */
+mls_status mls_server_submit(mls_server *s, const mls_request *req, int64_t *id);
+
+/* Move up to `cap` completion records into done[] (*n receives the count). */
+mls_status mls_server_poll(mls_server *s, mls_request_done *done, int32_t cap, int32_t *n);
+
+/* Wait until every submitted request has completed (watchdog timeout_s). */
+mls_status mls_server_drain(mls_server *s, double timeout_s, mls_server_stats *stats);
+
+/* Drain, stop the worker and release the server. */
+mls_status mls_server_destroy(mls_server *s);
+
 /* Most levels (D * L) that mls_bands_noalloc accepts. */
 #define MLS_NOALLOC_MAX_LEVELS 4096
 

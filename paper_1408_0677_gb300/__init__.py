@@ -16,7 +16,8 @@ from ._abi import (MLS_P_BF16, MLS_P_FP16, MLS_P_FP32, MLS_P_FP64, MLS_W_GAUSS, 
                    MLS_W_WENDLAND, MLS_BATCH_AUTOTUNE, MlsBatchStats, MlsDesc, MlsError, MlsStats, MlsView,
                    mls_abi_version, mls_bands, mls_batch_create, mls_batch_destroy, mls_batch_render,
                    mls_batch_sync, mls_create, mls_desc_default, mls_destroy, mls_last_error, mls_render,
-                   mls_sync)
+                   mls_server_create, mls_server_destroy, mls_server_drain, mls_server_poll, mls_server_submit,
+                   mls_sync, MlsRequest)
 
 PRECISIONS = {"fp64": MLS_P_FP64, "fp32": MLS_P_FP32, "bf16": MLS_P_BF16, "fp16": MLS_P_FP16}
 
@@ -193,6 +194,69 @@ class Batch:
     def close(self):
         if getattr(self, "handle", None):
             mls_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Request:
+    """One submitted render request: its id, host outputs (page-locked) and,
+    once polled, its completion record."""
+
+    def __init__(self, rid, bands, status, field, keep):
+        self.id, self.bands, self.status, self.field = rid, bands, status, field
+        self._keep = keep
+        self.done = None
+
+
+class Server:
+    """Continuous-batching render server over resident datasets
+    (``mls_server_*``): requests are admitted into ``slots`` stream slots
+    while the requests in flight hold less than ``mem_budget`` device bytes;
+    ``submit`` returns at once, ``poll`` collects completions."""
+
+    def __init__(self, slots=4, mem_budget=4 << 30):
+        import torch
+        self.torch = torch
+        self.handle = mls_server_create(slots, mem_budget)
+        self.pending = {}
+
+    def submit(self, renderer, W, H, view=(0.0, 0.0, 1.0, 1.0), levels=None, field=False, status=True):
+        torch = self.torch
+        D = renderer.D
+        lev = None if levels is None else np.ascontiguousarray(levels, dtype=np.float64)
+        bands = torch.empty((D, H, W), dtype=torch.uint8).pin_memory() if lev is not None else None
+        st = torch.empty((H, W), dtype=torch.uint8).pin_memory() if status else None
+        fdt = torch.float64 if renderer.desc.precision == MLS_P_FP64 else torch.float32
+        fld = torch.empty((D, H, W), dtype=fdt).pin_memory() if field else None
+        req = MlsRequest(renderer.handle, MlsView(W, H, *view), lev.ctypes.data if lev is not None else None,
+                         lev.shape[1] if lev is not None else 0, 0,
+                         bands.data_ptr() if bands is not None else None, st.data_ptr() if st is not None else None,
+                         fld.data_ptr() if fld is not None else None)
+        rid = mls_server_submit(self.handle, req)
+        r = Request(rid, bands, st, fld, (lev, renderer))
+        self.pending[rid] = r
+        return r
+
+    def poll(self):
+        out = []
+        for d in mls_server_poll(self.handle):
+            r = self.pending.pop(d.id, None)
+            if r is not None:
+                r.done = d
+                out.append(r)
+        return out
+
+    def drain(self, timeout_s=300.0):
+        return mls_server_drain(self.handle, timeout_s)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            mls_server_destroy(self.handle)
             self.handle = None
 
     def __del__(self):

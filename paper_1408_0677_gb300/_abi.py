@@ -54,6 +54,27 @@ class MlsBatchStats(ctypes.Structure):
 MLS_BATCH_AUTOTUNE = 1
 
 
+class MlsServerConfig(ctypes.Structure):
+    _fields_ = [("slots", ctypes.c_int32), ("reserved", ctypes.c_int32), ("mem_budget", ctypes.c_int64)]
+
+
+class MlsRequest(ctypes.Structure):
+    _fields_ = [("dataset", ctypes.c_void_p), ("view", MlsView), ("levels", ctypes.c_void_p), ("L", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("bands", ctypes.c_void_p), ("status", ctypes.c_void_p),
+                ("field", ctypes.c_void_p)]
+
+
+class MlsRequestDone(ctypes.Structure):
+    _fields_ = [("id", ctypes.c_int64), ("status", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("latency_ms", ctypes.c_double), ("queued_ms", ctypes.c_double), ("device_ms", ctypes.c_double),
+                ("footprint", ctypes.c_int64)]
+
+
+class MlsServerStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64), ("failed", ctypes.c_int64),
+                ("peak_inflight", ctypes.c_int64), ("peak_bytes", ctypes.c_int64)]
+
+
 class MlsError(RuntimeError):
     def __init__(self, status: int, where: str, message: str):
         super().__init__(f"{where}: {STATUS_NAMES.get(status, status)}: {message}")
@@ -101,6 +122,16 @@ def load(path: str | None = None):
     lib.mls_batch_sync.argtypes = [P, ctypes.c_double, ctypes.POINTER(MlsBatchStats)]
     lib.mls_batch_destroy.restype = ctypes.c_int
     lib.mls_batch_destroy.argtypes = [P]
+    lib.mls_server_create.restype = ctypes.c_int
+    lib.mls_server_create.argtypes = [ctypes.POINTER(MlsServerConfig), ctypes.POINTER(P)]
+    lib.mls_server_submit.restype = ctypes.c_int
+    lib.mls_server_submit.argtypes = [P, ctypes.POINTER(MlsRequest), ctypes.POINTER(ctypes.c_int64)]
+    lib.mls_server_poll.restype = ctypes.c_int
+    lib.mls_server_poll.argtypes = [P, P, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]
+    lib.mls_server_drain.restype = ctypes.c_int
+    lib.mls_server_drain.argtypes = [P, ctypes.c_double, ctypes.POINTER(MlsServerStats)]
+    lib.mls_server_destroy.restype = ctypes.c_int
+    lib.mls_server_destroy.argtypes = [P]
     lib.mls_bands_noalloc.restype = ctypes.c_int
     lib.mls_bands_noalloc.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, P, ctypes.c_int32, P,
                                       ctypes.c_int32, P, P]
@@ -186,6 +217,36 @@ def mls_batch_sync(batch: int, timeout_s: float = 60.0) -> MlsBatchStats:
 
 def mls_batch_destroy(batch: int):
     _check(load().mls_batch_destroy(P(batch)), "mls_batch_destroy")
+
+
+def mls_server_create(slots: int, mem_budget: int) -> int:
+    cfg = MlsServerConfig(int(slots), 0, int(mem_budget))
+    out = P()
+    _check(load().mls_server_create(ctypes.byref(cfg), ctypes.byref(out)), "mls_server_create")
+    return out.value
+
+
+def mls_server_submit(server: int, req: MlsRequest) -> int:
+    rid = ctypes.c_int64()
+    _check(load().mls_server_submit(P(server), ctypes.byref(req), ctypes.byref(rid)), "mls_server_submit")
+    return rid.value
+
+
+def mls_server_poll(server: int, cap: int = 1024) -> list:
+    arr = (MlsRequestDone * cap)()
+    n = ctypes.c_int32()
+    _check(load().mls_server_poll(P(server), ctypes.cast(arr, P), int(cap), ctypes.byref(n)), "mls_server_poll")
+    return [arr[i] for i in range(n.value)]
+
+
+def mls_server_drain(server: int, timeout_s: float = 120.0) -> MlsServerStats:
+    st = MlsServerStats()
+    _check(load().mls_server_drain(P(server), float(timeout_s), ctypes.byref(st)), "mls_server_drain")
+    return st
+
+
+def mls_server_destroy(server: int):
+    _check(load().mls_server_destroy(P(server)), "mls_server_destroy")
 
 
 def mls_sync(handle: int, timeout_s: float = 60.0) -> MlsStats:

@@ -4,8 +4,12 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <atomic>
 #include <chrono>
 #include <cmath>
+#include <condition_variable>
+#include <deque>
+#include <mutex>
 #include <string>
 #include <thread>
 #include <vector>
@@ -44,6 +48,31 @@ mls_status dev_alloc(mls_handle *h, void **p, size_t bytes, cudaStream_t st) {
   return MLS_OK;
 }
 
+static mls_status ctx_alloc(RenderCtx *c, void **p, size_t bytes, cudaStream_t st) {
+  *p = nullptr;
+  if (inject_nomem()) return fail(MLS_E_NOMEM, "device allocation failed (MLS_INJECT_NOMEM)");
+  cudaError_t e = cudaMallocAsync(p, bytes ? bytes : 16, st);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync");
+  c->owned.push_back(*p);
+  return MLS_OK;
+}
+
+static void ctx_release(RenderCtx *c, void *p, cudaStream_t st) {
+  if (!p) return;
+  for (size_t i = 0; i < c->owned.size(); ++i)
+    if (c->owned[i] == p) {
+      c->owned.erase(c->owned.begin() + i);
+      break;
+    }
+  cudaFreeAsync(p, st);
+}
+
+// Free every allocation of a context (stream-ordered on st).
+static void ctx_free_all(RenderCtx *c, cudaStream_t st) {
+  for (void *p : c->owned) cudaFreeAsync(p, st);
+  *c = RenderCtx();
+}
+
 static void release(mls_handle *h, void *p, cudaStream_t st) {
   if (!p) return;
   for (size_t i = 0; i < h->owned.size(); ++i)
@@ -78,52 +107,60 @@ static mls_status check_levels(const double *levels, int L, int D) {
   return MLS_OK;
 }
 
-// Grow the per-render scratch of the handle to fit a view.
-static mls_status ensure_scratch(mls_handle *h, int W, int H, cudaStream_t st) {
+size_t scratch_bytes_for(int W, int H) {
   const int tx = (W + kTile - 1) / kTile, ty = (H + kTile - 1) / kTile;
   const size_t padded = (size_t)tx * kTile * ty * kTile;
   const size_t ntile = (size_t)tx * ty;
-  const size_t need = 256 + padded * sizeof(float) + padded * sizeof(int) + 2 * (size_t)W * H * sizeof(int) +
-                      2 * ntile * sizeof(float) + 2 * ntile * sizeof(int) + 256;
-  if (need <= h->scratch_bytes) return MLS_OK;
-  release(h, h->scratch, st);
-  h->scratch = nullptr;
-  h->scratch_bytes = 0;
-  void *p;
-  mls_status s = dev_alloc(h, &p, need, st);
-  if (s != MLS_OK) return s;
-  h->scratch = p;
-  h->scratch_bytes = need;
-  char *b = (char *)p;
-  h->counters = (unsigned int *)b;           // [0] hand-over count, [1] FP64 count, [2] retried tiles
-  h->err = (int *)(b + 64);
-  h->mstab = (float *)(b + 256);
-  h->cnt = (int *)(b + 256 + padded * sizeof(float));
-  h->relist = (int *)(b + 256 + padded * (sizeof(float) + sizeof(int)));
-  h->relist2 = h->relist + (size_t)W * H;
-  h->tcen = (float *)(h->relist2 + (size_t)W * H);
-  h->tile_mark = (int *)(h->tcen + 2 * ntile);
-  h->retry_tiles = h->tile_mark + ntile;
+  return 256 + padded * sizeof(float) + padded * sizeof(int) + 2 * (size_t)W * H * sizeof(int) +
+         2 * ntile * sizeof(float) + 2 * ntile * sizeof(int) + 256;
+}
+
+// Grow a render context's scratch to fit a view.
+static mls_status ensure_scratch(RenderCtx *c, int W, int H, cudaStream_t st) {
+  const int tx = (W + kTile - 1) / kTile, ty = (H + kTile - 1) / kTile;
+  const size_t padded = (size_t)tx * kTile * ty * kTile;
+  const size_t ntile = (size_t)tx * ty;
+  const size_t need = scratch_bytes_for(W, H);
+  if (need > c->scratch_bytes) {
+    ctx_release(c, c->scratch, st);
+    c->scratch = nullptr;
+    c->scratch_bytes = 0;
+    void *p;
+    mls_status s = ctx_alloc(c, &p, need, st);
+    if (s != MLS_OK) return s;
+    c->scratch = p;
+    c->scratch_bytes = need;
+  }
+  char *b = (char *)c->scratch;
+  c->counters = (unsigned int *)b;           // [0] hand-over count, [1] FP64 count, [2] retried tiles
+  c->err = (int *)(b + 64);
+  c->mstab = (float *)(b + 256);
+  c->cnt = (int *)(b + 256 + padded * sizeof(float));
+  c->relist = (int *)(b + 256 + padded * (sizeof(float) + sizeof(int)));
+  c->relist2 = c->relist + (size_t)W * H;
+  c->tcen = (float *)(c->relist2 + (size_t)W * H);
+  c->tile_mark = (int *)(c->tcen + 2 * ntile);
+  c->retry_tiles = c->tile_mark + ntile;
   return MLS_OK;
 }
 
-static mls_status upload_levels(mls_handle *h, const double *levels, int L, cudaStream_t st) {
+static mls_status upload_levels(mls_handle *h, RenderCtx *c, const double *levels, int L, cudaStream_t st) {
   const int D = h->desc.D;
   const size_t cnt = (size_t)D * L;
   if (cnt == 0) return MLS_OK;
-  if (cnt > h->lev_cap) {
-    release(h, h->lev64, st);
-    release(h, h->lev32, st);
-    h->lev64 = nullptr;
-    h->lev32 = nullptr;
-    h->lev_cap = 0;
+  if (cnt > c->lev_cap) {
+    ctx_release(c, c->lev64, st);
+    ctx_release(c, c->lev32, st);
+    c->lev64 = nullptr;
+    c->lev32 = nullptr;
+    c->lev_cap = 0;
     void *p;
     mls_status s;
-    if ((s = dev_alloc(h, &p, cnt * sizeof(double), st)) != MLS_OK) return s;
-    h->lev64 = (double *)p;
-    if ((s = dev_alloc(h, &p, cnt * sizeof(float), st)) != MLS_OK) return s;
-    h->lev32 = (float *)p;
-    h->lev_cap = cnt;
+    if ((s = ctx_alloc(c, &p, cnt * sizeof(double), st)) != MLS_OK) return s;
+    c->lev64 = (double *)p;
+    if ((s = ctx_alloc(c, &p, cnt * sizeof(float), st)) != MLS_OK) return s;
+    c->lev32 = (float *)p;
+    c->lev_cap = cnt;
   }
   // float copies rounded up: for a float f, f >= t exactly when f >= t_up
   static thread_local std::vector<float> up;
@@ -135,23 +172,23 @@ static mls_status upload_levels(mls_handle *h, const double *levels, int L, cuda
     if ((double)f < levels[i]) f = nextafterf(f, INFINITY);
     up[i] = f;
   }
-  MLS_CUDA_TRY(cudaMemcpyAsync(h->lev64, dn.data(), cnt * sizeof(double), cudaMemcpyHostToDevice, st));
-  MLS_CUDA_TRY(cudaMemcpyAsync(h->lev32, up.data(), cnt * sizeof(float), cudaMemcpyHostToDevice, st));
+  MLS_CUDA_TRY(cudaMemcpyAsync(c->lev64, dn.data(), cnt * sizeof(double), cudaMemcpyHostToDevice, st));
+  MLS_CUDA_TRY(cudaMemcpyAsync(c->lev32, up.data(), cnt * sizeof(float), cudaMemcpyHostToDevice, st));
   // pageable sources: make sure the copies have consumed them
   MLS_CUDA_TRY(cudaStreamSynchronize(st));
   return MLS_OK;
 }
 
-static mls_status ensure_stage(mls_handle *h, size_t bytes, cudaStream_t st) {
-  if (bytes <= h->stage_bytes) return MLS_OK;
-  release(h, h->stage, st);
-  h->stage = nullptr;
-  h->stage_bytes = 0;
+static mls_status ensure_stage(RenderCtx *c, size_t bytes, cudaStream_t st) {
+  if (bytes <= c->stage_bytes) return MLS_OK;
+  ctx_release(c, c->stage, st);
+  c->stage = nullptr;
+  c->stage_bytes = 0;
   void *p;
-  mls_status s = dev_alloc(h, &p, bytes, st);
+  mls_status s = ctx_alloc(c, &p, bytes, st);
   if (s != MLS_OK) return s;
-  h->stage = p;
-  h->stage_bytes = bytes;
+  c->stage = p;
+  c->stage_bytes = bytes;
   return MLS_OK;
 }
 
@@ -163,7 +200,7 @@ constexpr float kLambdaSplitFp16 = 200.f;
 // Tile width (16 pixels) in units of h above which the tile frame is not used.
 constexpr double kTileFrameMaxH = 4.0;
 
-static mlsk::KParams base_params(const mls_handle *h, const mls_view *v) {
+static mlsk::KParams base_params(const mls_handle *h, const RenderCtx *c, const mls_view *v) {
   const PointSet &P = h->P;
   const mls_desc &d = h->desc;
   mlsk::KParams p;
@@ -215,14 +252,14 @@ static mlsk::KParams base_params(const mls_handle *h, const mls_view *v) {
   p.inv_s = 1.0 / P.s;
   p.tiles_x = (v->W + kTile - 1) / kTile;
   p.tiles_y = (v->H + kTile - 1) / kTile;
-  p.mstab = h->mstab;
-  p.cnt = h->cnt;
-  p.tcen = h->tcen;
-  p.relist = h->relist;
-  p.relist_count = h->counters;
-  p.err = h->err;
-  p.lev64 = h->lev64;
-  p.lev32 = h->lev32;
+  p.mstab = c->mstab;
+  p.cnt = c->cnt;
+  p.tcen = c->tcen;
+  p.relist = c->relist;
+  p.relist_count = c->counters;
+  p.err = c->err;
+  p.lev64 = c->lev64;
+  p.lev32 = c->lev32;
   return p;
 }
 
@@ -339,9 +376,9 @@ namespace mlsi {
 // Host-side part of a render: validation, scratch, level upload, staging;
 // fills the kernel parameters.  Everything here may allocate or synchronise,
 // so none of it runs inside a stream capture.
-static mls_status render_prepare(mls_handle *h, const mls_view *view, void *field, uint8_t *status,
-                                 const double *levels, int32_t L, uint8_t *bands, int32_t on_device,
-                                 cudaStream_t st, mlsk::KParams *out) {
+static mls_status render_prepare(mls_handle *h, RenderCtx *c, const mls_view *view, void *field,
+                                 uint8_t *status, const double *levels, int32_t L, uint8_t *bands,
+                                 int32_t on_device, cudaStream_t st, mlsk::KParams *out) {
   if (!h) return fail(MLS_E_INVAL, "handle is NULL");
   mls_status s = check_view(view);
   if (s != MLS_OK) return s;
@@ -352,20 +389,20 @@ static mls_status render_prepare(mls_handle *h, const mls_view *view, void *fiel
   const size_t plane = (size_t)W * H;
   const bool fp64 = h->desc.precision == MLS_P_FP64;
   const size_t esz = fp64 ? sizeof(double) : sizeof(float);
-  if ((s = ensure_scratch(h, W, H, st)) != MLS_OK) return s;
-  if (bands && L > 0 && (s = upload_levels(h, levels, L, st)) != MLS_OK) return s;
+  if ((s = ensure_scratch(c, W, H, st)) != MLS_OK) return s;
+  if (bands && L > 0 && (s = upload_levels(h, c, levels, L, st)) != MLS_OK) return s;
   void *field_d = field;
   uint8_t *status_d = status, *bands_d = bands;
   if (!on_device) {
     const size_t fbytes = (plane * h->desc.D * esz + 255) / 256 * 256;
     const size_t sbytes = (plane + 255) / 256 * 256;
     const size_t bbytes = bands ? plane * h->desc.D : 0;
-    if ((s = ensure_stage(h, fbytes + sbytes + bbytes, st)) != MLS_OK) return s;
-    field_d = h->stage;
-    status_d = status ? (uint8_t *)h->stage + fbytes : nullptr;
-    bands_d = bands ? (uint8_t *)h->stage + fbytes + sbytes : nullptr;
+    if ((s = ensure_stage(c, fbytes + sbytes + bbytes, st)) != MLS_OK) return s;
+    field_d = c->stage;
+    status_d = status ? (uint8_t *)c->stage + fbytes : nullptr;
+    bands_d = bands ? (uint8_t *)c->stage + fbytes + sbytes : nullptr;
   }
-  mlsk::KParams p = base_params(h, view);
+  mlsk::KParams p = base_params(h, c, view);
   p.field = field_d;
   p.field_fp64 = fp64 ? 1 : 0;
   p.status = status_d;
@@ -378,13 +415,13 @@ static mls_status render_prepare(mls_handle *h, const mls_view *view, void *fiel
 // Device part of a render: memsets and kernel launches only (capturable in
 // a CUDA graph).  With `timing` the handle's events bracket the render and
 // its main kernel.  *nlaunch receives the kernels launched.
-static mls_status render_enqueue(mls_handle *h, const mlsk::KParams &p, cudaStream_t st, bool timing,
-                                 int64_t *nlaunch) {
+static mls_status render_enqueue(mls_handle *h, RenderCtx *c, const mlsk::KParams &p, cudaStream_t st,
+                                 bool timing, int64_t *nlaunch) {
   mls_status s;
   const size_t plane = (size_t)p.W * p.H;
   const bool fp64 = h->desc.precision == MLS_P_FP64;
   int64_t launches = 0;
-  MLS_CUDA_TRY(cudaMemsetAsync(h->scratch, 0, 256, st));
+  MLS_CUDA_TRY(cudaMemsetAsync(c->scratch, 0, 256, st));
   if (timing) MLS_CUDA_TRY(cudaEventRecord(h->ev0, st));
   if (fp64) {
     if (timing) MLS_CUDA_TRY(cudaEventRecord(h->evk0, st));
@@ -412,18 +449,18 @@ static mls_status render_enqueue(mls_handle *h, const mlsk::KParams &p, cudaStre
         // single weights everywhere; tiles with a failing pixel are queued
         // and rendered again with split weights
         const int ntile = p.tiles_x * p.tiles_y;
-        MLS_CUDA_TRY(cudaMemsetAsync(h->tile_mark, 0, sizeof(int) * ntile, st));
+        MLS_CUDA_TRY(cudaMemsetAsync(c->tile_mark, 0, sizeof(int) * ntile, st));
         mlsk::KParams p1 = p;
-        p1.retry_tiles = h->retry_tiles;
-        p1.retry_count = h->counters + 2;
-        p1.tile_mark = h->tile_mark;
+        p1.retry_tiles = c->retry_tiles;
+        p1.retry_count = c->counters + 2;
+        p1.tile_mark = c->tile_mark;
         if ((s = launch_tc(p1, fp16, 0, st, &nl)) != MLS_OK) return s;
         launches += 1 + nl;
         if (timing) MLS_CUDA_TRY(cudaEventRecord(h->evk1, st));   // main kernel: the pass over every tile
         mlsk::KParams p2 = p;
         p2.lambda_max = fp16 ? kLambdaSplitFp16 : 50.f;
-        p2.tile_list = h->retry_tiles;
-        p2.tile_count = h->counters + 2;
+        p2.tile_list = c->retry_tiles;
+        p2.tile_count = c->counters + 2;
         if ((s = launch_tc(p2, fp16, 1, st, &nl)) != MLS_OK) return s;
         launches += nl;
       } else {
@@ -435,10 +472,10 @@ static mls_status render_enqueue(mls_handle *h, const mlsk::KParams &p, cudaStre
     launches += 2;
     // pixels handed over by the reduced-precision path: centroid-frame
     // recompute, and the pure FP64 kernel for what is left
-    launch_handover(p, h->relist, h->counters, (int64_t)plane, h->relist2, h->counters + 1, st);
+    launch_handover(p, c->relist, c->counters, (int64_t)plane, c->relist2, c->counters + 1, st);
     mlsk::KParams q = p;
-    q.list = h->relist2;
-    q.list_count = h->counters + 1;
+    q.list = c->relist2;
+    q.list_count = c->counters + 1;
     q.list_cap = (int64_t)plane;
     q.field_fp64 = 0;
     launch_f64(q, 0, st);
@@ -460,11 +497,12 @@ mls_status mls_render(mls_handle *h, const mls_view *view, void *field, uint8_t 
   g_err.clear();
   cudaStream_t st = (cudaStream_t)stream;
   mlsk::KParams p;
-  mls_status s = render_prepare(h, view, field, status, levels, L, bands, on_device, st, &p);
+  if (!h) return fail(MLS_E_INVAL, "handle is NULL");
+  mls_status s = render_prepare(h, &h->ctx, view, field, status, levels, L, bands, on_device, st, &p);
   if (s != MLS_OK) return s;
   h->stream = st;
   int64_t nl = 0;
-  if ((s = render_enqueue(h, p, st, true, &nl)) != MLS_OK) return s;
+  if ((s = render_enqueue(h, &h->ctx, p, st, true, &nl)) != MLS_OK) return s;
   h->launches += nl;
   if (!on_device) {
     const size_t plane = (size_t)view->W * view->H;
@@ -474,7 +512,7 @@ mls_status mls_render(mls_handle *h, const mls_view *view, void *field, uint8_t 
     if (bands) MLS_CUDA_TRY(cudaMemcpyAsync(bands, p.bands, plane * h->desc.D, cudaMemcpyDeviceToHost, st));
     MLS_CUDA_TRY(cudaStreamSynchronize(st));
     int err = 0;
-    MLS_CUDA_TRY(cudaMemcpy(&err, h->err, sizeof(int), cudaMemcpyDeviceToHost));
+    MLS_CUDA_TRY(cudaMemcpy(&err, h->ctx.err, sizeof(int), cudaMemcpyDeviceToHost));
     if (err) return fail(MLS_E_TIMEOUT, "a bounded device wait gave up (error word " + std::to_string(err) + ")");
   }
   return MLS_OK;
@@ -493,18 +531,18 @@ mls_status mls_bands(mls_handle *h, const mls_view *view, const void *field, con
   const size_t plane = (size_t)view->W * view->H;
   const bool fp64 = h->desc.precision == MLS_P_FP64;
   const size_t esz = fp64 ? sizeof(double) : sizeof(float);
-  if ((s = ensure_scratch(h, view->W, view->H, st)) != MLS_OK) return s;
-  if (L > 0 && (s = upload_levels(h, levels, L, st)) != MLS_OK) return s;
+  if ((s = ensure_scratch(&h->ctx, view->W, view->H, st)) != MLS_OK) return s;
+  if (L > 0 && (s = upload_levels(h, &h->ctx, levels, L, st)) != MLS_OK) return s;
   const void *field_d = field;
   uint8_t *bands_d = bands;
   if (!on_device) {
     const size_t fbytes = (plane * h->desc.D * esz + 255) / 256 * 256;
-    if ((s = ensure_stage(h, fbytes + plane * h->desc.D, st)) != MLS_OK) return s;
-    field_d = h->stage;
-    bands_d = (uint8_t *)h->stage + fbytes;
+    if ((s = ensure_stage(&h->ctx, fbytes + plane * h->desc.D, st)) != MLS_OK) return s;
+    field_d = h->ctx.stage;
+    bands_d = (uint8_t *)h->ctx.stage + fbytes;
     MLS_CUDA_TRY(cudaMemcpyAsync((void *)field_d, field, plane * h->desc.D * esz, cudaMemcpyHostToDevice, st));
   }
-  mlsk::KParams p = base_params(h, view);
+  mlsk::KParams p = base_params(h, &h->ctx, view);
   p.field = (void *)field_d;
   p.field_fp64 = fp64 ? 1 : 0;
   p.bands = bands_d;
@@ -533,9 +571,9 @@ mls_status mls_sync(mls_handle *h, double timeout_s, mls_stats *stats) {
   }
   unsigned int cnt[3] = {0, 0, 0};
   int err = 0;
-  if (h->scratch) {
-    MLS_CUDA_TRY(cudaMemcpy(cnt, h->counters, sizeof cnt, cudaMemcpyDeviceToHost));
-    MLS_CUDA_TRY(cudaMemcpy(&err, h->err, sizeof err, cudaMemcpyDeviceToHost));
+  if (h->ctx.scratch) {
+    MLS_CUDA_TRY(cudaMemcpy(cnt, h->ctx.counters, sizeof cnt, cudaMemcpyDeviceToHost));
+    MLS_CUDA_TRY(cudaMemcpy(&err, h->ctx.err, sizeof err, cudaMemcpyDeviceToHost));
   }
   if (stats) {
     memset(stats, 0, sizeof *stats);
@@ -560,6 +598,7 @@ mls_status mls_destroy(mls_handle *h) {
   cudaStream_t st = h->stream;
   cudaStreamSynchronize(st);
   for (void *p : h->owned) cudaFreeAsync(p, st);
+  ctx_free_all(&h->ctx, st);
   cudaStreamSynchronize(st);
   if (h->ev0) cudaEventDestroy(h->ev0);
   if (h->ev1) cudaEventDestroy(h->ev1);
@@ -635,13 +674,13 @@ static mls_status batch_tune(mls_batch *b, const mls_view *views, void *const *f
     for (int ws = 1; ws <= 2 && s == MLS_OK; ++ws) {
       h->desc.weight_split = ws;
       mlsk::KParams p;
-      s = render_prepare(h, &views[k], fields[k], status ? status[k] : nullptr, levels ? levels[k] : nullptr,
+      s = render_prepare(h, &h->ctx, &views[k], fields[k], status ? status[k] : nullptr, levels ? levels[k] : nullptr,
                          L ? L[k] : 0, bands ? bands[k] : nullptr, 1, b->origin, &p);
       float t = 0.f;
       for (int rep = 0; rep < 2 && s == MLS_OK; ++rep) {   // the first run warms up
         int64_t nl = 0;
         if (cudaEventRecord(e0, b->origin) != cudaSuccess) s = cuda_fail(cudaGetLastError(), "cudaEventRecord");
-        if (s == MLS_OK) s = render_enqueue(h, p, b->origin, false, &nl);
+        if (s == MLS_OK) s = render_enqueue(h, &h->ctx, p, b->origin, false, &nl);
         if (s == MLS_OK && cudaEventRecord(e1, b->origin) != cudaSuccess)
           s = cuda_fail(cudaGetLastError(), "cudaEventRecord");
         if (s == MLS_OK && cudaEventSynchronize(e1) != cudaSuccess)
@@ -716,7 +755,7 @@ mls_status mls_batch_render(mls_batch *b, const mls_view *views, void *const *fi
   std::vector<uint64_t> sig;
   for (size_t k = 0; k < n; ++k) {
     mls_handle *h = b->hs[k];
-    s = render_prepare(h, &views[k], fields[k], status ? status[k] : nullptr, levels ? levels[k] : nullptr,
+    s = render_prepare(h, &h->ctx, &views[k], fields[k], status ? status[k] : nullptr, levels ? levels[k] : nullptr,
                        L ? L[k] : 0, bands ? bands[k] : nullptr, 1, b->origin, &ps[k]);
     if (s != MLS_OK) return fail(s, "dataset " + std::to_string(k) + ": " + g_err);
     const mls_view &v = views[k];
@@ -729,9 +768,9 @@ mls_status mls_batch_render(mls_batch *b, const mls_view *views, void *const *fi
     sig_push(sig, (const void *)ps[k].status);
     sig_push(sig, (const void *)ps[k].bands);
     sig.push_back((uint64_t)ps[k].L);
-    sig_push(sig, h->scratch);
-    sig_push(sig, (const void *)h->lev64);
-    sig_push(sig, (const void *)h->lev32);
+    sig_push(sig, h->ctx.scratch);
+    sig_push(sig, (const void *)h->ctx.lev64);
+    sig_push(sig, (const void *)h->ctx.lev32);
     sig.push_back((uint64_t)h->desc.weight_split);
   }
   // every upload has landed before the graph reads it
@@ -750,7 +789,7 @@ mls_status mls_batch_render(mls_batch *b, const mls_view *views, void *const *fi
         cs = cuda_fail(cudaGetLastError(), "branch");
         break;
       }
-      cs = render_enqueue(b->hs[k], ps[k], b->child[k], false, &b->nl[k]);
+      cs = render_enqueue(b->hs[k], &b->hs[k]->ctx, ps[k], b->child[k], false, &b->nl[k]);
       if (cs == MLS_OK && (cudaEventRecord(b->join[k], b->child[k]) != cudaSuccess ||
                            cudaStreamWaitEvent(b->origin, b->join[k], 0) != cudaSuccess))
         cs = cuda_fail(cudaGetLastError(), "join");
@@ -802,9 +841,9 @@ mls_status mls_batch_sync(mls_batch *b, double timeout_s, mls_batch_stats *stats
     mls_handle *h = b->hs[k];
     unsigned int cnt[3] = {0, 0, 0};
     int err = 0;
-    if (h->scratch) {
-      MLS_CUDA_TRY(cudaMemcpy(cnt, h->counters, sizeof cnt, cudaMemcpyDeviceToHost));
-      MLS_CUDA_TRY(cudaMemcpy(&err, h->err, sizeof err, cudaMemcpyDeviceToHost));
+    if (h->ctx.scratch) {
+      MLS_CUDA_TRY(cudaMemcpy(cnt, h->ctx.counters, sizeof cnt, cudaMemcpyDeviceToHost));
+      MLS_CUDA_TRY(cudaMemcpy(&err, h->ctx.err, sizeof err, cudaMemcpyDeviceToHost));
     }
     bs.pairs += h->last_pairs;
     bs.recomputed += cnt[0];
@@ -828,6 +867,298 @@ mls_status mls_batch_destroy(mls_batch *b) {
   if (b->timed) cudaEventSynchronize(b->ev1);
   cudaStreamSynchronize(b->origin);
   batch_free(b);
+  return MLS_OK;
+}
+
+
+// ---------------------------------------------------------------------------
+// Serving: a worker thread, a FIFO of requests, a pool of stream slots and a
+// device-memory budget.
+
+}  // extern "C"
+
+namespace mlsi {
+
+using Clock = std::chrono::steady_clock;
+
+struct ServeReq {
+  int64_t id;
+  mls_request r;
+  std::vector<double> levels;        // copied at submit
+  int64_t footprint;
+  Clock::time_point t_submit, t_admit;
+};
+
+struct ServeSlot {
+  cudaStream_t st = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  bool busy = false;
+  ServeReq req;
+  RenderCtx ctx;
+  void *out = nullptr;               // device outputs of the request
+};
+
+}  // namespace mlsi
+
+struct mls_server {
+  mls_server_config cfg;
+  int device = 0;
+  std::mutex mu;
+  std::condition_variable cv;
+  std::deque<mlsi::ServeReq> queue;
+  std::vector<mlsi::ServeSlot> slots;
+  std::vector<mls_request_done> done;
+  int64_t next_id = 1, submitted = 0, completed = 0, failed = 0;
+  int64_t inflight = 0, bytes = 0, peak_inflight = 0, peak_bytes = 0;
+  bool stop = false;
+  std::thread worker;
+};
+
+namespace mlsi {
+
+static size_t out_bytes(const mls_handle *h, const mls_view &v, size_t *fbytes, size_t *sbytes) {
+  const size_t plane = (size_t)v.W * v.H;
+  const size_t esz = h->desc.precision == MLS_P_FP64 ? sizeof(double) : sizeof(float);
+  *fbytes = (plane * h->desc.D * esz + 255) / 256 * 256;
+  *sbytes = (plane + 255) / 256 * 256;
+  return *fbytes + *sbytes + plane * h->desc.D;
+}
+
+static int64_t footprint(const mls_request &r) {
+  size_t fb, sb;
+  return (int64_t)(scratch_bytes_for(r.view.W, r.view.H) + out_bytes(r.dataset, r.view, &fb, &sb) +
+                   (size_t)r.dataset->desc.D * r.L * (sizeof(double) + sizeof(float)) + 4096);
+}
+
+// Start an admitted request on its slot (worker thread).
+static mls_status serve_start(ServeSlot &sl) {
+  mls_request &r = sl.req.r;
+  mls_handle *h = r.dataset;
+  size_t fbytes, sbytes;
+  const size_t ob = out_bytes(h, r.view, &fbytes, &sbytes);
+  mls_status s = ctx_alloc(&sl.ctx, &sl.out, ob, sl.st);
+  if (s != MLS_OK) return s;
+  char *o = (char *)sl.out;
+  void *field_d = o;
+  uint8_t *status_d = (uint8_t *)(o + fbytes);
+  uint8_t *bands_d = r.L > 0 ? (uint8_t *)(o + fbytes + sbytes) : nullptr;
+  mlsk::KParams p;
+  s = render_prepare(h, &sl.ctx, &r.view, field_d, status_d, r.L > 0 ? sl.req.levels.data() : nullptr, r.L,
+                     bands_d, 1, sl.st, &p);
+  if (s != MLS_OK) return s;
+  MLS_CUDA_TRY(cudaEventRecord(sl.e0, sl.st));
+  int64_t nl = 0;
+  if ((s = render_enqueue(h, &sl.ctx, p, sl.st, false, &nl)) != MLS_OK) return s;
+  const size_t plane = (size_t)r.view.W * r.view.H;
+  const size_t esz = h->desc.precision == MLS_P_FP64 ? sizeof(double) : sizeof(float);
+  if (r.field) MLS_CUDA_TRY(cudaMemcpyAsync(r.field, field_d, plane * h->desc.D * esz, cudaMemcpyDeviceToHost, sl.st));
+  if (r.status) MLS_CUDA_TRY(cudaMemcpyAsync(r.status, status_d, plane, cudaMemcpyDeviceToHost, sl.st));
+  if (r.bands && bands_d)
+    MLS_CUDA_TRY(cudaMemcpyAsync(r.bands, bands_d, plane * h->desc.D, cudaMemcpyDeviceToHost, sl.st));
+  MLS_CUDA_TRY(cudaEventRecord(sl.e1, sl.st));
+  return MLS_OK;
+}
+
+static void serve_finish(mls_server *sv, ServeSlot &sl, mls_status st) {
+  mls_request_done d;
+  memset(&d, 0, sizeof d);
+  d.id = sl.req.id;
+  int err = 0;
+  if (st == MLS_OK && sl.ctx.err && cudaMemcpy(&err, sl.ctx.err, sizeof err, cudaMemcpyDeviceToHost) == cudaSuccess &&
+      err)
+    st = MLS_E_TIMEOUT;
+  float ms = 0.f;
+  if (st == MLS_OK && cudaEventElapsedTime(&ms, sl.e0, sl.e1) == cudaSuccess) d.device_ms = ms;
+  const auto now = Clock::now();
+  d.status = st;
+  d.latency_ms = std::chrono::duration<double, std::milli>(now - sl.req.t_submit).count();
+  d.queued_ms = std::chrono::duration<double, std::milli>(sl.req.t_admit - sl.req.t_submit).count();
+  d.footprint = sl.req.footprint;
+  ctx_free_all(&sl.ctx, sl.st);
+  sl.out = nullptr;
+  cudaGetLastError();
+  std::lock_guard<std::mutex> lk(sv->mu);
+  sv->done.push_back(d);
+  ++sv->completed;
+  if (st != MLS_OK) ++sv->failed;
+  --sv->inflight;
+  sv->bytes -= sl.req.footprint;
+  sl.busy = false;
+  sv->cv.notify_all();
+}
+
+static void serve_loop(mls_server *sv) {
+  cudaSetDevice(sv->device);
+  for (;;) {
+    // completions
+    bool any_busy = false;
+    for (ServeSlot &sl : sv->slots) {
+      if (!sl.busy) continue;
+      const cudaError_t e = cudaEventQuery(sl.e1);
+      if (e == cudaSuccess) serve_finish(sv, sl, MLS_OK);
+      else if (e != cudaErrorNotReady) serve_finish(sv, sl, cuda_fail(e, "request"));
+      else any_busy = true;
+    }
+    // admissions: FIFO head while a slot and the memory budget allow
+    for (;;) {
+      ServeSlot *free_slot = nullptr;
+      ServeReq req;
+      {
+        std::unique_lock<std::mutex> lk(sv->mu);
+        if (sv->queue.empty()) break;
+        for (ServeSlot &sl : sv->slots)
+          if (!sl.busy) {
+            free_slot = &sl;
+            break;
+          }
+        if (!free_slot || sv->bytes + sv->queue.front().footprint > sv->cfg.mem_budget) break;
+        req = std::move(sv->queue.front());
+        sv->queue.pop_front();
+        ++sv->inflight;
+        sv->bytes += req.footprint;
+        sv->peak_inflight = std::max(sv->peak_inflight, sv->inflight);
+        sv->peak_bytes = std::max(sv->peak_bytes, sv->bytes);
+        free_slot->busy = true;
+      }
+      req.t_admit = Clock::now();
+      free_slot->req = std::move(req);
+      const mls_status st = serve_start(*free_slot);
+      if (st != MLS_OK) {
+        cudaStreamSynchronize(free_slot->st);
+        serve_finish(sv, *free_slot, st);
+      } else {
+        any_busy = true;
+      }
+    }
+    {
+      std::unique_lock<std::mutex> lk(sv->mu);
+      if (sv->stop && sv->queue.empty() && sv->inflight == 0) break;
+      if (!any_busy && sv->queue.empty() && !sv->stop) {
+        sv->cv.wait_for(lk, std::chrono::milliseconds(5));
+        continue;
+      }
+    }
+    std::this_thread::sleep_for(std::chrono::microseconds(20));
+  }
+}
+
+}  // namespace mlsi
+
+extern "C" {
+
+mls_status mls_server_create(const mls_server_config *cfg, mls_server **out) {
+  g_err.clear();
+  if (!out || !cfg) return fail(MLS_E_INVAL, "cfg and out must not be NULL");
+  *out = nullptr;
+  if (cfg->slots < 1 || cfg->slots > 64) return fail(MLS_E_INVAL, "slots must be in [1, 64]");
+  if (cfg->mem_budget < (1 << 20)) return fail(MLS_E_INVAL, "mem_budget must be at least 1 MiB");
+  mls_server *sv = new mls_server;
+  sv->cfg = *cfg;
+  MLS_CUDA_TRY(cudaGetDevice(&sv->device));
+  sv->slots.resize(cfg->slots);
+  bool ok = true;
+  for (ServeSlot &sl : sv->slots)
+    ok = ok && cudaStreamCreateWithFlags(&sl.st, cudaStreamNonBlocking) == cudaSuccess &&
+         cudaEventCreate(&sl.e0) == cudaSuccess && cudaEventCreate(&sl.e1) == cudaSuccess;
+  if (!ok) {
+    mls_status s = cuda_fail(cudaGetLastError(), "server streams");
+    for (ServeSlot &sl : sv->slots) {
+      if (sl.st) cudaStreamDestroy(sl.st);
+      if (sl.e0) cudaEventDestroy(sl.e0);
+      if (sl.e1) cudaEventDestroy(sl.e1);
+    }
+    delete sv;
+    return s;
+  }
+  // freed request memory stays in the stream-ordered pool for the next one
+  cudaMemPool_t pool;
+  if (cudaDeviceGetDefaultMemPool(&pool, sv->device) == cudaSuccess) {
+    uint64_t keep = (uint64_t)cfg->mem_budget;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+  }
+  cudaGetLastError();
+  sv->worker = std::thread(serve_loop, sv);
+  *out = sv;
+  return MLS_OK;
+}
+
+mls_status mls_server_submit(mls_server *sv, const mls_request *req, int64_t *id) {
+  g_err.clear();
+  if (!sv || !req || !id) return fail(MLS_E_INVAL, "server, request and id must not be NULL");
+  if (!req->dataset) return fail(MLS_E_INVAL, "request has no dataset");
+  mls_status s = check_view(&req->view);
+  if (s != MLS_OK) return s;
+  if ((s = check_levels(req->levels, req->L, req->dataset->desc.D)) != MLS_OK) return s;
+  if (req->bands && req->L < 1) return fail(MLS_E_INVAL, "bands need levels");
+  ServeReq q;
+  q.r = *req;
+  if (req->L > 0) q.levels.assign(req->levels, req->levels + (size_t)req->dataset->desc.D * req->L);
+  q.r.levels = nullptr;
+  q.footprint = footprint(*req);
+  if (q.footprint > sv->cfg.mem_budget)
+    return fail(MLS_E_NOMEM, "request needs " + std::to_string(q.footprint) + " device bytes, more than the budget");
+  q.t_submit = Clock::now();
+  {
+    std::lock_guard<std::mutex> lk(sv->mu);
+    q.id = sv->next_id++;
+    *id = q.id;
+    ++sv->submitted;
+    sv->queue.push_back(std::move(q));
+  }
+  sv->cv.notify_all();
+  return MLS_OK;
+}
+
+mls_status mls_server_poll(mls_server *sv, mls_request_done *done, int32_t cap, int32_t *n) {
+  g_err.clear();
+  if (!sv || !n || (cap > 0 && !done)) return fail(MLS_E_INVAL, "server, done and n must not be NULL");
+  std::lock_guard<std::mutex> lk(sv->mu);
+  const int32_t k = (int32_t)std::min<size_t>((size_t)std::max(cap, 0), sv->done.size());
+  for (int32_t i = 0; i < k; ++i) done[i] = sv->done[i];
+  sv->done.erase(sv->done.begin(), sv->done.begin() + k);
+  *n = k;
+  return MLS_OK;
+}
+
+mls_status mls_server_drain(mls_server *sv, double timeout_s, mls_server_stats *stats) {
+  g_err.clear();
+  if (!sv) return fail(MLS_E_INVAL, "server is NULL");
+  const auto t0 = Clock::now();
+  std::unique_lock<std::mutex> lk(sv->mu);
+  while (sv->completed < sv->submitted) {
+    if (std::chrono::duration<double>(Clock::now() - t0).count() > timeout_s)
+      return fail(MLS_E_TIMEOUT, "requests did not complete within the watchdog time");
+    sv->cv.wait_for(lk, std::chrono::milliseconds(2));
+  }
+  if (stats) {
+    stats->submitted = sv->submitted;
+    stats->completed = sv->completed;
+    stats->failed = sv->failed;
+    stats->peak_inflight = sv->peak_inflight;
+    stats->peak_bytes = sv->peak_bytes;
+  }
+  return MLS_OK;
+}
+
+mls_status mls_server_destroy(mls_server *sv) {
+  g_err.clear();
+  if (!sv) return MLS_OK;
+  {
+    std::lock_guard<std::mutex> lk(sv->mu);
+    sv->stop = true;
+  }
+  sv->cv.notify_all();
+  if (sv->worker.joinable()) sv->worker.join();
+  for (ServeSlot &sl : sv->slots) {
+    cudaStreamSynchronize(sl.st);
+    ctx_free_all(&sl.ctx, sl.st);
+    cudaStreamSynchronize(sl.st);
+    cudaStreamDestroy(sl.st);
+    cudaEventDestroy(sl.e0);
+    cudaEventDestroy(sl.e1);
+  }
+  cudaGetLastError();
+  delete sv;
   return MLS_OK;
 }
 

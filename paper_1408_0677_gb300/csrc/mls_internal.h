@@ -33,15 +33,13 @@ struct PointSet {
   double gx0 = 0, gy0 = 0, cell = 0;
 };
 
-}  // namespace mlsi
-
-struct mls_handle {
-  mls_desc desc;
-  int device = 0;
-  cudaStream_t stream = nullptr;     // stream of the last call
-  mlsi::PointSet P;
-  std::vector<void *> owned;         // handle-lifetime device allocations
-  // per-render scratch, grown on demand
+// Per-render device scratch: the stabiliser and counts of the padded tile
+// grid, hand-over lists, tile frames and queue, counters and error word, the
+// uploaded levels and a staging area for host-pointer calls.  A handle owns
+// one for its own renders; the server gives every request in flight its own,
+// so renders of one resident dataset can overlap.
+struct RenderCtx {
+  std::vector<void *> owned;         // allocations of this context
   void *scratch = nullptr;
   size_t scratch_bytes = 0;
   float *mstab = nullptr;
@@ -56,9 +54,22 @@ struct mls_handle {
   double *lev64 = nullptr;
   float *lev32 = nullptr;
   size_t lev_cap = 0;
-  // staging for host-pointer calls
-  void *stage = nullptr;
+  void *stage = nullptr;             // staging for host-pointer calls
   size_t stage_bytes = 0;
+};
+
+// Bytes of the scratch a W x H render needs (see ensure_scratch).
+size_t scratch_bytes_for(int W, int H);
+
+}  // namespace mlsi
+
+struct mls_handle {
+  mls_desc desc;
+  int device = 0;
+  cudaStream_t stream = nullptr;     // stream of the last call
+  mlsi::PointSet P;
+  std::vector<void *> owned;         // handle-lifetime device allocations
+  mlsi::RenderCtx ctx;               // scratch of mls_render / mls_bands on this handle
   cudaEvent_t ev0 = nullptr, ev1 = nullptr, evk0 = nullptr, evk1 = nullptr;
   int64_t launches = 0;              // kernels launched by this handle
   int64_t last_pairs = 0;
