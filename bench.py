@@ -576,6 +576,61 @@ def run_serve(args):
     print(json.dumps(line), flush=True)
 
 
+# The paper's Table 1 (Section 4, Performance): MLS render time in seconds on
+# a GeForce GTX 285, 600 x 600 canvas, inverse-distance weights, for its mean
+# MLS (degree 0) and affine MLS (degree 1) modes.  Context, not a target.
+PAPER_TABLE1_S = {(306, 0): 0.017420, (1000, 0): 0.064938, (2245, 0): 0.147089,
+                  (306, 1): 0.026670, (1000, 1): 0.100724, (2245, 1): 0.242192}
+
+
+def run_table1(args):
+    """Table-1-shaped renders: n in {306, 1000, 2245} clustered points, D = 2
+    (the two texture coordinates), 600 x 600, inverse distance alpha = 1, mean
+    (degree 0) and affine (degree 1) MLS, timed beside the paper's numbers."""
+    import torch
+    world, rank, local = _dist()
+    torch.cuda.set_device(local)
+    from paper_1408_0677_gb300 import Renderer, inputs
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    rows, units, total_ms = [], 0, 0.0
+    for n in (306, 1000, 2245):
+        wl = inputs.small_random(3000 + n, n, 2, 600, 600, 1, inputs.WEIGHT_INVDIST, 0.05)
+        xy, F = torch.from_numpy(wl.xy).to(dev), torch.from_numpy(wl.F).to(dev)
+        for degree in (0, 1):
+            r = Renderer(xy, F, degree=degree, weight=inputs.WEIGHT_INVDIST, h=0.05, precision=args.precision,
+                         stream=stream.cuda_stream)
+            for _ in range(args.warmup):
+                r.render(600, 600, levels=wl.levels)
+                r.sync()
+            ts = []
+            for _ in range(args.steps):
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                r.render(600, 600, levels=wl.levels)
+                e1.record(stream)
+                r.sync()
+                e1.synchronize()
+                ts.append(e0.elapsed_time(e1))
+            r.close()
+            ms = float(np.median(ts))
+            paper = PAPER_TABLE1_S[(n, degree)]
+            rows.append({"n": n, "mode": "mean" if degree == 0 else "affine", "ours_ms": ms,
+                         "paper_gtx285_ms": 1e3 * paper, "ratio": 1e3 * paper / ms})
+            units += 600 * 600 * n * 2
+            total_ms += ms
+    if rank != 0:
+        return
+    line = {"metric": METRIC, "value": units / (total_ms * 1e-3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
+            "config": {"workload": "table1_idw_600sq_d2_n306-1000-2245_mean_affine",
+                       "note": "paper numbers: GTX 285 fragment shader (context only)"},
+            "table1": rows, "e2e": None, "roofline": None, "cpu_baseline": None}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -587,7 +642,7 @@ def main():
     ap.add_argument("--weight-split", type=int, default=None, choices=[0, 1, 2])
     ap.add_argument("--no-compare-fp32", dest="compare_fp32", action="store_false",
                     help="skip the plain FP32 comparison run")
-    ap.add_argument("--workload", default="fourier10k", choices=["fourier10k", "batch64", "serve"],
+    ap.add_argument("--workload", default="fourier10k", choices=["fourier10k", "batch64", "serve", "table1"],
                     help="the 10k-point render (default), 64 datasets in one graph, or the serving mix")
     ap.add_argument("--rate", type=float, default=200.0, help="serve: requests per second")
     ap.add_argument("--requests", type=int, default=400, help="serve: number of requests")
@@ -602,6 +657,8 @@ def main():
         run_batch(args)
     elif args.workload == "serve":
         run_serve(args)
+    elif args.workload == "table1":
+        run_table1(args)
     else:
         run_ours(args)
 

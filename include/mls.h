@@ -165,8 +165,11 @@ mls_status mls_create(const mls_desc *desc, const double *xy, const double *F,
  *   bands   D x H x W bytes, iso-band labels fused into the render
  *           (Section 3.4: band = #{j : t_dj <= f_d}, 255 for NaN), or NULL
  *   on_device  nonzero: field/status/bands are device pointers
- * Errors: MLS_E_INVAL, MLS_E_NOMEM, MLS_E_CUDA, MLS_E_UNSUPPORTED (the
- * tensor-core precisions with the inverse-distance weight).
+ * Precision routing: FP16/BF16 renders use the tensor-core kernel, except
+ * with the inverse-distance weight (no finite support for the tile operand's
+ * range clip) and when a 16-pixel tile spans more than 4 h (no moment frame
+ * suits all its pixels); those use the CUDA-core kernel with FP32 limits.
+ * Errors: MLS_E_INVAL, MLS_E_NOMEM, MLS_E_CUDA, MLS_E_UNSUPPORTED.
  */
 mls_status mls_render(mls_handle *h, const mls_view *view, void *field, uint8_t *status,
                       const double *levels, int32_t L, uint8_t *bands,

@@ -309,8 +309,6 @@ mls_status mls_create(const mls_desc *desc, const double *xy, const double *F, i
     return fail(MLS_E_INVAL, "rcond_degenerate must be in [0, 1)");
   if (!(d.cond_recompute >= 0.0)) return fail(MLS_E_INVAL, "cond_recompute must be >= 0");
   if (d.weight_split < -1 || d.weight_split > 2) return fail(MLS_E_INVAL, "weight_split must be -1, 0, 1 or 2");
-  if ((d.precision == MLS_P_BF16 || d.precision == MLS_P_FP16) && d.weight == MLS_W_INVDIST)
-    return fail(MLS_E_UNSUPPORTED, "the tensor-core precisions support the Gaussian and Wendland weights");
 
   mls_handle *h = new mls_handle();
   h->desc = d;
@@ -434,8 +432,10 @@ static mls_status render_enqueue(mls_handle *h, RenderCtx *c, const mlsk::KParam
     // A 16 x 16 tile much wider than h has no moment frame that suits all
     // its pixels (the tensor path shares one per tile): such renders use the
     // CUDA-core kernel with each pixel in its own frame, at FP32 limits.
+    // The inverse-distance weight (Eq. eq-weights) has no finite support or
+    // scale for the tile operand's range clip: it also takes this path.
     const double tile_h = kTile * fmax(fabs(p.sx), fabs(p.sy)) / h->desc.h;
-    if (tile_h > kTileFrameMaxH || h->desc.precision == MLS_P_FP32) {
+    if (tile_h > kTileFrameMaxH || h->desc.precision == MLS_P_FP32 || h->desc.weight == MLS_W_INVDIST) {
       mlsk::KParams pf = p;
       pf.pixel_frame = tile_h > kTileFrameMaxH ? 1 : 0;
       pf.lambda_max = 1000.f;

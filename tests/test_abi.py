@@ -88,7 +88,7 @@ def _desc(**kw):
     (dict(precision=9), _abi.MLS_E_INVAL),
     (dict(weight=_abi.MLS_W_INVDIST, alpha=-1.0), _abi.MLS_E_INVAL),
     (dict(rcond_degenerate=2.0), _abi.MLS_E_INVAL),
-    (dict(weight=_abi.MLS_W_INVDIST, precision=_abi.MLS_P_FP16), _abi.MLS_E_UNSUPPORTED),
+    (dict(weight_split=3), _abi.MLS_E_INVAL),
 ])
 def test_create_rejects_bad_descriptors_before_any_launch(lib, kw, code):
     buf = (ctypes.c_double * 64)()

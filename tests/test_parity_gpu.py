@@ -214,3 +214,15 @@ def test_tiles_much_wider_than_h_use_pixel_frames(precision, degree):
     wl = inputs.fourier_mix(51 + degree, 3000, 4, 64, 48, degree, G, 0.008)
     res = gpu_render(wl, precision)
     compare(wl, res, _ref(wl), precision)
+
+
+@pytest.mark.parametrize("precision", ["fp16", "bf16", "fp32"])
+@pytest.mark.parametrize("degree", [0, 1])
+def test_inverse_distance_table1_shape(precision, degree):
+    """The paper's own weight 1/r^(2 alpha) (alpha = 1) with the mean (degree 0)
+    and affine (degree 1) fits on a Table-1-shaped case (n = 306, D = 2, a
+    60 x 60 crop of the 600 x 600 canvas): every precision."""
+    wl = inputs.small_random(71 + degree, 306, 2, 60, 60, degree, ID, 0.05)
+    wl.view = (0.2, 0.3, 0.3, 0.4)
+    res = gpu_render(wl, precision)
+    compare(wl, res, _ref(wl), precision)
