@@ -8,4 +8,4 @@ never imports it, and it imports nothing from there.
 FP64, Section 3.3 of the paper); this module compiles it with gcc and calls
 it through ctypes.
 """
-from .oracle import build, mls, bands, OracleResult  # noqa: F401
+from .oracle import VARIANT_MEAN, VARIANT_RIGID, OracleResult, bands, build, mls, mls_variant  # noqa: F401

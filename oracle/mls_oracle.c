@@ -315,3 +315,138 @@ int oracle_bands(int64_t npix, int32_t D, const double *field, const double *lev
         }
     return 0;
 }
+
+/*
+ * The paper's other two MLS mappings of 2-D values (Section 3.3.1 Mean MLS,
+ * Eq. eq-meanmls; Section 3.3.3 Rigid MLS, Eqs. eq-rigidmls and
+ * eq-rigidmlspartial), for D = 2: the point values q_i are the original
+ * positions, p_i = xy_i the distorted ones, v the pixel centre, with the
+ * weights w_i of oracle_mls (same stabiliser, support and degenerate rules):
+ *
+ *   variant 1 (rigid):  p* = sum w p / sum w,  q* = sum w q / sum w,
+ *     dp_i = p_i - p*, dq_i = q_i - q*, dv = v - p*,
+ *     f'(v) = sum_i w_i dq_i [dp_i ; -dp_i^perp] [dv ; -dv^perp]^T
+ *             (dq_i a row vector, the brackets 2 x 2 matrices with the
+ *             given rows, (x, y)^perp = (-y, x)),
+ *     f(v)  = |dv| f'(v) / |f'(v)| + q*   (q* when dv or f'(v) is zero);
+ *   variant 2 (mean displacement):  f(v) = v + sum w (q - p) / sum w.
+ *
+ * Inverse distance with points exactly at v: the mean of their q (point
+ * identity, criterion 2 of Section 3.3).  No point in support: NaN.
+ */
+int oracle_mls_variant(int64_t n, const double *xy, const double *Q, int32_t variant, int32_t weight,
+                       double h, double alpha, int32_t W, int32_t H, double x0, double y0, double x1,
+                       double y1, int64_t npix, const int64_t *pix, double *field, int32_t nthreads) {
+    if (n < 1 || (variant != 1 && variant != 2) || !(h > 0.0) || W < 1 || H < 1) return -1;
+    if (weight != OR_GAUSS && weight != OR_WENDLAND && weight != OR_INVDIST) return -1;
+    if (pix == NULL) npix = (int64_t)W * H;
+    const double sx = (x1 - x0) / (double)W;
+    const double sy = (y1 - y0) / (double)H;
+    const double h2 = h * h;
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 16)
+#endif
+    for (int64_t q = 0; q < npix; ++q) {
+        const int64_t id = pix ? pix[q] : q;
+        const int64_t u = id % W, v = id / W;
+        const double vx = x0 + ((double)u + 0.5) * sx;
+        const double vy = y0 + ((double)v + 0.5) * sy;
+        double *out = field + 2 * q;
+        double m = INFINITY;
+        for (int64_t i = 0; i < n; ++i) {
+            const double dx = xy[2 * i] - vx, dy = xy[2 * i + 1] - vy;
+            const double r2 = dx * dx + dy * dy;
+            if (r2 < m) m = r2;
+        }
+        if (weight == OR_INVDIST && m == 0.0) {
+            double sq[2] = {0.0, 0.0}, c = 0.0;
+            for (int64_t i = 0; i < n; ++i) {
+                const double dx = xy[2 * i] - vx, dy = xy[2 * i + 1] - vy;
+                if (dx * dx + dy * dy == 0.0) {
+                    sq[0] += Q[2 * i];
+                    sq[1] += Q[2 * i + 1];
+                    c += 1.0;
+                }
+            }
+            out[0] = sq[0] / c;
+            out[1] = sq[1] / c;
+            continue;
+        }
+        /* weights, weighted centroids */
+        double sw = 0.0, sp[2] = {0.0, 0.0}, sq[2] = {0.0, 0.0};
+        for (int64_t i = 0; i < n; ++i) {
+            const double dx = xy[2 * i] - vx, dy = xy[2 * i + 1] - vy;
+            const double r2 = dx * dx + dy * dy;
+            double w;
+            if (weight == OR_GAUSS) w = exp(-(r2 - m) / h2);
+            else if (weight == OR_WENDLAND) {
+                if (r2 < h2) {
+                    const double qd = sqrt(r2) / h, t = 1.0 - qd;
+                    w = t * t * t * t * (4.0 * qd + 1.0);
+                } else {
+                    w = 0.0;
+                }
+            } else {
+                w = pow(m / r2, alpha);
+            }
+            sw += w;
+            sp[0] += w * xy[2 * i];
+            sp[1] += w * xy[2 * i + 1];
+            sq[0] += w * Q[2 * i];
+            sq[1] += w * Q[2 * i + 1];
+        }
+        if (!(sw > 0.0)) {
+            out[0] = out[1] = NAN;
+            continue;
+        }
+        const double ps[2] = {sp[0] / sw, sp[1] / sw}, qs[2] = {sq[0] / sw, sq[1] / sw};
+        if (variant == 2) {
+            /* v + sum w (q - p) / sum w */
+            out[0] = vx + (sq[0] - sp[0]) / sw;
+            out[1] = vy + (sq[1] - sp[1]) / sw;
+            continue;
+        }
+        const double dv[2] = {vx - ps[0], vy - ps[1]};
+        /* the 2 x 2 matrix [dv ; -dv^perp]^T, rows dv and -dv^perp = (dv_y, -dv_x) */
+        const double Vm[2][2] = {{dv[0], dv[1]}, {dv[1], -dv[0]}};
+        const double VT[2][2] = {{Vm[0][0], Vm[1][0]}, {Vm[0][1], Vm[1][1]}};
+        double fp[2] = {0.0, 0.0};
+        for (int64_t i = 0; i < n; ++i) {
+            const double dx = xy[2 * i] - vx, dy = xy[2 * i + 1] - vy;
+            const double r2 = dx * dx + dy * dy;
+            double w;
+            if (weight == OR_GAUSS) w = exp(-(r2 - m) / h2);
+            else if (weight == OR_WENDLAND) {
+                if (r2 < h2) {
+                    const double qd = sqrt(r2) / h, t = 1.0 - qd;
+                    w = t * t * t * t * (4.0 * qd + 1.0);
+                } else {
+                    w = 0.0;
+                }
+            } else {
+                w = pow(m / r2, alpha);
+            }
+            if (w == 0.0) continue;
+            const double dp[2] = {xy[2 * i] - ps[0], xy[2 * i + 1] - ps[1]};
+            const double dq[2] = {Q[2 * i] - qs[0], Q[2 * i + 1] - qs[1]};
+            /* [dp ; -dp^perp]: rows dp and (dp_y, -dp_x) */
+            const double Pm[2][2] = {{dp[0], dp[1]}, {dp[1], -dp[0]}};
+            /* row vector dq times Pm, then times VT */
+            const double t0 = dq[0] * Pm[0][0] + dq[1] * Pm[1][0];
+            const double t1 = dq[0] * Pm[0][1] + dq[1] * Pm[1][1];
+            fp[0] += w * (t0 * VT[0][0] + t1 * VT[1][0]);
+            fp[1] += w * (t0 * VT[0][1] + t1 * VT[1][1]);
+        }
+        const double ndv = sqrt(dv[0] * dv[0] + dv[1] * dv[1]);
+        const double nfp = sqrt(fp[0] * fp[0] + fp[1] * fp[1]);
+        if (ndv == 0.0 || nfp == 0.0) {
+            out[0] = qs[0];
+            out[1] = qs[1];
+        } else {
+            out[0] = ndv * fp[0] / nfp + qs[0];
+            out[1] = ndv * fp[1] / nfp + qs[1];
+        }
+    }
+    return 0;
+}

@@ -39,6 +39,11 @@ def load_library(path: str):
                                P, P, P, P, P, P, ctypes.c_int32]
     lib.oracle_bands.restype = ctypes.c_int
     lib.oracle_bands.argtypes = [ctypes.c_int64, ctypes.c_int32, P, P, ctypes.c_int32, P]
+    lib.oracle_mls_variant.restype = ctypes.c_int
+    lib.oracle_mls_variant.argtypes = [ctypes.c_int64, P, P, ctypes.c_int32, ctypes.c_int32, ctypes.c_double,
+                                       ctypes.c_double, ctypes.c_int32, ctypes.c_int32, ctypes.c_double,
+                                       ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_int64, P, P,
+                                       ctypes.c_int32]
     return lib
 
 
@@ -107,3 +112,31 @@ def bands(field, levels, lib=None) -> np.ndarray:
     if lib.oracle_bands(npix, D, _p(field), _p(levels), L, _p(out)) != 0:
         raise ValueError("oracle_bands rejected its arguments")
     return out
+
+
+VARIANT_RIGID = 1
+VARIANT_MEAN = 2
+
+
+def mls_variant(xy, Q, variant, weight, h, W, H, view=(0.0, 0.0, 1.0, 1.0), pixels=None, alpha=1.0, threads=0,
+                lib=None) -> np.ndarray:
+    """The paper's rigid (variant 1, Eqs. eq-rigidmls / eq-rigidmlspartial) or
+    mean-displacement (variant 2, Eq. eq-meanmls) mapping of 2-D values Q at
+    the listed pixels (all if None): (npix, 2) float64, NaN without support."""
+    lib = lib or _load()
+    xy = np.ascontiguousarray(xy, dtype=np.float64)
+    Q = np.ascontiguousarray(Q, dtype=np.float64)
+    n = xy.shape[0]
+    assert Q.shape == (n, 2)
+    if pixels is None:
+        npix, pix_arr = W * H, None
+    else:
+        pix_arr = np.ascontiguousarray(pixels, dtype=np.int64)
+        npix = pix_arr.size
+    field = np.empty((npix, 2), np.float64)
+    x0, y0, x1, y1 = view
+    rc = lib.oracle_mls_variant(n, _p(xy), _p(Q), int(variant), int(weight), float(h), float(alpha), W, H, x0, y0,
+                                x1, y1, npix, _p(pix_arr) if pix_arr is not None else None, _p(field), threads)
+    if rc != 0:
+        raise ValueError("oracle_mls_variant rejected its arguments")
+    return field
