@@ -71,6 +71,10 @@ static double basis_term(int a, double dx, double dy) {
     }
 }
 
+/* Centre of pixel column (row) u of width s starting at x0 (Section 3.3:
+ * the field is evaluated at each pixel's centre). */
+static double pixel_centre(double x0, double s, int64_t u) { return x0 + ((double)u + 0.5) * s; }
+
 static int n_terms(int degree) { return (degree + 1) * (degree + 2) / 2; }
 
 /* Cholesky of a k x k symmetric matrix A (row-major) into lower L.
@@ -167,8 +171,8 @@ int oracle_mls(int64_t n, int32_t D, const double *xy, const double *F,
         for (int64_t q = 0; q < npix; ++q) {
             const int64_t id = pix ? pix[q] : q;
             const int64_t u = id % W, v = id / W;
-            const double px = x0 + ((double)u + 0.5) * sx;
-            const double py = y0 + ((double)v + 0.5) * sy;
+            const double px = pixel_centre(x0, sx, u);
+            const double py = pixel_centre(y0, sy, v);
             double *out = field + q * D;
 
             /* squared distances and the stabiliser m = min r^2 */
@@ -316,6 +320,18 @@ int oracle_bands(int64_t npix, int32_t D, const double *field, const double *lev
     return 0;
 }
 
+/* w_i of oracle_mls for one pair at squared distance r2 from the pixel
+ * centre (Eq. eq-weights, the Wendland kernel; m = min r^2 stabiliser). */
+static double pair_weight(int32_t weight, double r2, double m, double h, double alpha) {
+    if (weight == OR_GAUSS) return exp(-(r2 - m) / (h * h));
+    if (weight == OR_WENDLAND) {
+        if (!(r2 < h * h)) return 0.0;
+        const double qd = sqrt(r2) / h, t = 1.0 - qd;
+        return t * t * t * t * (4.0 * qd + 1.0);
+    }
+    return pow(m / r2, alpha);
+}
+
 /*
  * The paper's other two MLS mappings of 2-D values (Section 3.3.1 Mean MLS,
  * Eq. eq-meanmls; Section 3.3.3 Rigid MLS, Eqs. eq-rigidmls and
@@ -328,21 +344,34 @@ int oracle_bands(int64_t npix, int32_t D, const double *field, const double *lev
  *     f'(v) = sum_i w_i dq_i [dp_i ; -dp_i^perp] [dv ; -dv^perp]^T
  *             (dq_i a row vector, the brackets 2 x 2 matrices with the
  *             given rows, (x, y)^perp = (-y, x)),
- *     f(v)  = |dv| f'(v) / |f'(v)| + q*   (q* when dv or f'(v) is zero);
+ *     f(v)  = |dv| f'(v) / |f'(v)| + q*;
  *   variant 2 (mean displacement):  f(v) = v + sum w (q - p) / sum w.
+ *
+ * The rigid form is dv turned by the rotation that best maps the dp_i onto
+ * the dq_i under the weights.  Where that rotation is undetermined -- every
+ * point of positive weight at one position (a single point in a Wendland
+ * support, duplicates), or f'(v) = 0 -- no rotation is taken: f(v) = dv + q*,
+ * the mean mapping.  (The paper's quotient is undefined there.)
  *
  * Inverse distance with points exactly at v: the mean of their q (point
  * identity, criterion 2 of Section 3.3).  No point in support: NaN.
+ *
+ * aux (NULL or npix x 4): q*_x, q*_y, |dv| and, for the rigid form, the
+ * conditioning kappa = sum w |dp| |dq| / |mu| of the rotation, where
+ * |mu| = |f'(v)| / |dv| is the size of the weighted cross moment that sets
+ * the angle (kappa >= 1; INFINITY where the rotation is undetermined, 0 for
+ * the mean form or dv = 0).  A relative error e in the moments turns the
+ * result by about e kappa radians.
  */
 int oracle_mls_variant(int64_t n, const double *xy, const double *Q, int32_t variant, int32_t weight,
                        double h, double alpha, int32_t W, int32_t H, double x0, double y0, double x1,
-                       double y1, int64_t npix, const int64_t *pix, double *field, int32_t nthreads) {
+                       double y1, int64_t npix, const int64_t *pix, double *field, double *aux,
+                       int32_t nthreads) {
     if (n < 1 || (variant != 1 && variant != 2) || !(h > 0.0) || W < 1 || H < 1) return -1;
     if (weight != OR_GAUSS && weight != OR_WENDLAND && weight != OR_INVDIST) return -1;
     if (pix == NULL) npix = (int64_t)W * H;
     const double sx = (x1 - x0) / (double)W;
     const double sy = (y1 - y0) / (double)H;
-    const double h2 = h * h;
 #ifdef _OPENMP
     if (nthreads > 0) omp_set_num_threads(nthreads);
 #pragma omp parallel for schedule(dynamic, 16)
@@ -350,9 +379,11 @@ int oracle_mls_variant(int64_t n, const double *xy, const double *Q, int32_t var
     for (int64_t q = 0; q < npix; ++q) {
         const int64_t id = pix ? pix[q] : q;
         const int64_t u = id % W, v = id / W;
-        const double vx = x0 + ((double)u + 0.5) * sx;
-        const double vy = y0 + ((double)v + 0.5) * sy;
+        const double vx = pixel_centre(x0, sx, u);
+        const double vy = pixel_centre(y0, sy, v);
         double *out = field + 2 * q;
+        double *ax = aux ? aux + 4 * q : NULL;
+        if (ax) ax[0] = ax[1] = ax[2] = ax[3] = NAN;
         double m = INFINITY;
         for (int64_t i = 0; i < n; ++i) {
             const double dx = xy[2 * i] - vx, dy = xy[2 * i + 1] - vy;
@@ -371,25 +402,23 @@ int oracle_mls_variant(int64_t n, const double *xy, const double *Q, int32_t var
             }
             out[0] = sq[0] / c;
             out[1] = sq[1] / c;
+            if (ax) {
+                ax[0] = out[0];
+                ax[1] = out[1];
+                ax[2] = ax[3] = 0.0;
+            }
             continue;
         }
-        /* weights, weighted centroids */
+        /* weights, weighted centroids; whether the support has two positions */
         double sw = 0.0, sp[2] = {0.0, 0.0}, sq[2] = {0.0, 0.0};
+        int64_t first = -1;
+        int spread = 0;
         for (int64_t i = 0; i < n; ++i) {
             const double dx = xy[2 * i] - vx, dy = xy[2 * i + 1] - vy;
-            const double r2 = dx * dx + dy * dy;
-            double w;
-            if (weight == OR_GAUSS) w = exp(-(r2 - m) / h2);
-            else if (weight == OR_WENDLAND) {
-                if (r2 < h2) {
-                    const double qd = sqrt(r2) / h, t = 1.0 - qd;
-                    w = t * t * t * t * (4.0 * qd + 1.0);
-                } else {
-                    w = 0.0;
-                }
-            } else {
-                w = pow(m / r2, alpha);
-            }
+            const double w = pair_weight(weight, dx * dx + dy * dy, m, h, alpha);
+            if (!(w > 0.0)) continue;
+            if (first < 0) first = i;
+            else if (xy[2 * i] != xy[2 * first] || xy[2 * i + 1] != xy[2 * first + 1]) spread = 1;
             sw += w;
             sp[0] += w * xy[2 * i];
             sp[1] += w * xy[2 * i + 1];
@@ -401,33 +430,28 @@ int oracle_mls_variant(int64_t n, const double *xy, const double *Q, int32_t var
             continue;
         }
         const double ps[2] = {sp[0] / sw, sp[1] / sw}, qs[2] = {sq[0] / sw, sq[1] / sw};
+        const double dv[2] = {vx - ps[0], vy - ps[1]};
+        const double ndv = sqrt(dv[0] * dv[0] + dv[1] * dv[1]);
+        if (ax) {
+            ax[0] = qs[0];
+            ax[1] = qs[1];
+            ax[2] = ndv;
+            ax[3] = 0.0;
+        }
         if (variant == 2) {
             /* v + sum w (q - p) / sum w */
             out[0] = vx + (sq[0] - sp[0]) / sw;
             out[1] = vy + (sq[1] - sp[1]) / sw;
             continue;
         }
-        const double dv[2] = {vx - ps[0], vy - ps[1]};
         /* the 2 x 2 matrix [dv ; -dv^perp]^T, rows dv and -dv^perp = (dv_y, -dv_x) */
         const double Vm[2][2] = {{dv[0], dv[1]}, {dv[1], -dv[0]}};
         const double VT[2][2] = {{Vm[0][0], Vm[1][0]}, {Vm[0][1], Vm[1][1]}};
-        double fp[2] = {0.0, 0.0};
-        for (int64_t i = 0; i < n; ++i) {
+        double fp[2] = {0.0, 0.0}, spq = 0.0;
+        for (int64_t i = 0; i < n && spread; ++i) {
             const double dx = xy[2 * i] - vx, dy = xy[2 * i + 1] - vy;
-            const double r2 = dx * dx + dy * dy;
-            double w;
-            if (weight == OR_GAUSS) w = exp(-(r2 - m) / h2);
-            else if (weight == OR_WENDLAND) {
-                if (r2 < h2) {
-                    const double qd = sqrt(r2) / h, t = 1.0 - qd;
-                    w = t * t * t * t * (4.0 * qd + 1.0);
-                } else {
-                    w = 0.0;
-                }
-            } else {
-                w = pow(m / r2, alpha);
-            }
-            if (w == 0.0) continue;
+            const double w = pair_weight(weight, dx * dx + dy * dy, m, h, alpha);
+            if (!(w > 0.0)) continue;
             const double dp[2] = {xy[2 * i] - ps[0], xy[2 * i + 1] - ps[1]};
             const double dq[2] = {Q[2 * i] - qs[0], Q[2 * i + 1] - qs[1]};
             /* [dp ; -dp^perp]: rows dp and (dp_y, -dp_x) */
@@ -437,15 +461,20 @@ int oracle_mls_variant(int64_t n, const double *xy, const double *Q, int32_t var
             const double t1 = dq[0] * Pm[0][1] + dq[1] * Pm[1][1];
             fp[0] += w * (t0 * VT[0][0] + t1 * VT[1][0]);
             fp[1] += w * (t0 * VT[0][1] + t1 * VT[1][1]);
+            spq += w * sqrt(dp[0] * dp[0] + dp[1] * dp[1]) * sqrt(dq[0] * dq[0] + dq[1] * dq[1]);
         }
-        const double ndv = sqrt(dv[0] * dv[0] + dv[1] * dv[1]);
         const double nfp = sqrt(fp[0] * fp[0] + fp[1] * fp[1]);
-        if (ndv == 0.0 || nfp == 0.0) {
+        if (ndv == 0.0) {
             out[0] = qs[0];
             out[1] = qs[1];
+        } else if (!spread || nfp == 0.0) {
+            out[0] = dv[0] + qs[0];
+            out[1] = dv[1] + qs[1];
+            if (ax) ax[3] = INFINITY;
         } else {
             out[0] = ndv * fp[0] / nfp + qs[0];
             out[1] = ndv * fp[1] / nfp + qs[1];
+            if (ax) ax[3] = spq * ndv / nfp;
         }
     }
     return 0;

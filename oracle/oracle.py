@@ -43,7 +43,7 @@ def load_library(path: str):
     lib.oracle_mls_variant.argtypes = [ctypes.c_int64, P, P, ctypes.c_int32, ctypes.c_int32, ctypes.c_double,
                                        ctypes.c_double, ctypes.c_int32, ctypes.c_int32, ctypes.c_double,
                                        ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_int64, P, P,
-                                       ctypes.c_int32]
+                                       P, ctypes.c_int32]
     return lib
 
 
@@ -119,10 +119,12 @@ VARIANT_MEAN = 2
 
 
 def mls_variant(xy, Q, variant, weight, h, W, H, view=(0.0, 0.0, 1.0, 1.0), pixels=None, alpha=1.0, threads=0,
-                lib=None) -> np.ndarray:
+                lib=None, aux=False):
     """The paper's rigid (variant 1, Eqs. eq-rigidmls / eq-rigidmlspartial) or
     mean-displacement (variant 2, Eq. eq-meanmls) mapping of 2-D values Q at
-    the listed pixels (all if None): (npix, 2) float64, NaN without support."""
+    the listed pixels (all if None): (npix, 2) float64, NaN without support.
+    With aux=True also (npix, 4): q*_x, q*_y, |v - p*| and the rotation's
+    conditioning kappa (see oracle_mls_variant)."""
     lib = lib or _load()
     xy = np.ascontiguousarray(xy, dtype=np.float64)
     Q = np.ascontiguousarray(Q, dtype=np.float64)
@@ -134,9 +136,11 @@ def mls_variant(xy, Q, variant, weight, h, W, H, view=(0.0, 0.0, 1.0, 1.0), pixe
         pix_arr = np.ascontiguousarray(pixels, dtype=np.int64)
         npix = pix_arr.size
     field = np.empty((npix, 2), np.float64)
+    ax = np.empty((npix, 4), np.float64) if aux else None
     x0, y0, x1, y1 = view
     rc = lib.oracle_mls_variant(n, _p(xy), _p(Q), int(variant), int(weight), float(h), float(alpha), W, H, x0, y0,
-                                x1, y1, npix, _p(pix_arr) if pix_arr is not None else None, _p(field), threads)
+                                x1, y1, npix, _p(pix_arr) if pix_arr is not None else None, _p(field),
+                                _p(ax) if aux else None, threads)
     if rc != 0:
         raise ValueError("oracle_mls_variant rejected its arguments")
-    return field
+    return (field, ax) if aux else field

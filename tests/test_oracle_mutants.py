@@ -23,7 +23,7 @@ MUTANTS = [
     ("Gaussian on r instead of r^2", "w = exp(-(r2[i] - m) / h2);", "w = exp(-(sqrt(r2[i]) - sqrt(m)) / h);"),
     ("Wendland (1-q)^3", "w = t * t * t * t * (4.0 * qd + 1.0);", "w = t * t * t * (4.0 * qd + 1.0);"),
     ("inverse distance 1/r^(4 alpha)", "w = pow(m / r2[i], alpha);", "w = pow(m / r2[i], 2.0 * alpha);"),
-    ("pixel centre without the half offset", "((double)u + 0.5) * sx", "((double)u) * sx"),
+    ("pixel centre without the half offset", "((double)u + 0.5) * s;", "((double)u) * s;"),
     ("fit read from the wrong coefficient", "sdiag[0] * Minv[0 * k + c]", "sdiag[k - 1] * Minv[(k - 1) * k + c]"),
     ("band tie counted below", "if (levels[d * L + j] <= f) c++;", "if (levels[d * L + j] < f) c++;"),
     ("value matrix read transposed", "Rbuf[a * D + d] += w * b[a] * F[i * D + d];",
@@ -49,6 +49,52 @@ def _battery():
     yield pins.test_golden_gauss_two_points
     yield lambda: [pins.test_golden_plane_four_points(w) for w in (G, WD, ID)]
     yield lambda: [pins.test_brute_force_tiny_cases(s) for s in range(6)]
+
+
+VARIANT_MUTANTS = [
+    ("perpendicular of dp with the wrong sign", "{{dp[0], dp[1]}, {dp[1], -dp[0]}}",
+     "{{dp[0], dp[1]}, {-dp[1], dp[0]}}"),
+    ("mean form without the pixel centre", "out[0] = vx + (sq[0] - sp[0]) / sw;", "out[0] = (sq[0] - sp[0]) / sw;"),
+    ("undetermined rotation collapses to q*", "out[0] = dv[0] + qs[0];", "out[0] = qs[0];"),
+    ("rigid result not rescaled to |dv|", "out[0] = ndv * fp[0] / nfp + qs[0];", "out[0] = fp[0] / nfp + qs[0];"),
+    ("q centroid from the positions", "sq[0] += w * Q[2 * i];", "sq[0] += w * xy[2 * i];"),
+]
+
+
+def _variant_battery():
+    from tests import test_oracle_variants as vp
+    yield lambda: [vp.test_rigid_reproduces_rigid_motions(w, h) for (w, h) in vp.GW]
+    yield lambda: [vp.test_identity_when_nothing_is_distorted(w, h, v) for (w, h) in vp.GW
+                   for v in (oracle.VARIANT_RIGID, oracle.VARIANT_MEAN)]
+    yield lambda: [vp.test_mean_reproduces_translations(w, h) for (w, h) in vp.GW]
+    yield vp.test_mean_is_pixel_plus_weighted_mean_displacement
+    yield vp.test_rigid_equals_best_weighted_rotation_by_search
+    yield lambda: [vp.test_single_point_support_is_a_translation(v)
+                   for v in (oracle.VARIANT_RIGID, oracle.VARIANT_MEAN)]
+    yield vp.test_coincident_support_is_a_translation
+
+
+def _caught_by(battery, old, new, monkeypatch):
+    src = open(os.path.join(os.path.dirname(oracle.__file__), "mls_oracle.c")).read()
+    assert src.count(old) == 1, f"mutation anchor not found: {old}"
+    with tempfile.TemporaryDirectory() as tmp:
+        path_c = os.path.join(tmp, "mut.c")
+        path_so = os.path.join(tmp, "libmut.so")
+        open(path_c, "w").write(src.replace(old, new))
+        subprocess.check_call(["gcc", "-O1", "-fopenmp", "-ffp-contract=off", "-shared", "-fPIC",
+                               "-o", path_so, path_c, "-lm"])
+        monkeypatch.setattr(orc, "_lib", orc.load_library(path_so))
+        for check in battery():
+            try:
+                check()
+            except (AssertionError, ValueError, FloatingPointError):
+                return True
+    return False
+
+
+@pytest.mark.parametrize("name,old,new", VARIANT_MUTANTS, ids=[m[0] for m in VARIANT_MUTANTS])
+def test_planted_variant_mistake_is_caught(name, old, new, monkeypatch):
+    assert _caught_by(_variant_battery, old, new, monkeypatch), f"no pin caught the planted mistake: {name}"
 
 
 @pytest.mark.parametrize("name,old,new", MUTANTS, ids=[m[0] for m in MUTANTS])

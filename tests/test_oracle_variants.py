@@ -109,3 +109,47 @@ def test_inverse_distance_point_identity(variant):
     Q = np.array([[3.0, -1.0], [5.0, 2.0], [0.5, 0.5]])
     f = oracle.mls_variant(xy, Q, variant, 2, 0.2, 2, 1, view=(0.0, 0.0, 1.0, 1.0))
     np.testing.assert_allclose(f, Q[:2], atol=0)
+
+
+@pytest.mark.parametrize("variant", [oracle.VARIANT_RIGID, oracle.VARIANT_MEAN])
+def test_single_point_support_is_a_translation(variant):
+    """One point in a Wendland support: the rotation of the rigid form is
+    undetermined and no rotation is taken, so both forms move the pixel by
+    that point's displacement q - p."""
+    xy = np.array([[0.3, 0.3], [0.9, 0.8], [0.95, 0.8]])
+    Q = np.array([[1.0, -2.0], [0.0, 0.0], [0.5, 0.1]])
+    f, ax = oracle.mls_variant(xy, Q, variant, 1, 0.2, 4, 4, aux=True)
+    P = _centres(4, 4)
+    d = np.hypot(*(P - xy[0]).T)
+    one = d < 0.2
+    assert one.sum() >= 2
+    np.testing.assert_allclose(f[one], (P + Q[0] - xy[0])[one], atol=1e-14)
+    if variant == oracle.VARIANT_RIGID:
+        assert np.all(np.isinf(ax[one, 3]))
+
+
+def test_coincident_support_is_a_translation():
+    """Every point of positive weight at one position (duplicates with
+    different values): the rigid form translates by the mean displacement."""
+    xy = np.array([[0.5, 0.5], [0.5, 0.5], [0.5, 0.5]])
+    Q = np.array([[1.0, 0.0], [2.0, 1.0], [0.0, 2.0]])
+    f = oracle.mls_variant(xy, Q, oracle.VARIANT_RIGID, 0, 0.3, 3, 3)
+    np.testing.assert_allclose(f, _centres(3, 3) + Q.mean(0) - xy[0], atol=1e-14)
+
+
+def test_rotation_conditioning():
+    """kappa = sum w |dp||dq| / |mu| is 1 for a rigid motion (every pair
+    agrees on the angle) and >= 1 always (triangle inequality); the reported
+    q* and |v - p*| match numpy weighted means."""
+    rng = np.random.default_rng(11)
+    xy = rng.uniform(0, 1, (40, 2))
+    h = 0.3
+    _, ax = oracle.mls_variant(xy, xy @ _rot(1.1).T + 2.0, oracle.VARIANT_RIGID, 0, h, 6, 5, aux=True)
+    np.testing.assert_allclose(ax[:, 3], 1.0, rtol=1e-12)
+    Q = rng.normal(size=(40, 2))
+    _, ax = oracle.mls_variant(xy, Q, oracle.VARIANT_RIGID, 0, h, 6, 5, aux=True)
+    assert np.all(ax[:, 3] >= 1.0 - 1e-12) and np.any(ax[:, 3] > 1.5)
+    for k, v in enumerate(_centres(6, 5)):
+        w = np.exp(-((xy - v) ** 2).sum(1) / h ** 2)
+        np.testing.assert_allclose(ax[k, :2], (w[:, None] * Q).sum(0) / w.sum(), rtol=1e-12, atol=1e-14)
+        np.testing.assert_allclose(ax[k, 2], np.hypot(*(v - (w[:, None] * xy).sum(0) / w.sum())), rtol=1e-12)
