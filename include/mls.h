@@ -98,6 +98,13 @@ typedef enum mls_precision {
  *               single weights first and renders again, with split weights,
  *               the 16 x 16 tiles where a pixel fails the single-weight
  *               checks; -1 (default) picks 2 for FP16 and 1 for BF16
+ *   variant     MLS_V_POLY: the polynomial fit of the given degree (Section
+ *               3.3.2 affine MLS for degree 1, the weighted mean for 0);
+ *               MLS_V_RIGID (Section 3.3.3, Eqs. eq-rigidmls and
+ *               eq-rigidmlspartial) or MLS_V_MEAN (Section 3.3.1, Eq.
+ *               eq-meanmls: v + sum w (q - p) / sum w): the paper's mappings
+ *               of 2-D values q_i (D must be 2; degree is ignored).  These
+ *               run on the CUDA-core kernels (FP32 limits for FP16/BF16).
  */
 typedef struct mls_desc {
     int64_t n;
@@ -111,8 +118,14 @@ typedef struct mls_desc {
     double rcond_degenerate;
     double cond_recompute;
     int32_t weight_split;
-    int32_t reserved[3];
+    int32_t variant;
+    int32_t reserved[2];
 } mls_desc;
+
+/* Mappings (mls_desc.variant). */
+#define MLS_V_POLY 0
+#define MLS_V_RIGID 1
+#define MLS_V_MEAN 2
 
 /* Output grid: W x H pixels over [x0, x1] x [y0, y1]. */
 typedef struct mls_view {

@@ -37,7 +37,8 @@ class Renderer:
     """
 
     def __init__(self, xy, F, degree=1, weight=MLS_W_GAUSS, h=0.05, precision="fp32", alpha=1.0,
-                 cond_fp64=None, rcond_degenerate=None, cond_recompute=None, weight_split=None, stream=None):
+                 cond_fp64=None, rcond_degenerate=None, cond_recompute=None, weight_split=None, stream=None,
+                 variant=0):
         import torch
         self.torch = torch
         d = mls_desc_default()
@@ -68,6 +69,7 @@ class Renderer:
             d.cond_recompute = cond_recompute
         if weight_split is not None:
             d.weight_split = int(weight_split)
+        d.variant = int(variant)
         self.desc = d
         self.n, self.D = n, D
         self.stream = _stream_ptr(stream)

@@ -31,7 +31,7 @@ class MlsDesc(ctypes.Structure):
                 ("weight", ctypes.c_int32), ("precision", ctypes.c_int32), ("h", ctypes.c_double),
                 ("alpha", ctypes.c_double), ("cond_fp64", ctypes.c_double),
                 ("rcond_degenerate", ctypes.c_double), ("cond_recompute", ctypes.c_double),
-                ("weight_split", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+                ("weight_split", ctypes.c_int32), ("variant", ctypes.c_int32), ("reserved", ctypes.c_int32 * 2)]
 
 
 class MlsView(ctypes.Structure):
@@ -52,6 +52,7 @@ class MlsBatchStats(ctypes.Structure):
 
 
 MLS_BATCH_AUTOTUNE = 1
+MLS_V_POLY, MLS_V_RIGID, MLS_V_MEAN = 0, 1, 2
 
 
 class MlsServerConfig(ctypes.Structure):

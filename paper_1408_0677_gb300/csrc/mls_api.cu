@@ -229,7 +229,8 @@ static mlsk::KParams base_params(const mls_handle *h, const RenderCtx *c, const 
   p.gx0 = P.gx0;
   p.gy0 = P.gy0;
   p.cell = P.cell;
-  p.degree = d.degree;
+  p.degree = d.variant != MLS_V_POLY ? 1 : d.degree;   // the mappings use the linear moments
+  p.variant = d.variant;
   p.weight = d.weight;
   p.h = d.h;
   p.alpha = d.alpha;
@@ -309,6 +310,8 @@ mls_status mls_create(const mls_desc *desc, const double *xy, const double *F, i
     return fail(MLS_E_INVAL, "rcond_degenerate must be in [0, 1)");
   if (!(d.cond_recompute >= 0.0)) return fail(MLS_E_INVAL, "cond_recompute must be >= 0");
   if (d.weight_split < -1 || d.weight_split > 2) return fail(MLS_E_INVAL, "weight_split must be -1, 0, 1 or 2");
+  if (d.variant < MLS_V_POLY || d.variant > MLS_V_MEAN) return fail(MLS_E_INVAL, "unknown variant");
+  if (d.variant != MLS_V_POLY && d.D != 2) return fail(MLS_E_INVAL, "the rigid and mean mappings take D = 2");
 
   mls_handle *h = new mls_handle();
   h->desc = d;
@@ -421,7 +424,14 @@ static mls_status render_enqueue(mls_handle *h, RenderCtx *c, const mlsk::KParam
   int64_t launches = 0;
   MLS_CUDA_TRY(cudaMemsetAsync(c->scratch, 0, 256, st));
   if (timing) MLS_CUDA_TRY(cudaEventRecord(h->ev0, st));
-  if (fp64) {
+  if (h->desc.variant != MLS_V_POLY) {
+    // the rigid and mean-displacement mappings: one kernel, FP64 for FP64
+    // renders and FP32 otherwise
+    if (timing) MLS_CUDA_TRY(cudaEventRecord(h->evk0, st));
+    launch_variant(p, fp64, st);
+    if (timing) MLS_CUDA_TRY(cudaEventRecord(h->evk1, st));
+    launches += 1;
+  } else if (fp64) {
     if (timing) MLS_CUDA_TRY(cudaEventRecord(h->evk0, st));
     launch_f64(p, (int64_t)plane, st);
     if (timing) MLS_CUDA_TRY(cudaEventRecord(h->evk1, st));

@@ -87,6 +87,8 @@ void launch_prepass(const mlsk::KParams &p, cudaStream_t st);
 void launch_f32(const mlsk::KParams &p, cudaStream_t st);
 void launch_f64(const mlsk::KParams &p, int64_t npix, cudaStream_t st);
 void launch_bands(const mlsk::KParams &p, bool fp64, cudaStream_t st);
+// rigid / mean-displacement mappings (KParams.variant), FP64 or FP32
+void launch_variant(const mlsk::KParams &p, bool fp64, cudaStream_t st);
 // handover.cu: ill-conditioned pixels of the reduced-precision renders
 void launch_handover(const mlsk::KParams &p, const int *list, const unsigned int *cnt, int64_t cap, int *list2,
                      unsigned int *cnt2, cudaStream_t st);
