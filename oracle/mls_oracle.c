@@ -126,6 +126,11 @@ static double norm1(int k, const double *A) {
  *   xy       n x 2 positions (row-major), F n x D values (row-major)
  *   degree   0, 1 or 2; weight OR_*; h = Gaussian h / Wendland radius /
  *            inverse-distance basis scale; alpha = inverse-distance exponent
+ *   trunc    Gaussian only: 0 for the full sum, or c > 0 for the truncated
+ *            Gaussian, whose weight is zero unless |x_i - p_x| < c h and
+ *            |y_i - p_y| < c h (a box of half-width c h around the pixel:
+ *            every pair left out has weight below exp(-c^2) of the kernel's
+ *            peak); its support count is the number of points in the box
  *   pix      npix pixel indices v*W+u (NULL: all W*H pixels in order)
  *   field    out, npix x D
  *   deg_used out, npix (-1: no point in support, value NaN)
@@ -135,12 +140,14 @@ static double norm1(int k, const double *A) {
  *   mstab    out, npix: m = min_i r_i^2 (0 for Wendland)
  *   amb      out, npix: bit 0 set when an rcond tested lay within a factor
  *            amb_factor of rcond_min; bit 1 set when a Wendland point lay
- *            within a relative amb_boundary of the support radius and could
- *            move the count across a k threshold.  Optional (NULL).
+ *            within a relative amb_boundary of the support radius (or a
+ *            truncated-Gaussian point's |dx| or |dy| within a relative
+ *            amb_boundary of c h) and could move the count across a k
+ *            threshold.  Optional (NULL).
  * Returns 0, or -1 on bad arguments.
  */
 int oracle_mls(int64_t n, int32_t D, const double *xy, const double *F,
-               int32_t degree, int32_t weight, double h, double alpha,
+               int32_t degree, int32_t weight, double h, double alpha, double trunc,
                int32_t W, int32_t H, double x0, double y0, double x1, double y1,
                int64_t npix, const int64_t *pix, double rcond_min,
                double amb_factor, double amb_boundary,
@@ -150,9 +157,11 @@ int oracle_mls(int64_t n, int32_t D, const double *xy, const double *F,
     if (n < 1 || D < 1 || degree < 0 || degree > 2 || !(h > 0.0) || W < 1 || H < 1)
         return -1;
     if (weight != OR_GAUSS && weight != OR_WENDLAND && weight != OR_INVDIST) return -1;
+    if (!(trunc >= 0.0) || (trunc > 0.0 && weight != OR_GAUSS)) return -1;
     if (pix == NULL) npix = (int64_t)W * H;
     const double sx = (x1 - x0) / (double)W;
     const double sy = (y1 - y0) / (double)H;
+    const double rho_box = trunc * h;
     const double inv_s = 1.0 / h;
     const double h2 = h * h;
     const double rho2 = h * h;
@@ -187,8 +196,19 @@ int oracle_mls(int64_t n, int32_t D, const double *xy, const double *F,
             for (int64_t i = 0; i < n; ++i) {
                 double w;
                 if (weight == OR_GAUSS) {
-                    w = exp(-(r2[i] - m) / h2);
-                    count++;
+                    int in_box = 1;
+                    if (trunc > 0.0) {
+                        const double ax = fabs(xy[2 * i] - px), ay = fabs(xy[2 * i + 1] - py);
+                        in_box = ax < rho_box && ay < rho_box;
+                        if (fabs(ax / rho_box - 1.0) < amb_boundary || fabs(ay / rho_box - 1.0) < amb_boundary)
+                            nboundary++;
+                    }
+                    if (in_box) {
+                        w = exp(-(r2[i] - m) / h2);
+                        count++;
+                    } else {
+                        w = 0.0;
+                    }
                 } else if (weight == OR_WENDLAND) {
                     const double qd = sqrt(r2[i]) / h;
                     if (r2[i] < rho2) {
@@ -231,7 +251,7 @@ int oracle_mls(int64_t n, int32_t D, const double *xy, const double *F,
             } else {
                 for (int deg = degree; deg >= 0 && used < 0; --deg) {
                     const int k = n_terms(deg);
-                    if (weight == OR_WENDLAND && nboundary > 0 &&
+                    if (nboundary > 0 &&
                         count - nboundary < k && k <= count + nboundary)
                         ambq |= 2;
                     if (count < k) continue;
@@ -320,9 +340,13 @@ int oracle_bands(int64_t npix, int32_t D, const double *field, const double *lev
     return 0;
 }
 
-/* w_i of oracle_mls for one pair at squared distance r2 from the pixel
- * centre (Eq. eq-weights, the Wendland kernel; m = min r^2 stabiliser). */
-static double pair_weight(int32_t weight, double r2, double m, double h, double alpha) {
+/* w_i of oracle_mls for one pair at offset (dx, dy) from the pixel centre
+ * (Eq. eq-weights, the Wendland kernel, the truncated Gaussian's box;
+ * m = min r^2 stabiliser). */
+static double pair_weight(int32_t weight, double dx, double dy, double m, double h, double alpha,
+                          double trunc) {
+    const double r2 = dx * dx + dy * dy;
+    if (weight == OR_GAUSS && trunc > 0.0 && !(fabs(dx) < trunc * h && fabs(dy) < trunc * h)) return 0.0;
     if (weight == OR_GAUSS) return exp(-(r2 - m) / (h * h));
     if (weight == OR_WENDLAND) {
         if (!(r2 < h * h)) return 0.0;
@@ -364,11 +388,12 @@ static double pair_weight(int32_t weight, double r2, double m, double h, double 
  * result by about e kappa radians.
  */
 int oracle_mls_variant(int64_t n, const double *xy, const double *Q, int32_t variant, int32_t weight,
-                       double h, double alpha, int32_t W, int32_t H, double x0, double y0, double x1,
+                       double h, double alpha, double trunc, int32_t W, int32_t H, double x0, double y0, double x1,
                        double y1, int64_t npix, const int64_t *pix, double *field, double *aux,
                        int32_t nthreads) {
     if (n < 1 || (variant != 1 && variant != 2) || !(h > 0.0) || W < 1 || H < 1) return -1;
     if (weight != OR_GAUSS && weight != OR_WENDLAND && weight != OR_INVDIST) return -1;
+    if (!(trunc >= 0.0) || (trunc > 0.0 && weight != OR_GAUSS)) return -1;
     if (pix == NULL) npix = (int64_t)W * H;
     const double sx = (x1 - x0) / (double)W;
     const double sy = (y1 - y0) / (double)H;
@@ -415,7 +440,7 @@ int oracle_mls_variant(int64_t n, const double *xy, const double *Q, int32_t var
         int spread = 0;
         for (int64_t i = 0; i < n; ++i) {
             const double dx = xy[2 * i] - vx, dy = xy[2 * i + 1] - vy;
-            const double w = pair_weight(weight, dx * dx + dy * dy, m, h, alpha);
+            const double w = pair_weight(weight, dx, dy, m, h, alpha, trunc);
             if (!(w > 0.0)) continue;
             if (first < 0) first = i;
             else if (xy[2 * i] != xy[2 * first] || xy[2 * i + 1] != xy[2 * first + 1]) spread = 1;
@@ -450,7 +475,7 @@ int oracle_mls_variant(int64_t n, const double *xy, const double *Q, int32_t var
         double fp[2] = {0.0, 0.0}, spq = 0.0;
         for (int64_t i = 0; i < n && spread; ++i) {
             const double dx = xy[2 * i] - vx, dy = xy[2 * i + 1] - vy;
-            const double w = pair_weight(weight, dx * dx + dy * dy, m, h, alpha);
+            const double w = pair_weight(weight, dx, dy, m, h, alpha, trunc);
             if (!(w > 0.0)) continue;
             const double dp[2] = {xy[2 * i] - ps[0], xy[2 * i + 1] - ps[1]};
             const double dq[2] = {Q[2 * i] - qs[0], Q[2 * i + 1] - qs[1]};

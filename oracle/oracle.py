@@ -33,7 +33,7 @@ def load_library(path: str):
     P = ctypes.c_void_p
     lib.oracle_mls.restype = ctypes.c_int
     lib.oracle_mls.argtypes = [ctypes.c_int64, ctypes.c_int32, P, P, ctypes.c_int32, ctypes.c_int32,
-                               ctypes.c_double, ctypes.c_double, ctypes.c_int32, ctypes.c_int32,
+                               ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_int32, ctypes.c_int32,
                                ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                ctypes.c_int64, P, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                P, P, P, P, P, P, ctypes.c_int32]
@@ -41,7 +41,7 @@ def load_library(path: str):
     lib.oracle_bands.argtypes = [ctypes.c_int64, ctypes.c_int32, P, P, ctypes.c_int32, P]
     lib.oracle_mls_variant.restype = ctypes.c_int
     lib.oracle_mls_variant.argtypes = [ctypes.c_int64, P, P, ctypes.c_int32, ctypes.c_int32, ctypes.c_double,
-                                       ctypes.c_double, ctypes.c_int32, ctypes.c_int32, ctypes.c_double,
+                                       ctypes.c_double, ctypes.c_double, ctypes.c_int32, ctypes.c_int32, ctypes.c_double,
                                        ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_int64, P, P,
                                        P, ctypes.c_int32]
     return lib
@@ -70,8 +70,10 @@ def _p(a):
 
 
 def mls(xy, F, degree, weight, h, W, H, view=(0.0, 0.0, 1.0, 1.0), pixels=None, alpha=1.0,
-        rcond_min=1e-12, amb_factor=100.0, amb_boundary=1e-6, threads=0, lib=None) -> OracleResult:
-    """Evaluate the FP64 MLS fit at the listed pixels (all pixels if None)."""
+        rcond_min=1e-12, amb_factor=100.0, amb_boundary=1e-6, threads=0, lib=None, trunc=0.0) -> OracleResult:
+    """Evaluate the FP64 MLS fit at the listed pixels (all pixels if None).
+    trunc = c > 0 (Gaussian only): the truncated Gaussian, zero outside the
+    box |dx|, |dy| < c h around each pixel."""
     lib = lib or _load()
     xy = np.ascontiguousarray(xy, dtype=np.float64)
     F = np.ascontiguousarray(F, dtype=np.float64)
@@ -92,7 +94,7 @@ def mls(xy, F, degree, weight, h, W, H, view=(0.0, 0.0, 1.0, 1.0), pixels=None, 
     ms = np.empty(npix, np.float64)
     amb = np.empty(npix, np.uint8)
     x0, y0, x1, y1 = view
-    rcode = lib.oracle_mls(n, D, _p(xy), _p(F), degree, weight, h, alpha, W, H, x0, y0, x1, y1,
+    rcode = lib.oracle_mls(n, D, _p(xy), _p(F), degree, weight, h, alpha, float(trunc), W, H, x0, y0, x1, y1,
                            npix, _p(pix_arr) if pix_arr is not None else None, rcond_min,
                            amb_factor, amb_boundary, _p(field), _p(deg), _p(rc), _p(cnt), _p(ms),
                            _p(amb), threads)
@@ -119,7 +121,7 @@ VARIANT_MEAN = 2
 
 
 def mls_variant(xy, Q, variant, weight, h, W, H, view=(0.0, 0.0, 1.0, 1.0), pixels=None, alpha=1.0, threads=0,
-                lib=None, aux=False):
+                lib=None, aux=False, trunc=0.0):
     """The paper's rigid (variant 1, Eqs. eq-rigidmls / eq-rigidmlspartial) or
     mean-displacement (variant 2, Eq. eq-meanmls) mapping of 2-D values Q at
     the listed pixels (all if None): (npix, 2) float64, NaN without support.
@@ -138,7 +140,8 @@ def mls_variant(xy, Q, variant, weight, h, W, H, view=(0.0, 0.0, 1.0, 1.0), pixe
     field = np.empty((npix, 2), np.float64)
     ax = np.empty((npix, 4), np.float64) if aux else None
     x0, y0, x1, y1 = view
-    rc = lib.oracle_mls_variant(n, _p(xy), _p(Q), int(variant), int(weight), float(h), float(alpha), W, H, x0, y0,
+    rc = lib.oracle_mls_variant(n, _p(xy), _p(Q), int(variant), int(weight), float(h), float(alpha), float(trunc),
+                                W, H, x0, y0,
                                 x1, y1, npix, _p(pix_arr) if pix_arr is not None else None, _p(field),
                                 _p(ax) if aux else None, threads)
     if rc != 0:

@@ -31,6 +31,9 @@ MUTANTS = [
     ("weight dropped from M", "M[a * k + c] += w * b[a] * b[c];", "M[a * k + c] += b[a] * b[c];"),
     ("degeneracy test inverted", "if (!(rc >= rcond_min)) ok = 0;", "if (!(rc <= rcond_min)) ok = 0;"),
     ("Wendland support test off", "if (r2[i] < rho2) {", "if (r2[i] < 4.0 * rho2) {"),
+    ("truncated box on one axis", "in_box = ax < rho_box && ay < rho_box;", "in_box = ax < rho_box;"),
+    ("truncated box edge counted in", "in_box = ax < rho_box && ay < rho_box;", "in_box = ax <= rho_box && ay <= rho_box;"),
+    ("truncated box half-width c h^2", "const double rho_box = trunc * h;", "const double rho_box = trunc * h * h;"),
 ]
 
 
@@ -49,6 +52,10 @@ def _battery():
     yield pins.test_golden_gauss_two_points
     yield lambda: [pins.test_golden_plane_four_points(w) for w in (G, WD, ID)]
     yield lambda: [pins.test_brute_force_tiny_cases(s) for s in range(6)]
+    from tests import test_oracle_trunc as tp
+    yield tp.test_box_not_disc_and_strict_edge
+    yield tp.test_equals_full_sum_over_the_points_in_the_box
+    yield tp.test_box_holding_every_point_is_the_full_sum
 
 
 VARIANT_MUTANTS = [
