@@ -39,7 +39,7 @@
 extern "C" {
 #endif
 
-#define MLS_ABI_VERSION 2
+#define MLS_ABI_VERSION 3
 
 typedef enum mls_status {
     MLS_OK = 0,
@@ -105,6 +105,16 @@ typedef enum mls_precision {
  *               eq-meanmls: v + sum w (q - p) / sum w): the paper's mappings
  *               of 2-D values q_i (D must be 2; degree is ignored).  These
  *               run on the CUDA-core kernels (FP32 limits for FP16/BF16).
+ *   support     MLS_W_GAUSS only: 0 (default) sums every point; c > 0 is
+ *               the truncated Gaussian, whose weight is zero unless
+ *               |x_i - p_x| < c h and |y_i - p_y| < c h (a box of
+ *               half-width c h around the pixel; every pair left out has
+ *               weight below exp(-c^2) of the kernel's peak, e.g. 2.3e-16
+ *               for c = 6).  Points are then visited through the uniform
+ *               grid, and a pixel's support count (the degree policy's
+ *               "points with non-zero weight") is the number of points in
+ *               its box: a pixel with an empty box is NaN.  Must be finite,
+ *               0 or in (0, 1e6].
  */
 typedef struct mls_desc {
     int64_t n;
@@ -119,7 +129,7 @@ typedef struct mls_desc {
     double cond_recompute;
     int32_t weight_split;
     int32_t variant;
-    int32_t reserved[2];
+    double support;
 } mls_desc;
 
 /* Mappings (mls_desc.variant). */

@@ -38,7 +38,7 @@ class Renderer:
 
     def __init__(self, xy, F, degree=1, weight=MLS_W_GAUSS, h=0.05, precision="fp32", alpha=1.0,
                  cond_fp64=None, rcond_degenerate=None, cond_recompute=None, weight_split=None, stream=None,
-                 variant=0):
+                 variant=0, support=0.0):
         import torch
         self.torch = torch
         d = mls_desc_default()
@@ -70,6 +70,7 @@ class Renderer:
         if weight_split is not None:
             d.weight_split = int(weight_split)
         d.variant = int(variant)
+        d.support = float(support)
         self.desc = d
         self.n, self.D = n, D
         self.stream = _stream_ptr(stream)

@@ -31,7 +31,7 @@ class MlsDesc(ctypes.Structure):
                 ("weight", ctypes.c_int32), ("precision", ctypes.c_int32), ("h", ctypes.c_double),
                 ("alpha", ctypes.c_double), ("cond_fp64", ctypes.c_double),
                 ("rcond_degenerate", ctypes.c_double), ("cond_recompute", ctypes.c_double),
-                ("weight_split", ctypes.c_int32), ("variant", ctypes.c_int32), ("reserved", ctypes.c_int32 * 2)]
+                ("weight_split", ctypes.c_int32), ("variant", ctypes.c_int32), ("support", ctypes.c_double)]
 
 
 class MlsView(ctypes.Structure):

@@ -118,6 +118,7 @@ struct KParams {
   const unsigned int *tile_count;
   int pixel_frame;             // FP32 kernel: moments in each pixel's own frame (not the tile's)
   int variant;                 // MLS_V_*: the polynomial fit, or the rigid / mean mapping of 2-D values
+  double trunc;                // truncated Gaussian: box half-width in units of h (0: full sum)
   const int *list;             // pixel indices, or null for all pixels
   const unsigned int *list_count;  // device count for list mode, or null
   int64_t list_cap;

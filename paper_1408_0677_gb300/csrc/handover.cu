@@ -88,10 +88,14 @@ __device__ __forceinline__ df32 df_warp_sum(df32 v) {
 // Near points and their weights.
 
 // Whether a point enters the sums: Gaussian weight above e^-kCut of the
-// largest, inside the Wendland support (double-float distance), any point
-// but a coincident one for inverse distance.
+// largest, or for the truncated Gaussian (cbox = c > 0) inside the box
+// |dx|, |dy| < c, every point of which counts (double-float offsets); inside
+// the Wendland support (double-float distance); any point but a coincident
+// one for inverse distance.
 template <int WK>
-__device__ __forceinline__ bool near_test(df32 ex, df32 ey, float mhat) {
+__device__ __forceinline__ bool near_test(df32 ex, df32 ey, float mhat, double cbox) {
+  if (WK == MLS_W_GAUSS && cbox > 0.0)
+    return fabs((double)ex.hi + (double)ex.lo) < cbox && fabs((double)ey.hi + (double)ey.lo) < cbox;
   if (WK == MLS_W_GAUSS) return fmaf(ex.hi, ex.hi, ey.hi * ey.hi) - mhat <= kCut;
   if (WK == MLS_W_WENDLAND) {
     const df32 r2d = df_add(df_mul(ex, ex), df_mul(ey, ey));
@@ -106,7 +110,12 @@ __device__ __forceinline__ bool near_test(df32 ex, df32 ey, float mhat) {
 template <int WK>
 __device__ __forceinline__ df32 pair_wdf(df32 ex, df32 ey, float mhat, double alpha, const float2 *tab) {
   const df32 r2 = df_add(df_mul(ex, ex), df_mul(ey, ey));
-  if (WK == MLS_W_GAUSS) return df_exp(df_add({mhat, 0.f}, {-r2.hi, -r2.lo}), tab);
+  if (WK == MLS_W_GAUSS) {
+    // below e^-87 of the largest weight (possible only in a wide truncation
+    // box) the pair adds nothing at FP64 rounding; df_exp's scale needs a >= -87
+    const df32 a = df_add({mhat, 0.f}, {-r2.hi, -r2.lo});
+    return a.hi < -87.f ? df32{0.f, 0.f} : df_exp(a, tab);
+  }
   if (WK == MLS_W_WENDLAND) return df_wendland(r2);
   const double w = pow((double)mhat / ((double)r2.hi + (double)r2.lo), alpha);
   return {(float)w, (float)(w - (double)(float)w)};
@@ -152,7 +161,7 @@ __device__ __forceinline__ int for_near(const KParams &p, const Ranges &R, float
       if (i < a1) {
         ex = df_diff(p.xs[i], p.xs_lo[i], pxh, pxl);
         ey = df_diff(p.ys[i], p.ys_lo[i], pyh, pyl);
-        nr = near_test<WK>(ex, ey, mhat);
+        nr = near_test<WK>(ex, ey, mhat, p.trunc);
         if (WK == MLS_W_INVDIST && !nr) coin = 1;
       }
       const unsigned int bal = __ballot_sync(0xffffffffu, nr);
@@ -419,10 +428,12 @@ __global__ __launch_bounds__(kWarps * 32, 4) void k_handover(KParams p, const in
       R.all_n = (int)p.n;
       R.cx0 = R.cx1 = R.cy0 = R.cy1 = 0;
     } else {
-      // near radius: the support (Wendland), or r^2 <= m + kCut (Gaussian),
-      // widened by a relative 1e-5 against rounding
-      const double rad = (WK == MLS_W_WENDLAND ? 1.0 : sqrt(fmax((double)mhat, 0.0) + (double)kCut)) * p.h *
-                         (1.0 + 1e-5);
+      // near radius: the support (Wendland), the box (truncated Gaussian), or
+      // r^2 <= m + kCut (Gaussian), widened by a relative 1e-5 against rounding
+      const double rad = (WK == MLS_W_WENDLAND ? 1.0
+                          : p.trunc > 0.0      ? p.trunc
+                                               : sqrt(fmax((double)mhat, 0.0) + (double)kCut)) *
+                         p.h * (1.0 + 1e-5);
       const double inv_cell = 1.0 / p.cell;
       R.all_n = 0;
       R.cx0 = max((int)floor((px - rad - p.gx0) * inv_cell), 0);
@@ -490,7 +501,7 @@ __global__ __launch_bounds__(kWarps * 32, 4) void k_handover(KParams p, const in
         if (lane == k) slots[j].S[k] = v;
       }
       if (lane == 0) {
-        slots[j].count = (WK == MLS_W_WENDLAND) ? nnear : p.n;
+        slots[j].count = (WK == MLS_W_WENDLAND || p.trunc > 0.0) ? nnear : p.n;
         // inverse distance: a coincident point (or a zero stabiliser) goes to
         // the FP64 kernel, which gives the pixel that point's value
         slots[j].flags = (WK == MLS_W_INVDIST && (coincident || !(mhat > 0.f))) ? 1 : 0;

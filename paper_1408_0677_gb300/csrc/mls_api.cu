@@ -231,6 +231,7 @@ static mlsk::KParams base_params(const mls_handle *h, const RenderCtx *c, const 
   p.cell = P.cell;
   p.degree = d.variant != MLS_V_POLY ? 1 : d.degree;   // the mappings use the linear moments
   p.variant = d.variant;
+  p.trunc = d.support;
   p.weight = d.weight;
   p.h = d.h;
   p.alpha = d.alpha;
@@ -312,6 +313,9 @@ mls_status mls_create(const mls_desc *desc, const double *xy, const double *F, i
   if (d.weight_split < -1 || d.weight_split > 2) return fail(MLS_E_INVAL, "weight_split must be -1, 0, 1 or 2");
   if (d.variant < MLS_V_POLY || d.variant > MLS_V_MEAN) return fail(MLS_E_INVAL, "unknown variant");
   if (d.variant != MLS_V_POLY && d.D != 2) return fail(MLS_E_INVAL, "the rigid and mean mappings take D = 2");
+  if (!(d.support >= 0.0 && d.support <= 1e6)) return fail(MLS_E_INVAL, "support must be 0 or in (0, 1e6]");
+  if (d.support > 0.0 && d.weight != MLS_W_GAUSS)
+    return fail(MLS_E_INVAL, "support (the truncated Gaussian) applies to the Gaussian weight only");
 
   mls_handle *h = new mls_handle();
   h->desc = d;

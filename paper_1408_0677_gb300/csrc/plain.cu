@@ -65,20 +65,24 @@ __global__ __launch_bounds__(128) void k_mls_f32(KParams p) {
   const float dpx = (float)((p.x0 + (u + 0.5) * p.sx - p.ctr_x) * p.inv_s - (double)cxs);
   const float dpy = (float)((p.y0 + (v + 0.5) * p.sy - p.ctr_y) * p.inv_s - (double)cys);
   const size_t pstride = (size_t)p.tiles_x * 16;
+  // compact support: the Wendland weight, or the truncated Gaussian's box |dx|, |dy| < c
+  const bool binned = (WK == MLS_W_WENDLAND) || (WK == MLS_W_GAUSS && p.trunc > 0.0);
+  const float cbox = (WK == MLS_W_GAUSS && p.trunc > 0.0) ? (float)p.trunc : INFINITY;
   const float m = (WK == MLS_W_WENDLAND) ? 0.f : p.mstab[(size_t)v * pstride + u];
-  const int cflag = (WK == MLS_W_WENDLAND) ? p.cnt[(size_t)v * pstride + u] : 0;
-  const int count = (WK == MLS_W_WENDLAND) ? (cflag & kCntMask) : (int)(p.n < (1 << 30) ? p.n : (1 << 30));
+  const int cflag = binned ? p.cnt[(size_t)v * pstride + u] : 0;
+  const int count = binned ? (cflag & kCntMask) : (int)(p.n < (1 << 30) ? p.n : (1 << 30));
   const float alpha = (float)p.alpha;
-  // point ranges: all points, or the cell rows overlapping the block's pixels +- h
+  // point ranges: all points, or the cell rows overlapping the block's pixels +- h (+- c h)
   int nr = 1, cx0 = 0, cx1 = 0, cy0 = 0;
-  if (WK == MLS_W_WENDLAND) {
+  if (binned) {
+    const double rad = (WK == MLS_W_WENDLAND) ? p.h : p.trunc * p.h * (1.0 + 1e-5);
     const int bu0 = blockIdx.x * 16, bv0 = blockIdx.y * 8;
     const double xa = p.x0 + (bu0 + 0.5) * p.sx, xb = p.x0 + (bu0 + 15.5) * p.sx;
     const double ya = p.y0 + (bv0 + 0.5) * p.sy, yb = p.y0 + (bv0 + 7.5) * p.sy;
     const double inv_cell = 1.0 / p.cell;
     int cy1;
-    cell_range_d(fmin(xa, xb), fmax(xa, xb), p.h, p.gx0, inv_cell, p.gx, cx0, cx1);
-    cell_range_d(fmin(ya, yb), fmax(ya, yb), p.h, p.gy0, inv_cell, p.gy, cy0, cy1);
+    cell_range_d(fmin(xa, xb), fmax(xa, xb), rad, p.gx0, inv_cell, p.gx, cx0, cx1);
+    cell_range_d(fmin(ya, yb), fmax(ya, yb), rad, p.gy0, inv_cell, p.gy, cy0, cy1);
     nr = (cx0 <= cx1) ? max(cy1 - cy0 + 1, 0) : 0;
   }
   const size_t plane = (size_t)p.W * p.H;
@@ -101,7 +105,7 @@ __global__ __launch_bounds__(128) void k_mls_f32(KParams p) {
     for (int dd = 0; dd < DC; ++dd) csum[dd] = 0.f;
     for (int r = 0; r < nr; ++r) {
       int a0, a1;
-      if (WK == MLS_W_WENDLAND) {
+      if (binned) {
         a0 = p.cell_start[(cy0 + r) * p.gx + cx0];
         a1 = p.cell_start[(cy0 + r) * p.gx + cx1 + 1];
       } else {
@@ -126,7 +130,7 @@ __global__ __launch_bounds__(128) void k_mls_f32(KParams p) {
           const float r2 = fmaf(qx, qx, qy * qy);
           float w;
           if (WK == MLS_W_GAUSS) {
-            w = exp2f((m - r2) * kLog2e);
+            w = (fabsf(qx) < cbox && fabsf(qy) < cbox) ? exp2f((m - r2) * kLog2e) : 0.f;
           } else if (WK == MLS_W_WENDLAND) {
             const float q = sqrtf(r2);
             const float o = 1.f - q;
@@ -173,7 +177,7 @@ __global__ __launch_bounds__(128) void k_mls_f32(KParams p) {
       }
       continue;
     }
-    const bool uncertain = (WK == MLS_W_WENDLAND) && count_uncertain<K>(cflag);
+    const bool uncertain = binned && count_uncertain<K>(cflag);
     if (count == 0 && !uncertain) {
       st = MLS_ST_NO_SUPPORT;
 #pragma unroll
@@ -251,6 +255,10 @@ __global__ __launch_bounds__(256) void k_mls_f64(KParams p, int64_t npix_all) {
   const double h2 = p.h * p.h;
   const int64_t n = p.n;
   OutT *field = (OutT *)p.field;
+  // compact support: the Wendland weight, or the truncated Gaussian's box
+  // |x_i - p_x|, |y_i - p_y| < rho = c h
+  const bool binned = (WK == MLS_W_WENDLAND) || (WK == MLS_W_GAUSS && p.trunc > 0.0);
+  const double rho = p.trunc * p.h;
 
   for (int64_t q = warp0; q < npix; q += nwarps) {
     const int64_t id = p.list ? p.list[q] : q;
@@ -258,22 +266,16 @@ __global__ __launch_bounds__(256) void k_mls_f64(KParams p, int64_t npix_all) {
     // the same expression order as the FP64 definition, without contraction
     const double px = __dadd_rn(p.x0, __dmul_rn(__dadd_rn((double)u, 0.5), p.sx));
     const double py = __dadd_rn(p.y0, __dmul_rn(__dadd_rn((double)v, 0.5), p.sy));
-    // candidate ranges
-    int a0s[3] = {0, 0, 0}, a1s[3] = {0, 0, 0};
-    int nr = 1;
-    if (WK == MLS_W_WENDLAND) {
+    // candidate ranges: all points, or the cell rows cy0..cy0+nr-1 (columns
+    // cx0..cx1) covering the support (Wendland) or the box (truncated Gaussian)
+    int nr = 1, cx0 = 0, cx1 = 0, cy0 = 0;
+    if (binned) {
       const double inv_cell = 1.0 / p.cell;
-      int cx0, cx1, cy0, cy1;
-      cell_range_d(px, px, p.h, p.gx0, inv_cell, p.gx, cx0, cx1);
-      cell_range_d(py, py, p.h, p.gy0, inv_cell, p.gy, cy0, cy1);
-      nr = 0;
-      for (int cy = cy0; cy <= cy1 && cx0 <= cx1 && nr < 3; ++cy) {
-        a0s[nr] = p.cell_start[cy * p.gx + cx0];
-        a1s[nr] = p.cell_start[cy * p.gx + cx1 + 1];
-        ++nr;
-      }
-    } else {
-      a1s[0] = (int)n;
+      const double rad = (WK == MLS_W_WENDLAND) ? p.h : rho * (1.0 + 1e-5);
+      int cy1;
+      cell_range_d(px, px, rad, p.gx0, inv_cell, p.gx, cx0, cx1);
+      cell_range_d(py, py, rad, p.gy0, inv_cell, p.gy, cy0, cy1);
+      nr = (cx0 <= cx1) ? max(cy1 - cy0 + 1, 0) : 0;
     }
     // stabiliser m = min r^2 (Gaussian, inverse distance); hand-over lists
     // take the prepass value (any common weight factor leaves the fit unchanged)
@@ -306,8 +308,10 @@ __global__ __launch_bounds__(256) void k_mls_f64(KParams p, int64_t npix_all) {
 #pragma unroll
       for (int dd = 0; dd < DC; ++dd) csum[dd] = 0.0;
       for (int r = 0; r < nr; ++r) {
-        for (int64_t i = a0s[r] + lane; i < a1s[r]; i += 32) {
-          if (WK == MLS_W_GAUSS && p.list) {
+        const int64_t a0 = binned ? p.cell_start[(cy0 + r) * p.gx + cx0] : 0;
+        const int64_t a1 = binned ? p.cell_start[(cy0 + r) * p.gx + cx1 + 1] : n;
+        for (int64_t i = a0 + lane; i < a1; i += 32) {
+          if (WK == MLS_W_GAUSS && p.list && !binned) {
             // conservative FP32 test before any FP64 work on far pairs
             const float dxs = p.xs[i] - pxs, dys = p.ys[i] - pys;
             if (fmaf(dxs, dxs, dys * dys) - mhat > (float)kGaussCut + 1.f) {
@@ -319,6 +323,7 @@ __global__ __launch_bounds__(256) void k_mls_f64(KParams p, int64_t npix_all) {
           const double r2 = __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy));
           double w;
           if (WK == MLS_W_GAUSS) {
+            if (binned && !(fabs(dx) < rho && fabs(dy) < rho)) continue;
             ++count;
             if (p.list && r2 - m > kGaussCut * h2) continue;
             w = exp(-(r2 - m) / h2);

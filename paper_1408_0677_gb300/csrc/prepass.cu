@@ -14,6 +14,10 @@
 // flag (kCntBoundary) when a point lies so close to the support boundary that
 // FP32 and FP64 could count it differently.
 //
+// Truncated Gaussian: the stabiliser as for the Gaussian, and the number of
+// points in each pixel's box |dx|, |dy| < c (units of h), with the same flag
+// for a point whose |dx| or |dy| lies within a relative kCntEdgeTol of c.
+//
 // Both also give each tile the frame its moments are accumulated in: the
 // weighted centroid of the points around the tile centre (Gaussian weights of
 // scale h, or the Wendland weights).  A pixel whose points lie to one side is
@@ -200,14 +204,55 @@ __global__ __launch_bounds__(256) void k_prepass_count(KParams p) {
   }
 }
 
+__global__ __launch_bounds__(256) void k_prepass_box(KParams p) {
+  __shared__ float cx[256], cy[256];
+  const int t = threadIdx.x;
+  const int u0 = blockIdx.x * 16, v0 = blockIdx.y * 16;
+  const int u = u0 + (t & 15), v = v0 + (t >> 4);
+  const float px = mlsk::scaled_px(p, u), py = mlsk::scaled_py(p, v);
+  const float c = (float)p.trunc;
+  // rounding of the scaled offsets grows with the coordinates' magnitude
+  const float tx = mlsk::kCntEdgeTol * (c + fabsf(px)), ty = mlsk::kCntEdgeTol * (c + fabsf(py));
+  const double xlo = p.x0 + (u0 + 0.5) * p.sx, xhi = p.x0 + (u0 + 15.5) * p.sx;
+  const double ylo = p.y0 + (v0 + 0.5) * p.sy, yhi = p.y0 + (v0 + 15.5) * p.sy;
+  const double inv_cell = 1.0 / p.cell, rad = p.trunc * p.h * (1.0 + 1e-5);
+  int cx0, cx1, cy0, cy1;
+  cell_range(fmin(xlo, xhi), fmax(xlo, xhi), rad, p.gx0, inv_cell, p.gx, cx0, cx1);
+  cell_range(fmin(ylo, yhi), fmax(ylo, yhi), rad, p.gy0, inv_cell, p.gy, cy0, cy1);
+  int count = 0;
+  bool edge = false;
+  for (int cyy = cy0; cyy <= cy1 && cx0 <= cx1; ++cyy) {
+    const int a = p.cell_start[cyy * p.gx + cx0];
+    const int e = p.cell_start[cyy * p.gx + cx1 + 1];
+    for (int base = a; base < e; base += 256) {
+      __syncthreads();
+      if (base + t < e) {
+        cx[t] = p.xs[base + t];
+        cy[t] = p.ys[base + t];
+      }
+      __syncthreads();
+      const int n = min(256, e - base);
+      for (int k = 0; k < n; ++k) {
+        const float ax = fabsf(cx[k] - px), ay = fabsf(cy[k] - py);
+        count += (ax < c && ay < c) ? 1 : 0;
+        edge = edge || fabsf(ax - c) < tx || fabsf(ay - c) < ty;
+      }
+    }
+  }
+  const int stride = p.tiles_x * 16;
+  const_cast<int *>(p.cnt)[(size_t)v * stride + u] = count | (edge ? mlsk::kCntBoundary : 0);
+}
+
 }  // namespace
 
 void launch_prepass(const KParams &p, cudaStream_t st) {
   dim3 grid(p.tiles_x, p.tiles_y);
-  if (p.weight == MLS_W_WENDLAND)
+  if (p.weight == MLS_W_WENDLAND) {
     k_prepass_count<<<grid, 256, 0, st>>>(p);
-  else
+  } else {
     k_prepass_min<<<grid, 256, 0, st>>>(p);
+    if (p.trunc > 0.0) k_prepass_box<<<grid, 256, 0, st>>>(p);
+  }
 }
 
 }  // namespace mlsi

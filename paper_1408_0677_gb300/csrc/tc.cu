@@ -259,8 +259,9 @@ __device__ __forceinline__ float pair_weight(float4 prm, float E, float dx, floa
 }
 
 // The sequence of point tiles a CTA visits: all points, or for the Wendland
-// weight the cell rows of the uniform grid overlapping the tile +- h.  Tile
-// starts are rounded down to 8 points; indices outside [lo, hi) are masked.
+// weight (truncated Gaussian) the cell rows of the uniform grid overlapping
+// the tile +- h (+- c h).  Tile starts are rounded down to 8 points; indices
+// outside [lo, hi) are masked.
 struct RangeIter {
   int cx0, cx1, cy0, cy1, cy;
   int lo, hi, base;
@@ -270,7 +271,7 @@ struct RangeIter {
 
 __device__ __forceinline__ void ranges_init(const KParams &p, int u0, int v0, int hgt, RangeIter &it) {
   it.n = (int)p.n;
-  if (p.weight != MLS_W_WENDLAND) {
+  if (p.weight != MLS_W_WENDLAND && !(p.trunc > 0.0)) {
     it.all = true;
     it.lo = 0;
     it.hi = it.n;
@@ -282,10 +283,11 @@ __device__ __forceinline__ void ranges_init(const KParams &p, int u0, int v0, in
   const double xlo = p.x0 + (u0 + 0.5) * p.sx, xhi = p.x0 + (u0 + 15.5) * p.sx;
   const double ylo = p.y0 + (v0 + 0.5) * p.sy, yhi = p.y0 + (v0 + hgt - 0.5) * p.sy;
   const double inv_cell = 1.0 / p.cell;
-  it.cx0 = max((int)floor((fmin(xlo, xhi) - p.h - p.gx0) * inv_cell), 0);
-  it.cx1 = min((int)floor((fmax(xlo, xhi) + p.h - p.gx0) * inv_cell), p.gx - 1);
-  it.cy0 = max((int)floor((fmin(ylo, yhi) - p.h - p.gy0) * inv_cell), 0);
-  it.cy1 = min((int)floor((fmax(ylo, yhi) + p.h - p.gy0) * inv_cell), p.gy - 1);
+  const double rad = p.weight == MLS_W_WENDLAND ? p.h : p.trunc * p.h * (1.0 + 1e-5);
+  it.cx0 = max((int)floor((fmin(xlo, xhi) - rad - p.gx0) * inv_cell), 0);
+  it.cx1 = min((int)floor((fmax(xlo, xhi) + rad - p.gx0) * inv_cell), p.gx - 1);
+  it.cy0 = max((int)floor((fmin(ylo, yhi) - rad - p.gy0) * inv_cell), 0);
+  it.cy1 = min((int)floor((fmax(ylo, yhi) + rad - p.gy0) * inv_cell), p.gy - 1);
   it.cy = it.cy0;
   it.lo = it.hi = it.base = 0;
   if (it.cx0 > it.cx1) it.cy = it.cy1 + 1;
@@ -394,7 +396,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_mls_tc(KParams p, int d0, int D
     // 2^(alpha_c + beta_r - L_p) <= 1, which one more multiply by its inverse
     // removes, so every pixel's largest weight is 1 as with the per-pixel
     // stabiliser (pixels whose factor would leave the FP32 range are handed over).
+    // The truncated Gaussian's box |dx|, |dy| < c is separable too: a column
+    // (row) factor is zero where the point is c or more away along x (y).
     const int t = threadIdx.x;
+    const bool boxed = p.trunc > 0.0;
+    const float cbox = (float)p.trunc;
     float *sAB = (float *)(smem + lay.offPrm) + 32 * warp;     // this warp's alpha[16], beta[16]
     float *exy = (float *)(smem + lay.offPrm + kGaussHdr);     // [2][32 rows][kEXS]
     {
@@ -461,8 +467,14 @@ __global__ void __launch_bounds__(kThreads, 1) k_mls_tc(KParams p, int d0, int D
         const float other = __shfl_xor_sync(0xffffffffu, mx, 1);
         const float sh = half ? 0.5f * (mx - other) : 0.5f * (other - mx);   // Y' = Y - sh, X' = X + sh
         float *dst = tab + 16 * half * kEXS + jp;
+        if (boxed) {   // uniform over the grid
 #pragma unroll
-        for (int k = 0; k < 16; ++k) dst[k * kEXS] = ok ? ex2_approx(half ? e[k] - sh : e[k] + sh) : 0.f;
+          for (int k = 0; k < 16; ++k)
+            dst[k * kEXS] = (ok && fabsf(off[k] - pos) < cbox) ? ex2_approx(half ? e[k] - sh : e[k] + sh) : 0.f;
+        } else {
+#pragma unroll
+          for (int k = 0; k < 16; ++k) dst[k * kEXS] = ok ? ex2_approx(half ? e[k] - sh : e[k] + sh) : 0.f;
+        }
       }
       __syncwarp();
       if (lane == 0) {
@@ -793,16 +805,23 @@ __global__ void __launch_bounds__(kThreads, 1) k_mls_tc(KParams p, int d0, int D
       for (int j = 0; j < 16; ++j) St[j] = 0.f;
     int count;
     bool handover = false;
+    bool cuncertain = false;
     if (WK == MLS_W_WENDLAND) {
       const int cflag = p.cnt[pi];
       count = cflag & kCntMask;
-      handover = count_uncertain<K>(cflag);
+      handover = cuncertain = count_uncertain<K>(cflag);
     } else {
       count = (int)(p.n < (1 << 30) ? p.n : (1 << 30));
+      if (p.trunc > 0.0) {
+        // truncated Gaussian: the points in the pixel's box
+        const int cflag = p.cnt[pi];
+        count = cflag & kCntMask;
+        cuncertain = count_uncertain<K>(cflag);
+      }
       // clipping |x~|_inf <= kRMax is exact in 16-bit arithmetic only when the
       // pixel has a point within (kRMax - |delta|_inf - 4.2) h
       const float reach = kRMax - fmaxf(fabsf(dxp), fabsf(dyp));
-      handover = !(p.mstab[pi] <= reach * reach - 18.f) || !read;
+      handover = cuncertain || !(p.mstab[pi] <= reach * reach - 18.f) || !read;
       {
         // the weight producers undo the split stabiliser's factor 2^-res up to kResMax
         const float *sAB0 = (const float *)(smem + lay.offPrm);
@@ -813,7 +832,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mls_tc(KParams p, int d0, int D
     float z[K];
     int outcome = SOLVE_RECOMPUTE;
     int degu = DEG;
-    const bool nosup = (count == 0) && !handover;
+    const bool nosup = (count == 0) && !cuncertain;
     if (!nosup && !handover) outcome = solve_by_count<K>(count, St, dxp, dyp, z, p, &degu);
     const bool done = !nosup && outcome != SOLVE_RECOMPUTE;
     const bool give = !nosup && outcome == SOLVE_RECOMPUTE;

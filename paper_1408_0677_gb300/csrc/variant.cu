@@ -70,11 +70,13 @@ __device__ __forceinline__ float dist2(float dx, float dy) { return fmaf(dx, dx,
 __device__ __forceinline__ double vmin(double a, double b) { return fmin(a, b); }
 __device__ __forceinline__ float vmin(float a, float b) { return fminf(a, b); }
 
-// w for a pair at squared distance r2 (raw units in double, units of h^2 in
-// float), m the stabiliser min r^2 (Eq. eq-weights; the Wendland kernel)
+// w for a pair at offset (dx, dy), squared distance r2 (raw units in double,
+// units of h in float), m the stabiliser min r^2 (Eq. eq-weights; the
+// Wendland kernel; the truncated Gaussian's box |dx|, |dy| < c h)
 template <int WK>
-__device__ __forceinline__ double pair_weight(double r2, double m, const KParams &p) {
+__device__ __forceinline__ double pair_weight(double dx, double dy, double r2, double m, const KParams &p) {
   const double h2 = p.h * p.h;
+  if (WK == MLS_W_GAUSS && p.trunc > 0.0 && !(fabs(dx) < p.trunc * p.h && fabs(dy) < p.trunc * p.h)) return 0.0;
   if (WK == MLS_W_GAUSS) return exp(-(r2 - m) / h2);
   if (WK == MLS_W_WENDLAND) {
     if (!(r2 < h2)) return 0.0;
@@ -84,7 +86,8 @@ __device__ __forceinline__ double pair_weight(double r2, double m, const KParams
   return pow(m / r2, p.alpha);
 }
 template <int WK>
-__device__ __forceinline__ float pair_weight(float r2, float m, const KParams &p) {
+__device__ __forceinline__ float pair_weight(float dx, float dy, float r2, float m, const KParams &p) {
+  if (WK == MLS_W_GAUSS && p.trunc > 0.0 && !(fabsf(dx) < (float)p.trunc && fabsf(dy) < (float)p.trunc)) return 0.f;
   if (WK == MLS_W_GAUSS) return exp2f((m - r2) * 1.4426950408889634f);
   if (WK == MLS_W_WENDLAND) {
     const float q = sqrtf(r2), o = 1.f - q, o2 = o * o;
@@ -103,17 +106,20 @@ __global__ __launch_bounds__(128) void k_mls_variant(KParams p, int tiles_x) {
   const bool inside = (u < p.W) && (v < p.H);
   T px, py;
   centre(p, u, v, px, py);
-  // point ranges: all points, or the cell rows overlapping the block's pixels +- h
+  // point ranges: all points, or the cell rows overlapping the block's pixels
+  // +- h (Wendland) or +- c h (the truncated Gaussian's box)
+  const bool binned = (WK == MLS_W_WENDLAND) || (WK == MLS_W_GAUSS && p.trunc > 0.0);
+  const double rad = (WK == MLS_W_WENDLAND) ? p.h : p.trunc * p.h * (1.0 + 1e-5);
   int nr = 1, cx0 = 0, cx1 = 0, cy0 = 0;
-  if (WK == MLS_W_WENDLAND) {
+  if (binned) {
     const double xa = p.x0 + (bx * 16 + 0.5) * p.sx, xb = p.x0 + (bx * 16 + 15.5) * p.sx;
     const double ya = p.y0 + (by * 8 + 0.5) * p.sy, yb = p.y0 + (by * 8 + 7.5) * p.sy;
     const double inv_cell = 1.0 / p.cell;
     int cy1;
-    cx0 = max((int)floor((fmin(xa, xb) - p.h - p.gx0) * inv_cell), 0);
-    cx1 = min((int)floor((fmax(xa, xb) + p.h - p.gx0) * inv_cell), p.gx - 1);
-    cy0 = max((int)floor((fmin(ya, yb) - p.h - p.gy0) * inv_cell), 0);
-    cy1 = min((int)floor((fmax(ya, yb) + p.h - p.gy0) * inv_cell), p.gy - 1);
+    cx0 = max((int)floor((fmin(xa, xb) - rad - p.gx0) * inv_cell), 0);
+    cx1 = min((int)floor((fmax(xa, xb) + rad - p.gx0) * inv_cell), p.gx - 1);
+    cy0 = max((int)floor((fmin(ya, yb) - rad - p.gy0) * inv_cell), 0);
+    cy1 = min((int)floor((fmax(ya, yb) + rad - p.gy0) * inv_cell), p.gy - 1);
     nr = (cx0 <= cx1) ? max(cy1 - cy0 + 1, 0) : 0;
   }
   // stabiliser (Gaussian, inverse distance): m = min r^2 over all points
@@ -135,7 +141,7 @@ __global__ __launch_bounds__(128) void k_mls_variant(KParams p, int tiles_x) {
   int ccnt = 0;
   for (int r = 0; r < nr; ++r) {
     int64_t a0 = 0, a1 = p.n;
-    if (WK == MLS_W_WENDLAND) {
+    if (binned) {
       a0 = p.cell_start[(cy0 + r) * p.gx + cx0];
       a1 = p.cell_start[(cy0 + r) * p.gx + cx1 + 1];
     }
@@ -156,7 +162,7 @@ __global__ __launch_bounds__(128) void k_mls_variant(KParams p, int tiles_x) {
           csb += sb[j];
           continue;
         }
-        const T w = pair_weight<WK>(r2, m, p);
+        const T w = pair_weight<WK>(dx, dy, r2, m, p);
         if (!(w > (T)0)) continue;
         const T Wn = W + w, rr = w / Wn, g = W * rr;   // g = W_old w / W_new
         const T dpx = dx - mpx, dpy = dy - mpy, dqa = sa[j] - mqa, dqb = sb[j] - mqb;

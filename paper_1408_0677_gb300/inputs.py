@@ -38,6 +38,7 @@ class Workload:
     view: tuple = (0.0, 0.0, 1.0, 1.0)   # x0, y0, x1, y1
     levels: np.ndarray = field(default=None)  # (D, L) float64 ascending
     alpha: float = 1.0       # IDW exponent (paper's Eq. eq-weights)
+    trunc: float = 0.0       # truncated Gaussian: box half-width in units of h (0: full sum)
 
     @property
     def n(self) -> int:

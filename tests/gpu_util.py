@@ -19,7 +19,8 @@ def gpu_render(wl, precision, device_inputs=True, levels=True, **kw):
         xy, F = torch.from_numpy(wl.xy).cuda(), torch.from_numpy(wl.F).cuda()
     else:
         xy, F = wl.xy, wl.F
-    r = Renderer(xy, F, degree=wl.degree, weight=wl.weight, h=wl.h, precision=precision, alpha=wl.alpha, **kw)
+    r = Renderer(xy, F, degree=wl.degree, weight=wl.weight, h=wl.h, precision=precision, alpha=wl.alpha,
+                 support=wl.trunc, **kw)
     out = r.render(wl.W, wl.H, view=wl.view, levels=wl.levels if levels else None)
     stats = r.sync()
     res = {k: (v.cpu().numpy() if v is not None else None) for k, v in out.items()}

@@ -48,7 +48,8 @@ def test_struct_layout_matches_header():
 #include <stddef.h>
 #include "mls.h"
 int main(void) {
-  printf("%zu %zu %zu %zu %zu\n", sizeof(mls_desc), offsetof(mls_desc, h), offsetof(mls_desc, cond_recompute),
+  printf("%zu %zu %zu %zu %zu %zu %zu\n", sizeof(mls_desc), offsetof(mls_desc, h),
+         offsetof(mls_desc, cond_recompute), offsetof(mls_desc, variant), offsetof(mls_desc, support),
          sizeof(mls_view), sizeof(mls_stats));
   return 0;
 }
@@ -60,13 +61,15 @@ int main(void) {
         subprocess.check_call(["gcc", "-I" + os.path.join(ROOT, "include"), c, "-o", exe])
         vals = [int(x) for x in subprocess.check_output([exe]).split()]
     assert vals == [ctypes.sizeof(_abi.MlsDesc), _abi.MlsDesc.h.offset, _abi.MlsDesc.cond_recompute.offset,
+                    _abi.MlsDesc.variant.offset, _abi.MlsDesc.support.offset,
                     ctypes.sizeof(_abi.MlsView), ctypes.sizeof(_abi.MlsStats)]
 
 
 def test_abi_version_and_defaults(lib):
-    assert _abi.mls_abi_version() == 2
+    assert _abi.mls_abi_version() == 3
     d = _abi.mls_desc_default()
     assert d.cond_fp64 == 1e6 and d.rcond_degenerate == 1e-12 and d.precision == _abi.MLS_P_FP32
+    assert d.variant == _abi.MLS_V_POLY and d.support == 0.0
 
 
 def _desc(**kw):
@@ -89,6 +92,13 @@ def _desc(**kw):
     (dict(weight=_abi.MLS_W_INVDIST, alpha=-1.0), _abi.MLS_E_INVAL),
     (dict(rcond_degenerate=2.0), _abi.MLS_E_INVAL),
     (dict(weight_split=3), _abi.MLS_E_INVAL),
+    (dict(support=-1.0), _abi.MLS_E_INVAL),
+    (dict(support=float("nan")), _abi.MLS_E_INVAL),
+    (dict(support=2e6), _abi.MLS_E_INVAL),
+    (dict(support=3.0, weight=_abi.MLS_W_WENDLAND), _abi.MLS_E_INVAL),
+    (dict(support=3.0, weight=_abi.MLS_W_INVDIST), _abi.MLS_E_INVAL),
+    (dict(variant=3), _abi.MLS_E_INVAL),
+    (dict(variant=_abi.MLS_V_RIGID, D=3), _abi.MLS_E_INVAL),
 ])
 def test_create_rejects_bad_descriptors_before_any_launch(lib, kw, code):
     buf = (ctypes.c_double * 64)()

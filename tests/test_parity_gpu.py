@@ -20,7 +20,7 @@ def built():
 
 def _ref(wl, pixels=None):
     return oracle.mls(wl.xy, wl.F, wl.degree, wl.weight, wl.h, wl.W, wl.H, view=wl.view, pixels=pixels,
-                      alpha=wl.alpha)
+                      alpha=wl.alpha, trunc=wl.trunc)
 
 
 @pytest.mark.parametrize("precision", ALL_PREC + ["fp16-ws0", "fp16-ws1"])
