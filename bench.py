@@ -12,7 +12,12 @@ inputs, and both fields' error against the FP64 oracle on the oracle's pixel
 sample (largest |f - f_oracle| / data range of the dimension).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp16|bf16|fp32|fp64]
+  python bench.py --support 6         # the truncated Gaussian (box of half-width 6 h)
   python bench.py --impl reference    # the FP64 CPU oracle on a bounded pixel sample
+
+With --support C the weight is the truncated Gaussian and the metric counts
+only the pairs inside each pixel's box (the pairs that carry weight); the
+full-sum-equivalent rate W * H * n * D / step time is reported beside it.
 
 With N > 1 (torchrun, one process per GPU) every rank renders its own
 replica (the pixels of one render are independent; no collective on the
@@ -21,6 +26,7 @@ data path): weak scaling, max time over ranks.
 from __future__ import annotations
 
 import argparse
+import dataclasses
 import hashlib
 import json
 import os
@@ -122,6 +128,29 @@ def max_over_ranks(x: float, world: int, device) -> float:
     return float(t.item())
 
 
+def pairs_in_boxes(wl):
+    """Pixel-point pairs of a render inside the truncated Gaussian's box
+    |x_i - p_x| < c h and |y_i - p_y| < c h: per point, the pixel columns
+    and rows whose centres lie within c h of it (a rectangle of pixels)."""
+    rho = wl.trunc * wl.h
+    x0, y0, x1, y1 = wl.view
+
+    def span(pos, lo, step, N):
+        a = np.ceil((pos - rho - lo) / step - 0.5).astype(np.int64)
+        b = np.floor((pos + rho - lo) / step - 0.5).astype(np.int64)
+        for k in (a, b):   # settle rounding at the edges with the pixel-centre expression
+            k[:] = np.clip(k, -1, N)
+        a = np.where((a > 0) & (np.abs(pos - (lo + (a - 1 + 0.5) * step)) < rho), a - 1, a)
+        a = np.where((a < N) & (np.abs(pos - (lo + (a + 0.5) * step)) >= rho), a + 1, a)
+        b = np.where((b < N - 1) & (np.abs(pos - (lo + (b + 1 + 0.5) * step)) < rho), b + 1, b)
+        b = np.where((b >= 0) & (np.abs(pos - (lo + (b + 0.5) * step)) >= rho), b - 1, b)
+        return np.maximum(np.minimum(b, N - 1) - np.maximum(a, 0) + 1, 0)
+
+    nu = span(wl.xy[:, 0], x0, (x1 - x0) / wl.W, wl.W)
+    nv = span(wl.xy[:, 1], y0, (y1 - y0) / wl.H, wl.H)
+    return int(np.sum(nu * nv))
+
+
 def cpu_baseline(wl, seconds=15.0):
     """FP64 oracle on a bounded pixel sample (all host cores).  Also returns the
     last sample's pixels and oracle result, against which the GPU fields'
@@ -129,23 +158,27 @@ def cpu_baseline(wl, seconds=15.0):
     import oracle
     npx = 64
     threads = os.cpu_count() or 1
-    t_used, px_done = 0.0, 0
+    t_used, px_done, pairs_done = 0.0, 0, 0
     seed = 0
     last = None
     while t_used < seconds and npx <= 1 << 16:
         pix = np.sort(np.random.default_rng(100 + seed).choice(wl.W * wl.H, size=npx, replace=False))
         t0 = time.perf_counter()
-        res = oracle.mls(wl.xy, wl.F, wl.degree, wl.weight, wl.h, wl.W, wl.H, pixels=pix, threads=threads)
+        res = oracle.mls(wl.xy, wl.F, wl.degree, wl.weight, wl.h, wl.W, wl.H, pixels=pix, threads=threads,
+                         trunc=wl.trunc)
         dt = time.perf_counter() - t0
         t_used += dt
         px_done += npx
+        pairs_done += int(res.count.sum()) if wl.trunc > 0 else npx * wl.n
         last = (pix, res)
         seed += 1
         if dt < seconds / 4:
             npx *= 2
-    value = px_done * wl.n * wl.D / t_used
+    value = pairs_done * wl.D / t_used
+    what = (f"full n={wl.n} sum each" if wl.trunc == 0 else
+            f"pairs in the box of half-width {wl.trunc} h counted (the oracle visits all n={wl.n})")
     return {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
-            "sample": f"{px_done} random pixels of the workload, full n={wl.n} sum each, FP64, {t_used:.1f} s"}, last
+            "sample": f"{px_done} random pixels of the workload, {what}, FP64, {t_used:.1f} s"}, last
 
 
 def _err_vs_oracle(wl, field_samples, last):
@@ -230,6 +263,8 @@ def run_ours(args):
     from paper_1408_0677_gb300 import _abi
 
     wl = inputs.fourier_10k()
+    if args.support > 0:
+        wl = dataclasses.replace(wl, trunc=args.support)
     n, D, W, H, L = wl.n, wl.D, wl.W, wl.H, wl.levels.shape[1]
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
@@ -245,7 +280,7 @@ def run_ours(args):
 
     def step_device():
         r = Renderer(xy_d, F_d, degree=wl.degree, weight=wl.weight, h=wl.h, precision=args.precision,
-                     weight_split=args.weight_split, stream=sptr)
+                     weight_split=args.weight_split, stream=sptr, support=wl.trunc)
         r.render(W, H, levels=lev, field=field, bands=bands, status_out=status)
         return r
 
@@ -285,7 +320,8 @@ def run_ours(args):
     clocks = sampler.stop()
     total_ms = max_over_ranks(total_ms, world, dev)
     ms_step = total_ms / args.steps
-    units = W * H * n * D
+    pairs = W * H * n if wl.trunc == 0 else pairs_in_boxes(wl)
+    units = pairs * D
     value = world * units / (ms_step * 1e-3)
 
     # ---- the plain FP32 CUDA-core form on the same inputs, for comparison
@@ -295,7 +331,8 @@ def run_ours(args):
         field32 = torch.empty((D, H, W), dtype=torch.float32, device=dev)
 
         def step_fp32():
-            r = Renderer(xy_d, F_d, degree=wl.degree, weight=wl.weight, h=wl.h, precision="fp32", stream=sptr)
+            r = Renderer(xy_d, F_d, degree=wl.degree, weight=wl.weight, h=wl.h, precision="fp32", stream=sptr,
+                         support=wl.trunc)
             r.render(W, H, levels=lev, field=field32, bands=bands, status_out=status)
             return r
 
@@ -328,7 +365,7 @@ def run_ours(args):
 
     def step_host():
         r = Renderer(xy_h, F_h, degree=wl.degree, weight=wl.weight, h=wl.h, precision=args.precision,
-                     weight_split=args.weight_split, stream=sptr)
+                     weight_split=args.weight_split, stream=sptr, support=wl.trunc)
         r.render_host(W, H, levels=lev, field=field_h, bands=bands_h, status_out=status_h)
         r.close()
 
@@ -352,11 +389,12 @@ def run_ours(args):
         return
     peaks, src = _peaks()
     k_ms = float(np.mean(kern_ms))
-    flops = 2.0 * (6 * D + 15) * W * H * n       # algorithmic contraction flops per launch
+    flops = 2.0 * (6 * D + 15) * pairs           # algorithmic contraction flops per launch
     achieved = flops / (k_ms * 1e-3) / 1e12
     peak = peaks.get("bf16_tflops", 1900.0)       # FP16 and BF16 share the dense tensor rate
     roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-            "traffic": _traffic(W * H), "peak_source": f"{src} bf16 burst (fp16 dense rate equal)",
+            "traffic": _traffic(W * H) if wl.trunc == 0 else None,
+            "peak_source": f"{src} bf16 burst (fp16 dense rate equal)",
             "kernel": "k_mls_tc", "kernel_ms": k_ms, "flops_per_launch": flops}
     cpu, err = None, None
     if args.cpu_seconds > 0:
@@ -371,7 +409,9 @@ def run_ours(args):
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
-            "config": {"workload": WORKLOAD, "n": n, "D": D, "W": W, "H": H, "degree": 2, "weight": "gauss",
+            "config": {"workload": WORKLOAD if wl.trunc == 0 else WORKLOAD + f"_trunc{wl.trunc:g}",
+                       "n": n, "D": D, "W": W, "H": H, "degree": 2,
+                       "weight": "gauss" if wl.trunc == 0 else f"gauss truncated to |dx|,|dy| < {wl.trunc:g} h",
                        "h": wl.h, "levels": L, "precision": args.precision, "l2": "flushed between steps",
                        "replicas": world},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
@@ -382,6 +422,9 @@ def run_ours(args):
             "gpu_launches": int(launches),
             "recompute": {"handed_over_pixels": int(handed), "fp64_pixels": int(handed64),
                           "split_weight_tiles": int(retried)}}
+    if wl.trunc > 0:
+        line["truncated"] = {"support": wl.trunc, "pairs_in_support": pairs, "full_pairs": W * H * n,
+                             "full_sum_equivalent": world * W * H * n * D / (ms_step * 1e-3)}
     print(json.dumps(line), flush=True)
 
 
@@ -644,6 +687,8 @@ def main():
                     help="skip the plain FP32 comparison run")
     ap.add_argument("--workload", default="fourier10k", choices=["fourier10k", "batch64", "serve", "table1"],
                     help="the 10k-point render (default), 64 datasets in one graph, or the serving mix")
+    ap.add_argument("--support", type=float, default=0.0,
+                    help="truncated Gaussian: box half-width in units of h (0: the full sum)")
     ap.add_argument("--rate", type=float, default=200.0, help="serve: requests per second")
     ap.add_argument("--requests", type=int, default=400, help="serve: number of requests")
     ap.add_argument("--slots", type=int, default=8, help="serve: requests in flight at most")
