@@ -373,6 +373,75 @@ mls_status mls_sync(mls_handle *h, double timeout_s, mls_stats *stats);
 /* Release the handle and its device memory (waits for its stream). */
 mls_status mls_destroy(mls_handle *h);
 
+/*
+ * Space mappings (Section 3.4): the field rendered as an RGBA8 image.  The
+ * paper describes the renderings in words; the definitions taken, per pixel
+ * and shown plane f (one or two of the field's D planes):
+ *   grad   |(f_x, f_y)| in value units per pixel: central differences,
+ *          one-sided at the image edge or next to a NaN neighbour
+ *   band   b = #{j : t_j <= f} (as mls_bands)
+ *   lines  coverage clamp(w/2 + 1/2 - d, 0, 1), d = the pixel distance
+ *          min |f - t| / grad to the band's bounding levels; black
+ *   colours a three-anchor ramp (blue, grey, red) for one plane, or four
+ *          corners (blue; pink along the first plane; cyan along the
+ *          second) for two
+ *
+ *   MLS_MAP_LINES          contour lines, black on white
+ *   MLS_MAP_DISCRETE       one colour per band, sampled at (b + 1/2) / (L + 1)
+ *   MLS_MAP_DISCRETE_LINES both
+ *   MLS_MAP_ADAPTIVE       contour lines plus sub-levels: the band spacing
+ *                          halved k = 1..sublevels times, depth-k levels at
+ *                          odd multiples of spacing / 2^k above the band's
+ *                          lower level, faded in by their pixel spacing
+ *                          (spacing / 2^k / grad) between fade_lo and fade_hi:
+ *                          more lines where space is expanded, fewer where
+ *                          it is compressed
+ *   MLS_MAP_GRADIENT       colours at clamp((f - lo) / (hi - lo), 0, 1), with
+ *                          the contour lines over them
+ *   MLS_MAP_TEXTURE        a texture looked up (bilinear, clamp to edge) at
+ *                          those coordinates (the second 1/2 for one plane)
+ * A pixel where a shown plane is NaN is transparent (0, 0, 0, 0); others
+ * have alpha 255 (the texture's own alpha for MLS_MAP_TEXTURE).  Every step
+ * is IEEE float arithmetic in a fixed order: the bytes do not depend on the
+ * device.
+ */
+#define MLS_MAP_LINES 0
+#define MLS_MAP_DISCRETE 1
+#define MLS_MAP_DISCRETE_LINES 2
+#define MLS_MAP_ADAPTIVE 3
+#define MLS_MAP_GRADIENT 4
+#define MLS_MAP_TEXTURE 5
+
+typedef struct mls_map_desc {
+    int32_t mode;            /* MLS_MAP_* */
+    int32_t ndim;            /* planes shown: 1 or 2 */
+    int32_t dim[2];          /* their indices in [0, D) */
+    float line_width;        /* pixels, in [0, 1e4] */
+    float fade_lo, fade_hi;  /* MLS_MAP_ADAPTIVE: 0 <= fade_lo < fade_hi (pixels) */
+    int32_t sublevels;       /* MLS_MAP_ADAPTIVE: halvings, 0 .. 16 */
+    int32_t reserved;
+    double lo[2], hi[2];     /* MLS_MAP_GRADIENT / _TEXTURE: value range per shown plane (lo != hi) */
+    const uint8_t *texture;  /* MLS_MAP_TEXTURE: device, tex_h rows of tex_w RGBA8 texels */
+    int32_t tex_w, tex_h;    /* 1 .. 65536 */
+} mls_map_desc;
+
+/*
+ * Render the mapping of a field into rgba.
+ *   D, W, H     planes and raster of the field
+ *   field       device, D x H x W, float (field_fp64 = 0) or double (1)
+ *   levels      host, D x L doubles, ascending per plane, finite (rows of
+ *               the shown planes are read); L in [0, 254] (0: no lines, one
+ *               band)
+ *   rgba        device, H x W x 4 bytes out (row 0 at y0, like the field)
+ *   stream      CUDA stream of the work (NULL: the legacy default stream)
+ * No device allocation; the levels travel with the launch, so the call
+ * returns as soon as the kernel is queued.  Errors: MLS_E_INVAL (bad
+ * description, sizes, levels or pointers, before any launch),
+ * MLS_E_UNSUPPORTED (more than 524,280 rows), MLS_E_CUDA.
+ */
+mls_status mls_space_map(const mls_map_desc *m, int32_t D, int32_t W, int32_t H, const void *field,
+                         int32_t field_fp64, const double *levels, int32_t L, uint8_t *rgba, void *stream);
+
 /* Thread-local message of the last error ("" when none). */
 const char *mls_last_error(void);
 

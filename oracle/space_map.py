@@ -189,7 +189,8 @@ def space_map(field, levels, dims, mode, line_width=1.0, fade=(2.0, 6.0, 3), lo=
         s = [_clamp01((g - f32(l)) / (f32(h) - f32(l))) for (g, _, _), l, h in zip(terms, lo, hi)]
         if mode == TEXTURE:
             t = s[1] if len(dims) == 2 else np.full((H, W), f32(0.5), f32)
-            rgba = _texture(np.asarray(texture), s[0], t)
+            # transparent pixels (NaN coordinates) look up texel 0, then are cleared
+            rgba = _texture(np.asarray(texture), np.where(valid, s[0], f32(0.0)), np.where(valid, t, f32(0.0)))
             rgba[~valid] = 0
             return rgba
         col = _ramp(s[0]) if len(dims) == 1 else _corner(s[0], s[1])

@@ -17,7 +17,8 @@ from ._abi import (MLS_P_BF16, MLS_P_FP16, MLS_P_FP32, MLS_P_FP64, MLS_W_GAUSS, 
                    mls_abi_version, mls_bands, mls_batch_create, mls_batch_destroy, mls_batch_render,
                    mls_batch_sync, mls_create, mls_desc_default, mls_destroy, mls_last_error, mls_render,
                    mls_server_create, mls_server_destroy, mls_server_drain, mls_server_poll, mls_server_submit,
-                   mls_sync, MlsRequest)
+                   mls_sync, MlsRequest, MlsMapDesc, mls_space_map, MLS_MAP_LINES, MLS_MAP_DISCRETE,
+                   MLS_MAP_DISCRETE_LINES, MLS_MAP_ADAPTIVE, MLS_MAP_GRADIENT, MLS_MAP_TEXTURE)
 
 PRECISIONS = {"fp64": MLS_P_FP64, "fp32": MLS_P_FP32, "bf16": MLS_P_BF16, "fp16": MLS_P_FP16}
 
@@ -27,6 +28,41 @@ def _stream_ptr(stream):
         import torch
         return torch.cuda.current_stream().cuda_stream
     return int(stream)
+
+
+def space_map(field, levels, dims, mode, line_width=1.0, fade=(2.0, 6.0, 3), lo=None, hi=None, texture=None,
+              out=None, stream=None):
+    """Space mapping of Section 3.4 (``mls_space_map``): field (D, H, W)
+    float32/float64 CUDA tensor, levels (D, L) host array, dims one or two
+    plane indices, mode an MLS_MAP_* code; texture (Th, Tw, 4) uint8 CUDA
+    tensor for MLS_MAP_TEXTURE.  Returns (H, W, 4) uint8 on the device."""
+    import torch
+
+    if not field.is_cuda or field.dtype not in (torch.float32, torch.float64) or field.dim() != 3:
+        raise ValueError("field must be a (D, H, W) float32 or float64 CUDA tensor")
+    field = field.contiguous()
+    D, H, W = field.shape
+    dims = list(dims)
+    lev = np.ascontiguousarray(levels, dtype=np.float64).reshape(D, -1)
+    if out is None:
+        out = torch.empty((H, W, 4), dtype=torch.uint8, device=field.device)
+    d = MlsMapDesc()
+    d.mode, d.ndim = int(mode), len(dims)
+    for k, x in enumerate(dims):
+        d.dim[k] = int(x)
+    d.line_width = float(line_width)
+    d.fade_lo, d.fade_hi, d.sublevels = float(fade[0]), float(fade[1]), int(fade[2])
+    lo = lo if lo is not None else [0.0] * len(dims)
+    hi = hi if hi is not None else [1.0] * len(dims)
+    for k in range(len(dims)):
+        d.lo[k], d.hi[k] = float(lo[k]), float(hi[k])
+    if texture is not None:
+        texture = texture.contiguous()
+        d.texture = texture.data_ptr()
+        d.tex_h, d.tex_w = int(texture.shape[0]), int(texture.shape[1])
+    mls_space_map(d, D, W, H, field.data_ptr(), field.dtype == torch.float64, lev.ctypes.data, lev.shape[1],
+                  out.data_ptr(), _stream_ptr(stream))
+    return out
 
 
 class Renderer:

@@ -53,6 +53,8 @@ class MlsBatchStats(ctypes.Structure):
 
 MLS_BATCH_AUTOTUNE = 1
 MLS_V_POLY, MLS_V_RIGID, MLS_V_MEAN = 0, 1, 2
+(MLS_MAP_LINES, MLS_MAP_DISCRETE, MLS_MAP_DISCRETE_LINES, MLS_MAP_ADAPTIVE, MLS_MAP_GRADIENT,
+ MLS_MAP_TEXTURE) = range(6)
 
 
 class MlsServerConfig(ctypes.Structure):
@@ -74,6 +76,14 @@ class MlsRequestDone(ctypes.Structure):
 class MlsServerStats(ctypes.Structure):
     _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64), ("failed", ctypes.c_int64),
                 ("peak_inflight", ctypes.c_int64), ("peak_bytes", ctypes.c_int64)]
+
+
+class MlsMapDesc(ctypes.Structure):
+    _fields_ = [("mode", ctypes.c_int32), ("ndim", ctypes.c_int32), ("dim", ctypes.c_int32 * 2),
+                ("line_width", ctypes.c_float), ("fade_lo", ctypes.c_float), ("fade_hi", ctypes.c_float),
+                ("sublevels", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("lo", ctypes.c_double * 2), ("hi", ctypes.c_double * 2),
+                ("texture", ctypes.c_void_p), ("tex_w", ctypes.c_int32), ("tex_h", ctypes.c_int32)]
 
 
 class MlsError(RuntimeError):
@@ -136,6 +146,9 @@ def load(path: str | None = None):
     lib.mls_bands_noalloc.restype = ctypes.c_int
     lib.mls_bands_noalloc.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, P, ctypes.c_int32, P,
                                       ctypes.c_int32, P, P]
+    lib.mls_space_map.restype = ctypes.c_int
+    lib.mls_space_map.argtypes = [P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, P, ctypes.c_int32, P,
+                                  ctypes.c_int32, P, P]
     # test hooks (include/mls_debug.h)
     lib.mls_debug_wait_selftest.restype = ctypes.c_int
     lib.mls_debug_wait_selftest.argtypes = [ctypes.c_int64, ctypes.POINTER(ctypes.c_int)]
@@ -190,6 +203,13 @@ def mls_bands_noalloc(D: int, W: int, H: int, field_ptr: int, field_fp64: bool, 
     """Iso-band labels into caller buffers, without any device allocation."""
     _check(load().mls_bands_noalloc(int(D), int(W), int(H), P(field_ptr), int(bool(field_fp64)), P(levels_ptr),
                                     int(L), P(bands_ptr), P(stream)), "mls_bands_noalloc")
+
+
+def mls_space_map(desc: MlsMapDesc, D: int, W: int, H: int, field_ptr: int, field_fp64: bool, levels_ptr: int,
+                  L: int, rgba_ptr: int, stream: int = 0):
+    """Space mapping of Section 3.4 into a caller RGBA8 buffer (no allocation)."""
+    _check(load().mls_space_map(ctypes.byref(desc), int(D), int(W), int(H), P(field_ptr), int(bool(field_fp64)),
+                                P(levels_ptr), int(L), P(rgba_ptr), P(stream)), "mls_space_map")
 
 
 def mls_batch_create(handles, flags: int = 0) -> int:

@@ -6,6 +6,7 @@ import re
 import subprocess
 import tempfile
 
+import numpy as np
 import pytest
 
 from paper_1408_0677_gb300 import _abi, build
@@ -48,9 +49,10 @@ def test_struct_layout_matches_header():
 #include <stddef.h>
 #include "mls.h"
 int main(void) {
-  printf("%zu %zu %zu %zu %zu %zu %zu\n", sizeof(mls_desc), offsetof(mls_desc, h),
+  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(mls_desc), offsetof(mls_desc, h),
          offsetof(mls_desc, cond_recompute), offsetof(mls_desc, variant), offsetof(mls_desc, support),
-         sizeof(mls_view), sizeof(mls_stats));
+         sizeof(mls_view), sizeof(mls_stats), sizeof(mls_map_desc), offsetof(mls_map_desc, lo),
+         offsetof(mls_map_desc, texture));
   return 0;
 }
 '''
@@ -62,7 +64,8 @@ int main(void) {
         vals = [int(x) for x in subprocess.check_output([exe]).split()]
     assert vals == [ctypes.sizeof(_abi.MlsDesc), _abi.MlsDesc.h.offset, _abi.MlsDesc.cond_recompute.offset,
                     _abi.MlsDesc.variant.offset, _abi.MlsDesc.support.offset,
-                    ctypes.sizeof(_abi.MlsView), ctypes.sizeof(_abi.MlsStats)]
+                    ctypes.sizeof(_abi.MlsView), ctypes.sizeof(_abi.MlsStats), ctypes.sizeof(_abi.MlsMapDesc),
+                    _abi.MlsMapDesc.lo.offset, _abi.MlsMapDesc.texture.offset]
 
 
 def test_abi_version_and_defaults(lib):
@@ -135,3 +138,38 @@ def test_injected_allocation_failure_returns_nomem(lib, monkeypatch):
     with pytest.raises(_abi.MlsError) as e:
         _abi.mls_create(_desc(), ctypes.addressof(buf), ctypes.addressof(buf), False)
     assert e.value.status == _abi.MLS_E_NOMEM
+
+
+def _map_desc(**kw):
+    d = _abi.MlsMapDesc()
+    d.mode, d.ndim, d.line_width = _abi.MLS_MAP_LINES, 1, 1.0
+    d.fade_lo, d.fade_hi, d.sublevels = 2.0, 6.0, 3
+    d.lo[0], d.hi[0], d.lo[1], d.hi[1] = 0.0, 1.0, 0.0, 1.0
+    for k, v in kw.items():
+        setattr(d, k, v)
+    return d
+
+
+@pytest.mark.parametrize("kw,D,L,levels", [
+    (dict(mode=6), 1, 2, [0.0, 1.0]),
+    (dict(ndim=3), 1, 2, [0.0, 1.0]),
+    (dict(ndim=2), 1, 2, [0.0, 1.0]),                 # dim[1] = 1 is out of range for D = 1
+    (dict(line_width=-1.0), 1, 2, [0.0, 1.0]),
+    (dict(mode=_abi.MLS_MAP_ADAPTIVE, fade_lo=6.0, fade_hi=2.0), 1, 2, [0.0, 1.0]),
+    (dict(mode=_abi.MLS_MAP_ADAPTIVE, sublevels=17), 1, 2, [0.0, 1.0]),
+    (dict(mode=_abi.MLS_MAP_TEXTURE), 1, 2, [0.0, 1.0]),          # no texture
+    (dict(mode=_abi.MLS_MAP_GRADIENT), 1, 2, [0.0, 1.0]),         # lo == hi set below
+    (dict(), 1, 2, [1.0, 0.0]),                                   # levels descend
+    (dict(), 1, 255, None),                                       # too many levels
+])
+def test_space_map_rejects_bad_arguments_before_any_launch(lib, kw, D, L, levels):
+    d = _map_desc(**kw)
+    if kw.get("mode") == _abi.MLS_MAP_GRADIENT:
+        d.hi[0] = d.lo[0]
+    if kw.get("ndim") == 2:
+        d.dim[1] = 1                                   # out of range for D = 1
+    lev = np.asarray(levels if levels is not None else np.arange(L), dtype=np.float64)
+    buf = (ctypes.c_double * 64)()
+    with pytest.raises(_abi.MlsError) as e:
+        _abi.mls_space_map(d, D, 4, 4, ctypes.addressof(buf), False, lev.ctypes.data, L, ctypes.addressof(buf))
+    assert e.value.status == _abi.MLS_E_INVAL
