@@ -674,6 +674,196 @@ def run_table1(args):
     print(json.dumps(line), flush=True)
 
 
+def _time_launches(fn, stream, steps, warmup):
+    """Device time of each of `steps` calls of fn (CUDA events on `stream`)."""
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(steps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        e1.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    return ts
+
+
+def run_spacemap(args):
+    """Space mappings (Section 3.4, mls_space_map) of an 8192 x 8192 two-plane
+    FP32 field (512 MiB, larger than L2, so no flush is needed) into RGBA8:
+    every mode, device time per launch against the HBM roofline.  The
+    algorithmic bytes of a launch are the shown planes read once and the image
+    written once: (4 * planes + 4) bytes per pixel."""
+    import torch
+    world, rank, local = _dist()
+    torch.cuda.set_device(local)
+    import paper_1408_0677_gb300 as G
+    from oracle import space_map as SM   # the CPU baseline leg only
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    W = H = 8192
+    u = torch.arange(W, device=dev, dtype=torch.float32)[None, :]
+    v = torch.arange(H, device=dev, dtype=torch.float32)[:, None]
+    F = torch.stack([torch.sin(u * 0.004) * torch.cos(v * 0.003) + u * 1e-4,
+                     torch.cos(u * 0.002 + v * 0.005) + v * 1e-4]).contiguous()
+    lo = F.amin(dim=(1, 2)).double().cpu().numpy()
+    hi = F.amax(dim=(1, 2)).double().cpu().numpy()
+    L = 16
+    lev = lo[:, None] + (hi - lo)[:, None] * (np.arange(1, L + 1) / (L + 1))[None, :]
+    tex = torch.randint(0, 256, (256, 256, 4), dtype=torch.uint8, device=dev)
+    out = torch.empty((H, W, 4), dtype=torch.uint8, device=dev)
+    modes = [("lines", G.MLS_MAP_LINES, [0]), ("discrete", G.MLS_MAP_DISCRETE, [0]),
+             ("discrete_lines", G.MLS_MAP_DISCRETE_LINES, [0]), ("adaptive", G.MLS_MAP_ADAPTIVE, [0, 1]),
+             ("gradient", G.MLS_MAP_GRADIENT, [0, 1]), ("texture", G.MLS_MAP_TEXTURE, [0, 1])]
+    peaks, src = _peaks()
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    rows, launches = {}, 0
+    for name, mode, dims in modes:
+        def call():
+            G.space_map(F, lev, dims, mode, line_width=1.5, fade=(2.0, 6.0, 3), lo=list(lo[dims]),
+                        hi=list(hi[dims]), texture=tex, out=out, stream=stream.cuda_stream)
+        ts = _time_launches(call, stream, args.steps, args.warmup)
+        launches += args.steps
+        ms = float(np.mean(ts))
+        nbytes = (4 * len(dims) + 4) * W * H
+        rows[name] = {"planes": len(dims), "ms": ms, "pixels_per_s": W * H / (ms * 1e-3),
+                      "gbs": nbytes / (ms * 1e-3) / 1e9, "frac_hbm": nbytes / (ms * 1e-3) / 1e9 / hbm}
+    clocks = sampler.stop()
+    head = rows["adaptive"]
+    # end to end through the public call: pinned host field in, image back to pinned host memory
+    Fh = torch.empty(F.shape, dtype=F.dtype).pin_memory()
+    Fh.copy_(F)
+    outh = torch.empty(out.shape, dtype=out.dtype).pin_memory()
+    Fd = torch.empty_like(F)
+
+    def e2e_step():
+        Fd.copy_(Fh, non_blocking=True)
+        G.space_map(Fd, lev, [0, 1], G.MLS_MAP_ADAPTIVE, line_width=1.5, fade=(2.0, 6.0, 3), out=out,
+                    stream=stream.cuda_stream)
+        outh.copy_(out, non_blocking=True)
+        torch.cuda.synchronize()
+
+    e2e_step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        e2e_step()
+    e2e_ms = 1e3 * (time.perf_counter() - t0) / args.steps
+    # the oracle (numpy float32 statement) on a 1024 x 1024 crop, one core
+    crop = F[:, :1024, :1024].cpu().numpy()
+    t0 = time.perf_counter()
+    SM.space_map(crop, lev, [0, 1], SM.ADAPTIVE, line_width=1.5, fade=(2.0, 6.0, 3))
+    cpu_s = time.perf_counter() - t0
+    if rank != 0:
+        return
+    nbytes = 12 * W * H
+    line = {"metric": "space-mapped pixels/s", "value": world * head["pixels_per_s"], "unit": "pixel/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": head["ms"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "spacemap_8192sq_2planes_f32_L16_adaptive", "W": W, "H": H, "levels": L,
+                       "mode": "adaptive lines, two planes, 3 halvings", "l2": "inputs larger than L2"},
+            "modes": rows,
+            "e2e": {"value": world * W * H / (e2e_ms * 1e-3), "unit": "pixel/s",
+                    "h2d_bytes_per_step": int(F.numel() * 4), "d2h_bytes_per_step": int(out.numel()),
+                    "ms_per_step": e2e_ms},
+            "roofline": {"bound": "hbm", "achieved": nbytes / (head["ms"] * 1e-3) / 1e9, "peak": hbm,
+                         "unit": "GB/s", "frac": nbytes / (head["ms"] * 1e-3) / 1e9 / hbm, "traffic": None,
+                         "peak_source": f"{src} copy bandwidth", "kernel": "k_space_map",
+                         "bytes_per_launch": nbytes},
+            "cpu_baseline": {"value": 1024 * 1024 / cpu_s, "unit": "pixel/s", "cores": 1, "kind": "oracle",
+                             "sample": f"1024 x 1024 crop, adaptive, numpy float32, {cpu_s:.2f} s"},
+            "clocks": clocks, "gpu_launches": launches}
+    print(json.dumps(line), flush=True)
+
+
+def run_variants(args):
+    """The rigid (Section 3.3.3) and mean (Section 3.3.1) mappings of 2-D
+    values: the 10k points' positions as p and a smooth distortion of them as
+    the values q, 1024 x 1024, Gaussian h = 0.02 over every point, FP32
+    (k_mls_variant), with 16 iso-levels per component."""
+    import torch
+    world, rank, local = _dist()
+    torch.cuda.set_device(local)
+    from paper_1408_0677_gb300 import MLS_V_MEAN, MLS_V_RIGID, Renderer, inputs
+    import oracle
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    wl = inputs.fourier_10k()
+    p = wl.xy
+    q = p + 0.01 * np.stack([np.sin(6 * np.pi * p[:, 1]), np.cos(6 * np.pi * p[:, 0])], axis=1)
+    W = H = 1024
+    n = p.shape[0]
+    lev = inputs.default_levels(q, 16)
+    pd, qd = torch.from_numpy(p).to(dev), torch.from_numpy(q).to(dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    peaks, src = _peaks()
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    rows, launches = {}, 0
+    for name, var in (("rigid", MLS_V_RIGID), ("mean", MLS_V_MEAN)):
+        r = Renderer(pd, qd, degree=1, weight=inputs.WEIGHT_GAUSS, h=0.02, precision=args.precision, variant=var,
+                     stream=stream.cuda_stream)
+
+        def call():
+            flush.fill_(1.0)
+            r.render(W, H, levels=lev)
+
+        for _ in range(args.warmup):
+            call()
+            r.sync()
+        ts = []
+        for _ in range(args.steps):
+            flush.fill_(1.0)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            r.render(W, H, levels=lev)
+            e1.record(stream)
+            st = r.sync()
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+            launches += st.launches
+        r.close()
+        ms = float(np.mean(ts))
+        rows[name] = {"ms": ms, "value": W * H * n * 2 / (ms * 1e-3)}
+    clocks = sampler.stop()
+    # the oracle on a bounded pixel sample (all host cores)
+    threads = os.cpu_count() or 1
+    pix = np.random.default_rng(9).choice(W * H, size=2048, replace=False)
+    t0 = time.perf_counter()
+    oracle.mls_variant(p, q, oracle.VARIANT_RIGID, inputs.WEIGHT_GAUSS, 0.02, W, H, pixels=pix, threads=threads)
+    cpu_s = time.perf_counter() - t0
+    if rank != 0:
+        return
+    # FP32 work per pair of the rigid kernel: offsets and r^2 (5), weight (3 + ex2),
+    # Welford update (1 divide + 17): about 25 flop; peak = 152 SMs x 128 FP32
+    # lanes x 2 flop per FMA x the maximum SM clock
+    flop = 25.0 * W * H * n
+    peak = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    ach = flop / (rows["rigid"]["ms"] * 1e-3) / 1e12
+    line = {"metric": METRIC, "value": world * rows["rigid"]["value"], "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": rows["rigid"]["ms"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.precision != "fp64" else "f64",
+            "data": "synthetic",
+            "config": {"workload": "rigid_mls_n10k_d2_1024x1024_gauss_h0.02_L16", "n": n, "D": 2, "W": W, "H": H,
+                       "l2": "flushed between steps"},
+            "variants": rows, "e2e": None,
+            "roofline": {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                         "traffic": None, "peak_source": "FP32 FMA rate from unit counts and the maximum SM clock",
+                         "kernel": "k_mls_variant", "flop_per_pair": 25},
+            "cpu_baseline": {"value": 2048 * n * 2 / cpu_s, "unit": UNIT, "cores": threads, "kind": "oracle",
+                             "sample": f"2048 random pixels, rigid, full n={n} sum each, FP64, {cpu_s:.2f} s"},
+            "clocks": clocks, "gpu_launches": launches}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -685,7 +875,8 @@ def main():
     ap.add_argument("--weight-split", type=int, default=None, choices=[0, 1, 2])
     ap.add_argument("--no-compare-fp32", dest="compare_fp32", action="store_false",
                     help="skip the plain FP32 comparison run")
-    ap.add_argument("--workload", default="fourier10k", choices=["fourier10k", "batch64", "serve", "table1"],
+    ap.add_argument("--workload", default="fourier10k",
+                    choices=["fourier10k", "batch64", "serve", "table1", "spacemap", "variants"],
                     help="the 10k-point render (default), 64 datasets in one graph, or the serving mix")
     ap.add_argument("--support", type=float, default=0.0,
                     help="truncated Gaussian: box half-width in units of h (0: the full sum)")
@@ -704,6 +895,12 @@ def main():
         run_serve(args)
     elif args.workload == "table1":
         run_table1(args)
+    elif args.workload == "spacemap":
+        run_spacemap(args)
+    elif args.workload == "variants":
+        if args.precision in ("fp16", "bf16"):
+            args.precision = "fp32"      # the mappings run on the CUDA-core kernel
+        run_variants(args)
     else:
         run_ours(args)
 

@@ -437,7 +437,7 @@ typedef struct mls_map_desc {
  * No device allocation; the levels travel with the launch, so the call
  * returns as soon as the kernel is queued.  Errors: MLS_E_INVAL (bad
  * description, sizes, levels or pointers, before any launch),
- * MLS_E_UNSUPPORTED (more than 524,280 rows), MLS_E_CUDA.
+ * MLS_E_UNSUPPORTED (more than 2,097,120 rows), MLS_E_CUDA.
  */
 mls_status mls_space_map(const mls_map_desc *m, int32_t D, int32_t W, int32_t H, const void *field,
                          int32_t field_fp64, const double *levels, int32_t L, uint8_t *rgba, void *stream);

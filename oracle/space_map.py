@@ -8,6 +8,9 @@ describes them in words only; this module writes down the reading used here
 in plain numpy, one image-wide step at a time.  Every step is a float32
 operation (+, -, *, /, sqrt, floor, comparisons) in a fixed order, so that a
 kernel doing the same operations in the same order gives the same bytes.
+Quotients are taken as products with a reciprocal formed once (1/grad and
+1/spacing per pixel and plane, 1/(L + 1), 1/(hi - lo), 1/(fade_hi - fade_lo)
+per image), which is the float sequence of this reading.
 
 Per pixel and shown dimension d (one or two of the field's planes):
   g      the field value rounded to float32
@@ -15,7 +18,7 @@ Per pixel and shown dimension d (one or two of the field's planes):
          at the image edge or next to a NaN neighbour, 0 with no neighbour
   b      the band #{t_j <= f} (compared in the field's own precision)
   delta  distance in pixels to the nearer bounding level of the band,
-         min |g - t| / grad (0 on a level, infinite where grad = 0)
+         min |g - t| * (1 / grad) (0 on a level, infinite where grad = 0)
   cov    line coverage clamp(w/2 + 1/2 - delta, 0, 1) (a one-pixel ramp at the
          edge of a line of width w)
 Adaptive lines: the band's level spacing is halved k = 1..K times; a level of
@@ -72,10 +75,15 @@ def gradient(g):
     return np.sqrt(gx * gx + gy * gy).astype(f32)
 
 
-def _px_distance(dv, grad):
-    with np.errstate(divide="ignore", invalid="ignore"):
-        q = dv / grad
-    return np.where(grad > 0, q, np.where(dv == 0, f32(0.0), f32(np.inf))).astype(f32)
+def _recip(x):
+    with np.errstate(divide="ignore"):
+        return (f32(1.0) / x).astype(f32)
+
+
+def _px_distance(dv, grad, inv_grad):
+    with np.errstate(invalid="ignore"):
+        q = dv * inv_grad
+    return np.where(dv == 0, f32(0.0), np.where(grad > 0, q, f32(np.inf))).astype(f32)
 
 
 def _coverage(delta, w):
@@ -95,6 +103,7 @@ def dim_terms(field_d, lev_d, w, adaptive=None):
     L = len(lev_d)
     g = field_d.astype(f32)
     grad = gradient(g)
+    inv_grad = _recip(grad)
     b = _band(field_d, lev_d)
     t32 = lev_d.astype(f32)
     dv = np.full(g.shape, np.inf, f32)
@@ -104,7 +113,7 @@ def dim_terms(field_d, lev_d, w, adaptive=None):
         dlo = np.where(b >= 1, np.abs(g - t32[bl]), f32(np.inf))
         dhi = np.where(b < L, np.abs(g - t32[bh]), f32(np.inf))
         dv = np.minimum(dlo, dhi)
-    cov = _coverage(_px_distance(dv, grad), w)
+    cov = _coverage(_px_distance(dv, grad, inv_grad), w)
     if adaptive is not None and L >= 2:
         fade_lo, fade_hi, K = adaptive
         inner = (b >= 1) & (b <= L - 1)
@@ -113,17 +122,19 @@ def dim_terms(field_d, lev_d, w, adaptive=None):
         spacing = np.where(inner, t32[bh] - t32[bl],
                            np.where(b == 0, t32[1] - t32[0], t32[L - 1] - t32[L - 2]))
         base = np.where(inner, t32[bl], np.where(b == 0, t32[0] - spacing, t32[L - 1]))
-        ok = spacing > 0
-        den = f32(fade_hi) - f32(fade_lo)
+        inv_spacing = _recip(spacing)
+        ok = (spacing > 0) & np.isfinite(inv_spacing)
+        inv_den = _recip(f32(fade_hi) - f32(fade_lo))
         for k in range(1, K + 1):
             dk = spacing * f32(1.0 / (1 << k))
-            with np.errstate(divide="ignore", invalid="ignore"):
-                sp = np.where(grad > 0, dk / grad, f32(np.inf))
-                alpha = _clamp01((sp - f32(fade_lo)) / den)
-                r = (g - base) / dk
+            inv_dk = inv_spacing * f32(1 << k)
+            with np.errstate(invalid="ignore", over="ignore"):
+                sp = np.where(grad > 0, dk * inv_grad, f32(np.inf))
+                alpha = _clamp01((sp - f32(fade_lo)) * inv_den)
+                r = (g - base) * inv_dk
             m = f32(2.0) * np.floor(r * f32(0.5)) + f32(1.0)
             dist = np.abs(r - m) * dk
-            ck = _coverage(_px_distance(dist, grad), w) * alpha
+            ck = _coverage(_px_distance(dist, grad, inv_grad), w) * alpha
             cov = np.where(ok & (alpha > 0), np.maximum(cov, ck), cov)
     return g, b, cov
 
@@ -183,10 +194,10 @@ def space_map(field, levels, dims, mode, line_width=1.0, fade=(2.0, 6.0, 3), lo=
             cov = np.maximum(cov, c)
     black = np.zeros(3, f32)
     if mode in (DISCRETE, DISCRETE_LINES):
-        s = [(b.astype(f32) + f32(0.5)) / f32(L + 1) for _, b, _ in terms]
+        s = [(b.astype(f32) + f32(0.5)) * _recip(f32(L + 1)) for _, b, _ in terms]
         col = _ramp(s[0]) if len(dims) == 1 else _corner(s[0], s[1])
     elif mode in (GRADIENT, TEXTURE):
-        s = [_clamp01((g - f32(l)) / (f32(h) - f32(l))) for (g, _, _), l, h in zip(terms, lo, hi)]
+        s = [_clamp01((g - f32(l)) * _recip(f32(h) - f32(l))) for (g, _, _), l, h in zip(terms, lo, hi)]
         if mode == TEXTURE:
             t = s[1] if len(dims) == 2 else np.full((H, W), f32(0.5), f32)
             # transparent pixels (NaN coordinates) look up texel 0, then are cleared

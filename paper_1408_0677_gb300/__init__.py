@@ -13,7 +13,7 @@ import numpy as np
 
 from . import _abi
 from ._abi import (MLS_P_BF16, MLS_P_FP16, MLS_P_FP32, MLS_P_FP64, MLS_W_GAUSS, MLS_W_INVDIST,  # noqa: F401
-                   MLS_W_WENDLAND, MLS_BATCH_AUTOTUNE, MlsBatchStats, MlsDesc, MlsError, MlsStats, MlsView,
+                   MLS_W_WENDLAND, MLS_BATCH_AUTOTUNE, MLS_V_POLY, MLS_V_RIGID, MLS_V_MEAN, MlsBatchStats, MlsDesc, MlsError, MlsStats, MlsView,
                    mls_abi_version, mls_bands, mls_batch_create, mls_batch_destroy, mls_batch_render,
                    mls_batch_sync, mls_create, mls_desc_default, mls_destroy, mls_last_error, mls_render,
                    mls_server_create, mls_server_destroy, mls_server_drain, mls_server_poll, mls_server_submit,

@@ -119,13 +119,15 @@ def test_pin(pin):
 MUTANTS = [
     ("central difference without the half", "both = (gr - gl) * f32(0.5)", "both = (gr - gl)"),
     ("line ramp not centred on the edge", "(f32(w) * f32(0.5) + f32(0.5)) - delta", "f32(w) * f32(0.5) - delta"),
-    ("band colour sampled at b / L", "(b.astype(f32) + f32(0.5)) / f32(L + 1)", "b.astype(f32) / f32(L)"),
+    ("band colour sampled at b / L", "(b.astype(f32) + f32(0.5)) * _recip(f32(L + 1))",
+     "b.astype(f32) * _recip(f32(L))"),
     ("sub-levels at even multiples", "m = f32(2.0) * np.floor(r * f32(0.5)) + f32(1.0)",
      "m = f32(2.0) * np.floor(r * f32(0.5))"),
     ("texture sampled at the texel corner", "x = s * f32(Tw) - f32(0.5)", "x = s * f32(Tw)"),
     ("corner colours swapped", "a = _lerp(CORNERS[0], CORNERS[1], s[..., None])",
      "a = _lerp(CORNERS[0], CORNERS[2], s[..., None])"),
-    ("fade inverted", "alpha = _clamp01((sp - f32(fade_lo)) / den)", "alpha = _clamp01((f32(fade_hi) - sp) / den)"),
+    ("fade inverted", "alpha = _clamp01((sp - f32(fade_lo)) * inv_den)",
+     "alpha = _clamp01((f32(fade_hi) - sp) * inv_den)"),
 ]
 
 
