@@ -31,6 +31,16 @@ int mls_debug_wait_selftest(int64_t limit_ns, int *code_out);
  * MLS_E_NOMEM / MLS_E_CUDA on device failures, MLS_OK otherwise. */
 int mls_debug_df_weight(int kind, const float *arg_hi, const float *arg_lo, int64_t n, double *out);
 
+/* Reduced-precision Gaussian renders visit, per 16 x 16 tile, only the points
+ * whose weight at some pixel of the tile is at least e^-28 of that pixel's
+ * largest (below it an FP16 weight rounds to exactly zero and a BF16 / FP32
+ * product lies below the FP32 resolution of the sums).  on = 0 makes the
+ * handle's later renders visit every point, so that a test can check that
+ * the cut changes nothing beyond FP32 rounding.  Returns MLS_E_INVAL for a
+ * null handle, MLS_OK otherwise. */
+struct mls_handle;
+int mls_debug_operand_cut(struct mls_handle *h, int32_t on);
+
 #ifdef __cplusplus
 }
 #endif

@@ -152,6 +152,8 @@ def load(path: str | None = None):
     # test hooks (include/mls_debug.h)
     lib.mls_debug_wait_selftest.restype = ctypes.c_int
     lib.mls_debug_wait_selftest.argtypes = [ctypes.c_int64, ctypes.POINTER(ctypes.c_int)]
+    lib.mls_debug_operand_cut.restype = ctypes.c_int
+    lib.mls_debug_operand_cut.argtypes = [P, ctypes.c_int32]
     lib.mls_debug_df_weight.restype = ctypes.c_int
     lib.mls_debug_df_weight.argtypes = [ctypes.c_int, P, P, ctypes.c_int64, P]
     if path == _build.LIB:

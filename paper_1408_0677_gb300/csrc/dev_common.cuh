@@ -35,6 +35,14 @@ constexpr uint64_t kWaitLimitNs = 2000000000ull;  // 2 s
 constexpr int kCntBoundary = 1 << 30;
 constexpr int kCntMask = kCntBoundary - 1;
 constexpr float kCntEdgeTol = 4e-6f;
+// Reduced-precision Gaussian renders visit, per tile, only the points within
+// h sqrt(max_p m_p + kGaussOperandCut) of its pixels.  Every pair left out has
+// weight below e^-28 < 2^-40 of its pixel's largest: FP16 weights (largest
+// scaled to 2^14) round such a weight to exactly zero (below 2^-25), and in
+// BF16 or FP32 it lies below the FP32 resolution of the sums (at most n
+// e^-28 of the largest weight's share for n < 2^16 points).  FP64 renders sum
+// every pair.
+constexpr float kGaussOperandCut = 28.f;
 
 // Monomials of degree <= 4 in (x, y), the entries of the moment matrix:
 // 0:1 1:x 2:y 3:xx 4:xy 5:yy 6:xxx 7:xxy 8:xyy 9:yyy 10:xxxx 11:xxxy 12:xxyy 13:xyyy 14:yyyy
@@ -107,6 +115,9 @@ struct KParams {
   const float *mstab;          // [tiles_y*16][tiles_x*16] stabiliser min r^2 / s^2
   const int *cnt;              // same shape, Wendland in-support counts
   const float *tcen;           // [tiles_y][tiles_x][2] moment frame centre of each tile (scaled)
+  const float *tmax;           // [tiles_y][tiles_x] largest stabiliser of the tile's pixels (units of h^2)
+  float gcut;                  // > 0: Gaussian tiles visit points within h sqrt(tmax + gcut) only
+  unsigned long long *visited; // non-null: the tensor kernel adds the pixel-point pairs it visits
   int *relist;                 // pixels handed to the FP64 path
   unsigned int *relist_count;
   int *err;

@@ -112,7 +112,7 @@ size_t scratch_bytes_for(int W, int H) {
   const size_t padded = (size_t)tx * kTile * ty * kTile;
   const size_t ntile = (size_t)tx * ty;
   return 256 + padded * sizeof(float) + padded * sizeof(int) + 2 * (size_t)W * H * sizeof(int) +
-         2 * ntile * sizeof(float) + 2 * ntile * sizeof(int) + 256;
+         3 * ntile * sizeof(float) + 2 * ntile * sizeof(int) + 256;
 }
 
 // Grow a render context's scratch to fit a view.
@@ -133,6 +133,7 @@ static mls_status ensure_scratch(RenderCtx *c, int W, int H, cudaStream_t st) {
   }
   char *b = (char *)c->scratch;
   c->counters = (unsigned int *)b;           // [0] hand-over count, [1] FP64 count, [2] retried tiles
+  c->visited = (unsigned long long *)(b + 16);
   c->err = (int *)(b + 64);
   c->mstab = (float *)(b + 256);
   c->cnt = (int *)(b + 256 + padded * sizeof(float));
@@ -141,6 +142,7 @@ static mls_status ensure_scratch(RenderCtx *c, int W, int H, cudaStream_t st) {
   c->tcen = (float *)(c->relist2 + (size_t)W * H);
   c->tile_mark = (int *)(c->tcen + 2 * ntile);
   c->retry_tiles = c->tile_mark + ntile;
+  c->tmax = (float *)(c->retry_tiles + ntile);
   return MLS_OK;
 }
 
@@ -257,6 +259,11 @@ static mlsk::KParams base_params(const mls_handle *h, const RenderCtx *c, const 
   p.mstab = c->mstab;
   p.cnt = c->cnt;
   p.tcen = c->tcen;
+  p.tmax = c->tmax;
+  p.gcut = (h->operand_cut && d.precision != MLS_P_FP64 && d.weight == MLS_W_GAUSS && !(d.support > 0.0) &&
+            d.variant == MLS_V_POLY)
+               ? mlsk::kGaussOperandCut
+               : 0.f;
   p.relist = c->relist;
   p.relist_count = c->counters;
   p.err = c->err;
@@ -451,6 +458,7 @@ static mls_status render_enqueue(mls_handle *h, RenderCtx *c, const mlsk::KParam
     const double tile_h = kTile * fmax(fabs(p.sx), fabs(p.sy)) / h->desc.h;
     if (tile_h > kTileFrameMaxH || h->desc.precision == MLS_P_FP32 || h->desc.weight == MLS_W_INVDIST) {
       mlsk::KParams pf = p;
+      pf.visited = c->visited;
       pf.pixel_frame = tile_h > kTileFrameMaxH ? 1 : 0;
       pf.lambda_max = 1000.f;
       launch_f32(pf, st);
@@ -465,6 +473,7 @@ static mls_status render_enqueue(mls_handle *h, RenderCtx *c, const mlsk::KParam
         const int ntile = p.tiles_x * p.tiles_y;
         MLS_CUDA_TRY(cudaMemsetAsync(c->tile_mark, 0, sizeof(int) * ntile, st));
         mlsk::KParams p1 = p;
+        p1.visited = c->visited;
         p1.retry_tiles = c->retry_tiles;
         p1.retry_count = c->counters + 2;
         p1.tile_mark = c->tile_mark;
@@ -478,7 +487,9 @@ static mls_status render_enqueue(mls_handle *h, RenderCtx *c, const mlsk::KParam
         if ((s = launch_tc(p2, fp16, 1, st, &nl)) != MLS_OK) return s;
         launches += nl;
       } else {
-        if ((s = launch_tc(p, fp16, h->desc.weight_split, st, &nl)) != MLS_OK) return s;
+        mlsk::KParams p1 = p;
+        p1.visited = c->visited;
+        if ((s = launch_tc(p1, fp16, h->desc.weight_split, st, &nl)) != MLS_OK) return s;
         launches += 1 + nl;
         if (timing) MLS_CUDA_TRY(cudaEventRecord(h->evk1, st));
       }
@@ -584,14 +595,16 @@ mls_status mls_sync(mls_handle *h, double timeout_s, mls_stats *stats) {
     std::this_thread::sleep_for(std::chrono::microseconds(50));
   }
   unsigned int cnt[3] = {0, 0, 0};
+  unsigned long long visited = 0;
   int err = 0;
   if (h->ctx.scratch) {
     MLS_CUDA_TRY(cudaMemcpy(cnt, h->ctx.counters, sizeof cnt, cudaMemcpyDeviceToHost));
+    MLS_CUDA_TRY(cudaMemcpy(&visited, h->ctx.visited, sizeof visited, cudaMemcpyDeviceToHost));
     MLS_CUDA_TRY(cudaMemcpy(&err, h->ctx.err, sizeof err, cudaMemcpyDeviceToHost));
   }
   if (stats) {
     memset(stats, 0, sizeof *stats);
-    stats->pairs = h->last_pairs;
+    stats->pairs = visited ? (int64_t)visited : h->last_pairs;
     stats->recomputed = cnt[0];
     stats->recomputed_fp64 = cnt[1];
     stats->retried_tiles = cnt[2];
@@ -603,6 +616,12 @@ mls_status mls_sync(mls_handle *h, double timeout_s, mls_stats *stats) {
     cudaGetLastError();
   }
   if (err) return fail(MLS_E_TIMEOUT, "a bounded device wait gave up (error word " + std::to_string(err) + ")");
+  return MLS_OK;
+}
+
+int mls_debug_operand_cut(mls_handle *h, int32_t on) {
+  if (!h) return fail(MLS_E_INVAL, "handle is NULL");
+  h->operand_cut = on != 0;
   return MLS_OK;
 }
 

@@ -50,6 +50,8 @@ struct RenderCtx {
   unsigned int *counters = nullptr;  // [0] recompute count, [1] FP64 count, [2] retried tiles
   int *tile_mark = nullptr;          // per tile: queued for the split-weight pass
   int *retry_tiles = nullptr;
+  float *tmax = nullptr;             // per-tile largest stabiliser (Gaussian)
+  unsigned long long *visited = nullptr;   // pixel-point pairs the main kernel visited
   int *err = nullptr;
   double *lev64 = nullptr;
   float *lev32 = nullptr;
@@ -74,6 +76,7 @@ struct mls_handle {
   int64_t launches = 0;              // kernels launched by this handle
   int64_t last_pairs = 0;
   bool timed = false;
+  bool operand_cut = true;           // reduced-precision Gaussian: skip pairs whose weight rounds to zero
 };
 
 namespace mlsi {

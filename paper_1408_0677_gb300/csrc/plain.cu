@@ -72,10 +72,15 @@ __global__ __launch_bounds__(128) void k_mls_f32(KParams p) {
   const int cflag = binned ? p.cnt[(size_t)v * pstride + u] : 0;
   const int count = binned ? (cflag & kCntMask) : (int)(p.n < (1 << 30) ? p.n : (1 << 30));
   const float alpha = (float)p.alpha;
-  // point ranges: all points, or the cell rows overlapping the block's pixels +- h (+- c h)
+  // point ranges: all points, or the cell rows overlapping the block's pixels
+  // +- h (+- c h; Gaussian: +- h sqrt(max m + gcut), beyond which every weight
+  // is below FP32 resolution of the sums)
+  const bool cut = (WK == MLS_W_GAUSS) && !binned && p.gcut > 0.f;
   int nr = 1, cx0 = 0, cx1 = 0, cy0 = 0;
-  if (binned) {
-    const double rad = (WK == MLS_W_WENDLAND) ? p.h : p.trunc * p.h * (1.0 + 1e-5);
+  if (binned || cut) {
+    const double rad = (WK == MLS_W_WENDLAND) ? p.h
+                       : binned ? p.trunc * p.h * (1.0 + 1e-5)
+                                : p.h * sqrt((double)p.tmax[tile] + (double)p.gcut) * (1.0 + 1e-5);
     const int bu0 = blockIdx.x * 16, bv0 = blockIdx.y * 8;
     const double xa = p.x0 + (bu0 + 0.5) * p.sx, xb = p.x0 + (bu0 + 15.5) * p.sx;
     const double ya = p.y0 + (bv0 + 0.5) * p.sy, yb = p.y0 + (bv0 + 7.5) * p.sy;
@@ -105,7 +110,7 @@ __global__ __launch_bounds__(128) void k_mls_f32(KParams p) {
     for (int dd = 0; dd < DC; ++dd) csum[dd] = 0.f;
     for (int r = 0; r < nr; ++r) {
       int a0, a1;
-      if (binned) {
+      if (binned || cut) {
         a0 = p.cell_start[(cy0 + r) * p.gx + cx0];
         a1 = p.cell_start[(cy0 + r) * p.gx + cx1 + 1];
       } else {
@@ -159,6 +164,15 @@ __global__ __launch_bounds__(128) void k_mls_f32(KParams p) {
           }
         }
       }
+    }
+    if (p.visited && d0 == 0 && t == 0) {
+      // pixel-point pairs of this block (points in its ranges x 128 pixels)
+      unsigned long long npts = 0;
+      for (int r = 0; r < nr; ++r)
+        npts += (binned || cut) ? (unsigned long long)(p.cell_start[(cy0 + r) * p.gx + cx1 + 1] -
+                                                       p.cell_start[(cy0 + r) * p.gx + cx0])
+                                : (unsigned long long)p.n;
+      if (npts) atomicAdd(p.visited, npts * 128ull);
     }
     // --- per-pixel solve
     if (!inside) continue;

@@ -56,6 +56,18 @@ __device__ __forceinline__ float block_min(float v, float *red) {
   return r;
 }
 
+__device__ __forceinline__ float block_max(float v, float *red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) red[w] = v;
+  __syncthreads();
+  float r = red[0];
+  for (int i = 1; i < (int)(blockDim.x >> 5); ++i) r = fmaxf(r, red[i]);
+  return r;
+}
+
 __global__ __launch_bounds__(256) void k_prepass_min(KParams p) {
   __shared__ float red[8];
   __shared__ float cx[256], cy[256];
@@ -102,6 +114,9 @@ __global__ __launch_bounds__(256) void k_prepass_min(KParams p) {
   }
   const int stride = p.tiles_x * 16;
   const_cast<float *>(p.mstab)[(size_t)v * stride + u] = m;
+  // the tile's largest stabiliser bounds the reach of its weights above e^-gcut
+  const float mx = block_max(m, red);
+  if (t == 0) const_cast<float *>(p.tmax)[blockIdx.y * p.tiles_x + blockIdx.x] = mx;
 
   // frame of the tile: Gaussian-weighted centroid of the points around its centre
   const float Cx = mlsk::scaled_px(p, u0 + 8) - 0.5f * (mlsk::scaled_px(p, u0 + 8) - mlsk::scaled_px(p, u0 + 7));

@@ -91,11 +91,11 @@ TcLayout make_layout(int N, int Dc) {
   L.offPrm = L.offB + kStages * 2 * L.bpart;
   L.offData = L.offPrm + kPrmBytes;
   L.dstage = (kKT / 8) * (kXB + Dc * 8 + 4) * 4;
-  const int fixed = L.offData + 256 + 1024;
+  const int fixed = L.offData + 512 + 1024;
   int ds = (kSmemLimit - fixed) / L.dstage;
   L.dstages = ds > 4 ? 4 : ds;
-  L.offBar = L.offData + L.dstages * L.dstage;
-  L.total = L.offBar + 256 + 1024;
+  L.offBar = L.offData + L.dstages * L.dstage;   // barriers, TMEM slot, then the tile geometry (+256)
+  L.total = L.offBar + 512 + 1024;
   return L;
 }
 
@@ -258,10 +258,12 @@ __device__ __forceinline__ float pair_weight(float4 prm, float E, float dx, floa
   }
 }
 
-// The sequence of point tiles a CTA visits: all points, or for the Wendland
-// weight (truncated Gaussian) the cell rows of the uniform grid overlapping
-// the tile +- h (+- c h).  Tile starts are rounded down to 8 points; indices
-// outside [lo, hi) are masked.
+// The sequence of point tiles a CTA visits: all points, or the cell rows of
+// the uniform grid overlapping the CTA's pixels +- r: r = h for the Wendland
+// weight, c h for the truncated Gaussian, h sqrt(max_p m_p + gcut) for the
+// Gaussian (beyond it every weight rounds to zero in the 16-bit operand).
+// Tile starts are rounded down to 8 points; indices outside [lo, hi) are
+// masked.
 struct RangeIter {
   int cx0, cx1, cy0, cy1, cy;
   int lo, hi, base;
@@ -269,9 +271,43 @@ struct RangeIter {
   int n;
 };
 
-__device__ __forceinline__ void ranges_init(const KParams &p, int u0, int v0, int hgt, RangeIter &it) {
+// Per-CTA geometry, computed once in FP64 by one warp (GB300's FP64 rate is a
+// small fraction of FP32's: every thread evaluating these cost more than the
+// contraction on short point ranges): the tile-frame offsets of the 16 pixel
+// columns and rows, and the cell range the CTA visits.
+struct TileGeo {
+  float col[16], row[16];
+  int cr[4];                // cx0, cx1, cy0, cy1
+};
+
+__device__ __forceinline__ bool ranges_all(const KParams &p) {
+  return p.weight != MLS_W_WENDLAND && !(p.trunc > 0.0) && !(p.gcut > 0.f);
+}
+
+// One warp: lane k < 16 column k, lane 16 + k row k; lanes 0..3 the cell range.
+__device__ void tile_geometry(const KParams &p, int u0, int v0, int hgt, float cxs, float cys, int lane,
+                              TileGeo *g) {
+  if (lane < 16) g->col[lane] = (float)((p.x0 + (u0 + lane + 0.5) * p.sx - p.ctr_x) * p.inv_s - (double)cxs);
+  else g->row[lane - 16] = (float)((p.y0 + (v0 + lane - 16 + 0.5) * p.sy - p.ctr_y) * p.inv_s - (double)cys);
+  if (lane < 4 && !ranges_all(p)) {
+    // r = h (Wendland), c h (truncated Gaussian), h sqrt(max m + gcut) (Gaussian)
+    const float rs = p.weight == MLS_W_WENDLAND ? 1.f
+                     : p.trunc > 0.0            ? (float)p.trunc
+                                                : sqrtf(p.tmax[(v0 >> 4) * p.tiles_x + (u0 >> 4)] + p.gcut);
+    const double rad = p.h * (double)rs * (1.0 + 1e-5);
+    const bool ax = lane < 2, upper = lane & 1;
+    const double s = ax ? p.sx : p.sy, o = ax ? p.x0 : p.y0, g0 = ax ? p.gx0 : p.gy0;
+    const int n0 = ax ? u0 : v0, n1 = ax ? u0 + 15 : v0 + hgt - 1, ng = ax ? p.gx : p.gy;
+    const double a = o + (n0 + 0.5) * s, b = o + (n1 + 0.5) * s;
+    const double e = upper ? fmax(a, b) + rad : fmin(a, b) - rad;
+    const int c = (int)floor((e - g0) * (1.0 / p.cell));   // the binning's expression
+    g->cr[lane] = upper ? min(c, ng - 1) : max(c, 0);
+  }
+}
+
+__device__ __forceinline__ void ranges_init(const KParams &p, const TileGeo *g, RangeIter &it) {
   it.n = (int)p.n;
-  if (p.weight != MLS_W_WENDLAND && !(p.trunc > 0.0)) {
+  if (ranges_all(p)) {
     it.all = true;
     it.lo = 0;
     it.hi = it.n;
@@ -280,14 +316,10 @@ __device__ __forceinline__ void ranges_init(const KParams &p, int u0, int v0, in
     return;
   }
   it.all = false;
-  const double xlo = p.x0 + (u0 + 0.5) * p.sx, xhi = p.x0 + (u0 + 15.5) * p.sx;
-  const double ylo = p.y0 + (v0 + 0.5) * p.sy, yhi = p.y0 + (v0 + hgt - 0.5) * p.sy;
-  const double inv_cell = 1.0 / p.cell;
-  const double rad = p.weight == MLS_W_WENDLAND ? p.h : p.trunc * p.h * (1.0 + 1e-5);
-  it.cx0 = max((int)floor((fmin(xlo, xhi) - rad - p.gx0) * inv_cell), 0);
-  it.cx1 = min((int)floor((fmax(xlo, xhi) + rad - p.gx0) * inv_cell), p.gx - 1);
-  it.cy0 = max((int)floor((fmin(ylo, yhi) - rad - p.gy0) * inv_cell), 0);
-  it.cy1 = min((int)floor((fmax(ylo, yhi) + rad - p.gy0) * inv_cell), p.gy - 1);
+  it.cx0 = g->cr[0];
+  it.cx1 = g->cr[1];
+  it.cy0 = g->cr[2];
+  it.cy1 = g->cr[3];
   it.cy = it.cy0;
   it.lo = it.hi = it.base = 0;
   if (it.cx0 > it.cx1) it.cy = it.cy1 + 1;
@@ -338,6 +370,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mls_tc(KParams p, int d0, int D
   const uint32_t bar_dempty0 = smem_u32(&bars[9]);  // staged point tile consumed [ds]
   const uint32_t bar_exy0 = smem_u32(&bars[13]);    // Gaussian factor table [kt & 1] written
   uint32_t *tmem_slot = (uint32_t *)(smem + lay.offBar + 128);
+  TileGeo *geo = (TileGeo *)(smem + lay.offBar + 256);
   const int DST = lay.dstages;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   int u0, v0;
@@ -367,21 +400,21 @@ __global__ void __launch_bounds__(kThreads, 1) k_mls_tc(KParams p, int d0, int D
     mbar_init(bar_exy0 + 8, 4);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if (warp == 8) tmem_alloc(smem_u32(tmem_slot), 512);
-  tc_fence_before();
-  __syncthreads();
-  tc_fence_after();
-  const uint32_t tmem = *tmem_slot;
-
   // moment frame of the tile: the weighted centroid of the points near its
   // centre (from the prepass); the fit is solved in this frame
   const int tile = (v0 >> 4) * p.tiles_x + (u0 >> 4);
   const float cxs = p.tcen[2 * tile], cys = p.tcen[2 * tile + 1];
+  if (warp == 8) tmem_alloc(smem_u32(tmem_slot), 512);
+  if (warp == 9) tile_geometry(p, u0, v0, TH, cxs, cys, lane, geo);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
   const uint64_t limit = kWaitLimitNs;
   bool alive = true;
 
   RangeIter it;
-  ranges_init(p, u0, v0, TH, it);
+  ranges_init(p, geo, it);
 
   if (warp < 4 && WK == MLS_W_GAUSS) {
     // ------------------------------------------------ weight producers (Gaussian, separable)
@@ -421,9 +454,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mls_tc(KParams p, int d0, int D
     const int jp = t >> 1, half = t & 1;
     float off[16];
 #pragma unroll
-    for (int k = 0; k < 16; ++k)
-      off[k] = half ? (float)((p.y0 + (v0 + k + 0.5) * p.sy - p.ctr_y) * p.inv_s - (double)cys)
-                    : (float)((p.x0 + (u0 + k + 0.5) * p.sx - p.ctr_x) * p.inv_s - (double)cxs);
+    for (int k = 0; k < 16; ++k) off[k] = half ? geo->row[k] : geo->col[k];
     // this thread's pixels: column c, rows r0 (and r0 + 8), and their
     // corrections 2^(L_p - alpha_c - beta_r)
     const int cown = t & 15, r0 = t >> 4;
@@ -524,8 +555,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_mls_tc(KParams p, int d0, int D
     for (int a = 0; a < NACC; ++a) {
       const int q = a * 128 + t;
       const int u = u0 + (q & 15), v = v0 + (q >> 4);
-      dx[a] = (float)((p.x0 + (u + 0.5) * p.sx - p.ctr_x) * p.inv_s - (double)cxs);
-      dy[a] = (float)((p.y0 + (v + 0.5) * p.sy - p.ctr_y) * p.inv_s - (double)cys);
+      dx[a] = geo->col[q & 15];
+      dy[a] = geo->row[q >> 4];
       const size_t pi = (size_t)v * (p.tiles_x * 16) + u;
       if (WK == MLS_W_GAUSS)
         E[a] = kLog2e * (p.mstab[pi] - (dx[a] * dx[a] + dy[a] * dy[a]));
@@ -711,6 +742,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mls_tc(KParams p, int d0, int D
     // ------------------------------------------------ point-tile loader (TMA bulk copies)
     if (lane == 0) {
       int kt = 0;
+      unsigned long long visited = 0;
       for (; ranges_valid(it) && alive; ranges_next(p, it), ++kt) {
         const int ds = kt % DST;
         if (!mbar_wait(bar_dempty0 + 8 * ds, ((kt / DST) & 1) ^ 1, p.err, ERR_WAIT_EMPTY, limit)) {
@@ -718,6 +750,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_mls_tc(KParams p, int d0, int D
           break;
         }
         const int cnt = (int)((p.n_pad - it.base) < kKT ? (p.n_pad - it.base) : kKT);  // multiple of 8
+        // points of this tile inside the visited ranges
+        visited += (unsigned long long)max(0, min(it.hi, it.base + kKT) - max(it.lo, it.base));
         const uint32_t nbk = (uint32_t)cnt / 8;                                         // blocks
         const uint32_t dst = sbase + lay.offData + ds * lay.dstage;
         const uint32_t bar = bar_dfull0 + 8 * ds;
@@ -731,6 +765,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mls_tc(KParams p, int d0, int D
         bulk_g2s(dst, p.xyb + blk * kXB, nbk * kXB * 4, bar);
         bulk_g2s(dst + kPosFloats * 4, p.fb + ((size_t)pass * nblk + blk) * (Dc * 8 + 4), nbk * fbb, bar);
       }
+      if (p.visited && d0 == 0 && visited) atomicAdd(p.visited, visited * (unsigned long long)(16 * TH));
       // every issued copy has landed before the CTA may exit
       const int first = kt > DST ? kt - DST : 0;
       for (int k2 = first; k2 < kt; ++k2)
@@ -778,7 +813,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mls_tc(KParams p, int d0, int D
   // ------------------------------------------------ epilogue (warps 0-7)
   // Has any point tile been visited?  (Recompute from the iterator start.)
   RangeIter it2;
-  ranges_init(p, u0, v0, TH, it2);
+  ranges_init(p, geo, it2);
   const bool any_tile = ranges_valid(it2);
   if (warp < 8) {
     const bool acc_ok = __all_sync(0xffffffffu, mbar_wait(bar_acc, 0, p.err, ERR_WAIT_ACC, limit));
@@ -794,8 +829,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_mls_tc(KParams p, int d0, int D
     const int u = u0 + (q & 15), v = v0 + (q >> 4);
     const bool inside = (u < p.W) && (v < p.H);
     const size_t pi = (size_t)v * (p.tiles_x * 16) + u;
-    const float dxp = (float)((p.x0 + (u + 0.5) * p.sx - p.ctr_x) * p.inv_s - (double)cxs);
-    const float dyp = (float)((p.y0 + (v + 0.5) * p.sy - p.ctr_y) * p.inv_s - (double)cys);
+    const float dxp = geo->col[q & 15];
+    const float dyp = geo->row[q >> 4];
     const uint32_t tbase = tmem + a * 256 + ((uint32_t)(32 * (warp & 3)) << 16);
     const bool read = acc_ok && any_tile;   // warp-uniform
     float St[16];

@@ -11,16 +11,20 @@ import numpy as np
 TOL = {"fp64": 1e-10, "fp32": 1e-3, "fp16": 1e-3, "bf16": 1e-3}
 
 
-def gpu_render(wl, precision, device_inputs=True, levels=True, **kw):
+def gpu_render(wl, precision, device_inputs=True, levels=True, operand_cut=True, **kw):
+    import ctypes
+
     import torch
 
-    from paper_1408_0677_gb300 import Renderer
+    from paper_1408_0677_gb300 import Renderer, _abi
     if device_inputs:
         xy, F = torch.from_numpy(wl.xy).cuda(), torch.from_numpy(wl.F).cuda()
     else:
         xy, F = wl.xy, wl.F
     r = Renderer(xy, F, degree=wl.degree, weight=wl.weight, h=wl.h, precision=precision, alpha=wl.alpha,
                  support=wl.trunc, **kw)
+    if not operand_cut:
+        assert _abi.load().mls_debug_operand_cut(ctypes.c_void_p(r.handle), 0) == _abi.MLS_OK
     out = r.render(wl.W, wl.H, view=wl.view, levels=wl.levels if levels else None)
     stats = r.sync()
     res = {k: (v.cpu().numpy() if v is not None else None) for k, v in out.items()}

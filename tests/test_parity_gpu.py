@@ -226,3 +226,25 @@ def test_inverse_distance_table1_shape(precision, degree):
     wl.view = (0.2, 0.3, 0.3, 0.4)
     res = gpu_render(wl, precision)
     compare(wl, res, _ref(wl), precision)
+
+
+@pytest.mark.parametrize("precision", ["fp16", "bf16", "fp32"])
+def test_operand_cut_changes_nothing_beyond_fp32_rounding(precision):
+    """Reduced-precision Gaussian renders visit, per tile, only the points whose
+    weight is at least e^-28 of some pixel's largest (an FP16 weight below it
+    is exactly zero; in BF16 / FP32 it is below the sums' resolution).  The
+    same render visiting every point agrees to FP32 rounding, and the cut
+    visits fewer pairs."""
+    wl = inputs.fourier_mix(31, 10000, 8, 320, 240, 2, G, 0.02)   # tiles 2.5 h wide: the tensor path
+    a = gpu_render(wl, precision)
+    b = gpu_render(wl, precision, operand_cut=False)
+    assert a["stats"].pairs < b["stats"].pairs
+    S = wl.F.max(0) - wl.F.min(0)
+    fa = a["field"].astype(np.float64).reshape(wl.D, -1)
+    fb = b["field"].astype(np.float64).reshape(wl.D, -1)
+    assert np.array_equal(np.isnan(fa), np.isnan(fb))
+    diff = np.nanmax(np.abs(fa - fb) / S[:, None])
+    assert diff <= 2e-5, diff
+    same = np.mean(a["status"] == b["status"])
+    assert same > 0.998, same
+    print(f"{precision}: visited {a['stats'].pairs / b['stats'].pairs:.3f} of the pairs, max diff {diff:.2g}")
