@@ -264,13 +264,6 @@ __device__ __forceinline__ float pair_weight(float4 prm, float E, float dx, floa
 // Gaussian (beyond it every weight rounds to zero in the 16-bit operand).
 // Tile starts are rounded down to 8 points; indices outside [lo, hi) are
 // masked.
-struct RangeIter {
-  int cx0, cx1, cy0, cy1, cy;
-  int lo, hi, base;
-  bool all;
-  int n;
-};
-
 // Per-CTA geometry, computed once in FP64 by one warp (GB300's FP64 rate is a
 // small fraction of FP32's: every thread evaluating these cost more than the
 // contraction on short point ranges): the tile-frame offsets of the 16 pixel
@@ -305,51 +298,84 @@ __device__ void tile_geometry(const KParams &p, int u0, int v0, int hgt, float c
   }
 }
 
-__device__ __forceinline__ void ranges_init(const KParams &p, const TileGeo *g, RangeIter &it) {
-  it.n = (int)p.n;
-  if (ranges_all(p)) {
-    it.all = true;
-    it.lo = 0;
-    it.hi = it.n;
-    it.base = 0;
-    it.cy = it.cy1 = 0;
+// The 8-point blocks of the visited ranges, packed densely into stages of 8
+// blocks (64 points): slot after slot takes the next block of the current
+// cell row and moves on to the next non-empty row when the row ends (a row
+// of ~50 points would otherwise start a half-empty stage of its own).  Every
+// role runs the same iterator, so all agree on each stage's contents.
+struct Slot {
+  int gb;       // 8-point block index (points 8 gb .. 8 gb + 7), < 0: empty slot
+  int lo, hi;   // point range of its row: points outside are masked
+};
+
+struct PackIter {
+  int cx0, cx1, cy, cy1;
+  int lo, hi;   // point range of the current row
+  int gb;       // its next block
+  bool all;
+};
+
+__device__ __forceinline__ void pack_row(const KParams &p, PackIter &it) {
+  while (it.cy <= it.cy1) {
+    it.lo = p.cell_start[it.cy * p.gx + it.cx0];
+    it.hi = p.cell_start[it.cy * p.gx + it.cx1 + 1];
+    if (it.hi > it.lo) break;
+    ++it.cy;
+  }
+  it.gb = it.lo >> 3;
+}
+
+__device__ __forceinline__ void pack_init(const KParams &p, const TileGeo *g, PackIter &it) {
+  it.cx0 = it.cx1 = it.cy = it.cy1 = 0;
+  it.lo = it.hi = it.gb = 0;
+  it.all = ranges_all(p);
+  if (it.all) {
+    it.hi = (int)p.n;
     return;
   }
-  it.all = false;
   it.cx0 = g->cr[0];
   it.cx1 = g->cr[1];
-  it.cy0 = g->cr[2];
+  it.cy = g->cr[2];
   it.cy1 = g->cr[3];
-  it.cy = it.cy0;
-  it.lo = it.hi = it.base = 0;
-  if (it.cx0 > it.cx1) it.cy = it.cy1 + 1;
-  // position on the first non-empty row
-  while (it.cy <= it.cy1) {
-    it.lo = p.cell_start[it.cy * p.gx + it.cx0];
-    it.hi = p.cell_start[it.cy * p.gx + it.cx1 + 1];
-    if (it.hi > it.lo) break;
-    ++it.cy;
+  if (it.cx0 > it.cx1) {
+    it.cy = it.cy1 + 1;
+    return;
   }
-  it.base = it.lo & ~7;
+  pack_row(p, it);
 }
 
-__device__ __forceinline__ bool ranges_valid(const RangeIter &it) {
-  return it.all ? (it.base < it.hi) : (it.cy <= it.cy1);
+__device__ __forceinline__ bool pack_valid(const PackIter &it) {
+  return it.all ? (it.gb * 8 < it.hi) : (it.cy <= it.cy1);
 }
 
-__device__ __forceinline__ void ranges_next(const KParams &p, RangeIter &it) {
-  it.base += kKT;
-  if (it.base < it.hi) return;
-  if (it.all) return;
-  ++it.cy;
-  while (it.cy <= it.cy1) {
-    it.lo = p.cell_start[it.cy * p.gx + it.cx0];
-    it.hi = p.cell_start[it.cy * p.gx + it.cx1 + 1];
-    if (it.hi > it.lo) break;
+__device__ __forceinline__ Slot pack_take(const KParams &p, PackIter &it) {
+  Slot s{-1, 0, 0};
+  if (!pack_valid(it)) return s;
+  s.gb = it.gb;
+  s.lo = it.lo;
+  s.hi = it.hi;
+  ++it.gb;
+  if (!it.all && it.gb * 8 >= it.hi) {
     ++it.cy;
+    pack_row(p, it);
   }
-  it.base = it.lo & ~7;
+  return s;
 }
+
+// One stage: the slots `want0` and `want1` of it (the rest are skipped).
+__device__ __forceinline__ void pack_stage(const KParams &p, PackIter &it, int want0, Slot &s0, int want1,
+                                           Slot &s1) {
+  s0 = Slot{-1, 0, 0};
+  s1 = Slot{-1, 0, 0};
+#pragma unroll 1
+  for (int q = 0; q < kKT / 8; ++q) {
+    const Slot sl = pack_take(p, it);
+    if (q == want0) s0 = sl;
+    if (q == want1) s1 = sl;
+  }
+}
+
+__device__ __forceinline__ bool slot_has(const Slot &s, int i) { return s.gb >= 0 && i >= s.lo && i < s.hi; }
 
 template <int DEG, int WK, bool FP16, int NACC, bool WSPLIT>
 __global__ void __launch_bounds__(kThreads, 1) k_mls_tc(KParams p, int d0, int Dc, int N, uint32_t idesc,
@@ -413,8 +439,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_mls_tc(KParams p, int d0, int D
   const uint64_t limit = kWaitLimitNs;
   bool alive = true;
 
-  RangeIter it;
-  ranges_init(p, geo, it);
+  PackIter it;
+  pack_init(p, geo, it);
 
   if (warp < 4 && WK == MLS_W_GAUSS) {
     // ------------------------------------------------ weight producers (Gaussian, separable)
@@ -468,9 +494,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_mls_tc(KParams p, int d0, int D
       gcor[a] = ex2_approx(fminf(res, kResMax)) * weight_scale<FP16>();
     }
     int kt = 0;
-    for (; ranges_valid(it) && alive; ranges_next(p, it), ++kt) {
+    for (; pack_valid(it) && alive; ++kt) {
       const int s = kt & 1;
       const int ds = kt % DST;
+      Slot mine, unused;
+      pack_stage(p, it, jp >> 3, mine, -1, unused);
       if (!mbar_wait(bar_dfull0 + 8 * ds, (kt / DST) & 1, p.err, ERR_WAIT_FULL, limit)) {
         alive = false;
         break;
@@ -478,9 +506,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_mls_tc(KParams p, int d0, int D
       const float *dxs = (const float *)(smem + lay.offData + ds * lay.dstage);
       float *tab = exy + s * kExyFloats;
       {
-        const int i = it.base + jp;
         float pos = 0.f;
-        bool ok = (i >= it.lo) && (i < it.hi);
+        bool ok = slot_has(mine, mine.gb * 8 + (jp & 7));
         if (ok) {
           const float x = dxs[(jp >> 3) * kXB + (jp & 7)] - cxs;
           const float y = dxs[(jp >> 3) * kXB + 8 + (jp & 7)] - cys;
@@ -565,9 +592,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_mls_tc(KParams p, int d0, int D
     }
     float4 *prm = (float4 *)(smem + lay.offPrm) + warp * kKT;
     int kt = 0;
-    for (; ranges_valid(it) && alive; ranges_next(p, it), ++kt) {
+    for (; pack_valid(it) && alive; ++kt) {
       const int s = kt & 1;
       const int ds = kt % DST;
+      Slot sl2[2];
+      pack_stage(p, it, lane >> 3, sl2[0], (lane >> 3) + 4, sl2[1]);
       if (!mbar_wait(bar_dfull0 + 8 * ds, (kt / DST) & 1, p.err, ERR_WAIT_FULL, limit)) {
         alive = false;
         break;
@@ -577,9 +606,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_mls_tc(KParams p, int d0, int D
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
         const int j = lane + 32 * h;
-        const int i = it.base + j;
         float x = 0.f, y = 0.f;
-        bool ok = (i >= it.lo) && (i < it.hi);
+        bool ok = slot_has(sl2[h], sl2[h].gb * 8 + (j & 7));
         if (ok) {
           // blocked tile: 8-point blocks of (x[8], y[8])
           x = dxs[(j >> 3) * kXB + (j & 7)] - cxs;
@@ -636,17 +664,19 @@ __global__ void __launch_bounds__(kThreads, 1) k_mls_tc(KParams p, int d0, int D
     const int mex = mono_ex(rr < 15 ? rr : 0), mey = mono_ey(rr < 15 ? rr : 0);
     const float mrow = (rr < NM) ? 1.f : 0.f;
     int kt = 0;
-    for (; ranges_valid(it) && alive; ranges_next(p, it), ++kt) {
+    for (; pack_valid(it) && alive; ++kt) {
       const int s = kt & 1;
       const int ds = kt % DST;
-      const int i0 = it.base + 8 * g;
+      Slot mine, unused;
+      pack_stage(p, it, g, mine, -1, unused);
+      const int i0 = mine.gb * 8;
       float xv[8], yv[8], msk[8];
       if (!mbar_wait(bar_dfull0 + 8 * ds, (kt / DST) & 1, p.err, ERR_WAIT_FULL, limit)) {
         alive = false;
         break;
       }
       const float *dsm = (const float *)(smem + lay.offData + ds * lay.dstage);
-      if (i0 < p.n_pad) {
+      if (mine.gb >= 0) {
         const float4 xa = *(const float4 *)(dsm + kXB * g), xb = *(const float4 *)(dsm + kXB * g + 4);
         const float4 ya = *(const float4 *)(dsm + kXB * g + 8), yb = *(const float4 *)(dsm + kXB * g + 12);
         xv[0] = xa.x; xv[1] = xa.y; xv[2] = xa.z; xv[3] = xa.w; xv[4] = xb.x; xv[5] = xb.y; xv[6] = xb.z; xv[7] = xb.w;
@@ -660,7 +690,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mls_tc(KParams p, int d0, int D
         const int i = i0 + j;
         xv[j] -= cxs;
         yv[j] -= cys;
-        const bool ok = (i >= it.lo) && (i < it.hi) && fmaxf(fabsf(xv[j]), fabsf(yv[j])) <= kRMax;
+        const bool ok = slot_has(mine, i) && fmaxf(fabsf(xv[j]), fabsf(yv[j])) <= kRMax;
         msk[j] = ok ? 1.f : 0.f;
         if (!ok) { xv[j] = 0.f; yv[j] = 0.f; }
       }
@@ -700,7 +730,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mls_tc(KParams p, int d0, int D
       }
       for (int d = rr; d < Dc; d += 16) {
         float fv[8];
-        if (i0 < p.n_pad) {
+        if (mine.gb >= 0) {
           const float *fr = dsm + kPosFloats + g * (Dc * 8 + 4) + d * 8;
           const float4 fa = *(const float4 *)fr, fb = *(const float4 *)(fr + 4);
           fv[0] = fa.x; fv[1] = fa.y; fv[2] = fa.z; fv[3] = fa.w; fv[4] = fb.x; fv[5] = fb.y; fv[6] = fb.z; fv[7] = fb.w;
@@ -743,27 +773,44 @@ __global__ void __launch_bounds__(kThreads, 1) k_mls_tc(KParams p, int d0, int D
     if (lane == 0) {
       int kt = 0;
       unsigned long long visited = 0;
-      for (; ranges_valid(it) && alive; ranges_next(p, it), ++kt) {
+      for (; pack_valid(it) && alive; ++kt) {
         const int ds = kt % DST;
+        Slot sl[kKT / 8];
+#pragma unroll 1
+        for (int q = 0; q < kKT / 8; ++q) sl[q] = pack_take(p, it);
         if (!mbar_wait(bar_dempty0 + 8 * ds, ((kt / DST) & 1) ^ 1, p.err, ERR_WAIT_EMPTY, limit)) {
           alive = false;
           break;
         }
-        const int cnt = (int)((p.n_pad - it.base) < kKT ? (p.n_pad - it.base) : kKT);  // multiple of 8
-        // points of this tile inside the visited ranges
-        visited += (unsigned long long)max(0, min(it.hi, it.base + kKT) - max(it.lo, it.base));
-        const uint32_t nbk = (uint32_t)cnt / 8;                                         // blocks
         const uint32_t dst = sbase + lay.offData + ds * lay.dstage;
         const uint32_t bar = bar_dfull0 + 8 * ds;
-        // point-blocked layouts: one copy for the positions, one for the
-        // values of this pass (blocks base/8 .. base/8 + cnt/8); block sizes
-        // 80 and 32 Dc + 16 bytes keep both copies 16-byte aligned
-        const int64_t blk = it.base >> 3;
+        // point-blocked layouts: slot q of the stage holds block sl[q].gb
+        // (positions 80 bytes, values 32 Dc + 16 bytes: every copy stays
+        // 16-byte aligned); the filled slots are a prefix of the stage
         const int64_t nblk = p.n_pad >> 3;
         const uint32_t fbb = (uint32_t)(Dc * 8 + 4) * 4;
-        mbar_expect_tx(bar, nbk * (kXB * 4 + fbb));
-        bulk_g2s(dst, p.xyb + blk * kXB, nbk * kXB * 4, bar);
-        bulk_g2s(dst + kPosFloats * 4, p.fb + ((size_t)pass * nblk + blk) * (Dc * 8 + 4), nbk * fbb, bar);
+        uint32_t nvalid = 0;
+#pragma unroll 1
+        for (int q = 0; q < kKT / 8; ++q) {
+          if (sl[q].gb < 0) break;
+          ++nvalid;
+          // points of this tile inside the visited ranges
+          visited += (unsigned long long)max(0, min(sl[q].hi, sl[q].gb * 8 + 8) - max(sl[q].lo, sl[q].gb * 8));
+        }
+        mbar_expect_tx(bar, nvalid * (kXB * 4 + fbb));
+        // one copy per run of consecutive blocks
+        int q = 0;
+#pragma unroll 1
+        while (q < (int)nvalid) {
+          int r = q + 1;
+          while (r < (int)nvalid && sl[r].gb == sl[r - 1].gb + 1) ++r;
+          const uint32_t nb = (uint32_t)(r - q);
+          const int64_t blk = sl[q].gb;
+          bulk_g2s(dst + q * kXB * 4, p.xyb + blk * kXB, nb * kXB * 4, bar);
+          bulk_g2s(dst + kPosFloats * 4 + q * fbb, p.fb + ((size_t)pass * nblk + blk) * (Dc * 8 + 4), nb * fbb,
+                   bar);
+          q = r;
+        }
       }
       if (p.visited && d0 == 0 && visited) atomicAdd(p.visited, visited * (unsigned long long)(16 * TH));
       // every issued copy has landed before the CTA may exit
@@ -776,8 +823,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_mls_tc(KParams p, int d0, int D
     // ------------------------------------------------ MMA issuer
     if (lane == 0) {
       int kt = 0;
-      for (; ranges_valid(it) && alive; ranges_next(p, it), ++kt) {
+      for (; pack_valid(it) && alive; ++kt) {
         const int s = kt & 1;
+        Slot ua, ub;
+        pack_stage(p, it, -1, ua, -1, ub);
         if (!mbar_wait(bar_full0 + 8 * s, (kt >> 1) & 1, p.err, ERR_WAIT_FULL, limit)) {
           alive = false;
           break;
@@ -812,9 +861,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_mls_tc(KParams p, int d0, int D
 
   // ------------------------------------------------ epilogue (warps 0-7)
   // Has any point tile been visited?  (Recompute from the iterator start.)
-  RangeIter it2;
-  ranges_init(p, geo, it2);
-  const bool any_tile = ranges_valid(it2);
+  PackIter it2;
+  pack_init(p, geo, it2);
+  const bool any_tile = pack_valid(it2);
   if (warp < 8) {
     const bool acc_ok = __all_sync(0xffffffffu, mbar_wait(bar_acc, 0, p.err, ERR_WAIT_ACC, limit));
     tc_fence_after();
