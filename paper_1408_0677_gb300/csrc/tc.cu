@@ -193,6 +193,35 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// 32 lanes x 48 columns (three 16-column loads at taddr, +16, +32), waited
+// in the same statement so that no use of the registers can precede the wait.
+__device__ __forceinline__ void tmem_ld48(uint32_t taddr, float (&v)[48]) {
+  uint32_t r[48];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%48];\n\t"
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%49];\n\t"
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%32,%33,%34,%35,%36,%37,%38,%39,%40,%41,%42,%43,%44,%45,%46,%47}, [%50];\n\t"
+      "tcgen05.wait::ld.sync.aligned;"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31]), "=r"(r[32]), "=r"(r[33]), "=r"(r[34]), "=r"(r[35]), "=r"(r[36]), "=r"(r[37]), "=r"(r[38]), "=r"(r[39]), "=r"(r[40]), "=r"(r[41]), "=r"(r[42]), "=r"(r[43]), "=r"(r[44]), "=r"(r[45]), "=r"(r[46]), "=r"(r[47])
+      : "r"(taddr), "r"(taddr + 16), "r"(taddr + 32)
+      : "memory");
+#pragma unroll
+  for (int i = 0; i < 48; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Iso-band label #{j : t_j <= f} over ascending levels (rounded up to float,
+// so the float comparison equals the double one), by binary search; 255 for NaN.
+__device__ __forceinline__ uint8_t band_search(float f, const float *lev, int L) {
+  if (f != f) return 255;
+  int lo = 0, hi = L;
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (lev[mid] <= f) lo = mid + 1;
+    else hi = mid;
+  }
+  return (uint8_t)lo;
+}
+
 // Byte offset of the 16-byte chunk c of row m in a 128B-swizzled K-major tile.
 __device__ __forceinline__ uint32_t sw128_off(int m, int c) {
   return (uint32_t)((m >> 3) * 1024 + (m & 7) * 128 + ((c ^ (m & 7)) << 4));
@@ -867,6 +896,22 @@ __global__ void __launch_bounds__(kThreads, 1) k_mls_tc(KParams p, int d0, int D
   if (warp < 8) {
     const bool acc_ok = __all_sync(0xffffffffu, mbar_wait(bar_acc, 0, p.err, ERR_WAIT_ACC, limit));
     tc_fence_after();
+    // every MMA has completed: the operand tiles' shared memory now holds this
+    // pass's levels (rounded up to float) and value scales, read per dimension
+    // below (levels [Dc][L], then scl[Dc], cen[Dc])
+    float *s_lev = (float *)(smem + kOffA);
+    float *s_scl = s_lev + Dc * p.L, *s_cen = s_scl + Dc;
+    for (int e = threadIdx.x; e < Dc * (p.L + 2); e += 256) {
+      if (e < Dc * p.L) {
+        const int d = e / p.L;
+        s_lev[e] = (d0 + d < p.D) ? p.lev32[(size_t)(d0 + d) * p.L + (e - d * p.L)] : 0.f;
+      } else {
+        const int d = e - Dc * p.L, dd = d % Dc, g = d0 + dd;
+        const float val = (g < p.D) ? (d < Dc ? p.fscl32[g] : p.fcen32[g]) : 0.f;
+        (d < Dc ? s_scl : s_cen)[dd] = val;
+      }
+    }
+    asm volatile("bar.sync 1, 256;" ::: "memory");   // the eight epilogue warps
     const int wg = warp >> 2;
     // two accumulators: one warpgroup each; one accumulator: the warpgroups
     // share it and take alternate groups of value columns
@@ -947,12 +992,19 @@ __global__ void __launch_bounds__(kThreads, 1) k_mls_tc(KParams p, int d0, int D
     for (int gbase = gfirst * GD; gbase < Dc; gbase += gstep * GD) {
       float rv[GC];
       if (read) {
+        if (GC == 48) {
+          float tmp[48];
+          tmem_ld48(tbase + 16 + gbase * K, tmp);
 #pragma unroll
-        for (int c = 0; c < GC / 16; ++c) {
-          float tmp[16];
-          tmem_ld16(tbase + 16 + gbase * K + 16 * c, tmp);
+          for (int j = 0; j < GC; ++j) rv[j] = tmp[j];
+        } else {
 #pragma unroll
-          for (int j = 0; j < 16; ++j) rv[16 * c + j] = tmp[j];
+          for (int c = 0; c < GC / 16; ++c) {
+            float tmp[16];
+            tmem_ld16(tbase + 16 + gbase * K + 16 * c, tmp);
+#pragma unroll
+            for (int j = 0; j < 16; ++j) rv[16 * c + j] = tmp[j];
+          }
         }
       }
       if (done && inside && read) {
@@ -964,9 +1016,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_mls_tc(KParams p, int d0, int D
 #pragma unroll
             for (int b = 0; b < K; ++b) acc = fmaf(z[b], rv[dd * K + b], acc);
             const int dg = d0 + d;
-            const float f = fmaf(acc, p.fscl32[dg], p.fcen32[dg]);
+            const float f = fmaf(acc, s_scl[d], s_cen[d]);
             field[(size_t)dg * plane + pix] = f;
-            if (p.bands) p.bands[(size_t)dg * plane + pix] = band_of(f, p.lev32 + (size_t)dg * p.L, p.L);
+            if (p.bands) p.bands[(size_t)dg * plane + pix] = band_search(f, s_lev + d * p.L, p.L);
           }
         }
       }
