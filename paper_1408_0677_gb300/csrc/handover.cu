@@ -382,7 +382,7 @@ __device__ int pixel_policy(const double (&Sd)[15], long long count, double rcon
 
 // ---------------------------------------------------------------------------
 
-// Per-warp state of a chunk of up to 32 pixels between the three phases.
+// Per-block state of a chunk of up to 32 pixels between the three phases.
 struct ChunkSlot {
   double S[15];    // pixel-frame moments
   double z[6];     // solution in the centroid frame
@@ -398,20 +398,21 @@ __global__ __launch_bounds__(kWarps * 32, 4) void k_handover(KParams p, const in
   constexpr int NM = n_moments(DEG);
   __shared__ int s_ri[kWarps][kRing];
   __shared__ float4 s_rx[kWarps][kRing];
-  __shared__ ChunkSlot s_chunk[kWarps][32];
+  __shared__ ChunkSlot s_chunk[32];
   __shared__ float2 s_tab[64];
   if (WK == MLS_W_GAUSS) df_exp_table_init(s_tab);
   __syncthreads();
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   int *ri = s_ri[wib];
   float4 *rx = s_rx[wib];
-  ChunkSlot *slots = s_chunk[wib];
-  const int64_t warp0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  ChunkSlot *slots = s_chunk;
   const int64_t npix = (int64_t)*list_count < cap ? (int64_t)*list_count : cap;
-  // pixels per chunk: up to 32 (one per lane in the policy phase), fewer
-  // when there are too few pixels to give every warp a full chunk
-  const int64_t per = (npix + nwarps - 1) / nwarps;
+  // pixels per block chunk: up to 32 (one per lane of the policy warp), fewer
+  // when there are too few pixels to give every block a full chunk.  The
+  // block's warps share the moment and value phases (warp per pixel); one
+  // warp runs the FP64 policy of all the chunk's pixels, one per lane (GB300's
+  // FP64 pipe takes a warp instruction's full cost however few lanes are active)
+  const int64_t per = (npix + gridDim.x - 1) / gridDim.x;
   const int csz = per >= 32 ? 32 : (per < 1 ? 1 : (int)per);
   const int64_t nchunks = (npix + csz - 1) / csz;
   const size_t plane = (size_t)p.W * p.H;
@@ -449,12 +450,12 @@ __global__ __launch_bounds__(kWarps * 32, 4) void k_handover(KParams p, const in
     pyl = (float)(pys64 - (double)pyh);
   };
 
-  for (int64_t ch = warp0; ch < nchunks; ch += nwarps) {
+  for (int64_t ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
     const int64_t q0 = ch * csz;
     const int nq = (int)((npix - q0) < csz ? (npix - q0) : csz);
 
     // ---- phase 1 (warp per pixel): double-float pixel-frame moments
-    for (int j = 0; j < nq; ++j) {
+    for (int j = wib; j < nq; j += kWarps) {
       const int id = list[q0 + j];
       Ranges R;
       float mhat, pxh, pxl, pyh, pyl;
@@ -509,8 +510,9 @@ __global__ __launch_bounds__(kWarps * 32, 4) void k_handover(KParams p, const in
       __syncwarp();
     }
 
+    __syncthreads();
     // ---- phase 2 (lane per pixel): degree policy and centroid-frame solve in FP64
-    if (lane < nq) {
+    if (wib == 0 && lane < nq) {
       ChunkSlot &sl = slots[lane];
       if (!(sl.flags & 1)) {
         double Sd[15], z[6];
@@ -526,10 +528,10 @@ __global__ __launch_bounds__(kWarps * 32, 4) void k_handover(KParams p, const in
         sl.flags = (bad ? 1 : 0) | ((used + 1) << 8);
       }
     }
-    __syncwarp();
+    __syncthreads();
 
     // ---- phase 3 (warp per pixel): value = sum_i phi_i f_i, phi_i = w_i z . b_c(x_i)
-    for (int j = 0; j < nq; ++j) {
+    for (int j = wib; j < nq; j += kWarps) {
       const int id = list[q0 + j];
       const int flags = slots[j].flags;
       if (flags & 1) {
@@ -607,7 +609,7 @@ __global__ __launch_bounds__(kWarps * 32, 4) void k_handover(KParams p, const in
       if (lane == 0 && p.status)
         p.status[id] = (uint8_t)(used | MLS_ST_RECOMPUTED | (used < DEG ? MLS_ST_DEGRADED : 0));
     }
-    __syncwarp();
+    __syncthreads();   // the slots are refilled by the next chunk
   }
 }
 
