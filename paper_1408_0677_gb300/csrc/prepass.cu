@@ -154,6 +154,138 @@ __device__ __forceinline__ void cell_range(double lo, double hi, double r, doubl
   c1 = min(c1, g - 1);
 }
 
+// Tile geometry computed once per block (GB300's FP64 rate is a small
+// fraction of FP32's: per-thread FP64 set-up cost more than the search):
+// scaled pixel-centre coordinates of the 16 columns and rows, and the cell
+// window covering the tile's pixel centres +- r (raw units).
+struct PreGeo {
+  float col[16], row[16];
+  int win[4];   // c0, c1, d0, d1
+};
+
+__device__ __forceinline__ void pre_geometry(const KParams &p, int u0, int v0, PreGeo *g) {
+  const int t = threadIdx.x;
+  if (t < 16) g->col[t] = mlsk::scaled_px(p, u0 + t);
+  else if (t < 32) g->row[t - 16] = mlsk::scaled_py(p, v0 + t - 16);
+}
+
+// Thread 0 sets the window for radius r, or, with bound >= 0, for radius
+// max(h sqrt(bound) (1 + 1e-5), rmin); the caller synchronises.
+__device__ __forceinline__ void pre_window(const KParams &p, int u0, int v0, double r, PreGeo *g,
+                                           float bound = -1.f, double rmin = 0.0) {
+  if (threadIdx.x == 0) {
+    if (bound >= 0.f) r = fmax(sqrt((double)bound) * p.h * (1.0 + 1e-5) + 1e-12, rmin);
+    const double inv_cell = 1.0 / p.cell;
+    const double xa = p.x0 + (u0 + 0.5) * p.sx, xb = p.x0 + (u0 + 15.5) * p.sx;
+    const double ya = p.y0 + (v0 + 0.5) * p.sy, yb = p.y0 + (v0 + 15.5) * p.sy;
+    cell_range(fmin(xa, xb), fmax(xa, xb), r, p.gx0, inv_cell, p.gx, g->win[0], g->win[1]);
+    cell_range(fmin(ya, yb), fmax(ya, yb), r, p.gy0, inv_cell, p.gy, g->win[2], g->win[3]);
+  }
+}
+
+// Gaussian weight (points binned on the uniform grid): the same stabiliser
+// and tile frame from the cells near the tile instead of all n points.  A
+// window of cells around the tile is grown until it holds a point; the bound
+// B = min over its points of the squared distance to the farthest tile corner
+// is at least every pixel's nearest squared distance, so every pixel's
+// nearest point lies in the cells within sqrt(B) of the tile, which are then
+// scanned exactly.  The frame (it only conditions the fit) is the Gaussian-
+// weighted centroid, around the tile centre, of the points in the cells within
+// 4 h of the tile (weights below e^-16 of the largest are left out).
+__global__ __launch_bounds__(256) void k_prepass_min_cells(KParams p) {
+  __shared__ float red[8];
+  __shared__ float cx[256], cy[256];
+  __shared__ PreGeo G;
+  const int t = threadIdx.x;
+  const int u0 = blockIdx.x * 16, v0 = blockIdx.y * 16;
+  pre_geometry(p, u0, v0, &G);
+  __syncthreads();
+  const float px = G.col[t & 15], py = G.row[t >> 4];
+  const float X0 = G.col[0], X1 = G.col[15], Y0 = G.row[0], Y1 = G.row[15];
+  // 1) bound from the first non-empty window of cells around the tile
+  float b = FLT_MAX;
+  double r = p.cell;
+  for (int round = 0; round < 40; ++round) {
+    __syncthreads();
+    pre_window(p, u0, v0, r, &G);
+    __syncthreads();
+    const int c0 = G.win[0], c1 = G.win[1], d0 = G.win[2], d1 = G.win[3];
+    for (int row = d0; row <= d1 && c0 <= c1; ++row) {
+      const int a = p.cell_start[row * p.gx + c0], e = p.cell_start[row * p.gx + c1 + 1];
+      for (int i = a + t; i < e; i += 256) {
+        const float x = p.xs[i], y = p.ys[i];
+        const float fx = fmaxf(fabsf(x - X0), fabsf(x - X1));
+        const float fy = fmaxf(fabsf(y - Y0), fabsf(y - Y1));
+        b = fminf(b, fx * fx + fy * fy);
+      }
+    }
+    if (block_min(b, red) < FLT_MAX) break;   // uniform: every thread sees the same minimum
+    r *= 2.0;
+  }
+  const float bound = block_min(b, red) * 1.0001f + 1e-30f;
+  // 2) exact nearest squared distance of each pixel over the cells within sqrt(bound)
+  __syncthreads();
+  pre_window(p, u0, v0, 0.0, &G, bound);
+  __syncthreads();
+  int c0 = G.win[0], c1 = G.win[1], d0 = G.win[2], d1 = G.win[3];
+  float m = FLT_MAX;
+  for (int row = d0; row <= d1 && c0 <= c1; ++row) {
+    const int a = p.cell_start[row * p.gx + c0], e = p.cell_start[row * p.gx + c1 + 1];
+    for (int base = a; base < e; base += 256) {
+      __syncthreads();
+      if (base + t < e) {
+        cx[t] = p.xs[base + t];
+        cy[t] = p.ys[base + t];
+      }
+      __syncthreads();
+      const int c = min(256, e - base);
+      for (int k = 0; k < c; ++k) {
+        const float dx = cx[k] - px, dy = cy[k] - py;
+        m = fminf(m, dx * dx + dy * dy);
+      }
+    }
+  }
+  const int stride = p.tiles_x * 16;
+  const_cast<float *>(p.mstab)[(size_t)(v0 + (t >> 4)) * stride + u0 + (t & 15)] = m;
+  const float mx = block_max(m, red);
+  if (t == 0) const_cast<float *>(p.tmax)[blockIdx.y * p.tiles_x + blockIdx.x] = mx;
+  // 3) frame: Gaussian-weighted centroid of the points within 4 h of the tile
+  const float Cx = G.col[8] - 0.5f * (G.col[8] - G.col[7]);
+  const float Cy = G.row[8] - 0.5f * (G.row[8] - G.row[7]);
+  __syncthreads();
+  pre_window(p, u0, v0, 0.0, &G, bound, 4.0 * p.h);
+  __syncthreads();
+  c0 = G.win[0]; c1 = G.win[1]; d0 = G.win[2]; d1 = G.win[3];
+  float mc = FLT_MAX;
+  for (int row = d0; row <= d1 && c0 <= c1; ++row) {
+    const int a = p.cell_start[row * p.gx + c0], e = p.cell_start[row * p.gx + c1 + 1];
+    for (int i = a + t; i < e; i += 256) {
+      const float dx = p.xs[i] - Cx, dy = p.ys[i] - Cy;
+      mc = fminf(mc, dx * dx + dy * dy);
+    }
+  }
+  mc = block_min(mc, red);
+  float sw = 0.f, swx = 0.f, swy = 0.f;
+  for (int row = d0; row <= d1 && c0 <= c1; ++row) {
+    const int a = p.cell_start[row * p.gx + c0], e = p.cell_start[row * p.gx + c1 + 1];
+    for (int i = a + t; i < e; i += 256) {
+      const float dx = p.xs[i] - Cx, dy = p.ys[i] - Cy;
+      const float w = exp2f((mc - (dx * dx + dy * dy)) * 1.4426950408889634f);
+      sw += w;
+      swx = fmaf(w, dx, swx);
+      swy = fmaf(w, dy, swy);
+    }
+  }
+  sw = block_sum(sw, red);
+  swx = block_sum(swx, red);
+  swy = block_sum(swy, red);
+  if (t == 0) {
+    float *tc = const_cast<float *>(p.tcen) + 2 * (blockIdx.y * p.tiles_x + blockIdx.x);
+    tc[0] = (sw > 0.f) ? Cx + swx / sw : Cx;
+    tc[1] = (sw > 0.f) ? Cy + swy / sw : Cy;
+  }
+}
+
 __global__ __launch_bounds__(256) void k_prepass_count(KParams p) {
   __shared__ float cx[256], cy[256];
   const int t = threadIdx.x;
@@ -265,7 +397,8 @@ void launch_prepass(const KParams &p, cudaStream_t st) {
   if (p.weight == MLS_W_WENDLAND) {
     k_prepass_count<<<grid, 256, 0, st>>>(p);
   } else {
-    k_prepass_min<<<grid, 256, 0, st>>>(p);
+    if (p.weight == MLS_W_GAUSS && p.cell_start) k_prepass_min_cells<<<grid, 256, 0, st>>>(p);
+    else k_prepass_min<<<grid, 256, 0, st>>>(p);
     if (p.trunc > 0.0) k_prepass_box<<<grid, 256, 0, st>>>(p);
   }
 }
