@@ -288,17 +288,15 @@ __global__ __launch_bounds__(256) void k_prepass_min_cells(KParams p) {
 
 __global__ __launch_bounds__(256) void k_prepass_count(KParams p) {
   __shared__ float cx[256], cy[256];
+  __shared__ PreGeo G;
   const int t = threadIdx.x;
   const int u0 = blockIdx.x * 16, v0 = blockIdx.y * 16;
   const int u = u0 + (t & 15), v = v0 + (t >> 4);
-  const float px = mlsk::scaled_px(p, u), py = mlsk::scaled_py(p, v);
-  // tile rectangle of pixel centres in raw coordinates
-  const double xlo = p.x0 + (u0 + 0.5) * p.sx, xhi = p.x0 + (u0 + 15.5) * p.sx;
-  const double ylo = p.y0 + (v0 + 0.5) * p.sy, yhi = p.y0 + (v0 + 15.5) * p.sy;
-  const double inv_cell = 1.0 / p.cell;
-  int cx0, cx1, cy0, cy1;
-  cell_range(fmin(xlo, xhi), fmax(xlo, xhi), p.h, p.gx0, inv_cell, p.gx, cx0, cx1);
-  cell_range(fmin(ylo, yhi), fmax(ylo, yhi), p.h, p.gy0, inv_cell, p.gy, cy0, cy1);
+  pre_geometry(p, u0, v0, &G);
+  pre_window(p, u0, v0, p.h, &G);   // the cells within the support radius of the tile's pixels
+  __syncthreads();
+  const float px = G.col[t & 15], py = G.row[t >> 4];
+  const int cx0 = G.win[0], cx1 = G.win[1], cy0 = G.win[2], cy1 = G.win[3];
   int count = 0;
   bool edge = false;
   for (int cyy = cy0; cyy <= cy1 && cx0 <= cx1; ++cyy) {
@@ -325,8 +323,8 @@ __global__ __launch_bounds__(256) void k_prepass_count(KParams p) {
 
   // frame of the tile: Wendland-weighted centroid around its centre
   __shared__ float red[8];
-  const float Cx = 0.5f * (mlsk::scaled_px(p, u0 + 7) + mlsk::scaled_px(p, u0 + 8));
-  const float Cy = 0.5f * (mlsk::scaled_py(p, v0 + 7) + mlsk::scaled_py(p, v0 + 8));
+  const float Cx = 0.5f * (G.col[7] + G.col[8]);
+  const float Cy = 0.5f * (G.row[7] + G.row[8]);
   float sw = 0.f, swx = 0.f, swy = 0.f;
   for (int cyy = cy0; cyy <= cy1 && cx0 <= cx1; ++cyy) {
     const int a = p.cell_start[cyy * p.gx + cx0];
@@ -353,19 +351,18 @@ __global__ __launch_bounds__(256) void k_prepass_count(KParams p) {
 
 __global__ __launch_bounds__(256) void k_prepass_box(KParams p) {
   __shared__ float cx[256], cy[256];
+  __shared__ PreGeo G;
   const int t = threadIdx.x;
   const int u0 = blockIdx.x * 16, v0 = blockIdx.y * 16;
   const int u = u0 + (t & 15), v = v0 + (t >> 4);
-  const float px = mlsk::scaled_px(p, u), py = mlsk::scaled_py(p, v);
+  pre_geometry(p, u0, v0, &G);
+  pre_window(p, u0, v0, p.trunc * p.h * (1.0 + 1e-5), &G);   // the cells within the box of the tile's pixels
+  __syncthreads();
+  const float px = G.col[t & 15], py = G.row[t >> 4];
   const float c = (float)p.trunc;
   // rounding of the scaled offsets grows with the coordinates' magnitude
   const float tx = mlsk::kCntEdgeTol * (c + fabsf(px)), ty = mlsk::kCntEdgeTol * (c + fabsf(py));
-  const double xlo = p.x0 + (u0 + 0.5) * p.sx, xhi = p.x0 + (u0 + 15.5) * p.sx;
-  const double ylo = p.y0 + (v0 + 0.5) * p.sy, yhi = p.y0 + (v0 + 15.5) * p.sy;
-  const double inv_cell = 1.0 / p.cell, rad = p.trunc * p.h * (1.0 + 1e-5);
-  int cx0, cx1, cy0, cy1;
-  cell_range(fmin(xlo, xhi), fmax(xlo, xhi), rad, p.gx0, inv_cell, p.gx, cx0, cx1);
-  cell_range(fmin(ylo, yhi), fmax(ylo, yhi), rad, p.gy0, inv_cell, p.gy, cy0, cy1);
+  const int cx0 = G.win[0], cx1 = G.win[1], cy0 = G.win[2], cy1 = G.win[3];
   int count = 0;
   bool edge = false;
   for (int cyy = cy0; cyy <= cy1 && cx0 <= cx1; ++cyy) {
