@@ -281,11 +281,17 @@ __global__ __launch_bounds__(256) void k_mls_f64(KParams p, int64_t npix_all) {
     const double px = __dadd_rn(p.x0, __dmul_rn(__dadd_rn((double)u, 0.5), p.sx));
     const double py = __dadd_rn(p.y0, __dmul_rn(__dadd_rn((double)v, 0.5), p.sy));
     // candidate ranges: all points, or the cell rows cy0..cy0+nr-1 (columns
-    // cx0..cx1) covering the support (Wendland) or the box (truncated Gaussian)
+    // cx0..cx1) covering the support (Wendland), the box (truncated Gaussian),
+    // or, for listed pixels of the Gaussian, the reach r^2 <= m + kGaussCut h^2
+    // of the pairs the list tier sums (the others are skipped below anyway)
+    const float mlist = (p.list && WK == MLS_W_GAUSS) ? p.mstab[(size_t)v * (p.tiles_x * 16) + u] : 0.f;
+    const bool reach = (WK == MLS_W_GAUSS) && p.list && !binned && p.cell_start != nullptr;
     int nr = 1, cx0 = 0, cx1 = 0, cy0 = 0;
-    if (binned) {
+    if (binned || reach) {
       const double inv_cell = 1.0 / p.cell;
-      const double rad = (WK == MLS_W_WENDLAND) ? p.h : rho * (1.0 + 1e-5);
+      const double rad = (WK == MLS_W_WENDLAND) ? p.h
+                         : binned ? rho * (1.0 + 1e-5)
+                                  : p.h * sqrt(fmax((double)mlist, 0.0) + kGaussCut + 1.0) * (1.0 + 1e-5);
       int cy1;
       cell_range_d(px, px, rad, p.gx0, inv_cell, p.gx, cx0, cx1);
       cell_range_d(py, py, rad, p.gy0, inv_cell, p.gy, cy0, cy1);
@@ -322,8 +328,8 @@ __global__ __launch_bounds__(256) void k_mls_f64(KParams p, int64_t npix_all) {
 #pragma unroll
       for (int dd = 0; dd < DC; ++dd) csum[dd] = 0.0;
       for (int r = 0; r < nr; ++r) {
-        const int64_t a0 = binned ? p.cell_start[(cy0 + r) * p.gx + cx0] : 0;
-        const int64_t a1 = binned ? p.cell_start[(cy0 + r) * p.gx + cx1 + 1] : n;
+        const int64_t a0 = (binned || reach) ? p.cell_start[(cy0 + r) * p.gx + cx0] : 0;
+        const int64_t a1 = (binned || reach) ? p.cell_start[(cy0 + r) * p.gx + cx1 + 1] : n;
         for (int64_t i = a0 + lane; i < a1; i += 32) {
           if (WK == MLS_W_GAUSS && p.list && !binned) {
             // conservative FP32 test before any FP64 work on far pairs
@@ -396,6 +402,7 @@ __global__ __launch_bounds__(256) void k_mls_f64(KParams p, int64_t npix_all) {
 #pragma unroll
         for (int dd = 0; dd < DC; ++dd) R[a][dd] = warp_sum(R[a][dd]);
       count = warp_sum(count);
+      if (WK == MLS_W_GAUSS && !binned) count = n;   // every point has positive weight
       if (WK == MLS_W_INVDIST) {
         ccnt = warp_sum(ccnt);
 #pragma unroll
