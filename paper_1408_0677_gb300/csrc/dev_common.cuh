@@ -262,8 +262,10 @@ __device__ __forceinline__ df32 df_wendland(df32 r2) {
 // ---------------------------------------------------------------------------
 // Small dense linear algebra on the K x K moment matrix (K = 1, 3, 6).
 
+// Cholesky factor L of the SPD matrix A, and the reciprocals of its pivots
+// (the triangular solves multiply by them instead of dividing).
 template <int K, typename T>
-__device__ __forceinline__ bool cholesky(const T (&A)[K][K], T (&L)[K][K]) {
+__device__ __forceinline__ bool cholesky(const T (&A)[K][K], T (&L)[K][K], T (&dinv)[K]) {
 #pragma unroll
   for (int j = 0; j < K; ++j) {
     T s = A[j][j];
@@ -273,6 +275,7 @@ __device__ __forceinline__ bool cholesky(const T (&A)[K][K], T (&L)[K][K]) {
     const T ljj = sqrt(s);
     const T inv = T(1) / ljj;
     L[j][j] = ljj;
+    dinv[j] = inv;
 #pragma unroll
     for (int i = j + 1; i < K; ++i) {
       T v = A[i][j];
@@ -287,33 +290,33 @@ __device__ __forceinline__ bool cholesky(const T (&A)[K][K], T (&L)[K][K]) {
 }
 
 template <int K, typename T>
-__device__ __forceinline__ void chol_solve(const T (&L)[K][K], T (&x)[K]) {
+__device__ __forceinline__ void chol_solve(const T (&L)[K][K], const T (&dinv)[K], T (&x)[K]) {
 #pragma unroll
   for (int i = 0; i < K; ++i) {
     T v = x[i];
 #pragma unroll
     for (int t = 0; t < i; ++t) v -= L[i][t] * x[t];
-    x[i] = v / L[i][i];
+    x[i] = v * dinv[i];
   }
 #pragma unroll
   for (int i = K - 1; i >= 0; --i) {
     T v = x[i];
 #pragma unroll
     for (int t = i + 1; t < K; ++t) v -= L[t][i] * x[t];
-    x[i] = v / L[i][i];
+    x[i] = v * dinv[i];
   }
 }
 
 // 1-norm condition number of the SPD matrix A from its Cholesky factor.
 template <int K, typename T>
-__device__ __forceinline__ T cond1(const T (&A)[K][K], const T (&L)[K][K]) {
+__device__ __forceinline__ T cond1(const T (&A)[K][K], const T (&L)[K][K], const T (&dinv)[K]) {
   T nA = 0, nI = 0;
 #pragma unroll
   for (int c = 0; c < K; ++c) {
     T col[K];
 #pragma unroll
     for (int a = 0; a < K; ++a) col[a] = (a == c) ? T(1) : T(0);
-    chol_solve<K, T>(L, col);
+    chol_solve<K, T>(L, dinv, col);
     T s = 0, sa = 0;
 #pragma unroll
     for (int a = 0; a < K; ++a) {
@@ -354,17 +357,17 @@ __device__ __forceinline__ int solve_pixel_fp32(const float *S, float dx, float 
     if (!(M[a][a] > 0.f)) return SOLVE_RECOMPUTE;
     sd[a] = rsqrtf(M[a][a]);
   }
-  float Me[K][K], Lf[K][K];
+  float Me[K][K], Lf[K][K], df[K];
 #pragma unroll
   for (int a = 0; a < K; ++a)
 #pragma unroll
     for (int b = 0; b < K; ++b) Me[a][b] = M[a][b] * sd[a] * sd[b];
-  if (!cholesky<K, float>(Me, Lf)) return SOLVE_RECOMPUTE;
+  if (!cholesky<K, float>(Me, Lf, df)) return SOLVE_RECOMPUTE;
   // a pivot this small means a condition beyond what FP32 can estimate
 #pragma unroll
   for (int a = 0; a < K; ++a)
     if (!(Lf[a][a] * Lf[a][a] > 1e-6f)) return SOLVE_RECOMPUTE;
-  const float cnd = (K == 1) ? 1.f : cond1<K, float>(Me, Lf);
+  const float cnd = (K == 1) ? 1.f : cond1<K, float>(Me, Lf, df);
   if (!(cnd <= (float)p.cond_recompute)) return SOLVE_RECOMPUTE;
   if (K > 1) {
     const float gr = 1.f + fmaxf(fabsf(dx), fabsf(dy));
@@ -374,7 +377,7 @@ __device__ __forceinline__ int solve_pixel_fp32(const float *S, float dx, float 
   }
   if (cnd > (float)p.cond_fp64) {
     // FP64 factorisation of the same moments
-    double Md[K][K], sdd[K], Med[K][K], Ld[K][K];
+    double Md[K][K], sdd[K], Med[K][K], Ld[K][K], dd[K];
 #pragma unroll
     for (int a = 0; a < K; ++a)
 #pragma unroll
@@ -385,11 +388,11 @@ __device__ __forceinline__ int solve_pixel_fp32(const float *S, float dx, float 
     for (int a = 0; a < K; ++a)
 #pragma unroll
       for (int b = 0; b < K; ++b) Med[a][b] = Md[a][b] * sdd[a] * sdd[b];
-    if (!cholesky<K, double>(Med, Ld)) return SOLVE_RECOMPUTE;
+    if (!cholesky<K, double>(Med, Ld, dd)) return SOLVE_RECOMPUTE;
     double y[K];
 #pragma unroll
     for (int a = 0; a < K; ++a) y[a] = (double)bv[a] * sdd[a];
-    chol_solve<K, double>(Ld, y);
+    chol_solve<K, double>(Ld, dd, y);
 #pragma unroll
     for (int a = 0; a < K; ++a) z[a] = (float)(y[a] * sdd[a]);
     return SOLVE_FP64;
@@ -398,7 +401,7 @@ __device__ __forceinline__ int solve_pixel_fp32(const float *S, float dx, float 
   float y[K];
 #pragma unroll
   for (int a = 0; a < K; ++a) y[a] = bv[a] * sd[a];
-  chol_solve<K, float>(Lf, y);
+  chol_solve<K, float>(Lf, df, y);
 #pragma unroll
   for (int a = 0; a < K; ++a) z[a] = y[a] * sd[a];
   // one refinement step: r = b - M z, z += M^{-1} r
@@ -410,7 +413,7 @@ __device__ __forceinline__ int solve_pixel_fp32(const float *S, float dx, float 
     for (int b = 0; b < K; ++b) acc = fmaf(-M[a][b], z[b], acc);
     r[a] = acc * sd[a];
   }
-  chol_solve<K, float>(Lf, r);
+  chol_solve<K, float>(Lf, df, r);
 #pragma unroll
   for (int a = 0; a < K; ++a) z[a] = fmaf(r[a], sd[a], z[a]);
   // rounding of each right-hand side R_a moves the value by at most about
