@@ -92,6 +92,7 @@ struct KParams {
   const int *cell_start;       // [gx * gy + 1] (Wendland)
   int gx, gy;
   double gx0, gy0, cell;       // grid origin and cell size in raw coordinates
+  double inv_cell;             // 1 / cell, formed on the host as the binning forms it
   // method
   int degree, weight;
   double h, alpha;

@@ -433,9 +433,9 @@ __global__ __launch_bounds__(kWarps * 32, 4) void k_handover(KParams p, const in
       // r^2 <= m + kCut (Gaussian), widened by a relative 1e-5 against rounding
       const double rad = (WK == MLS_W_WENDLAND ? 1.0
                           : p.trunc > 0.0      ? p.trunc
-                                               : sqrt(fmax((double)mhat, 0.0) + (double)kCut)) *
+                                               : (double)sqrtf(fmaxf(mhat, 0.f) + kCut)) *
                          p.h * (1.0 + 1e-5);
-      const double inv_cell = 1.0 / p.cell;
+      const double inv_cell = p.inv_cell;
       R.all_n = 0;
       R.cx0 = max((int)floor((px - rad - p.gx0) * inv_cell), 0);
       R.cx1 = min((int)floor((px + rad - p.gx0) * inv_cell), p.gx - 1);

@@ -231,6 +231,7 @@ static mlsk::KParams base_params(const mls_handle *h, const RenderCtx *c, const 
   p.gx0 = P.gx0;
   p.gy0 = P.gy0;
   p.cell = P.cell;
+  p.inv_cell = P.cell > 0.0 ? 1.0 / P.cell : 0.0;
   p.degree = d.variant != MLS_V_POLY ? 1 : d.degree;   // the mappings use the linear moments
   p.variant = d.variant;
   p.trunc = d.support;

@@ -54,6 +54,10 @@ __global__ __launch_bounds__(128) void k_mls_f32(KParams p) {
   constexpr int K = n_terms(DEG), NM = n_moments(DEG), DC = kF32DC;
   __shared__ float sx[kF32Chunk], sy[kF32Chunk];
   __shared__ float sf[DC][kF32Chunk];
+  // block geometry, formed once in FP64 (GB300's FP64 rate is a small
+  // fraction of FP32's): frame offsets of the 16 columns and 8 rows, cell range
+  __shared__ float s_col[16], s_row[8];
+  __shared__ int s_rng[4];
   const int t = threadIdx.x;
   const int u = blockIdx.x * 16 + (t & 15), v = blockIdx.y * 8 + (t >> 4);
   const bool inside = (u < p.W) && (v < p.H);
@@ -62,8 +66,8 @@ __global__ __launch_bounds__(128) void k_mls_f32(KParams p) {
   // compared with h (p.pixel_frame), in each pixel's own frame
   const int tile = (int)(blockIdx.y >> 1) * p.tiles_x + (int)blockIdx.x;
   const float cxs = p.tcen[2 * tile], cys = p.tcen[2 * tile + 1];
-  const float dpx = (float)((p.x0 + (u + 0.5) * p.sx - p.ctr_x) * p.inv_s - (double)cxs);
-  const float dpy = (float)((p.y0 + (v + 0.5) * p.sy - p.ctr_y) * p.inv_s - (double)cys);
+  if (t < 16) s_col[t] = (float)((p.x0 + (blockIdx.x * 16 + t + 0.5) * p.sx - p.ctr_x) * p.inv_s - (double)cxs);
+  else if (t < 24) s_row[t - 16] = (float)((p.y0 + (blockIdx.y * 8 + t - 16 + 0.5) * p.sy - p.ctr_y) * p.inv_s - (double)cys);
   const size_t pstride = (size_t)p.tiles_x * 16;
   // compact support: the Wendland weight, or the truncated Gaussian's box |dx|, |dy| < c
   const bool binned = (WK == MLS_W_WENDLAND) || (WK == MLS_W_GAUSS && p.trunc > 0.0);
@@ -76,19 +80,24 @@ __global__ __launch_bounds__(128) void k_mls_f32(KParams p) {
   // +- h (+- c h; Gaussian: +- h sqrt(max m + gcut), beyond which every weight
   // is below FP32 resolution of the sums)
   const bool cut = (WK == MLS_W_GAUSS) && !binned && p.gcut > 0.f;
-  int nr = 1, cx0 = 0, cx1 = 0, cy0 = 0;
-  if (binned || cut) {
+  if ((binned || cut) && t == 24) {
     const double rad = (WK == MLS_W_WENDLAND) ? p.h
                        : binned ? p.trunc * p.h * (1.0 + 1e-5)
-                                : p.h * sqrt((double)p.tmax[tile] + (double)p.gcut) * (1.0 + 1e-5);
+                                : p.h * (double)sqrtf(p.tmax[tile] + p.gcut) * (1.0 + 1e-5);
     const int bu0 = blockIdx.x * 16, bv0 = blockIdx.y * 8;
     const double xa = p.x0 + (bu0 + 0.5) * p.sx, xb = p.x0 + (bu0 + 15.5) * p.sx;
     const double ya = p.y0 + (bv0 + 0.5) * p.sy, yb = p.y0 + (bv0 + 7.5) * p.sy;
-    const double inv_cell = 1.0 / p.cell;
-    int cy1;
-    cell_range_d(fmin(xa, xb), fmax(xa, xb), rad, p.gx0, inv_cell, p.gx, cx0, cx1);
-    cell_range_d(fmin(ya, yb), fmax(ya, yb), rad, p.gy0, inv_cell, p.gy, cy0, cy1);
-    nr = (cx0 <= cx1) ? max(cy1 - cy0 + 1, 0) : 0;
+    cell_range_d(fmin(xa, xb), fmax(xa, xb), rad, p.gx0, p.inv_cell, p.gx, s_rng[0], s_rng[1]);
+    cell_range_d(fmin(ya, yb), fmax(ya, yb), rad, p.gy0, p.inv_cell, p.gy, s_rng[2], s_rng[3]);
+  }
+  __syncthreads();
+  const float dpx = s_col[t & 15], dpy = s_row[t >> 4];
+  int nr = 1, cx0 = 0, cx1 = 0, cy0 = 0;
+  if (binned || cut) {
+    cx0 = s_rng[0];
+    cx1 = s_rng[1];
+    cy0 = s_rng[2];
+    nr = (cx0 <= cx1) ? max(s_rng[3] - cy0 + 1, 0) : 0;
   }
   const size_t plane = (size_t)p.W * p.H;
   const size_t pix = (size_t)v * p.W + u;
@@ -288,7 +297,7 @@ __global__ __launch_bounds__(256) void k_mls_f64(KParams p, int64_t npix_all) {
     const bool reach = (WK == MLS_W_GAUSS) && p.list && !binned && p.cell_start != nullptr;
     int nr = 1, cx0 = 0, cx1 = 0, cy0 = 0;
     if (binned || reach) {
-      const double inv_cell = 1.0 / p.cell;
+      const double inv_cell = p.inv_cell;
       const double rad = (WK == MLS_W_WENDLAND) ? p.h
                          : binned ? rho * (1.0 + 1e-5)
                                   : p.h * sqrt(fmax((double)mlist, 0.0) + kGaussCut + 1.0) * (1.0 + 1e-5);

@@ -175,7 +175,7 @@ __device__ __forceinline__ void pre_window(const KParams &p, int u0, int v0, dou
                                            float bound = -1.f, double rmin = 0.0) {
   if (threadIdx.x == 0) {
     if (bound >= 0.f) r = fmax(sqrt((double)bound) * p.h * (1.0 + 1e-5) + 1e-12, rmin);
-    const double inv_cell = 1.0 / p.cell;
+    const double inv_cell = p.inv_cell;
     const double xa = p.x0 + (u0 + 0.5) * p.sx, xb = p.x0 + (u0 + 15.5) * p.sx;
     const double ya = p.y0 + (v0 + 0.5) * p.sy, yb = p.y0 + (v0 + 15.5) * p.sy;
     cell_range(fmin(xa, xb), fmax(xa, xb), r, p.gx0, inv_cell, p.gx, g->win[0], g->win[1]);

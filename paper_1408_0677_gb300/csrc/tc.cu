@@ -322,7 +322,7 @@ __device__ void tile_geometry(const KParams &p, int u0, int v0, int hgt, float c
     const int n0 = ax ? u0 : v0, n1 = ax ? u0 + 15 : v0 + hgt - 1, ng = ax ? p.gx : p.gy;
     const double a = o + (n0 + 0.5) * s, b = o + (n1 + 0.5) * s;
     const double e = upper ? fmax(a, b) + rad : fmin(a, b) - rad;
-    const int c = (int)floor((e - g0) * (1.0 / p.cell));   // the binning's expression
+    const int c = (int)floor((e - g0) * p.inv_cell);   // the binning's expression
     g->cr[lane] = upper ? min(c, ng - 1) : max(c, 0);
   }
 }

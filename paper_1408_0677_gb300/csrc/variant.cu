@@ -114,7 +114,7 @@ __global__ __launch_bounds__(128) void k_mls_variant(KParams p, int tiles_x) {
   if (binned) {
     const double xa = p.x0 + (bx * 16 + 0.5) * p.sx, xb = p.x0 + (bx * 16 + 15.5) * p.sx;
     const double ya = p.y0 + (by * 8 + 0.5) * p.sy, yb = p.y0 + (by * 8 + 7.5) * p.sy;
-    const double inv_cell = 1.0 / p.cell;
+    const double inv_cell = p.inv_cell;
     int cy1;
     cx0 = max((int)floor((fmin(xa, xb) - rad - p.gx0) * inv_cell), 0);
     cx1 = min((int)floor((fmax(xa, xb) + rad - p.gx0) * inv_cell), p.gx - 1);
