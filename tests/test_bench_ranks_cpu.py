@@ -64,3 +64,22 @@ def test_reference_arm_under_torchrun_prints_one_line():
     d = json.loads(lines[0])
     assert d["impl"] == "reference" and d["n_gpus"] == 2 and d["value"] > 0
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["cpu_baseline"]["kind"] == "oracle"
+
+
+def test_pairs_in_boxes_equals_the_oracle_counts():
+    """bench.py counts the truncated Gaussian's pixel-point pairs per point
+    (the rectangle of pixels its box covers); the oracle counts them per
+    pixel.  Both must agree exactly, including ragged rasters and zoomed
+    views."""
+    import dataclasses
+
+    import oracle
+    sys.path.insert(0, ROOT)
+    import bench
+    from paper_1408_0677_gb300 import inputs
+    for wl, c in ((inputs.small_random(61, 80, 3, 41, 29, 2, 0, 0.05), 2.0),
+                  (inputs.fourier_mix(51, 3000, 2, 77, 53, 1, 0, 0.02), 3.0)):
+        for view in ((0.0, 0.0, 1.0, 1.0), (0.2, 0.1, 0.7, 0.45)):
+            w = dataclasses.replace(wl, trunc=c, view=view)
+            r = oracle.mls(w.xy, w.F, w.degree, w.weight, w.h, w.W, w.H, view=view, trunc=c)
+            assert bench.pairs_in_boxes(w) == int(r.count.sum())
