@@ -50,7 +50,11 @@ constexpr int kPosFloats = (kKT / 8) * kXB; // 160 floats of positions per stage
 // separable Gaussian weights: per stage buffer of 16 column and 16 row factor
 // rows of 64 points (row stride 68 floats: rows fall on distinct banks)
 constexpr int kEXS = 68;
-constexpr int kExyFloats = 32 * kEXS;
+// The 16 row-factor rows start 16 floats past the column-factor rows
+// (kRowOff): 16 kEXS is a multiple of 32 banks, so without the shift a point's
+// column and row factors land on the same bank and every store pair conflicts.
+constexpr int kRowOff = 16 * kEXS + 16;
+constexpr int kExyFloats = 32 * kEXS + 16;
 constexpr int kGaussHdr = 4 * 32 * 4;        // per weight warp: alpha[16], beta[16]
 constexpr int kPrmBytes = kGaussHdr + 2 * kExyFloats * 4;   // >= the Wendland point parameters (4 KB)
 // Common factor of all FP16 weights (the fit does not depend on it): the
@@ -490,7 +494,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mls_tc(KParams p, int d0, int D
     const bool boxed = p.trunc > 0.0;
     const float cbox = (float)p.trunc;
     float *sAB = (float *)(smem + lay.offPrm) + 32 * warp;     // this warp's alpha[16], beta[16]
-    float *exy = (float *)(smem + lay.offPrm + kGaussHdr);     // [2][32 rows][kEXS]
+    float *exy = (float *)(smem + lay.offPrm + kGaussHdr);     // [2][16 column rows, 16 row rows at kRowOff]
     {
       const int stride = p.tiles_x * 16;
       const int r = lane & 15, c = lane & 15;
@@ -553,7 +557,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mls_tc(KParams p, int d0, int D
         }
         const float other = __shfl_xor_sync(0xffffffffu, mx, 1);
         const float sh = half ? 0.5f * (mx - other) : 0.5f * (other - mx);   // Y' = Y - sh, X' = X + sh
-        float *dst = tab + 16 * half * kEXS + jp;
+        float *dst = tab + half * kRowOff + jp;
         if (boxed) {   // uniform over the grid
 #pragma unroll
           for (int k = 0; k < 16; ++k)
@@ -576,8 +580,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_mls_tc(KParams p, int d0, int D
       unsigned char *A0 = smem + kOffA + (s * 2 + 0) * kABytes;
       unsigned char *A1 = smem + kOffA + (s * 2 + 1) * kABytes;
       const float *fx = tab + cown * kEXS;
-      const float *fy0 = tab + (16 + r0) * kEXS;
-      const float *fy1 = tab + (16 + r0 + 8) * kEXS;
+      const float *fy0 = tab + kRowOff + r0 * kEXS;
+      const float *fy1 = tab + kRowOff + (r0 + 8) * kEXS;
 #pragma unroll 2
       for (int c = 0; c < 8; ++c) {
         const float4 xa = *(const float4 *)(fx + 8 * c), xb = *(const float4 *)(fx + 8 * c + 4);
