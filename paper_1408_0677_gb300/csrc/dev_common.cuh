@@ -46,11 +46,6 @@ constexpr float kGaussOperandCut = 28.f;
 
 // Monomials of degree <= 4 in (x, y), the entries of the moment matrix:
 // 0:1 1:x 2:y 3:xx 4:xy 5:yy 6:xxx 7:xxy 8:xyy 9:yyy 10:xxxx 11:xxxy 12:xxyy 13:xyyy 14:yyyy
-// Basis terms b_a (a < 6): 1, x, y, xx, xy, yy.  M_ab = S[kMIdx[a][b]].
-__device__ __constant__ static const int kMIdx[6][6] = {
-    {0, 1, 2, 3, 4, 5},   {1, 3, 4, 6, 7, 8},    {2, 4, 5, 7, 8, 9},
-    {3, 6, 7, 10, 11, 12}, {4, 7, 8, 11, 12, 13}, {5, 8, 9, 12, 13, 14}};
-
 // Exponents (ex, ey) of monomial j.
 __host__ __device__ constexpr int mono_ex(int j) {
   return j == 0 ? 0 : j == 1 ? 1 : j == 2 ? 0 : j == 3 ? 2 : j == 4 ? 1 : j == 5 ? 0
@@ -66,6 +61,12 @@ __host__ __device__ constexpr int mono_index(int ex, int ey) {
   // inverse of (mono_ex, mono_ey) for ex + ey <= 4
   return (ex + ey) == 0 ? 0 : (ex + ey) == 1 ? 1 + ey : (ex + ey) == 2 ? 3 + ey
        : (ex + ey) == 3 ? 6 + ey : 10 + ey;
+}
+// Basis terms b_a (a < 6): 1, x, y, xx, xy, yy.  M_ab = S[midx(a, b)], the
+// moment of the product monomial; in unrolled loops the index folds to a
+// constant, so a moment array held in registers stays there.
+__host__ __device__ constexpr int midx(int a, int b) {
+  return mono_index(mono_ex(a) + mono_ex(b), mono_ey(a) + mono_ey(b));
 }
 __host__ __device__ constexpr int n_terms(int deg) { return (deg + 1) * (deg + 2) / 2; }
 // number of moment monomials needed by a degree-deg basis (degree <= 2 deg)
@@ -350,7 +351,7 @@ __device__ __forceinline__ int solve_pixel_fp32(const float *S, float dx, float 
 #pragma unroll
   for (int a = 0; a < K; ++a)
 #pragma unroll
-    for (int b = 0; b < K; ++b) M[a][b] = S[kMIdx[a][b]];
+    for (int b = 0; b < K; ++b) M[a][b] = S[midx(a, b)];
   float bv[6] = {1.f, dx, dy, dx * dx, dx * dy, dy * dy};
   float sd[K];
 #pragma unroll

@@ -44,11 +44,6 @@ constexpr float kCut = 40.f;            // Gaussian pairs with (r^2 - m)/h^2 abo
 // (moments and right-hand sides are double-float accurate, ~1e-14)
 constexpr double kKappaCentroid = 1e8;
 
-// moment index of the product of basis terms a and b
-__host__ __device__ constexpr int midx(int a, int b) {
-  return mono_index(mono_ex(a) + mono_ex(b), mono_ey(a) + mono_ey(b));
-}
-
 // ---------------------------------------------------------------------------
 // Double-float helpers without renormalisation, for long accumulations.
 

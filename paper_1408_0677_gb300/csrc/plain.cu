@@ -22,7 +22,7 @@ using namespace mlsk;
 
 constexpr float kLog2e = 1.4426950408889634f;
 
-// Monomials of degree <= 4 of (dx, dy) (index order of kMIdx).
+// Monomials of degree <= 4 of (dx, dy) (the moment index order of midx).
 template <int NM>
 __device__ __forceinline__ void monomials(float dx, float dy, float (&m)[15]) {
   m[0] = 1.f;
@@ -432,7 +432,7 @@ __global__ __launch_bounds__(256) void k_mls_f64(KParams p, int64_t npix_all) {
           double Mm[6][6], sdg[6], Me[6][6], Lm[6][6];
           bool ok = true;
           for (int a = 0; a < k; ++a)
-            for (int b = 0; b < k; ++b) Mm[a][b] = S[kMIdx[a][b]];
+            for (int b = 0; b < k; ++b) Mm[a][b] = S[midx(a, b)];
           for (int a = 0; a < k && ok; ++a) {
             if (!(Mm[a][a] > 0.0)) ok = false;
             else sdg[a] = 1.0 / sqrt(Mm[a][a]);

@@ -215,15 +215,30 @@ __device__ __forceinline__ void tmem_ld48(uint32_t taddr, float (&v)[48]) {
 
 // Iso-band label #{j : t_j <= f} over ascending levels (rounded up to float,
 // so the float comparison equals the double one), by binary search; 255 for NaN.
-__device__ __forceinline__ uint8_t band_search(float f, const float *lev, int L) {
-  if (f != f) return 255;
-  int lo = 0, hi = L;
-  while (lo < hi) {
-    const int mid = (lo + hi) >> 1;
-    if (lev[mid] <= f) lo = mid + 1;
-    else hi = mid;
+// Iso-band labels #{t <= f} of G values, value g against the level row
+// lev + row[g] * P: the L ascending levels, then NaN up to P (a power of two
+// >= L; NaN <= f is false).  Steps of P/2, ..., 1 find how many of the first
+// P - 1 entries are <= f, one more comparison takes the last entry.  Every
+// load is unconditional and every step a select, so there are no branches
+// and the G searches' shared-memory loads run side by side (a loop per value
+// would wait out each load in turn).  NaN values get 255.
+template <int G>
+__device__ __forceinline__ void band_labels(const float (&f)[G], const int (&row)[G], const float *lev, int P,
+                                            int (&band)[G]) {
+#pragma unroll
+  for (int g = 0; g < G; ++g) band[g] = 0;
+  for (int step = P >> 1; step > 0; step >>= 1) {
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+      const float t = lev[row[g] * P + band[g] + step - 1];
+      band[g] = (t <= f[g]) ? band[g] + step : band[g];
+    }
   }
-  return (uint8_t)lo;
+#pragma unroll
+  for (int g = 0; g < G; ++g) {
+    const float t = lev[row[g] * P + band[g]];
+    band[g] = (f[g] != f[g]) ? 255 : band[g] + (t <= f[g] ? 1 : 0);
+  }
 }
 
 // Byte offset of the 16-byte chunk c of row m in a 128B-swizzled K-major tile.
@@ -898,24 +913,6 @@ __global__ void __launch_bounds__(kThreads, 1) k_mls_tc(KParams p, int d0, int D
   pack_init(p, geo, it2);
   const bool any_tile = pack_valid(it2);
   if (warp < 8) {
-    const bool acc_ok = __all_sync(0xffffffffu, mbar_wait(bar_acc, 0, p.err, ERR_WAIT_ACC, limit));
-    tc_fence_after();
-    // every MMA has completed: the operand tiles' shared memory now holds this
-    // pass's levels (rounded up to float) and value scales, read per dimension
-    // below (levels [Dc][L], then scl[Dc], cen[Dc])
-    float *s_lev = (float *)(smem + kOffA);
-    float *s_scl = s_lev + Dc * p.L, *s_cen = s_scl + Dc;
-    for (int e = threadIdx.x; e < Dc * (p.L + 2); e += 256) {
-      if (e < Dc * p.L) {
-        const int d = e / p.L;
-        s_lev[e] = (d0 + d < p.D) ? p.lev32[(size_t)(d0 + d) * p.L + (e - d * p.L)] : 0.f;
-      } else {
-        const int d = e - Dc * p.L, dd = d % Dc, g = d0 + dd;
-        const float val = (g < p.D) ? (d < Dc ? p.fscl32[g] : p.fcen32[g]) : 0.f;
-        (d < Dc ? s_scl : s_cen)[dd] = val;
-      }
-    }
-    asm volatile("bar.sync 1, 256;" ::: "memory");   // the eight epilogue warps
     const int wg = warp >> 2;
     // two accumulators: one warpgroup each; one accumulator: the warpgroups
     // share it and take alternate groups of value columns
@@ -927,6 +924,47 @@ __global__ void __launch_bounds__(kThreads, 1) k_mls_tc(KParams p, int d0, int D
     const int u = u0 + (q & 15), v = v0 + (q >> 4);
     const bool inside = (u < p.W) && (v < p.H);
     const size_t pi = (size_t)v * (p.tiles_x * 16) + u;
+    // the pixel's stabiliser (Gaussian) and support count (Wendland,
+    // truncated Gaussian), and the first staged levels and scales (below),
+    // are fetched while the last MMAs drain
+    const float mst = (WK == MLS_W_WENDLAND) ? 0.f : p.mstab[pi];
+    const int cflag = (WK == MLS_W_WENDLAND || p.trunc > 0.0) ? p.cnt[pi] : 0;
+    // level rows padded with NaN to P entries, a power of two >= L
+    int P = 1;
+    while (P < p.L) P *= 2;
+    const int nstage = Dc * (P + 2);
+    auto staged = [&](int e) -> float {
+      if (e < Dc * P) {
+        const int d = e / P, j = e - d * P;
+        if (j >= p.L) return __int_as_float(0x7fc00000);
+        return (d0 + d < p.D) ? p.lev32[(size_t)(d0 + d) * p.L + j] : 0.f;
+      }
+      const int d = e - Dc * P, g = d0 + d % Dc;
+      return (g < p.D) ? (d < Dc ? p.fscl32[g] : p.fcen32[g]) : 0.f;
+    };
+    constexpr int kPre = 4;
+    float pre[kPre];
+#pragma unroll
+    for (int k = 0; k < kPre; ++k) {
+      const int e = threadIdx.x + 256 * k;
+      pre[k] = (e < nstage) ? staged(e) : 0.f;
+    }
+    const bool acc_ok = __all_sync(0xffffffffu, mbar_wait(bar_acc, 0, p.err, ERR_WAIT_ACC, limit));
+    tc_fence_after();
+    // every MMA has completed: the operand tiles' shared memory now holds this
+    // pass's levels (rounded up to float) and value scales, read per dimension
+    // below (levels [Dc][P], then scl[Dc], cen[Dc])
+    float *s_lev = (float *)(smem + kOffA);
+    float *s_scl = s_lev + Dc * P, *s_cen = s_scl + Dc;
+    // s_lev, s_scl and s_cen are consecutive: element e of the staging order
+    // sits at s_lev[e]
+#pragma unroll
+    for (int k = 0; k < kPre; ++k) {
+      const int e = threadIdx.x + 256 * k;
+      if (e < nstage) s_lev[e] = pre[k];
+    }
+    for (int e = threadIdx.x + 256 * kPre; e < nstage; e += 256) s_lev[e] = staged(e);
+    asm volatile("bar.sync 1, 256;" ::: "memory");   // the eight epilogue warps
     const float dxp = geo->col[q & 15];
     const float dyp = geo->row[q >> 4];
     const uint32_t tbase = tmem + a * 256 + ((uint32_t)(32 * (warp & 3)) << 16);
@@ -940,25 +978,23 @@ __global__ void __launch_bounds__(kThreads, 1) k_mls_tc(KParams p, int d0, int D
     bool handover = false;
     bool cuncertain = false;
     if (WK == MLS_W_WENDLAND) {
-      const int cflag = p.cnt[pi];
       count = cflag & kCntMask;
       handover = cuncertain = count_uncertain<K>(cflag);
     } else {
       count = (int)(p.n < (1 << 30) ? p.n : (1 << 30));
       if (p.trunc > 0.0) {
         // truncated Gaussian: the points in the pixel's box
-        const int cflag = p.cnt[pi];
         count = cflag & kCntMask;
         cuncertain = count_uncertain<K>(cflag);
       }
       // clipping |x~|_inf <= kRMax is exact in 16-bit arithmetic only when the
       // pixel has a point within (kRMax - |delta|_inf - 4.2) h
       const float reach = kRMax - fmaxf(fabsf(dxp), fabsf(dyp));
-      handover = cuncertain || !(p.mstab[pi] <= reach * reach - 18.f) || !read;
+      handover = cuncertain || !(mst <= reach * reach - 18.f) || !read;
       {
         // the weight producers undo the split stabiliser's factor 2^-res up to kResMax
         const float *sAB0 = (const float *)(smem + lay.offPrm);
-        const float res = kLog2e * p.mstab[pi] - sAB0[q & 15] - sAB0[16 + (q >> 4)];
+        const float res = kLog2e * mst - sAB0[q & 15] - sAB0[16 + (q >> 4)];
         handover = handover || !(res <= kResMax);
       }
     }
@@ -1012,17 +1048,28 @@ __global__ void __launch_bounds__(kThreads, 1) k_mls_tc(KParams p, int d0, int D
         }
       }
       if (done && inside && read) {
+        // the group's values (a column past the pass's last dimension reads
+        // that dimension's scales and is not stored)
+        float fv[GD];
+        int row[GD];
+#pragma unroll
+        for (int dd = 0; dd < GD; ++dd) {
+          const int d = min(gbase + dd, Dc - 1);
+          float acc = 0.f;
+#pragma unroll
+          for (int b = 0; b < K; ++b) acc = fmaf(z[b], rv[dd * K + b], acc);
+          fv[dd] = fmaf(acc, s_scl[d], s_cen[d]);
+          row[dd] = d;
+        }
+        int band[GD];
+        if (p.bands) band_labels<GD>(fv, row, s_lev, P, band);
 #pragma unroll
         for (int dd = 0; dd < GD; ++dd) {
           const int d = gbase + dd;
           if (d < Dc && d0 + d < p.D) {
-            float acc = 0.f;
-#pragma unroll
-            for (int b = 0; b < K; ++b) acc = fmaf(z[b], rv[dd * K + b], acc);
-            const int dg = d0 + d;
-            const float f = fmaf(acc, s_scl[d], s_cen[d]);
-            field[(size_t)dg * plane + pix] = f;
-            if (p.bands) p.bands[(size_t)dg * plane + pix] = band_search(f, s_lev + d * p.L, p.L);
+            const size_t o = (size_t)(d0 + d) * plane + pix;
+            field[o] = fv[dd];
+            if (p.bands) p.bands[o] = (uint8_t)band[dd];
           }
         }
       }

@@ -68,6 +68,11 @@ __device__ __forceinline__ float sub(float a, float b) { return a - b; }
 __device__ __forceinline__ double dist2(double dx, double dy) { return __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)); }
 __device__ __forceinline__ float dist2(float dx, float dy) { return fmaf(dx, dx, dy * dy); }
 __device__ __forceinline__ double vmin(double a, double b) { return fmin(a, b); }
+// w / W of the Welford update: exact in FP64; in FP32 the fast quotient (a
+// relative error of a few ulp in one point's share moves the means and
+// co-moments far less than the FP32 rounding of the sums themselves)
+__device__ __forceinline__ double share(double w, double W) { return w / W; }
+__device__ __forceinline__ float share(float w, float W) { return __fdividef(w, W); }
 __device__ __forceinline__ float vmin(float a, float b) { return fminf(a, b); }
 
 // w for a pair at offset (dx, dy), squared distance r2 (raw units in double,
@@ -164,7 +169,7 @@ __global__ __launch_bounds__(128) void k_mls_variant(KParams p, int tiles_x) {
         }
         const T w = pair_weight<WK>(dx, dy, r2, m, p);
         if (!(w > (T)0)) continue;
-        const T Wn = W + w, rr = w / Wn, g = W * rr;   // g = W_old w / W_new
+        const T Wn = W + w, rr = share(w, Wn), g = W * rr;   // g = W_old w / W_new
         const T dpx = dx - mpx, dpy = dy - mpy, dqa = sa[j] - mqa, dqb = sb[j] - mqb;
         mpx += rr * dpx;
         mpy += rr * dpy;
