@@ -446,12 +446,15 @@ __global__ __launch_bounds__(kWarps * 32, 4) void k_handover(KParams p, const in
   };
 
   for (int64_t ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
-    const int64_t q0 = ch * csz;
-    const int nq = (int)((npix - q0) < csz ? (npix - q0) : csz);
+    // chunk ch takes every nchunks-th listed pixel from ch on (nq <= csz of
+    // them).  Neighbouring list entries are often neighbouring pixels of one
+    // tile with similar costs; striding spreads the expensive ones (many near
+    // points) over the chunks, so no block is left with a run of them.
+    const int nq = (int)((npix - ch + nchunks - 1) / nchunks);
 
     // ---- phase 1 (warp per pixel): double-float pixel-frame moments
     for (int j = wib; j < nq; j += kWarps) {
-      const int id = list[q0 + j];
+      const int id = list[ch + (int64_t)j * nchunks];
       Ranges R;
       float mhat, pxh, pxl, pyh, pyl;
       setup(id, R, mhat, pxh, pxl, pyh, pyl);
@@ -527,7 +530,7 @@ __global__ __launch_bounds__(kWarps * 32, 4) void k_handover(KParams p, const in
 
     // ---- phase 3 (warp per pixel): value = sum_i phi_i f_i, phi_i = w_i z . b_c(x_i)
     for (int j = wib; j < nq; j += kWarps) {
-      const int id = list[q0 + j];
+      const int id = list[ch + (int64_t)j * nchunks];
       const int flags = slots[j].flags;
       if (flags & 1) {
         if (lane == 0) {
