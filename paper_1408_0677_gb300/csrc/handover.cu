@@ -384,6 +384,7 @@ struct ChunkSlot {
   float fr[5];     // centroid frame
   long long count;
   int flags;       // bit 0: needs the FP64 kernel; bits 8..: degree used + 1
+  int nnear;       // near points (the cost of the pixel's value phase)
 };
 
 template <int DEG, int WK>
@@ -395,7 +396,13 @@ __global__ __launch_bounds__(kWarps * 32, 4) void k_handover(KParams p, const in
   __shared__ float4 s_rx[kWarps][kRing];
   __shared__ ChunkSlot s_chunk[32];
   __shared__ float2 s_tab[64];
+  // the chunk's pixels are claimed one at a time by the warps (counters of
+  // the moment and value phases); the value phase takes them in decreasing
+  // order of their near points (longest first), so the warps finish together
+  __shared__ int s_next[2];
+  __shared__ int s_order[32];
   if (WK == MLS_W_GAUSS) df_exp_table_init(s_tab);
+  if (threadIdx.x == 0) s_next[0] = s_next[1] = 0;
   __syncthreads();
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   int *ri = s_ri[wib];
@@ -453,7 +460,11 @@ __global__ __launch_bounds__(kWarps * 32, 4) void k_handover(KParams p, const in
     const int nq = (int)((npix - ch + nchunks - 1) / nchunks);
 
     // ---- phase 1 (warp per pixel): double-float pixel-frame moments
-    for (int j = wib; j < nq; j += kWarps) {
+    for (;;) {
+      int j = 0;
+      if (lane == 0) j = atomicAdd(&s_next[0], 1);
+      j = __shfl_sync(0xffffffffu, j, 0);
+      if (j >= nq) break;
       const int id = list[ch + (int64_t)j * nchunks];
       Ranges R;
       float mhat, pxh, pxl, pyh, pyl;
@@ -501,6 +512,7 @@ __global__ __launch_bounds__(kWarps * 32, 4) void k_handover(KParams p, const in
       }
       if (lane == 0) {
         slots[j].count = (WK == MLS_W_WENDLAND || p.trunc > 0.0) ? nnear : p.n;
+        slots[j].nnear = nnear;
         // inverse distance: a coincident point (or a zero stabiliser) goes to
         // the FP64 kernel, which gives the pixel that point's value
         slots[j].flags = (WK == MLS_W_INVDIST && (coincident || !(mhat > 0.f))) ? 1 : 0;
@@ -510,6 +522,20 @@ __global__ __launch_bounds__(kWarps * 32, 4) void k_handover(KParams p, const in
 
     __syncthreads();
     // ---- phase 2 (lane per pixel): degree policy and centroid-frame solve in FP64
+    if (wib == 1) {
+      // value-phase order and counters; the moment counter is reset for the
+      // next chunk (every warp has left this chunk's moment phase)
+      if (lane < nq) {
+        const int c = slots[lane].nnear;
+        int rank = 0;
+        for (int k = 0; k < nq; ++k) {
+          const int ck = slots[k].nnear;
+          rank += (ck > c || (ck == c && k < lane)) ? 1 : 0;
+        }
+        s_order[rank] = lane;
+      }
+      if (lane == 0) s_next[0] = s_next[1] = 0;
+    }
     if (wib == 0 && lane < nq) {
       ChunkSlot &sl = slots[lane];
       if (!(sl.flags & 1)) {
@@ -529,7 +555,12 @@ __global__ __launch_bounds__(kWarps * 32, 4) void k_handover(KParams p, const in
     __syncthreads();
 
     // ---- phase 3 (warp per pixel): value = sum_i phi_i f_i, phi_i = w_i z . b_c(x_i)
-    for (int j = wib; j < nq; j += kWarps) {
+    for (;;) {
+      int k = 0;
+      if (lane == 0) k = atomicAdd(&s_next[1], 1);
+      k = __shfl_sync(0xffffffffu, k, 0);
+      if (k >= nq) break;
+      const int j = s_order[k];
       const int id = list[ch + (int64_t)j * nchunks];
       const int flags = slots[j].flags;
       if (flags & 1) {

@@ -146,10 +146,31 @@ static mls_status ensure_scratch(RenderCtx *c, int W, int H, cudaStream_t st) {
   return MLS_OK;
 }
 
+// Pinned host staging of the level uploads, per device and shared by every
+// handle on it, so that a render enqueues its level copies without waiting
+// for its stream (a copy from pageable memory would need the stream drained
+// before the source could be reused).  Uploads take the slots of a small
+// ring in turn; a slot is refilled only after the copy that last read it has
+// completed.
+namespace {
+constexpr int kStageSlots = 8;
+constexpr int kStageDevices = 64;
+struct LevelStage {
+  std::mutex mu;
+  int next = 0;
+  void *buf[kStageSlots] = {};
+  size_t cap[kStageSlots] = {};
+  cudaEvent_t done[kStageSlots] = {};
+  bool pending[kStageSlots] = {};
+};
+LevelStage g_level_stage[kStageDevices];
+}  // namespace
+
 static mls_status upload_levels(mls_handle *h, RenderCtx *c, const double *levels, int L, cudaStream_t st) {
   const int D = h->desc.D;
   const size_t cnt = (size_t)D * L;
   if (cnt == 0) return MLS_OK;
+  if (h->device < 0 || h->device >= kStageDevices) return fail(MLS_E_UNSUPPORTED, "device ordinal out of range");
   if (cnt > c->lev_cap) {
     ctx_release(c, c->lev64, st);
     ctx_release(c, c->lev32, st);
@@ -164,20 +185,36 @@ static mls_status upload_levels(mls_handle *h, RenderCtx *c, const double *level
     c->lev32 = (float *)p;
     c->lev_cap = cnt;
   }
+  LevelStage &g = g_level_stage[h->device];
+  std::lock_guard<std::mutex> lock(g.mu);
+  const int k = g.next;
+  g.next = (g.next + 1) % kStageSlots;
+  if (g.pending[k]) {
+    MLS_CUDA_TRY(cudaEventSynchronize(g.done[k]));
+    g.pending[k] = false;
+  }
+  if (!g.done[k]) MLS_CUDA_TRY(cudaEventCreateWithFlags(&g.done[k], cudaEventDisableTiming));
+  const size_t bytes = cnt * (sizeof(double) + sizeof(float));
+  if (g.cap[k] < bytes) {
+    if (g.buf[k]) cudaFreeHost(g.buf[k]);
+    g.buf[k] = nullptr;
+    g.cap[k] = 0;
+    MLS_CUDA_TRY(cudaMallocHost(&g.buf[k], bytes));
+    g.cap[k] = bytes;
+  }
+  double *dn = (double *)g.buf[k];
+  float *up = (float *)(dn + cnt);
   // float copies rounded up: for a float f, f >= t exactly when f >= t_up
-  static thread_local std::vector<float> up;
-  static thread_local std::vector<double> dn;
-  up.resize(cnt);
-  dn.assign(levels, levels + cnt);
   for (size_t i = 0; i < cnt; ++i) {
+    dn[i] = levels[i];
     float f = (float)levels[i];
     if ((double)f < levels[i]) f = nextafterf(f, INFINITY);
     up[i] = f;
   }
-  MLS_CUDA_TRY(cudaMemcpyAsync(c->lev64, dn.data(), cnt * sizeof(double), cudaMemcpyHostToDevice, st));
-  MLS_CUDA_TRY(cudaMemcpyAsync(c->lev32, up.data(), cnt * sizeof(float), cudaMemcpyHostToDevice, st));
-  // pageable sources: make sure the copies have consumed them
-  MLS_CUDA_TRY(cudaStreamSynchronize(st));
+  MLS_CUDA_TRY(cudaMemcpyAsync(c->lev64, dn, cnt * sizeof(double), cudaMemcpyHostToDevice, st));
+  MLS_CUDA_TRY(cudaMemcpyAsync(c->lev32, up, cnt * sizeof(float), cudaMemcpyHostToDevice, st));
+  MLS_CUDA_TRY(cudaEventRecord(g.done[k], st));
+  g.pending[k] = true;
   return MLS_OK;
 }
 
