@@ -432,7 +432,7 @@ def run_ours(args):
             "roofline": roof, "cpu_baseline": cpu, "clocks": clocks,
             "gpu_launches": int(launches),
             "recompute": {"handed_over_pixels": int(handed), "fp64_pixels": int(handed64),
-                          "split_weight_tiles": int(retried)},
+                          "split_weight_half_tiles": int(retried)},
             "pairs": {"workload": int(pairs), "visited_by_main_kernel": int(pairs_visited),
                       "visited_fraction": pairs_visited / (W * H * n),
                       "note": "the main kernel visits, per 16 x 16 tile, the grid cells holding points whose "

@@ -153,7 +153,8 @@ typedef struct mls_stats {
     double last_render_ms;    /* device time of the last render (CUDA events) */
     double main_kernel_ms;    /* device time of its main MLS kernel(s) over every tile, events on the
                                  same stream (weight_split 2: the single-weight pass only) */
-    int64_t retried_tiles;    /* tiles rendered again with split weights (weight_split 2) */
+    int64_t retried_tiles;    /* half tiles (16 x 8 pixels) rendered again with split weights
+                                 (weight_split 2) */
 } mls_stats;
 
 typedef struct mls_handle mls_handle;

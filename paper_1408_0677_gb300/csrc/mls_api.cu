@@ -112,7 +112,7 @@ size_t scratch_bytes_for(int W, int H) {
   const size_t padded = (size_t)tx * kTile * ty * kTile;
   const size_t ntile = (size_t)tx * ty;
   return 256 + padded * sizeof(float) + padded * sizeof(int) + 2 * (size_t)W * H * sizeof(int) +
-         3 * ntile * sizeof(float) + 2 * ntile * sizeof(int) + 256;
+         3 * ntile * sizeof(float) + 4 * ntile * sizeof(int) + 256;
 }
 
 // Grow a render context's scratch to fit a view.
@@ -132,7 +132,7 @@ static mls_status ensure_scratch(RenderCtx *c, int W, int H, cudaStream_t st) {
     c->scratch_bytes = need;
   }
   char *b = (char *)c->scratch;
-  c->counters = (unsigned int *)b;           // [0] hand-over count, [1] FP64 count, [2] retried tiles
+  c->counters = (unsigned int *)b;           // [0] hand-over count, [1] FP64 count, [2] retried half tiles
   c->visited = (unsigned long long *)(b + 16);
   c->err = (int *)(b + 64);
   c->mstab = (float *)(b + 256);
@@ -141,8 +141,8 @@ static mls_status ensure_scratch(RenderCtx *c, int W, int H, cudaStream_t st) {
   c->relist2 = c->relist + (size_t)W * H;
   c->tcen = (float *)(c->relist2 + (size_t)W * H);
   c->tile_mark = (int *)(c->tcen + 2 * ntile);
-  c->retry_tiles = c->tile_mark + ntile;
-  c->tmax = (float *)(c->retry_tiles + ntile);
+  c->retry_tiles = c->tile_mark + 2 * ntile;   // both indexed by half tile
+  c->tmax = (float *)(c->retry_tiles + 2 * ntile);
   return MLS_OK;
 }
 
@@ -506,10 +506,10 @@ static mls_status render_enqueue(mls_handle *h, RenderCtx *c, const mlsk::KParam
       const bool fp16 = h->desc.precision == MLS_P_FP16;
       int nl = 0;
       if (h->desc.weight_split == 2) {
-        // single weights everywhere; tiles with a failing pixel are queued
-        // and rendered again with split weights
+        // single weights everywhere; the 8-row halves of tiles with a
+        // failing pixel are queued and rendered again with split weights
         const int ntile = p.tiles_x * p.tiles_y;
-        MLS_CUDA_TRY(cudaMemsetAsync(c->tile_mark, 0, sizeof(int) * ntile, st));
+        MLS_CUDA_TRY(cudaMemsetAsync(c->tile_mark, 0, sizeof(int) * 2 * ntile, st));
         mlsk::KParams p1 = p;
         p1.visited = c->visited;
         p1.retry_tiles = c->retry_tiles;

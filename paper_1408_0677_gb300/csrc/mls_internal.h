@@ -47,8 +47,8 @@ struct RenderCtx {
   int *relist = nullptr;
   int *relist2 = nullptr;            // pixels the hand-over path passes to FP64
   float *tcen = nullptr;             // per-tile moment frame centres
-  unsigned int *counters = nullptr;  // [0] recompute count, [1] FP64 count, [2] retried tiles
-  int *tile_mark = nullptr;          // per tile: queued for the split-weight pass
+  unsigned int *counters = nullptr;  // [0] recompute count, [1] FP64 count, [2] retried half tiles
+  int *tile_mark = nullptr;          // per half tile: queued for the split-weight pass
   int *retry_tiles = nullptr;
   float *tmax = nullptr;             // per-tile largest stabiliser (Gaussian)
   unsigned long long *visited = nullptr;   // pixel-point pairs the main kernel visited

@@ -449,12 +449,14 @@ __global__ void __launch_bounds__(kThreads, 1) k_mls_tc(KParams p, int d0, int D
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   int u0, v0;
   if (p.tile_list) {
-    // second pass over listed tiles: 2 / NACC CTAs per tile, the rest exit
-    const int slot = blockIdx.x / (2 / NACC), part = blockIdx.x % (2 / NACC);
+    // second pass over listed half tiles (2 tile + the 8-row half): one CTA
+    // per entry, the rest exit.  An 8-row CTA (NACC == 1) takes its half; a
+    // 16-row CTA would take the whole tile.
+    const int slot = blockIdx.x;
     if (slot >= (int)*p.tile_count) return;
-    const int tl = p.tile_list[slot];
+    const int ht = p.tile_list[slot], tl = ht >> 1;
     u0 = (tl % p.tiles_x) * 16;
-    v0 = (tl / p.tiles_x) * 16 + part * TH;
+    v0 = (tl / p.tiles_x) * 16 + (NACC == 1 ? (ht & 1) * 8 : 0);
   } else {
     u0 = blockIdx.x * 16;
     v0 = blockIdx.y * TH;
@@ -1010,10 +1012,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_mls_tc(KParams p, int d0, int D
     float *field = (float *)p.field;
     if (primary && inside && give && d0 == 0) {
       if (p.retry_tiles) {
-        // first of two passes: queue the tile once for the split-weight pass
-        if (atomicExch(&p.tile_mark[tile], 1) == 0) {
+        // first of two passes: queue the pixel's 8-row half of the tile once
+        // for the split-weight pass (the other half keeps this pass's values)
+        const int ht = 2 * tile + ((v >> 3) & 1);
+        if (atomicExch(&p.tile_mark[ht], 1) == 0) {
           const unsigned int k = atomicAdd(p.retry_count, 1u);
-          p.retry_tiles[k] = tile;
+          p.retry_tiles[k] = ht;
         }
       } else {
         const unsigned int k = atomicAdd(p.relist_count, 1u);
@@ -1102,8 +1106,9 @@ __global__ void k_wait_selftest(int *err, uint64_t limit_ns) {
 
 template <int DEG, int WK, bool FP16, int NACC, bool WSPLIT>
 void launch_one(const KParams &p, int d0, int Dc, int N, uint32_t idesc, cudaStream_t st) {
-  // all tiles, or (tile list) one slot per tile of which the listed ones work
-  const dim3 grid = p.tile_list ? dim3((unsigned)(p.tiles_x * p.tiles_y * (2 / NACC)))
+  // all tiles, or (list of half tiles) one slot per half tile of which the
+  // listed ones work
+  const dim3 grid = p.tile_list ? dim3((unsigned)(2 * p.tiles_x * p.tiles_y))
                                 : dim3(p.tiles_x, p.tiles_y * (2 / NACC));
   auto k = k_mls_tc<DEG, WK, FP16, NACC, WSPLIT>;
   const TcLayout lay = make_layout(N, Dc);
