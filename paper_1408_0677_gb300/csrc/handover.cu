@@ -453,11 +453,16 @@ __global__ __launch_bounds__(kWarps * 32, 4) void k_handover(KParams p, const in
   };
 
   for (int64_t ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
-    // chunk ch takes every nchunks-th listed pixel from ch on (nq <= csz of
-    // them).  Neighbouring list entries are often neighbouring pixels of one
-    // tile with similar costs; striding spreads the expensive ones (many near
-    // points) over the chunks, so no block is left with a run of them.
-    const int nq = (int)((npix - ch + nchunks - 1) / nchunks);
+    // Neighbouring list entries are often neighbouring pixels of one tile,
+    // with similar costs and shared near points.  With at most one chunk per
+    // block, chunk ch takes every nchunks-th entry from ch on, which spreads
+    // the expensive pixels (many near points) over the blocks.  With more
+    // chunks than blocks, the blocks balance over their several chunks, and
+    // a chunk takes a contiguous run, whose pixels share near points in cache.
+    const bool strided = nchunks <= (int64_t)gridDim.x;
+    const int64_t first = strided ? ch : ch * csz, step = strided ? nchunks : 1;
+    const int nq = strided ? (int)((npix - ch + nchunks - 1) / nchunks)
+                           : (int)((npix - first) < csz ? (npix - first) : csz);
 
     // ---- phase 1 (warp per pixel): double-float pixel-frame moments
     for (;;) {
@@ -465,7 +470,7 @@ __global__ __launch_bounds__(kWarps * 32, 4) void k_handover(KParams p, const in
       if (lane == 0) j = atomicAdd(&s_next[0], 1);
       j = __shfl_sync(0xffffffffu, j, 0);
       if (j >= nq) break;
-      const int id = list[ch + (int64_t)j * nchunks];
+      const int id = list[first + (int64_t)j * step];
       Ranges R;
       float mhat, pxh, pxl, pyh, pyl;
       setup(id, R, mhat, pxh, pxl, pyh, pyl);
@@ -561,7 +566,7 @@ __global__ __launch_bounds__(kWarps * 32, 4) void k_handover(KParams p, const in
       k = __shfl_sync(0xffffffffu, k, 0);
       if (k >= nq) break;
       const int j = s_order[k];
-      const int id = list[ch + (int64_t)j * nchunks];
+      const int id = list[first + (int64_t)j * step];
       const int flags = slots[j].flags;
       if (flags & 1) {
         if (lane == 0) {
