@@ -64,6 +64,14 @@ def test_reference_arm_under_torchrun_prints_one_line():
     d = json.loads(lines[0])
     assert d["impl"] == "reference" and d["n_gpus"] == 2 and d["value"] > 0
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["cpu_baseline"]["kind"] == "oracle"
+    # every key of the one-line contract, with its type
+    for key, typ in (("metric", str), ("value", float), ("unit", str), ("steps", int), ("warmup", int),
+                     ("ms_per_step", float), ("higher_is_better", bool), ("scaling", str), ("dtype", str),
+                     ("data", str), ("config", dict), ("cpu_baseline", dict), ("e2e", dict)):
+        assert isinstance(d[key], typ), (key, d.get(key))
+    assert "vs_baseline" in d and d["warmup"] >= 3 and d["steps"] == 1
+    assert d["e2e"]["unit"] == d["unit"] and d["cpu_baseline"]["value"] == d["value"]
+    assert "workload" in d["config"]
 
 
 def test_pairs_in_boxes_equals_the_oracle_counts():
