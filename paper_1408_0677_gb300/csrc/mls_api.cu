@@ -423,6 +423,18 @@ bad:
 
 namespace mlsi {
 
+// The device address of a page-locked host buffer registered with the
+// handle's device, or nullptr for any other memory.
+static void *mapped_host(void *ptr, int device) {
+  cudaPointerAttributes a{};
+  if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  if (a.type != cudaMemoryTypeHost || !a.devicePointer || a.device != device) return nullptr;
+  return a.devicePointer;
+}
+
 // Host-side part of a render: validation, scratch, level upload, staging;
 // fills the kernel parameters.  Everything here may allocate or synchronise,
 // so none of it runs inside a stream capture.
@@ -443,7 +455,22 @@ static mls_status render_prepare(mls_handle *h, RenderCtx *c, const mls_view *vi
   if (bands && L > 0 && (s = upload_levels(h, c, levels, L, st)) != MLS_OK) return s;
   void *field_d = field;
   uint8_t *status_d = status, *bands_d = bands;
+  c->direct_out = false;
   if (!on_device) {
+    // Page-locked host outputs are written by the kernels directly (over
+    // NVLink-C2C on GB300, overlapped with the render); other host memory is
+    // staged in device memory and copied back after the render.
+    void *fm = mapped_host(field, h->device);
+    void *sm = status ? mapped_host(status, h->device) : nullptr;
+    void *bm = bands ? mapped_host(bands, h->device) : nullptr;
+    c->direct_out = fm && (!status || sm) && (!bands || bm);
+    if (c->direct_out) {
+      field_d = fm;
+      status_d = (uint8_t *)sm;
+      bands_d = (uint8_t *)bm;
+    }
+  }
+  if (!on_device && !c->direct_out) {
     const size_t fbytes = (plane * h->desc.D * esz + 255) / 256 * 256;
     const size_t sbytes = (plane + 255) / 256 * 256;
     const size_t bbytes = bands ? plane * h->desc.D : 0;
@@ -570,9 +597,11 @@ mls_status mls_render(mls_handle *h, const mls_view *view, void *field, uint8_t 
   if (!on_device) {
     const size_t plane = (size_t)view->W * view->H;
     const size_t esz = h->desc.precision == MLS_P_FP64 ? sizeof(double) : sizeof(float);
-    MLS_CUDA_TRY(cudaMemcpyAsync(field, p.field, plane * h->desc.D * esz, cudaMemcpyDeviceToHost, st));
-    if (status) MLS_CUDA_TRY(cudaMemcpyAsync(status, p.status, plane, cudaMemcpyDeviceToHost, st));
-    if (bands) MLS_CUDA_TRY(cudaMemcpyAsync(bands, p.bands, plane * h->desc.D, cudaMemcpyDeviceToHost, st));
+    if (!h->ctx.direct_out) {
+      MLS_CUDA_TRY(cudaMemcpyAsync(field, p.field, plane * h->desc.D * esz, cudaMemcpyDeviceToHost, st));
+      if (status) MLS_CUDA_TRY(cudaMemcpyAsync(status, p.status, plane, cudaMemcpyDeviceToHost, st));
+      if (bands) MLS_CUDA_TRY(cudaMemcpyAsync(bands, p.bands, plane * h->desc.D, cudaMemcpyDeviceToHost, st));
+    }
     MLS_CUDA_TRY(cudaStreamSynchronize(st));
     int err = 0;
     MLS_CUDA_TRY(cudaMemcpy(&err, h->ctx.err, sizeof(int), cudaMemcpyDeviceToHost));

@@ -58,6 +58,7 @@ struct RenderCtx {
   size_t lev_cap = 0;
   void *stage = nullptr;             // staging for host-pointer calls
   size_t stage_bytes = 0;
+  bool direct_out = false;           // host outputs written by the kernels themselves
 };
 
 // Bytes of the scratch a W x H render needs (see ensure_scratch).

@@ -189,6 +189,27 @@ def test_host_pointer_path_matches_device_path(precision):
     assert np.array_equal(host["status"], dev["status"])
 
 
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "fp16"])
+def test_page_locked_host_outputs_match_device_path(precision):
+    """Page-locked host outputs are written by the kernels directly (no
+    staging copy); the result is the device path's, bit for bit."""
+    import torch
+
+    from paper_1408_0677_gb300 import Renderer
+    wl = inputs.small_random(24, 120, 3, 33, 27, 1, G, 0.1)
+    dev = gpu_render(wl, precision)
+    fdt = torch.float64 if precision == "fp64" else torch.float32
+    field = torch.full((wl.D, wl.H, wl.W), 7.0, dtype=fdt).pin_memory().numpy()
+    status = torch.full((wl.H, wl.W), 77, dtype=torch.uint8).pin_memory().numpy()
+    bands = torch.full((wl.D, wl.H, wl.W), 77, dtype=torch.uint8).pin_memory().numpy()
+    r = Renderer(wl.xy, wl.F, degree=1, weight=G, h=0.1, precision=precision)
+    r.render_host(wl.W, wl.H, levels=wl.levels, field=field, bands=bands, status_out=status)
+    r.close()
+    assert np.array_equal(field, dev["field"], equal_nan=True)
+    assert np.array_equal(bands, dev["bands"])
+    assert np.array_equal(status, dev["status"])
+
+
 def test_injected_nomem_leaves_handle_usable(monkeypatch):
     import torch
 
