@@ -188,7 +188,13 @@ mls_status mls_create(const mls_desc *desc, const double *xy, const double *F,
  *   L       number of levels per dimension (0..254)
  *   bands   D x H x W bytes, iso-band labels fused into the render
  *           (Section 3.4: band = #{j : t_dj <= f_d}, 255 for NaN), or NULL
- *   on_device  nonzero: field/status/bands are device pointers
+ *   on_device  nonzero: field/status/bands are device pointers, and the
+ *           call returns once the work is enqueued on `stream`.  Zero: they
+ *           are host pointers and the call returns when the results are in
+ *           them.  Page-locked host buffers registered with the handle's
+ *           device (all three of those given) are written by the kernels
+ *           directly; other host memory is staged in device memory and
+ *           copied back.
  * Precision routing: FP16/BF16 renders use the tensor-core kernel, except
  * with the inverse-distance weight (no finite support for the tile operand's
  * range clip) and when a 16-pixel tile spans more than 4 h (no moment frame
