@@ -120,6 +120,27 @@ static double norm1(int k, const double *A) {
     return best;
 }
 
+/* Relative error bound, in units of u = 2^-53, of the computed weight
+ * w_i of one pair (first order), for ecoef_fix.  r2 = |x_i - p|^2 carries
+ * at most 4 u (two differences, two squares, one sum); a common factor on
+ * every weight (the stabiliser m, its rounding included) leaves the fit
+ * unchanged, so m counts as exact.
+ *  - Gaussian exp(-(r2 - m)/h2): argument error 4 u r2/h2 from r2, u and u
+ *    of |r2 - m|/h2 from the subtraction and the quotient, 2 u for exp.
+ *  - Wendland t^4 (4q + 1), q = sqrt(r2)/h, t = 1 - q: q carries 4 u, so
+ *    t carries (4 q/t + 1) u; t^4 multiplies that by 4 and adds 3 u; the
+ *    factor 4q + 1 carries at most 5 u; the final product u.
+ *  - inverse distance (m/r2)^alpha: the quotient carries 5 u (m exact, as
+ *    above), raised to alpha; 4 u for pow. */
+static double weight_rel_error(int32_t weight, double r2, double m, double h2, double h, double alpha) {
+    if (weight == OR_GAUSS) return 2.0 + (4.0 * r2 + 2.0 * fabs(r2 - m)) / h2;
+    if (weight == OR_WENDLAND) {
+        const double qd = sqrt(r2) / h, t = 1.0 - qd;
+        return 13.0 + 16.0 * qd / t;
+    }
+    return 5.0 * alpha + 4.0;
+}
+
 /*
  * Evaluate the MLS fit for a list of pixels.
  *
@@ -144,6 +165,28 @@ static double norm1(int k, const double *A) {
  *            truncated-Gaussian point's |dx| or |dy| within a relative
  *            amb_boundary of c h) and could move the count across a k
  *            threshold.  Optional (NULL).
+ *   ecoef_sum, ecoef_fix  out, npix x D, optional (NULL): coefficients of a
+ *            first-order bound on the rounding error of an FP64 evaluation
+ *            of this pixel's value (a test aid: not part of the method).
+ *            For any implementation that forms the same weights, basis
+ *            terms and moments in this pixel frame, sums each moment in
+ *            any order whose longest chain of additions has N terms, and
+ *            solves through the explicit inverse of the equilibrated Me,
+ *              |f_computed - f_exact| <= (N + 12) u ecoef_sum + ecoef_fix
+ *            to first order in the unit roundoff u = 2^-53.  With
+ *            y = M^{-1} e_0 and c = M^{-1} R (the value is f = y^T R, and
+ *            the normal equations give df = y^T (dR - dM c)):
+ *              ecoef_sum = sum_a |y_a| (T_ad + sum_b T_ab |c_bd|),
+ *                T_ab = sum_i w_i |b_a b_b|, T_ad = sum_i w_i |b_a f_id|
+ *                (the absolute sums that bound each moment's summation
+ *                error, 12 u covering the rounding of each basis product);
+ *              ecoef_fix = the same form with every w_i multiplied by the
+ *                relative error bound of the computed weight (delta_w
+ *                below), plus the error of the Cholesky solve Me z = e_0
+ *                and the final sum: (3k+3) u s_0 g_0 sum_b |c_bd| / s_b +
+ *                (k+3) u sum_c s_0 |z_c| s_c |R_cd|, s_a = M_aa^{-1/2},
+ *                g_0 = |z|_1.
+ *            0 where the value is NaN.
  * Returns 0, or -1 on bad arguments.
  */
 int oracle_mls(int64_t n, int32_t D, const double *xy, const double *F,
@@ -153,7 +196,7 @@ int oracle_mls(int64_t n, int32_t D, const double *xy, const double *F,
                double amb_factor, double amb_boundary,
                double *field, int8_t *deg_used, double *rcond_out,
                int64_t *count_out, double *mstab_out, uint8_t *amb,
-               int32_t nthreads) {
+               double *ecoef_sum, double *ecoef_fix, int32_t nthreads) {
     if (n < 1 || D < 1 || degree < 0 || degree > 2 || !(h > 0.0) || W < 1 || H < 1)
         return -1;
     if (weight != OR_GAUSS && weight != OR_WENDLAND && weight != OR_INVDIST) return -1;
@@ -174,6 +217,11 @@ int oracle_mls(int64_t n, int32_t D, const double *xy, const double *F,
         double *r2 = (double *)malloc(sizeof(double) * (size_t)n);
         double M[36], R6[6 * 256], Me[36], L[36], Minv[36], col[6];
         double *Rbuf = (D <= 256) ? R6 : (double *)malloc(sizeof(double) * 6 * (size_t)D);
+        /* error-bound sums (ecoef_*): T, Tw (k x k), TR, TRw (k x D) */
+        const int want_err = ecoef_sum != NULL && ecoef_fix != NULL;
+        double T[36], Tw[36];
+        double *TR = want_err ? (double *)malloc(sizeof(double) * 12 * (size_t)D) : NULL;
+        double *TRw = want_err ? TR + 6 * (size_t)D : NULL;
 #ifdef _OPENMP
 #pragma omp for schedule(dynamic, 16)
 #endif
@@ -236,6 +284,8 @@ int oracle_mls(int64_t n, int32_t D, const double *xy, const double *F,
 
             int used = -1;
             double rc_used = 0.0;
+            if (want_err)
+                for (int d = 0; d < D; ++d) ecoef_sum[q * D + d] = ecoef_fix[q * D + d] = 0.0;
             if (coincident) {
                 /* inverse distance, pixel centre on a data point: mean value */
                 double sw = 0.0;
@@ -248,6 +298,11 @@ int oracle_mls(int64_t n, int32_t D, const double *xy, const double *F,
                 for (int d = 0; d < D; ++d) out[d] /= sw;
                 used = 0;
                 rc_used = 1.0;
+                /* a plain mean: the sum of |f| over the points, per point */
+                if (want_err)
+                    for (int64_t i = 0; i < n; ++i)
+                        if (wt[i] != 0.0)
+                            for (int d = 0; d < D; ++d) ecoef_sum[q * D + d] += fabs(F[i * D + d]) / sw;
             } else {
                 for (int deg = degree; deg >= 0 && used < 0; --deg) {
                     const int k = n_terms(deg);
@@ -257,6 +312,11 @@ int oracle_mls(int64_t n, int32_t D, const double *xy, const double *F,
                     if (count < k) continue;
                     memset(M, 0, sizeof(M));
                     memset(Rbuf, 0, sizeof(double) * (size_t)k * D);
+                    if (want_err) {
+                        memset(T, 0, sizeof(T));
+                        memset(Tw, 0, sizeof(Tw));
+                        memset(TR, 0, sizeof(double) * 12 * (size_t)D);
+                    }
                     for (int64_t i = 0; i < n; ++i) {
                         const double w = wt[i];
                         if (w == 0.0) continue;
@@ -267,6 +327,21 @@ int oracle_mls(int64_t n, int32_t D, const double *xy, const double *F,
                         for (int a = 0; a < k; ++a) {
                             for (int c = 0; c < k; ++c) M[a * k + c] += w * b[a] * b[c];
                             for (int d = 0; d < D; ++d) Rbuf[a * D + d] += w * b[a] * F[i * D + d];
+                        }
+                        if (want_err) {
+                            const double dw = weight_rel_error(weight, r2[i], m, h2, h, alpha) * 0x1p-53;
+                            for (int a = 0; a < k; ++a) {
+                                for (int c = 0; c < k; ++c) {
+                                    const double t = w * fabs(b[a] * b[c]);
+                                    T[a * k + c] += t;
+                                    Tw[a * k + c] += dw * t;
+                                }
+                                for (int d = 0; d < D; ++d) {
+                                    const double t = w * fabs(b[a] * F[i * D + d]);
+                                    TR[a * D + d] += t;
+                                    TRw[a * D + d] += dw * t;
+                                }
+                            }
                         }
                     }
                     /* equilibrate, factor, condition */
@@ -296,15 +371,56 @@ int oracle_mls(int64_t n, int32_t D, const double *xy, const double *F,
                         rc = 0.0;
                     }
                     if (!ok) continue;
-                    /* f_d = row 0 of M^{-1} R, M^{-1} = S Me^{-1} S */
+                    /* f_d = row 0 of M^{-1} R = z^T R with z = M^{-1} e_0,
+                     * M^{-1} = S Me^{-1} S: z is column 0 of the inverse,
+                     * the one solve Me z' = e_0 (row 0 of the computed
+                     * inverse is the same number in exact arithmetic, but
+                     * gathers the rounding of every column's solve) */
                     for (int d = 0; d < D; ++d) {
                         double acc = 0.0;
                         for (int c = 0; c < k; ++c)
-                            acc += sdiag[0] * Minv[0 * k + c] * sdiag[c] * Rbuf[c * D + d];
+                            acc += sdiag[0] * Minv[c * k + 0] * sdiag[c] * Rbuf[c * D + d];
                         out[d] = acc;
                     }
                     used = deg;
                     rc_used = rc;
+                    if (want_err) {
+                        const double u53 = 0x1p-53;
+                        double y[6], g[6];
+                        for (int a = 0; a < k; ++a) {
+                            y[a] = sdiag[a] * Minv[a * k + 0] * sdiag[0];
+                            g[a] = 0.0;
+                            for (int c = 0; c < k; ++c) g[a] += fabs(Minv[c * k + a]);
+                        }
+                        for (int d = 0; d < D; ++d) {
+                            double cb[6], es = 0.0, ef = 0.0;
+                            for (int b2 = 0; b2 < k; ++b2) {
+                                cb[b2] = 0.0;
+                                for (int c = 0; c < k; ++c)
+                                    cb[b2] += sdiag[b2] * Minv[b2 * k + c] * sdiag[c] * Rbuf[c * D + d];
+                            }
+                            for (int a = 0; a < k; ++a) {
+                                double ts = TR[a * D + d], tf = TRw[a * D + d];
+                                for (int b2 = 0; b2 < k; ++b2) {
+                                    ts += T[a * k + b2] * fabs(cb[b2]);
+                                    tf += Tw[a * k + b2] * fabs(cb[b2]);
+                                }
+                                es += fabs(y[a]) * ts;
+                                ef += fabs(y[a]) * tf;
+                            }
+                            /* the solve (Me + E) z = e_0, |E| <= (3k+3) u (Cholesky with
+                             * unit-diagonal Me, and Me's own rounding), moves the value by
+                             * s_0 z^T E Me^{-1} S R = s_0 z^T E (c_b / s_b)_b; the final
+                             * sum of k products adds (k+3) u of its absolute terms */
+                            double cs = 0.0;
+                            for (int b2 = 0; b2 < k; ++b2) cs += fabs(cb[b2]) / sdiag[b2];
+                            ef += (3.0 * k + 3.0) * u53 * sdiag[0] * g[0] * cs;
+                            for (int c = 0; c < k; ++c)
+                                ef += (k + 3.0) * u53 * sdiag[0] * fabs(Minv[c * k + 0]) * sdiag[c] * fabs(Rbuf[c * D + d]);
+                            ecoef_sum[q * D + d] = es;
+                            ecoef_fix[q * D + d] = ef;
+                        }
+                    }
                 }
                 if (used < 0)
                     for (int d = 0; d < D; ++d) out[d] = NAN;
@@ -314,6 +430,7 @@ int oracle_mls(int64_t n, int32_t D, const double *xy, const double *F,
             if (amb) amb[q] = ambq;
         }
         if (Rbuf != R6) free(Rbuf);
+        free(TR);
         free(wt);
         free(r2);
     }

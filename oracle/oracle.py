@@ -36,7 +36,7 @@ def load_library(path: str):
                                ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_int32, ctypes.c_int32,
                                ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                ctypes.c_int64, P, ctypes.c_double, ctypes.c_double, ctypes.c_double,
-                               P, P, P, P, P, P, ctypes.c_int32]
+                               P, P, P, P, P, P, P, P, ctypes.c_int32]
     lib.oracle_bands.restype = ctypes.c_int
     lib.oracle_bands.argtypes = [ctypes.c_int64, ctypes.c_int32, P, P, ctypes.c_int32, P]
     lib.oracle_mls_variant.restype = ctypes.c_int
@@ -63,6 +63,12 @@ class OracleResult:
     count: np.ndarray     # (npix,) int64
     mstab: np.ndarray     # (npix,) float64
     amb: np.ndarray       # (npix,) uint8 ambiguity bits
+    # first-order rounding-error bound coefficients of each value (npix, D),
+    # only with ebound=True: an FP64 evaluation of the same fit whose longest
+    # summation chain has N terms is within (N + 12) u ecoef_sum + ecoef_fix
+    # of the exact value (u = 2^-53; see oracle_mls in mls_oracle.c)
+    ecoef_sum: np.ndarray = None
+    ecoef_fix: np.ndarray = None
 
 
 def _p(a):
@@ -70,10 +76,12 @@ def _p(a):
 
 
 def mls(xy, F, degree, weight, h, W, H, view=(0.0, 0.0, 1.0, 1.0), pixels=None, alpha=1.0,
-        rcond_min=1e-12, amb_factor=100.0, amb_boundary=1e-6, threads=0, lib=None, trunc=0.0) -> OracleResult:
+        rcond_min=1e-12, amb_factor=100.0, amb_boundary=1e-6, threads=0, lib=None, trunc=0.0,
+        ebound=False) -> OracleResult:
     """Evaluate the FP64 MLS fit at the listed pixels (all pixels if None).
     trunc = c > 0 (Gaussian only): the truncated Gaussian, zero outside the
-    box |dx|, |dy| < c h around each pixel."""
+    box |dx|, |dy| < c h around each pixel.  ebound=True also returns the
+    rounding-error bound coefficients (OracleResult.ecoef_sum / ecoef_fix)."""
     lib = lib or _load()
     xy = np.ascontiguousarray(xy, dtype=np.float64)
     F = np.ascontiguousarray(F, dtype=np.float64)
@@ -93,14 +101,16 @@ def mls(xy, F, degree, weight, h, W, H, view=(0.0, 0.0, 1.0, 1.0), pixels=None, 
     cnt = np.empty(npix, np.int64)
     ms = np.empty(npix, np.float64)
     amb = np.empty(npix, np.uint8)
+    es = np.empty((npix, D), np.float64) if ebound else None
+    ef = np.empty((npix, D), np.float64) if ebound else None
     x0, y0, x1, y1 = view
     rcode = lib.oracle_mls(n, D, _p(xy), _p(F), degree, weight, h, alpha, float(trunc), W, H, x0, y0, x1, y1,
                            npix, _p(pix_arr) if pix_arr is not None else None, rcond_min,
                            amb_factor, amb_boundary, _p(field), _p(deg), _p(rc), _p(cnt), _p(ms),
-                           _p(amb), threads)
+                           _p(amb), _p(es) if ebound else None, _p(ef) if ebound else None, threads)
     if rcode != 0:
         raise ValueError("oracle_mls rejected its arguments")
-    return OracleResult(field, deg, rc, cnt, ms, amb)
+    return OracleResult(field, deg, rc, cnt, ms, amb, es, ef)
 
 
 def bands(field, levels, lib=None) -> np.ndarray:

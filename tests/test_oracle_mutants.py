@@ -24,7 +24,7 @@ MUTANTS = [
     ("Wendland (1-q)^3", "w = t * t * t * t * (4.0 * qd + 1.0);", "w = t * t * t * (4.0 * qd + 1.0);"),
     ("inverse distance 1/r^(4 alpha)", "w = pow(m / r2[i], alpha);", "w = pow(m / r2[i], 2.0 * alpha);"),
     ("pixel centre without the half offset", "((double)u + 0.5) * s;", "((double)u) * s;"),
-    ("fit read from the wrong coefficient", "sdiag[0] * Minv[0 * k + c]", "sdiag[k - 1] * Minv[(k - 1) * k + c]"),
+    ("fit read from the wrong coefficient", "sdiag[0] * Minv[c * k + 0]", "sdiag[k - 1] * Minv[c * k + k - 1]"),
     ("band tie counted below", "if (levels[d * L + j] <= f) c++;", "if (levels[d * L + j] < f) c++;"),
     ("value matrix read transposed", "Rbuf[a * D + d] += w * b[a] * F[i * D + d];",
      "Rbuf[a * D + d] += w * b[a] * F[d * n + i];"),
