@@ -483,7 +483,9 @@ __global__ __launch_bounds__(256) void k_mls_f64(KParams p, int64_t npix_all) {
 #pragma unroll
           for (int dd = 0; dd < DC; ++dd) {
             double acc = 0.0;
-            for (int c = 0; c < k; ++c) acc += sdg[0] * Inv[0][c] * sdg[c] * R[c][dd];
+            // z = column 0 of the inverse (the one solve Me z = e_0): its
+            // rounding grows with the condition once, not with its square
+            for (int c = 0; c < k; ++c) acc += sdg[0] * Inv[c][0] * sdg[c] * R[c][dd];
             out[dd] = acc;
           }
           used = deg;

@@ -166,6 +166,55 @@ def fourier_mix(seed: int, n: int, D: int, W: int, H: int, degree: int, weight: 
     return w
 
 
+def heldout(seed: int) -> tuple:
+    """A randomly shaped case drawn from a wider family than the workloads
+    above, for parity checks on inputs that no threshold was tuned on.
+
+    Gaussian (two thirds) or Wendland weight; 3-16 clusters (sigma
+    U(0.01, 0.06)) plus 0-30% uniform points; n log-uniform in 2k-40k
+    (Gaussian) or 20k-150k (Wendland); D uniform in 3-40; linear or quadratic
+    basis; h U(0.012, 0.035) (Gaussian) or radius U(0.01, 0.03); fields with
+    3-12 modes of integer frequency up to between 2 and 1/(6 h) (wavelength
+    at least 6 h); a zoom window of side log-uniform in [1/16, 1] at a random
+    place in [0,1]^2, with pixels of 0.08-0.3 h (at most 1024 columns) and a
+    height of 0.6-1 times the width; 8-20 iso-levels.
+
+    Returns (workload, sampled pixel indices): 2048 random pixels plus one
+    dense 24 x 24 window."""
+    rng = np.random.default_rng(seed)
+    gauss = rng.random() < 2.0 / 3.0
+    if gauss:
+        n = int(round(np.exp(rng.uniform(np.log(2000), np.log(40000)))))
+        h = float(rng.uniform(0.012, 0.035))
+    else:
+        n = int(round(np.exp(rng.uniform(np.log(20000), np.log(150000)))))
+        h = float(rng.uniform(0.01, 0.03))
+    D = int(rng.integers(3, 41))
+    degree = int(rng.integers(1, 3))
+    k = int(rng.integers(3, 17))
+    n_uni = int(n * rng.uniform(0.0, 0.3))
+    centres = rng.uniform(0.1, 0.9, size=(k, 2))
+    sig = rng.uniform(0.01, 0.06, size=k)
+    xy = np.concatenate([_clusters(rng, n - n_uni, centres, sig),
+                         rng.uniform(0.0, 1.0, size=(n_uni, 2))], axis=0)
+    xy = xy[rng.permutation(n)]
+    modes = int(rng.integers(3, 13))
+    max_freq = int(rng.integers(2, max(3, int(1.0 / (6.0 * h))) + 1))
+    F = _fourier_fields(rng, xy, D, modes=modes, max_freq=max_freq)
+    side = float(np.exp(rng.uniform(np.log(1.0 / 16.0), 0.0)))
+    x0, y0 = rng.uniform(0.0, 1.0 - side, size=2)
+    W = int(min(1024, max(64, np.ceil(side / (h * rng.uniform(0.08, 0.3))))))
+    H = int(max(32, round(W * rng.uniform(0.6, 1.0))))
+    view = (float(x0), float(y0), float(x0 + side), float(y0 + side * H / W))
+    wt = WEIGHT_GAUSS if gauss else WEIGHT_WENDLAND
+    w = Workload(f"heldout{seed}_n{n}_d{D}_{W}x{H}_deg{degree}_w{wt}", xy, F, degree, wt, h, W, H, view=view)
+    w.levels = default_levels(F, int(rng.integers(8, 21)))
+    pix = sample_pixels(seed, W, H, 2048)
+    u0, v0 = int(rng.integers(0, W - 24)), int(rng.integers(0, H - 24))
+    win = np.array([(v0 + dv) * W + u0 + du for dv in range(24) for du in range(24)], np.int64)
+    return w, np.unique(np.concatenate([pix, win]))
+
+
 def batch_datasets(seed: int = 1004, count: int = 64, n_range=(200, 50_000), D_range=(4, 64),
                    side_range=(256, 1024)) -> list:
     """Independent datasets for batched rendering: n log-uniform in n_range,

@@ -7,7 +7,7 @@ import pytest
 
 import oracle
 from paper_1408_0677_gb300 import inputs
-from tests.gpu_util import compare
+from tests.gpu_util import compare, oracle_ref
 
 pytestmark = pytest.mark.gpu
 
@@ -82,7 +82,7 @@ def test_batch_with_autotune_matches_oracle(built):
     b.sync()
     for w, pr, o in zip(wls, PRECS, outs):
         pix = inputs.sample_pixels(5, w.W, w.H, 300)
-        ref = oracle.mls(w.xy, w.F, w.degree, w.weight, w.h, w.W, w.H, pixels=pix)
+        ref = oracle_ref(w, pix)
         res = {k: (v.cpu().numpy() if v is not None else None) for k, v in o.items()}
         compare(w, res, ref, pr, pixels=pix)
     b.close()

@@ -11,7 +11,7 @@ import pytest
 
 import oracle
 from paper_1408_0677_gb300 import inputs
-from tests.gpu_util import compare, gpu_render
+from tests.gpu_util import compare, gpu_render, oracle_ref
 
 pytestmark = pytest.mark.gpu
 
@@ -26,8 +26,7 @@ def built():
 
 
 def _ref(wl, pixels=None):
-    return oracle.mls(wl.xy, wl.F, wl.degree, wl.weight, wl.h, wl.W, wl.H, view=wl.view, pixels=pixels,
-                      alpha=wl.alpha, trunc=wl.trunc)
+    return oracle_ref(wl, pixels)
 
 
 @pytest.mark.parametrize("precision", ALL_PREC)
