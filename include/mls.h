@@ -39,7 +39,7 @@
 extern "C" {
 #endif
 
-#define MLS_ABI_VERSION 3
+#define MLS_ABI_VERSION 4
 
 typedef enum mls_status {
     MLS_OK = 0,
@@ -155,7 +155,18 @@ typedef struct mls_stats {
                                  same stream (weight_split 2: the single-weight pass only) */
     int64_t retried_tiles;    /* half tiles (16 x 8 pixels) rendered again with split weights
                                  (weight_split 2) */
+    int32_t main_path;        /* kernel family of the last render's main pass (MLS_PATH_*) */
+    int32_t reserved;
 } mls_stats;
+
+/* mls_stats.main_path: which kernels computed the moments of the last render. */
+enum {
+    MLS_PATH_NONE = 0,        /* no render yet */
+    MLS_PATH_TENSOR = 1,      /* tcgen05 tensor-core kernel (FP16/BF16 operands, FP32 accumulators) */
+    MLS_PATH_FP32 = 2,        /* FP32 CUDA-core kernel (FP32 renders, wide tiles, inverse distance) */
+    MLS_PATH_FP64 = 3,        /* FP64 kernel (FP64 renders) */
+    MLS_PATH_VARIANT = 4      /* rigid / mean-displacement mapping kernel */
+};
 
 typedef struct mls_handle mls_handle;
 
@@ -358,8 +369,11 @@ mls_status mls_server_destroy(mls_server *s);
  * on the device), so make the first call before any stream capture.  Every
  * call on a device shares the array and leaves its levels there; calls whose
  * work overlaps on the GPU race on it, so order them on one stream.  Nothing
- * in the array needs to start at zero.  The host levels may be reused when
- * the call returns; the labels are ready when the stream reaches them.
+ * in the array needs to start at zero.  Pageable host levels (ordinary
+ * malloc or numpy memory) have been copied when the call returns and may be
+ * reused at once; page-locked levels are read when the stream reaches the
+ * copy, so keep them unchanged until then.  The labels are ready when the
+ * stream reaches them.
  * Nothing is allocated: no cudaMalloc, cudaFree or allocating library call.
  * Errors: MLS_E_INVAL (bad sizes, D * L above the maximum, NULL pointers,
  * levels not ascending or not finite), MLS_E_UNSUPPORTED (device ordinal

@@ -65,6 +65,31 @@ def space_map(field, levels, dims, mode, line_width=1.0, fade=(2.0, 6.0, 3), lo=
     return out
 
 
+def _check_host_out(name, a, shape, dtype):
+    """A caller-supplied host output: a C-contiguous numpy array of exactly
+    this shape and type, or None."""
+    if a is None:
+        return
+    if not isinstance(a, np.ndarray):
+        raise ValueError(f"{name} must be a numpy array")
+    if a.shape != tuple(shape) or a.dtype != np.dtype(dtype) or not a.flags["C_CONTIGUOUS"] \
+            or not a.flags["WRITEABLE"]:
+        raise ValueError(f"{name} must be a writeable C-contiguous {np.dtype(dtype).name} array of shape "
+                         f"{tuple(shape)}, got {a.dtype.name} {a.shape}"
+                         f"{'' if a.flags['C_CONTIGUOUS'] else ' (not contiguous)'}")
+
+
+def _check_dev_out(name, t, shape, dtype):
+    """A caller-supplied device output: a contiguous CUDA tensor of exactly
+    this shape and type, or None."""
+    if t is None:
+        return
+    if not getattr(t, "is_cuda", False) or tuple(t.shape) != tuple(shape) or t.dtype != dtype \
+            or not t.is_contiguous():
+        raise ValueError(f"{name} must be a contiguous CUDA tensor of {dtype} and shape {tuple(shape)}, "
+                         f"got {getattr(t, 'dtype', type(t))} {tuple(getattr(t, 'shape', ()))}")
+
+
 class Renderer:
     """A resident point set and its MLS description (one ``mls_handle``).
 
@@ -120,6 +145,9 @@ class Renderer:
                status_out=None):
         torch = self.torch
         dev = torch.device("cuda", torch.cuda.current_device())
+        _check_dev_out("field", field, (self.D, H, W), self.field_dtype)
+        _check_dev_out("status_out", status_out, (H, W), torch.uint8)
+        _check_dev_out("bands", bands, (self.D, H, W), torch.uint8)
         if field is None:
             field = torch.empty((self.D, H, W), dtype=self.field_dtype, device=dev)
         st = status_out
@@ -140,8 +168,14 @@ class Renderer:
 
     def render_host(self, W, H, view=(0.0, 0.0, 1.0, 1.0), levels=None, status=True, field=None, bands=None,
                     status_out=None):
-        """Same as render, with host (numpy) outputs; returns after the copy-back."""
+        """Same as render, with host (numpy) outputs; returns after the copy-back.
+        Supplied outputs must be C-contiguous numpy arrays of exactly the
+        rendered shape and type (the library writes page-locked ones from the
+        kernels and cannot check them itself)."""
         dt = np.float64 if self.desc.precision == MLS_P_FP64 else np.float32
+        _check_host_out("field", field, (self.D, H, W), dt)
+        _check_host_out("status_out", status_out, (H, W), np.uint8)
+        _check_host_out("bands", bands, (self.D, H, W), np.uint8)
         if field is None:
             field = np.empty((self.D, H, W), dtype=dt)
         st = status_out if status_out is not None else (np.empty((H, W), np.uint8) if status else None)

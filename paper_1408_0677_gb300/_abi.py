@@ -42,7 +42,11 @@ class MlsView(ctypes.Structure):
 class MlsStats(ctypes.Structure):
     _fields_ = [("pairs", ctypes.c_int64), ("recomputed", ctypes.c_int64), ("recomputed_fp64", ctypes.c_int64),
                 ("device_error", ctypes.c_int64), ("launches", ctypes.c_int64), ("last_render_ms", ctypes.c_double),
-                ("main_kernel_ms", ctypes.c_double), ("retried_tiles", ctypes.c_int64)]
+                ("main_kernel_ms", ctypes.c_double), ("retried_tiles", ctypes.c_int64),
+                ("main_path", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+MLS_PATH_NONE, MLS_PATH_TENSOR, MLS_PATH_FP32, MLS_PATH_FP64, MLS_PATH_VARIANT = 0, 1, 2, 3, 4
 
 
 class MlsBatchStats(ctypes.Structure):

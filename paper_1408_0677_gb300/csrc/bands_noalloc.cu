@@ -84,7 +84,8 @@ mls_status mls_bands_noalloc(int32_t D, int32_t W, int32_t H, const void *field,
   double *lev64 = (double *)base;
   float *lev32 = (float *)((unsigned char *)base + (size_t)MLS_NOALLOC_MAX_LEVELS * sizeof(double));
   cudaStream_t st = (cudaStream_t)stream;
-  // pageable source: the copy has taken the levels when the call returns
+  // from pageable memory the copy has taken the levels when the call
+  // returns; page-locked levels are read when the stream reaches the copy
   MLS_CUDA_TRY(cudaMemcpyAsync(lev64, levels, sizeof(double) * cnt, cudaMemcpyHostToDevice, st));
   k_levels_round_up<<<(cnt + 255) / 256, 256, 0, st>>>(lev64, lev32, cnt);
   MLS_CUDA_TRY(cudaGetLastError());

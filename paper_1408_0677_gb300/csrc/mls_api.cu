@@ -423,15 +423,28 @@ bad:
 
 namespace mlsi {
 
-// The device address of a page-locked host buffer registered with the
-// handle's device, or nullptr for any other memory.
-static void *mapped_host(void *ptr, int device) {
-  cudaPointerAttributes a{};
+// The device address of a page-locked host buffer of `bytes` bytes registered
+// with the handle's device, or nullptr for any other memory.  Both the first
+// and the last byte must be page-locked for this device, and the last byte's
+// device address must lie bytes - 1 past the first's (one mapped range): a
+// buffer that runs past the end of its page-locked block is staged instead,
+// so the kernels never write outside a mapped range.
+static void *mapped_host(void *ptr, size_t bytes, int device) {
+  if (!ptr || bytes == 0) return nullptr;
+  cudaPointerAttributes a{}, e{};
   if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) {
     cudaGetLastError();
     return nullptr;
   }
   if (a.type != cudaMemoryTypeHost || !a.devicePointer || a.device != device) return nullptr;
+  const char *last = (const char *)ptr + (bytes - 1);
+  if (cudaPointerGetAttributes(&e, last) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  if (e.type != cudaMemoryTypeHost || e.device != device ||
+      (const char *)e.devicePointer != (const char *)a.devicePointer + (bytes - 1))
+    return nullptr;
   return a.devicePointer;
 }
 
@@ -460,9 +473,9 @@ static mls_status render_prepare(mls_handle *h, RenderCtx *c, const mls_view *vi
     // Page-locked host outputs are written by the kernels directly (over
     // NVLink-C2C on GB300, overlapped with the render); other host memory is
     // staged in device memory and copied back after the render.
-    void *fm = mapped_host(field, h->device);
-    void *sm = status ? mapped_host(status, h->device) : nullptr;
-    void *bm = bands ? mapped_host(bands, h->device) : nullptr;
+    void *fm = mapped_host(field, plane * h->desc.D * esz, h->device);
+    void *sm = status ? mapped_host(status, plane, h->device) : nullptr;
+    void *bm = bands ? mapped_host(bands, plane * h->desc.D, h->device) : nullptr;
     c->direct_out = fm && (!status || sm) && (!bands || bm);
     if (c->direct_out) {
       field_d = fm;
@@ -507,8 +520,10 @@ static mls_status render_enqueue(mls_handle *h, RenderCtx *c, const mlsk::KParam
     launch_variant(p, fp64, st);
     if (timing) MLS_CUDA_TRY(cudaEventRecord(h->evk1, st));
     launches += 1;
+    h->last_path = MLS_PATH_VARIANT;
   } else if (fp64) {
     if (timing) MLS_CUDA_TRY(cudaEventRecord(h->evk0, st));
+    h->last_path = MLS_PATH_FP64;
     launch_f64(p, (int64_t)plane, st);
     if (timing) MLS_CUDA_TRY(cudaEventRecord(h->evk1, st));
     launches += 1;
@@ -526,12 +541,14 @@ static mls_status render_enqueue(mls_handle *h, RenderCtx *c, const mlsk::KParam
       pf.visited = c->visited;
       pf.pixel_frame = tile_h > kTileFrameMaxH ? 1 : 0;
       pf.lambda_max = 1000.f;
+      h->last_path = MLS_PATH_FP32;
       launch_f32(pf, st);
       launches += 2;
       if (timing) MLS_CUDA_TRY(cudaEventRecord(h->evk1, st));
     } else {
       const bool fp16 = h->desc.precision == MLS_P_FP16;
       int nl = 0;
+      h->last_path = MLS_PATH_TENSOR;
       if (h->desc.weight_split == 2) {
         // single weights everywhere; the 8-row halves of tiles with a
         // failing pixel are queued and rendered again with split weights
@@ -680,6 +697,7 @@ mls_status mls_sync(mls_handle *h, double timeout_s, mls_stats *stats) {
     if (h->timed && cudaEventElapsedTime(&ms, h->ev0, h->ev1) == cudaSuccess) stats->last_render_ms = ms;
     if (h->timed && cudaEventElapsedTime(&ms, h->evk0, h->evk1) == cudaSuccess) stats->main_kernel_ms = ms;
     stats->launches = h->launches;
+    stats->main_path = h->last_path;
     cudaGetLastError();
   }
   if (err) return fail(MLS_E_TIMEOUT, "a bounded device wait gave up (error word " + std::to_string(err) + ")");

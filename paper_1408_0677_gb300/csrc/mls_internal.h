@@ -76,6 +76,7 @@ struct mls_handle {
   cudaEvent_t ev0 = nullptr, ev1 = nullptr, evk0 = nullptr, evk1 = nullptr;
   int64_t launches = 0;              // kernels launched by this handle
   int64_t last_pairs = 0;
+  int32_t last_path = 0;   // MLS_PATH_* of the last render's main pass
   bool timed = false;
   bool operand_cut = true;           // reduced-precision Gaussian: skip pairs whose weight rounds to zero
 };

@@ -69,7 +69,7 @@ int main(void) {
 
 
 def test_abi_version_and_defaults(lib):
-    assert _abi.mls_abi_version() == 3
+    assert _abi.mls_abi_version() == 4
     d = _abi.mls_desc_default()
     assert d.cond_fp64 == 1e6 and d.rcond_degenerate == 1e-12 and d.precision == _abi.MLS_P_FP32
     assert d.variant == _abi.MLS_V_POLY and d.support == 0.0
@@ -173,3 +173,23 @@ def test_space_map_rejects_bad_arguments_before_any_launch(lib, kw, D, L, levels
     with pytest.raises(_abi.MlsError) as e:
         _abi.mls_space_map(d, D, 4, 4, ctypes.addressof(buf), False, lev.ctypes.data, L, ctypes.addressof(buf))
     assert e.value.status == _abi.MLS_E_INVAL
+
+
+def test_host_outputs_are_checked_before_the_call():
+    """render_host refuses caller-supplied outputs of the wrong shape, type or
+    layout before anything reaches the library (page-locked outputs are
+    written by the kernels, which cannot check them)."""
+    import numpy as np
+
+    from paper_1408_0677_gb300 import _check_host_out
+    _check_host_out("field", None, (2, 3, 4), np.float32)
+    _check_host_out("field", np.zeros((2, 3, 4), np.float32), (2, 3, 4), np.float32)
+    bad = [np.zeros((2, 3, 5), np.float32), np.zeros((2, 3, 4), np.float64), np.zeros((2, 4, 3), np.float32).T,
+           np.zeros((2, 3, 8), np.float32)[:, :, ::2], [[0.0]]]
+    for a in bad:
+        with pytest.raises(ValueError):
+            _check_host_out("field", a, (2, 3, 4), np.float32)
+    ro = np.zeros((3, 4), np.uint8)
+    ro.flags.writeable = False
+    with pytest.raises(ValueError):
+        _check_host_out("status_out", ro, (3, 4), np.uint8)
