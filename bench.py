@@ -151,6 +151,52 @@ def pairs_in_boxes(wl):
     return int(np.sum(nu * nv))
 
 
+def pairs_in_discs(wl):
+    """Pixel-point pairs with |x_i - p| < rho (the Wendland support, rho =
+    wl.h): per point and pixel row, the run of pixel columns whose centres
+    lie inside the disc, its ends settled with the FP64 pixel-centre
+    expression and r^2 < rho^2 (the support test of the definition)."""
+    rho = wl.h
+    rho2 = rho * rho
+    x0, y0, x1, y1 = wl.view
+    sx, sy = (x1 - x0) / wl.W, (y1 - y0) / wl.H
+    X, Y = wl.xy[:, 0], wl.xy[:, 1]
+    va = np.clip(np.ceil((Y - rho - y0) / sy - 0.5).astype(np.int64) - 1, 0, wl.H - 1)
+    vb = np.clip(np.floor((Y + rho - y0) / sy - 0.5).astype(np.int64) + 1, 0, wl.H - 1)
+    total = 0
+    for k in range(int((vb - va).max()) + 1 if len(X) else 0):
+        v = va + k
+        dy = Y - (y0 + (v + 0.5) * sy)
+        dy2 = dy * dy
+        live = (v <= vb) & (dy2 < rho2)
+        half = np.sqrt(np.maximum(rho2 - dy2, 0.0))
+
+        def inside(u):
+            dx = X - (x0 + (u + 0.5) * sx)
+            return (u >= 0) & (u < wl.W) & (dx * dx + dy2 < rho2)
+        a = np.clip(np.ceil((X - half - x0) / sx - 0.5).astype(np.int64), 0, wl.W - 1)
+        b = np.clip(np.floor((X + half - x0) / sx - 0.5).astype(np.int64), 0, wl.W - 1)
+        for _ in range(2):      # the rounded ends are off by at most one column
+            a = np.where(inside(a - 1), a - 1, a)
+            a = np.where(~inside(a) & (a <= b), a + 1, a)
+            b = np.where(inside(b + 1), b + 1, b)
+            b = np.where(~inside(b) & (b >= a), b - 1, b)
+        total += int(np.sum(np.where(live & inside(a) & inside(b), b - a + 1, 0)))
+    return total
+
+
+def workload_pairs(wl):
+    """The pixel-point pairs the method must visit (the metric's work):
+    W * H * n for the full-sum Gaussian, the pairs in support for the
+    Wendland weight and the truncated Gaussian's boxes."""
+    from paper_1408_0677_gb300 import inputs
+    if wl.weight == inputs.WEIGHT_WENDLAND:
+        return pairs_in_discs(wl)
+    if wl.trunc > 0:
+        return pairs_in_boxes(wl)
+    return wl.W * wl.H * wl.n
+
+
 def cpu_baseline(wl, seconds=15.0):
     """FP64 oracle on a bounded pixel sample (all host cores).  Also returns the
     last sample's pixels and oracle result, against which the GPU fields'
@@ -169,14 +215,16 @@ def cpu_baseline(wl, seconds=15.0):
         dt = time.perf_counter() - t0
         t_used += dt
         px_done += npx
-        pairs_done += int(res.count.sum()) if wl.trunc > 0 else npx * wl.n
+        pairs_done += int(res.count.sum()) if (wl.trunc > 0 or wl.weight == 1) else npx * wl.n
         last = (pix, res)
         seed += 1
         if dt < seconds / 4:
             npx *= 2
     value = pairs_done * wl.D / t_used
-    what = (f"full n={wl.n} sum each" if wl.trunc == 0 else
-            f"pairs in the box of half-width {wl.trunc} h counted (the oracle visits all n={wl.n})")
+    what = (f"pairs in the box of half-width {wl.trunc} h counted (the oracle visits all n={wl.n})"
+            if wl.trunc > 0 else
+            f"pairs within the support radius counted (the oracle visits all n={wl.n})" if wl.weight == 1 else
+            f"full n={wl.n} sum each")
     return {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
             "sample": f"{px_done} random pixels of the workload, {what}, FP64, {t_used:.1f} s"}, last
 
@@ -204,26 +252,35 @@ def run_reference(args):
         return
     from paper_1408_0677_gb300 import inputs
     import oracle
-    wl = inputs.fourier_10k()
+    cfg_name, gen, _ = WORKLOADS.get(args.workload, WORKLOADS["fourier10k"])
+    wl = getattr(inputs, gen)()
+    if args.support > 0:
+        wl = dataclasses.replace(wl, trunc=args.support)
+    counted = wl.trunc > 0 or wl.weight == inputs.WEIGHT_WENDLAND
     threads = os.cpu_count() or 1
-    npx = 256
+    npx = 256 if not counted else 4096
     pix = np.random.default_rng(7).choice(wl.W * wl.H, size=npx, replace=False)
     for _ in range(args.warmup):
-        oracle.mls(wl.xy, wl.F, wl.degree, wl.weight, wl.h, wl.W, wl.H, pixels=pix[:16], threads=threads)
-    times = []
+        oracle.mls(wl.xy, wl.F, wl.degree, wl.weight, wl.h, wl.W, wl.H, pixels=pix[:16], threads=threads,
+                   trunc=wl.trunc)
+    times, pairs = [], 0
     for k in range(args.steps):
         p = np.random.default_rng(1000 + k).choice(wl.W * wl.H, size=npx, replace=False)
         t0 = time.perf_counter()
-        oracle.mls(wl.xy, wl.F, wl.degree, wl.weight, wl.h, wl.W, wl.H, pixels=p, threads=threads)
+        res = oracle.mls(wl.xy, wl.F, wl.degree, wl.weight, wl.h, wl.W, wl.H, pixels=p, threads=threads,
+                         trunc=wl.trunc)
         times.append(time.perf_counter() - t0)
+        pairs += int(res.count.sum()) if counted else npx * wl.n
     t = float(np.sum(times))
-    value = args.steps * npx * wl.n * wl.D / t
+    value = pairs * wl.D / t
+    what = "pairs in support counted" if counted else f"full sum over n={wl.n}"
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": WORKLOAD, "sample_pixels_per_step": npx},
+            "data": "synthetic", "config": {"workload": cfg_name if wl.trunc == 0 else cfg_name + f"_trunc{wl.trunc:g}",
+                                            "sample_pixels_per_step": npx},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
-                             "sample": f"{npx} random pixels per step (full sum over n={wl.n})"},
+                             "sample": f"{npx} random pixels per step ({what})"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -236,13 +293,13 @@ def tc_source_hash():
     return h.hexdigest()
 
 
-def _traffic(n_launch_units):
+def _traffic(n_launch_units, profile=PROFILE):
     """DRAM bytes per launch from the committed ncu summary of the kernel
     (lines 'source_sha256: ...', 'dram_bytes_per_launch: ...',
     'pixels_per_launch: ...'), or None when the kernel changed since."""
     try:
         kv = {}
-        for ln in open(PROFILE):
+        for ln in open(profile):
             if ":" in ln and not ln.startswith("|"):
                 k, v = ln.split(":", 1)
                 kv[k.strip("-* `").lower()] = v.strip(" `\n")
@@ -251,6 +308,65 @@ def _traffic(n_launch_units):
         return float(kv["dram_bytes_per_launch"]) / float(kv["pixels_per_launch"]) * n_launch_units
     except Exception:
         return None
+
+
+# the configurations timed by run_ours: (config name, input generator, default precision)
+WORKLOADS = {
+    "fourier10k": (WORKLOAD, "fourier_10k", "fp16"),
+    "clusters200k": ("clusters_n200k_d64_2048x2048_quadratic_wendland_r0.015_L16", "clusters_200k", "fp16"),
+    "wine": ("wine_shaped_n178_d13_256x256_linear_gauss_h0.05_L10", "wine_shaped", "fp64"),
+}
+FP32_FMA_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12     # 152 SMs x 128 FP32 lanes x FMA x 2.07 GHz
+FP64_NOMINAL_TFLOPS = 1.25                          # GB300 FP64, nominal
+
+
+def _error_sample(wl, name):
+    """Pixels on which the GPU fields are compared with the oracle: the
+    cpu_baseline leg's last sample, or for the 200k-point workload 2^16
+    random pixels plus two full 128 x 128 windows, one in the densest
+    cluster core and one in the sparsest populated region."""
+    if name != "clusters200k":
+        return None
+    rng = np.random.default_rng(2026)
+    pix = rng.choice(wl.W * wl.H, size=1 << 16, replace=False)
+    cnt = np.zeros((wl.H // 128, wl.W // 128), np.int64)
+    bx = np.clip((wl.xy[:, 0] * wl.W).astype(np.int64) // 128, 0, cnt.shape[1] - 1)
+    by = np.clip((wl.xy[:, 1] * wl.H).astype(np.int64) // 128, 0, cnt.shape[0] - 1)
+    np.add.at(cnt, (by, bx), 1)
+    dense = np.unravel_index(np.argmax(cnt), cnt.shape)
+    sparse = np.unravel_index(np.argmin(np.where(cnt > 0, cnt, cnt.max() + 1)), cnt.shape)
+    wins = []
+    for (ty, tx) in (dense, sparse):
+        v, u = np.meshgrid(np.arange(128) + ty * 128, np.arange(128) + tx * 128, indexing="ij")
+        wins.append((v * wl.W + u).ravel())
+    return np.unique(np.concatenate([pix] + wins)).astype(np.int64)
+
+
+def _err_detail(wl, fields, pix, res, precision):
+    """Largest |f - f_oracle| / range per field; for FP64 also over the
+    pixels whose first-order rounding bound (both sides) stays within 1e-10,
+    how many pixels exceed that, and the largest error / bound."""
+    S = wl.F.max(axis=0) - wl.F.min(axis=0)
+    S = np.where(S > 0, S, 1.0)
+    ok = res.amb == 0
+    ref = res.field[ok].T
+    fin = np.isfinite(ref)
+    out = {"pixels": int(ok.sum())}
+    for nm, f in fields.items():
+        d = np.where(fin, np.abs(f[:, ok] - ref) / S[:, None], 0.0)
+        out[nm] = float(d.max()) if d.size else None
+        if nm == "fp64" and res.ecoef_sum is not None:
+            u = 2.0 ** -53
+            cnt = res.count[ok].astype(np.float64)[None, :]
+            es, ef = res.ecoef_sum[ok].T, res.ecoef_fix[ok].T
+            chain_gpu = np.minimum(cnt, np.ceil(wl.n / 32.0)) + 5
+            b = ((cnt + 12 + chain_gpu + 12) * u * es + 2 * ef) / S[:, None]
+            b = np.where(fin, b, 0.0)
+            wide = (b > 1e-10).any(axis=0)
+            out["fp64_well_conditioned"] = float(d[:, ~wide].max()) if (~wide).any() else None
+            out["fp64_pixels_beyond_1e-10_bound"] = int(wide.sum())
+            out["fp64_max_err_over_bound"] = float((d / np.maximum(b, 1e-10)).max()) if d.size else None
+    return out
 
 
 def run_ours(args):
@@ -262,10 +378,13 @@ def run_ours(args):
     from paper_1408_0677_gb300 import MLS_P_FP64, MlsView, Renderer, inputs, mls_create, mls_desc_default  # noqa
     from paper_1408_0677_gb300 import _abi
 
-    wl = inputs.fourier_10k()
+    cfg_name, gen, _ = WORKLOADS[args.workload]
+    wl = getattr(inputs, gen)()
     if args.support > 0:
         wl = dataclasses.replace(wl, trunc=args.support)
     n, D, W, H, L = wl.n, wl.D, wl.W, wl.H, wl.levels.shape[1]
+    k_terms = (wl.degree + 1) * (wl.degree + 2) // 2
+    n_mono = (2 * wl.degree + 1) * (2 * wl.degree + 2) // 2
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
     sptr = stream.cuda_stream
@@ -300,6 +419,7 @@ def run_ours(args):
     torch.cuda.synchronize()
     total_ms, kern_ms, step_ms, launches, handed, handed64, retried = 0.0, [], [], 0, 0, 0, 0
     visited = []
+    path = 0
     for _ in range(args.steps):
         flush.fill_(1.0)                                  # L2 flush outside the timed step
         e0 = torch.cuda.Event(enable_timing=True)
@@ -315,6 +435,7 @@ def run_ours(args):
         visited.append(st.pairs)
         launches += st.launches
         handed, handed64, retried = st.recomputed, st.recomputed_fp64, st.retried_tiles
+        path = st.main_path
         r.close()
     torch.cuda.synchronize()
     if world > 1:
@@ -322,7 +443,7 @@ def run_ours(args):
     clocks = sampler.stop()
     total_ms = max_over_ranks(total_ms, world, dev)
     ms_step = total_ms / args.steps
-    pairs = W * H * n if wl.trunc == 0 else pairs_in_boxes(wl)
+    pairs = workload_pairs(wl)
     units = pairs * D
     value = world * units / (ms_step * 1e-3)
 
@@ -395,34 +516,61 @@ def run_ours(args):
         return
     peaks, src = _peaks()
     k_ms = float(np.mean(kern_ms))
-    # algorithmic contraction flops of the pairs the kernel visits: the full
-    # sum skips, per tile, the points whose weight rounds to zero in the
-    # 16-bit operand (their products are exactly zero); the truncated
-    # Gaussian counts the pairs inside the boxes
+    # algorithmic contraction flops of the pairs the main kernel visits
+    # (2 (k D + monomials) per pair): the full sum skips, per tile, the points
+    # whose weight rounds to zero in the 16-bit operand (their products are
+    # exactly zero); compact supports count the pairs in support
     pairs_visited = float(np.mean(visited)) if visited else float(pairs)
-    flops = 2.0 * (6 * D + 15) * (pairs if wl.trunc > 0 else min(pairs_visited, pairs))
+    flop_pair = 2.0 * (k_terms * D + n_mono)
+    flops = flop_pair * (pairs if (wl.trunc > 0 or wl.weight == inputs.WEIGHT_WENDLAND)
+                         else min(pairs_visited, pairs))
     achieved = flops / (k_ms * 1e-3) / 1e12
-    peak = peaks.get("bf16_tflops", 1900.0)       # FP16 and BF16 share the dense tensor rate
-    roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-            "traffic": _traffic(W * H) if wl.trunc == 0 else None,
-            "peak_source": f"{src} bf16 burst (fp16 dense rate equal)",
-            "kernel": "k_mls_tc", "kernel_ms": k_ms, "flops_per_launch": flops}
+    if path == _abi.MLS_PATH_TENSOR:
+        peak = peaks.get("bf16_tflops", 1900.0)       # FP16 and BF16 share the dense tensor rate
+        roof = {"bound": "tensor", "peak_source": f"{src} bf16 burst (fp16 dense rate equal)", "kernel": "k_mls_tc"}
+    elif path == _abi.MLS_PATH_FP64:
+        peak = FP64_NOMINAL_TFLOPS
+        roof = {"bound": "alu", "peak_source": "nominal GB300 FP64 rate", "kernel": "k_mls_f64"}
+    else:
+        peak = FP32_FMA_TFLOPS
+        roof = {"bound": "alu", "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz", "kernel": "k_mls_f32"}
+    prof = os.path.join(ROOT, "profiles", f"k_mls_tc_{args.workload}_{args.precision}.md")
+    roof.update({"achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                 "traffic": (_traffic(W * H, prof) if (path == _abi.MLS_PATH_TENSOR and wl.trunc == 0) else None),
+                 "kernel_ms": k_ms, "flops_per_launch": flops, "flops_per_pair": flop_pair})
     cpu, err = None, None
     if args.cpu_seconds > 0:
         cpu, last = cpu_baseline(wl, seconds=args.cpu_seconds)
-        pix_t = torch.from_numpy(last[0]).to(dev)
+        import oracle
+        pix = _error_sample(wl, args.workload)
+        if pix is None and args.workload == "wine":
+            pix = np.arange(W * H, dtype=np.int64)      # every pixel of the 256 x 256 grid
+        if pix is None:
+            pix, res = last
+            if args.precision == "fp64":
+                res = oracle.mls(wl.xy, wl.F, wl.degree, wl.weight, wl.h, W, H, pixels=pix, trunc=wl.trunc,
+                                 threads=os.cpu_count() or 1, ebound=True)
+        else:
+            res = oracle.mls(wl.xy, wl.F, wl.degree, wl.weight, wl.h, W, H, pixels=pix, trunc=wl.trunc,
+                             threads=os.cpu_count() or 1, ebound=args.precision == "fp64")
+        pix_t = torch.from_numpy(np.asarray(pix, np.int64)).to(dev)
         fs = {k: v.reshape(D, -1)[:, pix_t].double().cpu().numpy() for k, v in samples.items()}
-        err = _err_vs_oracle(wl, fs, last)
+        err = _err_detail(wl, fs, pix, res, args.precision)
+        err["sample"] = ("2^16 random pixels + 128 x 128 windows in the densest and the sparsest populated cluster "
+                         "regions" if args.workload == "clusters200k" else
+                         "every pixel" if args.workload == "wine" else "the cpu_baseline leg's last pixel sample")
     if plain is not None:
         plain["err_vs_oracle"] = err.get("fp32") if err else None
     lat = {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99)),
            "steps": len(step_ms), "what": "device time of one step (create + render + bands)"}
+    wname = {inputs.WEIGHT_GAUSS: "gauss", inputs.WEIGHT_WENDLAND: "wendland", inputs.WEIGHT_INVDIST: "invdist"}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
-            "config": {"workload": WORKLOAD if wl.trunc == 0 else WORKLOAD + f"_trunc{wl.trunc:g}",
-                       "n": n, "D": D, "W": W, "H": H, "degree": 2,
-                       "weight": "gauss" if wl.trunc == 0 else f"gauss truncated to |dx|,|dy| < {wl.trunc:g} h",
+            "config": {"workload": cfg_name if wl.trunc == 0 else cfg_name + f"_trunc{wl.trunc:g}",
+                       "n": n, "D": D, "W": W, "H": H, "degree": wl.degree,
+                       "weight": (wname[wl.weight] if wl.trunc == 0 else
+                                  f"gauss truncated to |dx|,|dy| < {wl.trunc:g} h"),
                        "h": wl.h, "levels": L, "precision": args.precision, "l2": "flushed between steps",
                        "replicas": world},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
@@ -435,12 +583,17 @@ def run_ours(args):
                           "split_weight_half_tiles": int(retried)},
             "pairs": {"workload": int(pairs), "visited_by_main_kernel": int(pairs_visited),
                       "visited_fraction": pairs_visited / (W * H * n),
-                      "note": "the main kernel visits, per 16 x 16 tile, the grid cells holding points whose "
-                              "weight reaches e^-28 of some pixel's largest; the others have FP16 weight exactly "
-                              "0 (value counts the workload's pairs)"}}
+                      "visited_rate": world * pairs_visited * D / (ms_step * 1e-3),
+                      "note": ("pixel*point*dim/s of the pairs the main kernel visited (visited_rate): per 16 x 16 "
+                               "tile, the grid cells holding points whose weight reaches e^-28 of some pixel's "
+                               "largest; the others have FP16 weight exactly 0.  value counts the workload's "
+                               "pairs (the full sum's W*H*n, or the pairs in support)")}}
     if wl.trunc > 0:
         line["truncated"] = {"support": wl.trunc, "pairs_in_support": pairs, "full_pairs": W * H * n,
                              "full_sum_equivalent": world * W * H * n * D / (ms_step * 1e-3)}
+    if wl.weight == inputs.WEIGHT_WENDLAND:
+        line["support"] = {"radius": wl.h, "pairs_in_support": pairs, "full_pairs": W * H * n,
+                           "full_sum_equivalent": world * W * H * n * D / (ms_step * 1e-3)}
     print(json.dumps(line), flush=True)
 
 
@@ -886,14 +1039,17 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="fp16", choices=["fp16", "bf16", "fp32", "fp64"])
+    ap.add_argument("--precision", default=None, choices=["fp16", "bf16", "fp32", "fp64"],
+                    help="default: fp16, or fp64 for the wine-shaped workload (the FP64 configuration)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--weight-split", type=int, default=None, choices=[0, 1, 2])
     ap.add_argument("--no-compare-fp32", dest="compare_fp32", action="store_false",
                     help="skip the plain FP32 comparison run")
     ap.add_argument("--workload", default="fourier10k",
-                    choices=["fourier10k", "batch64", "serve", "table1", "spacemap", "variants"],
-                    help="the 10k-point render (default), 64 datasets in one graph, or the serving mix")
+                    choices=["fourier10k", "clusters200k", "wine", "batch64", "serve", "table1", "spacemap",
+                             "variants"],
+                    help="the 10k-point render (default), the 200k-point Wendland render, the wine-shaped FP64 "
+                         "render, 64 datasets in one graph, or the serving mix")
     ap.add_argument("--support", type=float, default=0.0,
                     help="truncated Gaussian: box half-width in units of h (0: the full sum)")
     ap.add_argument("--rate", type=float, default=200.0, help="serve: requests per second")
@@ -903,6 +1059,8 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
+    if args.precision is None:
+        args.precision = WORKLOADS[args.workload][2] if args.workload in WORKLOADS else "fp16"
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "batch64":

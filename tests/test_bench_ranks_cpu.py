@@ -2,6 +2,7 @@
 max-over-ranks timing and the reference arm under torchrun, where rank 0
 alone prints one JSON line.  Each rank renders its own replica, so the data
 path has no collective; only the timing reduction crosses ranks."""
+import dataclasses
 import json
 import os
 import socket
@@ -91,3 +92,20 @@ def test_pairs_in_boxes_equals_the_oracle_counts():
             w = dataclasses.replace(wl, trunc=c, view=view)
             r = oracle.mls(w.xy, w.F, w.degree, w.weight, w.h, w.W, w.H, view=view, trunc=c)
             assert bench.pairs_in_boxes(w) == int(r.count.sum())
+
+
+def test_pairs_in_discs_equals_the_oracle_counts():
+    """bench.py counts the Wendland weight's in-support pairs per point (the
+    pixel columns of each row inside its disc); the oracle counts them per
+    pixel.  Both must agree exactly, including ragged rasters and zoomed
+    views."""
+    import oracle
+    sys.path.insert(0, ROOT)
+    import bench
+    from paper_1408_0677_gb300 import inputs
+    for wl in (inputs.small_random(62, 300, 2, 41, 29, 2, 1, 0.07),
+               inputs.fourier_mix(52, 20000, 2, 77, 53, 2, 1, 0.02)):
+        for view in ((0.0, 0.0, 1.0, 1.0), (0.2, 0.1, 0.7, 0.45), (0.31, 0.42, 0.3725, 0.4625)):
+            w = dataclasses.replace(wl, view=view)
+            r = oracle.mls(w.xy, w.F, w.degree, w.weight, w.h, w.W, w.H, view=view)
+            assert bench.pairs_in_discs(w) == int(r.count.sum())
