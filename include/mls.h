@@ -205,7 +205,9 @@ mls_status mls_create(const mls_desc *desc, const double *xy, const double *F,
  *           them.  Page-locked host buffers registered with the handle's
  *           device (all three of those given) are written by the kernels
  *           directly; other host memory is staged in device memory and
- *           copied back.
+ *           copied back.  A host output whose first byte is page-locked
+ *           but whose extent runs past that page-locked block is rejected
+ *           (MLS_E_INVAL) before any launch.
  * Precision routing: FP16/BF16 renders use the tensor-core kernel, except
  * with the inverse-distance weight (no finite support for the tile operand's
  * range clip) and when a 16-pixel tile spans more than 4 h (no moment frame

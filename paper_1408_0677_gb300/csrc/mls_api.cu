@@ -423,29 +423,34 @@ bad:
 
 namespace mlsi {
 
-// The device address of a page-locked host buffer of `bytes` bytes registered
-// with the handle's device, or nullptr for any other memory.  Both the first
-// and the last byte must be page-locked for this device, and the last byte's
-// device address must lie bytes - 1 past the first's (one mapped range): a
-// buffer that runs past the end of its page-locked block is staged instead,
-// so the kernels never write outside a mapped range.
-static void *mapped_host(void *ptr, size_t bytes, int device) {
-  if (!ptr || bytes == 0) return nullptr;
+// Where a host output of `bytes` bytes lives: page-locked and mapped for the
+// handle's device as one range (the kernels may write it directly through
+// *dev), pageable (staged in device memory and copied back), or neither: a
+// buffer whose first byte is page-locked but whose extent runs past that
+// mapped range.  The kernels could reach only the mapped part of such a
+// buffer and the copy engines refuse it, so it is rejected.
+enum HostKind { HOST_PAGEABLE, HOST_MAPPED, HOST_STRADDLES };
+
+static HostKind host_kind(void *ptr, size_t bytes, int device, void **dev) {
+  *dev = nullptr;
+  if (!ptr || bytes == 0) return HOST_PAGEABLE;
   cudaPointerAttributes a{}, e{};
   if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) {
     cudaGetLastError();
-    return nullptr;
+    return HOST_PAGEABLE;
   }
-  if (a.type != cudaMemoryTypeHost || !a.devicePointer || a.device != device) return nullptr;
+  if (a.type != cudaMemoryTypeHost) return HOST_PAGEABLE;
   const char *last = (const char *)ptr + (bytes - 1);
   if (cudaPointerGetAttributes(&e, last) != cudaSuccess) {
     cudaGetLastError();
-    return nullptr;
+    return HOST_STRADDLES;
   }
-  if (e.type != cudaMemoryTypeHost || e.device != device ||
+  if (e.type != cudaMemoryTypeHost || !a.devicePointer || !e.devicePointer ||
       (const char *)e.devicePointer != (const char *)a.devicePointer + (bytes - 1))
-    return nullptr;
-  return a.devicePointer;
+    return HOST_STRADDLES;
+  if (a.device != device || e.device != device) return HOST_PAGEABLE;   // another device's mapping: stage
+  *dev = a.devicePointer;
+  return HOST_MAPPED;
 }
 
 // Host-side part of a render: validation, scratch, level upload, staging;
@@ -473,9 +478,13 @@ static mls_status render_prepare(mls_handle *h, RenderCtx *c, const mls_view *vi
     // Page-locked host outputs are written by the kernels directly (over
     // NVLink-C2C on GB300, overlapped with the render); other host memory is
     // staged in device memory and copied back after the render.
-    void *fm = mapped_host(field, plane * h->desc.D * esz, h->device);
-    void *sm = status ? mapped_host(status, plane, h->device) : nullptr;
-    void *bm = bands ? mapped_host(bands, plane * h->desc.D, h->device) : nullptr;
+    void *fm = nullptr, *sm = nullptr, *bm = nullptr;
+    const HostKind fk = host_kind(field, plane * h->desc.D * esz, h->device, &fm);
+    const HostKind sk = status ? host_kind(status, plane, h->device, &sm) : HOST_PAGEABLE;
+    const HostKind bk = bands ? host_kind(bands, plane * h->desc.D, h->device, &bm) : HOST_PAGEABLE;
+    if (fk == HOST_STRADDLES || sk == HOST_STRADDLES || bk == HOST_STRADDLES)
+      return fail(MLS_E_INVAL, "a host output starts in page-locked memory but runs past its page-locked "
+                               "block; pass it wholly inside one page-locked block, or in pageable memory");
     c->direct_out = fm && (!status || sm) && (!bands || bm);
     if (c->direct_out) {
       field_d = fm;
