@@ -382,6 +382,10 @@ def run_ours(args):
     wl = getattr(inputs, gen)()
     if args.support > 0:
         wl = dataclasses.replace(wl, trunc=args.support)
+    if args.size > 0:
+        # a smaller raster of the same data and view (profiling captures)
+        wl = dataclasses.replace(wl, W=args.size, H=args.size)
+        cfg_name += f"_at{args.size}sq"
     n, D, W, H, L = wl.n, wl.D, wl.W, wl.H, wl.levels.shape[1]
     k_terms = (wl.degree + 1) * (wl.degree + 2) // 2
     n_mono = (2 * wl.degree + 1) * (2 * wl.degree + 2) // 2
@@ -694,13 +698,17 @@ def run_batch(args):
 
 
 def run_serve(args):
-    """Serving: Poisson arrivals (200 requests/s) of iso-band renders of four
-    resident datasets (1M points each, D = 16, 64 clusters, quadratic,
-    Wendland radius 0.006), viewports 512^2-2048^2 over zoom windows of side
-    log-uniform in [1/16, 1]; continuous batching in the library's server.
-    Latency counts from each request's arrival time."""
-    import ctypes
-
+    """Serving: Poisson arrivals of iso-band renders; continuous batching in
+    the library's server.  Resident datasets: four of 1M points each (D = 16,
+    64 clusters, quadratic, Wendland radius 0.006) and the 200k-point
+    configuration (D = 64, 64 clusters, quadratic, Wendland radius 0.015).
+    A request picks the 200k-point dataset with probability 1/5 (else one of
+    the four), a viewport of side log-uniform in 512-2048 pixels and a zoom
+    window of side log-uniform in [1/16, 1].  Latency counts from each
+    request's arrival time.  --rates runs the same request list at several
+    offered rates: the line reports each, and the highest rate the server
+    sustained (completions keep up with arrivals: at least 95% of the offered
+    rate) beside the offered 200 requests/s."""
     import torch
     world, rank, local = _dist()
     torch.cuda.set_device(local)
@@ -716,72 +724,90 @@ def run_serve(args):
         lev = inputs.default_levels(F, 16)
         r = Renderer(torch.from_numpy(xy).cuda(), torch.from_numpy(F).cuda(), degree=2,
                      weight=inputs.WEIGHT_WENDLAND, h=0.006, precision=args.precision)
-        dsets.append((r, np.ascontiguousarray(lev)))
+        dsets.append((r, np.ascontiguousarray(lev), 16))
+    c3 = inputs.clusters_200k()
+    r = Renderer(torch.from_numpy(c3.xy).cuda(), torch.from_numpy(c3.F).cuda(), degree=c3.degree,
+                 weight=c3.weight, h=c3.h, precision=args.precision)
+    dsets.append((r, np.ascontiguousarray(c3.levels), c3.D))
     nreq = args.requests
-    arrivals = np.cumsum(rng.exponential(1.0 / args.rate, size=nreq))
+    gaps = rng.exponential(1.0, size=nreq)             # arrivals in units of 1 / rate
     specs = []
     for _ in range(nreq):
-        k = int(rng.integers(4))
+        k = 4 if rng.random() < 0.2 else int(rng.integers(4))
         side = int(round(np.exp(rng.uniform(np.log(512), np.log(2048)))))
         win = float(np.exp(rng.uniform(np.log(1 / 16), 0.0)))
         x0, y0 = rng.uniform(0.0, 1.0 - win, size=2)
         specs.append((k, side, (x0, y0, x0 + win, y0 + win)))
-    pool = [torch.empty(16 * 2048 * 2048, dtype=torch.uint8).pin_memory() for _ in range(args.slots * 4)]
-    free = list(range(len(pool)))
+    pools = {16: [torch.empty(16 * 2048 * 2048, dtype=torch.uint8).pin_memory() for _ in range(args.slots * 3)],
+             64: [torch.empty(64 * 2048 * 2048, dtype=torch.uint8).pin_memory() for _ in range(args.slots + 2)]}
     srv = Server(slots=args.slots, mem_budget=args.mem_gb << 30)
     # warm-up: one request per dataset
-    for r, lev in dsets:
+    for r, lev, _ in dsets:
         srv.submit(r, 256, 256, levels=lev)
     srv.drain()
     srv.poll()
-    inflight = {}
-    lat, queued, dev_ms, px_dims = [], [], [], 0
-    t0 = time.perf_counter()
 
-    def collect():
-        nonlocal px_dims
-        for d in mls_server_poll(srv.handle):
-            k, side, t_arr, buf = inflight.pop(d.id)
-            free.append(buf)
-            t_done = time.perf_counter() - t0
-            lat.append(1e3 * (t_done - t_arr))
-            queued.append(d.queued_ms)
-            dev_ms.append(d.device_ms)
-            px_dims += side * side * 16
+    def one_rate(rate):
+        arrivals = np.cumsum(gaps) / rate
+        free = {D: list(range(len(pl))) for D, pl in pools.items()}
+        inflight = {}
+        lat, queued, dev_ms = [], [], []
+        px_dims = 0
+        t0 = time.perf_counter()
 
-    for i, (k, side, view) in enumerate(specs):
-        while time.perf_counter() - t0 < arrivals[i]:
+        def collect():
+            nonlocal px_dims
+            for d in mls_server_poll(srv.handle):
+                D, side, t_arr, buf = inflight.pop(d.id)
+                free[D].append(buf)
+                lat.append(1e3 * (time.perf_counter() - t0 - t_arr))
+                queued.append(d.queued_ms)
+                dev_ms.append(d.device_ms)
+                px_dims += side * side * D
+
+        for i, (k, side, view) in enumerate(specs):
+            while time.perf_counter() - t0 < arrivals[i]:
+                collect()
+                time.sleep(0.0002)
+            r, lev, D = dsets[k]
+            while not free[D]:
+                collect()
+                time.sleep(0.0002)
+            buf = free[D].pop()
+            req = MlsRequest(r.handle, MlsView(side, side, *view), lev.ctypes.data, lev.shape[1], 0,
+                             pools[D][buf].data_ptr(), None, None)
+            inflight[mls_server_submit(srv.handle, req)] = (D, side, arrivals[i], buf)
+        while inflight:
             collect()
-            time.sleep(0.0002)
-        while not free:
-            collect()
-            time.sleep(0.0002)
-        buf = free.pop()
-        r, lev = dsets[k]
-        req = MlsRequest(r.handle, MlsView(side, side, *view), lev.ctypes.data, lev.shape[1], 0,
-                         pool[buf].data_ptr(), None, None)
-        rid = mls_server_submit(srv.handle, req)
-        inflight[rid] = (k, side, arrivals[i], buf)
-    while inflight:
-        collect()
-        time.sleep(0.0005)
-    wall = time.perf_counter() - t0
+            time.sleep(0.0005)
+        wall = time.perf_counter() - t0
+        return {"offered_per_s": rate, "requests_per_s": nreq / wall, "wall_s": wall, "px_dims_per_s": px_dims / wall,
+                "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
+                "queued_ms": {"p50": float(np.percentile(queued, 50)), "p99": float(np.percentile(queued, 99))},
+                "device_ms": {"p50": float(np.percentile(dev_ms, 50)), "p99": float(np.percentile(dev_ms, 99))},
+                "sustained": nreq / wall >= 0.95 * rate}
+
+    rates = sorted({float(x) for x in args.rates.split(",")} | {args.rate})
+    runs = [one_rate(rt) for rt in rates]
     st = srv.drain()
     srv.close()
     if rank != 0:
         return
-    value = px_dims / wall
-    line = {"metric": "served pixel*dim/s (iso-band renders)", "value": value, "unit": "pixel*dim/s",
-            "n_gpus": 1, "steps": nreq, "warmup": len(dsets), "ms_per_step": 1e3 * wall / nreq,
+    head = next(rn for rn in runs if rn["offered_per_s"] == args.rate)
+    ok = [rn for rn in runs if rn["sustained"]]
+    best = max(ok, key=lambda rn: rn["offered_per_s"]) if ok else None
+    line = {"metric": "served pixel*dim/s (iso-band renders)", "value": head["px_dims_per_s"], "unit": "pixel*dim/s",
+            "n_gpus": 1, "steps": nreq, "warmup": len(dsets), "ms_per_step": 1e3 * head["wall_s"] / nreq,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": args.precision,
             "data": "synthetic",
-            "config": {"workload": "serve_poisson200_4x1M_d16_wendland_512-2048sq_zoom", "rate_per_s": args.rate,
-                       "requests": nreq, "slots": args.slots, "mem_budget_gb": args.mem_gb},
-            "requests_per_s": nreq / wall,
-            "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
-                           "what": "arrival to completion (bands on the host)"},
-            "queued_ms": {"p50": float(np.percentile(queued, 50)), "p99": float(np.percentile(queued, 99))},
-            "device_ms": {"p50": float(np.percentile(dev_ms, 50)), "p99": float(np.percentile(dev_ms, 99))},
+            "config": {"workload": "serve_poisson_4x1M_d16_r0.006_plus_200k_d64_r0.015_wendland_512-2048sq_zoom",
+                       "rate_per_s": args.rate, "requests": nreq, "slots": args.slots, "mem_budget_gb": args.mem_gb,
+                       "mix": "1/5 on the 200k-point D=64 dataset, 4/5 on the four 1M-point D=16 datasets"},
+            "requests_per_s": head["requests_per_s"],
+            "latency_ms": dict(head["latency_ms"], what="arrival to completion (bands on the host)"),
+            "queued_ms": head["queued_ms"], "device_ms": head["device_ms"],
+            "sustained_at_offered_rate": head["sustained"],
+            "highest_sustained": best, "rates": runs,
             "server": {"peak_inflight": int(st.peak_inflight), "peak_bytes": int(st.peak_bytes),
                        "failed": int(st.failed)},
             "e2e": None, "roofline": None, "cpu_baseline": None}
@@ -1052,7 +1078,10 @@ def main():
                          "render, 64 datasets in one graph, or the serving mix")
     ap.add_argument("--support", type=float, default=0.0,
                     help="truncated Gaussian: box half-width in units of h (0: the full sum)")
-    ap.add_argument("--rate", type=float, default=200.0, help="serve: requests per second")
+    ap.add_argument("--size", type=int, default=0,
+                    help="render the workload's data and view on a size x size raster instead (0: its own)")
+    ap.add_argument("--rate", type=float, default=200.0, help="serve: offered requests per second (headline)")
+    ap.add_argument("--rates", default="200", help="serve: comma-separated offered rates to run as well")
     ap.add_argument("--requests", type=int, default=400, help="serve: number of requests")
     ap.add_argument("--slots", type=int, default=8, help="serve: requests in flight at most")
     ap.add_argument("--mem-gb", type=int, default=16, help="serve: device memory budget (GiB)")

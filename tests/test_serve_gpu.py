@@ -112,3 +112,31 @@ def test_arrivals_while_busy_and_oversized_request(datasets):
         wk, rk = datasets[k]
         _check(q, _alone(wk, rk, W, H, view))
     srv.close()
+
+
+def test_served_results_match_the_oracle(datasets):
+    """Served renders of zoom windows (side 1/8 to 1 of the square, ragged
+    rasters) against the FP64 oracle on sampled pixels of every request: a
+    mistake common to the served and the lone render would pass the tests
+    above but not this one."""
+    import dataclasses
+
+    from paper_1408_0677_gb300 import Server
+    from tests.gpu_util import compare, oracle_ref
+    precs = ["fp16", "fp32", "bf16"]
+    reqs = _requests(datasets, 18, 3)
+    srv = Server(slots=4, mem_budget=2 << 30)
+    subs = []
+    for k, W, H, view in reqs:
+        w, r = datasets[k]
+        subs.append((srv.submit(r, W, H, view, levels=w.levels, field=True), k, W, H, view))
+    st = srv.drain()
+    srv.poll()
+    assert st.completed == len(reqs) and st.failed == 0
+    for i, (q, k, W, H, view) in enumerate(subs):
+        w, _ = datasets[k]
+        wl = dataclasses.replace(w, W=W, H=H, view=tuple(float(x) for x in view))
+        pix = inputs.sample_pixels(100 + i, W, H, 400)
+        res = {"field": q.field.numpy(), "status": q.status.numpy(), "bands": q.bands.numpy()}
+        compare(wl, res, oracle_ref(wl, pix), precs[k], pixels=pix)
+    srv.close()
