@@ -105,11 +105,14 @@ def library_path() -> str:
 
 
 def load(path: str | None = None):
-    """Open libmls.so (built in-tree by paper_1408_0677_gb300.build)."""
+    """Open libmls.so (built in-tree by paper_1408_0677_gb300.build), or the
+    in-tree variant named by the environment variable MLS_LIBRARY (the
+    checked or sanitized build)."""
     global _lib
     if _lib is not None and path is None:
         return _lib
-    path = path or _build.LIB
+    default = path is None
+    path = path or os.environ.get("MLS_LIBRARY") or _build.LIB
     if not os.path.exists(path):
         raise RuntimeError(f"CUDA library not built: {path} (run paper_1408_0677_gb300.build.build())")
     lib = ctypes.CDLL(path)
@@ -160,7 +163,7 @@ def load(path: str | None = None):
     lib.mls_debug_operand_cut.argtypes = [P, ctypes.c_int32]
     lib.mls_debug_df_weight.restype = ctypes.c_int
     lib.mls_debug_df_weight.argtypes = [ctypes.c_int, P, P, ctypes.c_int64, P]
-    if path == _build.LIB:
+    if default:
         _lib = lib
     return lib
 

@@ -2,6 +2,16 @@
 
 Each translation unit is compiled in parallel, then linked into
 ``paper_1408_0677_gb300/_build/libmls.so``.  Rebuilds only what changed.
+
+Variants (separate objects and library, same sources):
+  checked=True   -> _build/libmls_checked.so: -DMLS_CHECKED, every bin, tile,
+                    cell and list index of the kernels tested against its
+                    array (a bad one is recorded in the device error word,
+                    which mls_sync reports, and clamped; no trap)
+  sanitize=True  -> _build/libmls_asan.so: host code under AddressSanitizer
+                    and UndefinedBehaviorSanitizer (load it with the
+                    sanitizer runtime preloaded)
+The binding loads the library named by MLS_LIBRARY, else libmls.so.
 """
 from __future__ import annotations
 
@@ -33,17 +43,27 @@ def _headers_mtime() -> float:
     return max(os.path.getmtime(h) for h in hs)
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    os.makedirs(OUT, exist_ok=True)
+CHECKED_LIB = os.path.join(OUT, "libmls_checked.so")
+ASAN_LIB = os.path.join(OUT, "libmls_asan.so")
+# one -Xcompiler per flag: nvcc splits an -Xcompiler argument at its commas
+SAN_FLAGS = ["-Xcompiler=-fsanitize=address", "-Xcompiler=-fsanitize=undefined", "-Xcompiler=-fno-omit-frame-pointer",
+             "-Xcompiler=-fno-sanitize-recover=all"]
+
+
+def build(force: bool = False, verbose: bool = False, checked: bool = False, sanitize: bool = False) -> str:
+    odir = os.path.join(OUT, "checked" if checked else "asan" if sanitize else "")
+    lib = CHECKED_LIB if checked else ASAN_LIB if sanitize else LIB
+    extra = (["-DMLS_CHECKED"] if checked else []) + (SAN_FLAGS if sanitize else [])
+    os.makedirs(odir, exist_ok=True)
     hdr = _headers_mtime()
     nvcc = _nvcc()
 
     def compile_one(src):
         s = os.path.join(CSRC, src)
-        o = os.path.join(OUT, src.replace(".cu", ".o"))
+        o = os.path.join(odir, src.replace(".cu", ".o"))
         if not force and os.path.exists(o) and os.path.getmtime(o) >= max(os.path.getmtime(s), hdr):
             return o, False
-        cmd = [nvcc, *ARCH, *FLAGS, "-c", s, "-o", o + ".tmp"]
+        cmd = [nvcc, *ARCH, *FLAGS, *extra, "-c", s, "-o", o + ".tmp"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed for {src}:\n{r.stdout}\n{r.stderr}")
@@ -56,14 +76,14 @@ def build(force: bool = False, verbose: bool = False) -> str:
         results = list(ex.map(compile_one, SOURCES))
     objs = [o for o, _ in results]
     changed = any(c for _, c in results)
-    if force or changed or not os.path.exists(LIB) or os.path.getmtime(LIB) < max(os.path.getmtime(o) for o in objs):
-        tmp = LIB + f".tmp{os.getpid()}"
-        cmd = [nvcc, "-shared", *ARCH, "-o", tmp, *objs]
+    if force or changed or not os.path.exists(lib) or os.path.getmtime(lib) < max(os.path.getmtime(o) for o in objs):
+        tmp = lib + f".tmp{os.getpid()}"
+        cmd = [nvcc, "-shared", *ARCH, *(SAN_FLAGS if sanitize else []), "-o", tmp, *objs]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-        os.replace(tmp, LIB)
-    return LIB
+        os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

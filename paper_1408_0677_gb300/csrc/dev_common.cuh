@@ -17,7 +17,36 @@ enum : int {
   ERR_WAIT_EMPTY = 2,     // producer gave up waiting for a drained stage
   ERR_WAIT_ACC = 3,       // epilogue gave up waiting for the accumulator
   ERR_CAND_OVERFLOW = 4,  // (informational) candidate list overflowed, brute force used
+  ERR_INDEX = 0x100,      // checked build: ERR_INDEX + site, an index outside its array
 };
+
+// Index sites of the checked build (ERR_INDEX + site).
+enum : int {
+  SITE_CELL = 1,     // cell_start of the uniform grid: [gx gy + 1]
+  SITE_PIXEL = 2,    // per-pixel scratch of the padded tile grid (stabiliser, counts)
+  SITE_TILE = 3,     // per-tile scratch (frames, largest stabiliser): [tiles_x tiles_y]
+  SITE_LIST = 4,     // hand-over lists and their pixel ids: [W H]
+  SITE_QUEUE = 5,    // half-tile queue and marks: [2 tiles_x tiles_y]
+  SITE_BLOCK = 6,    // 8-point blocks of the tensor path's staged copies: [n_pad / 8]
+};
+
+#ifdef MLS_CHECKED
+constexpr bool kChecked = true;
+#else
+constexpr bool kChecked = false;
+#endif
+
+// Checked build (-DMLS_CHECKED): an index outside [0, n) records
+// ERR_INDEX + site in the error word (no trap: mls_sync reports it and the
+// context stays usable) and is clamped into the array, so the access itself
+// stays in bounds.  In the normal build this is the index itself.
+__device__ __forceinline__ int64_t chk(int *err, int64_t i, int64_t n, int site) {
+  if (kChecked && (i < 0 || i >= n)) {
+    if (err) atomicCAS(err, 0, ERR_INDEX + site);
+    return i < 0 || n <= 0 ? 0 : n - 1;
+  }
+  return i;
+}
 
 // One nanosecond-resolution global timer read.
 __device__ __forceinline__ uint64_t globaltimer_ns() {
@@ -136,6 +165,23 @@ struct KParams {
   const unsigned int *list_count;  // device count for list mode, or null
   int64_t list_cap;
 };
+
+// Indices of the library's scratch arrays, checked in the checked build.
+__device__ __forceinline__ int cell_at(const KParams &p, int64_t i) {
+  return p.cell_start[chk(p.err, i, (int64_t)p.gx * p.gy + 1, SITE_CELL)];
+}
+__device__ __forceinline__ int64_t pix_i(const KParams &p, int64_t i) {
+  return chk(p.err, i, (int64_t)p.tiles_x * p.tiles_y * 256, SITE_PIXEL);
+}
+__device__ __forceinline__ int64_t tile_i(const KParams &p, int64_t i) {
+  return chk(p.err, i, (int64_t)p.tiles_x * p.tiles_y, SITE_TILE);
+}
+__device__ __forceinline__ int64_t list_i(const KParams &p, int64_t i) {
+  return chk(p.err, i, (int64_t)p.W * p.H, SITE_LIST);
+}
+__device__ __forceinline__ int64_t queue_i(const KParams &p, int64_t i) {
+  return chk(p.err, i, 2 * (int64_t)p.tiles_x * p.tiles_y, SITE_QUEUE);
+}
 
 __device__ __forceinline__ void set_error(int *err, int code) {
   if (err) atomicCAS(err, 0, code);

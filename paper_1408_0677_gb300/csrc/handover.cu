@@ -143,8 +143,8 @@ __device__ __forceinline__ int for_near(const KParams &p, const Ranges &R, float
         my0 = 0;
         my1 = R.all_n;
       } else if (rr < nrow) {
-        my0 = p.cell_start[(R.cy0 + rr) * p.gx + R.cx0];
-        my1 = p.cell_start[(R.cy0 + rr) * p.gx + R.cx1 + 1];
+        my0 = cell_at(p, (int64_t)(R.cy0 + rr) * p.gx + R.cx0);
+        my1 = cell_at(p, (int64_t)(R.cy0 + rr) * p.gx + R.cx1 + 1);
       }
     }
     const int a0 = __shfl_sync(0xffffffffu, my0, r & 31);
@@ -426,7 +426,7 @@ __global__ __launch_bounds__(kWarps * 32, 4) void k_handover(KParams p, const in
     const int u = id % p.W, v = id / p.W;
     const double px = __dadd_rn(p.x0, __dmul_rn(__dadd_rn((double)u, 0.5), p.sx));
     const double py = __dadd_rn(p.y0, __dmul_rn(__dadd_rn((double)v, 0.5), p.sy));
-    mhat = (WK == MLS_W_WENDLAND) ? 0.f : p.mstab[(size_t)v * (p.tiles_x * 16) + u];
+    mhat = (WK == MLS_W_WENDLAND) ? 0.f : p.mstab[pix_i(p, (int64_t)v * (p.tiles_x * 16) + u)];
     if (WK == MLS_W_INVDIST) {
       R.all_n = (int)p.n;
       R.cx0 = R.cx1 = R.cy0 = R.cy1 = 0;
@@ -470,7 +470,7 @@ __global__ __launch_bounds__(kWarps * 32, 4) void k_handover(KParams p, const in
       if (lane == 0) j = atomicAdd(&s_next[0], 1);
       j = __shfl_sync(0xffffffffu, j, 0);
       if (j >= nq) break;
-      const int id = list[first + (int64_t)j * step];
+      const int id = (int)list_i(p, list[list_i(p, first + (int64_t)j * step)]);
       Ranges R;
       float mhat, pxh, pxl, pyh, pyl;
       setup(id, R, mhat, pxh, pxl, pyh, pyl);
@@ -566,12 +566,12 @@ __global__ __launch_bounds__(kWarps * 32, 4) void k_handover(KParams p, const in
       k = __shfl_sync(0xffffffffu, k, 0);
       if (k >= nq) break;
       const int j = s_order[k];
-      const int id = list[first + (int64_t)j * step];
+      const int id = (int)list_i(p, list[list_i(p, first + (int64_t)j * step)]);
       const int flags = slots[j].flags;
       if (flags & 1) {
         if (lane == 0) {
           const unsigned int k2 = atomicAdd(list2_count, 1u);
-          list2[k2] = id;
+          list2[list_i(p, k2)] = id;
         }
         continue;
       }

@@ -631,6 +631,9 @@ mls_status mls_render(mls_handle *h, const mls_view *view, void *field, uint8_t 
     MLS_CUDA_TRY(cudaStreamSynchronize(st));
     int err = 0;
     MLS_CUDA_TRY(cudaMemcpy(&err, h->ctx.err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (err >= mlsk::ERR_INDEX)
+      return fail(MLS_E_CUDA, "checked build: a kernel index lay outside its array (site " +
+                                  std::to_string(err - mlsk::ERR_INDEX) + ")");
     if (err) return fail(MLS_E_TIMEOUT, "a bounded device wait gave up (error word " + std::to_string(err) + ")");
   }
   return MLS_OK;
@@ -709,6 +712,9 @@ mls_status mls_sync(mls_handle *h, double timeout_s, mls_stats *stats) {
     stats->main_path = h->last_path;
     cudaGetLastError();
   }
+  if (err >= mlsk::ERR_INDEX)
+    return fail(MLS_E_CUDA, "checked build: a kernel index lay outside its array (site " +
+                                std::to_string(err - mlsk::ERR_INDEX) + ")");
   if (err) return fail(MLS_E_TIMEOUT, "a bounded device wait gave up (error word " + std::to_string(err) + ")");
   return MLS_OK;
 }

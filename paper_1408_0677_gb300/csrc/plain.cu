@@ -65,15 +65,15 @@ __global__ __launch_bounds__(128) void k_mls_f32(KParams p) {
   // (dpx, dpy) = pixel minus frame origin; or, when the tile is large
   // compared with h (p.pixel_frame), in each pixel's own frame
   const int tile = (int)(blockIdx.y >> 1) * p.tiles_x + (int)blockIdx.x;
-  const float cxs = p.tcen[2 * tile], cys = p.tcen[2 * tile + 1];
+  const float cxs = p.tcen[2 * tile_i(p, tile)], cys = p.tcen[2 * tile_i(p, tile) + 1];
   if (t < 16) s_col[t] = (float)((p.x0 + (blockIdx.x * 16 + t + 0.5) * p.sx - p.ctr_x) * p.inv_s - (double)cxs);
   else if (t < 24) s_row[t - 16] = (float)((p.y0 + (blockIdx.y * 8 + t - 16 + 0.5) * p.sy - p.ctr_y) * p.inv_s - (double)cys);
   const size_t pstride = (size_t)p.tiles_x * 16;
   // compact support: the Wendland weight, or the truncated Gaussian's box |dx|, |dy| < c
   const bool binned = (WK == MLS_W_WENDLAND) || (WK == MLS_W_GAUSS && p.trunc > 0.0);
   const float cbox = (WK == MLS_W_GAUSS && p.trunc > 0.0) ? (float)p.trunc : INFINITY;
-  const float m = (WK == MLS_W_WENDLAND) ? 0.f : p.mstab[(size_t)v * pstride + u];
-  const int cflag = binned ? p.cnt[(size_t)v * pstride + u] : 0;
+  const float m = (WK == MLS_W_WENDLAND) ? 0.f : p.mstab[pix_i(p, (int64_t)v * pstride + u)];
+  const int cflag = binned ? p.cnt[pix_i(p, (int64_t)v * pstride + u)] : 0;
   const int count = binned ? (cflag & kCntMask) : (int)(p.n < (1 << 30) ? p.n : (1 << 30));
   const float alpha = (float)p.alpha;
   // point ranges: all points, or the cell rows overlapping the block's pixels
@@ -83,7 +83,7 @@ __global__ __launch_bounds__(128) void k_mls_f32(KParams p) {
   if ((binned || cut) && t == 24) {
     const double rad = (WK == MLS_W_WENDLAND) ? p.h
                        : binned ? p.trunc * p.h * (1.0 + 1e-5)
-                                : p.h * (double)sqrtf(p.tmax[tile] + p.gcut) * (1.0 + 1e-5);
+                                : p.h * (double)sqrtf(p.tmax[tile_i(p, tile)] + p.gcut) * (1.0 + 1e-5);
     const int bu0 = blockIdx.x * 16, bv0 = blockIdx.y * 8;
     const double xa = p.x0 + (bu0 + 0.5) * p.sx, xb = p.x0 + (bu0 + 15.5) * p.sx;
     const double ya = p.y0 + (bv0 + 0.5) * p.sy, yb = p.y0 + (bv0 + 7.5) * p.sy;
@@ -120,8 +120,8 @@ __global__ __launch_bounds__(128) void k_mls_f32(KParams p) {
     for (int r = 0; r < nr; ++r) {
       int a0, a1;
       if (binned || cut) {
-        a0 = p.cell_start[(cy0 + r) * p.gx + cx0];
-        a1 = p.cell_start[(cy0 + r) * p.gx + cx1 + 1];
+        a0 = cell_at(p, (int64_t)(cy0 + r) * p.gx + cx0);
+        a1 = cell_at(p, (int64_t)(cy0 + r) * p.gx + cx1 + 1);
       } else {
         a0 = 0;
         a1 = (int)p.n;
@@ -178,8 +178,8 @@ __global__ __launch_bounds__(128) void k_mls_f32(KParams p) {
       // pixel-point pairs of this block (points in its ranges x 128 pixels)
       unsigned long long npts = 0;
       for (int r = 0; r < nr; ++r)
-        npts += (binned || cut) ? (unsigned long long)(p.cell_start[(cy0 + r) * p.gx + cx1 + 1] -
-                                                       p.cell_start[(cy0 + r) * p.gx + cx0])
+        npts += (binned || cut) ? (unsigned long long)(cell_at(p, (int64_t)(cy0 + r) * p.gx + cx1 + 1) -
+                                                       cell_at(p, (int64_t)(cy0 + r) * p.gx + cx0))
                                 : (unsigned long long)p.n;
       if (npts) atomicAdd(p.visited, npts * 128ull);
     }
@@ -223,7 +223,7 @@ __global__ __launch_bounds__(128) void k_mls_f32(KParams p) {
       write = false;
       if (d0 == 0) {
         const unsigned int k = atomicAdd(p.relist_count, 1u);
-        p.relist[k] = (int)pix;
+        p.relist[list_i(p, k)] = (int)pix;
       }
       handed_over = true;
     } else {
@@ -284,7 +284,7 @@ __global__ __launch_bounds__(256) void k_mls_f64(KParams p, int64_t npix_all) {
   const double rho = p.trunc * p.h;
 
   for (int64_t q = warp0; q < npix; q += nwarps) {
-    const int64_t id = p.list ? p.list[q] : q;
+    const int64_t id = p.list ? list_i(p, p.list[list_i(p, q)]) : q;
     const int u = (int)(id % p.W), v = (int)(id / p.W);
     // the same expression order as the FP64 definition, without contraction
     const double px = __dadd_rn(p.x0, __dmul_rn(__dadd_rn((double)u, 0.5), p.sx));
@@ -293,7 +293,7 @@ __global__ __launch_bounds__(256) void k_mls_f64(KParams p, int64_t npix_all) {
     // cx0..cx1) covering the support (Wendland), the box (truncated Gaussian),
     // or, for listed pixels of the Gaussian, the reach r^2 <= m + kGaussCut h^2
     // of the pairs the list tier sums (the others are skipped below anyway)
-    const float mlist = (p.list && WK == MLS_W_GAUSS) ? p.mstab[(size_t)v * (p.tiles_x * 16) + u] : 0.f;
+    const float mlist = (p.list && WK == MLS_W_GAUSS) ? p.mstab[pix_i(p, (int64_t)v * (p.tiles_x * 16) + u)] : 0.f;
     const bool reach = (WK == MLS_W_GAUSS) && p.list && !binned && p.cell_start != nullptr;
     int nr = 1, cx0 = 0, cx1 = 0, cy0 = 0;
     if (binned || reach) {
@@ -309,7 +309,7 @@ __global__ __launch_bounds__(256) void k_mls_f64(KParams p, int64_t npix_all) {
     // stabiliser m = min r^2 (Gaussian, inverse distance); hand-over lists
     // take the prepass value (any common weight factor leaves the fit unchanged)
     double m = 0.0;
-    const float mhat = (p.list && WK != MLS_W_WENDLAND) ? p.mstab[(size_t)v * (p.tiles_x * 16) + u] : 0.f;
+    const float mhat = (p.list && WK != MLS_W_WENDLAND) ? p.mstab[pix_i(p, (int64_t)v * (p.tiles_x * 16) + u)] : 0.f;
     const float pxs = scaled_px(p, u), pys = scaled_py(p, v);
     if (p.list && WK != MLS_W_WENDLAND) {
       m = (double)mhat * h2;
@@ -337,8 +337,8 @@ __global__ __launch_bounds__(256) void k_mls_f64(KParams p, int64_t npix_all) {
 #pragma unroll
       for (int dd = 0; dd < DC; ++dd) csum[dd] = 0.0;
       for (int r = 0; r < nr; ++r) {
-        const int64_t a0 = (binned || reach) ? p.cell_start[(cy0 + r) * p.gx + cx0] : 0;
-        const int64_t a1 = (binned || reach) ? p.cell_start[(cy0 + r) * p.gx + cx1 + 1] : n;
+        const int64_t a0 = (binned || reach) ? cell_at(p, (int64_t)(cy0 + r) * p.gx + cx0) : 0;
+        const int64_t a1 = (binned || reach) ? cell_at(p, (int64_t)(cy0 + r) * p.gx + cx1 + 1) : n;
         for (int64_t i = a0 + lane; i < a1; i += 32) {
           if (WK == MLS_W_GAUSS && p.list && !binned) {
             // conservative FP32 test before any FP64 work on far pairs

@@ -211,7 +211,7 @@ __global__ __launch_bounds__(256) void k_prepass_min_cells(KParams p) {
     __syncthreads();
     const int c0 = G.win[0], c1 = G.win[1], d0 = G.win[2], d1 = G.win[3];
     for (int row = d0; row <= d1 && c0 <= c1; ++row) {
-      const int a = p.cell_start[row * p.gx + c0], e = p.cell_start[row * p.gx + c1 + 1];
+      const int a = cell_at(p, (int64_t)row * p.gx + c0), e = cell_at(p, (int64_t)row * p.gx + c1 + 1);
       for (int i = a + t; i < e; i += 256) {
         const float x = p.xs[i], y = p.ys[i];
         const float fx = fmaxf(fabsf(x - X0), fabsf(x - X1));
@@ -230,7 +230,7 @@ __global__ __launch_bounds__(256) void k_prepass_min_cells(KParams p) {
   int c0 = G.win[0], c1 = G.win[1], d0 = G.win[2], d1 = G.win[3];
   float m = FLT_MAX;
   for (int row = d0; row <= d1 && c0 <= c1; ++row) {
-    const int a = p.cell_start[row * p.gx + c0], e = p.cell_start[row * p.gx + c1 + 1];
+    const int a = cell_at(p, (int64_t)row * p.gx + c0), e = cell_at(p, (int64_t)row * p.gx + c1 + 1);
     for (int base = a; base < e; base += 256) {
       __syncthreads();
       if (base + t < e) {
@@ -258,7 +258,7 @@ __global__ __launch_bounds__(256) void k_prepass_min_cells(KParams p) {
   c0 = G.win[0]; c1 = G.win[1]; d0 = G.win[2]; d1 = G.win[3];
   float mc = FLT_MAX;
   for (int row = d0; row <= d1 && c0 <= c1; ++row) {
-    const int a = p.cell_start[row * p.gx + c0], e = p.cell_start[row * p.gx + c1 + 1];
+    const int a = cell_at(p, (int64_t)row * p.gx + c0), e = cell_at(p, (int64_t)row * p.gx + c1 + 1);
     for (int i = a + t; i < e; i += 256) {
       const float dx = p.xs[i] - Cx, dy = p.ys[i] - Cy;
       mc = fminf(mc, dx * dx + dy * dy);
@@ -267,7 +267,7 @@ __global__ __launch_bounds__(256) void k_prepass_min_cells(KParams p) {
   mc = block_min(mc, red);
   float sw = 0.f, swx = 0.f, swy = 0.f;
   for (int row = d0; row <= d1 && c0 <= c1; ++row) {
-    const int a = p.cell_start[row * p.gx + c0], e = p.cell_start[row * p.gx + c1 + 1];
+    const int a = cell_at(p, (int64_t)row * p.gx + c0), e = cell_at(p, (int64_t)row * p.gx + c1 + 1);
     for (int i = a + t; i < e; i += 256) {
       const float dx = p.xs[i] - Cx, dy = p.ys[i] - Cy;
       const float w = exp2f((mc - (dx * dx + dy * dy)) * 1.4426950408889634f);
@@ -300,8 +300,8 @@ __global__ __launch_bounds__(256) void k_prepass_count(KParams p) {
   int count = 0;
   bool edge = false;
   for (int cyy = cy0; cyy <= cy1 && cx0 <= cx1; ++cyy) {
-    const int a = p.cell_start[cyy * p.gx + cx0];
-    const int e = p.cell_start[cyy * p.gx + cx1 + 1];
+    const int a = cell_at(p, (int64_t)cyy * p.gx + cx0);
+    const int e = cell_at(p, (int64_t)cyy * p.gx + cx1 + 1);
     for (int base = a; base < e; base += 256) {
       __syncthreads();
       if (base + t < e) {
@@ -327,8 +327,8 @@ __global__ __launch_bounds__(256) void k_prepass_count(KParams p) {
   const float Cy = 0.5f * (G.row[7] + G.row[8]);
   float sw = 0.f, swx = 0.f, swy = 0.f;
   for (int cyy = cy0; cyy <= cy1 && cx0 <= cx1; ++cyy) {
-    const int a = p.cell_start[cyy * p.gx + cx0];
-    const int e = p.cell_start[cyy * p.gx + cx1 + 1];
+    const int a = cell_at(p, (int64_t)cyy * p.gx + cx0);
+    const int e = cell_at(p, (int64_t)cyy * p.gx + cx1 + 1);
     for (int i = a + t; i < e; i += 256) {
       const float dx = p.xs[i] - Cx, dy = p.ys[i] - Cy;
       const float q = sqrtf(dx * dx + dy * dy);
@@ -366,8 +366,8 @@ __global__ __launch_bounds__(256) void k_prepass_box(KParams p) {
   int count = 0;
   bool edge = false;
   for (int cyy = cy0; cyy <= cy1 && cx0 <= cx1; ++cyy) {
-    const int a = p.cell_start[cyy * p.gx + cx0];
-    const int e = p.cell_start[cyy * p.gx + cx1 + 1];
+    const int a = cell_at(p, (int64_t)cyy * p.gx + cx0);
+    const int e = cell_at(p, (int64_t)cyy * p.gx + cx1 + 1);
     for (int base = a; base < e; base += 256) {
       __syncthreads();
       if (base + t < e) {

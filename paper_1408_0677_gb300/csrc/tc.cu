@@ -334,7 +334,7 @@ __device__ void tile_geometry(const KParams &p, int u0, int v0, int hgt, float c
     // r = h (Wendland), c h (truncated Gaussian), h sqrt(max m + gcut) (Gaussian)
     const float rs = p.weight == MLS_W_WENDLAND ? 1.f
                      : p.trunc > 0.0            ? (float)p.trunc
-                                                : sqrtf(p.tmax[(v0 >> 4) * p.tiles_x + (u0 >> 4)] + p.gcut);
+                                                : sqrtf(p.tmax[tile_i(p, (v0 >> 4) * p.tiles_x + (u0 >> 4))] + p.gcut);
     const double rad = p.h * (double)rs * (1.0 + 1e-5);
     const bool ax = lane < 2, upper = lane & 1;
     const double s = ax ? p.sx : p.sy, o = ax ? p.x0 : p.y0, g0 = ax ? p.gx0 : p.gy0;
@@ -365,8 +365,8 @@ struct PackIter {
 
 __device__ __forceinline__ void pack_row(const KParams &p, PackIter &it) {
   while (it.cy <= it.cy1) {
-    it.lo = p.cell_start[it.cy * p.gx + it.cx0];
-    it.hi = p.cell_start[it.cy * p.gx + it.cx1 + 1];
+    it.lo = cell_at(p, (int64_t)it.cy * p.gx + it.cx0);
+    it.hi = cell_at(p, (int64_t)it.cy * p.gx + it.cx1 + 1);
     if (it.hi > it.lo) break;
     ++it.cy;
   }
@@ -454,7 +454,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mls_tc(KParams p, int d0, int D
     // 16-row CTA would take the whole tile.
     const int slot = blockIdx.x;
     if (slot >= (int)*p.tile_count) return;
-    const int ht = p.tile_list[slot], tl = ht >> 1;
+    const int ht = (int)queue_i(p, p.tile_list[queue_i(p, slot)]), tl = ht >> 1;
     u0 = (tl % p.tiles_x) * 16;
     v0 = (tl / p.tiles_x) * 16 + (NACC == 1 ? (ht & 1) * 8 : 0);
   } else {
@@ -479,7 +479,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mls_tc(KParams p, int d0, int D
   // moment frame of the tile: the weighted centroid of the points near its
   // centre (from the prepass); the fit is solved in this frame
   const int tile = (v0 >> 4) * p.tiles_x + (u0 >> 4);
-  const float cxs = p.tcen[2 * tile], cys = p.tcen[2 * tile + 1];
+  const float cxs = p.tcen[2 * tile_i(p, tile)], cys = p.tcen[2 * tile_i(p, tile) + 1];
   if (warp == 8) tmem_alloc(smem_u32(tmem_slot), 512);
   if (warp == 9) tile_geometry(p, u0, v0, TH, cxs, cys, lane, geo);
   tc_fence_before();
@@ -517,11 +517,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_mls_tc(KParams p, int d0, int D
       const int r = lane & 15, c = lane & 15;
       float b = INFINITY;
       if (r < TH)
-        for (int cc = 0; cc < 16; ++cc) b = fminf(b, kLog2e * p.mstab[(size_t)(v0 + r) * stride + u0 + cc]);
+        for (int cc = 0; cc < 16; ++cc) b = fminf(b, kLog2e * p.mstab[pix_i(p, (int64_t)(v0 + r) * stride + u0 + cc)]);
       float a = INFINITY;
       for (int rr = 0; rr < TH; ++rr) {
         const float br = __shfl_sync(0xffffffffu, b, rr);
-        a = fminf(a, kLog2e * p.mstab[(size_t)(v0 + rr) * stride + u0 + c] - br);
+        a = fminf(a, kLog2e * p.mstab[pix_i(p, (int64_t)(v0 + rr) * stride + u0 + c)] - br);
       }
       sAB[lane] = (lane < 16) ? a : ((r < TH) ? b : 0.f);
       __syncwarp();
@@ -538,7 +538,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mls_tc(KParams p, int d0, int D
 #pragma unroll
     for (int a = 0; a < 2; ++a) {
       const int rr = r0 + 8 * a;
-      const float res = (rr < TH) ? kLog2e * p.mstab[(size_t)(v0 + rr) * (p.tiles_x * 16) + u0 + cown] -
+      const float res = (rr < TH) ? kLog2e * p.mstab[pix_i(p, (int64_t)(v0 + rr) * (p.tiles_x * 16) + u0 + cown)] -
                                         sAB[cown] - sAB[16 + rr]
                                   : 0.f;
       gcor[a] = ex2_approx(fminf(res, kResMax)) * weight_scale<FP16>();
@@ -636,7 +636,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mls_tc(KParams p, int d0, int D
       dy[a] = geo->row[q >> 4];
       const size_t pi = (size_t)v * (p.tiles_x * 16) + u;
       if (WK == MLS_W_GAUSS)
-        E[a] = kLog2e * (p.mstab[pi] - (dx[a] * dx[a] + dy[a] * dy[a]));
+        E[a] = kLog2e * (p.mstab[pix_i(p, pi)] - (dx[a] * dx[a] + dy[a] * dy[a]));
       else
         E[a] = dx[a] * dx[a] + dy[a] * dy[a];
     }
@@ -855,7 +855,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_mls_tc(KParams p, int d0, int D
           int r = q + 1;
           while (r < (int)nvalid && sl[r].gb == sl[r - 1].gb + 1) ++r;
           const uint32_t nb = (uint32_t)(r - q);
-          const int64_t blk = sl[q].gb;
+          // checked build: the copied blocks lie inside the point arrays
+          const int64_t blk = chk(p.err, sl[q].gb, nblk - nb + 1, SITE_BLOCK);
           bulk_g2s(dst + q * kXB * 4, p.xyb + blk * kXB, nb * kXB * 4, bar);
           bulk_g2s(dst + kPosFloats * 4 + q * fbb, p.fb + ((size_t)pass * nblk + blk) * (Dc * 8 + 4), nb * fbb,
                    bar);
@@ -929,8 +930,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_mls_tc(KParams p, int d0, int D
     // the pixel's stabiliser (Gaussian) and support count (Wendland,
     // truncated Gaussian), and the first staged levels and scales (below),
     // are fetched while the last MMAs drain
-    const float mst = (WK == MLS_W_WENDLAND) ? 0.f : p.mstab[pi];
-    const int cflag = (WK == MLS_W_WENDLAND || p.trunc > 0.0) ? p.cnt[pi] : 0;
+    const float mst = (WK == MLS_W_WENDLAND) ? 0.f : p.mstab[pix_i(p, pi)];
+    const int cflag = (WK == MLS_W_WENDLAND || p.trunc > 0.0) ? p.cnt[pix_i(p, pi)] : 0;
     // level rows padded with NaN to P entries, a power of two >= L
     int P = 1;
     while (P < p.L) P *= 2;
@@ -1015,13 +1016,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_mls_tc(KParams p, int d0, int D
         // first of two passes: queue the pixel's 8-row half of the tile once
         // for the split-weight pass (the other half keeps this pass's values)
         const int ht = 2 * tile + ((v >> 3) & 1);
-        if (atomicExch(&p.tile_mark[ht], 1) == 0) {
+        if (atomicExch(&p.tile_mark[queue_i(p, ht)], 1) == 0) {
           const unsigned int k = atomicAdd(p.retry_count, 1u);
-          p.retry_tiles[k] = ht;
+          p.retry_tiles[queue_i(p, k)] = ht;
         }
       } else {
         const unsigned int k = atomicAdd(p.relist_count, 1u);
-        p.relist[k] = (int)pix;
+        p.relist[list_i(p, k)] = (int)pix;
       }
     }
     if (primary && inside && nosup) {

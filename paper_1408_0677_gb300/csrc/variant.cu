@@ -147,8 +147,8 @@ __global__ __launch_bounds__(128) void k_mls_variant(KParams p, int tiles_x) {
   for (int r = 0; r < nr; ++r) {
     int64_t a0 = 0, a1 = p.n;
     if (binned) {
-      a0 = p.cell_start[(cy0 + r) * p.gx + cx0];
-      a1 = p.cell_start[(cy0 + r) * p.gx + cx1 + 1];
+      a0 = cell_at(p, (int64_t)(cy0 + r) * p.gx + cx0);
+      a1 = cell_at(p, (int64_t)(cy0 + r) * p.gx + cx1 + 1);
     }
     for (int64_t base = a0; base < a1; base += kVChunk) {
       const int cnt = (int)min((int64_t)kVChunk, a1 - base);
