@@ -39,7 +39,7 @@
 extern "C" {
 #endif
 
-#define MLS_ABI_VERSION 4
+#define MLS_ABI_VERSION 5
 
 typedef enum mls_status {
     MLS_OK = 0,
@@ -62,7 +62,11 @@ typedef enum mls_precision {
     MLS_P_FP64 = 0,        /* FP64 on CUDA cores; field is double */
     MLS_P_FP32 = 1,        /* FP32 on CUDA cores; field is float */
     MLS_P_BF16 = 2,        /* BF16 operands on tcgen05 tensor cores, FP32 accumulate */
-    MLS_P_FP16 = 3         /* FP16 operands on tcgen05 tensor cores, FP32 accumulate */
+    MLS_P_FP16 = 3,        /* FP16 operands on tcgen05 tensor cores, FP32 accumulate */
+    MLS_P_FP64_TC = 4      /* FP64-equivalent on tcgen05 tensor cores (weights and operands split
+                              into ten exact FP16 digits, exact FP32 partial sums, FP64 solve);
+                              field is double.  Gaussian (full sum) and Wendland weights, the
+                              polynomial fit (no truncated Gaussian, inverse distance or mappings) */
 } mls_precision;
 
 /* Per-pixel status bits (status image, one byte per pixel). */
@@ -165,7 +169,8 @@ enum {
     MLS_PATH_TENSOR = 1,      /* tcgen05 tensor-core kernel (FP16/BF16 operands, FP32 accumulators) */
     MLS_PATH_FP32 = 2,        /* FP32 CUDA-core kernel (FP32 renders, wide tiles, inverse distance) */
     MLS_PATH_FP64 = 3,        /* FP64 kernel (FP64 renders) */
-    MLS_PATH_VARIANT = 4      /* rigid / mean-displacement mapping kernel */
+    MLS_PATH_VARIANT = 4,     /* rigid / mean-displacement mapping kernel */
+    MLS_PATH_FP64_TC = 5      /* FP64-equivalent tensor-core kernel (MLS_P_FP64_TC) */
 };
 
 typedef struct mls_handle mls_handle;

@@ -12,7 +12,7 @@ import ctypes
 import numpy as np
 
 from . import _abi
-from ._abi import (MLS_P_BF16, MLS_P_FP16, MLS_P_FP32, MLS_P_FP64, MLS_W_GAUSS, MLS_W_INVDIST,  # noqa: F401
+from ._abi import (MLS_P_BF16, MLS_P_FP16, MLS_P_FP32, MLS_P_FP64, MLS_P_FP64_TC, MLS_W_GAUSS, MLS_W_INVDIST,  # noqa: F401
                    MLS_W_WENDLAND, MLS_BATCH_AUTOTUNE, MLS_V_POLY, MLS_V_RIGID, MLS_V_MEAN, MlsBatchStats, MlsDesc, MlsError, MlsStats, MlsView,
                    mls_abi_version, mls_bands, mls_batch_create, mls_batch_destroy, mls_batch_render,
                    mls_batch_sync, mls_create, mls_desc_default, mls_destroy, mls_last_error, mls_render,
@@ -20,7 +20,8 @@ from ._abi import (MLS_P_BF16, MLS_P_FP16, MLS_P_FP32, MLS_P_FP64, MLS_W_GAUSS, 
                    mls_sync, MlsRequest, MlsMapDesc, mls_space_map, MLS_MAP_LINES, MLS_MAP_DISCRETE,
                    MLS_MAP_DISCRETE_LINES, MLS_MAP_ADAPTIVE, MLS_MAP_GRADIENT, MLS_MAP_TEXTURE)
 
-PRECISIONS = {"fp64": MLS_P_FP64, "fp32": MLS_P_FP32, "bf16": MLS_P_BF16, "fp16": MLS_P_FP16}
+PRECISIONS = {"fp64": MLS_P_FP64, "fp32": MLS_P_FP32, "bf16": MLS_P_BF16, "fp16": MLS_P_FP16,
+              "fp64tc": MLS_P_FP64_TC}
 
 
 def _stream_ptr(stream):
@@ -139,7 +140,7 @@ class Renderer:
 
     @property
     def field_dtype(self):
-        return self.torch.float64 if self.desc.precision == MLS_P_FP64 else self.torch.float32
+        return self.torch.float64 if self.desc.precision in (MLS_P_FP64, MLS_P_FP64_TC) else self.torch.float32
 
     def render(self, W, H, view=(0.0, 0.0, 1.0, 1.0), levels=None, status=True, field=None, bands=None,
                status_out=None):
@@ -172,7 +173,7 @@ class Renderer:
         Supplied outputs must be C-contiguous numpy arrays of exactly the
         rendered shape and type (the library writes page-locked ones from the
         kernels and cannot check them itself)."""
-        dt = np.float64 if self.desc.precision == MLS_P_FP64 else np.float32
+        dt = np.float64 if self.desc.precision in (MLS_P_FP64, MLS_P_FP64_TC) else np.float32
         _check_host_out("field", field, (self.D, H, W), dt)
         _check_host_out("status_out", status_out, (H, W), np.uint8)
         _check_host_out("bands", bands, (self.D, H, W), np.uint8)
@@ -304,7 +305,7 @@ class Server:
         lev = None if levels is None else np.ascontiguousarray(levels, dtype=np.float64)
         bands = torch.empty((D, H, W), dtype=torch.uint8).pin_memory() if lev is not None else None
         st = torch.empty((H, W), dtype=torch.uint8).pin_memory() if status else None
-        fdt = torch.float64 if renderer.desc.precision == MLS_P_FP64 else torch.float32
+        fdt = torch.float64 if renderer.desc.precision in (MLS_P_FP64, MLS_P_FP64_TC) else torch.float32
         fld = torch.empty((D, H, W), dtype=fdt).pin_memory() if field else None
         req = MlsRequest(renderer.handle, MlsView(W, H, *view), lev.ctypes.data if lev is not None else None,
                          lev.shape[1] if lev is not None else 0, 0,

@@ -13,7 +13,7 @@ from . import build as _build
 
 MLS_OK, MLS_E_INVAL, MLS_E_NOMEM, MLS_E_CUDA, MLS_E_TIMEOUT, MLS_E_UNSUPPORTED = range(6)
 MLS_W_GAUSS, MLS_W_WENDLAND, MLS_W_INVDIST = range(3)
-MLS_P_FP64, MLS_P_FP32, MLS_P_BF16, MLS_P_FP16 = range(4)
+MLS_P_FP64, MLS_P_FP32, MLS_P_BF16, MLS_P_FP16, MLS_P_FP64_TC = range(5)
 MLS_ST_DEGREE_MASK = 0x03
 MLS_ST_NO_SUPPORT = 0x04
 MLS_ST_FP64_SOLVE = 0x08
@@ -46,7 +46,7 @@ class MlsStats(ctypes.Structure):
                 ("main_path", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
-MLS_PATH_NONE, MLS_PATH_TENSOR, MLS_PATH_FP32, MLS_PATH_FP64, MLS_PATH_VARIANT = 0, 1, 2, 3, 4
+MLS_PATH_NONE, MLS_PATH_TENSOR, MLS_PATH_FP32, MLS_PATH_FP64, MLS_PATH_VARIANT, MLS_PATH_FP64_TC = 0, 1, 2, 3, 4, 5
 
 
 class MlsBatchStats(ctypes.Structure):

@@ -26,8 +26,8 @@ CSRC = os.path.join(PKG, "csrc")
 OUT = os.path.join(PKG, "_build")
 LIB = os.path.join(OUT, "libmls.so")
 INCLUDE = os.path.join(ROOT, "include")
-SOURCES = ["mls_api.cu", "prep.cu", "prepass.cu", "plain.cu", "handover.cu", "tc.cu", "bands_noalloc.cu",
-           "variant.cu", "space_map.cu"]
+SOURCES = ["mls_api.cu", "prep.cu", "prepass.cu", "plain.cu", "handover.cu", "tc.cu", "tc64.cu",
+           "bands_noalloc.cu", "variant.cu", "space_map.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I" + INCLUDE, "-I" + CSRC]
 

@@ -114,6 +114,7 @@ struct KParams {
   const float *FT32;           // normalised values (f - cen) / scl, [D_pad][n_pad]
   const float *FR32;           // the same values point-major, [n_pad][D] (hand-over path)
   const float *fcen32, *fscl32;
+  const double *fcen64, *fscl64;   // value centre and half range per dimension (FP64)
   const double *x64, *y64;     // raw positions [n]
   const double *FT64;          // raw values [D][n]
   const float *xyb;            // tensor path: (x[8], y[8], pad[4]) per 8-point block, [n_pad/8][20]

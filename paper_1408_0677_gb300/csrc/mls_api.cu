@@ -256,6 +256,8 @@ static mlsk::KParams base_params(const mls_handle *h, const RenderCtx *c, const 
   p.FR32 = P.FR32;
   p.fcen32 = P.fcen32;
   p.fscl32 = P.fscl32;
+  p.fcen64 = P.fcen;
+  p.fscl64 = P.fscl;
   p.x64 = P.x64;
   p.y64 = P.y64;
   p.FT64 = P.FT64;
@@ -298,7 +300,7 @@ static mlsk::KParams base_params(const mls_handle *h, const RenderCtx *c, const 
   p.cnt = c->cnt;
   p.tcen = c->tcen;
   p.tmax = c->tmax;
-  p.gcut = (h->operand_cut && d.precision != MLS_P_FP64 && d.weight == MLS_W_GAUSS && !(d.support > 0.0) &&
+  p.gcut = (h->operand_cut && !field_is_fp64(d.precision) && d.weight == MLS_W_GAUSS && !(d.support > 0.0) &&
             d.variant == MLS_V_POLY)
                ? mlsk::kGaussOperandCut
                : 0.f;
@@ -348,7 +350,7 @@ mls_status mls_create(const mls_desc *desc, const double *xy, const double *F, i
   if (d.D < 1 || d.D > 256) return fail(MLS_E_INVAL, "D must be in [1, 256]");
   if (d.degree < 0 || d.degree > 2) return fail(MLS_E_INVAL, "degree must be 0, 1 or 2");
   if (d.weight < MLS_W_GAUSS || d.weight > MLS_W_INVDIST) return fail(MLS_E_INVAL, "unknown weight");
-  if (d.precision < MLS_P_FP64 || d.precision > MLS_P_FP16) return fail(MLS_E_INVAL, "unknown precision");
+  if (d.precision < MLS_P_FP64 || d.precision > MLS_P_FP64_TC) return fail(MLS_E_INVAL, "unknown precision");
   if (!finite_pos(d.h)) return fail(MLS_E_INVAL, "h must be finite and > 0");
   if (d.weight == MLS_W_INVDIST && !finite_pos(d.alpha)) return fail(MLS_E_INVAL, "alpha must be finite and > 0");
   if (!finite_pos(d.cond_fp64)) return fail(MLS_E_INVAL, "cond_fp64 must be > 0");
@@ -361,6 +363,10 @@ mls_status mls_create(const mls_desc *desc, const double *xy, const double *F, i
   if (!(d.support >= 0.0 && d.support <= 1e6)) return fail(MLS_E_INVAL, "support must be 0 or in (0, 1e6]");
   if (d.support > 0.0 && d.weight != MLS_W_GAUSS)
     return fail(MLS_E_INVAL, "support (the truncated Gaussian) applies to the Gaussian weight only");
+  if (d.precision == MLS_P_FP64_TC &&
+      (d.weight == MLS_W_INVDIST || d.support > 0.0 || d.variant != MLS_V_POLY))
+    return fail(MLS_E_UNSUPPORTED, "MLS_P_FP64_TC takes the full-sum Gaussian and the Wendland weight, "
+                                   "polynomial fit only");
 
   mls_handle *h = new mls_handle();
   h->desc = d;
@@ -467,7 +473,7 @@ static mls_status render_prepare(mls_handle *h, RenderCtx *c, const mls_view *vi
   if ((s = check_levels(levels, bands ? L : 0, h->desc.D)) != MLS_OK) return s;
   const int W = view->W, H = view->H;
   const size_t plane = (size_t)W * H;
-  const bool fp64 = h->desc.precision == MLS_P_FP64;
+  const bool fp64 = field_is_fp64(h->desc.precision);
   const size_t esz = fp64 ? sizeof(double) : sizeof(float);
   if ((s = ensure_scratch(c, W, H, st)) != MLS_OK) return s;
   if (bands && L > 0 && (s = upload_levels(h, c, levels, L, st)) != MLS_OK) return s;
@@ -530,6 +536,23 @@ static mls_status render_enqueue(mls_handle *h, RenderCtx *c, const mlsk::KParam
     if (timing) MLS_CUDA_TRY(cudaEventRecord(h->evk1, st));
     launches += 1;
     h->last_path = MLS_PATH_VARIANT;
+  } else if (h->desc.precision == MLS_P_FP64_TC) {
+    // FP64-equivalent moments on the tensor cores; pixels whose support count
+    // could cross a degree threshold are finished by the FP64 kernel
+    launch_prepass(p, st);
+    launches += 1;
+    if (timing) MLS_CUDA_TRY(cudaEventRecord(h->evk0, st));
+    h->last_path = MLS_PATH_FP64_TC;
+    int nl = 0;
+    if ((s = launch_tc64(p, st, &nl)) != MLS_OK) return s;
+    launches += nl;
+    if (timing) MLS_CUDA_TRY(cudaEventRecord(h->evk1, st));
+    mlsk::KParams q = p;
+    q.list = c->relist;
+    q.list_count = c->counters;
+    q.list_cap = (int64_t)plane;
+    launch_f64(q, 0, st);
+    launches += 1;
   } else if (fp64) {
     if (timing) MLS_CUDA_TRY(cudaEventRecord(h->evk0, st));
     h->last_path = MLS_PATH_FP64;
@@ -622,7 +645,7 @@ mls_status mls_render(mls_handle *h, const mls_view *view, void *field, uint8_t 
   h->launches += nl;
   if (!on_device) {
     const size_t plane = (size_t)view->W * view->H;
-    const size_t esz = h->desc.precision == MLS_P_FP64 ? sizeof(double) : sizeof(float);
+    const size_t esz = field_is_fp64(h->desc.precision) ? sizeof(double) : sizeof(float);
     if (!h->ctx.direct_out) {
       MLS_CUDA_TRY(cudaMemcpyAsync(field, p.field, plane * h->desc.D * esz, cudaMemcpyDeviceToHost, st));
       if (status) MLS_CUDA_TRY(cudaMemcpyAsync(status, p.status, plane, cudaMemcpyDeviceToHost, st));
@@ -650,7 +673,7 @@ mls_status mls_bands(mls_handle *h, const mls_view *view, const void *field, con
   cudaStream_t st = (cudaStream_t)stream;
   h->stream = st;
   const size_t plane = (size_t)view->W * view->H;
-  const bool fp64 = h->desc.precision == MLS_P_FP64;
+  const bool fp64 = field_is_fp64(h->desc.precision);
   const size_t esz = fp64 ? sizeof(double) : sizeof(float);
   if ((s = ensure_scratch(&h->ctx, view->W, view->H, st)) != MLS_OK) return s;
   if (L > 0 && (s = upload_levels(h, &h->ctx, levels, L, st)) != MLS_OK) return s;
@@ -1051,7 +1074,7 @@ namespace mlsi {
 
 static size_t out_bytes(const mls_handle *h, const mls_view &v, size_t *fbytes, size_t *sbytes) {
   const size_t plane = (size_t)v.W * v.H;
-  const size_t esz = h->desc.precision == MLS_P_FP64 ? sizeof(double) : sizeof(float);
+  const size_t esz = field_is_fp64(h->desc.precision) ? sizeof(double) : sizeof(float);
   *fbytes = (plane * h->desc.D * esz + 255) / 256 * 256;
   *sbytes = (plane + 255) / 256 * 256;
   return *fbytes + *sbytes + plane * h->desc.D;
@@ -1083,7 +1106,7 @@ static mls_status serve_start(ServeSlot &sl) {
   int64_t nl = 0;
   if ((s = render_enqueue(h, &sl.ctx, p, sl.st, false, &nl)) != MLS_OK) return s;
   const size_t plane = (size_t)r.view.W * r.view.H;
-  const size_t esz = h->desc.precision == MLS_P_FP64 ? sizeof(double) : sizeof(float);
+  const size_t esz = field_is_fp64(h->desc.precision) ? sizeof(double) : sizeof(float);
   if (r.field) MLS_CUDA_TRY(cudaMemcpyAsync(r.field, field_d, plane * h->desc.D * esz, cudaMemcpyDeviceToHost, sl.st));
   if (r.status) MLS_CUDA_TRY(cudaMemcpyAsync(r.status, status_d, plane, cudaMemcpyDeviceToHost, sl.st));
   if (r.bands && bands_d)

@@ -100,6 +100,11 @@ void launch_handover(const mlsk::KParams &p, const int *list, const unsigned int
 // tc.cu
 mls_status launch_tc(const mlsk::KParams &p, int fp16, int wsplit, cudaStream_t st, int *nlaunch);
 int tc_dims_per_pass(int D, int degree);
+// tc64.cu: FP64-equivalent moments on the tensor cores (MLS_P_FP64_TC)
+mls_status launch_tc64(const mlsk::KParams &p, cudaStream_t st, int *nlaunch);
+
+// Renders whose field is double: FP64 and its tensor-core emulation.
+inline bool field_is_fp64(int precision) { return precision == MLS_P_FP64 || precision == MLS_P_FP64_TC; }
 
 // errors (mls_api.cu)
 mls_status fail(mls_status s, const std::string &msg);

@@ -23,7 +23,14 @@ at the end of the session.  Reduced precisions add the oracle's own bound
 to their 1e-3."""
 import numpy as np
 
-TOL = {"fp64": 1e-10, "fp32": 1e-3, "fp16": 1e-3, "bf16": 1e-3}
+TOL = {"fp64": 1e-10, "fp64tc": 1e-10, "fp32": 1e-3, "fp16": 1e-3, "bf16": 1e-3}
+# The FP64 emulation on tensor cores (fp64tc) has no long summation chain
+# (its digit products are summed exactly in FP32); its error model is a
+# relative error of 2^-40 on every weight and operand entry (double-float
+# weights and products, 60-bit fixed-point digits), which enters the bound
+# like a chain of 2^-40 / u = 8192 additions, plus 64 for the FP64
+# combination of the diagonals, the frame shift and the solve.
+CHAIN_FP64TC = 8192 + 64
 U = 2.0 ** -53
 # one line per comparison: (test, precision, pixels compared, pixels with an
 # allowance above the tolerance, largest error / range, largest error / allowance)
@@ -49,8 +56,9 @@ def allowance(wl, ref, precision):
     cnt = ref.count.astype(np.float64)[:, None]
     b_or = ((cnt + 12) * U * ref.ecoef_sum + ref.ecoef_fix) / S[None, :]
     b_or = np.where(np.isfinite(b_or), b_or, 0.0)
-    if precision == "fp64":
-        chain_gpu = np.minimum(cnt, np.ceil(wl.n / 32.0)) + 5
+    if precision in ("fp64", "fp64tc"):
+        chain_gpu = (np.minimum(cnt, np.ceil(wl.n / 32.0)) + 5 if precision == "fp64"
+                     else np.full_like(cnt, CHAIN_FP64TC))
         b_gpu = ((chain_gpu + 12) * U * ref.ecoef_sum + ref.ecoef_fix) / S[None, :]
         b_gpu = np.where(np.isfinite(b_gpu), b_gpu, 0.0)
         return np.maximum(tol, b_or + b_gpu)
@@ -84,7 +92,7 @@ def gpu_render(wl, precision, device_inputs=True, levels=True, operand_cut=True,
 # rounding bound exceeds 1e-10 of the range; for the reduced precisions,
 # pixels where the oracle's own bound exceeds a tenth of 1e-3 (far from the
 # data, where the fit extrapolates from a few dominant weights)
-MAX_ALLOW_FRAC = {"fp64": 0.05, "fp32": 0.10, "fp16": 0.10, "bf16": 0.10}
+MAX_ALLOW_FRAC = {"fp64": 0.05, "fp64tc": 0.05, "fp32": 0.10, "fp16": 0.10, "bf16": 0.10}
 
 
 def compare(wl, res, ref, precision, pixels=None, check_bands=True, check_status=True, max_allow_frac=None):
@@ -113,7 +121,7 @@ def compare(wl, res, ref, precision, pixels=None, check_bands=True, check_status
     err = np.abs(f - ref.field) / S[None, :]
     err = np.where(nan_or, 0.0, err)
     allow = allowance(wl, ref, precision)
-    widened = ((allow > tol * (1.0 if precision == "fp64" else 1.1)) & ~nan_or).any(axis=1) & ok
+    widened = ((allow > tol * (1.0 if precision in ("fp64", "fp64tc") else 1.1)) & ~nan_or).any(axis=1) & ok
     n_allow = int(widened.sum())
     npx = int(ok.sum())
     bad = (err > allow) & ok[:, None]

@@ -69,7 +69,7 @@ int main(void) {
 
 
 def test_abi_version_and_defaults(lib):
-    assert _abi.mls_abi_version() == 4
+    assert _abi.mls_abi_version() == 5
     d = _abi.mls_desc_default()
     assert d.cond_fp64 == 1e6 and d.rcond_degenerate == 1e-12 and d.precision == _abi.MLS_P_FP32
     assert d.variant == _abi.MLS_V_POLY and d.support == 0.0
