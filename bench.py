@@ -355,17 +355,20 @@ def _err_detail(wl, fields, pix, res, precision):
     for nm, f in fields.items():
         d = np.where(fin, np.abs(f[:, ok] - ref) / S[:, None], 0.0)
         out[nm] = float(d.max()) if d.size else None
-        if nm == "fp64" and res.ecoef_sum is not None:
+        if nm in ("fp64", "fp64tc") and res.ecoef_sum is not None:
             u = 2.0 ** -53
             cnt = res.count[ok].astype(np.float64)[None, :]
             es, ef = res.ecoef_sum[ok].T, res.ecoef_fix[ok].T
-            chain_gpu = np.minimum(cnt, np.ceil(wl.n / 32.0)) + 5
+            # the FP64 kernel's summation chain, or the emulation's error model
+            # (2^-40 per entry: like 8192 additions, plus 64)
+            chain_gpu = (np.minimum(cnt, np.ceil(wl.n / 32.0)) + 5 if nm == "fp64"
+                         else np.full_like(cnt, 8192 + 64))
             b = ((cnt + 12 + chain_gpu + 12) * u * es + 2 * ef) / S[:, None]
             b = np.where(fin, b, 0.0)
             wide = (b > 1e-10).any(axis=0)
-            out["fp64_well_conditioned"] = float(d[:, ~wide].max()) if (~wide).any() else None
-            out["fp64_pixels_beyond_1e-10_bound"] = int(wide.sum())
-            out["fp64_max_err_over_bound"] = float((d / np.maximum(b, 1e-10)).max()) if d.size else None
+            out[nm + "_well_conditioned"] = float(d[:, ~wide].max()) if (~wide).any() else None
+            out[nm + "_pixels_beyond_1e-10_bound"] = int(wide.sum())
+            out[nm + "_max_err_over_bound"] = float((d / np.maximum(b, 1e-10)).max()) if d.size else None
     return out
 
 
@@ -394,7 +397,7 @@ def run_ours(args):
     sptr = stream.cuda_stream
     xy_d = torch.from_numpy(wl.xy).to(dev)
     F_d = torch.from_numpy(wl.F).to(dev)
-    fdt = torch.float64 if args.precision == "fp64" else torch.float32
+    fdt = torch.float64 if args.precision in ("fp64", "fp64tc") else torch.float32
     field = torch.empty((D, H, W), dtype=fdt, device=dev)
     status = torch.empty((H, W), dtype=torch.uint8, device=dev)
     bands = torch.empty((D, H, W), dtype=torch.uint8, device=dev)
@@ -532,6 +535,19 @@ def run_ours(args):
     if path == _abi.MLS_PATH_TENSOR:
         peak = peaks.get("bf16_tflops", 1900.0)       # FP16 and BF16 share the dense tensor rate
         roof = {"bound": "tensor", "peak_source": f"{src} bf16 burst (fp16 dense rate equal)", "kernel": "k_mls_tc"}
+    elif path == _abi.MLS_PATH_FP64_TC:
+        # executed tensor work: 55 digit-pair products of 48 columns (2 flop
+        # each) per visited pair and value pass
+        passes = -(-D // ((48 - 16) // k_terms))
+        exec_pair = 55 * 2 * 48 * passes
+        peak = peaks.get("bf16_tflops", 1900.0)
+        roof = {"bound": "tensor", "peak_source": f"{src} bf16 burst (fp16 dense rate equal)", "kernel": "k_mls_tc64",
+                "executed_flops_per_pair": exec_pair,
+                "fp64_equivalent_tflops": flop_pair * pairs_visited / (k_ms * 1e-3) / 1e12,
+                "fp64_nominal_tflops": FP64_NOMINAL_TFLOPS}
+        flop_pair = exec_pair
+        flops = exec_pair * pairs_visited
+        achieved = flops / (k_ms * 1e-3) / 1e12
     elif path == _abi.MLS_PATH_FP64:
         peak = FP64_NOMINAL_TFLOPS
         roof = {"bound": "alu", "peak_source": "nominal GB300 FP64 rate", "kernel": "k_mls_f64"}
@@ -551,12 +567,12 @@ def run_ours(args):
             pix = np.arange(W * H, dtype=np.int64)      # every pixel of the 256 x 256 grid
         if pix is None:
             pix, res = last
-            if args.precision == "fp64":
+            if args.precision in ("fp64", "fp64tc"):
                 res = oracle.mls(wl.xy, wl.F, wl.degree, wl.weight, wl.h, W, H, pixels=pix, trunc=wl.trunc,
                                  threads=os.cpu_count() or 1, ebound=True)
         else:
             res = oracle.mls(wl.xy, wl.F, wl.degree, wl.weight, wl.h, W, H, pixels=pix, trunc=wl.trunc,
-                             threads=os.cpu_count() or 1, ebound=args.precision == "fp64")
+                             threads=os.cpu_count() or 1, ebound=args.precision in ("fp64", "fp64tc"))
         pix_t = torch.from_numpy(np.asarray(pix, np.int64)).to(dev)
         fs = {k: v.reshape(D, -1)[:, pix_t].double().cpu().numpy() for k, v in samples.items()}
         err = _err_detail(wl, fs, pix, res, args.precision)
@@ -580,7 +596,7 @@ def run_ours(args):
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                     "ms_per_step": e2e_ms / args.steps},
             "latency_ms": lat, "plain_fp32": plain,
-            "err_vs_oracle": err, "tolerance": 1e-3 if args.precision != "fp64" else 1e-10,
+            "err_vs_oracle": err, "tolerance": 1e-10 if args.precision in ("fp64", "fp64tc") else 1e-3,
             "roofline": roof, "cpu_baseline": cpu, "clocks": clocks,
             "gpu_launches": int(launches),
             "recompute": {"handed_over_pixels": int(handed), "fp64_pixels": int(handed64),
@@ -1068,7 +1084,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default=None, choices=["fp16", "bf16", "fp32", "fp64"],
+    ap.add_argument("--precision", default=None, choices=["fp16", "bf16", "fp32", "fp64", "fp64tc"],
                     help="default: fp16, or fp64 for the wine-shaped workload (the FP64 configuration)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--weight-split", type=int, default=None, choices=[0, 1, 2])

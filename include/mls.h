@@ -66,7 +66,8 @@ typedef enum mls_precision {
     MLS_P_FP64_TC = 4      /* FP64-equivalent on tcgen05 tensor cores (weights and operands split
                               into ten exact FP16 digits, exact FP32 partial sums, FP64 solve);
                               field is double.  Gaussian (full sum) and Wendland weights, the
-                              polynomial fit (no truncated Gaussian, inverse distance or mappings) */
+                              polynomial fit (no truncated Gaussian, inverse distance or mappings);
+                              views whose 16-pixel tile spans more than 4 h take the FP64 kernel */
 } mls_precision;
 
 /* Per-pixel status bits (status image, one byte per pixel). */

@@ -536,6 +536,15 @@ static mls_status render_enqueue(mls_handle *h, RenderCtx *c, const mlsk::KParam
     if (timing) MLS_CUDA_TRY(cudaEventRecord(h->evk1, st));
     launches += 1;
     h->last_path = MLS_PATH_VARIANT;
+  } else if (h->desc.precision == MLS_P_FP64_TC &&
+             kTile * fmax(fabs(p.sx), fabs(p.sy)) / h->desc.h > kTileFrameMaxH) {
+    // tiles too wide for one moment frame: the FP64 kernel (each pixel in
+    // its own frame)
+    if (timing) MLS_CUDA_TRY(cudaEventRecord(h->evk0, st));
+    h->last_path = MLS_PATH_FP64;
+    launch_f64(p, (int64_t)plane, st);
+    if (timing) MLS_CUDA_TRY(cudaEventRecord(h->evk1, st));
+    launches += 1;
   } else if (h->desc.precision == MLS_P_FP64_TC) {
     // FP64-equivalent moments on the tensor cores; pixels whose support count
     // could cross a degree threshold are finished by the FP64 kernel
@@ -544,7 +553,9 @@ static mls_status render_enqueue(mls_handle *h, RenderCtx *c, const mlsk::KParam
     if (timing) MLS_CUDA_TRY(cudaEventRecord(h->evk0, st));
     h->last_path = MLS_PATH_FP64_TC;
     int nl = 0;
-    if ((s = launch_tc64(p, st, &nl)) != MLS_OK) return s;
+    mlsk::KParams pt = p;
+    pt.visited = c->visited;
+    if ((s = launch_tc64(pt, st, &nl)) != MLS_OK) return s;
     launches += nl;
     if (timing) MLS_CUDA_TRY(cudaEventRecord(h->evk1, st));
     mlsk::KParams q = p;

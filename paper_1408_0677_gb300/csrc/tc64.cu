@@ -26,6 +26,10 @@
 //     FP64 degree policy and solve of the definition (Section 3.3: the
 //     weighted least-squares fit evaluated at the pixel).
 //
+// The tile frame is shared by the 16 x 8 pixels, so the tile must be narrow
+// compared with h: renders whose 16-pixel tile spans more than 4 h take the
+// FP64 kernel instead (the same rule as the reduced-precision path).
+//
 // One CTA of 128 threads (one per pixel) works one tile, stage by stage:
 // digits of 64 points are written to shared memory, one thread issues the
 // MMAs of the first five weight digits, then of the last five (the weight
@@ -191,7 +195,10 @@ __global__ void __launch_bounds__(kThr64, 1) k_mls_tc64(KParams p, int d0, int D
 
   const int u0 = blockIdx.x * 16, v0 = blockIdx.y * 8;
   const int tile = (v0 >> 4) * p.tiles_x + (u0 >> 4);
-  const float cxs = p.tcen[2 * tile_i(p, tile)], cys = p.tcen[2 * tile_i(p, tile) + 1];
+  // the moment frame: the tile's geometric centre, which keeps every pixel's
+  // offset |delta| at most half the tile (the shift to the pixel frame
+  // cancels terms of size |delta|^4 times the moments)
+  const double ox = p.x0 + (u0 + 8) * p.sx, oy = p.y0 + (v0 + 4) * p.sy;
   const int u = u0 + (t & 15), v = v0 + (t >> 4);
   const bool inside = (u < p.W) && (v < p.H);
   const size_t pi = (size_t)pix_i(p, (int64_t)v * (p.tiles_x * 16) + u);
@@ -234,11 +241,13 @@ __global__ void __launch_bounds__(kThr64, 1) k_mls_tc64(KParams p, int d0, int D
     s_rpre[nrow] = total;
     s_misc[0] = nrow;
     s_misc[1] = total;
+    // pixel-point pairs this tile visits (once, in the first value pass)
+    if (p.visited && d0 == 0 && total) atomicAdd(p.visited, (unsigned long long)total * 128ull);
     // tile-frame extent of the visited cells (scaled by 1/h), with a margin
-    const double ex0 = (p.gx0 + cx0 * p.cell - p.ctr_x) * p.inv_s - cxs;
-    const double ex1 = (p.gx0 + (cx1 + 1) * p.cell - p.ctr_x) * p.inv_s - cxs;
-    const double ey0 = (p.gy0 + cy0 * p.cell - p.ctr_y) * p.inv_s - cys;
-    const double ey1 = (p.gy0 + (cy1 + 1) * p.cell - p.ctr_y) * p.inv_s - cys;
+    const double ex0 = (p.gx0 + cx0 * p.cell - ox) * p.inv_s;
+    const double ex1 = (p.gx0 + (cx1 + 1) * p.cell - ox) * p.inv_s;
+    const double ey0 = (p.gy0 + cy0 * p.cell - oy) * p.inv_s;
+    const double ey1 = (p.gy0 + (cy1 + 1) * p.cell - oy) * p.inv_s;
     s_bound[0] = fmax(fabs(ex0), fabs(ex1)) * (1.0 + 1e-6) + 1e-6;
     s_bound[1] = fmax(fabs(ey0), fabs(ey1)) * (1.0 + 1e-6) + 1e-6;
   }
@@ -249,9 +258,9 @@ __global__ void __launch_bounds__(kThr64, 1) k_mls_tc64(KParams p, int d0, int D
   const int total = s_misc[1], nrow = s_misc[0];
   const double bx = s_bound[0], by = s_bound[1];
 
-  // this thread's pixel offset from the tile frame (scaled by 1/h)
-  const double dpx = (p.x0 + (u + 0.5) * p.sx - p.ctr_x) * p.inv_s - (double)cxs;
-  const double dpy = (p.y0 + (v + 0.5) * p.sy - p.ctr_y) * p.inv_s - (double)cys;
+  // this thread's pixel offset from the frame origin (scaled by 1/h)
+  const double dpx = (p.x0 + (u + 0.5) * p.sx - ox) * p.inv_s;
+  const double dpy = (p.y0 + (v + 0.5) * p.sy - oy) * p.inv_s;
   const df32 dpx32{(float)dpx, (float)(dpx - (double)(float)dpx)};
   const df32 dpy32{(float)dpy, (float)(dpy - (double)(float)dpy)};
   const float mst = (WK == MLS_W_WENDLAND) ? 0.f : p.mstab[pi];
@@ -303,9 +312,10 @@ __global__ void __launch_bounds__(kThr64, 1) k_mls_tc64(KParams p, int d0, int D
         int r = 0;
         while (r + 1 < nrow && s_rpre[r + 1] <= kidx) ++r;
         i = s_rstart[r] + (kidx - s_rpre[r]);
-        const df32 x = df_diff(p.xs[i], p.xs_lo[i], cxs, 0.f);
-        const df32 y = df_diff(p.ys[i], p.ys_lo[i], cys, 0.f);
-        pt = make_float4(x.hi, x.lo, y.hi, y.lo);
+        // offset from the tile frame's origin in FP64 (the raw position minus
+        // an origin near the point, then scaled by 1/h), as double-float
+        const double xd = (p.x64[i] - ox) * p.inv_s, yd = (p.y64[i] - oy) * p.inv_s;
+        pt = make_float4((float)xd, (float)(xd - (double)(float)xd), (float)yd, (float)(yd - (double)(float)yd));
       }
       s_pt[t] = pt;
       for (int dd = 0; dd < Dc; ++dd) {
