@@ -308,7 +308,10 @@ mls_status prep_points(mls_handle *h, const double *xy, const double *F, cudaStr
   // hand-over path visits only the cells within its cut radius; the full-sum
   // kernels read every point and do not depend on the order)
   if (d.weight != MLS_W_INVDIST) {
-    double cell = d.h;
+    // cells of h; for the Wendland weight h/2: a tile and the pixels it
+    // holds visit the cells within h of them, and half-size cells follow
+    // the union of their support discs more closely (fewer zero weights)
+    double cell = d.weight == MLS_W_WENDLAND ? 0.5 * d.h : d.h;
     const double ex = hi[0] - lo[0], ey = hi[1] - lo[1];
     // keep the grid below 16M cells
     while ((floor(ex / cell) + 1) * (floor(ey / cell) + 1) > 16.0e6) cell *= 2.0;
