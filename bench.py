@@ -798,13 +798,13 @@ def run_serve(args):
             collect()
             time.sleep(0.0005)
         wall = time.perf_counter() - t0
-        arrived = nreq / arrivals[-1]          # the rate the drawn arrivals actually offered
+        arrived = float(nreq / arrivals[-1])   # the rate the drawn arrivals actually offered
         return {"offered_per_s": rate, "arrived_per_s": arrived, "requests_per_s": nreq / wall, "wall_s": wall,
                 "px_dims_per_s": px_dims / wall,
                 "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
                 "queued_ms": {"p50": float(np.percentile(queued, 50)), "p99": float(np.percentile(queued, 99))},
                 "device_ms": {"p50": float(np.percentile(dev_ms, 50)), "p99": float(np.percentile(dev_ms, 99))},
-                "sustained": nreq / wall >= 0.9 * arrived}
+                "sustained": bool(nreq / wall >= 0.9 * arrived)}
 
     rates = sorted({float(x) for x in args.rates.split(",")} | {args.rate})
     runs = [one_rate(rt) for rt in rates]

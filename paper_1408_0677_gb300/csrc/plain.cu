@@ -265,10 +265,21 @@ __device__ __forceinline__ T warp_sum(T v) {
   return v;
 }
 
+// Per-lane cache of the points with a positive weight (index and weight),
+// filled while the first DC dimensions are summed: the later dimension
+// chunks of the same pixel read it instead of recomputing every candidate's
+// distance and weight (the moments and the degree policy do not change with
+// the dimensions).  Bit-identical: each lane sums its points in the same order.
+constexpr int kF64Slots = 24;                  // cache entries per lane
+constexpr int kF64SmemBytes = 8 * kF64Slots * 32 * (4 + 8);
+
 template <int DEG, int WK, typename OutT>
 __global__ __launch_bounds__(256) void k_mls_f64(KParams p, int64_t npix_all) {
   constexpr int NM = n_moments(DEG), DC = kF64DC;
   const int lane = threadIdx.x & 31;
+  extern __shared__ __align__(16) unsigned char f64_smem[];
+  double *c_w = (double *)f64_smem + (size_t)(threadIdx.x >> 5) * kF64Slots * 32;            // [slot][lane]
+  int *c_i = (int *)(f64_smem + (size_t)8 * kF64Slots * 32 * 8) + (size_t)(threadIdx.x >> 5) * kF64Slots * 32;
   const int64_t warp0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   const int64_t npix = p.list ? (int64_t)((int64_t)*p.list_count < p.list_cap ? (int64_t)*p.list_count : p.list_cap)
@@ -325,18 +336,55 @@ __global__ __launch_bounds__(256) void k_mls_f64(KParams p, int64_t npix_all) {
     }
     const bool coincident = (WK == MLS_W_INVDIST) && (m == 0.0);
     uint8_t st = MLS_ST_RECOMPUTED;
+    // moments, count and policy of the first chunk, reused by the later ones
+    // when every lane's positive-weight points fit its cache (not for the
+    // inverse distance, whose coincident points take the other branch)
+    double S[15];
+    int64_t count = 0;
+    int ncache = 0;
+    bool cached = false;
+    int used_saved = -1, k_saved = 1;
+    double sdg_saved[6], inv0_saved[6];
     for (int d0 = 0; d0 < p.D; d0 += DC) {
-      double S[15], R[6][DC], csum[DC];
-      int64_t count = 0, ccnt = 0;
+      double R[6][DC], csum[DC];
+      int64_t ccnt = 0;
+      const bool fresh = !cached;
+      if (fresh) {
+        count = 0;
+        ncache = 0;
 #pragma unroll
-      for (int j = 0; j < 15; ++j) S[j] = 0.0;
+        for (int j = 0; j < 15; ++j) S[j] = 0.0;
+      }
 #pragma unroll
       for (int a = 0; a < 6; ++a)
 #pragma unroll
         for (int dd = 0; dd < DC; ++dd) R[a][dd] = 0.0;
 #pragma unroll
       for (int dd = 0; dd < DC; ++dd) csum[dd] = 0.0;
-      for (int r = 0; r < nr; ++r) {
+      if (!fresh) {
+        // the cached points: same order, same weights and basis terms
+        for (int k = 0; k < ncache; ++k) {
+          const double w = c_w[k * 32 + lane];
+          const int64_t i = c_i[k * 32 + lane];
+          const double dx = __dadd_rn(p.x64[i], -px), dy = __dadd_rn(p.y64[i], -py);
+          const double ddx = dx * inv_s, ddy = dy * inv_s;
+          double mo[6];
+          mo[0] = 1.0;
+          if (NM > 1) {
+            mo[1] = ddx; mo[2] = ddy; mo[3] = ddx * ddx; mo[4] = ddx * ddy; mo[5] = ddy * ddy;
+          }
+          double fv[DC];
+#pragma unroll
+          for (int dd = 0; dd < DC; ++dd) fv[dd] = (d0 + dd < p.D) ? p.FT64[(size_t)(d0 + dd) * n + i] : 0.0;
+#pragma unroll
+          for (int a = 0; a < n_terms(DEG); ++a) {
+            const double wb = w * mo[a];
+#pragma unroll
+            for (int dd = 0; dd < DC; ++dd) R[a][dd] += wb * fv[dd];
+          }
+        }
+      }
+      for (int r = 0; r < nr && fresh; ++r) {
         const int64_t a0 = (binned || reach) ? cell_at(p, (int64_t)(cy0 + r) * p.gx + cx0) : 0;
         const int64_t a1 = (binned || reach) ? cell_at(p, (int64_t)(cy0 + r) * p.gx + cx1 + 1) : n;
         for (int64_t i = a0 + lane; i < a1; i += 32) {
@@ -380,6 +428,11 @@ __global__ __launch_bounds__(256) void k_mls_f64(KParams p, int64_t npix_all) {
             }
           }
           if (w == 0.0) continue;
+          if (ncache < kF64Slots) {
+            c_w[ncache * 32 + lane] = w;
+            c_i[ncache * 32 + lane] = (int)i;
+          }
+          ++ncache;
           const double ddx = dx * inv_s, ddy = dy * inv_s;
           double mo[15];
           mo[0] = 1.0;
@@ -404,14 +457,16 @@ __global__ __launch_bounds__(256) void k_mls_f64(KParams p, int64_t npix_all) {
           }
         }
       }
+      if (fresh) {
 #pragma unroll
-      for (int j = 0; j < NM; ++j) S[j] = warp_sum(S[j]);
+        for (int j = 0; j < NM; ++j) S[j] = warp_sum(S[j]);
+        count = warp_sum(count);
+        if (WK == MLS_W_GAUSS && !binned) count = n;   // every point has positive weight
+      }
 #pragma unroll
       for (int a = 0; a < n_terms(DEG); ++a)
 #pragma unroll
         for (int dd = 0; dd < DC; ++dd) R[a][dd] = warp_sum(R[a][dd]);
-      count = warp_sum(count);
-      if (WK == MLS_W_GAUSS && !binned) count = n;   // every point has positive weight
       if (WK == MLS_W_INVDIST) {
         ccnt = warp_sum(ccnt);
 #pragma unroll
@@ -425,6 +480,16 @@ __global__ __launch_bounds__(256) void k_mls_f64(KParams p, int64_t npix_all) {
         for (int dd = 0; dd < DC; ++dd) out[dd] = csum[dd] / (double)ccnt;
         used = 0;
         st |= MLS_ST_COINCIDENT;
+      } else if (!fresh) {
+        used = used_saved;
+        if (used >= 0) {
+#pragma unroll
+          for (int dd = 0; dd < DC; ++dd) {
+            double acc = 0.0;
+            for (int c = 0; c < k_saved; ++c) acc += sdg_saved[0] * inv0_saved[c] * sdg_saved[c] * R[c][dd];
+            out[dd] = acc;
+          }
+        }
       } else {
         for (int deg = DEG; deg >= 0 && used < 0; --deg) {
           const int k = n_terms(deg);
@@ -489,8 +554,16 @@ __global__ __launch_bounds__(256) void k_mls_f64(KParams p, int64_t npix_all) {
             out[dd] = acc;
           }
           used = deg;
+          k_saved = k;
+          for (int c = 0; c < k; ++c) {
+            sdg_saved[c] = sdg[c];
+            inv0_saved[c] = Inv[c][0];
+          }
         }
+        used_saved = used;
       }
+      // the later chunks may read the cache when no lane overflowed it
+      if (fresh && WK != MLS_W_INVDIST) cached = __all_sync(0xffffffffu, ncache <= kF64Slots);
       if (used < 0) {
         st |= MLS_ST_NO_SUPPORT;
 #pragma unroll
@@ -572,9 +645,18 @@ void f64_dispatch_w(const KParams &p, int64_t npix, cudaStream_t st) {
   if (p.list) grid = 152 * 8;
   else grid = (int)std::min<int64_t>((npix + 7) / 8, 152 * 64);
   if (grid < 1) grid = 1;
-  if (p.weight == MLS_W_GAUSS) k_mls_f64<DEG, MLS_W_GAUSS, OutT><<<grid, 256, 0, st>>>(p, npix);
-  else if (p.weight == MLS_W_WENDLAND) k_mls_f64<DEG, MLS_W_WENDLAND, OutT><<<grid, 256, 0, st>>>(p, npix);
-  else k_mls_f64<DEG, MLS_W_INVDIST, OutT><<<grid, 256, 0, st>>>(p, npix);
+  if (p.weight == MLS_W_GAUSS) {
+    cudaFuncSetAttribute(k_mls_f64<DEG, MLS_W_GAUSS, OutT>, cudaFuncAttributeMaxDynamicSharedMemorySize, kF64SmemBytes);
+    k_mls_f64<DEG, MLS_W_GAUSS, OutT><<<grid, 256, kF64SmemBytes, st>>>(p, npix);
+  } else if (p.weight == MLS_W_WENDLAND) {
+    cudaFuncSetAttribute(k_mls_f64<DEG, MLS_W_WENDLAND, OutT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         kF64SmemBytes);
+    k_mls_f64<DEG, MLS_W_WENDLAND, OutT><<<grid, 256, kF64SmemBytes, st>>>(p, npix);
+  } else {
+    cudaFuncSetAttribute(k_mls_f64<DEG, MLS_W_INVDIST, OutT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         kF64SmemBytes);
+    k_mls_f64<DEG, MLS_W_INVDIST, OutT><<<grid, 256, kF64SmemBytes, st>>>(p, npix);
+  }
 }
 
 }  // namespace
