@@ -160,6 +160,7 @@ struct KParams {
   const int *tile_list;        // tensor path, second pass: the tiles to render, or null
   const unsigned int *tile_count;
   int pixel_frame;             // FP32 kernel: moments in each pixel's own frame (not the tile's)
+  int f32_shape;               // FP32 kernel block shape: 0 16 x 8, 1 8 x 8, 2 8 x 4 (Gaussian)
   int variant;                 // MLS_V_*: the polynomial fit, or the rigid / mean mapping of 2-D values
   double trunc;                // truncated Gaussian: box half-width in units of h (0: full sum)
   const int *list;             // pixel indices, or null for all pixels

@@ -307,6 +307,7 @@ static mlsk::KParams base_params(const mls_handle *h, const RenderCtx *c, const 
   p.relist = c->relist;
   p.relist_count = c->counters;
   p.err = c->err;
+  p.f32_shape = (d.weight == MLS_W_GAUSS) ? h->f32_shape : 0;
   p.lev64 = c->lev64;
   p.lev32 = c->lev32;
   return p;
@@ -833,6 +834,52 @@ static mls_status batch_tune(mls_batch *b, const mls_view *views, void *const *f
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
     return cuda_fail(cudaGetLastError(), "cudaEventCreate");
   mls_status s = MLS_OK;
+  // time one render of dataset k as it is configured now (the first run warms up)
+  auto time_render = [&](size_t k, float *ms) -> mls_status {
+    mls_handle *h = b->hs[k];
+    mlsk::KParams p;
+    mls_status r = render_prepare(h, &h->ctx, &views[k], fields[k], status ? status[k] : nullptr,
+                                  levels ? levels[k] : nullptr, L ? L[k] : 0, bands ? bands[k] : nullptr, 1,
+                                  b->origin, &p);
+    float t = 0.f;
+    for (int rep = 0; rep < 2 && r == MLS_OK; ++rep) {
+      int64_t nl = 0;
+      if (cudaEventRecord(e0, b->origin) != cudaSuccess) r = cuda_fail(cudaGetLastError(), "cudaEventRecord");
+      if (r == MLS_OK) r = render_enqueue(h, &h->ctx, p, b->origin, false, &nl);
+      if (r == MLS_OK && cudaEventRecord(e1, b->origin) != cudaSuccess)
+        r = cuda_fail(cudaGetLastError(), "cudaEventRecord");
+      if (r == MLS_OK && cudaEventSynchronize(e1) != cudaSuccess)
+        r = cuda_fail(cudaGetLastError(), "cudaEventSynchronize");
+      if (r == MLS_OK) cudaEventElapsedTime(&t, e0, e1);
+      h->launches += nl;
+    }
+    *ms = t;
+    return r;
+  };
+  for (size_t k = 0; k < b->hs.size() && s == MLS_OK; ++k) {
+    // renders on the FP32 kernel (FP32 precision, tiles wider than 4 h): its
+    // block shape, for the Gaussian
+    mls_handle *h = b->hs[k];
+    const mls_view &v = views[k];
+    const double tile_h = kTile * fmax(fabs((v.x1 - v.x0) / v.W), fabs((v.y1 - v.y0) / v.H)) / h->desc.h;
+    const bool f32_route = h->desc.variant == MLS_V_POLY && h->desc.weight == MLS_W_GAUSS &&
+                           (h->desc.precision == MLS_P_FP32 ||
+                            ((h->desc.precision == MLS_P_FP16 || h->desc.precision == MLS_P_BF16) &&
+                             tile_h > kTileFrameMaxH));
+    if (!f32_route) continue;
+    float best = 1e30f;
+    int best_shape = 0;
+    for (int shape = 0; shape <= 2 && s == MLS_OK; ++shape) {
+      h->f32_shape = shape;
+      float t = 0.f;
+      s = time_render(k, &t);
+      if (s == MLS_OK && t < best) {
+        best = t;
+        best_shape = shape;
+      }
+    }
+    h->f32_shape = best_shape;
+  }
   for (size_t k = 0; k < b->hs.size() && s == MLS_OK; ++k) {
     mls_handle *h = b->hs[k];
     if (h->desc.precision != MLS_P_FP16 && h->desc.precision != MLS_P_BF16) continue;

@@ -77,6 +77,7 @@ struct mls_handle {
   int64_t launches = 0;              // kernels launched by this handle
   int64_t last_pairs = 0;
   int32_t last_path = 0;   // MLS_PATH_* of the last render's main pass
+  int32_t f32_shape = 0;   // FP32 kernel block shape (the batch autotuner may change it)
   bool timed = false;
   bool operand_cut = true;           // reduced-precision Gaussian: skip pairs whose weight rounds to zero
 };

@@ -49,25 +49,32 @@ __device__ __forceinline__ void cell_range_d(double lo, double hi, double r, dou
 constexpr int kF32Chunk = 128;
 constexpr int kF32DC = 16;
 
-template <int DEG, int WK>
-__global__ __launch_bounds__(128) void k_mls_f32(KParams p) {
+// Block shapes of the FP32 kernel (KParams.f32_shape): BW x BH pixels, one
+// thread each.  A block visits the points within reach of all its pixels, so
+// where the reach is a few pixels a smaller block visits fewer points per
+// pixel, while a larger one reuses each staged point over more threads; the
+// batch autotuner times the shapes per dataset.
+template <int DEG, int WK, int BW, int BH>
+__global__ __launch_bounds__(BW * BH) void k_mls_f32(KParams p) {
   constexpr int K = n_terms(DEG), NM = n_moments(DEG), DC = kF32DC;
+  constexpr int NT = BW * BH;
   __shared__ float sx[kF32Chunk], sy[kF32Chunk];
   __shared__ float sf[DC][kF32Chunk];
   // block geometry, formed once in FP64 (GB300's FP64 rate is a small
-  // fraction of FP32's): frame offsets of the 16 columns and 8 rows, cell range
-  __shared__ float s_col[16], s_row[8];
+  // fraction of FP32's): frame offsets of the BW columns and BH rows, cell range
+  __shared__ float s_col[BW], s_row[BH];
   __shared__ int s_rng[4];
   const int t = threadIdx.x;
-  const int u = blockIdx.x * 16 + (t & 15), v = blockIdx.y * 8 + (t >> 4);
+  const int bu0 = blockIdx.x * BW, bv0 = blockIdx.y * BH;
+  const int u = bu0 + t % BW, v = bv0 + t / BW;
   const bool inside = (u < p.W) && (v < p.H);
   // moments in the frame of the tile's weighted centroid (see the prepass),
   // (dpx, dpy) = pixel minus frame origin; or, when the tile is large
   // compared with h (p.pixel_frame), in each pixel's own frame
-  const int tile = (int)(blockIdx.y >> 1) * p.tiles_x + (int)blockIdx.x;
+  const int tile = (bv0 >> 4) * p.tiles_x + (bu0 >> 4);
   const float cxs = p.tcen[2 * tile_i(p, tile)], cys = p.tcen[2 * tile_i(p, tile) + 1];
-  if (t < 16) s_col[t] = (float)((p.x0 + (blockIdx.x * 16 + t + 0.5) * p.sx - p.ctr_x) * p.inv_s - (double)cxs);
-  else if (t < 24) s_row[t - 16] = (float)((p.y0 + (blockIdx.y * 8 + t - 16 + 0.5) * p.sy - p.ctr_y) * p.inv_s - (double)cys);
+  if (t < BW) s_col[t] = (float)((p.x0 + (bu0 + t + 0.5) * p.sx - p.ctr_x) * p.inv_s - (double)cxs);
+  else if (t < BW + BH) s_row[t - BW] = (float)((p.y0 + (bv0 + t - BW + 0.5) * p.sy - p.ctr_y) * p.inv_s - (double)cys);
   const size_t pstride = (size_t)p.tiles_x * 16;
   // compact support: the Wendland weight, or the truncated Gaussian's box |dx|, |dy| < c
   const bool binned = (WK == MLS_W_WENDLAND) || (WK == MLS_W_GAUSS && p.trunc > 0.0);
@@ -80,18 +87,17 @@ __global__ __launch_bounds__(128) void k_mls_f32(KParams p) {
   // +- h (+- c h; Gaussian: +- h sqrt(max m + gcut), beyond which every weight
   // is below FP32 resolution of the sums)
   const bool cut = (WK == MLS_W_GAUSS) && !binned && p.gcut > 0.f;
-  if ((binned || cut) && t == 24) {
+  if ((binned || cut) && t == BW + BH) {
     const double rad = (WK == MLS_W_WENDLAND) ? p.h
                        : binned ? p.trunc * p.h * (1.0 + 1e-5)
                                 : p.h * (double)sqrtf(p.tmax[tile_i(p, tile)] + p.gcut) * (1.0 + 1e-5);
-    const int bu0 = blockIdx.x * 16, bv0 = blockIdx.y * 8;
-    const double xa = p.x0 + (bu0 + 0.5) * p.sx, xb = p.x0 + (bu0 + 15.5) * p.sx;
-    const double ya = p.y0 + (bv0 + 0.5) * p.sy, yb = p.y0 + (bv0 + 7.5) * p.sy;
+    const double xa = p.x0 + (bu0 + 0.5) * p.sx, xb = p.x0 + (bu0 + BW - 0.5) * p.sx;
+    const double ya = p.y0 + (bv0 + 0.5) * p.sy, yb = p.y0 + (bv0 + BH - 0.5) * p.sy;
     cell_range_d(fmin(xa, xb), fmax(xa, xb), rad, p.gx0, p.inv_cell, p.gx, s_rng[0], s_rng[1]);
     cell_range_d(fmin(ya, yb), fmax(ya, yb), rad, p.gy0, p.inv_cell, p.gy, s_rng[2], s_rng[3]);
   }
   __syncthreads();
-  const float dpx = s_col[t & 15], dpy = s_row[t >> 4];
+  const float dpx = s_col[t % BW], dpy = s_row[t / BW];
   int nr = 1, cx0 = 0, cx1 = 0, cy0 = 0;
   if (binned || cut) {
     cx0 = s_rng[0];
@@ -129,11 +135,11 @@ __global__ __launch_bounds__(128) void k_mls_f32(KParams p) {
       for (int base = a0; base < a1; base += kF32Chunk) {
         __syncthreads();
         const int cnt = min(kF32Chunk, a1 - base);
-        if (t < cnt) {
-          sx[t] = p.xs[base + t] - cxs;
-          sy[t] = p.ys[base + t] - cys;
+        for (int j = t; j < cnt; j += NT) {
+          sx[j] = p.xs[base + j] - cxs;
+          sy[j] = p.ys[base + j] - cys;
         }
-        for (int e = t; e < DC * kF32Chunk; e += 128) {
+        for (int e = t; e < DC * kF32Chunk; e += NT) {
           const int dd = e / kF32Chunk, j = e % kF32Chunk;
           sf[dd][j] = (j < cnt) ? p.FT32[(size_t)(d0 + dd) * p.n_pad + base + j] : 0.f;
         }
@@ -175,13 +181,13 @@ __global__ __launch_bounds__(128) void k_mls_f32(KParams p) {
       }
     }
     if (p.visited && d0 == 0 && t == 0) {
-      // pixel-point pairs of this block (points in its ranges x 128 pixels)
+      // pixel-point pairs of this block (points in its ranges x its pixels)
       unsigned long long npts = 0;
       for (int r = 0; r < nr; ++r)
         npts += (binned || cut) ? (unsigned long long)(cell_at(p, (int64_t)(cy0 + r) * p.gx + cx1 + 1) -
                                                        cell_at(p, (int64_t)(cy0 + r) * p.gx + cx0))
                                 : (unsigned long long)p.n;
-      if (npts) atomicAdd(p.visited, npts * 128ull);
+      if (npts) atomicAdd(p.visited, npts * (unsigned long long)NT);
     }
     // --- per-pixel solve
     if (!inside) continue;
@@ -633,10 +639,19 @@ __global__ void k_bands(const T *field, const double *lev64, const float *lev32,
 
 template <int DEG>
 void f32_dispatch_w(const KParams &p, cudaStream_t st) {
+  // block shapes 16 x 8 (every weight), 8 x 8 and 8 x 4 (the Gaussian)
+  if (p.weight == MLS_W_GAUSS && p.f32_shape == 1) {
+    k_mls_f32<DEG, MLS_W_GAUSS, 8, 8><<<dim3(p.tiles_x * 2, p.tiles_y * 2), 64, 0, st>>>(p);
+    return;
+  }
+  if (p.weight == MLS_W_GAUSS && p.f32_shape == 2) {
+    k_mls_f32<DEG, MLS_W_GAUSS, 8, 4><<<dim3(p.tiles_x * 2, p.tiles_y * 4), 32, 0, st>>>(p);
+    return;
+  }
   dim3 grid(p.tiles_x, p.tiles_y * 2);
-  if (p.weight == MLS_W_GAUSS) k_mls_f32<DEG, MLS_W_GAUSS><<<grid, 128, 0, st>>>(p);
-  else if (p.weight == MLS_W_WENDLAND) k_mls_f32<DEG, MLS_W_WENDLAND><<<grid, 128, 0, st>>>(p);
-  else k_mls_f32<DEG, MLS_W_INVDIST><<<grid, 128, 0, st>>>(p);
+  if (p.weight == MLS_W_GAUSS) k_mls_f32<DEG, MLS_W_GAUSS, 16, 8><<<grid, 128, 0, st>>>(p);
+  else if (p.weight == MLS_W_WENDLAND) k_mls_f32<DEG, MLS_W_WENDLAND, 16, 8><<<grid, 128, 0, st>>>(p);
+  else k_mls_f32<DEG, MLS_W_INVDIST, 16, 8><<<grid, 128, 0, st>>>(p);
 }
 
 template <int DEG, typename OutT>
