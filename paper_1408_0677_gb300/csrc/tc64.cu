@@ -30,10 +30,13 @@
 // compared with h: renders whose 16-pixel tile spans more than 4 h take the
 // FP64 kernel instead (the same rule as the reduced-precision path).
 //
-// One CTA of 128 threads (one per pixel) works one tile, stage by stage:
-// digits of 64 points are written to shared memory, one thread issues the
-// MMAs of the first five weight digits, then of the last five (the weight
-// digit tiles are reused), and every wait is bounded (globaltimer).  The
+// One CTA of 256 threads (two per pixel) works one tile, stage by stage:
+// digits of 64 points are written to shared memory (each pixel's two threads
+// take half the points each; Gaussian weights are a column factor times a
+// row factor times the pixel's correction, 24 double-float exps per point
+// instead of 128), one thread issues the MMAs of the first five weight
+// digits, then of the last five (the weight digit tiles are reused), and
+// every wait is bounded (globaltimer).  The
 // Wendland support count comes from the prepass; pixels whose count could
 // cross a degree threshold go to the FP64 kernel.
 #include "mls_internal.h"
@@ -45,7 +48,8 @@ namespace {
 using namespace mlsk;
 using namespace tcx;
 
-constexpr int kThr64 = 128;                    // one thread per pixel of a 16 x 8 tile
+constexpr int kThr64 = 256;                    // two threads per pixel of a 16 x 8 tile
+constexpr int kPix = 128;                      // pixels per tile (TMEM lanes)
 constexpr int kN64 = 48;                       // operand columns
 constexpr int kDig = 10;                       // digits per entry
 constexpr int kHalfDig = 5;                    // weight digit tiles resident at once
@@ -53,17 +57,19 @@ constexpr int kKP = 64;                        // points per stage
 constexpr int kChunkStages = 24;               // stages between drains (1536 points)
 constexpr float kReach64 = 45.f;               // Gaussian: points with r^2 - m <= 45 h^2
 constexpr int kMaxRows = 96;                   // cell rows a tile may visit
+constexpr int kVS = 33;                        // value row stride (float2): rows on distinct banks
 constexpr int kADig = 128 * 128;               // 16 KB per weight digit tile
 constexpr int kBDig = kN64 * 128;              // 6 KB per operand digit tile
 constexpr int kOffA = 0;
 constexpr int kOffB = kOffA + kHalfDig * kADig;           // 80 KB
 constexpr int kOffRem = kOffB + kDig * kBDig;              // 140 KB: weight remainders [64][128] int32
-constexpr int kOffPt = kOffRem + kKP * kThr64 * 4;         // 172 KB: x~ (hi, lo), y~ (hi, lo) per point
-constexpr int kOffVal = kOffPt + kKP * 16;                 // values (hi, lo) [64][Dc <= 32]
-constexpr int kOffTab = kOffVal + kKP * 32 * 8;            // exp table (64 float2)
+constexpr int kOffPt = kOffRem + kKP * kPix * 4;           // 172 KB: x~ (hi, lo), y~ (hi, lo) per point
+constexpr int kOffVal = kOffPt + kKP * 16;                 // values (hi, lo) [64][kVS]
+constexpr int kOffFac = kOffVal + kKP * kVS * 8;           // Gaussian factors [24][64] (hi, lo)
+constexpr int kOffTab = kOffFac + 24 * kKP * 8;            // exp table (64 float2)
 constexpr int kOffRow = kOffTab + 64 * 8;                  // row start[kMaxRows], prefix[kMaxRows + 1]
 constexpr int kOffMisc = kOffRow + (2 * kMaxRows + 1) * 4 + 12;
-constexpr int kSmem64 = kOffMisc + 256 + 1024;             // + alignment slack
+constexpr int kSmem64 = kOffMisc + 2048 + 1024;            // misc (2 KB) + alignment slack
 
 // v in [-1, 1] (double-float) as a 60-bit fixed-point integer round(v 2^59).
 __device__ __forceinline__ long long fixed59(df32 v) {
@@ -183,14 +189,23 @@ __global__ void __launch_bounds__(kThr64, 1) k_mls_tc64(KParams p, int d0, int D
   unsigned char *smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
   const uint32_t sbase = smem_u32(smem);
   const int t = threadIdx.x, warp = t >> 5;
+  const int pp = t & (kPix - 1), hf = t >> 7;      // pixel, and which half of its points / columns
   float4 *s_pt = (float4 *)(smem + kOffPt);
   float2 *s_val = (float2 *)(smem + kOffVal);
+  float2 *s_fac = (float2 *)(smem + kOffFac);        // [16 columns + 8 rows][64 points]
   float2 *s_tab = (float2 *)(smem + kOffTab);
   int *s_rstart = (int *)(smem + kOffRow);
   int *s_rpre = s_rstart + kMaxRows;
-  int *s_misc = (int *)(smem + kOffMisc);          // [0] rows, [1] total points
-  uint64_t *bar = (uint64_t *)(smem + kOffMisc + 64);
-  uint32_t *tmem_slot = (uint32_t *)(smem + kOffMisc + 128);
+  unsigned char *misc = smem + kOffMisc;
+  int *s_misc = (int *)misc;                          // [0] rows, [1] total points
+  uint64_t *bar = (uint64_t *)(misc + 16);
+  uint32_t *tmem_slot = (uint32_t *)(misc + 24);
+  double *s_bound = (double *)(misc + 32);            // |x~|, |y~| bounds of the visited cells
+  float *s_ab = (float *)(misc + 48);                 // alpha[16], beta[8]: split stabiliser
+  float *s_sh = (float *)(misc + 160);                // per-point exponent shift [64]
+  float *s_m = (float *)(misc + 416);                 // stabiliser of each pixel [128]
+  double *s_inv = (double *)(misc + 928);             // 1 / value scale of the pass's dimensions (<= 32)
+  float2 *s_off = (float2 *)(misc + 1184);            // offsets of the 16 columns, then 8 rows (hi, lo)
   const uint32_t bar_mma = smem_u32(bar);
 
   const int u0 = blockIdx.x * 16, v0 = blockIdx.y * 8;
@@ -199,7 +214,7 @@ __global__ void __launch_bounds__(kThr64, 1) k_mls_tc64(KParams p, int d0, int D
   // offset |delta| at most half the tile (the shift to the pixel frame
   // cancels terms of size |delta|^4 times the moments)
   const double ox = p.x0 + (u0 + 8) * p.sx, oy = p.y0 + (v0 + 4) * p.sy;
-  const int u = u0 + (t & 15), v = v0 + (t >> 4);
+  const int u = u0 + (pp & 15), v = v0 + (pp >> 4);
   const bool inside = (u < p.W) && (v < p.H);
   const size_t pi = (size_t)pix_i(p, (int64_t)v * (p.tiles_x * 16) + u);
 
@@ -209,15 +224,21 @@ __global__ void __launch_bounds__(kThr64, 1) k_mls_tc64(KParams p, int d0, int D
   }
   if (warp == 0) tmem_alloc(smem_u32(tmem_slot), 512);
   df_exp_table_init(s_tab);
+  if (hf == 0) s_m[pp] = (WK == MLS_W_WENDLAND) ? 0.f : p.mstab[pi];
+  for (int dd = t; dd < Dc; dd += kThr64) s_inv[dd] = (d0 + dd < p.D) ? 1.0 / p.fscl64[d0 + dd] : 0.0;
+  if (t < 24) {
+    // the tile's column (row) centres from the frame origin, scaled by 1/h
+    const double o = (t < 16) ? (p.x0 + (u0 + t + 0.5) * p.sx - ox) * p.inv_s
+                              : (p.y0 + (v0 + t - 16 + 0.5) * p.sy - oy) * p.inv_s;
+    s_off[t] = make_float2((float)o, (float)(o - (double)(float)o));
+  }
   // cell rows visited: the pixels' extent +- r (Wendland r = h; Gaussian
   // r = h sqrt(max m + 45), beyond which every weight is below e^-45)
-  __shared__ double s_bound[2];   // |x~|, |y~| bounds of the visited cells
   if (t == 0) {
     const double rs = (WK == MLS_W_WENDLAND) ? 1.0 : sqrt((double)p.tmax[tile_i(p, tile)] + (double)kReach64);
     const double rad = p.h * rs * (1.0 + 1e-5);
-    const int hgt = 8;
     const double xa = p.x0 + (u0 + 0.5) * p.sx, xb = p.x0 + (u0 + 15.5) * p.sx;
-    const double ya = p.y0 + (v0 + 0.5) * p.sy, yb = p.y0 + (v0 + hgt - 0.5) * p.sy;
+    const double ya = p.y0 + (v0 + 0.5) * p.sy, yb = p.y0 + (v0 + 7.5) * p.sy;
     int cx0 = (int)floor((fmin(xa, xb) - rad - p.gx0) * p.inv_cell);
     int cx1 = (int)floor((fmax(xa, xb) + rad - p.gx0) * p.inv_cell);
     int cy0 = (int)floor((fmin(ya, yb) - rad - p.gy0) * p.inv_cell);
@@ -254,6 +275,22 @@ __global__ void __launch_bounds__(kThr64, 1) k_mls_tc64(KParams p, int d0, int D
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
+  // the Gaussian stabiliser split alpha_c + beta_r <= m_p over the tile's
+  // 16 columns and 8 rows (beta_r = min over the row, alpha_c = min over the
+  // column of m - beta), so that each weight is a column factor times a row
+  // factor times the pixel's correction exp(m_p - alpha_c - beta_r) >= 1
+  if (WK == MLS_W_GAUSS && t < 8) {
+    float b = INFINITY;
+    for (int c = 0; c < 16; ++c) b = fminf(b, s_m[t * 16 + c]);
+    s_ab[16 + t] = b;
+  }
+  __syncthreads();
+  if (WK == MLS_W_GAUSS && t < 16) {
+    float a = INFINITY;
+    for (int r = 0; r < 8; ++r) a = fminf(a, s_m[r * 16 + t] - s_ab[16 + r]);
+    s_ab[t] = a;
+  }
+  __syncthreads();
   const uint32_t tmem = *tmem_slot;
   const int total = s_misc[1], nrow = s_misc[0];
   const double bx = s_bound[0], by = s_bound[1];
@@ -263,23 +300,31 @@ __global__ void __launch_bounds__(kThr64, 1) k_mls_tc64(KParams p, int d0, int D
   const double dpy = (p.y0 + (v + 0.5) * p.sy - oy) * p.inv_s;
   const df32 dpx32{(float)dpx, (float)(dpx - (double)(float)dpx)};
   const df32 dpy32{(float)dpy, (float)(dpy - (double)(float)dpy)};
-  const float mst = (WK == MLS_W_WENDLAND) ? 0.f : p.mstab[pi];
   const int cflag = (WK == MLS_W_WENDLAND) ? p.cnt[pi] : 0;
+  // Gaussian: the pixel's correction factor exp(m - alpha_c - beta_r)
+  // (every offset enters the double-float exponent on its own, exactly, so
+  // that alpha, beta and the point shift cancel in the product to the
+  // double-float rounding of the exponents)
+  df32 corr{1.f, 0.f};
+  if (WK == MLS_W_GAUSS) {
+    const df32 res = df_add(df_add({s_m[pp], 0.f}, {-s_ab[pp & 15], 0.f}), {-s_ab[16 + (pp >> 4)], 0.f});
+    corr = df_exp(res, s_tab);
+  }
 
-  // power-of-two bound of each operand column (exponent e: |g| <= 2^e)
-  // this thread builds columns rr, rr + 16, rr + 32 for points 8 g .. 8 g + 7
+  // power-of-two bound of each operand column (exponent e: |g| <= 2^e);
+  // this thread builds columns rr and rr + 32 (below 48) for points 8 g .. 8 g + 7
   const int g8 = t & 7, rr = t >> 3;
-  int cole[3];
-  int colkind[3];   // 0: monomial, 1: basis x value, 2: zero
-  int colm[3], cold[3];
+  int cole[2], colkind[2], colm[2], cold[2];
 #pragma unroll
-  for (int q = 0; q < 3; ++q) {
-    const int c = rr + 16 * q;
+  for (int q = 0; q < 2; ++q) {
+    const int c = rr + 32 * q;
     double bound = 0.0;
-    if (c < 15) {
+    colm[q] = cold[q] = 0;
+    if (c >= kN64) {
+      colkind[q] = 3;                         // not built by this thread
+    } else if (c < 15) {
       colkind[q] = (c < n_moments(DEG)) ? 0 : 2;
       colm[q] = c;
-      cold[q] = 0;
       bound = pow(bx, mono_ex(c)) * pow(by, mono_ey(c));
     } else if (c >= 16 && c < 16 + Dc * K && d0 + (c - 16) / K < p.D) {
       colkind[q] = 1;
@@ -288,51 +333,90 @@ __global__ void __launch_bounds__(kThr64, 1) k_mls_tc64(KParams p, int d0, int D
       bound = pow(bx, mono_ex(colm[q])) * pow(by, mono_ey(colm[q]));   // |value| <= 1
     } else {
       colkind[q] = 2;
-      colm[q] = cold[q] = 0;
     }
     cole[q] = bound > 0.0 ? (int)ceil(log2(bound * 1.001)) : 0;
   }
 
-  double acc[kN64];
+  double acc[24];                              // this thread's 24 columns: 24 hf .. 24 hf + 23
 #pragma unroll
-  for (int c = 0; c < kN64; ++c) acc[c] = 0.0;
+  for (int c = 0; c < 24; ++c) acc[c] = 0.0;
   const uint64_t limit = kWaitLimitNs;
   bool alive = true;
   uint32_t phase = 0;
   const int nstages = (total + kKP - 1) / kKP;
+  int *s_rem = (int *)(smem + kOffRem);
 
   for (int s = 0; s < nstages && alive; ++s) {
     const int sc = s % kChunkStages;
-    // ---- point data of this stage
+    // ---- point data of this stage (threads 0..63 a point each, 64..255 its values)
     if (t < kKP) {
       const int kidx = s * kKP + t;
       float4 pt = make_float4(0.f, 0.f, 0.f, 0.f);
-      int i = -1;
+      float sh = 0.f;
       if (kidx < total) {
         int r = 0;
         while (r + 1 < nrow && s_rpre[r + 1] <= kidx) ++r;
-        i = s_rstart[r] + (kidx - s_rpre[r]);
-        // offset from the tile frame's origin in FP64 (the raw position minus
-        // an origin near the point, then scaled by 1/h), as double-float
+        const int i = s_rstart[r] + (kidx - s_rpre[r]);
+        // offset from the frame's origin in FP64, then double-float
         const double xd = (p.x64[i] - ox) * p.inv_s, yd = (p.y64[i] - oy) * p.inv_s;
         pt = make_float4((float)xd, (float)(xd - (double)(float)xd), (float)yd, (float)(yd - (double)(float)yd));
+        if (WK == MLS_W_GAUSS) {
+          // exponent shift balancing the point's largest column and row factors
+          float ex = -INFINITY, ey = -INFINITY;
+          for (int c = 0; c < 16; ++c) {
+            const float d = (float)xd - s_off[c].x;
+            ex = fmaxf(ex, s_ab[c] - d * d);
+          }
+          for (int r2 = 0; r2 < 8; ++r2) {
+            const float d = (float)yd - s_off[16 + r2].x;
+            ey = fmaxf(ey, s_ab[16 + r2] - d * d);
+          }
+          sh = 0.5f * (ex - ey);
+        }
       }
       s_pt[t] = pt;
-      for (int dd = 0; dd < Dc; ++dd) {
-        float2 fv = make_float2(0.f, 0.f);
-        if (i >= 0 && d0 + dd < p.D) {
-          const int d = d0 + dd;
-          const double val = (p.FT64[(size_t)d * p.n + i] - p.fcen64[d]) / p.fscl64[d];
-          fv = make_float2((float)val, (float)(val - (double)(float)val));
-        }
-        s_val[t * 32 + dd] = fv;
+      s_sh[t] = sh;
+    }
+    for (int e = t; e < kKP * Dc; e += kThr64) {
+      const int j = e / Dc, dd = e - j * Dc;
+      const int kidx = s * kKP + j;
+      float2 fv = make_float2(0.f, 0.f);
+      if (kidx < total && d0 + dd < p.D) {
+        int r = 0;
+        while (r + 1 < nrow && s_rpre[r + 1] <= kidx) ++r;
+        const int i = s_rstart[r] + (kidx - s_rpre[r]);
+        const int d = d0 + dd;
+        const double val = (p.FT64[(size_t)d * p.n + i] - p.fcen64[d]) * s_inv[dd];
+        fv = make_float2((float)val, (float)(val - (double)(float)val));
       }
+      s_val[j * kVS + dd] = fv;
     }
     __syncthreads();
-    // ---- operand digits: this thread's three columns for its eight points
+    // ---- Gaussian factors: 16 column and 8 row factors per point
+    if (WK == MLS_W_GAUSS) {
+      for (int e = t; e < 24 * kKP; e += kThr64) {
+        const int f = e / kKP, j = e - f * kKP;
+        const float4 pt = s_pt[j];
+        df32 d, arg;
+        const float2 o = s_off[f];
+        if (f < 16) {
+          d = df_add({pt.x, pt.y}, {-o.x, -o.y});
+          arg = df_add(df_add(df_mul(d, d), {-s_ab[f], 0.f}), {s_sh[j], 0.f});
+        } else {
+          d = df_add({pt.z, pt.w}, {-o.x, -o.y});
+          arg = df_add(df_add(df_mul(d, d), {-s_ab[f], 0.f}), {-s_sh[j], 0.f});
+        }
+        df32 w{0.f, 0.f};
+        if (s * kKP + j < total && -arg.hi > -70.f) w = df_exp({-arg.hi, -arg.lo}, s_tab);
+        s_fac[f * kKP + j] = make_float2(w.hi, w.lo);
+      }
+      __syncthreads();
+    }
+    // ---- operand digits: this thread's columns for its eight points
 #pragma unroll
-    for (int q = 0; q < 3; ++q) {
-      const int c = rr + 16 * q;
+    for (int q = 0; q < 2; ++q) {
+      if (colkind[q] == 3) continue;
+      const int c = rr + 32 * q;
       uint32_t w[kDig][4];
 #pragma unroll
       for (int jj = 0; jj < 8; jj += 2) {
@@ -345,7 +429,7 @@ __global__ void __launch_bounds__(kThr64, 1) k_mls_tc64(KParams p, int d0, int D
           if (colkind[q] == 0) {
             gval = df_mono({pt.x, pt.y}, {pt.z, pt.w}, mono_ex(colm[q]), mono_ey(colm[q]));
           } else if (colkind[q] == 1) {
-            const float2 fv = s_val[j * 32 + cold[q]];
+            const float2 fv = s_val[j * kVS + cold[q]];
             gval = df_mul(df_mono({pt.x, pt.y}, {pt.z, pt.w}, mono_ex(colm[q]), mono_ey(colm[q])), {fv.x, fv.y});
           }
           if (s * kKP + j >= total) gval = {0.f, 0.f};
@@ -367,10 +451,9 @@ __global__ void __launch_bounds__(kThr64, 1) k_mls_tc64(KParams p, int d0, int D
       for (int i = 0; i < kDig; ++i)
         *(uint4 *)(smem + kOffB + i * kBDig + sw128_off(c, g8)) = make_uint4(w[i][0], w[i][1], w[i][2], w[i][3]);
     }
-    // ---- weight digits 0-4 of this thread's pixel for the stage's 64 points
-    int *s_rem = (int *)(smem + kOffRem);
+    // ---- weight digits 0-4 of this thread's pixel, its half of the 64 points
 #pragma unroll 1
-    for (int c8 = 0; c8 < 8; ++c8) {
+    for (int c8 = 4 * hf; c8 < 4 * hf + 4; ++c8) {
       uint32_t w[kHalfDig][4];
 #pragma unroll
       for (int jj = 0; jj < 8; jj += 2) {
@@ -378,22 +461,22 @@ __global__ void __launch_bounds__(kThr64, 1) k_mls_tc64(KParams p, int d0, int D
 #pragma unroll
         for (int h2 = 0; h2 < 2; ++h2) {
           const int j = 8 * c8 + jj + h2;
-          const float4 pt = s_pt[j];
-          const df32 dx = df_add({pt.x, pt.y}, {-dpx32.hi, -dpx32.lo});
-          const df32 dy = df_add({pt.z, pt.w}, {-dpy32.hi, -dpy32.lo});
-          const df32 r2 = df_add(df_mul(dx, dx), df_mul(dy, dy));
           df32 wt{0.f, 0.f};
           if (s * kKP + j < total) {
             if (WK == MLS_W_GAUSS) {
-              const df32 arg = df_add({mst, 0.f}, {-r2.hi, -r2.lo});
-              if (arg.hi > -70.f) wt = df_exp(arg, s_tab);
-            } else if (r2.hi < 1.f) {
-              wt = df_wendland(r2);
+              const float2 X = s_fac[(pp & 15) * kKP + j], Y = s_fac[(16 + (pp >> 4)) * kKP + j];
+              wt = df_mul(df_mul({X.x, X.y}, {Y.x, Y.y}), corr);
+            } else {
+              const float4 pt = s_pt[j];
+              const df32 dx = df_add({pt.x, pt.y}, {-dpx32.hi, -dpx32.lo});
+              const df32 dy = df_add({pt.z, pt.w}, {-dpy32.hi, -dpy32.lo});
+              const df32 r2 = df_add(df_mul(dx, dx), df_mul(dy, dy));
+              if (r2.hi < 1.f) wt = df_wendland(r2);
             }
           }
           long long V = fixed59({0.5f * wt.hi, 0.5f * wt.lo});
           int hi5[5];
-          s_rem[j * kThr64 + t] = top5(V, hi5);
+          s_rem[j * kPix + pp] = top5(V, hi5);
 #pragma unroll
           for (int i = 0; i < kHalfDig; ++i) dg[h2][i] = hi5[i];
         }
@@ -402,7 +485,7 @@ __global__ void __launch_bounds__(kThr64, 1) k_mls_tc64(KParams p, int d0, int D
       }
 #pragma unroll
       for (int i = 0; i < kHalfDig; ++i)
-        *(uint4 *)(smem + kOffA + i * kADig + sw128_off(t, c8)) = make_uint4(w[i][0], w[i][1], w[i][2], w[i][3]);
+        *(uint4 *)(smem + kOffA + i * kADig + sw128_off(pp, c8)) = make_uint4(w[i][0], w[i][1], w[i][2], w[i][3]);
     }
     fence_proxy_async();
     tc_fence_before();
@@ -430,19 +513,19 @@ __global__ void __launch_bounds__(kThr64, 1) k_mls_tc64(KParams p, int d0, int D
     }
     // ---- weight digits 5-9 from the remainders
 #pragma unroll 1
-    for (int c8 = 0; c8 < 8; ++c8) {
+    for (int c8 = 4 * hf; c8 < 4 * hf + 4; ++c8) {
       uint32_t w[kHalfDig][4];
 #pragma unroll
       for (int jj = 0; jj < 8; jj += 2) {
         int lo0[5], lo1[5];
-        low5(s_rem[(8 * c8 + jj) * kThr64 + t], lo0);
-        low5(s_rem[(8 * c8 + jj + 1) * kThr64 + t], lo1);
+        low5(s_rem[(8 * c8 + jj) * kPix + pp], lo0);
+        low5(s_rem[(8 * c8 + jj + 1) * kPix + pp], lo1);
 #pragma unroll
         for (int i = 0; i < kHalfDig; ++i) w[i][jj >> 1] = h2pack(lo0[i], lo1[i]);
       }
 #pragma unroll
       for (int i = 0; i < kHalfDig; ++i)
-        *(uint4 *)(smem + kOffA + i * kADig + sw128_off(t, c8)) = make_uint4(w[i][0], w[i][1], w[i][2], w[i][3]);
+        *(uint4 *)(smem + kOffA + i * kADig + sw128_off(pp, c8)) = make_uint4(w[i][0], w[i][1], w[i][2], w[i][3]);
     }
     fence_proxy_async();
     tc_fence_before();
@@ -466,16 +549,27 @@ __global__ void __launch_bounds__(kThr64, 1) k_mls_tc64(KParams p, int d0, int D
       alive = false;
       break;
     }
-    // ---- drain: after every kChunkStages stages and after the last
+    // ---- drain: after every kChunkStages stages and after the last; this
+    // thread reads its pixel's columns 24 hf .. 24 hf + 23 of every diagonal
     if (sc == kChunkStages - 1 || s == nstages - 1) {
-      const uint32_t tb = tmem + ((uint32_t)(32 * warp) << 16);
+      const uint32_t tb = tmem + ((uint32_t)(32 * (warp & 3)) << 16);
 #pragma unroll 1
       for (int dg = 0; dg < kDig; ++dg) {
-        float vals[48];
-        tmem_ld48(tb + (uint32_t)(dg * kN64), vals);
+        float v16[16], v8[8];
+        const uint32_t base = tb + (uint32_t)(dg * kN64);
+        if (hf == 0) {
+          tmem_ld16(base, v16);
+          tmem_ld8(base + 16, v8);
+        } else {
+          tmem_ld8(base + 24, v8);
+          tmem_ld16(base + 32, v16);
+        }
         const double sc6 = ldexp(1.0, -6 * dg);
 #pragma unroll
-        for (int c = 0; c < kN64; ++c) acc[c] = fma((double)vals[c], sc6, acc[c]);
+        for (int c = 0; c < 24; ++c) {
+          const float x = (hf == 0) ? (c < 16 ? v16[c] : v8[c - 16]) : (c < 8 ? v8[c] : v16[c - 8]);
+          acc[c] = fma((double)x, sc6, acc[c]);
+        }
       }
       tc_fence_before();
       __syncthreads();
@@ -483,21 +577,27 @@ __global__ void __launch_bounds__(kThr64, 1) k_mls_tc64(KParams p, int d0, int D
     }
   }
 
-  // ---- epilogue: FP64 moments in the tile frame -> pixel frame -> policy
+  // ---- epilogue: the second half of every pixel's columns to shared memory
+  // (the digit tiles are free now), then FP64 moments in the tile frame ->
+  // pixel frame -> policy, one thread per pixel
+  double *s_acc = (double *)(smem + kOffA);          // [128][24]
+  if (hf == 1) {
+#pragma unroll
+    for (int c = 0; c < 24; ++c) s_acc[pp * 24 + c] = acc[c];
+  }
+  __syncthreads();
   const size_t plane = (size_t)p.W * p.H;
   const size_t pix = (size_t)v * p.W + u;
   double *field = (double *)p.field;
-  if (alive && inside) {
+  if (alive && inside && hf == 0) {
+    auto col = [&](int c) -> double { return c < 24 ? acc[c] : s_acc[pp * 24 + c - 24]; };
     // column scales: weights carry 2, operand columns 2^e, digit products 2^-10
     double S[15];
-    {
-      int e_m[15];
 #pragma unroll
-      for (int c = 0; c < 15; ++c) {
-        const double bound = pow(bx, mono_ex(c)) * pow(by, mono_ey(c));
-        e_m[c] = bound > 0.0 ? (int)ceil(log2(bound * 1.001)) : 0;
-        S[c] = (c < n_moments(DEG)) ? ldexp(acc[c], e_m[c] + 1 - 10) : 0.0;
-      }
+    for (int c = 0; c < 15; ++c) {
+      const double bound = pow(bx, mono_ex(c)) * pow(by, mono_ey(c));
+      const int e = bound > 0.0 ? (int)ceil(log2(bound * 1.001)) : 0;
+      S[c] = (c < n_moments(DEG)) ? ldexp(col(c), e + 1 - 10) : 0.0;
     }
     double Mt[6][6], Rt[K][DCM];
 #pragma unroll
@@ -507,7 +607,7 @@ __global__ void __launch_bounds__(kThr64, 1) k_mls_tc64(KParams p, int d0, int D
     for (int a = 0; a < K; ++a) {
       const double bound = pow(bx, mono_ex(a)) * pow(by, mono_ey(a));
       const int e = bound > 0.0 ? (int)ceil(log2(bound * 1.001)) : 0;
-      for (int dd = 0; dd < Dc; ++dd) Rt[a][dd] = ldexp(acc[16 + dd * K + a], e + 1 - 10);
+      for (int dd = 0; dd < Dc; ++dd) Rt[a][dd] = ldexp(col(16 + dd * K + a), e + 1 - 10);
     }
     // basis shift b(x~ - delta) = T b(x~): pixel-frame M = T Mt T^T, R = T Rt
     double T[6][6];
@@ -579,6 +679,7 @@ __global__ void __launch_bounds__(kThr64, 1) k_mls_tc64(KParams p, int d0, int D
     tmem_dealloc(tmem, 512);
   }
 }
+
 
 template <int DEG, int WK>
 void launch_one64(const KParams &p, int d0, int Dc, uint32_t idesc, cudaStream_t st) {
