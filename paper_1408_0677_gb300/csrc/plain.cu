@@ -615,25 +615,31 @@ __global__ void k_bands(const T *field, const double *lev64, const float *lev32,
     for (int j = threadIdx.x; j < L; j += blockDim.x) lv[j] = lev32[(size_t)d * L + j];
   }
   __syncthreads();
-  const int64_t i0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) * 16;
-  if (i0 >= plane) return;
   const T *f = field + (size_t)d * plane;
   uint8_t *b = bands + (size_t)d * plane;
-  uint8_t out[16];
+  // four consecutive values per thread, neighbouring threads on neighbouring
+  // values: one 16-byte load and one 4-byte store per thread where aligned
+  const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i0 = 4 * ((int64_t)blockIdx.x * blockDim.x + threadIdx.x); i0 < plane; i0 += 4 * nthreads) {
+    T x[4];
+    const bool full = i0 + 4 <= plane;
+    if (sizeof(T) == 4 && full && ((((uintptr_t)(f + i0)) & 15) == 0)) {
+      const float4 v = *(const float4 *)(f + i0);
+      x[0] = (T)v.x; x[1] = (T)v.y; x[2] = (T)v.z; x[3] = (T)v.w;
+    } else {
 #pragma unroll
-  for (int k = 0; k < 16; ++k) {
-    if (i0 + k < plane) {
-      const T x = f[i0 + k];
-      out[k] = (sizeof(T) == 8) ? band_of((double)x, (const double *)smem_raw, L)
-                                : band_of((float)x, (const float *)smem_raw, L);
+      for (int k = 0; k < 4; ++k) x[k] = (i0 + k < plane) ? f[i0 + k] : T(0);
     }
-  }
-  if (i0 + 16 <= plane && (((uintptr_t)(b + i0)) & 15) == 0) {
-    uint4 pk;
-    memcpy(&pk, out, 16);
-    *(uint4 *)(b + i0) = pk;
-  } else {
-    for (int k = 0; k < 16 && i0 + k < plane; ++k) b[i0 + k] = out[k];
+    uint8_t out[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+      out[k] = (sizeof(T) == 8) ? band_of((double)x[k], (const double *)smem_raw, L)
+                                : band_of((float)x[k], (const float *)smem_raw, L);
+    if (full && (((uintptr_t)(b + i0)) & 3) == 0) {
+      *(uchar4 *)(b + i0) = make_uchar4(out[0], out[1], out[2], out[3]);
+    } else {
+      for (int k = 0; k < 4 && i0 + k < plane; ++k) b[i0 + k] = out[k];
+    }
   }
 }
 
@@ -697,7 +703,10 @@ void launch_f64(const KParams &p, int64_t npix, cudaStream_t st) {
 
 void launch_bands(const KParams &p, bool fp64, cudaStream_t st) {
   const int64_t plane = (int64_t)p.W * p.H;
-  dim3 grid((unsigned)((plane + 16 * 256 - 1) / (16 * 256)), (unsigned)p.D);
+  // blocks of 256 threads, four values per thread and pass, at most 1024
+  // blocks per dimension (the loop strides over the rest)
+  const int64_t need = (plane + 4 * 256 - 1) / (4 * 256);
+  dim3 grid((unsigned)(need < 1024 ? (need < 1 ? 1 : need) : 1024), (unsigned)p.D);
   const size_t sm = (size_t)p.L * (fp64 ? 8 : 4) + 16;
   if (fp64) k_bands<double><<<grid, 256, sm, st>>>((const double *)p.field, p.lev64, p.lev32, p.L, plane, p.D, p.bands);
   else k_bands<float><<<grid, 256, sm, st>>>((const float *)p.field, p.lev64, p.lev32, p.L, plane, p.D, p.bands);
