@@ -43,7 +43,7 @@ sys.path.insert(0, ROOT)
 METRIC = "MLS pixel*point*dim updates/s"
 UNIT = "pixel*point*dim/s"
 WORKLOAD = "fourier_n10k_d32_1024x1024_quadratic_gauss_h0.02_L16"
-TC_SRCS = [os.path.join(ROOT, "paper_1408_0677_gb300", "csrc", f) for f in ("tc.cu", "dev_common.cuh")]
+TC_SRCS = [os.path.join(ROOT, "paper_1408_0677_gb300", "csrc", f) for f in ("tc.cu", "dev_common.cuh", "tcgen05.cuh")]
 PROFILE = os.path.join(ROOT, "profiles", "k_mls_tc_fourier10k_fp16.md")
 
 
@@ -286,7 +286,7 @@ def run_reference(args):
 
 
 def tc_source_hash():
-    """sha256 over the tensor-core kernel's sources (tc.cu, dev_common.cuh)."""
+    """sha256 over the tensor-core kernel's sources (tc.cu, dev_common.cuh, tcgen05.cuh)."""
     h = hashlib.sha256()
     for f in TC_SRCS:
         h.update(open(f, "rb").read())
