@@ -555,8 +555,15 @@ def run_ours(args):
         peak = FP32_FMA_TFLOPS
         roof = {"bound": "alu", "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz", "kernel": "k_mls_f32"}
     prof = os.path.join(ROOT, "profiles", f"k_mls_tc_{args.workload}_{args.precision}.md")
+    # the tensor pass runs one launch per group of value dimensions (at most
+    # 40 per launch for the quadratic basis, balanced): the profile's traffic
+    # of one launch, scaled by the pixels, times the launches
+    dpp = min(40, (256 - 16) // k_terms)
+    dpp -= dpp % (16 if k_terms == 1 else 48 // k_terms)
+    vpasses = -(-D // dpp)
+    traffic = _traffic(W * H, prof) if (path == _abi.MLS_PATH_TENSOR and wl.trunc == 0) else None
     roof.update({"achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                 "traffic": (_traffic(W * H, prof) if (path == _abi.MLS_PATH_TENSOR and wl.trunc == 0) else None),
+                 "traffic": traffic * vpasses if traffic is not None else None,
                  "kernel_ms": k_ms, "flops_per_launch": flops, "flops_per_pair": flop_pair})
     cpu, err = None, None
     if args.cpu_seconds > 0:
