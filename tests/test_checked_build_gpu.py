@@ -6,9 +6,10 @@ device error word (no trap), which mls_sync turns into an error.  A child
 process loads that library (MLS_LIBRARY) and renders small cases through
 every path: the tensor-core kernel in FP16 (two passes, split weights) and
 BF16, the FP32 kernel in tile and pixel frames, the FP64 kernel, the
-double-float hand-over and its FP64 tier, Gaussian / Wendland / inverse
-distance / truncated Gaussian, the rigid and mean mappings, host-pointer
-renders, standalone bands and the batch.  Each render must leave the error
+double-float hand-over and its FP64 tier, the FP64 emulation on the tensor
+cores, Gaussian / Wendland / inverse distance / truncated Gaussian, the
+rigid and mean mappings, host-pointer renders, standalone bands and the
+batch.  Each render must leave the error
 word at zero and match the oracle.
 """
 import os
@@ -40,6 +41,16 @@ cases = [
     (inputs.small_random(7, 50, 3, 29, 21, 1, ID, 0.2), ["fp32", "fp64"], {}),
     (inputs.small_random(4, 400, 4, 45, 38, 2, WD, 0.15), ["fp32", "fp64"], {}),
 ]
+# the FP64 emulation on the tensor cores (zoom windows: 16 pixels span at most 4 h)
+for seed, n, D, W, H, deg, wt, h, view in ((31, 10000, 8, 100, 75, 2, G, 0.02, (0.1, 0.2, 0.4, 0.425)),
+                                           (34, 100000, 6, 90, 70, 2, WD, 0.02, (0.3, 0.2, 0.6, 0.45))):
+    wl = inputs.fourier_mix(seed, n, D, W, H, deg, wt, h)
+    wl.view = view
+    ref = oracle_ref(wl)
+    res = gpu_render(wl, "fp64tc")
+    assert res["stats"].device_error == 0 and res["stats"].main_path == 5
+    compare(wl, res, ref, "fp64tc", max_allow_frac=1.0)
+    print("ok fp64tc", wl.name, flush=True)
 for wl, precs, kw in cases:
     wl.view = (0.05, 0.1, 0.9, 0.85)
     ref = oracle_ref(wl)
