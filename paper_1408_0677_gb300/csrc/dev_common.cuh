@@ -128,6 +128,11 @@ struct KParams {
   int degree, weight;
   double h, alpha;
   double cond_fp64, rcond_min, cond_recompute;
+  // the same thresholds rounded to float on the host ((float)cond_fp64,
+  // (float)cond_recompute, (float)(1 / rcond_min)): GB300's FP64 pipe is a
+  // small fraction of its FP32 rate, and every conversion or division of a
+  // double in a per-pixel solve costs the whole warp that fraction
+  float cond_fp64_f, cond_recompute_f, inv_rcond_min_f;
   float lambda_max;            // bound on sum_a |z_a| sqrt(M_00 M_aa) kept on the fast path
   // view
   int W, H;
@@ -163,6 +168,8 @@ struct KParams {
   int f32_shape;               // FP32 kernel block shape: 0 16 x 8, 1 8 x 8, 2 8 x 4 (Gaussian)
   int variant;                 // MLS_V_*: the polynomial fit, or the rigid / mean mapping of 2-D values
   double trunc;                // truncated Gaussian: box half-width in units of h (0: full sum)
+  float trunc_f;               // (float)trunc
+  int trunc_on;                // trunc > 0
   const int *list;             // pixel indices, or null for all pixels
   const unsigned int *list_count;  // device count for list mode, or null
   int64_t list_cap;
@@ -418,14 +425,14 @@ __device__ __forceinline__ int solve_pixel_fp32(const float *S, float dx, float 
   for (int a = 0; a < K; ++a)
     if (!(Lf[a][a] * Lf[a][a] > 1e-6f)) return SOLVE_RECOMPUTE;
   const float cnd = (K == 1) ? 1.f : cond1<K, float>(Me, Lf, df);
-  if (!(cnd <= (float)p.cond_recompute)) return SOLVE_RECOMPUTE;
+  if (!(cnd <= p.cond_recompute_f)) return SOLVE_RECOMPUTE;
   if (K > 1) {
     const float gr = 1.f + fmaxf(fabsf(dx), fabsf(dy));
     const float g2 = gr * gr;
     const float growth = (K == 3) ? g2 : g2 * g2;
-    if (!(cnd * growth * 100.f < (float)(1.0 / p.rcond_min))) return SOLVE_RECOMPUTE;
+    if (!(cnd * growth * 100.f < p.inv_rcond_min_f)) return SOLVE_RECOMPUTE;
   }
-  if (cnd > (float)p.cond_fp64) {
+  if (cnd > p.cond_fp64_f) {
     // FP64 factorisation of the same moments
     double Md[K][K], sdd[K], Med[K][K], Ld[K][K], dd[K];
 #pragma unroll

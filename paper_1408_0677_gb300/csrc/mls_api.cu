@@ -280,6 +280,11 @@ static mlsk::KParams base_params(const mls_handle *h, const RenderCtx *c, const 
   p.cond_fp64 = d.cond_fp64;
   p.rcond_min = d.rcond_degenerate;
   p.cond_recompute = d.cond_recompute;
+  p.cond_fp64_f = (float)d.cond_fp64;
+  p.cond_recompute_f = (float)d.cond_recompute;
+  p.inv_rcond_min_f = (float)(1.0 / d.rcond_degenerate);
+  p.trunc_f = (float)d.support;
+  p.trunc_on = d.support > 0.0 ? 1 : 0;
   // amplification of right-hand-side rounding the fast path accepts, from the
   // precision of its weights and operands (calibrated against the FP64 oracle)
   p.lambda_max = d.precision == MLS_P_FP32 ? 1000.f

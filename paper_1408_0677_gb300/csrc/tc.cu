@@ -82,6 +82,11 @@ constexpr int kSmemLimit = 232448;                        // 227 KB per CTA
 // pass Dc: A tiles, B tiles (2 x N rows of 128 B per stage), per-warp point
 // parameters, a ring of staged point tiles (x, y and Dc value rows of 64
 // floats each, filled by TMA bulk copies), barriers.
+// bytes past offBar: barriers, TMEM slot and tile geometry (512), then the
+// slot table of the staged point tiles (4 stages x 8 slots x 16 bytes)
+constexpr int kMisc = 1024;
+constexpr int kOffSlots = 512;
+
 struct TcLayout {
   int offB, bpart;          // B tiles: offset, bytes per tile
   int offPrm;
@@ -97,11 +102,12 @@ TcLayout make_layout(int N, int Dc) {
   L.offPrm = L.offB + kStages * 2 * L.bpart;
   L.offData = L.offPrm + kPrmBytes;
   L.dstage = (kKT / 8) * (kXB + Dc * 8 + 4) * 4;
-  const int fixed = L.offData + 512 + 1024;
+  const int fixed = L.offData + kMisc + 1024;
   int ds = (kSmemLimit - fixed) / L.dstage;
   L.dstages = ds > 4 ? 4 : ds;
-  L.offBar = L.offData + L.dstages * L.dstage;   // barriers, TMEM slot, then the tile geometry (+256)
-  L.total = L.offBar + 512 + 1024;
+  // barriers, TMEM slot, the tile geometry (+256), the stage slot table (+512)
+  L.offBar = L.offData + L.dstages * L.dstage;
+  L.total = L.offBar + kMisc + 1024;
   return L;
 }
 
@@ -153,19 +159,23 @@ __device__ __forceinline__ float ex2_approx(float x) {
   return y;
 }
 
-// Weight of one (pixel, point) pair from the tile-frame point parameters
-// prm = (a, b, c): Gaussian log2 weight a + b dx + c dy + E, or Wendland q^2.
-template <int WK>
-__device__ __forceinline__ float pair_weight(float4 prm, float E, float dx, float dy) {
-  const float t = fmaf(prm.y, dx, fmaf(prm.z, dy, prm.x + E));
-  if (WK == MLS_W_GAUSS) {
-    return ex2_approx(t);
-  } else {
-    const float q = sqrtf(fmaxf(t, 0.f));
-    const float o = 1.f - q;
-    const float o2 = o * o;
-    return (q < 1.f) ? o2 * o2 * fmaf(4.f, q, 1.f) : 0.f;
-  }
+__device__ __forceinline__ float sqrt_approx(float x) {
+  float y;
+  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+// Wendland weight S (1 - q)^4 (4 q + 1) of a pair with q^2 = t, zero for
+// t >= 1.  The weight is rounded to a 16-bit operand next, so the square root
+// is the approximate one (relative error near 2^-23, far below that
+// rounding); S is the common factor of all weights (a power of two, exact).
+template <bool FP16>
+__device__ __forceinline__ float wendland_weight(float t) {
+  const float S = weight_scale<FP16>();
+  const float q = sqrt_approx(fmaxf(t, 0.f));
+  const float o = 1.f - q;
+  const float o2 = o * o;
+  return (t < 1.f) ? o2 * o2 * fmaf(4.f * S, q, S) : 0.f;
 }
 
 // The sequence of point tiles a CTA visits: all points, or the cell rows of
@@ -173,7 +183,8 @@ __device__ __forceinline__ float pair_weight(float4 prm, float E, float dx, floa
 // weight, c h for the truncated Gaussian, h sqrt(max_p m_p + gcut) for the
 // Gaussian (beyond it every weight rounds to zero in the 16-bit operand).
 // Tile starts are rounded down to 8 points; indices outside [lo, hi) are
-// masked.
+// masked.  One thread (the loader) walks them; the other roles read each
+// stage's slots from shared memory.
 // Per-CTA geometry, computed once in FP64 by one warp (GB300's FP64 rate is a
 // small fraction of FP32's: every thread evaluating these cost more than the
 // contraction on short point ranges): the tile-frame offsets of the 16 pixel
@@ -184,7 +195,7 @@ struct TileGeo {
 };
 
 __device__ __forceinline__ bool ranges_all(const KParams &p) {
-  return p.weight != MLS_W_WENDLAND && !(p.trunc > 0.0) && !(p.gcut > 0.f);
+  return p.weight != MLS_W_WENDLAND && !p.trunc_on && !(p.gcut > 0.f);
 }
 
 // One warp: lane k < 16 column k, lane 16 + k row k; lanes 0..3 the cell range.
@@ -211,8 +222,7 @@ __device__ void tile_geometry(const KParams &p, int u0, int v0, int hgt, float c
 // The 8-point blocks of the visited ranges, packed densely into stages of 8
 // blocks (64 points): slot after slot takes the next block of the current
 // cell row and moves on to the next non-empty row when the row ends (a row
-// of ~50 points would otherwise start a half-empty stage of its own).  Every
-// role runs the same iterator, so all agree on each stage's contents.
+// of ~50 points would otherwise start a half-empty stage of its own).
 struct Slot {
   int gb;       // 8-point block index (points 8 gb .. 8 gb + 7), < 0: empty slot
   int lo, hi;   // point range of its row: points outside are masked
@@ -272,20 +282,13 @@ __device__ __forceinline__ Slot pack_take(const KParams &p, PackIter &it) {
   return s;
 }
 
-// One stage: the slots `want0` and `want1` of it (the rest are skipped).
-__device__ __forceinline__ void pack_stage(const KParams &p, PackIter &it, int want0, Slot &s0, int want1,
-                                           Slot &s1) {
-  s0 = Slot{-1, 0, 0};
-  s1 = Slot{-1, 0, 0};
-#pragma unroll 1
-  for (int q = 0; q < kKT / 8; ++q) {
-    const Slot sl = pack_take(p, it);
-    if (q == want0) s0 = sl;
-    if (q == want1) s1 = sl;
-  }
-}
-
 __device__ __forceinline__ bool slot_has(const Slot &s, int i) { return s.gb >= 0 && i >= s.lo && i < s.hi; }
+
+// Slot q of staged point tile ds, as the loader wrote it.
+__device__ __forceinline__ Slot slot_read(const int4 *tab, int ds, int q) {
+  const int4 e = tab[ds * 8 + q];
+  return Slot{e.x, e.y, e.z};
+}
 
 template <int DEG, int WK, bool FP16, int NACC, bool WSPLIT>
 __global__ void __launch_bounds__(kThreads, 1) k_mls_tc(KParams p, int d0, int Dc, int N, uint32_t idesc,
@@ -332,7 +335,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mls_tc(KParams p, int d0, int D
     mbar_init(bar_acc, 1);
     for (int ds = 0; ds < DST; ++ds) {
       mbar_init(bar_dfull0 + 8 * ds, 1);
-      mbar_init(bar_dempty0 + 8 * ds, 8);
+      mbar_init(bar_dempty0 + 8 * ds, 9);   // eight producer warps and the MMA issuer
     }
     mbar_init(bar_exy0, 4);
     mbar_init(bar_exy0 + 8, 4);
@@ -351,8 +354,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_mls_tc(KParams p, int d0, int D
   const uint64_t limit = kWaitLimitNs;
   bool alive = true;
 
-  PackIter it;
-  pack_init(p, geo, it);
+  // The loader walks the cell rows and writes each staged point tile's slots
+  // {8-point block, row range} into the slot table beside it; the other roles
+  // read them there.  A stage whose first slot is empty ends the tile.
+  int4 *slot_tab = (int4 *)(smem + lay.offBar + kOffSlots);
+  int nst = 0;   // point tiles this thread consumed (the epilogue reads whether any)
 
   if (warp < 4 && WK == MLS_W_GAUSS) {
     // ------------------------------------------------ weight producers (Gaussian, separable)
@@ -370,8 +376,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_mls_tc(KParams p, int d0, int D
     // The truncated Gaussian's box |dx|, |dy| < c is separable too: a column
     // (row) factor is zero where the point is c or more away along x (y).
     const int t = threadIdx.x;
-    const bool boxed = p.trunc > 0.0;
-    const float cbox = (float)p.trunc;
+    const bool boxed = p.trunc_on;
+    const float cbox = p.trunc_f;
     float *sAB = (float *)(smem + lay.offPrm) + 32 * warp;     // this warp's alpha[16], beta[16]
     float *exy = (float *)(smem + lay.offPrm + kGaussHdr);     // [2][16 column rows, 16 row rows at kRowOff]
     {
@@ -406,15 +412,15 @@ __global__ void __launch_bounds__(kThreads, 1) k_mls_tc(KParams p, int d0, int D
       gcor[a] = ex2_approx(fminf(res, kResMax)) * weight_scale<FP16>();
     }
     int kt = 0;
-    for (; pack_valid(it) && alive; ++kt) {
+    for (; alive; ++kt) {
       const int s = kt & 1;
       const int ds = kt % DST;
-      Slot mine, unused;
-      pack_stage(p, it, jp >> 3, mine, -1, unused);
       if (!mbar_wait(bar_dfull0 + 8 * ds, (kt / DST) & 1, p.err, ERR_WAIT_FULL, limit)) {
         alive = false;
         break;
       }
+      if (slot_tab[ds * 8].x < 0) break;
+      const Slot mine = slot_read(slot_tab, ds, jp >> 3);
       const float *dxs = (const float *)(smem + lay.offData + ds * lay.dstage);
       float *tab = exy + s * kExyFloats;
       {
@@ -486,6 +492,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mls_tc(KParams p, int d0, int D
       __syncwarp();
       if (lane == 0) mbar_arrive(bar_full0 + 8 * s);
     }
+    nst = kt;
   } else if (warp < 4) {
     // ------------------------------------------------ weight producers (Wendland)
     const int t = threadIdx.x;                 // row t of every accumulator
@@ -504,15 +511,15 @@ __global__ void __launch_bounds__(kThreads, 1) k_mls_tc(KParams p, int d0, int D
     }
     float4 *prm = (float4 *)(smem + lay.offPrm) + warp * kKT;
     int kt = 0;
-    for (; pack_valid(it) && alive; ++kt) {
+    for (; alive; ++kt) {
       const int s = kt & 1;
       const int ds = kt % DST;
-      Slot sl2[2];
-      pack_stage(p, it, lane >> 3, sl2[0], (lane >> 3) + 4, sl2[1]);
       if (!mbar_wait(bar_dfull0 + 8 * ds, (kt / DST) & 1, p.err, ERR_WAIT_FULL, limit)) {
         alive = false;
         break;
       }
+      if (slot_tab[ds * 8].x < 0) break;
+      const Slot sl2[2] = {slot_read(slot_tab, ds, lane >> 3), slot_read(slot_tab, ds, (lane >> 3) + 4)};
       const float *dxs = (const float *)(smem + lay.offData + ds * lay.dstage);
       __syncwarp();
 #pragma unroll
@@ -548,8 +555,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_mls_tc(KParams p, int d0, int D
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
           const float4 pr = prm[8 * c + j];
-          w0[j] = pair_weight<WK>(pr, E[0], dx[0], dy[0]) * weight_scale<FP16>();
-          if (NACC == 2) w1[j] = pair_weight<WK>(pr, E[NACC - 1], dx[NACC - 1], dy[NACC - 1]) * weight_scale<FP16>();
+          // q^2 = |x~|^2 - 2 x~ . delta + |delta|^2 (the point's and the pixel's parts)
+          w0[j] = wendland_weight<FP16>(fmaf(pr.y, dx[0], fmaf(pr.z, dy[0], pr.x + E[0])));
+          if (NACC == 2)
+            w1[j] = wendland_weight<FP16>(fmaf(pr.y, dx[NACC - 1], fmaf(pr.z, dy[NACC - 1], pr.x + E[NACC - 1])));
         }
         uint4 q0, q1;
         if (WSPLIT) {
@@ -567,6 +576,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mls_tc(KParams p, int d0, int D
       __syncwarp();
       if (lane == 0) mbar_arrive(bar_full0 + 8 * s);
     }
+    nst = kt;
   } else if (warp < 8) {
     // ------------------------------------------------ operand builders
     const int tt = threadIdx.x - 128;
@@ -576,17 +586,17 @@ __global__ void __launch_bounds__(kThreads, 1) k_mls_tc(KParams p, int d0, int D
     const int mex = mono_ex(rr < 15 ? rr : 0), mey = mono_ey(rr < 15 ? rr : 0);
     const float mrow = (rr < NM) ? 1.f : 0.f;
     int kt = 0;
-    for (; pack_valid(it) && alive; ++kt) {
+    for (; alive; ++kt) {
       const int s = kt & 1;
       const int ds = kt % DST;
-      Slot mine, unused;
-      pack_stage(p, it, g, mine, -1, unused);
-      const int i0 = mine.gb * 8;
       float xv[8], yv[8], msk[8];
       if (!mbar_wait(bar_dfull0 + 8 * ds, (kt / DST) & 1, p.err, ERR_WAIT_FULL, limit)) {
         alive = false;
         break;
       }
+      if (slot_tab[ds * 8].x < 0) break;
+      const Slot mine = slot_read(slot_tab, ds, g);
+      const int i0 = mine.gb * 8;
       const float *dsm = (const float *)(smem + lay.offData + ds * lay.dstage);
       if (mine.gb >= 0) {
         const float4 xa = *(const float4 *)(dsm + kXB * g), xb = *(const float4 *)(dsm + kXB * g + 4);
@@ -680,9 +690,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_mls_tc(KParams p, int d0, int D
         mbar_arrive(bar_full0 + 8 * s);
       }
     }
+    nst = kt;
   } else if (warp == 9) {
     // ------------------------------------------------ point-tile loader (TMA bulk copies)
     if (lane == 0) {
+      PackIter it;
+      pack_init(p, geo, it);
       int kt = 0;
       unsigned long long visited = 0;
       for (; pack_valid(it) && alive; ++kt) {
@@ -694,6 +707,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_mls_tc(KParams p, int d0, int D
           alive = false;
           break;
         }
+        // the slots travel with the copies: the arrive below releases them
+#pragma unroll 1
+        for (int q = 0; q < kKT / 8; ++q) slot_tab[ds * 8 + q] = make_int4(sl[q].gb, sl[q].lo, sl[q].hi, 0);
         const uint32_t dst = sbase + lay.offData + ds * lay.dstage;
         const uint32_t bar = bar_dfull0 + 8 * ds;
         // point-blocked layouts: slot q of the stage holds block sl[q].gb
@@ -726,20 +742,38 @@ __global__ void __launch_bounds__(kThreads, 1) k_mls_tc(KParams p, int d0, int D
         }
       }
       if (p.visited && d0 == 0 && visited) atomicAdd(p.visited, visited * (unsigned long long)(16 * TH));
-      // every issued copy has landed before the CTA may exit
+      // every issued copy has landed before the CTA may exit (waited before
+      // the end marker below completes one of these barriers once more)
       const int first = kt > DST ? kt - DST : 0;
       for (int k2 = first; k2 < kt; ++k2)
         mbar_wait(bar_dfull0 + 8 * (k2 % DST), (k2 / DST) & 1, p.err, ERR_WAIT_FULL, limit);
+      // end marker: stage kt with an empty first slot and no copies
+      if (alive) {
+        const int ds = kt % DST;
+        if (mbar_wait(bar_dempty0 + 8 * ds, ((kt / DST) & 1) ^ 1, p.err, ERR_WAIT_EMPTY, limit)) {
+          slot_tab[ds * 8] = make_int4(-1, 0, 0, 0);
+          mbar_arrive(bar_dfull0 + 8 * ds);
+        }
+      }
     }
     __syncwarp();
   } else {
     // ------------------------------------------------ MMA issuer
     if (lane == 0) {
       int kt = 0;
-      for (; pack_valid(it) && alive; ++kt) {
+      for (; alive; ++kt) {
         const int s = kt & 1;
-        Slot ua, ub;
-        pack_stage(p, it, -1, ua, -1, ub);
+        const int ds = kt % DST;
+        // the staged tile's first slot says whether stage kt exists; this
+        // thread is the ninth consumer of the staged tile, so the loader
+        // cannot reuse the slot table before it is read
+        if (!mbar_wait(bar_dfull0 + 8 * ds, (kt / DST) & 1, p.err, ERR_WAIT_FULL, limit)) {
+          alive = false;
+          break;
+        }
+        const bool last = slot_tab[ds * 8].x < 0;
+        mbar_arrive(bar_dempty0 + 8 * ds);
+        if (last) break;
         if (!mbar_wait(bar_full0 + 8 * s, (kt >> 1) & 1, p.err, ERR_WAIT_FULL, limit)) {
           alive = false;
           break;
@@ -773,10 +807,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_mls_tc(KParams p, int d0, int D
   __syncthreads();   // every role has left its loop (the stabiliser split is read below)
 
   // ------------------------------------------------ epilogue (warps 0-7)
-  // Has any point tile been visited?  (Recompute from the iterator start.)
-  PackIter it2;
-  pack_init(p, geo, it2);
-  const bool any_tile = pack_valid(it2);
+  // has any point tile been visited?
+  const bool any_tile = nst > 0;
   if (warp < 8) {
     const int wg = warp >> 2;
     // two accumulators: one warpgroup each; one accumulator: the warpgroups
@@ -793,7 +825,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mls_tc(KParams p, int d0, int D
     // truncated Gaussian), and the first staged levels and scales (below),
     // are fetched while the last MMAs drain
     const float mst = (WK == MLS_W_WENDLAND) ? 0.f : p.mstab[pix_i(p, pi)];
-    const int cflag = (WK == MLS_W_WENDLAND || p.trunc > 0.0) ? p.cnt[pix_i(p, pi)] : 0;
+    const int cflag = (WK == MLS_W_WENDLAND || p.trunc_on) ? p.cnt[pix_i(p, pi)] : 0;
     // level rows padded with NaN to P entries, a power of two >= L
     int P = 1;
     while (P < p.L) P *= 2;
@@ -847,7 +879,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mls_tc(KParams p, int d0, int D
       handover = cuncertain = count_uncertain<K>(cflag);
     } else {
       count = (int)(p.n < (1 << 30) ? p.n : (1 << 30));
-      if (p.trunc > 0.0) {
+      if (p.trunc_on) {
         // truncated Gaussian: the points in the pixel's box
         count = cflag & kCntMask;
         cuncertain = count_uncertain<K>(cflag);
