@@ -228,17 +228,33 @@ struct Slot {
   int lo, hi;   // point range of its row: points outside are masked
 };
 
+// The walk is warp-collective: every lane holds the same state, and lane k
+// caches the point range of row rbase + k, so one round trip of 32 parallel
+// loads serves 32 cell rows (a single thread loading row after row spent
+// longer on those loads than the producers spend on a stage).
 struct PackIter {
   int cx0, cx1, cy, cy1;
   int lo, hi;   // point range of the current row
   int gb;       // its next block
   bool all;
+  int rbase, rlo, rhi;   // this lane's cached row rbase + lane
 };
 
 __device__ __forceinline__ void pack_row(const KParams &p, PackIter &it) {
+  const int lane = threadIdx.x & 31;
   while (it.cy <= it.cy1) {
-    it.lo = cell_at(p, (int64_t)it.cy * p.gx + it.cx0);
-    it.hi = cell_at(p, (int64_t)it.cy * p.gx + it.cx1 + 1);
+    if (it.cy >= it.rbase + 32) {
+      it.rbase = it.cy;
+      const int r = it.cy + lane;
+      it.rlo = it.rhi = 0;
+      if (r <= it.cy1) {
+        it.rlo = cell_at(p, (int64_t)r * p.gx + it.cx0);
+        it.rhi = cell_at(p, (int64_t)r * p.gx + it.cx1 + 1);
+      }
+    }
+    const int k = it.cy - it.rbase;
+    it.lo = __shfl_sync(0xffffffffu, it.rlo, k);
+    it.hi = __shfl_sync(0xffffffffu, it.rhi, k);
     if (it.hi > it.lo) break;
     ++it.cy;
   }
@@ -248,6 +264,7 @@ __device__ __forceinline__ void pack_row(const KParams &p, PackIter &it) {
 __device__ __forceinline__ void pack_init(const KParams &p, const TileGeo *g, PackIter &it) {
   it.cx0 = it.cx1 = it.cy = it.cy1 = 0;
   it.lo = it.hi = it.gb = 0;
+  it.rbase = it.rlo = it.rhi = 0;
   it.all = ranges_all(p);
   if (it.all) {
     it.hi = (int)p.n;
@@ -257,6 +274,8 @@ __device__ __forceinline__ void pack_init(const KParams &p, const TileGeo *g, Pa
   it.cx1 = g->cr[1];
   it.cy = g->cr[2];
   it.cy1 = g->cr[3];
+  it.rbase = it.cy - 32;   // nothing cached yet
+  it.rlo = it.rhi = 0;
   if (it.cx0 > it.cx1) {
     it.cy = it.cy1 + 1;
     return;
@@ -693,62 +712,71 @@ __global__ void __launch_bounds__(kThreads, 1) k_mls_tc(KParams p, int d0, int D
     nst = kt;
   } else if (warp == 9) {
     // ------------------------------------------------ point-tile loader (TMA bulk copies)
-    if (lane == 0) {
+    // The whole warp walks the cell rows (collectively, see PackIter); lane q
+    // keeps slot q, lanes 0-7 write the slot table, lane 0 waits and arms the
+    // barrier, and the first slot of each run of consecutive blocks copies it.
+    {
       PackIter it;
       pack_init(p, geo, it);
       int kt = 0;
       unsigned long long visited = 0;
       for (; pack_valid(it) && alive; ++kt) {
         const int ds = kt % DST;
-        Slot sl[kKT / 8];
+        // lane q keeps slot q of the stage (no per-thread slot array: indexed
+        // in a loop it would live in local memory)
+        Slot mine{-1, 0, 0};
 #pragma unroll 1
-        for (int q = 0; q < kKT / 8; ++q) sl[q] = pack_take(p, it);
-        if (!mbar_wait(bar_dempty0 + 8 * ds, ((kt / DST) & 1) ^ 1, p.err, ERR_WAIT_EMPTY, limit)) {
+        for (int q = 0; q < kKT / 8; ++q) {
+          const Slot sq = pack_take(p, it);
+          if (lane == q) mine = sq;
+        }
+        int ok = 1;
+        if (lane == 0) ok = mbar_wait(bar_dempty0 + 8 * ds, ((kt / DST) & 1) ^ 1, p.err, ERR_WAIT_EMPTY, limit);
+        if (!__shfl_sync(0xffffffffu, ok, 0)) {
           alive = false;
           break;
         }
         // the slots travel with the copies: the arrive below releases them
-#pragma unroll 1
-        for (int q = 0; q < kKT / 8; ++q) slot_tab[ds * 8 + q] = make_int4(sl[q].gb, sl[q].lo, sl[q].hi, 0);
-        const uint32_t dst = sbase + lay.offData + ds * lay.dstage;
-        const uint32_t bar = bar_dfull0 + 8 * ds;
-        // point-blocked layouts: slot q of the stage holds block sl[q].gb
+        if (lane < kKT / 8) slot_tab[ds * 8 + lane] = make_int4(mine.gb, mine.lo, mine.hi, 0);
+        const bool valid = lane < kKT / 8 && mine.gb >= 0;
+        // points of this tile inside the visited ranges
+        if (valid) visited += (unsigned long long)max(0, min(mine.hi, mine.gb * 8 + 8) - max(mine.lo, mine.gb * 8));
+        // point-blocked layouts: slot q of the stage holds block gb_q
         // (positions 80 bytes, values 32 Dc + 16 bytes: every copy stays
         // 16-byte aligned); the filled slots are a prefix of the stage
         const int64_t nblk = p.n_pad >> 3;
         const uint32_t fbb = (uint32_t)(Dc * 8 + 4) * 4;
-        uint32_t nvalid = 0;
-#pragma unroll 1
-        for (int q = 0; q < kKT / 8; ++q) {
-          if (sl[q].gb < 0) break;
-          ++nvalid;
-          // points of this tile inside the visited ranges
-          visited += (unsigned long long)max(0, min(sl[q].hi, sl[q].gb * 8 + 8) - max(sl[q].lo, sl[q].gb * 8));
-        }
-        mbar_expect_tx(bar, nvalid * (kXB * 4 + fbb));
-        // one copy per run of consecutive blocks
-        int q = 0;
-#pragma unroll 1
-        while (q < (int)nvalid) {
-          int r = q + 1;
-          while (r < (int)nvalid && sl[r].gb == sl[r - 1].gb + 1) ++r;
-          const uint32_t nb = (uint32_t)(r - q);
+        const uint32_t vmask = __ballot_sync(0xffffffffu, valid);
+        const int prev = __shfl_up_sync(0xffffffffu, mine.gb, 1);
+        // one copy per run of consecutive blocks, issued by its first slot
+        const bool start = valid && (lane == 0 || prev + 1 != mine.gb);
+        const uint32_t smask = __ballot_sync(0xffffffffu, start);
+        const uint32_t dst = sbase + lay.offData + ds * lay.dstage;
+        const uint32_t bar = bar_dfull0 + 8 * ds;
+        if (lane == 0) mbar_expect_tx(bar, (uint32_t)__popc(vmask) * (kXB * 4 + fbb));
+        __syncwarp();
+        if (start) {
+          const uint32_t above = smask & ~((2u << lane) - 1u);    // later run starts
+          const int end = above ? __ffs(above) - 1 : __popc(vmask);
+          const uint32_t nb = (uint32_t)(end - lane);
           // checked build: the copied blocks lie inside the point arrays
-          const int64_t blk = chk(p.err, sl[q].gb, nblk - nb + 1, SITE_BLOCK);
-          bulk_g2s(dst + q * kXB * 4, p.xyb + blk * kXB, nb * kXB * 4, bar);
-          bulk_g2s(dst + kPosFloats * 4 + q * fbb, p.fb + ((size_t)pass * nblk + blk) * (Dc * 8 + 4), nb * fbb,
-                   bar);
-          q = r;
+          const int64_t blk = chk(p.err, mine.gb, nblk - nb + 1, SITE_BLOCK);
+          bulk_g2s(dst + lane * kXB * 4, p.xyb + blk * kXB, nb * kXB * 4, bar);
+          bulk_g2s(dst + kPosFloats * 4 + lane * fbb, p.fb + ((size_t)pass * nblk + blk) * (Dc * 8 + 4), nb * fbb, bar);
         }
+        __syncwarp();
       }
-      if (p.visited && d0 == 0 && visited) atomicAdd(p.visited, visited * (unsigned long long)(16 * TH));
+      __syncwarp();
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) visited += __shfl_xor_sync(0xffffffffu, visited, o);
+      if (lane == 0 && p.visited && d0 == 0 && visited) atomicAdd(p.visited, visited * (unsigned long long)(16 * TH));
       // every issued copy has landed before the CTA may exit (waited before
       // the end marker below completes one of these barriers once more)
       const int first = kt > DST ? kt - DST : 0;
-      for (int k2 = first; k2 < kt; ++k2)
+      for (int k2 = first; k2 < kt && lane == 0; ++k2)
         mbar_wait(bar_dfull0 + 8 * (k2 % DST), (k2 / DST) & 1, p.err, ERR_WAIT_FULL, limit);
       // end marker: stage kt with an empty first slot and no copies
-      if (alive) {
+      if (alive && lane == 0) {
         const int ds = kt % DST;
         if (mbar_wait(bar_dempty0 + 8 * ds, ((kt / DST) & 1) ^ 1, p.err, ERR_WAIT_EMPTY, limit)) {
           slot_tab[ds * 8] = make_int4(-1, 0, 0, 0);
