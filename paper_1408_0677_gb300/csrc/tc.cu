@@ -228,77 +228,100 @@ struct Slot {
   int lo, hi;   // point range of its row: points outside are masked
 };
 
-// The walk is warp-collective: every lane holds the same state, and lane k
-// caches the point range of row rbase + k, so one round trip of 32 parallel
-// loads serves 32 cell rows (a single thread loading row after row spent
-// longer on those loads than the producers spend on a stage).
-struct PackIter {
-  int cx0, cx1, cy, cy1;
-  int lo, hi;   // point range of the current row
-  int gb;       // its next block
-  bool all;
-  int rbase, rlo, rhi;   // this lane's cached row rbase + lane
+// The walk is warp-collective.  A window of 32 cell rows is loaded at once
+// (lane k: the k-th row of the window, one round trip of parallel loads); each row's
+// 8-point blocks get consecutive global slot numbers, starting at S_k (a
+// prefix sum over the window, continuing the previous windows).  Stage kt
+// holds the global slots 8 kt .. 8 kt + 7; lane q < 8 finds the row of slot
+// 8 kt + q as the last row k with S_k <= 8 kt + q (a ballot per slot) and
+// forms its slot from that row's range, so no thread walks slot by slot.
+struct PackW {
+  int cx0, cx1, cy1;
+  int rnext;          // first row not yet loaded
+  int W0, T;          // global slots [W0, T) belong to the loaded window
+  int J;              // first global slot of the next stage
+  bool all;           // every point (one row [0, n))
+  int rlo, rhi, S;    // this lane's row of the window: point range, first slot
 };
 
-__device__ __forceinline__ void pack_row(const KParams &p, PackIter &it) {
+__device__ __forceinline__ void packw_load(const KParams &p, PackW &w) {
   const int lane = threadIdx.x & 31;
-  while (it.cy <= it.cy1) {
-    if (it.cy >= it.rbase + 32) {
-      it.rbase = it.cy;
-      const int r = it.cy + lane;
-      it.rlo = it.rhi = 0;
-      if (r <= it.cy1) {
-        it.rlo = cell_at(p, (int64_t)r * p.gx + it.cx0);
-        it.rhi = cell_at(p, (int64_t)r * p.gx + it.cx1 + 1);
-      }
-    }
-    const int k = it.cy - it.rbase;
-    it.lo = __shfl_sync(0xffffffffu, it.rlo, k);
-    it.hi = __shfl_sync(0xffffffffu, it.rhi, k);
-    if (it.hi > it.lo) break;
-    ++it.cy;
+  const int r = w.rnext + lane;
+  w.rlo = w.rhi = 0;
+  if (r <= w.cy1) {
+    w.rlo = cell_at(p, (int64_t)r * p.gx + w.cx0);
+    w.rhi = cell_at(p, (int64_t)r * p.gx + w.cx1 + 1);
   }
-  it.gb = it.lo >> 3;
+  const int nb = (w.rhi > w.rlo) ? ((w.rhi - 1) >> 3) - (w.rlo >> 3) + 1 : 0;
+  int inc = nb;   // inclusive prefix sum over the lanes
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int v = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += v;
+  }
+  w.W0 = w.T;
+  w.S = w.W0 + inc - nb;
+  w.T = w.W0 + __shfl_sync(0xffffffffu, inc, 31);
+  w.rnext += 32;
 }
 
-__device__ __forceinline__ void pack_init(const KParams &p, const TileGeo *g, PackIter &it) {
-  it.cx0 = it.cx1 = it.cy = it.cy1 = 0;
-  it.lo = it.hi = it.gb = 0;
-  it.rbase = it.rlo = it.rhi = 0;
-  it.all = ranges_all(p);
-  if (it.all) {
-    it.hi = (int)p.n;
+__device__ __forceinline__ void packw_init(const KParams &p, const TileGeo *g, PackW &w) {
+  w.all = ranges_all(p);
+  w.J = 0;
+  w.W0 = 0;
+  w.rlo = w.rhi = w.S = 0;
+  w.cx0 = w.cx1 = w.cy1 = 0;
+  if (w.all) {
+    w.T = (int)((p.n + 7) >> 3);   // blocks of [0, n)
+    w.rnext = 1;
+    w.cy1 = 0;
     return;
   }
-  it.cx0 = g->cr[0];
-  it.cx1 = g->cr[1];
-  it.cy = g->cr[2];
-  it.cy1 = g->cr[3];
-  it.rbase = it.cy - 32;   // nothing cached yet
-  it.rlo = it.rhi = 0;
-  if (it.cx0 > it.cx1) {
-    it.cy = it.cy1 + 1;
-    return;
-  }
-  pack_row(p, it);
+  w.cx0 = g->cr[0];
+  w.cx1 = g->cr[1];
+  w.cy1 = g->cr[3];
+  w.rnext = g->cr[2];
+  w.T = 0;
+  if (w.cx0 > w.cx1) w.rnext = w.cy1 + 1;   // no cells: nothing to visit
 }
 
-__device__ __forceinline__ bool pack_valid(const PackIter &it) {
-  return it.all ? (it.gb * 8 < it.hi) : (it.cy <= it.cy1);
+// Make the window hold slot J (load windows while it lies past them and rows
+// remain); returns whether the stage starting at J exists.
+__device__ __forceinline__ bool packw_valid(const KParams &p, PackW &w) {
+  while (w.J >= w.T && w.rnext <= w.cy1) packw_load(p, w);
+  return w.J < w.T;
 }
 
-__device__ __forceinline__ Slot pack_take(const KParams &p, PackIter &it) {
-  Slot s{-1, 0, 0};
-  if (!pack_valid(it)) return s;
-  s.gb = it.gb;
-  s.lo = it.lo;
-  s.hi = it.hi;
-  ++it.gb;
-  if (!it.all && it.gb * 8 >= it.hi) {
-    ++it.cy;
-    pack_row(p, it);
+// The stage starting at J: lane q < 8 returns slot q (gb < 0: empty), J
+// advances by 8.  Requires packw_valid.
+__device__ __forceinline__ Slot packw_stage(const KParams &p, PackW &w) {
+  const int lane = threadIdx.x & 31;
+  Slot mine{-1, 0, 0};
+  if (w.all) {
+    const int j = w.J + lane;
+    if (lane < kKT / 8 && j < w.T) mine = Slot{j, 0, (int)p.n};
+    w.J += kKT / 8;
+    return mine;
   }
-  return s;
+  for (;;) {
+    // slots of this stage inside the loaded window
+    uint32_t m[kKT / 8];
+#pragma unroll
+    for (int q = 0; q < kKT / 8; ++q) m[q] = __ballot_sync(0xffffffffu, w.S <= w.J + q);
+    uint32_t mq = m[0];
+#pragma unroll
+    for (int q = 1; q < kKT / 8; ++q) mq = (lane == q) ? m[q] : mq;
+    const int j = w.J + lane;
+    const int k = mq ? 31 - __clz(mq) : 0;
+    const int lo = __shfl_sync(0xffffffffu, w.rlo, k);
+    const int hi = __shfl_sync(0xffffffffu, w.rhi, k);
+    const int S0 = __shfl_sync(0xffffffffu, w.S, k);
+    if (lane < kKT / 8 && j >= w.W0 && j < w.T) mine = Slot{(lo >> 3) + (j - S0), lo, hi};
+    if (w.J + kKT / 8 <= w.T || w.rnext > w.cy1) break;
+    packw_load(p, w);   // the stage continues into the next window
+  }
+  w.J += kKT / 8;
+  return mine;
 }
 
 __device__ __forceinline__ bool slot_has(const Slot &s, int i) { return s.gb >= 0 && i >= s.lo && i < s.hi; }
@@ -712,24 +735,18 @@ __global__ void __launch_bounds__(kThreads, 1) k_mls_tc(KParams p, int d0, int D
     nst = kt;
   } else if (warp == 9) {
     // ------------------------------------------------ point-tile loader (TMA bulk copies)
-    // The whole warp walks the cell rows (collectively, see PackIter); lane q
+    // The whole warp walks the cell rows (collectively, see PackW); lane q
     // keeps slot q, lanes 0-7 write the slot table, lane 0 waits and arms the
     // barrier, and the first slot of each run of consecutive blocks copies it.
     {
-      PackIter it;
-      pack_init(p, geo, it);
+      PackW it;
+      packw_init(p, geo, it);
       int kt = 0;
       unsigned long long visited = 0;
-      for (; pack_valid(it) && alive; ++kt) {
+      for (; alive && packw_valid(p, it); ++kt) {
         const int ds = kt % DST;
-        // lane q keeps slot q of the stage (no per-thread slot array: indexed
-        // in a loop it would live in local memory)
-        Slot mine{-1, 0, 0};
-#pragma unroll 1
-        for (int q = 0; q < kKT / 8; ++q) {
-          const Slot sq = pack_take(p, it);
-          if (lane == q) mine = sq;
-        }
+        // lane q keeps slot q of the stage
+        const Slot mine = packw_stage(p, it);
         int ok = 1;
         if (lane == 0) ok = mbar_wait(bar_dempty0 + 8 * ds, ((kt / DST) & 1) ^ 1, p.err, ERR_WAIT_EMPTY, limit);
         if (!__shfl_sync(0xffffffffu, ok, 0)) {
