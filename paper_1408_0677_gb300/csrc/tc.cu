@@ -10,16 +10,19 @@
 // operand G depends only on the tile and the points; only w is generated per
 // (pixel, point) pair.  This is the P.V product of attention with
 // P = exp(...):
-//   - warps 0-3 generate the weights in registers (one exp2 per pair, FP32)
+//   - warps 0-7 generate the weights in registers (FP32; separable factors
+//     for the Gaussian, one approximate square root per pair for Wendland)
 //     and store them as FP16/BF16 into a 128B-swizzled K-major A tile;
-//   - warps 4-7 build G for the point tile as a hi + lo pair of FP16/BF16
+//   - warps 8-15 build G for the point tile as a hi + lo pair of FP16/BF16
 //     operands (G = G_hi + G_lo to ~22 / 16 bits: the moment matrix needs more
 //     than one 16-bit rounding, the weights do not);
-//   - one thread of warp 8 issues tcgen05.mma (kind::f16, FP32 accumulate in
+//   - one thread of warp 16 issues tcgen05.mma (kind::f16, FP32 accumulate in
 //     TMEM) for two 128-pixel accumulators, D += A.G_hi + A.G_lo;
-//   - the epilogue reads the moments back with tcgen05.ld, shifts M to the
-//     pixel frame, solves (FP32 Cholesky + refinement, FP64 above cond_fp64),
-//     evaluates the fit, labels the iso-bands and stores.
+//   - warp 17 walks the point cells and stages the point tiles by TMA bulk
+//     copies;
+//   - the epilogue (warps 0-15) reads the moments back with tcgen05.ld, shifts
+//     M to the pixel frame, solves (FP32 Cholesky + refinement, FP64 above
+//     cond_fp64), evaluates the fit, labels the iso-bands and stores.
 // Pixels whose condition estimate exceeds cond_recompute, whose support count
 // sits near a degree threshold, or whose nearest point is so far that range
 // clipping of G could matter, are handed to the FP64 path.
@@ -42,7 +45,15 @@ constexpr int kM = 128;           // pixels per accumulator (TMEM lanes)
 constexpr int kKT = 64;           // points per stage = one 128-byte row of 16-bit values
 constexpr int kStages = 2;
 constexpr int kNMax = 256;        // operand columns per accumulator (TMEM budget 2 x 256)
-constexpr int kThreads = 320;     // 10 warps: 4 weights, 4 operand, 1 MMA, 1 loader
+// 18 warps: 8 weight producers (each half of a stage's points for one pixel
+// row of both accumulators; the epilogue's warps too), 8 operand builders,
+// the MMA issuer and the point-tile loader
+constexpr int kWeightWarps = 8;
+constexpr int kBuildWarps = 8;
+constexpr int kMmaWarp = kWeightWarps + kBuildWarps;
+constexpr int kLoadWarp = kMmaWarp + 1;
+constexpr int kThreads = 32 * (kLoadWarp + 1);
+static_assert(kWeightWarps == 8 && kBuildWarps == 8, "the weight warps cover 256 pixels; the epilogue pairs each with a builder warp");
 constexpr int kDcMax = 40;        // value dimensions per pass (bounds the staged point tile)
 constexpr float kRMax = 15.f;     // |x~|_inf clip of the operand (FP16 range of x~^4)
 constexpr float kLog2e = 1.4426950408889634f;
@@ -57,8 +68,8 @@ constexpr int kEXS = 68;
 // column and row factors land on the same bank and every store pair conflicts.
 constexpr int kRowOff = 16 * kEXS + 16;
 constexpr int kExyFloats = 32 * kEXS + 16;
-constexpr int kGaussHdr = 4 * 32 * 4;        // per weight warp: alpha[16], beta[16]
-constexpr int kPrmBytes = kGaussHdr + 2 * kExyFloats * 4;   // >= the Wendland point parameters (4 KB)
+constexpr int kGaussHdr = kWeightWarps * 32 * 4;   // per weight warp: alpha[16], beta[16]
+constexpr int kPrmBytes = kGaussHdr + 2 * kExyFloats * 4;   // >= the Wendland point parameters (8 KB)
 // Common factor of all FP16 weights (the fit does not depend on it): the
 // largest weight becomes 2^14, so the low half of a split weight stays in
 // the FP16 normal range for weights down to 2^-17 of the largest (unscaled,
@@ -151,6 +162,20 @@ __device__ __forceinline__ void split8(const float (&x)[8], uint4 &hi, uint4 &lo
   }
   hi = make_uint4(h[0], h[1], h[2], h[3]);
   lo = make_uint4(l[0], l[1], l[2], l[3]);
+}
+
+// Four operand values -> hi and lo 8-byte chunks (G = hi + lo).
+template <bool FP16>
+__device__ __forceinline__ void split4(const float (&x)[4], uint2 &hi, uint2 &lo) {
+  uint32_t h[2], l[2];
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    h[q] = pack2<FP16>(x[2 * q], x[2 * q + 1]);
+    const float2 b = unpack2<FP16>(h[q]);
+    l[q] = pack2<FP16>(x[2 * q] - b.x, x[2 * q + 1] - b.y);
+  }
+  hi = make_uint2(h[0], h[1]);
+  lo = make_uint2(l[0], l[1]);
 }
 
 __device__ __forceinline__ float ex2_approx(float x) {
@@ -371,24 +396,24 @@ __global__ void __launch_bounds__(kThreads, 1) k_mls_tc(KParams p, int d0, int D
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < kStages; ++s) {
-      mbar_init(bar_full0 + 8 * s, 8);
+      mbar_init(bar_full0 + 8 * s, kWeightWarps + kBuildWarps);
       mbar_init(bar_empty0 + 8 * s, 1);
     }
     mbar_init(bar_acc, 1);
     for (int ds = 0; ds < DST; ++ds) {
       mbar_init(bar_dfull0 + 8 * ds, 1);
-      mbar_init(bar_dempty0 + 8 * ds, 9);   // eight producer warps and the MMA issuer
+      mbar_init(bar_dempty0 + 8 * ds, kWeightWarps + kBuildWarps + 1);   // the producer warps and the MMA issuer
     }
-    mbar_init(bar_exy0, 4);
-    mbar_init(bar_exy0 + 8, 4);
+    mbar_init(bar_exy0, kWeightWarps);
+    mbar_init(bar_exy0 + 8, kWeightWarps);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   // moment frame of the tile: the weighted centroid of the points near its
   // centre (from the prepass); the fit is solved in this frame
   const int tile = (v0 >> 4) * p.tiles_x + (u0 >> 4);
   const float cxs = p.tcen[2 * tile_i(p, tile)], cys = p.tcen[2 * tile_i(p, tile) + 1];
-  if (warp == 8) tmem_alloc(smem_u32(tmem_slot), 512);
-  if (warp == 9) tile_geometry(p, u0, v0, TH, cxs, cys, lane, geo);
+  if (warp == kMmaWarp) tmem_alloc(smem_u32(tmem_slot), 512);
+  if (warp == kLoadWarp) tile_geometry(p, u0, v0, TH, cxs, cys, lane, geo);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -402,7 +427,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mls_tc(KParams p, int d0, int D
   int4 *slot_tab = (int4 *)(smem + lay.offBar + kOffSlots);
   int nst = 0;   // point tiles this thread consumed (the epilogue reads whether any)
 
-  if (warp < 4 && WK == MLS_W_GAUSS) {
+  if (warp < kWeightWarps && WK == MLS_W_GAUSS) {
     // ------------------------------------------------ weight producers (Gaussian, separable)
     // w = exp2(L_p - log2e |x~ - delta_p|^2) with L_p = log2e m_p.  The tile's
     // pixels lie on 16 columns dx_c and 16 rows dy_r, so with the stabiliser
@@ -417,7 +442,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_mls_tc(KParams p, int d0, int D
     // stabiliser (pixels whose factor would leave the FP32 range are handed over).
     // The truncated Gaussian's box |dx|, |dy| < c is separable too: a column
     // (row) factor is zero where the point is c or more away along x (y).
+    // thread t: pixel row m = t mod 128 of both accumulators, chunks (8
+    // points each) 4 hh .. 4 hh + 3 of every stage
     const int t = threadIdx.x;
+    const int m = t & 127, hh = t >> 7;
     const bool boxed = p.trunc_on;
     const float cbox = p.trunc_f;
     float *sAB = (float *)(smem + lay.offPrm) + 32 * warp;     // this warp's alpha[16], beta[16]
@@ -436,14 +464,19 @@ __global__ void __launch_bounds__(kThreads, 1) k_mls_tc(KParams p, int d0, int D
       sAB[lane] = (lane < 16) ? a : ((r < TH) ? b : 0.f);
       __syncwarp();
     }
-    // this thread's factor rows: point j, columns (half 0) or rows (half 1)
-    const int jp = t >> 1, half = t & 1;
-    float off[16];
+    // this thread's factor rows: point jp, columns (half 0) or rows (half 1),
+    // entries fk(kk) = 4 (kk >> 1) + (kk & 1) + 2 kh, kk = 0..7, of the 16
+    // (the partners of a point are lanes ^ 1, the other half, and ^ 2, the
+    // other entries; with entries 2 rows apart the 32 lanes' stores fall on
+    // distinct banks)
+    const int jp = t >> 2, kh = (t >> 1) & 1, half = t & 1;
+    auto fk = [&](int kk) { return 4 * (kk >> 1) + (kk & 1) + 2 * kh; };
+    float off[8];
 #pragma unroll
-    for (int k = 0; k < 16; ++k) off[k] = half ? geo->row[k] : geo->col[k];
+    for (int kk = 0; kk < 8; ++kk) off[kk] = half ? geo->row[fk(kk)] : geo->col[fk(kk)];
     // this thread's pixels: column c, rows r0 (and r0 + 8), and their
     // corrections 2^(L_p - alpha_c - beta_r)
-    const int cown = t & 15, r0 = t >> 4;
+    const int cown = m & 15, r0 = m >> 4;
     float gcor[2];
 #pragma unroll
     for (int a = 0; a < 2; ++a) {
@@ -474,24 +507,23 @@ __global__ void __launch_bounds__(kThreads, 1) k_mls_tc(KParams p, int d0, int D
           ok = fmaxf(fabsf(x), fabsf(y)) <= kRMax;
           pos = half ? y : x;
         }
-        float e[16];
+        float e[8];
         float mx = -INFINITY;
 #pragma unroll
-        for (int k = 0; k < 16; ++k) {
-          const float d = off[k] - pos;
-          e[k] = fmaf(-kLog2e * d, d, sAB[16 * half + k]);
-          if (half == 0 || k < TH) mx = fmaxf(mx, e[k]);
+        for (int kk = 0; kk < 8; ++kk) {
+          const float d = off[kk] - pos;
+          e[kk] = fmaf(-kLog2e * d, d, sAB[16 * half + fk(kk)]);
+          if (half == 0 || fk(kk) < TH) mx = fmaxf(mx, e[kk]);
         }
+        mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 2));
         const float other = __shfl_xor_sync(0xffffffffu, mx, 1);
         const float sh = half ? 0.5f * (mx - other) : 0.5f * (other - mx);   // Y' = Y - sh, X' = X + sh
         float *dst = tab + half * kRowOff + jp;
-        if (boxed) {   // uniform over the grid
 #pragma unroll
-          for (int k = 0; k < 16; ++k)
-            dst[k * kEXS] = (ok && fabsf(off[k] - pos) < cbox) ? ex2_approx(half ? e[k] - sh : e[k] + sh) : 0.f;
-        } else {
-#pragma unroll
-          for (int k = 0; k < 16; ++k) dst[k * kEXS] = ok ? ex2_approx(half ? e[k] - sh : e[k] + sh) : 0.f;
+        for (int kk = 0; kk < 8; ++kk) {
+          // the truncated Gaussian's box (uniform over the grid)
+          const bool in = ok && (!boxed || fabsf(off[kk] - pos) < cbox);
+          dst[fk(kk) * kEXS] = in ? ex2_approx(half ? e[kk] - sh : e[kk] + sh) : 0.f;
         }
       }
       __syncwarp();
@@ -510,7 +542,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mls_tc(KParams p, int d0, int D
       const float *fy0 = tab + kRowOff + r0 * kEXS;
       const float *fy1 = tab + kRowOff + (r0 + 8) * kEXS;
 #pragma unroll 2
-      for (int c = 0; c < 8; ++c) {
+      for (int c = 4 * hh; c < 4 * hh + 4; ++c) {
         const float4 xa = *(const float4 *)(fx + 8 * c), xb = *(const float4 *)(fx + 8 * c + 4);
         const float4 ya = *(const float4 *)(fy0 + 8 * c), yb = *(const float4 *)(fy0 + 8 * c + 4);
         const float g0 = gcor[0];
@@ -527,21 +559,24 @@ __global__ void __launch_bounds__(kThreads, 1) k_mls_tc(KParams p, int d0, int D
           q1.x = pack2<FP16>(xa.x * za.x * g1, xa.y * za.y * g1); q1.y = pack2<FP16>(xa.z * za.z * g1, xa.w * za.w * g1);
           q1.z = pack2<FP16>(xb.x * zb.x * g1, xb.y * zb.y * g1); q1.w = pack2<FP16>(xb.z * zb.z * g1, xb.w * zb.w * g1);
         }
-        *(uint4 *)(A0 + sw128_off(t, c)) = q0;
-        *(uint4 *)(A1 + sw128_off(t, c)) = q1;
+        *(uint4 *)(A0 + sw128_off(m, c)) = q0;
+        *(uint4 *)(A1 + sw128_off(m, c)) = q1;
       }
       fence_proxy_async();
       __syncwarp();
       if (lane == 0) mbar_arrive(bar_full0 + 8 * s);
     }
     nst = kt;
-  } else if (warp < 4) {
+  } else if (warp < kWeightWarps) {
     // ------------------------------------------------ weight producers (Wendland)
-    const int t = threadIdx.x;                 // row t of every accumulator
+    // thread t: row m = t mod 128 of every accumulator, the stage's points
+    // 32 hh .. 32 hh + 31 (this warp's point parameters)
+    const int t = threadIdx.x;
+    const int m = t & 127, hh = t >> 7;
     float dx[NACC], dy[NACC], E[NACC];
 #pragma unroll
     for (int a = 0; a < NACC; ++a) {
-      const int q = a * 128 + t;
+      const int q = a * 128 + m;
       const int u = u0 + (q & 15), v = v0 + (q >> 4);
       dx[a] = geo->col[q & 15];
       dy[a] = geo->row[q >> 4];
@@ -561,14 +596,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_mls_tc(KParams p, int d0, int D
         break;
       }
       if (slot_tab[ds * 8].x < 0) break;
-      const Slot sl2[2] = {slot_read(slot_tab, ds, lane >> 3), slot_read(slot_tab, ds, (lane >> 3) + 4)};
       const float *dxs = (const float *)(smem + lay.offData + ds * lay.dstage);
       __syncwarp();
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const int j = lane + 32 * h;
+      {
+        const int j = 32 * hh + lane;
+        const Slot sl = slot_read(slot_tab, ds, j >> 3);
         float x = 0.f, y = 0.f;
-        bool ok = slot_has(sl2[h], sl2[h].gb * 8 + (j & 7));
+        bool ok = slot_has(sl, sl.gb * 8 + (j & 7));
         if (ok) {
           // blocked tile: 8-point blocks of (x[8], y[8])
           x = dxs[(j >> 3) * kXB + (j & 7)] - cxs;
@@ -592,7 +626,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mls_tc(KParams p, int d0, int D
       unsigned char *A0 = smem + kOffA + (s * 2 + 0) * kABytes;
       unsigned char *A1 = smem + kOffA + (s * 2 + 1) * kABytes;
 #pragma unroll 1
-      for (int c = 0; c < 8; ++c) {
+      for (int c = 4 * hh; c < 4 * hh + 4; ++c) {
         float w0[8], w1[8];
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
@@ -611,19 +645,23 @@ __global__ void __launch_bounds__(kThreads, 1) k_mls_tc(KParams p, int d0, int D
           q1.x = pack2<FP16>(w1[0], w1[1]); q1.y = pack2<FP16>(w1[2], w1[3]);
           q1.z = pack2<FP16>(w1[4], w1[5]); q1.w = pack2<FP16>(w1[6], w1[7]);
         }
-        *(uint4 *)(A0 + sw128_off(t, c)) = q0;
-        *(uint4 *)(A1 + sw128_off(t, c)) = q1;
+        *(uint4 *)(A0 + sw128_off(m, c)) = q0;
+        *(uint4 *)(A1 + sw128_off(m, c)) = q1;
       }
       fence_proxy_async();
       __syncwarp();
       if (lane == 0) mbar_arrive(bar_full0 + 8 * s);
     }
     nst = kt;
-  } else if (warp < 8) {
+  } else if (warp < kMmaWarp) {
     // ------------------------------------------------ operand builders
-    const int tt = threadIdx.x - 128;
-    const int g = tt & 7;          // 8-point group of the tile
-    const int rr = tt >> 3;        // row class 0..15
+    // thread: points 4 hp .. 4 hp + 3 of the 8-point group g, the moment row
+    // rr and the value rows of dimensions rr, rr + 16, ...  (a warp writes two
+    // whole 128-byte rows per store; the per-point masking and basis values
+    // are shared by the rows of a thread)
+    const int tt = threadIdx.x - 32 * kWeightWarps;
+    const int hp = tt & 1, g = (tt >> 1) & 7;
+    const int rr = tt >> 4;        // row class 0..15
     // exponents of this thread's monomial row (fixed for the whole kernel)
     const int mex = mono_ex(rr < 15 ? rr : 0), mey = mono_ey(rr < 15 ? rr : 0);
     const float mrow = (rr < NM) ? 1.f : 0.f;
@@ -631,26 +669,26 @@ __global__ void __launch_bounds__(kThreads, 1) k_mls_tc(KParams p, int d0, int D
     for (; alive; ++kt) {
       const int s = kt & 1;
       const int ds = kt % DST;
-      float xv[8], yv[8], msk[8];
+      float xv[4], yv[4], msk[4];
       if (!mbar_wait(bar_dfull0 + 8 * ds, (kt / DST) & 1, p.err, ERR_WAIT_FULL, limit)) {
         alive = false;
         break;
       }
       if (slot_tab[ds * 8].x < 0) break;
       const Slot mine = slot_read(slot_tab, ds, g);
-      const int i0 = mine.gb * 8;
+      const int i0 = mine.gb * 8 + 4 * hp;
       const float *dsm = (const float *)(smem + lay.offData + ds * lay.dstage);
       if (mine.gb >= 0) {
-        const float4 xa = *(const float4 *)(dsm + kXB * g), xb = *(const float4 *)(dsm + kXB * g + 4);
-        const float4 ya = *(const float4 *)(dsm + kXB * g + 8), yb = *(const float4 *)(dsm + kXB * g + 12);
-        xv[0] = xa.x; xv[1] = xa.y; xv[2] = xa.z; xv[3] = xa.w; xv[4] = xb.x; xv[5] = xb.y; xv[6] = xb.z; xv[7] = xb.w;
-        yv[0] = ya.x; yv[1] = ya.y; yv[2] = ya.z; yv[3] = ya.w; yv[4] = yb.x; yv[5] = yb.y; yv[6] = yb.z; yv[7] = yb.w;
+        const float4 xa = *(const float4 *)(dsm + kXB * g + 4 * hp);
+        const float4 ya = *(const float4 *)(dsm + kXB * g + 8 + 4 * hp);
+        xv[0] = xa.x; xv[1] = xa.y; xv[2] = xa.z; xv[3] = xa.w;
+        yv[0] = ya.x; yv[1] = ya.y; yv[2] = ya.z; yv[3] = ya.w;
       } else {
 #pragma unroll
-        for (int j = 0; j < 8; ++j) xv[j] = yv[j] = 0.f;
+        for (int j = 0; j < 4; ++j) xv[j] = yv[j] = 0.f;
       }
 #pragma unroll
-      for (int j = 0; j < 8; ++j) {
+      for (int j = 0; j < 4; ++j) {
         const int i = i0 + j;
         xv[j] -= cxs;
         yv[j] -= cys;
@@ -662,28 +700,28 @@ __global__ void __launch_bounds__(kThreads, 1) k_mls_tc(KParams p, int d0, int D
         alive = false;
         break;
       }
-      unsigned char *Bh = smem + lay.offB + (s * 2 + 0) * lay.bpart;
-      unsigned char *Bl = smem + lay.offB + (s * 2 + 1) * lay.bpart;
+      unsigned char *Bh = smem + lay.offB + (s * 2 + 0) * lay.bpart + 8 * hp;
+      unsigned char *Bl = smem + lay.offB + (s * 2 + 1) * lay.bpart + 8 * hp;
       // monomial row rr of the moment part (rows 0..15; rows >= NM are zero),
       // branch-free: x^ex = (x or 1)(x^2 or 1)(x^4 or 1) by the bits of ex
       {
-        float val[8];
+        float val[4];
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
+        for (int j = 0; j < 4; ++j) {
           const float x1 = xv[j], x2 = x1 * x1, y1 = yv[j], y2 = y1 * y1;
           const float px = ((mex & 1) ? x1 : 1.f) * ((mex & 2) ? x2 : 1.f) * ((mex & 4) ? x2 * x2 : 1.f);
           const float py = ((mey & 1) ? y1 : 1.f) * ((mey & 2) ? y2 : 1.f) * ((mey & 4) ? y2 * y2 : 1.f);
           val[j] = mrow * msk[j] * px * py;
         }
-        uint4 hi, lo;
-        split8<FP16>(val, hi, lo);
-        *(uint4 *)(Bh + sw128_off(rr, g)) = hi;
-        *(uint4 *)(Bl + sw128_off(rr, g)) = lo;
+        uint2 hi, lo;
+        split4<FP16>(val, hi, lo);
+        *(uint2 *)(Bh + sw128_off(rr, g)) = hi;
+        *(uint2 *)(Bl + sw128_off(rr, g)) = lo;
       }
       // value rows 16 + d K + a, dimensions d = rr, rr + 16, ...
-      float bas[K][8];
+      float bas[K][4];
 #pragma unroll
-      for (int j = 0; j < 8; ++j) {
+      for (int j = 0; j < 4; ++j) {
         bas[0][j] = msk[j];
         if (K > 1) { bas[1][j] = msk[j] * xv[j]; bas[2][j] = msk[j] * yv[j]; }
         if (K > 3) {
@@ -693,37 +731,34 @@ __global__ void __launch_bounds__(kThreads, 1) k_mls_tc(KParams p, int d0, int D
         }
       }
       for (int d = rr; d < Dc; d += 16) {
-        float fv[8];
+        float fv[4];
         if (mine.gb >= 0) {
-          const float *fr = dsm + kPosFloats + g * (Dc * 8 + 4) + d * 8;
-          const float4 fa = *(const float4 *)fr, fb = *(const float4 *)(fr + 4);
-          fv[0] = fa.x; fv[1] = fa.y; fv[2] = fa.z; fv[3] = fa.w; fv[4] = fb.x; fv[5] = fb.y; fv[6] = fb.z; fv[7] = fb.w;
+          const float4 fa = *(const float4 *)(dsm + kPosFloats + g * (Dc * 8 + 4) + d * 8 + 4 * hp);
+          fv[0] = fa.x; fv[1] = fa.y; fv[2] = fa.z; fv[3] = fa.w;
           // slots past the copied tile hold stale shared memory: never multiply them
 #pragma unroll
-          for (int j = 0; j < 8; ++j) fv[j] = (msk[j] != 0.f) ? fv[j] : 0.f;
+          for (int j = 0; j < 4; ++j) fv[j] = (msk[j] != 0.f) ? fv[j] : 0.f;
         } else {
 #pragma unroll
-          for (int j = 0; j < 8; ++j) fv[j] = 0.f;
+          for (int j = 0; j < 4; ++j) fv[j] = 0.f;
         }
 #pragma unroll
         for (int a = 0; a < K; ++a) {
-          float val[8];
+          float val[4];
 #pragma unroll
-          for (int j = 0; j < 8; ++j) val[j] = bas[a][j] * fv[j];
-          uint4 hi, lo;
-          split8<FP16>(val, hi, lo);
+          for (int j = 0; j < 4; ++j) val[j] = bas[a][j] * fv[j];
+          uint2 hi, lo;
+          split4<FP16>(val, hi, lo);
           const int row = 16 + d * K + a;
-          *(uint4 *)(Bh + sw128_off(row, g)) = hi;
-          *(uint4 *)(Bl + sw128_off(row, g)) = lo;
+          *(uint2 *)(Bh + sw128_off(row, g)) = hi;
+          *(uint2 *)(Bl + sw128_off(row, g)) = lo;
         }
       }
       // zero rows that pad N to a multiple of 16
       for (int row = 16 + Dc * K + rr; row < N; row += 16) {
-        if (row >= 16 + Dc * K) {
-          const uint4 z = make_uint4(0, 0, 0, 0);
-          *(uint4 *)(Bh + sw128_off(row, g)) = z;
-          *(uint4 *)(Bl + sw128_off(row, g)) = z;
-        }
+        const uint2 z = make_uint2(0, 0);
+        *(uint2 *)(Bh + sw128_off(row, g)) = z;
+        *(uint2 *)(Bl + sw128_off(row, g)) = z;
       }
       fence_proxy_async();
       __syncwarp();
@@ -733,7 +768,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mls_tc(KParams p, int d0, int D
       }
     }
     nst = kt;
-  } else if (warp == 9) {
+  } else if (warp == kLoadWarp) {
     // ------------------------------------------------ point-tile loader (TMA bulk copies)
     // The whole warp walks the cell rows (collectively, see PackW); lane q
     // keeps slot q, lanes 0-7 write the slot table, lane 0 waits and arms the
@@ -851,16 +886,20 @@ __global__ void __launch_bounds__(kThreads, 1) k_mls_tc(KParams p, int d0, int D
 
   __syncthreads();   // every role has left its loop (the stabiliser split is read below)
 
-  // ------------------------------------------------ epilogue (warps 0-7)
+  // ------------------------------------------------ epilogue (the 16 producer warps)
   // has any point tile been visited?
   const bool any_tile = nst > 0;
-  if (warp < 8) {
-    const int wg = warp >> 2;
-    // two accumulators: one warpgroup each; one accumulator: the warpgroups
-    // share it and take alternate groups of value columns
+  if (warp < kMmaWarp) {
+    // weight warp w and builder warp w + 8 read the same TMEM lanes (pixels):
+    // both solve the pixel's system, and they take alternate groups of value
+    // columns; the weight warps (eh = 0) write the pixel's status
+    const int eh = warp / kWeightWarps;
+    const int wg = (warp >> 2) & 1;
+    // two accumulators: one warpgroup of each half each; one accumulator: the
+    // four warpgroups share it
     const int a = (NACC == 2) ? wg : 0;
-    const bool primary = (NACC == 2) || wg == 0;
-    const int gfirst = (NACC == 2) ? 0 : wg, gstep = (NACC == 2) ? 1 : 2;
+    const bool primary = eh == 0 && ((NACC == 2) || wg == 0);
+    const int gfirst = (NACC == 2) ? eh : (warp >> 2), gstep = (NACC == 2) ? 2 : 4;
     const int m = 32 * (warp & 3) + lane;
     const int q = a * 128 + m;
     const int u = u0 + (q & 15), v = v0 + (q >> 4);
@@ -889,7 +928,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mls_tc(KParams p, int d0, int D
 #pragma unroll
     for (int k = 0; k < kPre; ++k) {
       const int e = threadIdx.x + 256 * k;
-      pre[k] = (e < nstage) ? staged(e) : 0.f;
+      pre[k] = (eh == 0 && e < nstage) ? staged(e) : 0.f;
     }
     const bool acc_ok = __all_sync(0xffffffffu, mbar_wait(bar_acc, 0, p.err, ERR_WAIT_ACC, limit));
     tc_fence_after();
@@ -900,13 +939,15 @@ __global__ void __launch_bounds__(kThreads, 1) k_mls_tc(KParams p, int d0, int D
     float *s_scl = s_lev + Dc * P, *s_cen = s_scl + Dc;
     // s_lev, s_scl and s_cen are consecutive: element e of the staging order
     // sits at s_lev[e]
+    if (eh == 0) {
 #pragma unroll
-    for (int k = 0; k < kPre; ++k) {
-      const int e = threadIdx.x + 256 * k;
-      if (e < nstage) s_lev[e] = pre[k];
+      for (int k = 0; k < kPre; ++k) {
+        const int e = threadIdx.x + 256 * k;
+        if (e < nstage) s_lev[e] = pre[k];
+      }
+      for (int e = threadIdx.x + 256 * kPre; e < nstage; e += 256) s_lev[e] = staged(e);
     }
-    for (int e = threadIdx.x + 256 * kPre; e < nstage; e += 256) s_lev[e] = staged(e);
-    asm volatile("bar.sync 1, 256;" ::: "memory");   // the eight epilogue warps
+    asm volatile("bar.sync 1, %0;" ::"n"(32 * kMmaWarp) : "memory");   // the sixteen epilogue warps
     const float dxp = geo->col[q & 15];
     const float dyp = geo->row[q >> 4];
     const uint32_t tbase = tmem + a * 256 + ((uint32_t)(32 * (warp & 3)) << 16);
@@ -970,17 +1011,20 @@ __global__ void __launch_bounds__(kThreads, 1) k_mls_tc(KParams p, int d0, int D
         if (p.bands) p.bands[(size_t)d * plane + pix] = 255;
       }
     }
-    // value columns in groups of 48 (K = 3, 6) or 16 (K = 1)
-    constexpr int GC = (K == 1) ? 16 : 48;
+    // value columns in groups of 24 (K = 3, 6) or 16 (K = 1)
+    constexpr int GC = (K == 1) ? 16 : 24;
     constexpr int GD = GC / K;
     for (int gbase = gfirst * GD; gbase < Dc; gbase += gstep * GD) {
       float rv[GC];
       if (read) {
-        if (GC == 48) {
-          float tmp[48];
-          tmem_ld48(tbase + 16 + gbase * K, tmp);
+        if (GC == 24) {
+          float t16[16], t8[8];
+          tmem_ld16(tbase + 16 + gbase * K, t16);
+          tmem_ld8(tbase + 16 + gbase * K + 16, t8);
 #pragma unroll
-          for (int j = 0; j < GC; ++j) rv[j] = tmp[j];
+          for (int j = 0; j < 16; ++j) rv[j] = t16[j];
+#pragma unroll
+          for (int j = 0; j < 8; ++j) rv[16 + j] = t8[j];
         } else {
 #pragma unroll
           for (int c = 0; c < GC / 16; ++c) {
@@ -1025,7 +1069,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mls_tc(KParams p, int d0, int D
   }
   tc_fence_before();
   __syncthreads();
-  if (warp == 8) {
+  if (warp == kMmaWarp) {
     tc_fence_after();
     tmem_dealloc(tmem, 512);
   }
@@ -1073,7 +1117,7 @@ void launch_deg_w(const KParams &p, int fp16, int wsplit, int d0, int Dc, int N,
 // Dimensions per pass so that 16 + K Dc columns fit one 256-column accumulator.
 int dims_per_pass(int degree) {
   const int K = mlsk::n_terms(degree);
-  const int group = (K == 1) ? 16 : 48 / K;   // the epilogue reads whole groups
+  const int group = (K == 1) ? 16 : 24 / K;   // the epilogue reads whole groups
   int dc = (kNMax - 16) / K;
   if (dc > kDcMax) dc = kDcMax;
   dc -= dc % group;
@@ -1093,7 +1137,7 @@ mls_status launch_tc(const KParams &p, int fp16, int wsplit, cudaStream_t st, in
   if (per != p.fb_dc) return fail(MLS_E_INVAL, "blocked value layout does not match the pass split");
   for (int d0 = 0; d0 < p.D; d0 += per) {
     const int Dc = per;   // the last pass reads zero-padded dimensions
-    const int group = (K == 1) ? 16 : 48 / K;
+    const int group = (K == 1) ? 16 : 24 / K;
     const int Dg = (Dc + group - 1) / group * group;    // columns the epilogue reads
     int N = 16 + Dg * K;
     N = (N + 15) / 16 * 16;
