@@ -96,6 +96,10 @@ constexpr int kSmemLimit = 232448;                        // 227 KB per CTA
 // bytes past offBar: barriers, TMEM slot and tile geometry (512), then the
 // slot table of the staged point tiles (4 stages x 8 slots x 16 bytes)
 constexpr int kMisc = 1024;
+// epilogue: each pixel's z and keep flag (8 floats) at the end of the 64 KB
+// of A tiles, past the staged levels (Dc (P + 2) floats: Dc <= 40 and P <= 256
+// for L <= 254 levels, so below 41 KB)
+constexpr int kZOff = 56 * 1024;
 constexpr int kOffSlots = 512;
 
 struct TcLayout {
@@ -952,42 +956,62 @@ __global__ void __launch_bounds__(kThreads, 1) k_mls_tc(KParams p, int d0, int D
     const float dyp = geo->row[q >> 4];
     const uint32_t tbase = tmem + a * 256 + ((uint32_t)(32 * (warp & 3)) << 16);
     const bool read = acc_ok && any_tile;   // warp-uniform
-    float St[16];
-    if (read) tmem_ld16(tbase, St);
-    else
-#pragma unroll
-      for (int j = 0; j < 16; ++j) St[j] = 0.f;
-    int count;
-    bool handover = false;
-    bool cuncertain = false;
-    if (WK == MLS_W_WENDLAND) {
-      count = cflag & kCntMask;
-      handover = cuncertain = count_uncertain<K>(cflag);
-    } else {
-      count = (int)(p.n < (1 << 30) ? p.n : (1 << 30));
-      if (p.trunc_on) {
-        // truncated Gaussian: the points in the pixel's box
-        count = cflag & kCntMask;
-        cuncertain = count_uncertain<K>(cflag);
-      }
-      // clipping |x~|_inf <= kRMax is exact in 16-bit arithmetic only when the
-      // pixel has a point within (kRMax - |delta|_inf - 4.2) h
-      const float reach = kRMax - fmaxf(fabsf(dxp), fabsf(dyp));
-      handover = cuncertain || !(mst <= reach * reach - 18.f) || !read;
-      {
-        // the weight producers undo the split stabiliser's factor 2^-res up to kResMax
-        const float *sAB0 = (const float *)(smem + lay.offPrm);
-        const float res = kLog2e * mst - sAB0[q & 15] - sAB0[16 + (q >> 4)];
-        handover = handover || !(res <= kResMax);
-      }
-    }
+    // The primary thread of each pixel solves and publishes z and whether the
+    // value is kept ([q][0..K-1], [q][7]) past the end of the staged levels
+    // (the operand tiles are free now); the other threads of the pixel read it.
+    float *s_z = (float *)(smem + kOffA + kZOff);
     float z[K];
+#pragma unroll
+    for (int b2 = 0; b2 < K; ++b2) z[b2] = 0.f;
     int outcome = SOLVE_RECOMPUTE;
     int degu = DEG;
-    const bool nosup = (count == 0) && !cuncertain;
-    if (!nosup && !handover) outcome = solve_by_count<K>(count, St, dxp, dyp, z, p, &degu);
-    const bool done = !nosup && outcome != SOLVE_RECOMPUTE;
-    const bool give = !nosup && outcome == SOLVE_RECOMPUTE;
+    bool nosup = false;
+    if (primary) {
+      float St[16];
+      if (read) tmem_ld16(tbase, St);
+      else
+  #pragma unroll
+        for (int j = 0; j < 16; ++j) St[j] = 0.f;
+      int count;
+      bool handover = false;
+      bool cuncertain = false;
+      if (WK == MLS_W_WENDLAND) {
+        count = cflag & kCntMask;
+        handover = cuncertain = count_uncertain<K>(cflag);
+      } else {
+        count = (int)(p.n < (1 << 30) ? p.n : (1 << 30));
+        if (p.trunc_on) {
+          // truncated Gaussian: the points in the pixel's box
+          count = cflag & kCntMask;
+          cuncertain = count_uncertain<K>(cflag);
+        }
+        // clipping |x~|_inf <= kRMax is exact in 16-bit arithmetic only when the
+        // pixel has a point within (kRMax - |delta|_inf - 4.2) h
+        const float reach = kRMax - fmaxf(fabsf(dxp), fabsf(dyp));
+        handover = cuncertain || !(mst <= reach * reach - 18.f) || !read;
+        {
+          // the weight producers undo the split stabiliser's factor 2^-res up to kResMax
+          const float *sAB0 = (const float *)(smem + lay.offPrm);
+          const float res = kLog2e * mst - sAB0[q & 15] - sAB0[16 + (q >> 4)];
+          handover = handover || !(res <= kResMax);
+        }
+      }
+      nosup = (count == 0) && !cuncertain;
+      if (!nosup && !handover) outcome = solve_by_count<K>(count, St, dxp, dyp, z, p, &degu);
+#pragma unroll
+      for (int b2 = 0; b2 < K; ++b2) s_z[q * 8 + b2] = z[b2];
+      s_z[q * 8 + 7] = (!nosup && outcome != SOLVE_RECOMPUTE) ? 1.f : 0.f;
+    }
+    asm volatile("bar.sync 2, %0;" ::"n"(32 * kMmaWarp) : "memory");   // z published
+    bool done;
+    if (primary) {
+      done = !nosup && outcome != SOLVE_RECOMPUTE;
+    } else {
+#pragma unroll
+      for (int b2 = 0; b2 < K; ++b2) z[b2] = s_z[q * 8 + b2];
+      done = s_z[q * 8 + 7] != 0.f;
+    }
+    const bool give = primary && !nosup && outcome == SOLVE_RECOMPUTE;
     const size_t plane = (size_t)p.W * p.H;
     const size_t pix = (size_t)v * p.W + u;
     float *field = (float *)p.field;
@@ -1018,13 +1042,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_mls_tc(KParams p, int d0, int D
       float rv[GC];
       if (read) {
         if (GC == 24) {
-          float t16[16], t8[8];
-          tmem_ld16(tbase + 16 + gbase * K, t16);
-          tmem_ld8(tbase + 16 + gbase * K + 16, t8);
+          float t24[24];
+          tmem_ld24(tbase + 16 + gbase * K, t24);
 #pragma unroll
-          for (int j = 0; j < 16; ++j) rv[j] = t16[j];
-#pragma unroll
-          for (int j = 0; j < 8; ++j) rv[16 + j] = t8[j];
+          for (int j = 0; j < 24; ++j) rv[j] = t24[j];
         } else {
 #pragma unroll
           for (int c = 0; c < GC / 16; ++c) {
