@@ -377,14 +377,18 @@ __device__ int pixel_policy(const double (&Sd)[15], long long count, double rcon
 
 // ---------------------------------------------------------------------------
 
-// Per-block state of a chunk of up to 32 pixels between the three phases.
+// Per-block state of a chunk of up to 32 pixels between its phases.
 struct ChunkSlot {
-  double S[15];    // pixel-frame moments
   double z[6];     // solution in the centroid frame
+  float Sh[15], Sl[15];   // pixel-frame moments, double-float
   float fr[5];     // centroid frame
   long long count;
   int flags;       // bit 0: needs the FP64 kernel; bits 8..: degree used + 1
   int nnear;       // near points (the cost of the pixel's value phase)
+  // the pixel's setup (formed once per chunk, one lane per pixel)
+  int id;
+  Ranges R;
+  float mhat, pxh, pxl, pyh, pyl;
 };
 
 template <int DEG, int WK>
@@ -464,16 +468,28 @@ __global__ __launch_bounds__(kWarps * 32, 4) void k_handover(KParams p, const in
     const int nq = strided ? (int)((npix - ch + nchunks - 1) / nchunks)
                            : (int)((npix - first) < csz ? (npix - first) : csz);
 
+    // ---- phase 0 (lane per pixel): each pixel's setup, once.  Its FP64
+    // arithmetic is warp-uniform per pixel; GB300 charges an FP64 warp
+    // instruction in full however few lanes need it, so 32 pixels a lane
+    // each cost what one pixel on a whole warp did (twice, for the moment and
+    // value phases)
+    if (wib == 0 && lane < nq) {
+      ChunkSlot &sl = slots[lane];
+      const int id = (int)list_i(p, list[list_i(p, first + (int64_t)lane * step)]);
+      sl.id = id;
+      setup(id, sl.R, sl.mhat, sl.pxh, sl.pxl, sl.pyh, sl.pyl);
+    }
+    __syncthreads();
+
     // ---- phase 1 (warp per pixel): double-float pixel-frame moments
     for (;;) {
       int j = 0;
       if (lane == 0) j = atomicAdd(&s_next[0], 1);
       j = __shfl_sync(0xffffffffu, j, 0);
       if (j >= nq) break;
-      const int id = (int)list_i(p, list[list_i(p, first + (int64_t)j * step)]);
-      Ranges R;
-      float mhat, pxh, pxl, pyh, pyl;
-      setup(id, R, mhat, pxh, pxl, pyh, pyl);
+      const Ranges R = slots[j].R;
+      const float mhat = slots[j].mhat, pxh = slots[j].pxh, pxl = slots[j].pxl, pyh = slots[j].pyh,
+                  pyl = slots[j].pyl;
       df32 S[NM];
 #pragma unroll
       for (int k = 0; k < NM; ++k) S[k] = {0.f, 0.f};
@@ -506,14 +522,15 @@ __global__ __launch_bounds__(kWarps * 32, 4) void k_handover(KParams p, const in
           }
         }
       });
+      // the sums as double-float (the policy lane forms the doubles)
 #pragma unroll
       for (int k = 0; k < 15; ++k) {
-        double v = 0.0;
-        if (k < NM) {
-          const df32 t = df_warp_sum(S[k]);
-          v = (double)t.hi + (double)t.lo;
+        df32 t = {0.f, 0.f};
+        if (k < NM) t = df_warp_sum(S[k]);
+        if (lane == k) {
+          slots[j].Sh[k] = t.hi;
+          slots[j].Sl[k] = t.lo;
         }
-        if (lane == k) slots[j].S[k] = v;
       }
       if (lane == 0) {
         slots[j].count = (WK == MLS_W_WENDLAND || p.trunc > 0.0) ? nnear : p.n;
@@ -547,7 +564,7 @@ __global__ __launch_bounds__(kWarps * 32, 4) void k_handover(KParams p, const in
         double Sd[15], z[6];
         float fr[5];
 #pragma unroll
-        for (int k = 0; k < 15; ++k) Sd[k] = sl.S[k];
+        for (int k = 0; k < 15; ++k) Sd[k] = (double)sl.Sh[k] + (double)sl.Sl[k];
         bool bad = false;
         const int used = pixel_policy<DEG>(Sd, sl.count, p.rcond_min, z, fr, &bad);
 #pragma unroll
@@ -566,7 +583,7 @@ __global__ __launch_bounds__(kWarps * 32, 4) void k_handover(KParams p, const in
       k = __shfl_sync(0xffffffffu, k, 0);
       if (k >= nq) break;
       const int j = s_order[k];
-      const int id = (int)list_i(p, list[list_i(p, first + (int64_t)j * step)]);
+      const int id = slots[j].id;
       const int flags = slots[j].flags;
       if (flags & 1) {
         if (lane == 0) {
@@ -584,9 +601,9 @@ __global__ __launch_bounds__(kWarps * 32, 4) void k_handover(KParams p, const in
         if (lane == 0 && p.status) p.status[id] = MLS_ST_NO_SUPPORT | MLS_ST_RECOMPUTED;
         continue;
       }
-      Ranges R;
-      float mhat, pxh, pxl, pyh, pyl;
-      setup(id, R, mhat, pxh, pxl, pyh, pyl);
+      const Ranges R = slots[j].R;
+      const float mhat = slots[j].mhat, pxh = slots[j].pxh, pxl = slots[j].pxl, pyh = slots[j].pyh,
+                  pyl = slots[j].pyl;
       const int ku = n_terms(used);
       df32 zd[6];
 #pragma unroll
