@@ -379,7 +379,7 @@ __device__ int pixel_policy(const double (&Sd)[15], long long count, double rcon
 
 // Per-block state of a chunk of up to 32 pixels between its phases.
 struct ChunkSlot {
-  double z[6];     // solution in the centroid frame
+  float zh[6], zl[6];     // solution in the centroid frame, double-float
   float Sh[15], Sl[15];   // pixel-frame moments, double-float
   float fr[5];     // centroid frame
   long long count;
@@ -568,7 +568,10 @@ __global__ __launch_bounds__(kWarps * 32, 4) void k_handover(KParams p, const in
         bool bad = false;
         const int used = pixel_policy<DEG>(Sd, sl.count, p.rcond_min, z, fr, &bad);
 #pragma unroll
-        for (int a = 0; a < 6; ++a) sl.z[a] = z[a];
+        for (int a = 0; a < 6; ++a) {
+          sl.zh[a] = (float)z[a];
+          sl.zl[a] = (float)(z[a] - (double)sl.zh[a]);
+        }
 #pragma unroll
         for (int a = 0; a < 5; ++a) sl.fr[a] = fr[a];
         sl.flags = (bad ? 1 : 0) | ((used + 1) << 8);
@@ -608,8 +611,7 @@ __global__ __launch_bounds__(kWarps * 32, 4) void k_handover(KParams p, const in
       df32 zd[6];
 #pragma unroll
       for (int a = 0; a < 6; ++a) {
-        const double za = slots[j].z[a];
-        zd[a] = {(float)za, (float)(za - (double)(float)za)};
+        zd[a] = {slots[j].zh[a], slots[j].zl[a]};
       }
       const float cxh = slots[j].fr[0], cxl = slots[j].fr[1], cyh = slots[j].fr[2], cyl = slots[j].fr[3],
                   isg = slots[j].fr[4];
@@ -650,8 +652,12 @@ __global__ __launch_bounds__(kWarps * 32, 4) void k_handover(KParams p, const in
         for (int t = 0; t < kDL; ++t) {
           const int d = d0 + lane + 32 * t;
           if (d < p.D) {
-            const double fv = (double)acc[t].hi + (double)acc[t].lo;
-            const float f = (float)((double)p.fcen32[d] + (double)p.fscl32[d] * fv);
+            // fcen + fscl (hi + lo) in double-float, rounded to float at the
+            // end (FP32 arithmetic: per-lane FP64 here cost a warp
+            // instruction per pixel and dimension sweep)
+            const df32 sv = df_prod_f(df_two_sum(acc[t].hi, acc[t].lo), p.fscl32[d]);
+            const df32 fs = df_add({p.fcen32[d], 0.f}, sv);
+            const float f = fs.hi + fs.lo;
             field[(size_t)d * plane + id] = f;
             if (p.bands) p.bands[(size_t)d * plane + id] = band_of(f, p.lev32 + (size_t)d * p.L, p.L);
           }
