@@ -225,50 +225,69 @@ __device__ double ldl_rcond(const double (&S)[15], double (&L)[6][6], double (&d
   for (int a = 0; a < K; ++a)
 #pragma unroll
     for (int b = 0; b <= a; ++b) Me[a][b] = Me[b][a] = S[midx(a, b)] * sd[a] * sd[b];
-  // LDL^T (no square roots): D_j = Me_jj - sum_t L_jt^2 D_t,
-  // L_ij = (Me_ij - sum_t L_it L_jt D_t) / D_j
-  double Dg[K];
+  // LDL^T (no square roots): D_j = Me_jj - sum_t L_jt (L_jt D_t),
+  // L_ij = (Me_ij - sum_t L_it (L_jt D_t)) / D_j, with LD_jt = L_jt D_t kept
+  // (it is the numerator of L_jt before the division)
+  double LD[K][K];
 #pragma unroll
   for (int j = 0; j < K; ++j) {
     double dj = Me[j][j];
 #pragma unroll
-    for (int t = 0; t < j; ++t) dj -= L[j][t] * L[j][t] * Dg[t];
+    for (int t = 0; t < j; ++t) dj -= L[j][t] * LD[j][t];
     if (!(dj > 0.0)) return 0.0;
-    Dg[j] = dj;
     dinv[j] = rcp64(dj);
 #pragma unroll
     for (int i = j + 1; i < K; ++i) {
       double v = Me[i][j];
 #pragma unroll
-      for (int t = 0; t < j; ++t) v -= L[i][t] * L[j][t] * Dg[t];
+      for (int t = 0; t < j; ++t) v -= L[i][t] * LD[j][t];
+      LD[i][j] = v;
       L[i][j] = v * dinv[j];
     }
   }
-  // 1-norms of Me and of its inverse (columns by forward / back substitution)
+  // 1-norms of Me and of its inverse.  Me^-1 = L^-T D^-1 L^-1 is symmetric:
+  // with Li = L^-1 (unit lower) and G_kj = dinv_k Li_kj, its entry (i, j),
+  // i <= j, is sum_{k >= j} Li_ki G_kj (about a third of the FP64 operations
+  // of K forward and back substitutions)
+  double Li[K][K], G[K][K];
+#pragma unroll
+  for (int i = 0; i < K; ++i)
+#pragma unroll
+    for (int j = 0; j < i; ++j) {
+      double v = -L[i][j];
+#pragma unroll
+      for (int t = j + 1; t < i; ++t) v -= L[i][t] * Li[t][j];
+      Li[i][j] = v;
+    }
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    G[k][k] = dinv[k];
+#pragma unroll
+    for (int j = 0; j < k; ++j) G[k][j] = dinv[k] * Li[k][j];
+  }
+  double cI[K], cA[K];
+#pragma unroll
+  for (int c = 0; c < K; ++c) cI[c] = cA[c] = 0.0;
+#pragma unroll
+  for (int j = 0; j < K; ++j)
+#pragma unroll
+    for (int i = 0; i <= j; ++i) {
+      double v = 0.0;
+#pragma unroll
+      for (int k = j; k < K; ++k) v += (k == i ? 1.0 : Li[k][i]) * G[k][j];
+      const double av = fabs(v), am = fabs(Me[i][j]);
+      cI[j] += av;
+      cA[j] += am;
+      if (i != j) {
+        cI[i] += av;
+        cA[i] += am;
+      }
+    }
   double nI = 0.0, nA = 0.0;
 #pragma unroll
   for (int c = 0; c < K; ++c) {
-    double col[K];
-#pragma unroll
-    for (int a = 0; a < K; ++a) col[a] = (a == c) ? 1.0 : 0.0;
-#pragma unroll
-    for (int i = 0; i < K; ++i)
-#pragma unroll
-      for (int t = 0; t < i; ++t) col[i] -= L[i][t] * col[t];
-#pragma unroll
-    for (int i = 0; i < K; ++i) col[i] *= dinv[i];
-#pragma unroll
-    for (int i = K - 1; i >= 0; --i)
-#pragma unroll
-      for (int t = i + 1; t < K; ++t) col[i] -= L[t][i] * col[t];
-    double si = 0.0, sa = 0.0;
-#pragma unroll
-    for (int a = 0; a < K; ++a) {
-      si += fabs(col[a]);
-      sa += fabs(Me[a][c]);
-    }
-    nI = fmax(nI, si);
-    nA = fmax(nA, sa);
+    nI = fmax(nI, cI[c]);
+    nA = fmax(nA, cA[c]);
   }
   return 1.0 / (nA * nI);
 }
@@ -294,33 +313,36 @@ __device__ __forceinline__ void ldl_solve(const double (&L)[6][6], const double 
 }
 
 // Moments of the frame centred on (cx, cy) and scaled by isg, from the
-// pixel-frame moments: binomial expansion of (x - cx)^bx (y - cy)^by.
+// pixel-frame moments: sum_i w_i (x_i - cx)^bx (y_i - cy)^by, by binomial
+// expansion.  The expansion is separable: a shift in x of every row of equal
+// y exponent, then a shift in y of every column.  A 1-D shift of moments
+// a_0..a_m by c is the Taylor shift: m passes, pass i replacing a_k by
+// a_k - c a_(k-1) for k = m down to i (m (m + 1) / 2 multiply-adds).
 template <int NM>
 __device__ __forceinline__ void centroid_moments(const double (&S)[15], double cx, double cy, double isg,
                                                  double (&Sc)[15]) {
-  double pcx[5], pcy[5], ps[5];
-  pcx[0] = pcy[0] = ps[0] = 1.0;
+  constexpr int DM = NM == 15 ? 4 : NM == 6 ? 2 : 0;   // total degree of the moments
+  double a[15];
 #pragma unroll
-  for (int e = 1; e < 5; ++e) {
-    pcx[e] = pcx[e - 1] * -cx;
-    pcy[e] = pcy[e - 1] * -cy;
-    ps[e] = ps[e - 1] * isg;
-  }
+  for (int j = 0; j < 15; ++j) a[j] = (j < NM) ? S[j] : 0.0;
 #pragma unroll
-  for (int j = 0; j < 15; ++j) {
-    double acc = 0.0;
-    if (j < NM) {
-      const int bx = mono_ex(j), by = mono_ey(j);
+  for (int ey = 0; ey <= DM; ++ey)
 #pragma unroll
-      for (int jx = 0; jx <= 4; ++jx)
+    for (int i = 1; i <= DM - ey; ++i)
 #pragma unroll
-        for (int jy = 0; jy <= 4; ++jy)
-          if (jx <= bx && jy <= by)
-            acc += (double)(binom(bx, jx) * binom(by, jy)) * pcx[bx - jx] * pcy[by - jy] * S[mono_index(jx, jy)];
-      acc *= ps[bx + by];
-    }
-    Sc[j] = acc;
-  }
+      for (int k = DM - ey; k >= i; --k) a[mono_index(k, ey)] = fma(-cx, a[mono_index(k - 1, ey)], a[mono_index(k, ey)]);
+#pragma unroll
+  for (int ex = 0; ex <= DM; ++ex)
+#pragma unroll
+    for (int i = 1; i <= DM - ex; ++i)
+#pragma unroll
+      for (int k = DM - ex; k >= i; --k) a[mono_index(ex, k)] = fma(-cy, a[mono_index(ex, k - 1)], a[mono_index(ex, k)]);
+  double ps[5];
+  ps[0] = 1.0;
+#pragma unroll
+  for (int e = 1; e < 5; ++e) ps[e] = ps[e - 1] * isg;
+#pragma unroll
+  for (int j = 0; j < 15; ++j) Sc[j] = (j < NM) ? a[j] * ps[mono_ex(j) + mono_ey(j)] : 0.0;
 }
 
 // z = M_c^-1 b_c(pixel) in the frame of the weighted centroid (degree of K
@@ -409,6 +431,10 @@ __global__ __launch_bounds__(kWarps * 32, 4) void k_handover(KParams p, const in
   if (threadIdx.x == 0) s_next[0] = s_next[1] = 0;
   __syncthreads();
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  // the warp of the lane-per-pixel phases (setup, FP64 policy) rotates with
+  // the block, so that the blocks sharing an SM run those phases on
+  // different warp schedulers; the next warp forms the value-phase order
+  const int wpol = (int)(blockIdx.x % kWarps), word = (wpol + 1) % kWarps;
   int *ri = s_ri[wib];
   float4 *rx = s_rx[wib];
   ChunkSlot *slots = s_chunk;
@@ -473,7 +499,7 @@ __global__ __launch_bounds__(kWarps * 32, 4) void k_handover(KParams p, const in
     // instruction in full however few lanes need it, so 32 pixels a lane
     // each cost what one pixel on a whole warp did (twice, for the moment and
     // value phases)
-    if (wib == 0 && lane < nq) {
+    if (wib == wpol && lane < nq) {
       ChunkSlot &sl = slots[lane];
       const int id = (int)list_i(p, list[list_i(p, first + (int64_t)lane * step)]);
       sl.id = id;
@@ -544,7 +570,7 @@ __global__ __launch_bounds__(kWarps * 32, 4) void k_handover(KParams p, const in
 
     __syncthreads();
     // ---- phase 2 (lane per pixel): degree policy and centroid-frame solve in FP64
-    if (wib == 1) {
+    if (wib == word) {
       // value-phase order and counters; the moment counter is reset for the
       // next chunk (every warp has left this chunk's moment phase)
       if (lane < nq) {
@@ -558,7 +584,7 @@ __global__ __launch_bounds__(kWarps * 32, 4) void k_handover(KParams p, const in
       }
       if (lane == 0) s_next[0] = s_next[1] = 0;
     }
-    if (wib == 0 && lane < nq) {
+    if (wib == wpol && lane < nq) {
       ChunkSlot &sl = slots[lane];
       if (!(sl.flags & 1)) {
         double Sd[15], z[6];

@@ -383,11 +383,11 @@ mls_status mls_create(const mls_desc *desc, const double *xy, const double *F, i
   mls_status s = MLS_OK;
   const double *xy_d = xy, *F_d = F;
   if (!on_device) {
+    // one staging block for both inputs
     void *p;
-    if ((s = dev_alloc(h, &p, sizeof(double) * 2 * d.n, st)) != MLS_OK) goto bad;
+    if ((s = dev_alloc(h, &p, sizeof(double) * d.n * (2 + d.D), st)) != MLS_OK) goto bad;
     xy_d = (const double *)p;
-    if ((s = dev_alloc(h, &p, sizeof(double) * d.n * d.D, st)) != MLS_OK) goto bad;
-    F_d = (const double *)p;
+    F_d = xy_d + 2 * d.n;
     {
       cudaError_t e = cudaMemcpyAsync((void *)xy_d, xy, sizeof(double) * 2 * d.n, cudaMemcpyHostToDevice, st);
       if (e == cudaSuccess)
@@ -402,21 +402,21 @@ mls_status mls_create(const mls_desc *desc, const double *xy, const double *F, i
     s = cuda_fail(cudaGetLastError(), "cudaGetDevice");
     goto bad;
   }
-  if ((s = prep_points(h, xy_d, F_d, st)) != MLS_OK) goto bad;
-  if (!on_device) {
-    // the staging copies of the inputs are not needed once prepared
-    release(h, (void *)xy_d, st);
-    release(h, (void *)F_d, st);
-  }
+  // the events first: prep_points waits once for the device (the point
+  // ranges), and host work after that wait leaves the device idle
   if (cudaEventCreate(&h->ev0) != cudaSuccess || cudaEventCreate(&h->ev1) != cudaSuccess ||
       cudaEventCreate(&h->evk0) != cudaSuccess || cudaEventCreate(&h->evk1) != cudaSuccess) {
     s = cuda_fail(cudaGetLastError(), "cudaEventCreate");
     goto bad;
   }
-  if (!on_device && cudaStreamSynchronize(st) != cudaSuccess) {
-    s = cuda_fail(cudaGetLastError(), "cudaStreamSynchronize");
-    goto bad;
+  if ((s = prep_points(h, xy_d, F_d, st)) != MLS_OK) goto bad;
+  if (!on_device) {
+    // the staging copies of the inputs are not needed once prepared
+    release(h, (void *)xy_d, st);
   }
+  // host inputs: the copies above have completed, since prep_points waited
+  // for the stream after them (the point ranges), so the caller may reuse
+  // its buffers without another wait here
   *out = h;
   return MLS_OK;
 bad:

@@ -51,9 +51,29 @@ __global__ void k_colminmax(const double *A, int64_t rows, int cols, unsigned lo
   }
 }
 
-__global__ void k_fill_u64(unsigned long long *p, int n, unsigned long long v) {
+// Centre and half-range of every value column from its range keys (the
+// values are normalised to [-1, 1] by these; a constant column keeps scale 1).
+__global__ void k_value_frames(const unsigned long long *kmin, const unsigned long long *kmax, int D, double *cen,
+                               double *scl, float *cen32, float *scl32) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= D) return;
+  const unsigned long long a = kmin[c], b = kmax[c];
+  const double lo = __longlong_as_double((long long)((a >> 63) ? (a & 0x7fffffffffffffffull) : ~a));
+  const double hi = __longlong_as_double((long long)((b >> 63) ? (b & 0x7fffffffffffffffull) : ~b));
+  const double ce = 0.5 * (lo + hi);
+  double sc = 0.5 * (hi - lo);
+  if (!(sc > 0.0)) sc = 1.0;
+  cen[c] = ce;
+  scl[c] = sc;
+  cen32[c] = (float)ce;
+  scl32[c] = (float)sc;
+}
+
+// Range keys before the reduction: m minima at the largest key, then m
+// maxima at the smallest.
+__global__ void k_init_keys(unsigned long long *p, int m) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) p[i] = v;
+  if (i < 2 * m) p[i] = i < m ? ~0ull : 0ull;
 }
 
 // Cell of each point on the uniform grid (the same expression is used by
@@ -203,23 +223,39 @@ __global__ void k_block(const float *xs, const float *ys, const float *FT32, int
   const int64_t b = i >> 3;
   const int j = (int)(i & 7);
   const int64_t fstride = (int64_t)dc * 8 + 4;
-  if (blockIdx.y == 0) {
-    xyb[b * 20 + j] = xs[i];
-    xyb[b * 20 + 8 + j] = ys[i];
-    if (j < 4) xyb[b * 20 + 16 + j] = 0.f;
-  }
   const int64_t nblk = n_pad >> 3;
-  for (int pass = blockIdx.y; pass < passes; pass += gridDim.y) {
-    float *blk = fb + (pass * nblk + b) * fstride;
-    for (int dd = 0; dd < dc; ++dd) {
+  // grid row 0: the positions; row 1 + pass dc + dd: value column dd of pass
+  // `pass` (one column per grid row, so that small point sets still fill
+  // the GPU)
+  for (int y = blockIdx.y; y < 1 + passes * dc; y += gridDim.y) {
+    if (y == 0) {
+      xyb[b * 20 + j] = xs[i];
+      xyb[b * 20 + 8 + j] = ys[i];
+      if (j < 4) xyb[b * 20 + 16 + j] = 0.f;
+    } else {
+      const int pass = (y - 1) / dc, dd = (y - 1) % dc;
       const int d = pass * dc + dd;
+      float *blk = fb + (pass * nblk + b) * fstride;
       blk[dd * 8 + j] = (d < D) ? FT32[(int64_t)d * n_pad + i] : 0.f;
+      if (dd == 0 && j < 4) blk[dc * 8 + j] = 0.f;
     }
-    if (j < 4) blk[dc * 8 + j] = 0.f;
   }
 }
 
 }  // namespace
+
+// Offsets of the arrays carved out of one device block (each 256-byte
+// aligned): a handle's arrays cost one stream-ordered allocation instead of
+// one each (every allocation is a driver call on the host, and create's host
+// time is device idle time after its one wait for the point ranges).
+struct Carve {
+  size_t bytes = 0;
+  size_t add(size_t nbytes) {
+    const size_t o = bytes;
+    bytes += (nbytes + 255) / 256 * 256;
+    return o;
+  }
+};
 
 mls_status prep_points(mls_handle *h, const double *xy, const double *F, cudaStream_t st) {
   PointSet &P = h->P;
@@ -232,13 +268,58 @@ mls_status prep_points(mls_handle *h, const double *xy, const double *F, cudaStr
   const int64_t n = P.n;
   const int D = P.D;
 
-  // --- ranges of x, y and every value column
-  unsigned long long *keys = nullptr;
+  // --- one block for the range keys and every array whose size depends
+  // only on n and D
+  const bool binned = d.weight != MLS_W_INVDIST;
+  const bool blocked = d.precision == MLS_P_FP16 || d.precision == MLS_P_BF16;
+  int dc = 0, passes = 0;
+  if (blocked) {
+    dc = tc_dims_per_pass(D, d.degree);
+    passes = (D + dc - 1) / dc;
+    P.fb_dc = dc;
+  }
+  Carve cv;
+  const size_t o_keys = cv.add(sizeof(unsigned long long) * 2 * (D + 2));
+  const size_t o_x64 = cv.add(sizeof(double) * n), o_y64 = cv.add(sizeof(double) * n);
+  const size_t o_FT64 = cv.add(sizeof(double) * n * D);
+  const size_t o_xs = cv.add(sizeof(float) * P.n_pad), o_ys = cv.add(sizeof(float) * P.n_pad);
+  const size_t o_xs_lo = cv.add(sizeof(float) * P.n_pad), o_ys_lo = cv.add(sizeof(float) * P.n_pad);
+  const size_t o_FT32 = cv.add(sizeof(float) * P.n_pad * P.D_pad);
+  const size_t o_FR32 = d.precision != MLS_P_FP64 ? cv.add(sizeof(float) * P.n_pad * D) : 0;
+  const size_t o_fcen = cv.add(sizeof(double) * D), o_fscl = cv.add(sizeof(double) * D);
+  const size_t o_fcen32 = cv.add(sizeof(float) * D), o_fscl32 = cv.add(sizeof(float) * D);
+  const size_t o_key = binned ? cv.add(sizeof(int) * n) : 0;
+  const size_t o_perm_tmp = binned ? cv.add(sizeof(int) * n) : 0;
+  const size_t o_perm = binned ? cv.add(sizeof(int) * n) : 0;
+  const size_t o_xyb = blocked ? cv.add(sizeof(float) * (P.n_pad / 8) * 20) : 0;
+  const size_t o_fb = blocked ? cv.add(sizeof(float) * (P.n_pad / 8) * ((size_t)dc * 8 + 4) * passes) : 0;
   mls_status ms;
-  if ((ms = dev_alloc(h, (void **)&keys, sizeof(unsigned long long) * 2 * (D + 2), st)) != MLS_OK) return ms;
-  k_fill_u64<<<(D + 2 + 255) / 256, 256, 0, st>>>(keys, D + 2, ~0ull);
-  ++h->launches;
-  k_fill_u64<<<(D + 2 + 255) / 256, 256, 0, st>>>(keys + D + 2, D + 2, 0ull);
+  char *blk = nullptr;
+  if ((ms = dev_alloc(h, (void **)&blk, cv.bytes, st)) != MLS_OK) return ms;
+  unsigned long long *keys = (unsigned long long *)(blk + o_keys);
+  P.x64 = (double *)(blk + o_x64);
+  P.y64 = (double *)(blk + o_y64);
+  P.FT64 = (double *)(blk + o_FT64);
+  P.xs = (float *)(blk + o_xs);
+  P.ys = (float *)(blk + o_ys);
+  P.xs_lo = (float *)(blk + o_xs_lo);
+  P.ys_lo = (float *)(blk + o_ys_lo);
+  P.FT32 = (float *)(blk + o_FT32);
+  if (d.precision != MLS_P_FP64) P.FR32 = (float *)(blk + o_FR32);
+  P.fcen = (double *)(blk + o_fcen);
+  P.fscl = (double *)(blk + o_fscl);
+  P.fcen32 = (float *)(blk + o_fcen32);
+  P.fscl32 = (float *)(blk + o_fscl32);
+  int *perm = binned ? (int *)(blk + o_perm) : nullptr;
+  int *key = binned ? (int *)(blk + o_key) : nullptr;
+  int *perm_tmp = binned ? (int *)(blk + o_perm_tmp) : nullptr;
+  if (blocked) {
+    P.xyb = (float *)(blk + o_xyb);
+    P.fb = (float *)(blk + o_fb);
+  }
+
+  // --- ranges of x, y and every value column
+  k_init_keys<<<(2 * (D + 2) + 255) / 256, 256, 0, st>>>(keys, D + 2);
   ++h->launches;
   {
     const int64_t tot = n * 2;
@@ -251,6 +332,13 @@ mls_status prep_points(mls_handle *h, const double *xy, const double *F, cudaStr
     ++h->launches;
   }
   MLS_CUDA_TRY(cudaGetLastError());
+
+  // --- the value frames, formed on the device while the host waits for
+  // the ranges below (only the bounding box and the grid need them there)
+  k_value_frames<<<(D + 127) / 128, 128, 0, st>>>(keys + 2, keys + D + 4, D, P.fcen, P.fscl, P.fcen32, P.fscl32);
+  ++h->launches;
+  MLS_CUDA_TRY(cudaGetLastError());
+  // --- the ranges on the host: finiteness, the bounding box and the grid
   std::vector<unsigned long long> hk(2 * (D + 2));
   MLS_CUDA_TRY(cudaMemcpyAsync(hk.data(), keys, hk.size() * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
   MLS_CUDA_TRY(cudaStreamSynchronize(st));
@@ -267,47 +355,11 @@ mls_status prep_points(mls_handle *h, const double *xy, const double *F, cudaStr
   P.bbox[3] = hi[1];
   P.ctr_x = 0.5 * (lo[0] + hi[0]);
   P.ctr_y = 0.5 * (lo[1] + hi[1]);
-  std::vector<double> cen(D), scl(D);
-  std::vector<float> cen32(D), scl32(D);
-  for (int c = 0; c < D; ++c) {
-    cen[c] = 0.5 * (lo[c + 2] + hi[c + 2]);
-    scl[c] = 0.5 * (hi[c + 2] - lo[c + 2]);
-    if (!(scl[c] > 0.0)) scl[c] = 1.0;
-    cen32[c] = (float)cen[c];
-    scl32[c] = (float)scl[c];
-  }
 
-  // --- device arrays
-  void *p;
-#define ALLOC(ptr, bytes)                                                   \
-  do {                                                                      \
-    if ((ms = dev_alloc(h, &p, (bytes), st)) != MLS_OK) return ms;          \
-    ptr = (decltype(ptr))p;                                                 \
-  } while (0)
-  ALLOC(P.x64, sizeof(double) * n);
-  ALLOC(P.y64, sizeof(double) * n);
-  ALLOC(P.FT64, sizeof(double) * n * D);
-  ALLOC(P.xs, sizeof(float) * P.n_pad);
-  ALLOC(P.ys, sizeof(float) * P.n_pad);
-  ALLOC(P.xs_lo, sizeof(float) * P.n_pad);
-  ALLOC(P.ys_lo, sizeof(float) * P.n_pad);
-  ALLOC(P.FT32, sizeof(float) * P.n_pad * P.D_pad);
-  if (d.precision != MLS_P_FP64) ALLOC(P.FR32, sizeof(float) * P.n_pad * D);
-  ALLOC(P.fcen, sizeof(double) * D);
-  ALLOC(P.fscl, sizeof(double) * D);
-  ALLOC(P.fcen32, sizeof(float) * D);
-  ALLOC(P.fscl32, sizeof(float) * D);
-  MLS_CUDA_TRY(cudaMemcpyAsync(P.fcen, cen.data(), sizeof(double) * D, cudaMemcpyHostToDevice, st));
-  MLS_CUDA_TRY(cudaMemcpyAsync(P.fscl, scl.data(), sizeof(double) * D, cudaMemcpyHostToDevice, st));
-  MLS_CUDA_TRY(cudaMemcpyAsync(P.fcen32, cen32.data(), sizeof(float) * D, cudaMemcpyHostToDevice, st));
-  MLS_CUDA_TRY(cudaMemcpyAsync(P.fscl32, scl32.data(), sizeof(float) * D, cudaMemcpyHostToDevice, st));
-
-  // --- binning for the compact-support weight
-  int *perm = nullptr;
-  // binning for the compact-support weight, and for the Gaussian (the
+  // --- binning for the compact-support weight, and for the Gaussian (the
   // hand-over path visits only the cells within its cut radius; the full-sum
   // kernels read every point and do not depend on the order)
-  if (d.weight != MLS_W_INVDIST) {
+  if (binned) {
     // cells of h; for the Wendland weight h/2: a tile and the pixels it
     // holds visit the cells within h of them, and half-size cells follow
     // the union of their support discs more closely (fewer zero weights)
@@ -321,16 +373,16 @@ mls_status prep_points(mls_handle *h, const double *xy, const double *F, cudaStr
     P.gx = (int)floor(ex / cell) + 1;
     P.gy = (int)floor(ey / cell) + 1;
     const int ncell = P.gx * P.gy;
-    int *key, *counts, *cursor, *perm_tmp, *totals, *grand;
     const int nb = (ncell + 1 + 1023) / 1024;
-    ALLOC(P.cell_start, sizeof(int) * (ncell + 1));
-    ALLOC(key, sizeof(int) * n);
-    ALLOC(counts, sizeof(int) * (ncell + 1));
-    ALLOC(cursor, sizeof(int) * ncell);
-    ALLOC(perm_tmp, sizeof(int) * n);
-    ALLOC(perm, sizeof(int) * n);
-    ALLOC(totals, sizeof(int) * nb);
-    ALLOC(grand, sizeof(int));
+    Carve cc;
+    const size_t o_start = cc.add(sizeof(int) * (ncell + 1)), o_counts = cc.add(sizeof(int) * (ncell + 1));
+    const size_t o_cursor = cc.add(sizeof(int) * ncell), o_totals = cc.add(sizeof(int) * nb);
+    const size_t o_grand = cc.add(sizeof(int));
+    char *cb = nullptr;
+    if ((ms = dev_alloc(h, (void **)&cb, cc.bytes, st)) != MLS_OK) return ms;
+    P.cell_start = (int *)(cb + o_start);
+    int *counts = (int *)(cb + o_counts), *cursor = (int *)(cb + o_cursor);
+    int *totals = (int *)(cb + o_totals), *grand = (int *)(cb + o_grand);
     MLS_CUDA_TRY(cudaMemsetAsync(counts, 0, sizeof(int) * (ncell + 1), st));
     MLS_CUDA_TRY(cudaMemsetAsync(cursor, 0, sizeof(int) * ncell, st));
     const int nbk = (int)((n + 255) / 256);
@@ -360,18 +412,13 @@ mls_status prep_points(mls_handle *h, const double *xy, const double *F, cudaStr
     ++h->launches;
     MLS_CUDA_TRY(cudaGetLastError());
   }
-  if (d.precision == MLS_P_FP16 || d.precision == MLS_P_BF16) {
-    const int dc = tc_dims_per_pass(D, d.degree);
-    const int passes = (D + dc - 1) / dc;
-    P.fb_dc = dc;
-    ALLOC(P.xyb, sizeof(float) * (P.n_pad / 8) * 20);
-    ALLOC(P.fb, sizeof(float) * (P.n_pad / 8) * ((size_t)dc * 8 + 4) * passes);
-    dim3 g3((unsigned)((P.n_pad + 255) / 256), (unsigned)(passes < 8 ? passes : 8));
+  if (blocked) {
+    const int rows = 1 + passes * dc;
+    dim3 g3((unsigned)((P.n_pad + 255) / 256), (unsigned)(rows < 65535 ? rows : 65535));
     k_block<<<g3, 256, 0, st>>>(P.xs, P.ys, P.FT32, P.n_pad, D, dc, passes, P.xyb, P.fb);
     ++h->launches;
     MLS_CUDA_TRY(cudaGetLastError());
   }
-#undef ALLOC
   return MLS_OK;
 }
 

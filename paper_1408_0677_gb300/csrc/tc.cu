@@ -154,6 +154,39 @@ __device__ __forceinline__ void band_labels(const float (&f)[G], const int (&row
   }
 }
 
+// Two FP32 lanes in one 64-bit register pair: sm_100-family cores execute
+// add / mul / fma on both halves in one instruction (IEEE round to nearest
+// per half, the same results as two scalar operations).
+__device__ __forceinline__ uint64_t f2(float a, float b) {
+  uint64_t r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+  return r;
+}
+__device__ __forceinline__ float2 f2_get(uint64_t v) {
+  float2 r;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(r.x), "=f"(r.y) : "l"(v));
+  return r;
+}
+__device__ __forceinline__ uint64_t f2_mul(uint64_t a, uint64_t b) {
+  uint64_t r;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ uint64_t f2_add(uint64_t a, uint64_t b) {
+  uint64_t r;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ uint64_t f2_fma(uint64_t a, uint64_t b, uint64_t c) {
+  uint64_t r;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+  return r;
+}
+__device__ __forceinline__ uint64_t f2_sub(uint64_t a, uint64_t b) {
+  uint64_t r;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
 // Eight operand values -> hi and lo 16-byte chunks (G = hi + lo).
 template <bool FP16>
 __device__ __forceinline__ void split8(const float (&x)[8], uint4 &hi, uint4 &lo) {
@@ -162,10 +195,22 @@ __device__ __forceinline__ void split8(const float (&x)[8], uint4 &hi, uint4 &lo
   for (int q = 0; q < 4; ++q) {
     h[q] = pack2<FP16>(x[2 * q], x[2 * q + 1]);
     const float2 b = unpack2<FP16>(h[q]);
-    l[q] = pack2<FP16>(x[2 * q] - b.x, x[2 * q + 1] - b.y);
+    const float2 r = f2_get(f2_sub(f2(x[2 * q], x[2 * q + 1]), f2(b.x, b.y)));
+    l[q] = pack2<FP16>(r.x, r.y);
   }
   hi = make_uint4(h[0], h[1], h[2], h[3]);
   lo = make_uint4(l[0], l[1], l[2], l[3]);
+}
+
+// Four operand values, as two lane pairs, -> hi and lo 8-byte chunks (as split4).
+template <bool FP16>
+__device__ __forceinline__ void split4p(uint64_t v01, uint64_t v23, uint2 &hi, uint2 &lo) {
+  const float2 a = f2_get(v01), b = f2_get(v23);
+  const uint32_t h0 = pack2<FP16>(a.x, a.y), h1 = pack2<FP16>(b.x, b.y);
+  const float2 ua = unpack2<FP16>(h0), ub = unpack2<FP16>(h1);
+  const float2 ra = f2_get(f2_sub(v01, f2(ua.x, ua.y))), rb = f2_get(f2_sub(v23, f2(ub.x, ub.y)));
+  hi = make_uint2(h0, h1);
+  lo = make_uint2(pack2<FP16>(ra.x, ra.y), pack2<FP16>(rb.x, rb.y));
 }
 
 // Four operand values -> hi and lo 8-byte chunks (G = hi + lo).
@@ -194,6 +239,13 @@ __device__ __forceinline__ float sqrt_approx(float x) {
   return y;
 }
 
+// the products x_k y_k g of four lanes, two at a time
+__device__ __forceinline__ void prod4(const float4 &x, const float4 &y, uint64_t g, float *w) {
+  const float2 a = f2_get(f2_mul(f2_mul(f2(x.x, x.y), f2(y.x, y.y)), g));
+  const float2 b = f2_get(f2_mul(f2_mul(f2(x.z, x.w), f2(y.z, y.w)), g));
+  w[0] = a.x; w[1] = a.y; w[2] = b.x; w[3] = b.y;
+}
+
 // Wendland weight S (1 - q)^4 (4 q + 1) of a pair with q^2 = t, zero for
 // t >= 1.  The weight is rounded to a 16-bit operand next, so the square root
 // is the approximate one (relative error near 2^-23, far below that
@@ -205,6 +257,20 @@ __device__ __forceinline__ float wendland_weight(float t) {
   const float o = 1.f - q;
   const float o2 = o * o;
   return (t < 1.f) ? o2 * o2 * fmaf(4.f * S, q, S) : 0.f;
+}
+
+// wendland_weight of two pairs (q^2 = t.x and t.y) with two-lane arithmetic:
+// the same operations, so the same results
+template <bool FP16>
+__device__ __forceinline__ float2 wendland_weight2(uint64_t t2) {
+  const float S = weight_scale<FP16>();
+  const float2 t = f2_get(t2);
+  const float qa = sqrt_approx(fmaxf(t.x, 0.f)), qb = sqrt_approx(fmaxf(t.y, 0.f));
+  const uint64_t q = f2(qa, qb);
+  const uint64_t o = f2_sub(f2(1.f, 1.f), q);
+  const uint64_t o2 = f2_mul(o, o);
+  const float2 w = f2_get(f2_mul(f2_mul(o2, o2), f2_fma(f2(4.f * S, 4.f * S), q, f2(S, S))));
+  return make_float2(t.x < 1.f ? w.x : 0.f, t.y < 1.f ? w.y : 0.f);
 }
 
 // The sequence of point tiles a CTA visits: all points, or the cell rows of
@@ -490,6 +556,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mls_tc(KParams p, int d0, int D
                                   : 0.f;
       gcor[a] = ex2_approx(fminf(res, kResMax)) * weight_scale<FP16>();
     }
+    const uint64_t g0x2 = f2(gcor[0], gcor[0]), g1x2 = f2(gcor[1], gcor[1]);
     int kt = 0;
     for (; alive; ++kt) {
       const int s = kt & 1;
@@ -549,19 +616,22 @@ __global__ void __launch_bounds__(kThreads, 1) k_mls_tc(KParams p, int d0, int D
       for (int c = 4 * hh; c < 4 * hh + 4; ++c) {
         const float4 xa = *(const float4 *)(fx + 8 * c), xb = *(const float4 *)(fx + 8 * c + 4);
         const float4 ya = *(const float4 *)(fy0 + 8 * c), yb = *(const float4 *)(fy0 + 8 * c + 4);
-        const float g0 = gcor[0];
-        float w0[8] = {xa.x * ya.x * g0, xa.y * ya.y * g0, xa.z * ya.z * g0, xa.w * ya.w * g0,
-                       xb.x * yb.x * g0, xb.y * yb.y * g0, xb.z * yb.z * g0, xb.w * yb.w * g0};
+        // w = (column factor x row factor) x correction, two lanes per instruction
+        float w0[8];
+        prod4(xa, ya, g0x2, w0);
+        prod4(xb, yb, g0x2, w0 + 4);
         uint4 q0, q1;
         if (WSPLIT) {
           split8<FP16>(w0, q0, q1);          // A0 = hi, A1 = lo of accumulator 0
         } else {
           const float4 za = *(const float4 *)(fy1 + 8 * c), zb = *(const float4 *)(fy1 + 8 * c + 4);
-          const float g1 = gcor[1];
+          float w1[8];
+          prod4(xa, za, g1x2, w1);
+          prod4(xb, zb, g1x2, w1 + 4);
           q0.x = pack2<FP16>(w0[0], w0[1]); q0.y = pack2<FP16>(w0[2], w0[3]);
           q0.z = pack2<FP16>(w0[4], w0[5]); q0.w = pack2<FP16>(w0[6], w0[7]);
-          q1.x = pack2<FP16>(xa.x * za.x * g1, xa.y * za.y * g1); q1.y = pack2<FP16>(xa.z * za.z * g1, xa.w * za.w * g1);
-          q1.z = pack2<FP16>(xb.x * zb.x * g1, xb.y * zb.y * g1); q1.w = pack2<FP16>(xb.z * zb.z * g1, xb.w * zb.w * g1);
+          q1.x = pack2<FP16>(w1[0], w1[1]); q1.y = pack2<FP16>(w1[2], w1[3]);
+          q1.z = pack2<FP16>(w1[4], w1[5]); q1.w = pack2<FP16>(w1[6], w1[7]);
         }
         *(uint4 *)(A0 + sw128_off(m, c)) = q0;
         *(uint4 *)(A1 + sw128_off(m, c)) = q1;
@@ -590,6 +660,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_mls_tc(KParams p, int d0, int D
       else
         E[a] = dx[a] * dx[a] + dy[a] * dy[a];
     }
+    // the pixel parts as lane pairs: both accumulators' pixels, or one twice
+    const uint64_t E2 = f2(E[0], E[NACC - 1]), dx2 = f2(dx[0], dx[NACC - 1]), dy2 = f2(dy[0], dy[NACC - 1]);
     float4 *prm = (float4 *)(smem + lay.offPrm) + warp * kKT;
     int kt = 0;
     for (; alive; ++kt) {
@@ -632,13 +704,31 @@ __global__ void __launch_bounds__(kThreads, 1) k_mls_tc(KParams p, int d0, int D
 #pragma unroll 1
       for (int c = 4 * hh; c < 4 * hh + 4; ++c) {
         float w0[8], w1[8];
+        // q^2 = |x~|^2 - 2 x~ . delta + |delta|^2 (the point's and the pixel's
+        // parts), two lanes per instruction: the two accumulators' pixels of
+        // one point, or (one accumulator) two points
+        if (NACC == 2) {
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
-          const float4 pr = prm[8 * c + j];
-          // q^2 = |x~|^2 - 2 x~ . delta + |delta|^2 (the point's and the pixel's parts)
-          w0[j] = wendland_weight<FP16>(fmaf(pr.y, dx[0], fmaf(pr.z, dy[0], pr.x + E[0])));
-          if (NACC == 2)
-            w1[j] = wendland_weight<FP16>(fmaf(pr.y, dx[NACC - 1], fmaf(pr.z, dy[NACC - 1], pr.x + E[NACC - 1])));
+          for (int j = 0; j < 8; ++j) {
+            const float4 pr = prm[8 * c + j];
+            uint64_t t2 = f2_add(f2(pr.x, pr.x), E2);
+            t2 = f2_fma(f2(pr.z, pr.z), dy2, t2);
+            t2 = f2_fma(f2(pr.y, pr.y), dx2, t2);
+            const float2 w = wendland_weight2<FP16>(t2);
+            w0[j] = w.x;
+            w1[j] = w.y;
+          }
+        } else {
+#pragma unroll
+          for (int j = 0; j < 8; j += 2) {
+            const float4 pa = prm[8 * c + j], pb = prm[8 * c + j + 1];
+            uint64_t t2 = f2_add(f2(pa.x, pb.x), E2);
+            t2 = f2_fma(f2(pa.z, pb.z), dy2, t2);
+            t2 = f2_fma(f2(pa.y, pb.y), dx2, t2);
+            const float2 w = wendland_weight2<FP16>(t2);
+            w0[j] = w.x;
+            w0[j + 1] = w.y;
+          }
         }
         uint4 q0, q1;
         if (WSPLIT) {
@@ -722,16 +812,19 @@ __global__ void __launch_bounds__(kThreads, 1) k_mls_tc(KParams p, int d0, int D
         *(uint2 *)(Bh + sw128_off(rr, g)) = hi;
         *(uint2 *)(Bl + sw128_off(rr, g)) = lo;
       }
-      // value rows 16 + d K + a, dimensions d = rr, rr + 16, ...
-      float bas[K][4];
+      // value rows 16 + d K + a, dimensions d = rr, rr + 16, ...: basis values
+      // b_a of points (0, 1) and (2, 3) as lane pairs (a masked point has
+      // x = y = 0 and a zero value, so its products are zero without the mask)
+      uint64_t bas[K][2];
 #pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        bas[0][j] = msk[j];
-        if (K > 1) { bas[1][j] = msk[j] * xv[j]; bas[2][j] = msk[j] * yv[j]; }
+      for (int hq = 0; hq < 2; ++hq) {
+        const uint64_t x = f2(xv[2 * hq], xv[2 * hq + 1]), y = f2(yv[2 * hq], yv[2 * hq + 1]);
+        bas[0][hq] = f2(msk[2 * hq], msk[2 * hq + 1]);
+        if (K > 1) { bas[1][hq] = x; bas[2][hq] = y; }
         if (K > 3) {
-          bas[3][j] = msk[j] * xv[j] * xv[j];
-          bas[4][j] = msk[j] * xv[j] * yv[j];
-          bas[5][j] = msk[j] * yv[j] * yv[j];
+          bas[3][hq] = f2_mul(x, x);
+          bas[4][hq] = f2_mul(x, y);
+          bas[5][hq] = f2_mul(y, y);
         }
       }
       for (int d = rr; d < Dc; d += 16) {
@@ -746,13 +839,14 @@ __global__ void __launch_bounds__(kThreads, 1) k_mls_tc(KParams p, int d0, int D
 #pragma unroll
           for (int j = 0; j < 4; ++j) fv[j] = 0.f;
         }
+        const uint64_t fp0 = f2(fv[0], fv[1]), fp1 = f2(fv[2], fv[3]);
 #pragma unroll
         for (int a = 0; a < K; ++a) {
-          float val[4];
-#pragma unroll
-          for (int j = 0; j < 4; ++j) val[j] = bas[a][j] * fv[j];
+          // b_0 f = f (the value is zero where the mask is)
+          const uint64_t v0 = a == 0 ? fp0 : f2_mul(bas[a][0], fp0);
+          const uint64_t v1 = a == 0 ? fp1 : f2_mul(bas[a][1], fp1);
           uint2 hi, lo;
-          split4<FP16>(val, hi, lo);
+          split4p<FP16>(v0, v1, hi, lo);
           const int row = 16 + d * K + a;
           *(uint2 *)(Bh + sw128_off(row, g)) = hi;
           *(uint2 *)(Bl + sw128_off(row, g)) = lo;
