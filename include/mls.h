@@ -191,6 +191,11 @@ mls_status mls_desc_default(mls_desc *desc);
  * Converts the values to the layouts the kernels read, normalises them per
  * dimension and, for the Wendland weight, bins the points on a uniform grid
  * of cell size h (counting sort; deterministic order).
+ * Device memory of handles, renders, batches and server requests comes from
+ * one stream-ordered memory pool per device, created by the library on first
+ * use.  It keeps freed memory for reuse instead of returning it to the
+ * system: the pool holds up to the largest working set the process has had
+ * until the process exits.
  * Errors: MLS_E_INVAL (desc, pointers), MLS_E_NOMEM, MLS_E_CUDA.
  */
 mls_status mls_create(const mls_desc *desc, const double *xy, const double *F,

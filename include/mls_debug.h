@@ -41,6 +41,18 @@ int mls_debug_df_weight(int kind, const float *arg_hi, const float *arg_lo, int6
 struct mls_handle;
 int mls_debug_operand_cut(struct mls_handle *h, int32_t on);
 
+/* Pixels that the reduced-precision passes hand over are recomputed by four
+ * kernels (setup, moments, degree policy, values) for the first entries of
+ * the list, up to a state capacity of an eighth of the W H pixels (at least
+ * min(W H, 1024) entries, at most 2^19), when the list holds at least
+ * 19,456 entries; by one fused kernel for shorter lists and for the entries
+ * past that capacity.  For the handle's later renders, cap >= 0 lowers the
+ * capacity (0: every entry through the fused kernel) and least >= 0 sets the
+ * shortest list the four kernels take, so that a test can check both
+ * paths; -1 restores either.  Returns MLS_E_INVAL for a null handle or an
+ * argument below -1, MLS_OK otherwise. */
+int mls_debug_handover_split(struct mls_handle *h, int64_t cap, int64_t least);
+
 #ifdef __cplusplus
 }
 #endif

@@ -194,32 +194,107 @@ __device__ __forceinline__ int for_near(const KParams &p, const Ranges &R, float
 }
 
 // ---------------------------------------------------------------------------
-// FP64 degree policy and centroid-frame solve, one lane per pixel (GB300's
-// FP64 units are few: running the policy once per lane for 32 pixels instead
-// of redundantly on every lane of a warp cuts its FP64 instructions 32-fold).
+// Degree policy and centroid-frame solve, one lane per pixel, in a scalar
+// type T: FP64 (double), or double-float (dd: hi + lo pairs of FP32, about
+// 46 significant bits) on the FP32 pipes.  GB300 runs FP64 at a small
+// fraction of its FP32 rate: the split kernels' policy kernel, which has the
+// SM to itself, runs in double-float; the fused kernel, whose blocks overlap
+// one block's policy warp with the other blocks' double-float phases, in
+// FP64 (fewer instructions and registers on its one policy warp).  46 bits
+// resolve the rcond_1 threshold test of the definition with room to spare
+// (the decision is ambiguous only within a factor around the threshold, far
+// wider than the rounding here), and z carries a relative error of about
+// 2^-46 times the centroid-frame condition (<= 1e8).
 
-// 1/d for a positive normal d: FP32 seed and two Newton steps (each doubles
-// the number of correct bits: 2^-23 -> 2^-46 -> FP64 rounding).
-__device__ __forceinline__ double rcp64(double d) {
+struct dd {
+  float hi, lo;
+};
+__device__ __forceinline__ dd ddf(float a) { return {a, 0.f}; }
+__device__ __forceinline__ dd ddd(double a) {
+  const float h = (float)a;
+  return {h, (float)(a - (double)h)};
+}
+__device__ __forceinline__ dd operator+(dd a, dd b) {
+  const df32 r = df_add({a.hi, a.lo}, {b.hi, b.lo});
+  return {r.hi, r.lo};
+}
+__device__ __forceinline__ dd operator-(dd a) { return {-a.hi, -a.lo}; }
+__device__ __forceinline__ dd operator-(dd a, dd b) { return a + (-b); }
+__device__ __forceinline__ dd operator*(dd a, dd b) {
+  const df32 r = df_mul({a.hi, a.lo}, {b.hi, b.lo});
+  return {r.hi, r.lo};
+}
+__device__ __forceinline__ dd &operator+=(dd &a, dd b) { return a = a + b; }
+__device__ __forceinline__ dd &operator-=(dd &a, dd b) { return a = a - b; }
+// the sign is that of hi (a normalised pair has |lo| <= ulp(hi) / 2)
+__device__ __forceinline__ bool operator>(dd a, dd b) { return a.hi > b.hi || (a.hi == b.hi && a.lo > b.lo); }
+__device__ __forceinline__ bool operator>=(dd a, dd b) { return a.hi > b.hi || (a.hi == b.hi && a.lo >= b.lo); }
+// a / b: the FP32 quotient q1, then the quotient of the remainder a - q1 b
+__device__ __forceinline__ dd ddiv(dd a, dd b) {
+  const float q1 = a.hi / b.hi;
+  const df32 qb = df_mul_f({b.hi, b.lo}, q1);
+  const dd r = a - dd{qb.hi, qb.lo};
+  const float q2 = r.hi / b.hi;
+  const df32 q = df_two_sum(q1, q2);
+  return {q.hi, q.lo};
+}
+
+// The operations the policy needs, for both scalar types.
+template <typename T> __device__ __forceinline__ T tc_(float a);
+template <> __device__ __forceinline__ double tc_<double>(float a) { return (double)a; }
+template <> __device__ __forceinline__ dd tc_<dd>(float a) { return ddf(a); }
+__device__ __forceinline__ double tabs(double a) { return fabs(a); }
+__device__ __forceinline__ dd tabs(dd a) { return a.hi < 0.f ? -a : a; }
+__device__ __forceinline__ double tmax(double a, double b) { return fmax(a, b); }
+__device__ __forceinline__ dd tmax(dd a, dd b) { return b > a ? b : a; }
+// 1/d for a positive normal d: FP32 seed and two Newton steps in FP64 (each
+// doubles the number of correct bits: 2^-23 -> 2^-46 -> FP64 rounding)
+__device__ __forceinline__ double trcp(double d) {
   double r = (double)__frcp_rn((float)d);
   r = r * fma(-d, r, 2.0);
   r = r * fma(-d, r, 2.0);
   return r;
 }
+__device__ __forceinline__ dd trcp(dd b) { return ddiv(ddf(1.f), b); }
+__device__ __forceinline__ double trsqrt(double b) { return rsqrt(b); }
+// 1/sqrt(b), b > 0: the FP32 estimate r and one Newton step in double-float,
+// r + r (1 - b r^2) / 2 (the step doubles the correct bits, 2^-22 -> 2^-44)
+__device__ __forceinline__ dd trsqrt(dd b) {
+  const float r = rsqrtf(b.hi);
+  const dd e = ddf(1.f) - b * (ddf(r) * ddf(r));
+  return ddf(r) + ddf(0.5f * r) * e;
+}
+// v as a pair of floats hi + lo (the form the value phase reads)
+__device__ __forceinline__ void tsplit(double v, float &hi, float &lo) {
+  hi = (float)v;
+  lo = (float)(v - (double)hi);
+}
+__device__ __forceinline__ void tsplit(dd v, float &hi, float &lo) {
+  hi = v.hi;
+  lo = v.lo;
+}
+__device__ __forceinline__ void tjoin(float hi, float lo, double &v) { v = (double)hi + (double)lo; }
+__device__ __forceinline__ void tjoin(float hi, float lo, dd &v) {
+  const df32 t = df_two_sum(hi, lo);
+  v = {t.hi, t.lo};
+}
+__device__ __forceinline__ void tfrom(double a, double &v) { v = a; }
+__device__ __forceinline__ void tfrom(double a, dd &v) { v = ddd(a); }
 
 // Equilibrated LDL^T factorisation of the K x K moment matrix S[midx(a, b)]
 // and rcond_1 = 1 / (|Me|_1 |Me^-1|_1) of the equilibrated matrix Me.
 // Returns 0 when a diagonal entry or a pivot is not positive.  L (unit
 // lower), dinv (inverse pivots) and sd (equilibration 1/sqrt(M_aa)) receive
 // the factorisation.
-template <int K>
-__device__ double ldl_rcond(const double (&S)[15], double (&L)[6][6], double (&dinv)[6], double (&sd)[6]) {
-  double Me[K][K];
+template <int K, typename T>
+__device__ T ldl_rcond(const T (&S)[15], T (&L)[6][6], T (&dinv)[6], T (&sd)[6]) {
+  const T zero = tc_<T>(0.f);
+  T Me[K][K];
 #pragma unroll
   for (int a = 0; a < K; ++a) {
-    const double d = S[midx(a, a)];
-    if (!(d > 0.0)) return 0.0;
-    sd[a] = rsqrt(d);
+    const T d = S[midx(a, a)];
+    if (!(d > zero)) return zero;
+    sd[a] = trsqrt(d);
   }
 #pragma unroll
   for (int a = 0; a < K; ++a)
@@ -228,17 +303,17 @@ __device__ double ldl_rcond(const double (&S)[15], double (&L)[6][6], double (&d
   // LDL^T (no square roots): D_j = Me_jj - sum_t L_jt (L_jt D_t),
   // L_ij = (Me_ij - sum_t L_it (L_jt D_t)) / D_j, with LD_jt = L_jt D_t kept
   // (it is the numerator of L_jt before the division)
-  double LD[K][K];
+  T LD[K][K];
 #pragma unroll
   for (int j = 0; j < K; ++j) {
-    double dj = Me[j][j];
+    T dj = Me[j][j];
 #pragma unroll
     for (int t = 0; t < j; ++t) dj -= L[j][t] * LD[j][t];
-    if (!(dj > 0.0)) return 0.0;
-    dinv[j] = rcp64(dj);
+    if (!(dj > zero)) return zero;
+    dinv[j] = trcp(dj);
 #pragma unroll
     for (int i = j + 1; i < K; ++i) {
-      double v = Me[i][j];
+      T v = Me[i][j];
 #pragma unroll
       for (int t = 0; t < j; ++t) v -= L[i][t] * LD[j][t];
       LD[i][j] = v;
@@ -247,14 +322,14 @@ __device__ double ldl_rcond(const double (&S)[15], double (&L)[6][6], double (&d
   }
   // 1-norms of Me and of its inverse.  Me^-1 = L^-T D^-1 L^-1 is symmetric:
   // with Li = L^-1 (unit lower) and G_kj = dinv_k Li_kj, its entry (i, j),
-  // i <= j, is sum_{k >= j} Li_ki G_kj (about a third of the FP64 operations
-  // of K forward and back substitutions)
-  double Li[K][K], G[K][K];
+  // i <= j, is sum_{k >= j} Li_ki G_kj (about a third of the operations of K
+  // forward and back substitutions)
+  T Li[K][K], G[K][K];
 #pragma unroll
   for (int i = 0; i < K; ++i)
 #pragma unroll
     for (int j = 0; j < i; ++j) {
-      double v = -L[i][j];
+      T v = -L[i][j];
 #pragma unroll
       for (int t = j + 1; t < i; ++t) v -= L[i][t] * Li[t][j];
       Li[i][j] = v;
@@ -265,17 +340,17 @@ __device__ double ldl_rcond(const double (&S)[15], double (&L)[6][6], double (&d
 #pragma unroll
     for (int j = 0; j < k; ++j) G[k][j] = dinv[k] * Li[k][j];
   }
-  double cI[K], cA[K];
+  T cI[K], cA[K];
 #pragma unroll
-  for (int c = 0; c < K; ++c) cI[c] = cA[c] = 0.0;
+  for (int c = 0; c < K; ++c) cI[c] = cA[c] = zero;
 #pragma unroll
   for (int j = 0; j < K; ++j)
 #pragma unroll
     for (int i = 0; i <= j; ++i) {
-      double v = 0.0;
+      T v = G[j][j] * (j == i ? tc_<T>(1.f) : Li[j][i]);
 #pragma unroll
-      for (int k = j; k < K; ++k) v += (k == i ? 1.0 : Li[k][i]) * G[k][j];
-      const double av = fabs(v), am = fabs(Me[i][j]);
+      for (int k = j + 1; k < K; ++k) v += Li[k][i] * G[k][j];
+      const T av = tabs(v), am = tabs(Me[i][j]);
       cI[j] += av;
       cA[j] += am;
       if (i != j) {
@@ -283,33 +358,32 @@ __device__ double ldl_rcond(const double (&S)[15], double (&L)[6][6], double (&d
         cA[i] += am;
       }
     }
-  double nI = 0.0, nA = 0.0;
+  T nI = zero, nA = zero;
 #pragma unroll
   for (int c = 0; c < K; ++c) {
-    nI = fmax(nI, cI[c]);
-    nA = fmax(nA, cA[c]);
+    nI = tmax(nI, cI[c]);
+    nA = tmax(nA, cA[c]);
   }
-  return 1.0 / (nA * nI);
+  return trcp(nA * nI);
 }
 
 // b <- M^-1 b with M = S^-1 Me S^-1 factorised as above: S Me^-1 S b.
-template <int K>
-__device__ __forceinline__ void ldl_solve(const double (&L)[6][6], const double (&dinv)[6], const double (&sd)[6],
-                                          double (&b)[6]) {
+template <int K, typename T>
+__device__ __forceinline__ void ldl_solve(const T (&L)[6][6], const T (&dinv)[6], const T (&sd)[6], T (&b)[6]) {
 #pragma unroll
-  for (int a = 0; a < K; ++a) b[a] *= sd[a];
+  for (int a = 0; a < K; ++a) b[a] = b[a] * sd[a];
 #pragma unroll
   for (int i = 0; i < K; ++i)
 #pragma unroll
     for (int t = 0; t < i; ++t) b[i] -= L[i][t] * b[t];
 #pragma unroll
-  for (int i = 0; i < K; ++i) b[i] *= dinv[i];
+  for (int i = 0; i < K; ++i) b[i] = b[i] * dinv[i];
 #pragma unroll
   for (int i = K - 1; i >= 0; --i)
 #pragma unroll
     for (int t = i + 1; t < K; ++t) b[i] -= L[t][i] * b[t];
 #pragma unroll
-  for (int a = 0; a < K; ++a) b[a] *= sd[a];
+  for (int a = 0; a < K; ++a) b[a] = b[a] * sd[a];
 }
 
 // Moments of the frame centred on (cx, cy) and scaled by isg, from the
@@ -318,60 +392,63 @@ __device__ __forceinline__ void ldl_solve(const double (&L)[6][6], const double 
 // y exponent, then a shift in y of every column.  A 1-D shift of moments
 // a_0..a_m by c is the Taylor shift: m passes, pass i replacing a_k by
 // a_k - c a_(k-1) for k = m down to i (m (m + 1) / 2 multiply-adds).
-template <int NM>
-__device__ __forceinline__ void centroid_moments(const double (&S)[15], double cx, double cy, double isg,
-                                                 double (&Sc)[15]) {
+template <int NM, typename T>
+__device__ __forceinline__ void centroid_moments(const T (&S)[15], T cx, T cy, T isg, T (&Sc)[15]) {
   constexpr int DM = NM == 15 ? 4 : NM == 6 ? 2 : 0;   // total degree of the moments
-  double a[15];
+  T a[15];
 #pragma unroll
-  for (int j = 0; j < 15; ++j) a[j] = (j < NM) ? S[j] : 0.0;
+  for (int j = 0; j < 15; ++j) a[j] = (j < NM) ? S[j] : tc_<T>(0.f);
 #pragma unroll
   for (int ey = 0; ey <= DM; ++ey)
 #pragma unroll
     for (int i = 1; i <= DM - ey; ++i)
 #pragma unroll
-      for (int k = DM - ey; k >= i; --k) a[mono_index(k, ey)] = fma(-cx, a[mono_index(k - 1, ey)], a[mono_index(k, ey)]);
+      for (int k = DM - ey; k >= i; --k) a[mono_index(k, ey)] -= cx * a[mono_index(k - 1, ey)];
 #pragma unroll
   for (int ex = 0; ex <= DM; ++ex)
 #pragma unroll
     for (int i = 1; i <= DM - ex; ++i)
 #pragma unroll
-      for (int k = DM - ex; k >= i; --k) a[mono_index(ex, k)] = fma(-cy, a[mono_index(ex, k - 1)], a[mono_index(ex, k)]);
-  double ps[5];
-  ps[0] = 1.0;
+      for (int k = DM - ex; k >= i; --k) a[mono_index(ex, k)] -= cy * a[mono_index(ex, k - 1)];
+  T ps[5];
+  ps[0] = tc_<T>(1.f);
 #pragma unroll
   for (int e = 1; e < 5; ++e) ps[e] = ps[e - 1] * isg;
 #pragma unroll
-  for (int j = 0; j < 15; ++j) Sc[j] = (j < NM) ? a[j] * ps[mono_ex(j) + mono_ey(j)] : 0.0;
+  for (int j = 0; j < 15; ++j) Sc[j] = (j < NM) ? a[j] * ps[mono_ex(j) + mono_ey(j)] : tc_<T>(0.f);
 }
 
 // z = M_c^-1 b_c(pixel) in the frame of the weighted centroid (degree of K
 // terms); fr receives that frame as pass 2 applies it (centre hi, lo in x
 // and y; 1/sigma).  Returns false when the centroid frame is degenerate or
 // still ill conditioned.
-template <int K>
-__device__ bool centroid_solve(const double (&Sd)[15], double (&z)[6], float (&fr)[5]) {
+template <int K, typename T>
+__device__ bool centroid_solve(const T (&Sd)[15], T (&z)[6], float (&fr)[5]) {
   constexpr int DEGK = K == 6 ? 2 : 1;
-  const double cx0 = Sd[1] / Sd[0], cy0 = Sd[2] / Sd[0];
-  const double var = (Sd[3] + Sd[5]) / Sd[0] - cx0 * cx0 - cy0 * cy0;
-  if (!(var > 0.0)) return false;
-  fr[0] = (float)cx0;
-  fr[1] = (float)(cx0 - (double)fr[0]);
-  fr[2] = (float)cy0;
-  fr[3] = (float)(cy0 - (double)fr[2]);
-  fr[4] = (float)rsqrt(var);
-  const double cx = (double)fr[0] + (double)fr[1], cy = (double)fr[2] + (double)fr[3];
-  const double isg = (double)fr[4];
-  double Sc[15];
-  centroid_moments<n_moments(DEGK)>(Sd, cx, cy, isg, Sc);
-  double L[6][6], dinv[6], sd[6];
-  const double rcc = ldl_rcond<K>(Sc, L, dinv, sd);
-  if (!(rcc > 1.0 / kKappaCentroid)) return false;
-  const double ex = -cx * isg, ey = -cy * isg;
-  double b[6] = {1.0, ex, ey, ex * ex, ex * ey, ey * ey};
+  const T i0 = trcp(Sd[0]);
+  const T cx0 = Sd[1] * i0, cy0 = Sd[2] * i0;
+  const T var = (Sd[3] + Sd[5]) * i0 - cx0 * cx0 - cy0 * cy0;
+  if (!(var > tc_<T>(0.f))) return false;
+  tsplit(cx0, fr[0], fr[1]);
+  tsplit(cy0, fr[2], fr[3]);
+  float isg_lo;
+  tsplit(trsqrt(var), fr[4], isg_lo);
+  T cx, cy;
+  tjoin(fr[0], fr[1], cx);
+  tjoin(fr[2], fr[3], cy);
+  const T isg = tc_<T>(fr[4]);
+  T Sc[15];
+  centroid_moments<n_moments(DEGK), T>(Sd, cx, cy, isg, Sc);
+  T L[6][6], dinv[6], sd[6];
+  const T rcc = ldl_rcond<K>(Sc, L, dinv, sd);
+  T rmin;
+  tfrom(1.0 / kKappaCentroid, rmin);
+  if (!(rcc > rmin)) return false;
+  const T ex = -(cx * isg), ey = -(cy * isg);
+  T b[6] = {tc_<T>(1.f), ex, ey, ex * ex, ex * ey, ey * ey};
   ldl_solve<K>(L, dinv, sd, b);
 #pragma unroll
-  for (int a = 0; a < 6; ++a) z[a] = (a < K) ? b[a] : 0.0;
+  for (int a = 0; a < 6; ++a) z[a] = (a < K) ? b[a] : tc_<T>(0.f);
   return true;
 }
 
@@ -379,25 +456,389 @@ __device__ bool centroid_solve(const double (&Sd)[15], double (&z)[6], float (&f
 // the equilibrated matrix against rcond_min, highest degree first), then z.
 // Returns the degree used (-1: no degree qualifies); *bad is set when the
 // pixel needs the FP64 kernel.
-template <int DEG>
-__device__ int pixel_policy(const double (&Sd)[15], long long count, double rcond_min, double (&z)[6],
-                            float (&fr)[5], bool *bad) {
-  double L[6][6], dinv[6], sd[6];
+template <int DEG, typename T>
+__device__ int pixel_policy(const T (&Sd)[15], long long count, T rcond_min, T (&z)[6], float (&fr)[5], bool *bad) {
+  T L[6][6], dinv[6], sd[6];
   int used = -1;
   if (DEG >= 2 && count >= 6 && ldl_rcond<6>(Sd, L, dinv, sd) >= rcond_min) used = 2;
   else if (DEG >= 1 && count >= 3 && ldl_rcond<3>(Sd, L, dinv, sd) >= rcond_min) used = 1;
-  else if (count >= 1 && Sd[0] > 0.0) used = 0;
-  for (int a = 0; a < 6; ++a) z[a] = 0.0;
+  else if (count >= 1 && Sd[0] > tc_<T>(0.f)) used = 0;
+  for (int a = 0; a < 6; ++a) z[a] = tc_<T>(0.f);
   fr[0] = fr[1] = fr[2] = fr[3] = 0.f;
   fr[4] = 1.f;
   *bad = false;
-  if (used == 0) z[0] = 1.0 / Sd[0];
-  else if (used == 1) *bad = !centroid_solve<3>(Sd, z, fr);
-  else if (used == 2) *bad = !centroid_solve<6>(Sd, z, fr);
+  if (used == 0) z[0] = trcp(Sd[0]);
+  else if (used == 1) *bad = !centroid_solve<3, T>(Sd, z, fr);
+  else if (used == 2) *bad = !centroid_solve<6, T>(Sd, z, fr);
   return used;
 }
 
 // ---------------------------------------------------------------------------
+
+// ---------------------------------------------------------------------------
+// The phases of one listed pixel, shared by the split kernels and the fused
+// kernel below.
+
+// Everything the moment and value phases need about pixel `id`: its
+// candidate cells, stabiliser and scaled position (hi + lo).  FP64 and
+// warp-uniform per pixel: run it one lane per pixel.
+template <int WK>
+__device__ void pixel_setup(const KParams &p, int id, Ranges &R, float &mhat, float &pxh, float &pxl, float &pyh,
+                            float &pyl) {
+  const int u = id % p.W, v = id / p.W;
+  const double px = __dadd_rn(p.x0, __dmul_rn(__dadd_rn((double)u, 0.5), p.sx));
+  const double py = __dadd_rn(p.y0, __dmul_rn(__dadd_rn((double)v, 0.5), p.sy));
+  mhat = (WK == MLS_W_WENDLAND) ? 0.f : p.mstab[pix_i(p, (int64_t)v * (p.tiles_x * 16) + u)];
+  if (WK == MLS_W_INVDIST) {
+    R.all_n = (int)p.n;
+    R.cx0 = R.cx1 = R.cy0 = R.cy1 = 0;
+  } else {
+    // near radius: the support (Wendland), the box (truncated Gaussian), or
+    // r^2 <= m + kCut (Gaussian), widened by a relative 1e-5 against rounding
+    const double rad = (WK == MLS_W_WENDLAND ? 1.0
+                        : p.trunc > 0.0      ? p.trunc
+                                             : (double)sqrtf(fmaxf(mhat, 0.f) + kCut)) *
+                       p.h * (1.0 + 1e-5);
+    const double inv_cell = p.inv_cell;
+    R.all_n = 0;
+    R.cx0 = max((int)floor((px - rad - p.gx0) * inv_cell), 0);
+    R.cx1 = min((int)floor((px + rad - p.gx0) * inv_cell), p.gx - 1);
+    R.cy0 = max((int)floor((py - rad - p.gy0) * inv_cell), 0);
+    R.cy1 = min((int)floor((py + rad - p.gy0) * inv_cell), p.gy - 1);
+  }
+  // pixel position in the scaled frame as hi + lo
+  const double inv_s = 1.0 / p.h;
+  const double pxs64 = (px - p.ctr_x) * inv_s, pys64 = (py - p.ctr_y) * inv_s;
+  pxh = (float)pxs64;
+  pxl = (float)(pxs64 - (double)pxh);
+  pyh = (float)pys64;
+  pyl = (float)(pys64 - (double)pyh);
+}
+
+// Double-float pixel-frame moments of one pixel, a warp per pixel.  store(k,
+// t) is called on every lane with the warp's total t of moment k < NM.
+// Returns the near points; *coincident as for_near.
+template <int DEG, int WK, typename Store>
+__device__ __forceinline__ int pixel_moments(const KParams &p, const Ranges &R, float mhat, float pxh, float pxl,
+                                             float pyh, float pyl, int lane, int *ri, float4 *rx,
+                                             const float2 *s_tab, int *coincident, Store store) {
+  constexpr int NM = n_moments(DEG);
+  df32 S[NM];
+#pragma unroll
+  for (int k = 0; k < NM; ++k) S[k] = {0.f, 0.f};
+  const int nnear = for_near<WK>(p, R, pxh, pxl, pyh, pyl, mhat, lane, ri, rx, coincident,
+                                 [&](bool valid, int, df32 ex, df32 ey) {
+    if (!valid) return;
+    const df32 w = pair_wdf<WK>(ex, ey, mhat, p.alpha, s_tab);
+    df_acc(S[0], w);
+    if (NM > 1) {
+      const df32 wx = df_prod(w, ex), wy = df_prod(w, ey);
+      const df32 wxx = df_prod(wx, ex), wxy = df_prod(wx, ey), wyy = df_prod(wy, ey);
+      df_acc(S[1], wx);
+      df_acc(S[2], wy);
+      df_acc(S[3], wxx);
+      df_acc(S[4], wxy);
+      df_acc(S[5], wyy);
+      if (NM > 6) {
+        const df32 wxxx = df_prod(wxx, ex), wxxy = df_prod(wxx, ey);
+        const df32 wxyy = df_prod(wyy, ex), wyyy = df_prod(wyy, ey);
+        df_acc(S[6], wxxx);
+        df_acc(S[7], wxxy);
+        df_acc(S[8], wxyy);
+        df_acc(S[9], wyyy);
+        df_acc(S[10], df_prod(wxxx, ex));
+        df_acc(S[11], df_prod(wxxx, ey));
+        df_acc(S[12], df_prod(wxxy, ey));
+        df_acc(S[13], df_prod(wxyy, ey));
+        df_acc(S[14], df_prod(wyyy, ey));
+      }
+    }
+  });
+#pragma unroll
+  for (int k = 0; k < NM; ++k) store(k, df_warp_sum(S[k]));
+  return nnear;
+}
+
+// Field values (and bands, status) of one pixel whose policy chose degree
+// `used` >= 0, a warp per pixel: value_d = sum_i phi_i f_id with the shape
+// functions phi_i = w_i z . b_c(x_i) in the centroid frame fr (centre hi,
+// lo in x and y; 1/sigma), z as double-float.
+template <int DEG, int WK>
+__device__ __forceinline__ void pixel_values(const KParams &p, int id, int used, const Ranges &R, float mhat,
+                                             float pxh, float pxl, float pyh, float pyl, const df32 (&zd)[6],
+                                             const float (&fr)[5], int lane, int *ri, float4 *rx,
+                                             const float2 *s_tab) {
+  const size_t plane = (size_t)p.W * p.H;
+  float *field = (float *)p.field;
+  const int ku = n_terms(used);
+  const float cxh = fr[0], cxl = fr[1], cyh = fr[2], cyl = fr[3], isg = fr[4];
+  for (int d0 = 0; d0 < p.D; d0 += 32 * kDL) {
+    df32 acc[kDL];
+#pragma unroll
+    for (int t = 0; t < kDL; ++t) acc[t] = {0.f, 0.f};
+    int unused;
+    for_near<WK>(p, R, pxh, pxl, pyh, pyl, mhat, lane, ri, rx, &unused, [&](bool valid, int i, df32 ex, df32 ey) {
+      df32 phi = {0.f, 0.f};
+      if (valid) {
+        const df32 w = pair_wdf<WK>(ex, ey, mhat, p.alpha, s_tab);
+        df32 zb = zd[0];
+        if (ku > 1) {
+          const df32 cxe = df_mul_f(df_diff(ex.hi, ex.lo, cxh, cxl), isg);
+          const df32 cye = df_mul_f(df_diff(ey.hi, ey.lo, cyh, cyl), isg);
+          zb = df_add(zb, df_add(df_mul(zd[1], cxe), df_mul(zd[2], cye)));
+          if (ku > 3) {
+            const df32 t = df_add(df_mul(zd[3], cxe), df_mul(zd[4], cye));
+            zb = df_add(zb, df_add(df_mul(t, cxe), df_mul(df_mul(zd[5], cye), cye)));
+          }
+        }
+        phi = df_mul(w, zb);
+      }
+      const int nb = __popc(__ballot_sync(0xffffffffu, valid));
+#pragma unroll 4
+      for (int jj = 0; jj < nb; ++jj) {
+        const df32 ph = {__shfl_sync(0xffffffffu, phi.hi, jj), __shfl_sync(0xffffffffu, phi.lo, jj)};
+        const int ij = __shfl_sync(0xffffffffu, i, jj);
+        const float *fp = p.FR32 + (size_t)ij * p.D + d0 + lane;
+#pragma unroll
+        for (int t = 0; t < kDL; ++t)
+          if (d0 + lane + 32 * t < p.D) df_acc(acc[t], df_prod_f(ph, fp[32 * t]));
+      }
+    });
+#pragma unroll
+    for (int t = 0; t < kDL; ++t) {
+      const int d = d0 + lane + 32 * t;
+      if (d < p.D) {
+        // fcen + fscl (hi + lo) in double-float, rounded to float at the
+        // end (FP32 arithmetic: per-lane FP64 here cost a warp
+        // instruction per pixel and dimension sweep)
+        const df32 sv = df_prod_f(df_two_sum(acc[t].hi, acc[t].lo), p.fscl32[d]);
+        const df32 fs = df_add({p.fcen32[d], 0.f}, sv);
+        const float f = fs.hi + fs.lo;
+        field[(size_t)d * plane + id] = f;
+        if (p.bands) p.bands[(size_t)d * plane + id] = band_of(f, p.lev32 + (size_t)d * p.L, p.L);
+      }
+    }
+  }
+  if (lane == 0 && p.status)
+    p.status[id] = (uint8_t)(used | MLS_ST_RECOMPUTED | (used < DEG ? MLS_ST_DEGRADED : 0));
+}
+
+// A pixel without a qualifying degree (no support): NaN and band 255.
+__device__ __forceinline__ void pixel_nosupport(const KParams &p, int id, int lane) {
+  const size_t plane = (size_t)p.W * p.H;
+  float *field = (float *)p.field;
+  for (int d = lane; d < p.D; d += 32) {
+    field[(size_t)d * plane + id] = __int_as_float(0x7fc00000);
+    if (p.bands) p.bands[(size_t)d * plane + id] = 255;
+  }
+  if (lane == 0 && p.status) p.status[id] = MLS_ST_NO_SUPPORT | MLS_ST_RECOMPUTED;
+}
+
+// Policy of one pixel (lane per pixel) from its double-float moments, in
+// scalar type T: degree used (-1: none) in bits 8.., bit 0 when the pixel
+// needs the FP64 kernel; z as double-float pairs and the centroid frame.
+template <int DEG, typename T>
+__device__ __forceinline__ int pixel_decide(const float *Sh, const float *Sl, long long count, double rcond_min,
+                                            float (&zh)[6], float (&zl)[6], float (&fr)[5]) {
+  T Sd[15], z[6], rmin;
+#pragma unroll
+  for (int k = 0; k < 15; ++k) tjoin(Sh[k], Sl[k], Sd[k]);
+  tfrom(rcond_min, rmin);
+  bool bad = false;
+  const int used = pixel_policy<DEG, T>(Sd, count, rmin, z, fr, &bad);
+#pragma unroll
+  for (int a = 0; a < 6; ++a) tsplit(z[a], zh[a], zl[a]);
+  return (bad ? 1 : 0) | ((used + 1) << 8);
+}
+
+// ---------------------------------------------------------------------------
+// Split hand-over: the list's first entries (up to the state capacity) in
+// four kernels, so that the warp-per-pixel phases run at the occupancy
+// their registers allow and wait on no block barrier, and the FP64 phases
+// run one lane per pixel over full warps:
+//   k_ho_setup    lane per entry: the pixel's setup
+//   k_ho_moments  warp per entry (claimed from a counter): moments
+//   k_ho_policy   lane per entry: FP64 degree policy and centroid solve
+//   k_ho_values   warp per entry: values, bands, status; FP64-tier list
+// The entries' state lives in global memory between the kernels.
+
+// State of one list entry between the split kernels (48 words).  The
+// moments (S, hi and lo interleaved) are replaced by the solution (zh[6],
+// zl[6], fr[5]) once the policy has read them.
+struct HoEntry {
+  float S[30];
+  int count, nnear, flags, id;
+  int cx0, cx1, cy0, cy1;
+  float mhat, pxh, pxl, pyh, pyl;
+  int pad[5];
+};
+static_assert(sizeof(HoEntry) == 192, "hand-over entry layout");
+
+// Entries the split kernels take: the list's first min(count, cap), when the
+// list holds at least `least` entries (shorter lists go to the fused kernel
+// whole: a block per chunk of them, with its FP64 policy overlapping the
+// other blocks' double-float phases, is faster there than four launches
+// with a policy kernel that occupies few warps).
+__device__ __forceinline__ int64_t split_count(const unsigned int *list_count, int64_t cap, int64_t least) {
+  const int64_t n = (int64_t)*list_count;
+  if (n < least) return 0;
+  return n < cap ? n : cap;
+}
+
+template <int WK>
+__global__ __launch_bounds__(128) void k_ho_setup(KParams p, const int *list, const unsigned int *list_count,
+                                                  int64_t cap, int64_t least, HoEntry *E) {
+  const int64_t n = split_count(list_count, cap, least);
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+    HoEntry &e = E[k];
+    const int id = (int)list_i(p, list[list_i(p, k)]);
+    Ranges R;
+    float mhat, pxh, pxl, pyh, pyl;
+    pixel_setup<WK>(p, id, R, mhat, pxh, pxl, pyh, pyl);
+    e.id = id;
+    e.cx0 = R.cx0;
+    e.cx1 = R.cx1;
+    e.cy0 = R.cy0;
+    e.cy1 = R.cy1;
+    e.mhat = mhat;
+    e.pxh = pxh;
+    e.pxl = pxl;
+    e.pyh = pyh;
+    e.pyl = pyl;
+  }
+}
+
+__device__ __forceinline__ Ranges entry_ranges(const KParams &p, const HoEntry &e, int wk) {
+  Ranges R;
+  R.cx0 = e.cx0;
+  R.cx1 = e.cx1;
+  R.cy0 = e.cy0;
+  R.cy1 = e.cy1;
+  R.all_n = (wk == MLS_W_INVDIST) ? (int)p.n : 0;
+  return R;
+}
+
+// warps take entries one at a time from *claim
+__device__ __forceinline__ int64_t claim_next(unsigned int *claim, int lane) {
+  unsigned int k = 0;
+  if (lane == 0) k = atomicAdd(claim, 1u);
+  return (int64_t)__shfl_sync(0xffffffffu, k, 0);
+}
+
+template <int DEG, int WK>
+__global__ __launch_bounds__(kWarps * 32, 8) void k_ho_moments(KParams p, const unsigned int *list_count,
+                                                               int64_t cap, int64_t least, HoEntry *E,
+                                                               unsigned int *claim) {
+  __shared__ int s_ri[kWarps][kRing];
+  __shared__ float4 s_rx[kWarps][kRing];
+  __shared__ float2 s_tab[64];
+  const int64_t n = split_count(list_count, cap, least);
+  if (n == 0) return;   // uniform over the grid: a short list goes to the fused kernel
+  if (WK == MLS_W_GAUSS) df_exp_table_init(s_tab);
+  __syncthreads();
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  for (int64_t k = claim_next(claim, lane); k < n; k = claim_next(claim, lane)) {
+    HoEntry &e = E[k];
+    const Ranges R = entry_ranges(p, e, WK);
+    int coincident = 0;
+    const float mhat = e.mhat;
+    const int nnear = pixel_moments<DEG, WK>(p, R, mhat, e.pxh, e.pxl, e.pyh, e.pyl, lane, s_ri[wib], s_rx[wib], s_tab,
+                                             &coincident, [&](int q, df32 t) {
+      if (lane == q) {
+        e.S[2 * q] = t.hi;
+        e.S[2 * q + 1] = t.lo;
+      }
+    });
+    if (lane == 0) {
+      e.count = (WK == MLS_W_WENDLAND || p.trunc > 0.0) ? nnear : (int)(p.n < (1 << 30) ? p.n : (1 << 30));
+      e.nnear = nnear;
+      // inverse distance: a coincident point (or a zero stabiliser) goes to
+      // the FP64 kernel, which gives the pixel that point's value
+      e.flags = (WK == MLS_W_INVDIST && (coincident || !(mhat > 0.f))) ? 1 : 0;
+    }
+  }
+}
+
+// The policy is a long chain of dependent double-float operations per lane:
+// a short list is spread over more warps (fewer lanes each, down to 4) so
+// that the warp schedulers have other warps to issue while one waits.
+template <int DEG>
+__global__ __launch_bounds__(32) void k_ho_policy(KParams p, const unsigned int *list_count, int64_t cap,
+                                                   int64_t least, HoEntry *E) {
+  constexpr int NM = n_moments(DEG);
+  const int64_t n = split_count(list_count, cap, least);
+  const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+  const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  int lpw = 32;
+  while (lpw > 4 && (n + lpw - 1) / lpw < nw) lpw >>= 1;
+  for (int64_t base = gw * lpw; base < n; base += nw * lpw) {
+    const int64_t k = base + lane;
+    if (lane >= lpw || k >= n) continue;
+    HoEntry &e = E[k];
+    if (e.flags & 1) continue;
+    float Sh[15], Sl[15];
+#pragma unroll
+    for (int q = 0; q < 15; ++q) {
+      Sh[q] = q < NM ? e.S[2 * q] : 0.f;
+      Sl[q] = q < NM ? e.S[2 * q + 1] : 0.f;
+    }
+    float zh[6], zl[6], fr[5];
+    const int flags = pixel_decide<DEG, dd>(Sh, Sl, e.count, p.rcond_min, zh, zl, fr);
+#pragma unroll
+    for (int a = 0; a < 6; ++a) {
+      e.S[a] = zh[a];
+      e.S[6 + a] = zl[a];
+    }
+#pragma unroll
+    for (int a = 0; a < 5; ++a) e.S[12 + a] = fr[a];
+    e.flags = flags;
+  }
+}
+
+template <int DEG, int WK>
+__global__ __launch_bounds__(kWarps * 32, 8) void k_ho_values(KParams p, const unsigned int *list_count,
+                                                              int64_t cap, int64_t least, HoEntry *E,
+                                                              unsigned int *claim, int *list2,
+                                                              unsigned int *list2_count) {
+  __shared__ int s_ri[kWarps][kRing];
+  __shared__ float4 s_rx[kWarps][kRing];
+  __shared__ float2 s_tab[64];
+  const int64_t n = split_count(list_count, cap, least);
+  if (n == 0) return;   // uniform over the grid: a short list goes to the fused kernel
+  if (WK == MLS_W_GAUSS) df_exp_table_init(s_tab);
+  __syncthreads();
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  for (int64_t k = claim_next(claim, lane); k < n; k = claim_next(claim, lane)) {
+    const HoEntry &e = E[k];
+    const int id = e.id, flags = e.flags;
+    if (flags & 1) {
+      if (lane == 0) {
+        const unsigned int k2 = atomicAdd(list2_count, 1u);
+        list2[list_i(p, k2)] = id;
+      }
+      continue;
+    }
+    const int used = (flags >> 8) - 1;
+    if (used < 0) {
+      pixel_nosupport(p, id, lane);
+      continue;
+    }
+    df32 zd[6];
+#pragma unroll
+    for (int a = 0; a < 6; ++a) zd[a] = {e.S[a], e.S[6 + a]};
+    float fr[5];
+#pragma unroll
+    for (int a = 0; a < 5; ++a) fr[a] = e.S[12 + a];
+    pixel_values<DEG, WK>(p, id, used, entry_ranges(p, e, WK), e.mhat, e.pxh, e.pxl, e.pyh, e.pyl, zd, fr, lane,
+                          s_ri[wib], s_rx[wib], s_tab);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Fused hand-over of the list entries from `first` on (those past the split
+// kernels' state capacity): one block per chunk of up to 32 pixels, its
+// phases separated by block barriers with the chunk's state in shared memory.
 
 // Per-block state of a chunk of up to 32 pixels between its phases.
 struct ChunkSlot {
@@ -415,9 +856,9 @@ struct ChunkSlot {
 
 template <int DEG, int WK>
 __global__ __launch_bounds__(kWarps * 32, 4) void k_handover(KParams p, const int *list,
-                                                          const unsigned int *list_count, int64_t cap, int *list2,
+                                                          const unsigned int *list_count, int64_t split_cap,
+                                                          int64_t least, int64_t cap, int *list2,
                                                           unsigned int *list2_count) {
-  constexpr int NM = n_moments(DEG);
   __shared__ int s_ri[kWarps][kRing];
   __shared__ float4 s_rx[kWarps][kRing];
   __shared__ ChunkSlot s_chunk[32];
@@ -427,6 +868,11 @@ __global__ __launch_bounds__(kWarps * 32, 4) void k_handover(KParams p, const in
   // order of their near points (longest first), so the warps finish together
   __shared__ int s_next[2];
   __shared__ int s_order[32];
+  const int64_t total = (int64_t)*list_count < cap ? (int64_t)*list_count : cap;
+  const int64_t first = split_count(list_count, split_cap, least);   // taken by the split kernels
+  const int64_t npix = total - first;
+  if (npix <= 0) return;   // uniform over the grid: nothing past the split kernels
+  list += first;
   if (WK == MLS_W_GAUSS) df_exp_table_init(s_tab);
   if (threadIdx.x == 0) s_next[0] = s_next[1] = 0;
   __syncthreads();
@@ -438,7 +884,6 @@ __global__ __launch_bounds__(kWarps * 32, 4) void k_handover(KParams p, const in
   int *ri = s_ri[wib];
   float4 *rx = s_rx[wib];
   ChunkSlot *slots = s_chunk;
-  const int64_t npix = (int64_t)*list_count < cap ? (int64_t)*list_count : cap;
   // pixels per block chunk: up to 32 (one per lane of the policy warp), fewer
   // when there are too few pixels to give every block a full chunk.  The
   // block's warps share the moment and value phases (warp per pixel); one
@@ -447,40 +892,6 @@ __global__ __launch_bounds__(kWarps * 32, 4) void k_handover(KParams p, const in
   const int64_t per = (npix + gridDim.x - 1) / gridDim.x;
   const int csz = per >= 32 ? 32 : (per < 1 ? 1 : (int)per);
   const int64_t nchunks = (npix + csz - 1) / csz;
-  const size_t plane = (size_t)p.W * p.H;
-  const double inv_s = 1.0 / p.h;
-  float *field = (float *)p.field;
-
-  // everything pass 1 and pass 2 need about pixel `id`
-  auto setup = [&](int id, Ranges &R, float &mhat, float &pxh, float &pxl, float &pyh, float &pyl) {
-    const int u = id % p.W, v = id / p.W;
-    const double px = __dadd_rn(p.x0, __dmul_rn(__dadd_rn((double)u, 0.5), p.sx));
-    const double py = __dadd_rn(p.y0, __dmul_rn(__dadd_rn((double)v, 0.5), p.sy));
-    mhat = (WK == MLS_W_WENDLAND) ? 0.f : p.mstab[pix_i(p, (int64_t)v * (p.tiles_x * 16) + u)];
-    if (WK == MLS_W_INVDIST) {
-      R.all_n = (int)p.n;
-      R.cx0 = R.cx1 = R.cy0 = R.cy1 = 0;
-    } else {
-      // near radius: the support (Wendland), the box (truncated Gaussian), or
-      // r^2 <= m + kCut (Gaussian), widened by a relative 1e-5 against rounding
-      const double rad = (WK == MLS_W_WENDLAND ? 1.0
-                          : p.trunc > 0.0      ? p.trunc
-                                               : (double)sqrtf(fmaxf(mhat, 0.f) + kCut)) *
-                         p.h * (1.0 + 1e-5);
-      const double inv_cell = p.inv_cell;
-      R.all_n = 0;
-      R.cx0 = max((int)floor((px - rad - p.gx0) * inv_cell), 0);
-      R.cx1 = min((int)floor((px + rad - p.gx0) * inv_cell), p.gx - 1);
-      R.cy0 = max((int)floor((py - rad - p.gy0) * inv_cell), 0);
-      R.cy1 = min((int)floor((py + rad - p.gy0) * inv_cell), p.gy - 1);
-    }
-    // pixel position in the scaled frame as hi + lo
-    const double pxs64 = (px - p.ctr_x) * inv_s, pys64 = (py - p.ctr_y) * inv_s;
-    pxh = (float)pxs64;
-    pxl = (float)(pxs64 - (double)pxh);
-    pyh = (float)pys64;
-    pyl = (float)(pys64 - (double)pyh);
-  };
 
   for (int64_t ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
     // Neighbouring list entries are often neighbouring pixels of one tile,
@@ -490,9 +901,9 @@ __global__ __launch_bounds__(kWarps * 32, 4) void k_handover(KParams p, const in
     // chunks than blocks, the blocks balance over their several chunks, and
     // a chunk takes a contiguous run, whose pixels share near points in cache.
     const bool strided = nchunks <= (int64_t)gridDim.x;
-    const int64_t first = strided ? ch : ch * csz, step = strided ? nchunks : 1;
+    const int64_t firstk = strided ? ch : ch * csz, step = strided ? nchunks : 1;
     const int nq = strided ? (int)((npix - ch + nchunks - 1) / nchunks)
-                           : (int)((npix - first) < csz ? (npix - first) : csz);
+                           : (int)((npix - firstk) < csz ? (npix - firstk) : csz);
 
     // ---- phase 0 (lane per pixel): each pixel's setup, once.  Its FP64
     // arithmetic is warp-uniform per pixel; GB300 charges an FP64 warp
@@ -501,9 +912,9 @@ __global__ __launch_bounds__(kWarps * 32, 4) void k_handover(KParams p, const in
     // value phases)
     if (wib == wpol && lane < nq) {
       ChunkSlot &sl = slots[lane];
-      const int id = (int)list_i(p, list[list_i(p, first + (int64_t)lane * step)]);
+      const int id = (int)list_i(p, list[list_i(p, firstk + (int64_t)lane * step)]);
       sl.id = id;
-      setup(id, sl.R, sl.mhat, sl.pxh, sl.pxl, sl.pyh, sl.pyl);
+      pixel_setup<WK>(p, id, sl.R, sl.mhat, sl.pxh, sl.pxl, sl.pyh, sl.pyl);
     }
     __syncthreads();
 
@@ -513,57 +924,26 @@ __global__ __launch_bounds__(kWarps * 32, 4) void k_handover(KParams p, const in
       if (lane == 0) j = atomicAdd(&s_next[0], 1);
       j = __shfl_sync(0xffffffffu, j, 0);
       if (j >= nq) break;
-      const Ranges R = slots[j].R;
-      const float mhat = slots[j].mhat, pxh = slots[j].pxh, pxl = slots[j].pxl, pyh = slots[j].pyh,
-                  pyl = slots[j].pyl;
-      df32 S[NM];
-#pragma unroll
-      for (int k = 0; k < NM; ++k) S[k] = {0.f, 0.f};
+      ChunkSlot &sl = slots[j];
       int coincident = 0;
-      const int nnear = for_near<WK>(p, R, pxh, pxl, pyh, pyl, mhat, lane, ri, rx, &coincident,
-                                     [&](bool valid, int, df32 ex, df32 ey) {
-        if (!valid) return;
-        const df32 w = pair_wdf<WK>(ex, ey, mhat, p.alpha, s_tab);
-        df_acc(S[0], w);
-        if (NM > 1) {
-          const df32 wx = df_prod(w, ex), wy = df_prod(w, ey);
-          const df32 wxx = df_prod(wx, ex), wxy = df_prod(wx, ey), wyy = df_prod(wy, ey);
-          df_acc(S[1], wx);
-          df_acc(S[2], wy);
-          df_acc(S[3], wxx);
-          df_acc(S[4], wxy);
-          df_acc(S[5], wyy);
-          if (NM > 6) {
-            const df32 wxxx = df_prod(wxx, ex), wxxy = df_prod(wxx, ey);
-            const df32 wxyy = df_prod(wyy, ex), wyyy = df_prod(wyy, ey);
-            df_acc(S[6], wxxx);
-            df_acc(S[7], wxxy);
-            df_acc(S[8], wxyy);
-            df_acc(S[9], wyyy);
-            df_acc(S[10], df_prod(wxxx, ex));
-            df_acc(S[11], df_prod(wxxx, ey));
-            df_acc(S[12], df_prod(wxxy, ey));
-            df_acc(S[13], df_prod(wxyy, ey));
-            df_acc(S[14], df_prod(wyyy, ey));
-          }
+      const float mhat = sl.mhat;
+      const int nnear = pixel_moments<DEG, WK>(p, sl.R, mhat, sl.pxh, sl.pxl, sl.pyh, sl.pyl, lane, ri, rx, s_tab,
+                                               &coincident, [&](int q, df32 t) {
+        if (lane == q) {
+          sl.Sh[q] = t.hi;
+          sl.Sl[q] = t.lo;
         }
       });
-      // the sums as double-float (the policy lane forms the doubles)
-#pragma unroll
-      for (int k = 0; k < 15; ++k) {
-        df32 t = {0.f, 0.f};
-        if (k < NM) t = df_warp_sum(S[k]);
-        if (lane == k) {
-          slots[j].Sh[k] = t.hi;
-          slots[j].Sl[k] = t.lo;
-        }
+      if (lane < 15 && lane >= n_moments(DEG)) {
+        sl.Sh[lane] = 0.f;
+        sl.Sl[lane] = 0.f;
       }
       if (lane == 0) {
-        slots[j].count = (WK == MLS_W_WENDLAND || p.trunc > 0.0) ? nnear : p.n;
-        slots[j].nnear = nnear;
+        sl.count = (WK == MLS_W_WENDLAND || p.trunc > 0.0) ? nnear : p.n;
+        sl.nnear = nnear;
         // inverse distance: a coincident point (or a zero stabiliser) goes to
         // the FP64 kernel, which gives the pixel that point's value
-        slots[j].flags = (WK == MLS_W_INVDIST && (coincident || !(mhat > 0.f))) ? 1 : 0;
+        sl.flags = (WK == MLS_W_INVDIST && (coincident || !(mhat > 0.f))) ? 1 : 0;
       }
       __syncwarp();
     }
@@ -586,22 +966,7 @@ __global__ __launch_bounds__(kWarps * 32, 4) void k_handover(KParams p, const in
     }
     if (wib == wpol && lane < nq) {
       ChunkSlot &sl = slots[lane];
-      if (!(sl.flags & 1)) {
-        double Sd[15], z[6];
-        float fr[5];
-#pragma unroll
-        for (int k = 0; k < 15; ++k) Sd[k] = (double)sl.Sh[k] + (double)sl.Sl[k];
-        bool bad = false;
-        const int used = pixel_policy<DEG>(Sd, sl.count, p.rcond_min, z, fr, &bad);
-#pragma unroll
-        for (int a = 0; a < 6; ++a) {
-          sl.zh[a] = (float)z[a];
-          sl.zl[a] = (float)(z[a] - (double)sl.zh[a]);
-        }
-#pragma unroll
-        for (int a = 0; a < 5; ++a) sl.fr[a] = fr[a];
-        sl.flags = (bad ? 1 : 0) | ((used + 1) << 8);
-      }
+      if (!(sl.flags & 1)) sl.flags = pixel_decide<DEG, double>(sl.Sh, sl.Sl, sl.count, p.rcond_min, sl.zh, sl.zl, sl.fr);
     }
     __syncthreads();
 
@@ -623,95 +988,62 @@ __global__ __launch_bounds__(kWarps * 32, 4) void k_handover(KParams p, const in
       }
       const int used = (flags >> 8) - 1;
       if (used < 0) {
-        for (int d = lane; d < p.D; d += 32) {
-          field[(size_t)d * plane + id] = __int_as_float(0x7fc00000);
-          if (p.bands) p.bands[(size_t)d * plane + id] = 255;
-        }
-        if (lane == 0 && p.status) p.status[id] = MLS_ST_NO_SUPPORT | MLS_ST_RECOMPUTED;
+        pixel_nosupport(p, id, lane);
         continue;
       }
-      const Ranges R = slots[j].R;
-      const float mhat = slots[j].mhat, pxh = slots[j].pxh, pxl = slots[j].pxl, pyh = slots[j].pyh,
-                  pyl = slots[j].pyl;
-      const int ku = n_terms(used);
       df32 zd[6];
 #pragma unroll
-      for (int a = 0; a < 6; ++a) {
-        zd[a] = {slots[j].zh[a], slots[j].zl[a]};
-      }
-      const float cxh = slots[j].fr[0], cxl = slots[j].fr[1], cyh = slots[j].fr[2], cyl = slots[j].fr[3],
-                  isg = slots[j].fr[4];
-      for (int d0 = 0; d0 < p.D; d0 += 32 * kDL) {
-        df32 acc[kDL];
+      for (int a = 0; a < 6; ++a) zd[a] = {slots[j].zh[a], slots[j].zl[a]};
+      float fr[5];
 #pragma unroll
-        for (int t = 0; t < kDL; ++t) acc[t] = {0.f, 0.f};
-        int unused;
-        for_near<WK>(p, R, pxh, pxl, pyh, pyl, mhat, lane, ri, rx, &unused,
-                     [&](bool valid, int i, df32 ex, df32 ey) {
-          df32 phi = {0.f, 0.f};
-          if (valid) {
-            const df32 w = pair_wdf<WK>(ex, ey, mhat, p.alpha, s_tab);
-            df32 zb = zd[0];
-            if (ku > 1) {
-              const df32 cxe = df_mul_f(df_diff(ex.hi, ex.lo, cxh, cxl), isg);
-              const df32 cye = df_mul_f(df_diff(ey.hi, ey.lo, cyh, cyl), isg);
-              zb = df_add(zb, df_add(df_mul(zd[1], cxe), df_mul(zd[2], cye)));
-              if (ku > 3) {
-                const df32 t = df_add(df_mul(zd[3], cxe), df_mul(zd[4], cye));
-                zb = df_add(zb, df_add(df_mul(t, cxe), df_mul(df_mul(zd[5], cye), cye)));
-              }
-            }
-            phi = df_mul(w, zb);
-          }
-          const int nb = __popc(__ballot_sync(0xffffffffu, valid));
-#pragma unroll 4
-          for (int jj = 0; jj < nb; ++jj) {
-            const df32 ph = {__shfl_sync(0xffffffffu, phi.hi, jj), __shfl_sync(0xffffffffu, phi.lo, jj)};
-            const int ij = __shfl_sync(0xffffffffu, i, jj);
-            const float *fp = p.FR32 + (size_t)ij * p.D + d0 + lane;
-#pragma unroll
-            for (int t = 0; t < kDL; ++t)
-              if (d0 + lane + 32 * t < p.D) df_acc(acc[t], df_prod_f(ph, fp[32 * t]));
-          }
-        });
-#pragma unroll
-        for (int t = 0; t < kDL; ++t) {
-          const int d = d0 + lane + 32 * t;
-          if (d < p.D) {
-            // fcen + fscl (hi + lo) in double-float, rounded to float at the
-            // end (FP32 arithmetic: per-lane FP64 here cost a warp
-            // instruction per pixel and dimension sweep)
-            const df32 sv = df_prod_f(df_two_sum(acc[t].hi, acc[t].lo), p.fscl32[d]);
-            const df32 fs = df_add({p.fcen32[d], 0.f}, sv);
-            const float f = fs.hi + fs.lo;
-            field[(size_t)d * plane + id] = f;
-            if (p.bands) p.bands[(size_t)d * plane + id] = band_of(f, p.lev32 + (size_t)d * p.L, p.L);
-          }
-        }
-      }
-      if (lane == 0 && p.status)
-        p.status[id] = (uint8_t)(used | MLS_ST_RECOMPUTED | (used < DEG ? MLS_ST_DEGRADED : 0));
+      for (int a = 0; a < 5; ++a) fr[a] = slots[j].fr[a];
+      pixel_values<DEG, WK>(p, id, used, slots[j].R, slots[j].mhat, slots[j].pxh, slots[j].pxl, slots[j].pyh,
+                            slots[j].pyl, zd, fr, lane, ri, rx, s_tab);
     }
     __syncthreads();   // the slots are refilled by the next chunk
   }
 }
 
+template <int DEG, int WK>
+void launch_dw(const KParams &p, const int *list, const unsigned int *cnt, int64_t cap, int64_t split_cap,
+               int64_t least, void *state, unsigned int *claims, int *list2, unsigned int *cnt2, cudaStream_t st) {
+  const int64_t sc = state ? (split_cap < cap ? split_cap : cap) : 0;
+  if (sc > 0) {
+    HoEntry *E = (HoEntry *)state;
+    // one resident wave each: 4 blocks of 128 threads per SM for the setup,
+    // 8 for the warp phases (entries claimed dynamically), 16 one-warp
+    // blocks for the policy
+    k_ho_setup<WK><<<152 * 4, 128, 0, st>>>(p, list, cnt, sc, least, E);
+    k_ho_moments<DEG, WK><<<152 * 8, kWarps * 32, 0, st>>>(p, cnt, sc, least, E, claims);
+    k_ho_policy<DEG><<<152 * 16, 32, 0, st>>>(p, cnt, sc, least, E);
+    k_ho_values<DEG, WK><<<152 * 8, kWarps * 32, 0, st>>>(p, cnt, sc, least, E, claims + 1, list2, cnt2);
+  }
+  // lists shorter than `least`, and entries past the split kernels'
+  // capacity (one resident wave: 4 blocks of 4 warps per SM; every block
+  // returns at once when there are none)
+  k_handover<DEG, WK><<<152 * 4, kWarps * 32, 0, st>>>(p, list, cnt, sc, least, cap, list2, cnt2);
+}
+
 template <int WK>
-void launch_w(const KParams &p, const int *list, const unsigned int *cnt, int64_t cap, int *list2,
-              unsigned int *cnt2, cudaStream_t st) {
-  const int grid = 152 * 4;   // one resident wave (4 blocks of 4 warps per SM)
-  if (p.degree == 0) k_handover<0, WK><<<grid, kWarps * 32, 0, st>>>(p, list, cnt, cap, list2, cnt2);
-  else if (p.degree == 1) k_handover<1, WK><<<grid, kWarps * 32, 0, st>>>(p, list, cnt, cap, list2, cnt2);
-  else k_handover<2, WK><<<grid, kWarps * 32, 0, st>>>(p, list, cnt, cap, list2, cnt2);
+void launch_w(const KParams &p, const int *list, const unsigned int *cnt, int64_t cap, int64_t split_cap,
+              int64_t least, void *state, unsigned int *claims, int *list2, unsigned int *cnt2, cudaStream_t st) {
+  if (p.degree == 0) launch_dw<0, WK>(p, list, cnt, cap, split_cap, least, state, claims, list2, cnt2, st);
+  else if (p.degree == 1) launch_dw<1, WK>(p, list, cnt, cap, split_cap, least, state, claims, list2, cnt2, st);
+  else launch_dw<2, WK>(p, list, cnt, cap, split_cap, least, state, claims, list2, cnt2, st);
 }
 
 }  // namespace
 
-void launch_handover(const KParams &p, const int *list, const unsigned int *cnt, int64_t cap, int *list2,
-                     unsigned int *cnt2, cudaStream_t st) {
-  if (p.weight == MLS_W_GAUSS) launch_w<MLS_W_GAUSS>(p, list, cnt, cap, list2, cnt2, st);
-  else if (p.weight == MLS_W_WENDLAND) launch_w<MLS_W_WENDLAND>(p, list, cnt, cap, list2, cnt2, st);
-  else launch_w<MLS_W_INVDIST>(p, list, cnt, cap, list2, cnt2, st);
+size_t handover_entry_bytes() { return sizeof(HoEntry); }
+
+void launch_handover(const KParams &p, const int *list, const unsigned int *cnt, int64_t cap, int64_t split_cap,
+                     int64_t least, void *state, unsigned int *claims, int *list2, unsigned int *cnt2,
+                     cudaStream_t st) {
+  if (p.weight == MLS_W_GAUSS)
+    launch_w<MLS_W_GAUSS>(p, list, cnt, cap, split_cap, least, state, claims, list2, cnt2, st);
+  else if (p.weight == MLS_W_WENDLAND)
+    launch_w<MLS_W_WENDLAND>(p, list, cnt, cap, split_cap, least, state, claims, list2, cnt2, st);
+  else launch_w<MLS_W_INVDIST>(p, list, cnt, cap, split_cap, least, state, claims, list2, cnt2, st);
 }
 
 // Test hook: the double-float weight functions on given arguments.

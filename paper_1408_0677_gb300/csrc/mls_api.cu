@@ -39,10 +39,49 @@ static bool inject_nomem() {
   return e && atoi(e) != 0;
 }
 
+// Device memory of handles and render contexts comes from one stream-ordered
+// pool per device that keeps freed memory for reuse (release threshold at
+// its maximum).  A pool that gives memory back to the system at every
+// synchronisation (the default pool's behaviour) maps it again at the next
+// allocation, and a render's scratch of tens of MB then costs more host time
+// than its kernels take on the device.  The pool holds at most the largest
+// working set the process has had, until the process exits.
+constexpr int kPoolDevices = 64;
+static cudaMemPool_t g_pool[kPoolDevices];
+static std::mutex g_pool_mu;
+
+static cudaError_t pool_alloc(void **p, size_t bytes, cudaStream_t st) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kPoolDevices) return cudaMallocAsync(p, bytes, st);
+  cudaMemPool_t pool;
+  {
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    if (!g_pool[dev]) {
+      cudaMemPoolProps props;
+      memset(&props, 0, sizeof props);
+      props.allocType = cudaMemAllocationTypePinned;
+      props.location.type = cudaMemLocationTypeDevice;
+      props.location.id = dev;
+      cudaMemPool_t np;
+      if ((e = cudaMemPoolCreate(&np, &props)) != cudaSuccess) return e;
+      uint64_t keep = UINT64_MAX;
+      if ((e = cudaMemPoolSetAttribute(np, cudaMemPoolAttrReleaseThreshold, &keep)) != cudaSuccess) {
+        cudaMemPoolDestroy(np);
+        return e;
+      }
+      g_pool[dev] = np;
+    }
+    pool = g_pool[dev];
+  }
+  return cudaMallocFromPoolAsync(p, bytes, pool, st);
+}
+
 mls_status dev_alloc(mls_handle *h, void **p, size_t bytes, cudaStream_t st) {
   *p = nullptr;
   if (inject_nomem()) return fail(MLS_E_NOMEM, "device allocation failed (MLS_INJECT_NOMEM)");
-  cudaError_t e = cudaMallocAsync(p, bytes ? bytes : 16, st);
+  cudaError_t e = pool_alloc(p, bytes ? bytes : 16, st);
   if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync");
   h->owned.push_back(*p);
   return MLS_OK;
@@ -51,7 +90,7 @@ mls_status dev_alloc(mls_handle *h, void **p, size_t bytes, cudaStream_t st) {
 static mls_status ctx_alloc(RenderCtx *c, void **p, size_t bytes, cudaStream_t st) {
   *p = nullptr;
   if (inject_nomem()) return fail(MLS_E_NOMEM, "device allocation failed (MLS_INJECT_NOMEM)");
-  cudaError_t e = cudaMallocAsync(p, bytes ? bytes : 16, st);
+  cudaError_t e = pool_alloc(p, bytes ? bytes : 16, st);
   if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync");
   c->owned.push_back(*p);
   return MLS_OK;
@@ -112,7 +151,8 @@ size_t scratch_bytes_for(int W, int H) {
   const size_t padded = (size_t)tx * kTile * ty * kTile;
   const size_t ntile = (size_t)tx * ty;
   return 256 + padded * sizeof(float) + padded * sizeof(int) + 2 * (size_t)W * H * sizeof(int) +
-         3 * ntile * sizeof(float) + 4 * ntile * sizeof(int) + 256;
+         3 * ntile * sizeof(float) + 4 * ntile * sizeof(int) + 256 +
+         (size_t)handover_split_cap((int64_t)W * H) * handover_entry_bytes();
 }
 
 // Grow a render context's scratch to fit a view.
@@ -143,6 +183,11 @@ static mls_status ensure_scratch(RenderCtx *c, int W, int H, cudaStream_t st) {
   c->tile_mark = (int *)(c->tcen + 2 * ntile);
   c->retry_tiles = c->tile_mark + 2 * ntile;   // both indexed by half tile
   c->tmax = (float *)(c->retry_tiles + 2 * ntile);
+  c->ho_claims = (unsigned int *)(b + 32);  // in the header zeroed before every render
+  // the split hand-over's entries, 256-byte aligned past the per-tile arrays
+  const size_t ho_off = ((size_t)((char *)(c->tmax + ntile) - b) + 255) / 256 * 256;
+  c->ho_state = b + ho_off;
+  c->ho_cap = handover_split_cap((int64_t)W * H);
   return MLS_OK;
 }
 
@@ -628,7 +673,10 @@ static mls_status render_enqueue(mls_handle *h, RenderCtx *c, const mlsk::KParam
     launches += 2;
     // pixels handed over by the reduced-precision path: centroid-frame
     // recompute, and the pure FP64 kernel for what is left
-    launch_handover(p, c->relist, c->counters, (int64_t)plane, c->relist2, c->counters + 1, st);
+    const int64_t split_cap = h->ho_cap_limit >= 0 && h->ho_cap_limit < c->ho_cap ? h->ho_cap_limit : c->ho_cap;
+    const int64_t least = h->ho_least >= 0 ? h->ho_least : kHandoverSplitLeast;
+    launch_handover(p, c->relist, c->counters, (int64_t)plane, split_cap, least, c->ho_state, c->ho_claims,
+                    c->relist2, c->counters + 1, st);
     mlsk::KParams q = p;
     q.list = c->relist2;
     q.list_count = c->counters + 1;
@@ -762,6 +810,14 @@ mls_status mls_sync(mls_handle *h, double timeout_s, mls_stats *stats) {
 int mls_debug_operand_cut(mls_handle *h, int32_t on) {
   if (!h) return fail(MLS_E_INVAL, "handle is NULL");
   h->operand_cut = on != 0;
+  return MLS_OK;
+}
+
+int mls_debug_handover_split(mls_handle *h, int64_t cap, int64_t least) {
+  if (!h) return fail(MLS_E_INVAL, "handle is NULL");
+  if (cap < -1 || least < -1) return fail(MLS_E_INVAL, "cap and least must be -1 or >= 0");
+  h->ho_cap_limit = cap;
+  h->ho_least = least;
   return MLS_OK;
 }
 

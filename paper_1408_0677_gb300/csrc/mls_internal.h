@@ -48,6 +48,9 @@ struct RenderCtx {
   int *relist2 = nullptr;            // pixels the hand-over path passes to FP64
   float *tcen = nullptr;             // per-tile moment frame centres
   unsigned int *counters = nullptr;  // [0] recompute count, [1] FP64 count, [2] retried half tiles
+  unsigned int *ho_claims = nullptr; // [0], [1]: entries claimed by the split hand-over's warp kernels
+  void *ho_state = nullptr;          // per-entry state of the split hand-over
+  int64_t ho_cap = 0;                // its capacity in entries
   int *tile_mark = nullptr;          // per half tile: queued for the split-weight pass
   int *retry_tiles = nullptr;
   float *tmax = nullptr;             // per-tile largest stabiliser (Gaussian)
@@ -80,6 +83,8 @@ struct mls_handle {
   int32_t f32_shape = 0;   // FP32 kernel block shape (the batch autotuner may change it)
   bool timed = false;
   bool operand_cut = true;           // reduced-precision Gaussian: skip pairs whose weight rounds to zero
+  int64_t ho_cap_limit = -1;         // test hooks: split hand-over capacity limit (-1: none)
+  int64_t ho_least = -1;             // and shortest list it takes (-1: kHandoverSplitLeast)
 };
 
 namespace mlsi {
@@ -96,8 +101,25 @@ void launch_bands(const mlsk::KParams &p, bool fp64, cudaStream_t st);
 // rigid / mean-displacement mappings (KParams.variant), FP64 or FP32
 void launch_variant(const mlsk::KParams &p, bool fp64, cudaStream_t st);
 // handover.cu: ill-conditioned pixels of the reduced-precision renders
-void launch_handover(const mlsk::KParams &p, const int *list, const unsigned int *cnt, int64_t cap, int *list2,
+// (a list of at least `least` entries: its first min(count, split_cap)
+// entries through four kernels whose per-entry state, handover_entry_bytes()
+// each, is at `state`, with two zeroed claim counters at `claims`; shorter
+// lists and the rest through one fused kernel)
+void launch_handover(const mlsk::KParams &p, const int *list, const unsigned int *cnt, int64_t cap,
+                     int64_t split_cap, int64_t least, void *state, unsigned int *claims, int *list2,
                      unsigned int *cnt2, cudaStream_t st);
+// the shortest list the split kernels take: one chunk of 32 pixels for each
+// of the fused kernel's 608 blocks (below it the fused kernel is faster)
+constexpr int64_t kHandoverSplitLeast = 608 * 32;
+size_t handover_entry_bytes();
+// state capacity of the split hand-over kernels for a plane of `plane`
+// pixels: an eighth of the plane (at least 1024 entries, at most 2^19)
+inline int64_t handover_split_cap(int64_t plane) {
+  int64_t c = plane >> 3;
+  if (c < 1024) c = 1024;
+  if (c > (1 << 19)) c = 1 << 19;
+  return c < plane ? c : plane;
+}
 // tc.cu
 mls_status launch_tc(const mlsk::KParams &p, int fp16, int wsplit, cudaStream_t st, int *nlaunch);
 int tc_dims_per_pass(int D, int degree);

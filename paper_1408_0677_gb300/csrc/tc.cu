@@ -287,6 +287,10 @@ __device__ __forceinline__ float2 wendland_weight2(uint64_t t2) {
 struct TileGeo {
   float col[16], row[16];
   int cr[4];                // cx0, cx1, cy0, cy1
+  // trimming of the cell rows to the reach of the tile's pixels (the tile's
+  // pixel-centre extent and the reach, in cells relative to (cx0, cy0))
+  float tx0, tx1, ty0, ty1, rc;
+  int trim;
 };
 
 __device__ __forceinline__ bool ranges_all(const KParams &p) {
@@ -312,6 +316,28 @@ __device__ void tile_geometry(const KParams &p, int u0, int v0, int hgt, float c
     const int c = (int)floor((e - g0) * p.inv_cell);   // the binning's expression
     g->cr[lane] = upper ? min(c, ng - 1) : max(c, 0);
   }
+  __syncwarp();
+  if (lane == 0) {
+    // The points within reach of some pixel of the tile lie in the tile's
+    // pixel-centre rectangle widened by the disc of radius r (the box of the
+    // truncated Gaussian widens it to a rectangle: no trimming there).  A
+    // cell row at distance dy from the rectangle needs only the columns
+    // within sqrt(r^2 - dy^2) of it; the other cells hold points whose
+    // weight is zero at every pixel of the tile.
+    g->trim = (!ranges_all(p) && !p.trunc_on) ? 1 : 0;
+    if (g->trim) {
+      const float rs = p.weight == MLS_W_WENDLAND ? 1.f
+                                                  : sqrtf(p.tmax[tile_i(p, (v0 >> 4) * p.tiles_x + (u0 >> 4))] + p.gcut);
+      const double rad = p.h * (double)rs * (1.0 + 1e-5);
+      const double xa = p.x0 + (u0 + 0.5) * p.sx, xb = p.x0 + (u0 + 15 + 0.5) * p.sx;
+      const double ya = p.y0 + (v0 + 0.5) * p.sy, yb = p.y0 + (v0 + hgt - 1 + 0.5) * p.sy;
+      g->tx0 = (float)((fmin(xa, xb) - p.gx0) * p.inv_cell - g->cr[0]);
+      g->tx1 = (float)((fmax(xa, xb) - p.gx0) * p.inv_cell - g->cr[0]);
+      g->ty0 = (float)((fmin(ya, yb) - p.gy0) * p.inv_cell - g->cr[2]);
+      g->ty1 = (float)((fmax(ya, yb) - p.gy0) * p.inv_cell - g->cr[2]);
+      g->rc = (float)(rad * p.inv_cell);
+    }
+  }
 }
 
 // The 8-point blocks of the visited ranges, packed densely into stages of 8
@@ -331,7 +357,9 @@ struct Slot {
 // 8 kt + q as the last row k with S_k <= 8 kt + q (a ballot per slot) and
 // forms its slot from that row's range, so no thread walks slot by slot.
 struct PackW {
-  int cx0, cx1, cy1;
+  int cx0, cx1, cy0, cy1;
+  bool trim;                    // rows trimmed to the reach (TileGeo)
+  float tx0, tx1, ty0, ty1, rc;
   int rnext;          // first row not yet loaded
   int W0, T;          // global slots [W0, T) belong to the loaded window
   int J;              // first global slot of the next stage
@@ -344,8 +372,26 @@ __device__ __forceinline__ void packw_load(const KParams &p, PackW &w) {
   const int r = w.rnext + lane;
   w.rlo = w.rhi = 0;
   if (r <= w.cy1) {
-    w.rlo = cell_at(p, (int64_t)r * p.gx + w.cx0);
-    w.rhi = cell_at(p, (int64_t)r * p.gx + w.cx1 + 1);
+    int c0 = w.cx0, c1 = w.cx1;
+    if (w.trim) {
+      // the row's distance from the tile's rectangle and the columns within
+      // reach, widened by 0.01 cell against the FP32 rounding of the
+      // (small, tile-relative) coordinates
+      const float rr = (float)(r - w.cy0);
+      const float dy = fmaxf(0.f, fmaxf(rr - w.ty1, w.ty0 - (rr + 1.f)));
+      const float h2 = w.rc * w.rc - dy * dy;
+      const float hw = sqrtf(fmaxf(h2, 0.f)) + 0.01f;
+      if (dy > w.rc + 0.01f) {
+        c1 = c0 - 1;   // no point of the row is within reach
+      } else {
+        c0 = w.cx0 + max(0, (int)floorf(w.tx0 - hw));
+        c1 = w.cx0 + min(w.cx1 - w.cx0, (int)floorf(w.tx1 + hw));
+      }
+    }
+    if (c0 <= c1) {
+      w.rlo = cell_at(p, (int64_t)r * p.gx + c0);
+      w.rhi = cell_at(p, (int64_t)r * p.gx + c1 + 1);
+    }
   }
   const int nb = (w.rhi > w.rlo) ? ((w.rhi - 1) >> 3) - (w.rlo >> 3) + 1 : 0;
   int inc = nb;   // inclusive prefix sum over the lanes
@@ -365,7 +411,9 @@ __device__ __forceinline__ void packw_init(const KParams &p, const TileGeo *g, P
   w.J = 0;
   w.W0 = 0;
   w.rlo = w.rhi = w.S = 0;
-  w.cx0 = w.cx1 = w.cy1 = 0;
+  w.cx0 = w.cx1 = w.cy0 = w.cy1 = 0;
+  w.trim = false;
+  w.tx0 = w.tx1 = w.ty0 = w.ty1 = w.rc = 0.f;
   if (w.all) {
     w.T = (int)((p.n + 7) >> 3);   // blocks of [0, n)
     w.rnext = 1;
@@ -374,8 +422,15 @@ __device__ __forceinline__ void packw_init(const KParams &p, const TileGeo *g, P
   }
   w.cx0 = g->cr[0];
   w.cx1 = g->cr[1];
+  w.cy0 = g->cr[2];
   w.cy1 = g->cr[3];
   w.rnext = g->cr[2];
+  w.trim = g->trim != 0;
+  w.tx0 = g->tx0;
+  w.tx1 = g->tx1;
+  w.ty0 = g->ty0;
+  w.ty1 = g->ty1;
+  w.rc = g->rc;
   w.T = 0;
   if (w.cx0 > w.cx1) w.rnext = w.cy1 + 1;   // no cells: nothing to visit
 }

@@ -65,7 +65,7 @@ def allowance(wl, ref, precision):
     return tol + b_or
 
 
-def gpu_render(wl, precision, device_inputs=True, levels=True, operand_cut=True, **kw):
+def gpu_render(wl, precision, device_inputs=True, levels=True, operand_cut=True, handover_split=None, **kw):
     import ctypes
 
     import torch
@@ -79,6 +79,9 @@ def gpu_render(wl, precision, device_inputs=True, levels=True, operand_cut=True,
                  support=wl.trunc, **kw)
     if not operand_cut:
         assert _abi.load().mls_debug_operand_cut(ctypes.c_void_p(r.handle), 0) == _abi.MLS_OK
+    if handover_split is not None:
+        cap, least = handover_split
+        assert _abi.load().mls_debug_handover_split(ctypes.c_void_p(r.handle), int(cap), int(least)) == _abi.MLS_OK
     out = r.render(wl.W, wl.H, view=wl.view, levels=wl.levels if levels else None)
     stats = r.sync()
     res = {k: (v.cpu().numpy() if v is not None else None) for k, v in out.items()}
