@@ -192,9 +192,22 @@ __device__ __forceinline__ void pre_window(const KParams &p, int u0, int v0, dou
 // scanned exactly.  The frame (it only conditions the fit) is the Gaussian-
 // weighted centroid, around the tile centre, of the points in the cells within
 // 4 h of the tile (weights below e^-16 of the largest are left out).
+// The index ranges [a, e) of the cell rows d0 .. d0 + nr - 1 of a window
+// (columns c0 .. c1), fetched by the first nr threads at once (one round
+// trip for the rows instead of one per row); the caller synchronises.
+__device__ __forceinline__ void pre_rows(const KParams &p, int c0, int c1, int d0, int nr, int *ra, int *re) {
+  const int t = threadIdx.x;
+  if (t < nr) {
+    const int64_t row = (int64_t)(d0 + t) * p.gx;
+    ra[t] = cell_at(p, row + c0);
+    re[t] = cell_at(p, row + c1 + 1);
+  }
+}
+
 __global__ __launch_bounds__(256) void k_prepass_min_cells(KParams p) {
   __shared__ float red[8];
   __shared__ float cx[256], cy[256];
+  __shared__ int ra[256], re[256];
   __shared__ PreGeo G;
   const int t = threadIdx.x;
   const int u0 = blockIdx.x * 16, v0 = blockIdx.y * 16;
@@ -210,14 +223,18 @@ __global__ __launch_bounds__(256) void k_prepass_min_cells(KParams p) {
     pre_window(p, u0, v0, r, &G);
     __syncthreads();
     const int c0 = G.win[0], c1 = G.win[1], d0 = G.win[2], d1 = G.win[3];
-    for (int row = d0; row <= d1 && c0 <= c1; ++row) {
-      const int a = cell_at(p, (int64_t)row * p.gx + c0), e = cell_at(p, (int64_t)row * p.gx + c1 + 1);
-      for (int i = a + t; i < e; i += 256) {
-        const float x = p.xs[i], y = p.ys[i];
-        const float fx = fmaxf(fabsf(x - X0), fabsf(x - X1));
-        const float fy = fmaxf(fabsf(y - Y0), fabsf(y - Y1));
-        b = fminf(b, fx * fx + fy * fy);
-      }
+    for (int rb = d0; rb <= d1 && c0 <= c1; rb += 256) {
+      const int nr = min(256, d1 - rb + 1);
+      __syncthreads();
+      pre_rows(p, c0, c1, rb, nr, ra, re);
+      __syncthreads();
+      for (int k = 0; k < nr; ++k)
+        for (int i = ra[k] + t; i < re[k]; i += 256) {
+          const float x = p.xs[i], y = p.ys[i];
+          const float fx = fmaxf(fabsf(x - X0), fabsf(x - X1));
+          const float fy = fmaxf(fabsf(y - Y0), fabsf(y - Y1));
+          b = fminf(b, fx * fx + fy * fy);
+        }
     }
     if (block_min(b, red) < FLT_MAX) break;   // uniform: every thread sees the same minimum
     r *= 2.0;
@@ -229,19 +246,25 @@ __global__ __launch_bounds__(256) void k_prepass_min_cells(KParams p) {
   __syncthreads();
   int c0 = G.win[0], c1 = G.win[1], d0 = G.win[2], d1 = G.win[3];
   float m = FLT_MAX;
-  for (int row = d0; row <= d1 && c0 <= c1; ++row) {
-    const int a = cell_at(p, (int64_t)row * p.gx + c0), e = cell_at(p, (int64_t)row * p.gx + c1 + 1);
-    for (int base = a; base < e; base += 256) {
-      __syncthreads();
-      if (base + t < e) {
-        cx[t] = p.xs[base + t];
-        cy[t] = p.ys[base + t];
-      }
-      __syncthreads();
-      const int c = min(256, e - base);
-      for (int k = 0; k < c; ++k) {
-        const float dx = cx[k] - px, dy = cy[k] - py;
-        m = fminf(m, dx * dx + dy * dy);
+  for (int rb = d0; rb <= d1 && c0 <= c1; rb += 256) {
+    const int nr = min(256, d1 - rb + 1);
+    __syncthreads();
+    pre_rows(p, c0, c1, rb, nr, ra, re);
+    __syncthreads();
+    for (int k = 0; k < nr; ++k) {
+      const int a = ra[k], e = re[k];
+      for (int base = a; base < e; base += 256) {
+        __syncthreads();
+        if (base + t < e) {
+          cx[t] = p.xs[base + t];
+          cy[t] = p.ys[base + t];
+        }
+        __syncthreads();
+        const int c = min(256, e - base);
+        for (int q = 0; q < c; ++q) {
+          const float dx = cx[q] - px, dy = cy[q] - py;
+          m = fminf(m, dx * dx + dy * dy);
+        }
       }
     }
   }
@@ -249,36 +272,45 @@ __global__ __launch_bounds__(256) void k_prepass_min_cells(KParams p) {
   const_cast<float *>(p.mstab)[(size_t)(v0 + (t >> 4)) * stride + u0 + (t & 15)] = m;
   const float mx = block_max(m, red);
   if (t == 0) const_cast<float *>(p.tmax)[blockIdx.y * p.tiles_x + blockIdx.x] = mx;
-  // 3) frame: Gaussian-weighted centroid of the points within 4 h of the tile
+  // 3) frame: Gaussian-weighted centroid of the points within 4 h of the
+  // tile, in one pass: each thread keeps the sums relative to the smallest
+  // squared distance it has seen so far (rescaling them when a nearer point
+  // comes), and the block combines them relative to the overall smallest
   const float Cx = G.col[8] - 0.5f * (G.col[8] - G.col[7]);
   const float Cy = G.row[8] - 0.5f * (G.row[8] - G.row[7]);
+  constexpr float kL2e = 1.4426950408889634f;
   __syncthreads();
   pre_window(p, u0, v0, 0.0, &G, bound, 4.0 * p.h);
   __syncthreads();
   c0 = G.win[0]; c1 = G.win[1]; d0 = G.win[2]; d1 = G.win[3];
-  float mc = FLT_MAX;
-  for (int row = d0; row <= d1 && c0 <= c1; ++row) {
-    const int a = cell_at(p, (int64_t)row * p.gx + c0), e = cell_at(p, (int64_t)row * p.gx + c1 + 1);
-    for (int i = a + t; i < e; i += 256) {
-      const float dx = p.xs[i] - Cx, dy = p.ys[i] - Cy;
-      mc = fminf(mc, dx * dx + dy * dy);
-    }
+  float ml = FLT_MAX, sw = 0.f, swx = 0.f, swy = 0.f;
+  for (int rb = d0; rb <= d1 && c0 <= c1; rb += 256) {
+    const int nr = min(256, d1 - rb + 1);
+    __syncthreads();
+    pre_rows(p, c0, c1, rb, nr, ra, re);
+    __syncthreads();
+    for (int k = 0; k < nr; ++k)
+      for (int i = ra[k] + t; i < re[k]; i += 256) {
+        const float dx = p.xs[i] - Cx, dy = p.ys[i] - Cy;
+        const float d2 = dx * dx + dy * dy;
+        if (d2 < ml) {
+          const float sc = (ml == FLT_MAX) ? 0.f : exp2f((d2 - ml) * kL2e);
+          sw *= sc;
+          swx *= sc;
+          swy *= sc;
+          ml = d2;
+        }
+        const float w = exp2f((ml - d2) * kL2e);
+        sw += w;
+        swx = fmaf(w, dx, swx);
+        swy = fmaf(w, dy, swy);
+      }
   }
-  mc = block_min(mc, red);
-  float sw = 0.f, swx = 0.f, swy = 0.f;
-  for (int row = d0; row <= d1 && c0 <= c1; ++row) {
-    const int a = cell_at(p, (int64_t)row * p.gx + c0), e = cell_at(p, (int64_t)row * p.gx + c1 + 1);
-    for (int i = a + t; i < e; i += 256) {
-      const float dx = p.xs[i] - Cx, dy = p.ys[i] - Cy;
-      const float w = exp2f((mc - (dx * dx + dy * dy)) * 1.4426950408889634f);
-      sw += w;
-      swx = fmaf(w, dx, swx);
-      swy = fmaf(w, dy, swy);
-    }
-  }
-  sw = block_sum(sw, red);
-  swx = block_sum(swx, red);
-  swy = block_sum(swy, red);
+  const float mc = block_min(ml, red);
+  const float sc = (ml == FLT_MAX) ? 0.f : exp2f((mc - ml) * kL2e);
+  sw = block_sum(sw * sc, red);
+  swx = block_sum(swx * sc, red);
+  swy = block_sum(swy * sc, red);
   if (t == 0) {
     float *tc = const_cast<float *>(p.tcen) + 2 * (blockIdx.y * p.tiles_x + blockIdx.x);
     tc[0] = (sw > 0.f) ? Cx + swx / sw : Cx;
