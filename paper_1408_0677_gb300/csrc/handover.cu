@@ -83,13 +83,14 @@ __device__ __forceinline__ df32 df_warp_sum(df32 v) {
 // Near points and their weights.
 
 // Whether a point enters the sums: Gaussian weight above e^-kCut of the
-// largest, or for the truncated Gaussian (cbox = c > 0) inside the box
+// largest, or for the truncated Gaussian (boxed: cbox = c > 0) inside the box
 // |dx|, |dy| < c, every point of which counts (double-float offsets); inside
 // the Wendland support (double-float distance); any point but a coincident
-// one for inverse distance.
+// one for inverse distance.  `boxed` is decided once per walk: a comparison
+// of doubles per candidate took GB300's FP64 pipe a tenth busy.
 template <int WK>
-__device__ __forceinline__ bool near_test(df32 ex, df32 ey, float mhat, double cbox) {
-  if (WK == MLS_W_GAUSS && cbox > 0.0)
+__device__ __forceinline__ bool near_test(df32 ex, df32 ey, float mhat, double cbox, bool boxed) {
+  if (WK == MLS_W_GAUSS && boxed)
     return fabs((double)ex.hi + (double)ex.lo) < cbox && fabs((double)ey.hi + (double)ey.lo) < cbox;
   if (WK == MLS_W_GAUSS) return fmaf(ex.hi, ex.hi, ey.hi * ey.hi) - mhat <= kCut;
   if (WK == MLS_W_WENDLAND) {
@@ -132,6 +133,7 @@ __device__ __forceinline__ int for_near(const KParams &p, const Ranges &R, float
                                         float pyl, float mhat, int lane, int *ri, float4 *rx, int *coincident,
                                         Body body) {
   const unsigned int lt = (1u << lane) - 1u;
+  const bool boxed = WK == MLS_W_GAUSS && p.trunc > 0.0;
   int head = 0, total = 0, coin = 0;
   const int nrow = R.all_n > 0 ? 1 : (R.cx0 <= R.cx1 ? R.cy1 - R.cy0 + 1 : 0);
   // the lanes fetch the index ranges of up to 32 cell rows at once
@@ -156,7 +158,7 @@ __device__ __forceinline__ int for_near(const KParams &p, const Ranges &R, float
       if (i < a1) {
         ex = df_diff(p.xs[i], p.xs_lo[i], pxh, pxl);
         ey = df_diff(p.ys[i], p.ys_lo[i], pyh, pyl);
-        nr = near_test<WK>(ex, ey, mhat, p.trunc);
+        nr = near_test<WK>(ex, ey, mhat, p.trunc, boxed);
         if (WK == MLS_W_INVDIST && !nr) coin = 1;
       }
       const unsigned int bal = __ballot_sync(0xffffffffu, nr);
