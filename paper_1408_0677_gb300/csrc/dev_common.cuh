@@ -113,6 +113,7 @@ struct KParams {
   const float *xs_lo, *ys_lo;  // low parts: xs + xs_lo = (x - ctr) / s to ~48 bits
   const float *FT32;           // normalised values (f - cen) / scl, [D_pad][n_pad]
   const float *FR32;           // the same values point-major, [n_pad][D] (hand-over path)
+  const float *FR32lo;         // their low parts: FR32 + FR32lo = the value to ~48 bits
   const float *fcen32, *fscl32;
   const double *fcen64, *fscl64;   // value centre and half range per dimension (FP64)
   const double *x64, *y64;     // raw positions [n]
@@ -249,6 +250,28 @@ __device__ __forceinline__ df32 df_mul_f(df32 a, float b) {
   const float p = a.hi * b;
   const float e = fmaf(a.hi, b, -p);
   return df_quick(p, fmaf(a.lo, b, e));
+}
+// Double-float helpers without renormalisation, for long accumulations.
+// a * b as an unevaluated pair (p, e)
+__device__ __forceinline__ df32 df_prod(df32 a, df32 b) {
+  const float p = a.hi * b.hi;
+  float e = fmaf(a.hi, b.hi, -p);
+  e = fmaf(a.hi, b.lo, e);
+  e = fmaf(a.lo, b.hi, e);
+  return {p, e};
+}
+__device__ __forceinline__ df32 df_prod_f(df32 a, float b) {
+  const float p = a.hi * b;
+  const float e = fmaf(a.lo, b, fmaf(a.hi, b, -p));
+  return {p, e};
+}
+// s += x (two-sum on the high parts, low parts summed)
+__device__ __forceinline__ void df_acc(df32 &s, df32 x) {
+  const float t = s.hi + x.hi;
+  const float bb = t - s.hi;
+  const float err = (s.hi - (t - bb)) + (x.hi - bb);
+  s.lo += err + x.lo;
+  s.hi = t;
 }
 // (ahi + alo) - (bhi + blo)
 __device__ __forceinline__ df32 df_diff(float ahi, float alo, float bhi, float blo) {

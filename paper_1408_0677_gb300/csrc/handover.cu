@@ -45,30 +45,8 @@ constexpr float kCut = 40.f;            // Gaussian pairs with (r^2 - m)/h^2 abo
 constexpr double kKappaCentroid = 1e8;
 
 // ---------------------------------------------------------------------------
-// Double-float helpers without renormalisation, for long accumulations.
-
-// a * b as an unevaluated pair (p, e)
-__device__ __forceinline__ df32 df_prod(df32 a, df32 b) {
-  const float p = a.hi * b.hi;
-  float e = fmaf(a.hi, b.hi, -p);
-  e = fmaf(a.hi, b.lo, e);
-  e = fmaf(a.lo, b.hi, e);
-  return {p, e};
-}
-__device__ __forceinline__ df32 df_prod_f(df32 a, float b) {
-  const float p = a.hi * b;
-  const float e = fmaf(a.lo, b, fmaf(a.hi, b, -p));
-  return {p, e};
-}
-// s += x (two-sum on the high parts, low parts summed)
-__device__ __forceinline__ void df_acc(df32 &s, df32 x) {
-  const float t = s.hi + x.hi;
-  const float bb = t - s.hi;
-  const float err = (s.hi - (t - bb)) + (x.hi - bb);
-  s.lo += err + x.lo;
-  s.hi = t;
-}
-// normalised warp-wide sum
+// Normalised warp-wide double-float sum (the accumulation helpers df_prod,
+// df_prod_f and df_acc are shared with the FP64 tier's value sums).
 __device__ __forceinline__ df32 df_warp_sum(df32 v) {
   v = df_two_sum(v.hi, v.lo);
 #pragma unroll

@@ -299,6 +299,7 @@ static mlsk::KParams base_params(const mls_handle *h, const RenderCtx *c, const 
   p.ys_lo = P.ys_lo;
   p.FT32 = P.FT32;
   p.FR32 = P.FR32;
+  p.FR32lo = P.FR32lo;
   p.fcen32 = P.fcen32;
   p.fscl32 = P.fscl32;
   p.fcen64 = P.fcen;

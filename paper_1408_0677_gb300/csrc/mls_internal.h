@@ -23,6 +23,7 @@ struct PointSet {
   double *x64 = nullptr, *y64 = nullptr, *FT64 = nullptr;
   float *xs = nullptr, *ys = nullptr, *FT32 = nullptr;
   float *FR32 = nullptr;             // point-major normalised values (reduced-precision renders)
+  float *FR32lo = nullptr;           // their low parts (FR32 + FR32lo: the values to ~48 bits)
   float *xs_lo = nullptr, *ys_lo = nullptr;
   double *fcen = nullptr, *fscl = nullptr;
   float *fcen32 = nullptr, *fscl32 = nullptr;

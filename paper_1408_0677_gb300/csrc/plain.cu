@@ -279,6 +279,78 @@ __device__ __forceinline__ T warp_sum(T v) {
 constexpr int kF64Slots = 24;                  // cache entries per lane
 constexpr int kF64SmemBytes = 8 * kF64Slots * 32 * (4 + 8);
 
+// Degree policy of the FP64 definition on the distinct moments S (every lane
+// of a warp, identical arithmetic): the highest degree whose support count
+// suffices, whose equilibrated matrix factorises and whose rcond_1 reaches
+// rcond_min.  Returns the degree (-1: none) and, with k its basis terms, the
+// fit's weights on the right-hand sides, zc_c = s_0 (Me^-1)_c0 s_c with s
+// the equilibration (the value is sum_c zc_c R_c: column 0 of the inverse,
+// the one solve Me z = e_0, whose rounding grows with the condition once).
+template <int DEG>
+__device__ __forceinline__ int f64_policy(const double (&S)[15], int64_t count, double rcond_min, double (&zc)[6],
+                                          int &k_out) {
+  int used = -1;
+  for (int deg = DEG; deg >= 0 && used < 0; --deg) {
+    const int k = n_terms(deg);
+    if (count < k) continue;
+    double Mm[6][6], sdg[6], Me[6][6], Lm[6][6];
+    bool ok = true;
+    for (int a = 0; a < k; ++a)
+      for (int b = 0; b < k; ++b) Mm[a][b] = S[midx(a, b)];
+    for (int a = 0; a < k && ok; ++a) {
+      if (!(Mm[a][a] > 0.0)) ok = false;
+      else sdg[a] = 1.0 / sqrt(Mm[a][a]);
+    }
+    if (!ok) continue;
+    for (int a = 0; a < k; ++a)
+      for (int b = 0; b < k; ++b) Me[a][b] = Mm[a][b] * sdg[a] * sdg[b];
+    // Cholesky
+    for (int j = 0; j < k && ok; ++j) {
+      double s = Me[j][j];
+      for (int tt = 0; tt < j; ++tt) s -= Lm[j][tt] * Lm[j][tt];
+      if (!(s > 0.0)) { ok = false; break; }
+      const double ljj = sqrt(s);
+      Lm[j][j] = ljj;
+      for (int i2 = j + 1; i2 < k; ++i2) {
+        double vv = Me[i2][j];
+        for (int tt = 0; tt < j; ++tt) vv -= Lm[i2][tt] * Lm[j][tt];
+        Lm[i2][j] = vv / ljj;
+      }
+    }
+    if (!ok) continue;
+    // inverse, rcond_1
+    double Inv[6][6];
+    for (int c = 0; c < k; ++c) {
+      double col[6];
+      for (int a = 0; a < k; ++a) col[a] = (a == c) ? 1.0 : 0.0;
+      for (int i2 = 0; i2 < k; ++i2) {
+        double vv = col[i2];
+        for (int tt = 0; tt < i2; ++tt) vv -= Lm[i2][tt] * col[tt];
+        col[i2] = vv / Lm[i2][i2];
+      }
+      for (int i2 = k - 1; i2 >= 0; --i2) {
+        double vv = col[i2];
+        for (int tt = i2 + 1; tt < k; ++tt) vv -= Lm[tt][i2] * col[tt];
+        col[i2] = vv / Lm[i2][i2];
+      }
+      for (int a = 0; a < k; ++a) Inv[a][c] = col[a];
+    }
+    double nA = 0.0, nI = 0.0;
+    for (int c = 0; c < k; ++c) {
+      double sa = 0.0, si = 0.0;
+      for (int a = 0; a < k; ++a) { sa += fabs(Me[a][c]); si += fabs(Inv[a][c]); }
+      nA = fmax(nA, sa);
+      nI = fmax(nI, si);
+    }
+    const double rc = 1.0 / (nA * nI);
+    if (!(rc >= rcond_min)) continue;
+    for (int c = 0; c < k; ++c) zc[c] = sdg[0] * Inv[c][0] * sdg[c];
+    used = deg;
+    k_out = k;
+  }
+  return used;
+}
+
 template <int DEG, int WK, typename OutT>
 __global__ __launch_bounds__(256) void k_mls_f64(KParams p, int64_t npix_all) {
   constexpr int NM = n_moments(DEG), DC = kF64DC;
@@ -350,7 +422,7 @@ __global__ __launch_bounds__(256) void k_mls_f64(KParams p, int64_t npix_all) {
     int ncache = 0;
     bool cached = false;
     int used_saved = -1, k_saved = 1;
-    double sdg_saved[6], inv0_saved[6];
+    double zc_saved[6];
     for (int d0 = 0; d0 < p.D; d0 += DC) {
       double R[6][DC], csum[DC];
       int64_t ccnt = 0;
@@ -492,79 +564,21 @@ __global__ __launch_bounds__(256) void k_mls_f64(KParams p, int64_t npix_all) {
 #pragma unroll
           for (int dd = 0; dd < DC; ++dd) {
             double acc = 0.0;
-            for (int c = 0; c < k_saved; ++c) acc += sdg_saved[0] * inv0_saved[c] * sdg_saved[c] * R[c][dd];
+            for (int c = 0; c < k_saved; ++c) acc += zc_saved[c] * R[c][dd];
             out[dd] = acc;
           }
         }
       } else {
-        for (int deg = DEG; deg >= 0 && used < 0; --deg) {
-          const int k = n_terms(deg);
-          if (count < k) continue;
-          double Mm[6][6], sdg[6], Me[6][6], Lm[6][6];
-          bool ok = true;
-          for (int a = 0; a < k; ++a)
-            for (int b = 0; b < k; ++b) Mm[a][b] = S[midx(a, b)];
-          for (int a = 0; a < k && ok; ++a) {
-            if (!(Mm[a][a] > 0.0)) ok = false;
-            else sdg[a] = 1.0 / sqrt(Mm[a][a]);
-          }
-          if (!ok) continue;
-          for (int a = 0; a < k; ++a)
-            for (int b = 0; b < k; ++b) Me[a][b] = Mm[a][b] * sdg[a] * sdg[b];
-          // Cholesky
-          for (int j = 0; j < k && ok; ++j) {
-            double s = Me[j][j];
-            for (int tt = 0; tt < j; ++tt) s -= Lm[j][tt] * Lm[j][tt];
-            if (!(s > 0.0)) { ok = false; break; }
-            const double ljj = sqrt(s);
-            Lm[j][j] = ljj;
-            for (int i2 = j + 1; i2 < k; ++i2) {
-              double vv = Me[i2][j];
-              for (int tt = 0; tt < j; ++tt) vv -= Lm[i2][tt] * Lm[j][tt];
-              Lm[i2][j] = vv / ljj;
-            }
-          }
-          if (!ok) continue;
-          // inverse, rcond_1
-          double Inv[6][6];
-          for (int c = 0; c < k; ++c) {
-            double col[6];
-            for (int a = 0; a < k; ++a) col[a] = (a == c) ? 1.0 : 0.0;
-            for (int i2 = 0; i2 < k; ++i2) {
-              double vv = col[i2];
-              for (int tt = 0; tt < i2; ++tt) vv -= Lm[i2][tt] * col[tt];
-              col[i2] = vv / Lm[i2][i2];
-            }
-            for (int i2 = k - 1; i2 >= 0; --i2) {
-              double vv = col[i2];
-              for (int tt = i2 + 1; tt < k; ++tt) vv -= Lm[tt][i2] * col[tt];
-              col[i2] = vv / Lm[i2][i2];
-            }
-            for (int a = 0; a < k; ++a) Inv[a][c] = col[a];
-          }
-          double nA = 0.0, nI = 0.0;
-          for (int c = 0; c < k; ++c) {
-            double sa = 0.0, si = 0.0;
-            for (int a = 0; a < k; ++a) { sa += fabs(Me[a][c]); si += fabs(Inv[a][c]); }
-            nA = fmax(nA, sa);
-            nI = fmax(nI, si);
-          }
-          const double rc = 1.0 / (nA * nI);
-          if (!(rc >= p.rcond_min)) continue;
+        double zc[6];
+        used = f64_policy<DEG>(S, count, p.rcond_min, zc, k_saved);
+        if (used >= 0) {
 #pragma unroll
           for (int dd = 0; dd < DC; ++dd) {
             double acc = 0.0;
-            // z = column 0 of the inverse (the one solve Me z = e_0): its
-            // rounding grows with the condition once, not with its square
-            for (int c = 0; c < k; ++c) acc += sdg[0] * Inv[c][0] * sdg[c] * R[c][dd];
+            for (int c = 0; c < k_saved; ++c) acc += zc[c] * R[c][dd];
             out[dd] = acc;
           }
-          used = deg;
-          k_saved = k;
-          for (int c = 0; c < k; ++c) {
-            sdg_saved[c] = sdg[c];
-            inv0_saved[c] = Inv[c][0];
-          }
+          for (int c = 0; c < k_saved; ++c) zc_saved[c] = zc[c];
         }
         used_saved = used;
       }
@@ -643,6 +657,233 @@ __global__ void k_bands(const T *field, const double *lev64, const float *lev32,
   }
 }
 
+// FP64 monomials of degree <= 4 of (dx, dy) in the moment index order, as
+// k_mls_f64 forms them.
+template <int NM>
+__device__ __forceinline__ void monomials64(double dx, double dy, double (&mo)[15]) {
+  mo[0] = 1.0;
+  if (NM > 1) {
+    mo[1] = dx; mo[2] = dy; mo[3] = dx * dx; mo[4] = dx * dy; mo[5] = dy * dy;
+  }
+  if (NM > 6) {
+    mo[6] = mo[3] * dx; mo[7] = mo[3] * dy; mo[8] = mo[5] * dx; mo[9] = mo[5] * dy;
+    mo[10] = mo[3] * mo[3]; mo[11] = mo[3] * mo[4]; mo[12] = mo[3] * mo[5];
+    mo[13] = mo[4] * mo[5]; mo[14] = mo[5] * mo[5];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// The last tier of a reduced-precision render's hand-over (the pixels still
+// ill conditioned in the centroid frame, or whose support count is in doubt):
+// the weights, support count, moments and degree policy of the FP64
+// definition as k_mls_f64 forms them, then the value as sum_i phi_i f_id
+// with the shape functions phi_i = w_i (zc . b(x_i)) formed in FP64 and the
+// sums over the points in double-float on the FP32 pipes, lanes over the
+// dimensions.  k_mls_f64 instead accumulates every right-hand side
+// R_ad = sum w_i b_a f_id in FP64: six FP64 multiply-adds per point and
+// dimension, which took this tier a sixth of the 200k-point render on
+// GB300's FP64 units.  The sums here carry about 2^-46 of sum |phi_i f_id|
+// (the fit's Lebesgue sum, in units of the value range), the values
+// (FR32 + FR32lo) about 2^-48 each: far inside the reduced precisions'
+// tolerance.  Gaussian and Wendland weights (inverse-distance pixels on a
+// data point take k_mls_f64).
+template <int DEG, int WK>
+__global__ __launch_bounds__(256) void k_mls_f64v(KParams p) {
+  constexpr int NM = n_moments(DEG);
+  constexpr int kVL = 2;   // value dimensions per lane per sweep
+  static_assert(WK != MLS_W_INVDIST, "inverse distance takes k_mls_f64");
+  const int lane = threadIdx.x & 31;
+  extern __shared__ __align__(16) unsigned char f64_smem[];
+  double *c_w = (double *)f64_smem + (size_t)(threadIdx.x >> 5) * kF64Slots * 32;            // [slot][lane]
+  int *c_i = (int *)(f64_smem + (size_t)8 * kF64Slots * 32 * 8) + (size_t)(threadIdx.x >> 5) * kF64Slots * 32;
+  const int64_t warp0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int64_t npix = (int64_t)*p.list_count < p.list_cap ? (int64_t)*p.list_count : p.list_cap;
+  const size_t plane = (size_t)p.W * p.H;
+  const double inv_s = 1.0 / p.h;
+  const double h2 = p.h * p.h;
+  const int64_t n = p.n;
+  float *field = (float *)p.field;
+  const bool binned = (WK == MLS_W_WENDLAND) || (WK == MLS_W_GAUSS && p.trunc > 0.0);
+  const double rho = p.trunc * p.h;
+  const bool reach = (WK == MLS_W_GAUSS) && !binned && p.cell_start != nullptr;
+
+  for (int64_t q = warp0; q < npix; q += nwarps) {
+    const int64_t id = list_i(p, p.list[list_i(p, q)]);
+    const int u = (int)(id % p.W), v = (int)(id / p.W);
+    // the same expression order as the FP64 definition, without contraction
+    const double px = __dadd_rn(p.x0, __dmul_rn(__dadd_rn((double)u, 0.5), p.sx));
+    const double py = __dadd_rn(p.y0, __dmul_rn(__dadd_rn((double)v, 0.5), p.sy));
+    const float mhat = (WK == MLS_W_GAUSS) ? p.mstab[pix_i(p, (int64_t)v * (p.tiles_x * 16) + u)] : 0.f;
+    int nr = 1, cx0 = 0, cx1 = 0, cy0 = 0;
+    if (binned || reach) {
+      const double rad = (WK == MLS_W_WENDLAND) ? p.h
+                         : binned ? rho * (1.0 + 1e-5)
+                                  : p.h * sqrt(fmax((double)mhat, 0.0) + kGaussCut + 1.0) * (1.0 + 1e-5);
+      int cy1;
+      cell_range_d(px, px, rad, p.gx0, p.inv_cell, p.gx, cx0, cx1);
+      cell_range_d(py, py, rad, p.gy0, p.inv_cell, p.gy, cy0, cy1);
+      nr = (cx0 <= cx1) ? max(cy1 - cy0 + 1, 0) : 0;
+    }
+    const double m = (WK == MLS_W_GAUSS) ? (double)mhat * h2 : 0.0;
+    const float pxs = scaled_px(p, u), pys = scaled_py(p, v);
+    // the weight of candidate i (0: outside the support or the sums), with
+    // its scaled offsets; *counted when it enters the support count
+    auto weight = [&](int64_t i, bool *counted, double *ddx, double *ddy) -> double {
+      *counted = false;
+      if (WK == MLS_W_GAUSS && !binned) {
+        // conservative FP32 test before any FP64 work on far pairs
+        const float dxs = p.xs[i] - pxs, dys = p.ys[i] - pys;
+        if (fmaf(dxs, dxs, dys * dys) - mhat > (float)kGaussCut + 1.f) {
+          *counted = true;
+          return 0.0;
+        }
+      }
+      const double dx = __dadd_rn(p.x64[i], -px), dy = __dadd_rn(p.y64[i], -py);
+      const double r2 = __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy));
+      *ddx = dx * inv_s;
+      *ddy = dy * inv_s;
+      if (WK == MLS_W_GAUSS) {
+        if (binned && !(fabs(dx) < rho && fabs(dy) < rho)) return 0.0;
+        *counted = true;
+        if (r2 - m > kGaussCut * h2) return 0.0;
+        return exp(-(r2 - m) / h2);
+      }
+      if (r2 < h2) {
+        const double qd = sqrt(r2) / p.h;
+        const double o = 1.0 - qd;
+        *counted = true;
+        return o * o * o * o * (4.0 * qd + 1.0);
+      }
+      return 0.0;
+    };
+    // ---- weights, support count and moments (FP64, lanes over the points);
+    // the lane's positive-weight points are cached for the value sweeps
+    double S[15];
+#pragma unroll
+    for (int j = 0; j < 15; ++j) S[j] = 0.0;
+    int64_t count = 0;
+    int ncache = 0;
+    for (int r = 0; r < nr; ++r) {
+      const int64_t a0 = (binned || reach) ? cell_at(p, (int64_t)(cy0 + r) * p.gx + cx0) : 0;
+      const int64_t a1 = (binned || reach) ? cell_at(p, (int64_t)(cy0 + r) * p.gx + cx1 + 1) : n;
+      for (int64_t i = a0 + lane; i < a1; i += 32) {
+        bool counted;
+        double ddx = 0.0, ddy = 0.0;
+        const double w = weight(i, &counted, &ddx, &ddy);
+        if (counted) ++count;
+        if (w == 0.0) continue;
+        if (ncache < kF64Slots) {
+          c_w[ncache * 32 + lane] = w;
+          c_i[ncache * 32 + lane] = (int)i;
+        }
+        ++ncache;
+        double mo[15];
+        monomials64<NM>(ddx, ddy, mo);
+#pragma unroll
+        for (int j = 0; j < NM; ++j) S[j] += w * mo[j];
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < NM; ++j) S[j] = warp_sum(S[j]);
+    count = warp_sum(count);
+    if (WK == MLS_W_GAUSS && !binned) count = n;   // every point has positive weight
+    double zc[6];
+    int k = 1;
+    const int used = f64_policy<DEG>(S, count, p.rcond_min, zc, k);
+    if (used < 0) {
+      for (int d = lane; d < p.D; d += 32) {
+        field[(size_t)d * plane + id] = __int_as_float(0x7fc00000);
+        if (p.bands) p.bands[(size_t)d * plane + id] = 255;
+      }
+      if (lane == 0 && p.status) p.status[id] = MLS_ST_NO_SUPPORT | MLS_ST_RECOMPUTED;
+      continue;
+    }
+    const bool cached = __all_sync(0xffffffffu, ncache <= kF64Slots);
+    int nbatch = ncache;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) nbatch = max(nbatch, __shfl_xor_sync(0xffffffffu, nbatch, o));
+    // phi of a point with weight w at scaled offset (ddx, ddy), double-float
+    auto phi_of = [&](double w, double ddx, double ddy) -> df32 {
+      double mo[15];
+      monomials64<NM>(ddx, ddy, mo);
+      double zb = 0.0;
+      for (int c = 0; c < k; ++c) zb += zc[c] * mo[c];
+      const double ph = w * zb;
+      const float hi = (float)ph;
+      return {hi, (float)(ph - (double)hi)};
+    };
+    // one batch of up to 32 points (lane j's point, valid), summed into the
+    // lanes' dimensions
+    auto sum_batch = [&](bool valid, int idx, df32 phi, int d0, df32 (&acc)[kVL]) {
+      const unsigned int vm = __ballot_sync(0xffffffffu, valid);
+      for (unsigned int mm = vm; mm; mm &= mm - 1) {
+        const int jj = __ffs(mm) - 1;
+        const df32 ph = {__shfl_sync(0xffffffffu, phi.hi, jj), __shfl_sync(0xffffffffu, phi.lo, jj)};
+        const int ij = __shfl_sync(0xffffffffu, idx, jj);
+        const float *fh = p.FR32 + (size_t)ij * p.D + d0 + lane;
+        const float *fl = p.FR32lo + (size_t)ij * p.D + d0 + lane;
+#pragma unroll
+        for (int t = 0; t < kVL; ++t)
+          if (d0 + lane + 32 * t < p.D) df_acc(acc[t], df_prod(ph, {fh[32 * t], fl[32 * t]}));
+      }
+    };
+    // ---- values (lanes over the dimensions)
+    for (int d0 = 0; d0 < p.D; d0 += 32 * kVL) {
+      df32 acc[kVL];
+#pragma unroll
+      for (int t = 0; t < kVL; ++t) acc[t] = {0.f, 0.f};
+      if (cached) {
+        for (int b = 0; b < nbatch; ++b) {
+          const bool valid = b < ncache;
+          df32 phi = {0.f, 0.f};
+          int idx = 0;
+          if (valid) {
+            idx = c_i[b * 32 + lane];
+            const double dx = __dadd_rn(p.x64[idx], -px), dy = __dadd_rn(p.y64[idx], -py);
+            phi = phi_of(c_w[b * 32 + lane], dx * inv_s, dy * inv_s);
+          }
+          sum_batch(valid, idx, phi, d0, acc);
+        }
+      } else {
+        for (int r = 0; r < nr; ++r) {
+          const int64_t a0 = (binned || reach) ? cell_at(p, (int64_t)(cy0 + r) * p.gx + cx0) : 0;
+          const int64_t a1 = (binned || reach) ? cell_at(p, (int64_t)(cy0 + r) * p.gx + cx1 + 1) : n;
+          for (int64_t base = a0; base < a1; base += 32) {
+            const int64_t i = base + lane;
+            bool valid = false;
+            df32 phi = {0.f, 0.f};
+            if (i < a1) {
+              bool counted;
+              double ddx = 0.0, ddy = 0.0;
+              const double w = weight(i, &counted, &ddx, &ddy);
+              if (w != 0.0) {
+                valid = true;
+                phi = phi_of(w, ddx, ddy);
+              }
+            }
+            sum_batch(valid, (int)i, phi, d0, acc);
+          }
+        }
+      }
+#pragma unroll
+      for (int t = 0; t < kVL; ++t) {
+        const int d = d0 + lane + 32 * t;
+        if (d < p.D) {
+          // fcen + fscl acc in double-float, rounded to float at the end
+          const df32 sv = df_prod_f(df_two_sum(acc[t].hi, acc[t].lo), p.fscl32[d]);
+          const df32 fs = df_add({p.fcen32[d], 0.f}, sv);
+          const float f = fs.hi + fs.lo;
+          field[(size_t)d * plane + id] = f;
+          if (p.bands) p.bands[(size_t)d * plane + id] = band_of(f, p.lev32 + (size_t)d * p.L, p.L);
+        }
+      }
+    }
+    if (lane == 0 && p.status)
+      p.status[id] = (uint8_t)(used | MLS_ST_RECOMPUTED | (used < DEG ? MLS_ST_DEGRADED : 0));
+  }
+}
+
 template <int DEG>
 void f32_dispatch_w(const KParams &p, cudaStream_t st) {
   // block shapes 16 x 8 (every weight), 8 x 8 and 8 x 4 (the Gaussian)
@@ -666,6 +907,19 @@ void f64_dispatch_w(const KParams &p, int64_t npix, cudaStream_t st) {
   if (p.list) grid = 152 * 8;
   else grid = (int)std::min<int64_t>((npix + 7) / 8, 152 * 64);
   if (grid < 1) grid = 1;
+  // a reduced-precision render's last hand-over tier: FP64 moments and
+  // policy, double-float value sums (inverse distance keeps k_mls_f64)
+  if (p.list && sizeof(OutT) == 4 && p.FR32 && p.FR32lo && p.weight != MLS_W_INVDIST) {
+    if (p.weight == MLS_W_GAUSS) {
+      cudaFuncSetAttribute(k_mls_f64v<DEG, MLS_W_GAUSS>, cudaFuncAttributeMaxDynamicSharedMemorySize, kF64SmemBytes);
+      k_mls_f64v<DEG, MLS_W_GAUSS><<<grid, 256, kF64SmemBytes, st>>>(p);
+    } else {
+      cudaFuncSetAttribute(k_mls_f64v<DEG, MLS_W_WENDLAND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           kF64SmemBytes);
+      k_mls_f64v<DEG, MLS_W_WENDLAND><<<grid, 256, kF64SmemBytes, st>>>(p);
+    }
+    return;
+  }
   if (p.weight == MLS_W_GAUSS) {
     cudaFuncSetAttribute(k_mls_f64<DEG, MLS_W_GAUSS, OutT>, cudaFuncAttributeMaxDynamicSharedMemorySize, kF64SmemBytes);
     k_mls_f64<DEG, MLS_W_GAUSS, OutT><<<grid, 256, kF64SmemBytes, st>>>(p, npix);

@@ -193,14 +193,18 @@ __global__ void k_gather_transpose(const double *xy, const double *F, int64_t n,
 __global__ void k_finish(const double *x64, const double *y64, const double *FT64, int64_t n, int64_t n_pad,
                          int D, int D_pad, double ctr_x, double ctr_y, double inv_s, const double *cen,
                          const double *scl, float *xs, float *ys, float *FT32, float *xs_lo, float *ys_lo,
-                         float *FR32) {
+                         float *FR32, float *FR32lo) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int d = blockIdx.y;
   if (i >= n_pad) return;
-  float v = 0.f;
-  if (d < D && i < n) v = (float)((FT64[(int64_t)d * n + i] - cen[d]) / scl[d]);
+  double vd = 0.0;
+  if (d < D && i < n) vd = (FT64[(int64_t)d * n + i] - cen[d]) / scl[d];
+  const float v = (float)vd;
   FT32[(int64_t)d * n_pad + i] = v;
-  if (FR32 && d < D) FR32[i * D + d] = v;
+  if (FR32 && d < D) {
+    FR32[i * D + d] = v;
+    FR32lo[i * D + d] = (float)(vd - (double)v);
+  }
   if (d == 0) {
     const double X = (i < n) ? (x64[i] - ctr_x) * inv_s : 0.0;
     const double Y = (i < n) ? (y64[i] - ctr_y) * inv_s : 0.0;
@@ -286,6 +290,7 @@ mls_status prep_points(mls_handle *h, const double *xy, const double *F, cudaStr
   const size_t o_xs_lo = cv.add(sizeof(float) * P.n_pad), o_ys_lo = cv.add(sizeof(float) * P.n_pad);
   const size_t o_FT32 = cv.add(sizeof(float) * P.n_pad * P.D_pad);
   const size_t o_FR32 = d.precision != MLS_P_FP64 ? cv.add(sizeof(float) * P.n_pad * D) : 0;
+  const size_t o_FR32lo = d.precision != MLS_P_FP64 ? cv.add(sizeof(float) * P.n_pad * D) : 0;
   const size_t o_fcen = cv.add(sizeof(double) * D), o_fscl = cv.add(sizeof(double) * D);
   const size_t o_fcen32 = cv.add(sizeof(float) * D), o_fscl32 = cv.add(sizeof(float) * D);
   const size_t o_key = binned ? cv.add(sizeof(int) * n) : 0;
@@ -305,7 +310,10 @@ mls_status prep_points(mls_handle *h, const double *xy, const double *F, cudaStr
   P.xs_lo = (float *)(blk + o_xs_lo);
   P.ys_lo = (float *)(blk + o_ys_lo);
   P.FT32 = (float *)(blk + o_FT32);
-  if (d.precision != MLS_P_FP64) P.FR32 = (float *)(blk + o_FR32);
+  if (d.precision != MLS_P_FP64) {
+    P.FR32 = (float *)(blk + o_FR32);
+    P.FR32lo = (float *)(blk + o_FR32lo);
+  }
   P.fcen = (double *)(blk + o_fcen);
   P.fscl = (double *)(blk + o_fscl);
   P.fcen32 = (float *)(blk + o_fcen32);
@@ -408,7 +416,8 @@ mls_status prep_points(mls_handle *h, const double *xy, const double *F, cudaStr
     ++h->launches;
     dim3 g2((unsigned)((P.n_pad + 255) / 256), (unsigned)P.D_pad);
     k_finish<<<g2, 256, 0, st>>>(P.x64, P.y64, P.FT64, n, P.n_pad, D, P.D_pad, P.ctr_x, P.ctr_y, 1.0 / P.s,
-                                 P.fcen, P.fscl, P.xs, P.ys, P.FT32, P.xs_lo, P.ys_lo, P.FR32);
+                                 P.fcen, P.fscl, P.xs, P.ys, P.FT32, P.xs_lo, P.ys_lo, P.FR32,
+                                 P.FR32lo);
     ++h->launches;
     MLS_CUDA_TRY(cudaGetLastError());
   }
