@@ -188,30 +188,61 @@ __global__ void k_gather_transpose(const double *xy, const double *F, int64_t n,
   }
 }
 
-// FP32 layouts: scaled positions and normalised values, zero padded;
-// optionally the values point-major as well.
+// FP32 layouts: scaled positions and normalised values (f - cen) / scl,
+// zero padded, dimension-major [D_pad][n_pad]; for the reduced precisions
+// the same values point-major [n_pad][D] as hi + lo floats as well (the
+// hand-over paths read all dimensions of one point at a time).  A block
+// takes 32 points x 32 dimensions: the dimension-major reads and writes are
+// coalesced along the points, the point-major writes along the dimensions
+// through a transpose in shared memory.  The block forms 1/scl once per
+// dimension (GB300's FP64 divisions are slow: one per value bound the
+// kernel).
 __global__ void k_finish(const double *x64, const double *y64, const double *FT64, int64_t n, int64_t n_pad,
                          int D, int D_pad, double ctr_x, double ctr_y, double inv_s, const double *cen,
                          const double *scl, float *xs, float *ys, float *FT32, float *xs_lo, float *ys_lo,
                          float *FR32, float *FR32lo) {
-  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  const int d = blockIdx.y;
-  if (i >= n_pad) return;
-  double vd = 0.0;
-  if (d < D && i < n) vd = (FT64[(int64_t)d * n + i] - cen[d]) / scl[d];
-  const float v = (float)vd;
-  FT32[(int64_t)d * n_pad + i] = v;
-  if (FR32 && d < D) {
-    FR32[i * D + d] = v;
-    FR32lo[i * D + d] = (float)(vd - (double)v);
+  __shared__ double tile[32][33];
+  __shared__ double s_cen[32], s_rs[32];
+  const int64_t i0 = (int64_t)blockIdx.x * 32;
+  const int d0 = blockIdx.y * 32;
+  const int tx = threadIdx.x;
+  if (threadIdx.y == 0) {
+    const int d = d0 + tx;
+    s_cen[tx] = d < D ? cen[d] : 0.0;
+    s_rs[tx] = d < D ? 1.0 / scl[d] : 0.0;
   }
-  if (d == 0) {
-    const double X = (i < n) ? (x64[i] - ctr_x) * inv_s : 0.0;
-    const double Y = (i < n) ? (y64[i] - ctr_y) * inv_s : 0.0;
-    xs[i] = (float)X;
-    ys[i] = (float)Y;
-    xs_lo[i] = (float)(X - (double)(float)X);
-    ys_lo[i] = (float)(Y - (double)(float)Y);
+  __syncthreads();
+  for (int k = threadIdx.y; k < 32; k += blockDim.y) {   // tile rows: dimensions
+    const int d = d0 + k;
+    const int64_t i = i0 + tx;
+    double v = 0.0;
+    if (d < D && i < n) v = (FT64[(int64_t)d * n + i] - s_cen[k]) * s_rs[k];
+    if (d < D_pad && i < n_pad) FT32[(int64_t)d * n_pad + i] = (float)v;
+    tile[k][tx] = v;
+  }
+  if (blockIdx.y == 0 && threadIdx.y == 0) {
+    const int64_t i = i0 + tx;
+    if (i < n_pad) {
+      const double X = (i < n) ? (x64[i] - ctr_x) * inv_s : 0.0;
+      const double Y = (i < n) ? (y64[i] - ctr_y) * inv_s : 0.0;
+      xs[i] = (float)X;
+      ys[i] = (float)Y;
+      xs_lo[i] = (float)(X - (double)(float)X);
+      ys_lo[i] = (float)(Y - (double)(float)Y);
+    }
+  }
+  if (FR32) {
+    __syncthreads();
+    for (int k = threadIdx.y; k < 32; k += blockDim.y) {   // tile rows: points
+      const int64_t i = i0 + k;
+      const int d = d0 + tx;
+      if (i < n_pad && d < D) {
+        const double v = tile[tx][k];
+        const float h = (float)v;
+        FR32[i * D + d] = h;
+        FR32lo[i * D + d] = (float)(v - (double)h);
+      }
+    }
   }
 }
 
@@ -414,10 +445,10 @@ mls_status prep_points(mls_handle *h, const double *xy, const double *F, cudaStr
     dim3 g((unsigned)((n + 31) / 32), (unsigned)((D + 31) / 32));
     k_gather_transpose<<<g, dim3(32, 8), 0, st>>>(xy, F, n, D, perm, P.x64, P.y64, P.FT64);
     ++h->launches;
-    dim3 g2((unsigned)((P.n_pad + 255) / 256), (unsigned)P.D_pad);
-    k_finish<<<g2, 256, 0, st>>>(P.x64, P.y64, P.FT64, n, P.n_pad, D, P.D_pad, P.ctr_x, P.ctr_y, 1.0 / P.s,
-                                 P.fcen, P.fscl, P.xs, P.ys, P.FT32, P.xs_lo, P.ys_lo, P.FR32,
-                                 P.FR32lo);
+    dim3 g2((unsigned)((P.n_pad + 31) / 32), (unsigned)((P.D_pad + 31) / 32));
+    k_finish<<<g2, dim3(32, 8), 0, st>>>(P.x64, P.y64, P.FT64, n, P.n_pad, D, P.D_pad, P.ctr_x, P.ctr_y,
+                                         1.0 / P.s, P.fcen, P.fscl, P.xs, P.ys, P.FT32, P.xs_lo, P.ys_lo, P.FR32,
+                                         P.FR32lo);
     ++h->launches;
     MLS_CUDA_TRY(cudaGetLastError());
   }
