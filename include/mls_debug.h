@@ -53,6 +53,14 @@ int mls_debug_operand_cut(struct mls_handle *h, int32_t on);
  * argument below -1, MLS_OK otherwise. */
 int mls_debug_handover_split(struct mls_handle *h, int64_t cap, int64_t least);
 
+/* Page-locked host outputs of mls_render (on_device = 0): with a field of at
+ * most 256 MiB the kernels write them directly; above it the render goes to
+ * device staging and one copy kernel writes them.  mode 1 takes the staged
+ * copy and mode 2 the direct writes for the handle's later renders whatever
+ * the size, so that a test can check both; 0 restores the choice by size.
+ * Returns MLS_E_INVAL for a null handle or another mode, MLS_OK otherwise. */
+int mls_debug_host_output(struct mls_handle *h, int32_t mode);
+
 #ifdef __cplusplus
 }
 #endif

@@ -163,6 +163,8 @@ def load(path: str | None = None):
     lib.mls_debug_operand_cut.argtypes = [P, ctypes.c_int32]
     lib.mls_debug_handover_split.restype = ctypes.c_int
     lib.mls_debug_handover_split.argtypes = [P, ctypes.c_int64, ctypes.c_int64]
+    lib.mls_debug_host_output.restype = ctypes.c_int
+    lib.mls_debug_host_output.argtypes = [P, ctypes.c_int32]
     lib.mls_debug_df_weight.restype = ctypes.c_int
     lib.mls_debug_df_weight.argtypes = [ctypes.c_int, P, P, ctypes.c_int64, P]
     if default:

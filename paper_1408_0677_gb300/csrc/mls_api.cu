@@ -489,6 +489,10 @@ namespace mlsi {
 // buffer and the copy engines refuse it, so it is rejected.
 enum HostKind { HOST_PAGEABLE, HOST_MAPPED, HOST_STRADDLES };
 
+// Largest field written into page-locked host memory by the kernels
+// themselves (256 MiB; above it the render is staged and copied).
+constexpr size_t kDirectOutMaxBytes = (size_t)256 << 20;
+
 static HostKind host_kind(void *ptr, size_t bytes, int device, void **dev) {
   *dev = nullptr;
   if (!ptr || bytes == 0) return HOST_PAGEABLE;
@@ -532,6 +536,7 @@ static mls_status render_prepare(mls_handle *h, RenderCtx *c, const mls_view *vi
   void *field_d = field;
   uint8_t *status_d = status, *bands_d = bands;
   c->direct_out = false;
+  c->copy_out = false;
   if (!on_device) {
     // Page-locked host outputs are written by the kernels directly (over
     // NVLink-C2C on GB300, overlapped with the render); other host memory is
@@ -543,12 +548,25 @@ static mls_status render_prepare(mls_handle *h, RenderCtx *c, const mls_view *vi
     if (fk == HOST_STRADDLES || sk == HOST_STRADDLES || bk == HOST_STRADDLES)
       return fail(MLS_E_INVAL, "a host output starts in page-locked memory but runs past its page-locked "
                                "block; pass it wholly inside one page-locked block, or in pageable memory");
-    c->direct_out = fm && (!status || sm) && (!bands || bm);
+    // Page-locked outputs (all those given).  Small ones are written by the
+    // kernels directly, overlapped with the render.  Large ones are rendered
+    // into device staging and copied afterwards by a kernel through their
+    // device addresses: the hand-over's writes are scattered (one pixel of
+    // every dimension plane at a time), and over NVLink-C2C scattered writes
+    // of a large render cost more than one coalesced copy.
+    const bool mapped = fm && (!status || sm) && (!bands || bm);
+    const size_t fbytes = plane * h->desc.D * esz;
+    const bool large = h->out_mode == 1 || (h->out_mode == 0 && fbytes > kDirectOutMaxBytes);
+    c->direct_out = mapped && !large;
+    c->copy_out = mapped && large;
     if (c->direct_out) {
       field_d = fm;
       status_d = (uint8_t *)sm;
       bands_d = (uint8_t *)bm;
     }
+    c->out_dev[0] = fm;
+    c->out_dev[1] = sm;
+    c->out_dev[2] = bm;
   }
   if (!on_device && !c->direct_out) {
     const size_t fbytes = (plane * h->desc.D * esz + 255) / 256 * 256;
@@ -712,7 +730,12 @@ mls_status mls_render(mls_handle *h, const mls_view *view, void *field, uint8_t 
   if (!on_device) {
     const size_t plane = (size_t)view->W * view->H;
     const size_t esz = field_is_fp64(h->desc.precision) ? sizeof(double) : sizeof(float);
-    if (!h->ctx.direct_out) {
+    if (h->ctx.copy_out) {
+      launch_copy(h->ctx.out_dev[0], p.field, plane * h->desc.D * esz, st);
+      if (status) launch_copy(h->ctx.out_dev[1], p.status, plane, st);
+      if (bands) launch_copy(h->ctx.out_dev[2], p.bands, plane * h->desc.D, st);
+      MLS_CUDA_TRY(cudaGetLastError());
+    } else if (!h->ctx.direct_out) {
       MLS_CUDA_TRY(cudaMemcpyAsync(field, p.field, plane * h->desc.D * esz, cudaMemcpyDeviceToHost, st));
       if (status) MLS_CUDA_TRY(cudaMemcpyAsync(status, p.status, plane, cudaMemcpyDeviceToHost, st));
       if (bands) MLS_CUDA_TRY(cudaMemcpyAsync(bands, p.bands, plane * h->desc.D, cudaMemcpyDeviceToHost, st));
@@ -811,6 +834,13 @@ mls_status mls_sync(mls_handle *h, double timeout_s, mls_stats *stats) {
 int mls_debug_operand_cut(mls_handle *h, int32_t on) {
   if (!h) return fail(MLS_E_INVAL, "handle is NULL");
   h->operand_cut = on != 0;
+  return MLS_OK;
+}
+
+int mls_debug_host_output(mls_handle *h, int32_t mode) {
+  if (!h) return fail(MLS_E_INVAL, "handle is NULL");
+  if (mode < 0 || mode > 2) return fail(MLS_E_INVAL, "mode must be 0, 1 or 2");
+  h->out_mode = mode;
   return MLS_OK;
 }
 

@@ -63,6 +63,8 @@ struct RenderCtx {
   void *stage = nullptr;             // staging for host-pointer calls
   size_t stage_bytes = 0;
   bool direct_out = false;           // host outputs written by the kernels themselves
+  bool copy_out = false;             // page-locked host outputs filled from the staging by a copy kernel
+  void *out_dev[3] = {nullptr, nullptr, nullptr};   // their device addresses (field, status, bands)
 };
 
 // Bytes of the scratch a W x H render needs (see ensure_scratch).
@@ -86,6 +88,7 @@ struct mls_handle {
   bool operand_cut = true;           // reduced-precision Gaussian: skip pairs whose weight rounds to zero
   int64_t ho_cap_limit = -1;         // test hooks: split hand-over capacity limit (-1: none)
   int64_t ho_least = -1;             // and shortest list it takes (-1: kHandoverSplitLeast)
+  int32_t out_mode = 0;              // test hook: page-locked outputs 0 by size, 1 staged + copy, 2 direct
 };
 
 namespace mlsi {
@@ -99,6 +102,8 @@ void launch_prepass(const mlsk::KParams &p, cudaStream_t st);
 void launch_f32(const mlsk::KParams &p, cudaStream_t st);
 void launch_f64(const mlsk::KParams &p, int64_t npix, cudaStream_t st);
 void launch_bands(const mlsk::KParams &p, bool fp64, cudaStream_t st);
+// device-to-host copy by a kernel (dst: page-locked host memory's device address)
+void launch_copy(void *dst, const void *src, size_t bytes, cudaStream_t st);
 // rigid / mean-displacement mappings (KParams.variant), FP64 or FP32
 void launch_variant(const mlsk::KParams &p, bool fp64, cudaStream_t st);
 // handover.cu: ill-conditioned pixels of the reduced-precision renders

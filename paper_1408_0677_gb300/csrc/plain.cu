@@ -955,6 +955,27 @@ void launch_f64(const KParams &p, int64_t npix, cudaStream_t st) {
   }
 }
 
+// Device-to-host copy by the SMs (the destination is page-locked host memory
+// through its device address): 16-byte loads and stores when both ends are
+// 16-byte aligned, 4-byte ones when both are 4-byte aligned, else bytes.
+__global__ void k_copy(void *dst, const void *src, size_t bytes) {
+  const size_t tid = blockIdx.x * (size_t)blockDim.x + threadIdx.x, nt = (size_t)gridDim.x * blockDim.x;
+  const uintptr_t a = (uintptr_t)dst | (uintptr_t)src;
+  if ((a & 15) == 0) {
+    const size_t nv = bytes / 16;
+    uint4 *d = (uint4 *)dst;
+    const uint4 *s = (const uint4 *)src;
+    for (size_t k = tid; k < nv; k += nt) d[k] = s[k];
+    for (size_t k = nv * 16 + tid; k < bytes; k += nt) ((char *)dst)[k] = ((const char *)src)[k];
+  } else if ((a & 3) == 0) {
+    const size_t nv = bytes / 4;
+    for (size_t k = tid; k < nv; k += nt) ((unsigned *)dst)[k] = ((const unsigned *)src)[k];
+    for (size_t k = nv * 4 + tid; k < bytes; k += nt) ((char *)dst)[k] = ((const char *)src)[k];
+  } else {
+    for (size_t k = tid; k < bytes; k += nt) ((char *)dst)[k] = ((const char *)src)[k];
+  }
+}
+
 void launch_bands(const KParams &p, bool fp64, cudaStream_t st) {
   const int64_t plane = (int64_t)p.W * p.H;
   // blocks of 256 threads, four values per thread and pass, at most 1024
@@ -964,6 +985,13 @@ void launch_bands(const KParams &p, bool fp64, cudaStream_t st) {
   const size_t sm = (size_t)p.L * (fp64 ? 8 : 4) + 16;
   if (fp64) k_bands<double><<<grid, 256, sm, st>>>((const double *)p.field, p.lev64, p.lev32, p.L, plane, p.D, p.bands);
   else k_bands<float><<<grid, 256, sm, st>>>((const float *)p.field, p.lev64, p.lev32, p.L, plane, p.D, p.bands);
+}
+
+void launch_copy(void *dst, const void *src, size_t bytes, cudaStream_t st) {
+  if (bytes == 0) return;
+  const size_t chunks = (bytes + 15) / 16;
+  const size_t blocks = (chunks + 255) / 256;
+  k_copy<<<(unsigned)(blocks < 152 * 8 ? (blocks < 1 ? 1 : blocks) : 152 * 8), 256, 0, st>>>(dst, src, bytes);
 }
 
 }  // namespace mlsi

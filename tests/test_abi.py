@@ -130,6 +130,7 @@ def test_null_arguments(lib):
     assert lib.mls_debug_df_weight(0, None, None, 4, None) == _abi.MLS_E_INVAL
     assert lib.mls_debug_df_weight(0, None, None, 0, None) == _abi.MLS_OK
     assert lib.mls_debug_handover_split(None, 0, 0) == _abi.MLS_E_INVAL
+    assert lib.mls_debug_host_output(None, 1) == _abi.MLS_E_INVAL
 
 
 def test_injected_allocation_failure_returns_nomem(lib, monkeypatch):

@@ -199,13 +199,18 @@ def test_host_pointer_path_matches_device_path(precision):
     assert np.array_equal(host["status"], dev["status"])
 
 
+@pytest.mark.parametrize("mode", [0, 1, 2], ids=["by-size", "staged-copy", "direct"])
 @pytest.mark.parametrize("precision", ["fp64", "fp32", "fp16"])
-def test_page_locked_host_outputs_match_device_path(precision):
-    """Page-locked host outputs are written by the kernels directly (no
-    staging copy); the result is the device path's, bit for bit."""
+def test_page_locked_host_outputs_match_device_path(precision, mode):
+    """Page-locked host outputs are written by the kernels directly (small
+    renders) or by one copy kernel from device staging (large renders; mode
+    1 forces it, mode 2 forces the direct writes); the result is the device
+    path's, bit for bit."""
+    import ctypes
+
     import torch
 
-    from paper_1408_0677_gb300 import Renderer
+    from paper_1408_0677_gb300 import Renderer, _abi
     wl = inputs.small_random(24, 120, 3, 33, 27, 1, G, 0.1)
     dev = gpu_render(wl, precision)
     fdt = torch.float64 if precision == "fp64" else torch.float32
@@ -213,6 +218,7 @@ def test_page_locked_host_outputs_match_device_path(precision):
     status = torch.full((wl.H, wl.W), 77, dtype=torch.uint8).pin_memory().numpy()
     bands = torch.full((wl.D, wl.H, wl.W), 77, dtype=torch.uint8).pin_memory().numpy()
     r = Renderer(wl.xy, wl.F, degree=1, weight=G, h=0.1, precision=precision)
+    assert _abi.load().mls_debug_host_output(ctypes.c_void_p(r.handle), mode) == _abi.MLS_OK
     r.render_host(wl.W, wl.H, levels=wl.levels, field=field, bands=bands, status_out=status)
     r.close()
     assert np.array_equal(field, dev["field"], equal_nan=True)
