@@ -14,9 +14,28 @@
 #include <thread>
 #include <vector>
 
+#if __has_include(<nvtx3/nvToolsExt.h>)
+#include <nvtx3/nvToolsExt.h>
+#define MLS_HAVE_NVTX 1
+#endif
+
 #include "mls_internal.h"
 
 namespace mlsi {
+
+// A named NVTX range around each public call, for profilers and timeline
+// tools (header-only NVTX: with no tool attached the calls do nothing; a
+// toolkit without the NVTX headers builds the ranges as no-ops).
+struct NvtxRange {
+#ifdef MLS_HAVE_NVTX
+  explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+#else
+  explicit NvtxRange(const char *) {}
+#endif
+  NvtxRange(const NvtxRange &) = delete;
+  NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 static thread_local std::string g_err;
 
@@ -393,6 +412,7 @@ mls_status mls_desc_default(mls_desc *desc) {
 
 mls_status mls_create(const mls_desc *desc, const double *xy, const double *F, int32_t on_device, void *stream,
                       mls_handle **out) {
+  mlsi::NvtxRange nvtx_range("mls_create");
   g_err.clear();
   if (!out) return fail(MLS_E_INVAL, "out is NULL");
   *out = nullptr;
@@ -717,6 +737,7 @@ extern "C" {
 
 mls_status mls_render(mls_handle *h, const mls_view *view, void *field, uint8_t *status, const double *levels,
                       int32_t L, uint8_t *bands, int32_t on_device, void *stream) {
+  mlsi::NvtxRange nvtx_range("mls_render");
   g_err.clear();
   cudaStream_t st = (cudaStream_t)stream;
   mlsk::KParams p;
@@ -753,6 +774,7 @@ mls_status mls_render(mls_handle *h, const mls_view *view, void *field, uint8_t 
 
 mls_status mls_bands(mls_handle *h, const mls_view *view, const void *field, const double *levels, int32_t L,
                      uint8_t *bands, int32_t on_device, void *stream) {
+  mlsi::NvtxRange nvtx_range("mls_bands");
   g_err.clear();
   if (!h) return fail(MLS_E_INVAL, "handle is NULL");
   mls_status s = check_view(view);
@@ -790,6 +812,7 @@ mls_status mls_bands(mls_handle *h, const mls_view *view, const void *field, con
 }
 
 mls_status mls_sync(mls_handle *h, double timeout_s, mls_stats *stats) {
+  mlsi::NvtxRange nvtx_range("mls_sync");
   g_err.clear();
   if (!h) return fail(MLS_E_INVAL, "handle is NULL");
   if (!(timeout_s > 0.0)) return fail(MLS_E_INVAL, "timeout_s must be > 0");
@@ -853,6 +876,7 @@ int mls_debug_handover_split(mls_handle *h, int64_t cap, int64_t least) {
 }
 
 mls_status mls_destroy(mls_handle *h) {
+  mlsi::NvtxRange nvtx_range("mls_destroy");
   g_err.clear();
   if (!h) return MLS_OK;
   cudaStream_t st = h->stream;
@@ -1011,6 +1035,7 @@ static mls_status batch_tune(mls_batch *b, const mls_view *views, void *const *f
 extern "C" {
 
 mls_status mls_batch_create(int32_t count, mls_handle *const *handles, int32_t flags, mls_batch **out) {
+  mlsi::NvtxRange nvtx_range("mls_batch_create");
   g_err.clear();
   if (!out) return fail(MLS_E_INVAL, "out is NULL");
   *out = nullptr;
@@ -1046,6 +1071,7 @@ mls_status mls_batch_create(int32_t count, mls_handle *const *handles, int32_t f
 
 mls_status mls_batch_render(mls_batch *b, const mls_view *views, void *const *fields, uint8_t *const *status,
                             const double *const *levels, const int32_t *L, uint8_t *const *bands, void *stream) {
+  mlsi::NvtxRange nvtx_range("mls_batch_render");
   g_err.clear();
   if (!b || !views || !fields) return fail(MLS_E_INVAL, "batch, views and fields must not be NULL");
   const size_t n = b->hs.size();
@@ -1126,6 +1152,7 @@ mls_status mls_batch_render(mls_batch *b, const mls_view *views, void *const *fi
 }
 
 mls_status mls_batch_sync(mls_batch *b, double timeout_s, mls_batch_stats *stats) {
+  mlsi::NvtxRange nvtx_range("mls_batch_sync");
   g_err.clear();
   if (!b) return fail(MLS_E_INVAL, "batch is NULL");
   const auto t0 = std::chrono::steady_clock::now();
@@ -1168,6 +1195,7 @@ mls_status mls_batch_sync(mls_batch *b, double timeout_s, mls_batch_stats *stats
 }
 
 mls_status mls_batch_destroy(mls_batch *b) {
+  mlsi::NvtxRange nvtx_range("mls_batch_destroy");
   g_err.clear();
   if (!b) return MLS_OK;
   if (b->timed) cudaEventSynchronize(b->ev1);
@@ -1353,6 +1381,7 @@ static void serve_loop(mls_server *sv) {
 extern "C" {
 
 mls_status mls_server_create(const mls_server_config *cfg, mls_server **out) {
+  mlsi::NvtxRange nvtx_range("mls_server_create");
   g_err.clear();
   if (!out || !cfg) return fail(MLS_E_INVAL, "cfg and out must not be NULL");
   *out = nullptr;
@@ -1389,6 +1418,7 @@ mls_status mls_server_create(const mls_server_config *cfg, mls_server **out) {
 }
 
 mls_status mls_server_submit(mls_server *sv, const mls_request *req, int64_t *id) {
+  mlsi::NvtxRange nvtx_range("mls_server_submit");
   g_err.clear();
   if (!sv || !req || !id) return fail(MLS_E_INVAL, "server, request and id must not be NULL");
   if (!req->dataset) return fail(MLS_E_INVAL, "request has no dataset");
@@ -1427,6 +1457,7 @@ mls_status mls_server_poll(mls_server *sv, mls_request_done *done, int32_t cap, 
 }
 
 mls_status mls_server_drain(mls_server *sv, double timeout_s, mls_server_stats *stats) {
+  mlsi::NvtxRange nvtx_range("mls_server_drain");
   g_err.clear();
   if (!sv) return fail(MLS_E_INVAL, "server is NULL");
   const auto t0 = Clock::now();
@@ -1447,6 +1478,7 @@ mls_status mls_server_drain(mls_server *sv, double timeout_s, mls_server_stats *
 }
 
 mls_status mls_server_destroy(mls_server *sv) {
+  mlsi::NvtxRange nvtx_range("mls_server_destroy");
   g_err.clear();
   if (!sv) return MLS_OK;
   {
