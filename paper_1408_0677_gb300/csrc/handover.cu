@@ -985,10 +985,12 @@ __global__ __launch_bounds__(kWarps * 32, 4) void k_handover(KParams p, const in
 }
 
 template <int DEG, int WK>
-void launch_dw(const KParams &p, const int *list, const unsigned int *cnt, int64_t cap, int64_t split_cap,
-               int64_t least, void *state, unsigned int *claims, int *list2, unsigned int *cnt2, cudaStream_t st) {
+int launch_dw(const KParams &p, const int *list, const unsigned int *cnt, int64_t cap, int64_t split_cap,
+              int64_t least, void *state, unsigned int *claims, int *list2, unsigned int *cnt2, cudaStream_t st) {
   const int64_t sc = state ? (split_cap < cap ? split_cap : cap) : 0;
+  int launches = 1;
   if (sc > 0) {
+    launches += 4;
     HoEntry *E = (HoEntry *)state;
     // one resident wave each: 4 blocks of 128 threads per SM for the setup,
     // 8 for the warp phases (entries claimed dynamically), 16 one-warp
@@ -1002,28 +1004,29 @@ void launch_dw(const KParams &p, const int *list, const unsigned int *cnt, int64
   // capacity (one resident wave: 4 blocks of 4 warps per SM; every block
   // returns at once when there are none)
   k_handover<DEG, WK><<<152 * 4, kWarps * 32, 0, st>>>(p, list, cnt, sc, least, cap, list2, cnt2);
+  return launches;
 }
 
 template <int WK>
-void launch_w(const KParams &p, const int *list, const unsigned int *cnt, int64_t cap, int64_t split_cap,
-              int64_t least, void *state, unsigned int *claims, int *list2, unsigned int *cnt2, cudaStream_t st) {
-  if (p.degree == 0) launch_dw<0, WK>(p, list, cnt, cap, split_cap, least, state, claims, list2, cnt2, st);
-  else if (p.degree == 1) launch_dw<1, WK>(p, list, cnt, cap, split_cap, least, state, claims, list2, cnt2, st);
-  else launch_dw<2, WK>(p, list, cnt, cap, split_cap, least, state, claims, list2, cnt2, st);
+int launch_w(const KParams &p, const int *list, const unsigned int *cnt, int64_t cap, int64_t split_cap,
+             int64_t least, void *state, unsigned int *claims, int *list2, unsigned int *cnt2, cudaStream_t st) {
+  if (p.degree == 0) return launch_dw<0, WK>(p, list, cnt, cap, split_cap, least, state, claims, list2, cnt2, st);
+  if (p.degree == 1) return launch_dw<1, WK>(p, list, cnt, cap, split_cap, least, state, claims, list2, cnt2, st);
+  return launch_dw<2, WK>(p, list, cnt, cap, split_cap, least, state, claims, list2, cnt2, st);
 }
 
 }  // namespace
 
 size_t handover_entry_bytes() { return sizeof(HoEntry); }
 
-void launch_handover(const KParams &p, const int *list, const unsigned int *cnt, int64_t cap, int64_t split_cap,
-                     int64_t least, void *state, unsigned int *claims, int *list2, unsigned int *cnt2,
-                     cudaStream_t st) {
+int launch_handover(const KParams &p, const int *list, const unsigned int *cnt, int64_t cap, int64_t split_cap,
+                    int64_t least, void *state, unsigned int *claims, int *list2, unsigned int *cnt2,
+                    cudaStream_t st) {
   if (p.weight == MLS_W_GAUSS)
-    launch_w<MLS_W_GAUSS>(p, list, cnt, cap, split_cap, least, state, claims, list2, cnt2, st);
-  else if (p.weight == MLS_W_WENDLAND)
-    launch_w<MLS_W_WENDLAND>(p, list, cnt, cap, split_cap, least, state, claims, list2, cnt2, st);
-  else launch_w<MLS_W_INVDIST>(p, list, cnt, cap, split_cap, least, state, claims, list2, cnt2, st);
+    return launch_w<MLS_W_GAUSS>(p, list, cnt, cap, split_cap, least, state, claims, list2, cnt2, st);
+  if (p.weight == MLS_W_WENDLAND)
+    return launch_w<MLS_W_WENDLAND>(p, list, cnt, cap, split_cap, least, state, claims, list2, cnt2, st);
+  return launch_w<MLS_W_INVDIST>(p, list, cnt, cap, split_cap, least, state, claims, list2, cnt2, st);
 }
 
 // Test hook: the double-float weight functions on given arguments.

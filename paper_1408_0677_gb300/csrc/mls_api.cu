@@ -709,13 +709,13 @@ static mls_status render_enqueue(mls_handle *h, RenderCtx *c, const mlsk::KParam
         if (timing) MLS_CUDA_TRY(cudaEventRecord(h->evk1, st));
       }
     }
-    launches += 2;
     // pixels handed over by the reduced-precision path: centroid-frame
-    // recompute, and the pure FP64 kernel for what is left
+    // recompute, and the FP64 tier for what is left
     const int64_t split_cap = h->ho_cap_limit >= 0 && h->ho_cap_limit < c->ho_cap ? h->ho_cap_limit : c->ho_cap;
     const int64_t least = h->ho_least >= 0 ? h->ho_least : kHandoverSplitLeast;
-    launch_handover(p, c->relist, c->counters, (int64_t)plane, split_cap, least, c->ho_state, c->ho_claims,
-                    c->relist2, c->counters + 1, st);
+    launches += launch_handover(p, c->relist, c->counters, (int64_t)plane, split_cap, least, c->ho_state,
+                                c->ho_claims, c->relist2, c->counters + 1, st) +
+                1;
     mlsk::KParams q = p;
     q.list = c->relist2;
     q.list_count = c->counters + 1;

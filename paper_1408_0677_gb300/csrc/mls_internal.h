@@ -111,9 +111,10 @@ void launch_variant(const mlsk::KParams &p, bool fp64, cudaStream_t st);
 // entries through four kernels whose per-entry state, handover_entry_bytes()
 // each, is at `state`, with two zeroed claim counters at `claims`; shorter
 // lists and the rest through one fused kernel)
-void launch_handover(const mlsk::KParams &p, const int *list, const unsigned int *cnt, int64_t cap,
-                     int64_t split_cap, int64_t least, void *state, unsigned int *claims, int *list2,
-                     unsigned int *cnt2, cudaStream_t st);
+// Returns the kernels launched.
+int launch_handover(const mlsk::KParams &p, const int *list, const unsigned int *cnt, int64_t cap,
+                    int64_t split_cap, int64_t least, void *state, unsigned int *claims, int *list2,
+                    unsigned int *cnt2, cudaStream_t st);
 // the shortest list the split kernels take: one chunk of 32 pixels for each
 // of the fused kernel's 608 blocks (below it the fused kernel is faster)
 constexpr int64_t kHandoverSplitLeast = 608 * 32;
